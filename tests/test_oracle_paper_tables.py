@@ -1,0 +1,64 @@
+"""The oracle against the numbers the paper prints for its worked example
+(Section 5, Tables 1 and 5), stored in tests/golden with their citation.
+
+The coarse-space sizes #V_0 and n_- are exact integers fixed by A, the
+subdomains and tau: they pin the splitting (Def. 5), the eigen-split
+(Def. 6) and the GenEO selection (Def. 9, Thm. 4) together.  The condition
+number and the iteration count are printed to two or three digits; they are
+checked to that precision (kappa within 5 %, It within 2, because the
+Lanczos estimate of lambda_min is taken from the run's own coefficients).
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import awg_inputs as gi
+import oracle as O
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                   "paper_elasticity_tables.json")))
+
+_CACHE = {}
+
+
+def _setup(layers, E1, E2):
+    key = (layers, E1, E2)
+    if key not in _CACHE:
+        p = gi.paper_elasticity(layers=layers, E1=E1, E2=E2)
+        _CACHE[key] = (p, O.setup_problem(p))
+    return _CACHE[key]
+
+
+def test_paper_mesh_size():
+    """h = 1/21 on [0,3]^2 with the left edge clamped gives n = 8064 (Section 5)."""
+    p = gi.paper_elasticity(6)
+    assert p.n == 8064
+    assert len(p.subsets) == 9
+
+
+@pytest.mark.parametrize("case", GOLD["cases"], ids=[c["where"] for c in GOLD["cases"]])
+def test_paper_tables(case):
+    p, st = _setup(case["layers"], case["E1"], case["E2"])
+    assert st.n0 == case["n0"]
+    assert st.n_minus == case["n_minus"]
+    M = (lambda r: O.H3_ad_apply(st, r)) if case["variant"] == "H3_ad" else \
+        (lambda r: O.H3_hyb_apply(st, r))
+    res = O.pcg(lambda v: st.A @ v, p.b, M, rtol=1e-10, norm="preconditioned")
+    assert abs(res.iters - case["It"]) <= 2
+    lo, hi = O.lanczos_extremes(res.alphas, res.betas)
+    assert lo >= 1.0 - 1e-6  # Thm. 8 with H^NN: lambda_min >= 1
+    kappa = hi / lo
+    assert abs(kappa - case["kappa"]) <= 0.05 * case["kappa"]
+    if "lambda_max" in case:
+        assert abs(hi - case["lambda_max"]) <= 0.05 * case["lambda_max"]
+
+
+def test_paper_central_subdomain_modes():
+    """Fig. 3: the central subdomain selects 9 vectors, 8 of them for a zero
+    GenEO eigenvalue (a negative eigenvalue of B^s) and one more."""
+    p, st = _setup(6, 1e11, 1e7)
+    assert st.splits[4].n_strict == 8
+    assert st.Y[4].shape[1] == 9

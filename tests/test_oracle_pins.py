@@ -1,0 +1,440 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks one oracle function against something other than itself:
+an exact identity stated by a theorem of the paper, a closed form, brute
+force on tiny inputs, a dense inverse, or an independent library routine.
+"""
+
+import itertools
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import awg_inputs as gi
+import oracle as O
+
+
+def _tiny_problems():
+    return [
+        gi.poisson2d(12, qx=2, overlap=1, tau=0.1, seed=0),
+        gi.poisson2d(10, ny=9, qx=3, qy=2, overlap=2, tau=0.2, seed=1),
+        gi.channels2d(24, q=3, nchan=3, contrast=1e3, seed=5, overlap=2, tau=0.1),
+        gi.random_spd(60, nparts=4, density=0.06, seed=3, overlap=1, tau=0.1),
+    ]
+
+
+TINY = _tiny_problems()
+
+
+@pytest.fixture(scope="module", params=range(len(TINY)), ids=[p.name for p in TINY])
+def tiny(request):
+    p = TINY[request.param]
+    st = O.setup_problem(p, dense=True)
+    return p, st
+
+
+# ----------------------------------------------------------------------------
+# Section 2: subdomains, minimal overlap, partition of unity
+# ----------------------------------------------------------------------------
+
+def test_overlap_growth_bruteforce():
+    """Omega^s after k layers = dofs within graph distance k of the owned
+    set, computed by breadth-first search in plain Python."""
+    p = gi.poisson2d(9, qx=3, overlap=2)
+    A = O.csr_from(p.rowptr, p.colidx, p.val, p.n)
+    subs = O.grow_subdomains(A, p.part, p.nparts, 2)
+    nbrs = [set(p.colidx[p.rowptr[i]:p.rowptr[i + 1]].tolist()) for i in range(p.n)]
+    for s in range(p.nparts):
+        dist = {i: 0 for i in range(p.n) if p.part[i] == s}
+        frontier = list(dist)
+        for lvl in (1, 2):
+            nxt = []
+            for i in frontier:
+                for j in nbrs[i]:
+                    if j not in dist:
+                        dist[j] = lvl
+                        nxt.append(j)
+            frontier = nxt
+        assert sorted(dist) == subs[s].tolist()
+
+
+def test_minimal_overlap_detects_violation():
+    """Assumption 1 holds after one layer of growth and fails without it
+    for a box partition (edges that cross a box boundary are uncovered);
+    the splitting of Def. 5 must then refuse to divide by M_mu = 0."""
+    p = gi.poisson2d(8, qx=2, overlap=1)
+    A = O.csr_from(p.rowptr, p.colidx, p.val, p.n)
+    s1 = O.grow_subdomains(A, p.part, p.nparts, 1)
+    s0 = O.grow_subdomains(A, p.part, p.nparts, 0)
+    assert O.minimal_overlap_holds(A, s1)
+    assert not O.minimal_overlap_holds(A, s0)
+    with pytest.raises(ValueError):
+        O.splitting_matrix(A, O.pair_multiplicity(A, s0))
+
+
+def test_partition_of_unity(tiny):
+    """eq. (POU): sum_s R^sT D^s R^s = I, and D^s entries are inverse
+    multiplicities (Def. 3)."""
+    p, st = tiny
+    S = np.zeros((st.n, st.n))
+    for idx, Ds in zip(st.subs, st.Ds):
+        S[idx, idx] += Ds
+    assert np.max(np.abs(S - np.eye(st.n))) < 1e-15
+    mult = np.zeros(st.n)
+    for idx in st.subs:
+        mult[idx] += 1
+    assert np.array_equal(st.d, 1.0 / mult)
+
+
+def test_pair_multiplicity_bruteforce():
+    """M_mu(i, j) = #{s : {i, j} in Omega^s} for stored A_ij (proof of Thm. 1),
+    counted by Python loops over the sets."""
+    p = gi.random_spd(30, nparts=3, density=0.1, seed=7, overlap=1)
+    A = O.csr_from(p.rowptr, p.colidx, p.val, p.n)
+    subs = O.grow_subdomains(A, p.part, p.nparts, 1)
+    M = O.pair_multiplicity(A, subs).toarray()
+    sets = [set(s.tolist()) for s in subs]
+    for i in range(p.n):
+        for k in range(p.rowptr[i], p.rowptr[i + 1]):
+            j = p.colidx[k]
+            assert M[i, j] == sum(1 for s in sets if i in s and j in s)
+    Ad = A.toarray()
+    assert np.all(M[Ad == 0] == 0)
+
+
+# ----------------------------------------------------------------------------
+# Section 3.1-3.2: splitting, eigen-split, A_+ and A_-
+# ----------------------------------------------------------------------------
+
+def test_thm1_splitting_sums_to_A(tiny):
+    """Thm. 1: A = sum_s R^sT B^s R^s (to rounding of the division)."""
+    p, st = tiny
+    S = np.zeros((st.n, st.n))
+    for idx in st.subs:
+        S[np.ix_(idx, idx)] += O.local_B(st.B, idx)
+    Ad = st.A.toarray()
+    assert np.all(np.abs(S - Ad) <= 8 * np.finfo(float).eps * np.abs(Ad) + 1e-300)
+
+
+def test_eigen_split_local_identities(tiny):
+    """Def. 6 and Section 4.4 item 3: B^s = A^s_+ - A^s_-, both SPSD,
+    A^s_+ = P B^s P and (A^s_+)^dagger = P (B^s)^dagger P with
+    P = I - V^s_- V^s_-^T (pseudo-inverse from numpy.linalg.pinv)."""
+    p, st = tiny
+    for idx, spl in zip(st.subs, st.splits):
+        Bs = O.local_B(st.B, idx)
+        Ap, Am = spl.A_plus(), spl.A_minus()
+        nB = np.linalg.norm(Bs, 2)
+        assert np.linalg.norm(Bs - (Ap - Am), 2) < 1e-11 * nB
+        assert np.linalg.eigvalsh(Ap).min() > -1e-12 * nB
+        assert np.linalg.eigvalsh(Am).min() > -1e-12 * nB
+        P = np.eye(len(idx)) - spl.V_minus @ spl.V_minus.T
+        assert np.linalg.norm(Ap - P @ Bs @ P, 2) < 1e-12 * nB
+        if spl.n_minus == spl.n_strict:  # B^s non-singular
+            Bp = np.linalg.pinv(Bs)
+            Pinv = spl.A_plus_pinv()
+            assert np.linalg.norm(Pinv - P @ Bp @ P, 2) < 1e-9 * np.linalg.norm(Pinv, 2)
+
+
+def test_thm2_and_rank_bound(tiny):
+    """Thm. 2: A = A_+ - A_-, A_- SPSD, A_+ SPD; Thm. 6: rank A_- = n_- <=
+    sum n^s - n."""
+    p, st = tiny
+    Ap = O.assemble_dense(st, "plus")
+    Am = O.assemble_dense(st, "minus")
+    Ad = st.A.toarray()
+    nA = np.linalg.norm(Ad, 2)
+    assert np.linalg.norm(Ad - (Ap - Am), 2) < 1e-11 * nA
+    ev_m = np.linalg.eigvalsh(Am)
+    assert ev_m.min() > -1e-12 * nA
+    assert np.linalg.eigvalsh(Ap).min() > 0
+    rank = int(np.sum(ev_m > 1e-10 * nA))
+    assert rank == st.n_minus
+    assert st.n_minus <= sum(len(s) for s in st.subs) - st.n
+
+
+def test_local_A_plus_block_formula(tiny):
+    """Section 4.4 item 4: R^s A_+ R^sT from A and the neighbours' V^t_-
+    equals the block of the densely assembled A_+."""
+    p, st = tiny
+    Ap = O.assemble_dense(st, "plus")
+    for s, idx in enumerate(st.subs):
+        blk = O.local_A_plus_block(st, s)
+        assert np.allclose(blk, Ap[np.ix_(idx, idx)], rtol=0, atol=1e-12 * np.abs(Ap).max())
+
+
+# ----------------------------------------------------------------------------
+# Section 3.3-3.4: H^NN and the GenEO coarse space
+# ----------------------------------------------------------------------------
+
+def test_HNN_definition_and_spd(tiny):
+    """Def. 8 with (A^s_+)^dagger from numpy.linalg.pinv; Lemma 1: SPD."""
+    p, st = tiny
+    H = O.dense_operator(lambda X: O.H_NN_apply(st, X), st.n)
+    Href = np.zeros((st.n, st.n))
+    for idx, Ds, spl in zip(st.subs, st.Ds, st.splits):
+        pinv = np.linalg.pinv(spl.A_plus(), rcond=1e-10, hermitian=True)
+        Href[np.ix_(idx, idx)] += (Ds[:, None] * pinv) * Ds[None, :]
+    assert np.linalg.norm(H - Href, 2) < 1e-8 * np.linalg.norm(Href, 2)
+    assert np.allclose(H, H.T, atol=1e-12 * np.abs(H).max())
+    assert np.linalg.eigvalsh(0.5 * (H + H.T)).min() > 0
+
+
+def test_Y_L_definition(tiny):
+    """Def. 9: columns are M_B-normalised eigenvectors of (M_A, M_B) with
+    lambda < tau, and every eigenvalue below tau is selected.  The pencil is
+    checked against the standard problem L^-1 M_A L^-T (L the Cholesky factor
+    of M_B), solved separately."""
+    p, st = tiny
+    Ap = O.assemble_dense(st, "plus")
+    for s, (idx, Ds, spl) in enumerate(zip(st.subs, st.Ds, st.splits)):
+        MA = spl.A_plus() / np.outer(Ds, Ds)
+        MB = Ap[np.ix_(idx, idx)]
+        Y = st.Y[s]
+        assert np.allclose(Y.T @ MB @ Y, np.eye(Y.shape[1]), atol=1e-9)
+        L = np.linalg.cholesky(MB)
+        C = np.linalg.solve(L, np.linalg.solve(L, MA).T).T
+        ev = np.linalg.eigvalsh(0.5 * (C + C.T))
+        assert Y.shape[1] == int(np.sum(ev < st.tau))
+        lam = np.diag(Y.T @ MA @ Y)
+        assert np.all(lam < st.tau + 1e-9)
+        assert np.linalg.norm(MA @ Y - MB @ Y * lam, 2) < 1e-8 * np.linalg.norm(MA, 2)
+
+
+def test_kernel_inclusion(tiny):
+    """Remark after Thm. 5: D^s V^s_- lies in range(Y^s) (the kernel of
+    D^s^-1 A^s_+ D^s^-1 is always selected)."""
+    p, st = tiny
+    for Ds, spl, Y in zip(st.Ds, st.splits, st.Y):
+        if spl.n_minus == 0:
+            continue
+        K = Ds[:, None] * spl.V_minus
+        Q, _ = np.linalg.qr(Y)
+        res = K - Q @ (Q.T @ K)
+        assert np.linalg.norm(res) < 1e-8 * np.linalg.norm(K)
+
+
+def _H2A_plus_spectrum(st):
+    H2 = O.dense_operator(lambda X: O.H2_apply(st, X), st.n)
+    Ap = O.assemble_dense(st, "plus")
+    return O.spectrum_HA(0.5 * (H2 + H2.T), Ap), H2, Ap
+
+
+def test_thm4_geneo_bounds(tiny):
+    """Thm. 4: 1 <= lambda(H^NN_hyb(tau) A_+) <= N(A_+)/tau, with N from a
+    valid (greedy) colouring."""
+    p, st = tiny
+    ev, H2, Ap = _H2A_plus_spectrum(st)
+    Ncol = O.colouring_constant(st.subs, O.A_plus_blocks_nonzero_fn(st))
+    assert ev.min() >= 1.0 - 1e-8
+    assert ev.max() <= Ncol / st.tau * (1 + 1e-8)
+
+
+def test_colouring_constant_bruteforce():
+    """Def. 4 on a 2x2 box partition: every pair of subdomains interacts, so
+    the optimal constant is 4 and greedy must find it."""
+    p = gi.poisson2d(8, qx=2, overlap=1)
+    st = O.setup_problem(p, dense=True)
+    pred = O.A_plus_blocks_nonzero_fn(st)
+    Ap = O.assemble_dense(st, "plus")
+    for s, t in itertools.combinations(range(st.N), 2):
+        blk = Ap[np.ix_(st.subs[s], st.subs[t])]
+        assert pred(s, t) == bool(np.any(blk != 0))
+    assert O.colouring_constant(st.subs, pred) == 4
+
+
+# ----------------------------------------------------------------------------
+# Section 4: Woodbury, second coarse space, AWG bounds
+# ----------------------------------------------------------------------------
+
+def test_woodbury_matches_dense_inverse():
+    """eq. (Woodbury) with V_-, L_- from the diagonalisation of A_- (Def. 8)
+    and with the factored form V = Vhat, C = |L^s_-| equals inv(A)."""
+    p = gi.poisson2d(10, qx=2, overlap=1)
+    st = O.setup_problem(p, dense=True)
+    Ad = st.A.toarray()
+    Ap = O.assemble_dense(st, "plus")
+    Am = O.assemble_dense(st, "minus")
+    Ainv = np.linalg.inv(Ad)
+    ev, V = np.linalg.eigh(Am)
+    keep = ev > 1e-10 * np.linalg.norm(Ad, 2)
+    Vm, Lm = V[:, keep], ev[keep]
+    assert Vm.shape[1] == st.n_minus
+    Apinv = np.linalg.inv(Ap)
+    inner = np.diag(1.0 / Lm) - Vm.T @ Apinv @ Vm
+    wood = Apinv + Apinv @ Vm @ np.linalg.solve(inner, Vm.T @ Apinv)
+    assert np.linalg.norm(wood - Ainv, 2) < 1e-10 * np.linalg.norm(Ainv, 2)
+    U = st.Vhat.toarray()
+    C = O.Lambda_strict(st)
+    inner2 = np.diag(1.0 / C) - U.T @ Apinv @ U
+    wood2 = Apinv + Apinv @ U @ np.linalg.solve(inner2, U.T @ Apinv)
+    assert np.linalg.norm(wood2 - Ainv, 2) < 1e-10 * np.linalg.norm(Ainv, 2)
+
+
+def _principal_sines(X, Y):
+    """Largest sine of the principal angles, as the largest singular value
+    of (I - Qx Qx^T) Qy (accurate for small angles)."""
+    Qx, _ = np.linalg.qr(X)
+    Qy, _ = np.linalg.qr(Y)
+    return np.linalg.norm(Qy - Qx @ (Qx.T @ Qy), 2)
+
+
+def test_range_lemma_and_sparse_W(tiny):
+    """Lemma 2: range(A_+^-1 V_-) = range(A^-1 V_-); the sparse route of
+    ``solve_A_plus`` (Woodbury on a sparse LU of A) gives the same W as the
+    dense Cholesky of A_+."""
+    p, st = tiny
+    if st.n_minus == 0:
+        pytest.skip("no negative eigenvalue")
+    Vh = st.Vhat.toarray()
+    X = np.linalg.solve(st.A.toarray(), Vh)
+    assert _principal_sines(st.W, X) < 1e-9
+    st2 = O.setup_problem(p, dense=False)
+    assert np.allclose(st2.W, st.W, rtol=0, atol=1e-9 * np.abs(st.W).max())
+
+
+def test_Pi3_projector(tiny):
+    """Thm. 8: Pi_3 is an A-orthogonal projection with range Ker(A_-) and
+    kernel range(A^-1 V_-)."""
+    p, st = tiny
+    if st.n_minus == 0:
+        pytest.skip("no negative eigenvalue")
+    P = O.dense_operator(lambda X: O.Pi3_apply(st, X), st.n)
+    Ad = st.A.toarray()
+    Am = O.assemble_dense(st, "minus")
+    nA = np.linalg.norm(Ad, 2)
+    assert np.linalg.norm(P @ P - P, 2) < 1e-9
+    AP = Ad @ P
+    assert np.linalg.norm(AP - AP.T, 2) < 1e-9 * nA
+    assert np.linalg.norm(Am @ P, 2) < 1e-9 * nA
+    assert np.linalg.norm(P @ st.W, 2) < 1e-9 * np.linalg.norm(st.W, 2)
+
+
+def test_awg_spectral_bounds(tiny):
+    """Thm. 8 (eqs. H2APi3, H3hybA, H3adA) and Thm. 7 for H_3,inex, with
+    H_2 = H^NN_hyb(tau) so that min(1, lambda_min(H_2 A_+)) = 1."""
+    p, st = tiny
+    ev2, H2, Ap = _H2A_plus_spectrum(st)
+    lo, hi = ev2.min(), ev2.max()
+    Ad = st.A.toarray()
+    tol = 1e-8
+    Had = O.dense_operator(lambda X: O.H3_ad_apply(st, X), st.n)
+    ev = O.spectrum_HA(0.5 * (Had + Had.T), Ad)
+    assert ev.min() >= min(1.0, lo) - tol and ev.min() >= 1 - tol
+    assert ev.max() <= hi + 1 + tol
+    Hh = O.dense_operator(lambda X: O.H3_hyb_apply(st, X), st.n)
+    ev = O.spectrum_HA(0.5 * (Hh + Hh.T), Ad)
+    assert ev.min() >= min(1.0, lo) - tol and ev.max() <= max(1.0, hi) + tol
+    Hi = O.dense_operator(lambda X: O.H3_inex_apply(st, X), st.n)
+    ev = O.spectrum_HA(0.5 * (Hi + Hi.T), Ad)
+    assert ev.min() >= min(1.0, lo) - tol and ev.max() <= max(1.0, hi) + tol
+    if st.n_minus:
+        P3 = O.dense_operator(lambda X: O.Pi3_apply(st, X), st.n)
+        M = H2 @ Ad @ P3
+        evp = np.sort(np.real(np.linalg.eigvals(M)))
+        nz = evp[np.abs(evp) > 1e-6]
+        assert nz.min() >= lo - 1e-6 and nz.max() <= hi + 1e-6
+
+
+# ----------------------------------------------------------------------------
+# Closed-form special cases
+# ----------------------------------------------------------------------------
+
+def test_special_case_huge_tau():
+    """tau above every pencil eigenvalue: V^0 = R^n, so H_2 = A_+^-1 and
+    H_3,hyb = A^-1 exactly; the spectrum of H_3,ad A lies in [1, 2]."""
+    p = gi.poisson2d(8, qx=2, overlap=1)
+    st = O.setup_problem(p, dense=True, tau=1e30, with_W=False)
+    assert st.n0 == sum(len(s) for s in st.subs)  # every eigenvector selected
+    # The selected vectors span R^n but are dependent; Assumption 3 asks for
+    # a basis of V^0, so take an orthonormal one and rebuild E.
+    U, sv, _ = np.linalg.svd(st.Z.toarray(), full_matrices=False)
+    assert np.sum(sv > 1e-10 * sv[0]) == st.n
+    st.Z = sp.csc_matrix(U[:, :st.n])
+    st.E = st.Z.T @ O.A_plus_apply(st, st.Z.toarray())
+    st.E_cho = sla.cho_factor(0.5 * (st.E + st.E.T), lower=True)
+    O.build_W(st)
+    Ad = st.A.toarray()
+    Ap = O.assemble_dense(st, "plus")
+    H2 = O.dense_operator(lambda X: O.H2_apply(st, X), st.n)
+    assert np.linalg.norm(H2 - np.linalg.inv(Ap), 2) < 1e-8 * np.linalg.norm(np.linalg.inv(Ap), 2)
+    Hh = O.dense_operator(lambda X: O.H3_hyb_apply(st, X), st.n)
+    Ainv = np.linalg.inv(Ad)
+    assert np.linalg.norm(Hh - Ainv, 2) < 1e-8 * np.linalg.norm(Ainv, 2)
+    Had = O.dense_operator(lambda X: O.H3_ad_apply(st, X), st.n)
+    ev = O.spectrum_HA(0.5 * (Had + Had.T), Ad)
+    assert ev.min() >= 1 - 1e-8 and ev.max() <= 2 + 1e-8
+
+
+def test_special_case_one_subdomain():
+    """N = 1: M_mu = S(A), B = A, A_- = 0, n_- = 0 and H_3 = H^NN = A^-1."""
+    p = gi.poisson2d(9, qx=1, overlap=0)
+    st = O.setup_problem(p, dense=True)
+    assert st.N == 1 and st.n_minus == 0
+    assert np.array_equal(st.B.toarray(), st.A.toarray())
+    H = O.dense_operator(lambda X: O.H3_ad_apply(st, X), st.n)
+    Ainv = np.linalg.inv(st.A.toarray())
+    assert np.linalg.norm(H - Ainv, 2) < 1e-12 * np.linalg.norm(Ainv, 2)
+
+
+def test_scale_invariance():
+    """A -> cA (Table 5: homogeneous E = 1e11 and 1e7 give identical rows):
+    counts are unchanged and H_3 scales by 1/c."""
+    p = gi.channels2d(24, q=3, nchan=3, contrast=1e3, seed=5, overlap=2)
+    st1 = O.setup_problem(p, dense=True)
+    c = 1e4
+    st2 = O.setup(p.rowptr, p.colidx, p.val * c, p.n, part=p.part, nparts=p.nparts,
+                  overlap=p.overlap, tau=p.tau, dense=True)
+    assert np.array_equal(O.mode_counts(st1), O.mode_counts(st2))
+    assert np.array_equal(O.minus_counts(st1), O.minus_counts(st2))
+    z1 = O.H3_ad_apply(st1, p.b)
+    z2 = O.H3_ad_apply(st2, p.b)
+    assert np.linalg.norm(z1 - c * z2) < 1e-9 * np.linalg.norm(z1)
+
+
+# ----------------------------------------------------------------------------
+# PCG
+# ----------------------------------------------------------------------------
+
+def test_pcg_exact_preconditioner_one_step():
+    """With H = A^-1, PCG converges in one iteration."""
+    p = gi.poisson2d(10, qx=2)
+    A = O.csr_from(p.rowptr, p.colidx, p.val, p.n)
+    lu = spla.splu(A.tocsc())
+    res = O.pcg(lambda v: A @ v, p.b, lu.solve, rtol=1e-12)
+    assert res.iters == 1 and res.converged
+
+
+def test_pcg_distinct_eigenvalues():
+    """CG on a matrix with k distinct eigenvalues terminates in k steps
+    (exact arithmetic); here k = 5 and n = 200."""
+    rng = np.random.default_rng(0)
+    Q, _ = np.linalg.qr(rng.standard_normal((200, 200)))
+    lam = np.repeat([1.0, 2.0, 3.0, 5.0, 8.0], 40)
+    M = (Q * lam) @ Q.T
+    b = rng.standard_normal(200)
+    res = O.pcg(lambda v: M @ v, b, rtol=1e-10)
+    assert res.converged and res.iters <= 6
+    assert np.linalg.norm(M @ res.x - b) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_pcg_matches_scipy_cg():
+    """Same iterates as scipy.sparse.linalg.cg with the same preconditioner
+    (checked through the solution) and Lanczos extremes close to the dense
+    spectrum of H A."""
+    p = gi.poisson2d(12, qx=2, overlap=1)
+    st = O.setup_problem(p, dense=True)
+    A = st.A
+    H = lambda v: O.H2_apply(st, v)
+    res = O.pcg(lambda v: A @ v, p.b, H, rtol=1e-12)
+    Mop = spla.LinearOperator(A.shape, matvec=H)
+    xs, info = spla.cg(A, p.b, M=Mop, rtol=1e-12, maxiter=500)
+    assert info == 0
+    assert np.linalg.norm(res.x - xs) < 1e-9 * np.linalg.norm(xs)
+    Hd = O.dense_operator(lambda X: O.H2_apply(st, X), st.n)
+    ev = np.sort(np.real(np.linalg.eigvals(Hd @ A.toarray())))
+    lo, hi = O.lanczos_extremes(res.alphas, res.betas)
+    assert abs(hi - ev[-1]) < 1e-3 * ev[-1]
