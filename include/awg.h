@@ -1,0 +1,199 @@
+/*
+ * awg.h — C ABI of libawg, a GB300 (sm_103a) implementation of the AWG
+ * (Algebraic-Woodbury-GenEO) preconditioned conjugate gradient method of
+ * Gouarin & Spillane, "Fully algebraic domain decomposition preconditioners
+ * with adaptive spectral bounds" (arXiv 2106.10913).
+ *
+ * The solver knows only a sparse SPD matrix A (Section 1, eq. (Ax=b)), a
+ * non-overlapping owner of every degree of freedom, an overlap width and the
+ * GenEO threshold tau (Thm. 4).  From those it builds, on the device:
+ *   - overlapping subdomains Omega^s (Def. 1, Assumption 1),
+ *   - the partition of unity D^s (Def. 3),
+ *   - the splitting B^s by pair multiplicity (Def. 5, Thm. 1),
+ *   - the eigen-split B^s = A^s_+ - A^s_- (Def. 6) and A_+ (Def. 7, Thm. 2),
+ *   - the one-level H^NN (Def. 8) through a Cholesky factorisation of
+ *     K^s = A^s_+ + sigma V^s_- V^s_-^T (Section 4.4 item 3),
+ *   - the GenEO coarse space and H^NN_hyb(tau) (Def. 9, Thm. 4),
+ *   - the second coarse space W = A_+^-1 [R^sT V^s_-] by multi-right-hand-
+ *     side PCG with H_2 (Section 4.4 items 1-2) and F = W^T A W (Def. 10),
+ * and applies H_3,ad (default), H_3,hyb (Def. 10) or H_3,inex (Thm. 7)
+ * inside PCG.
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named d_* are DEVICE pointers, h_* are HOST pointers.
+ *   - Dense vectors are float64 arrays of length n; several right-hand sides
+ *     are stored column by column with a leading dimension ld >= n.
+ *   - A is CSR with int32 row pointers (length n+1, rowptr[0] = 0) and int32
+ *     column indices (length nnz, sorted in each row, no duplicates, pattern
+ *     structurally symmetric), float64 values.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is ordered on that stream.  awg_setup and awg_pcg*
+ *     synchronise the stream before they return; awg_apply* and awg_spmv do
+ *     not (their status reports argument and launch errors only).
+ *   - Ownership: the caller owns every array it passes and may free it once
+ *     the call returns; the handle owns everything it allocates and frees it
+ *     in awg_destroy.  A handle must not be used from two host threads or on
+ *     two streams at the same time.
+ *   - Errors are returned as awg_status; no call aborts the process.  After
+ *     AWG_ERR_CUDA the handle should be destroyed.
+ */
+#ifndef AWG_H
+#define AWG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct awg_handle_s* awg_handle;
+
+typedef enum {
+    AWG_OK = 0,
+    AWG_ERR_INVALID_ARG = 1,   /* bad size, pointer or option */
+    AWG_ERR_MIN_OVERLAP = 2,   /* Assumption 1 fails: some A_ij in no Omega^s */
+    AWG_ERR_NOT_SPD = 3,       /* a Cholesky pivot <= 0 (A, K^s, M_B^s, E or F) */
+    AWG_ERR_EIG = 4,           /* a tridiagonal eigensolve did not converge */
+    AWG_ERR_BREAKDOWN = 5,     /* PCG p^T A p <= 0 or not finite */
+    AWG_ERR_MAXIT = 6,         /* PCG stopped at the iteration cap */
+    AWG_ERR_OOM = 7,           /* device allocation failed */
+    AWG_ERR_CUDA = 8,          /* any other CUDA runtime error */
+    AWG_ERR_NOT_SYMMETRIC = 9, /* the CSR pattern is not structurally symmetric */
+    AWG_ERR_STATE = 10         /* call not valid for this handle (e.g. no W) */
+} awg_status;
+
+/* Variant of the AWG preconditioner (Def. 10, Thm. 7). */
+typedef enum { AWG_H3_AD = 0, AWG_H3_HYB = 1, AWG_H3_INEX = 2 } awg_variant;
+
+/* Storage/arithmetic of the two largest operators of the apply: the local
+ * pseudo-inverses D^s (A^s_+)^+ D^s and the second coarse basis W.  FP64
+ * keeps everything in float64.  MIXED_FP32 / MIXED_BF16 store both in
+ * float32 / bfloat16 with float32 accumulation, keep the PCG recurrences,
+ * both coarse factorisations and solves and the GenEO selection test in
+ * float64, and assemble F from the same rounded W (so H_3 stays SPD). */
+typedef enum { AWG_FP64 = 0, AWG_MIXED_FP32 = 1, AWG_MIXED_BF16 = 2 } awg_precision;
+
+typedef struct {
+    int variant;            /* awg_variant, default AWG_H3_AD                  */
+    int precisions;         /* bit mask of awg_precision values to build
+                               (bit p = 1 << p); FP64 is always built          */
+    double zero_rtol;       /* |lambda| <= zero_rtol * max|lambda(B^s)| is a
+                               zero eigenvalue (in V^s_-, not in W); 1e-12     */
+    double w_rtol;          /* relative residual of the A_+ solves for W;
+                               default 1e-13                                   */
+    int w_maxit;            /* iteration cap of those solves; default 500      */
+    int maxit;              /* iteration cap of awg_pcg; default 1000          */
+    int verbose;            /* 1: print setup stage timings to stderr          */
+} awg_options;
+
+/* Per-handle figures reported after setup (cf. Table 1 of the paper). */
+typedef struct {
+    int n, nnz, nparts;
+    int64_t sum_ns;         /* sum of subdomain sizes n^s                       */
+    int max_ns;             /* largest n^s                                      */
+    int n0;                 /* GenEO coarse dimension #V_0                      */
+    int n_minus;            /* second coarse dimension (strictly negative
+                               eigenvalues of all B^s)                          */
+    int n_minus_all;        /* columns of all V^s_- (zeros included)            */
+    int w_iters;            /* iterations of the multi-RHS PCG that built W     */
+    double w_relres;        /* its largest final relative residual              */
+    double setup_ms[8];     /* stage times: subdomains, split, local factors,
+                               GenEO, E, W, F, total                            */
+    size_t device_bytes;    /* device memory held by the handle                 */
+} awg_info;
+
+/* Fill *opt with the defaults above. */
+void awg_default_options(awg_options* opt);
+
+/* Human-readable name of a status. */
+const char* awg_status_string(awg_status s);
+
+/*
+ * Build the AWG preconditioner for A (Sections 2-4 of the paper).
+ *   n, nnz          order and stored entries of A (n >= 1)
+ *   d_rowptr        device int32[n+1]
+ *   d_colidx        device int32[nnz]
+ *   d_val           device float64[nnz]
+ *   d_partition     device int32[n], owner subdomain of each dof, values in
+ *                   [0, nparts); every part non-empty
+ *   nparts          number of subdomains N (>= 1)
+ *   overlap         layers of graph neighbours added to each part (>= 0);
+ *                   Assumption 1 must hold afterwards (overlap >= 1 suffices)
+ *   tau             GenEO threshold tau_sharp of Thm. 4 (> 0)
+ *   opt             NULL for defaults
+ *   out             receives the handle (NULL on error)
+ * Errors: AWG_ERR_INVALID_ARG, AWG_ERR_NOT_SYMMETRIC, AWG_ERR_MIN_OVERLAP,
+ * AWG_ERR_NOT_SPD, AWG_ERR_EIG, AWG_ERR_OOM, AWG_ERR_CUDA.
+ */
+awg_status awg_setup(int n, int nnz, const int* d_rowptr, const int* d_colidx,
+                     const double* d_val, const int* d_partition, int nparts,
+                     int overlap, double tau, const awg_options* opt,
+                     void* stream, awg_handle* out);
+
+/* Release everything the handle owns.  NULL is accepted. */
+void awg_destroy(awg_handle h);
+
+/* Copy the setup figures into *info (host struct). */
+awg_status awg_get_info(awg_handle h, awg_info* info);
+
+/*
+ * z = H r for nrhs right-hand sides (columns of length n, leading dimension
+ * ld), with H the variant chosen at setup (H_3,ad: Def. 10) and the storage
+ * precision `precision` (must have been built).  d_r and d_z are device
+ * float64 arrays and must not overlap.
+ */
+awg_status awg_apply(awg_handle h, int precision, const double* d_r, double* d_z,
+                     int nrhs, int ld, void* stream);
+
+/*
+ * Apply one building block of the preconditioner (for stage-by-stage
+ * checks).  `which`:
+ *   0  y = A x                           (CSR SpMV)
+ *   1  y = A_+ x = A x + A_- x           (Thm. 2, Section 4.4 item 4)
+ *   2  y = H^NN x                        (Def. 8)
+ *   3  y = H^NN_hyb(tau) x = H_2 x       (Thm. 4)
+ *   4  y = H_3,ad x                      (Def. 10)
+ *   5  y = H_3,hyb x                     (Def. 10)
+ *   6  y = H_3,inex x                    (Thm. 7)
+ * Single right-hand side; d_x, d_y device float64[n].
+ */
+awg_status awg_apply_stage(awg_handle h, int which, int precision, const double* d_x,
+                           double* d_y, void* stream);
+
+/*
+ * Solve A x = b by PCG preconditioned with H (x_0 = 0), for nrhs columns
+ * (leading dimension ld) at once; each column stops when its recurrence
+ * residual satisfies ||b - A x|| <= rtol ||b|| and the true residual is
+ * confirmed.  h_iters (int[nrhs]) and h_relres (double[nrhs], true relative
+ * residual) are HOST arrays and may be NULL.
+ * Errors: AWG_ERR_MAXIT (some column hit opt.maxit), AWG_ERR_BREAKDOWN.
+ */
+awg_status awg_pcg(awg_handle h, int precision, const double* d_b, double* d_x,
+                   int nrhs, int ld, double rtol, int* h_iters, double* h_relres,
+                   void* stream);
+
+/*
+ * Copy setup results to HOST arrays, for checks.  `what`:
+ *   0  subdomain sizes n^s                      int32[nparts]
+ *   1  subdomain index lists, concatenated      int32[sum_ns]
+ *   2  n^s_- (zeros included)                   int32[nparts]
+ *   3  strictly negative counts                 int32[nparts]
+ *   4  GenEO mode counts m^s                    int32[nparts]
+ *   5  eigenvalues of B^s in V^s_-, concatenated float64[n_minus_all]
+ *   6  pair multiplicity M_mu per stored entry  float64[nnz]
+ *   7  partition of unity diagonal D            float64[n]
+ *   8  E = Z^T A_+ Z                            float64[n0*n0]
+ *   9  F = W^T A W                              float64[n_minus^2]
+ *  10  W (column-major n x n_minus)             float64[n*n_minus]
+ *  11  Z (column-major n x n0)                  float64[n*n0]
+ * `count` is the capacity of h_out in elements; AWG_ERR_INVALID_ARG if it
+ * is too small.
+ */
+awg_status awg_get_array(awg_handle h, int what, void* h_out, size_t count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AWG_H */

@@ -1,0 +1,11 @@
+"""GB300 (sm_103a) AWG preconditioned conjugate gradient (arXiv 2106.10913).
+
+The solver is the C-ABI library ``lib/libawg.so`` (declared in
+``include/awg.h``); this package is its Python binding.
+"""
+
+from .awg import (  # noqa: F401
+    AWGError, AWGSolver, EXPORTED, FP64, MIXED_BF16, MIXED_FP32, H3_AD, H3_HYB, H3_INEX, LIB_PATH,
+    STAGE, awg_apply, awg_apply_stage, awg_destroy, awg_get_array, awg_get_info, awg_pcg,
+    awg_setup, default_options, load_library,
+)

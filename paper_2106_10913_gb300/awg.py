@@ -1,0 +1,222 @@
+"""Thin ctypes binding of libawg (include/awg.h).
+
+Argument marshalling only: every step of setup, apply and PCG runs in the
+library's CUDA kernels.  Tensors are PyTorch CUDA tensors (device memory and
+streams are PyTorch's); the library is loaded from ``lib/libawg.so`` next to
+this file and importing fails loudly if it has not been built.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libawg.so")
+
+AWG_OK = 0
+STATUS = {0: "AWG_OK", 1: "AWG_ERR_INVALID_ARG", 2: "AWG_ERR_MIN_OVERLAP", 3: "AWG_ERR_NOT_SPD",
+          4: "AWG_ERR_EIG", 5: "AWG_ERR_BREAKDOWN", 6: "AWG_ERR_MAXIT", 7: "AWG_ERR_OOM",
+          8: "AWG_ERR_CUDA", 9: "AWG_ERR_NOT_SYMMETRIC", 10: "AWG_ERR_STATE"}
+H3_AD, H3_HYB, H3_INEX = 0, 1, 2
+FP64, MIXED_FP32, MIXED_BF16 = 0, 1, 2
+STAGE = {"spmv": 0, "aplus": 1, "hnn": 2, "h2": 3, "h3ad": 4, "h3hyb": 5, "h3inex": 6}
+ARRAY = {"ns": (0, np.int32), "sub_idx": (1, np.int32), "n_minus": (2, np.int32),
+         "n_strict": (3, np.int32), "modes": (4, np.int32), "lam_minus": (5, np.float64),
+         "mmu": (6, np.float64), "dvec": (7, np.float64), "E": (8, np.float64),
+         "F": (9, np.float64), "W": (10, np.float64), "Z": (11, np.float64)}
+
+
+class AWGError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+class awg_options(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("precisions", ctypes.c_int),
+                ("zero_rtol", ctypes.c_double), ("w_rtol", ctypes.c_double),
+                ("w_maxit", ctypes.c_int), ("maxit", ctypes.c_int), ("verbose", ctypes.c_int)]
+
+
+class awg_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("nnz", ctypes.c_int), ("nparts", ctypes.c_int),
+                ("sum_ns", ctypes.c_int64), ("max_ns", ctypes.c_int), ("n0", ctypes.c_int),
+                ("n_minus", ctypes.c_int), ("n_minus_all", ctypes.c_int),
+                ("w_iters", ctypes.c_int), ("w_relres", ctypes.c_double),
+                ("setup_ms", ctypes.c_double * 8), ("device_bytes", ctypes.c_size_t)]
+
+
+EXPORTED = ["awg_default_options", "awg_status_string", "awg_setup", "awg_destroy",
+            "awg_get_info", "awg_apply", "awg_apply_stage", "awg_pcg", "awg_get_array"]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libawg.so and declare its signatures (raises if absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libawg.so not found at {path}; build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    lib.awg_default_options.argtypes = [ctypes.POINTER(awg_options)]
+    lib.awg_default_options.restype = None
+    lib.awg_status_string.argtypes = [I]
+    lib.awg_status_string.restype = ctypes.c_char_p
+    lib.awg_setup.argtypes = [I, I, P, P, P, P, I, I, D, ctypes.POINTER(awg_options), P,
+                              ctypes.POINTER(P)]
+    lib.awg_setup.restype = I
+    lib.awg_destroy.argtypes = [P]
+    lib.awg_destroy.restype = None
+    lib.awg_get_info.argtypes = [P, ctypes.POINTER(awg_info)]
+    lib.awg_get_info.restype = I
+    lib.awg_apply.argtypes = [P, I, P, P, I, I, P]
+    lib.awg_apply.restype = I
+    lib.awg_apply_stage.argtypes = [P, I, I, P, P, P]
+    lib.awg_apply_stage.restype = I
+    lib.awg_pcg.argtypes = [P, I, P, P, I, I, D, ctypes.POINTER(I), ctypes.POINTER(D), P]
+    lib.awg_pcg.restype = I
+    lib.awg_get_array.argtypes = [P, I, P, S]
+    lib.awg_get_array.restype = I
+    _lib = lib
+    return lib
+
+
+def _check(st: int, where: str):
+    if st != AWG_OK:
+        raise AWGError(st, where)
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def default_options(**kw) -> awg_options:
+    o = awg_options()
+    load_library().awg_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+# ----------------------------------------------------------- C-named entry points
+def awg_setup(rowptr, colidx, val, partition, nparts: int, overlap: int, tau: float,
+              options: Optional[awg_options] = None, stream=None) -> ctypes.c_void_p:
+    """Build the preconditioner; all tensors on the same CUDA device."""
+    lib = load_library()
+    n = rowptr.numel() - 1
+    h = ctypes.c_void_p()
+    st = lib.awg_setup(n, colidx.numel(), rowptr.data_ptr(), colidx.data_ptr(), val.data_ptr(),
+                       partition.data_ptr(), nparts, overlap, float(tau),
+                       ctypes.byref(options) if options is not None else None,
+                       _stream_ptr(stream), ctypes.byref(h))
+    _check(st, "awg_setup")
+    return h
+
+
+def awg_destroy(h):
+    load_library().awg_destroy(h)
+
+
+def awg_get_info(h) -> dict:
+    info = awg_info()
+    _check(load_library().awg_get_info(h, ctypes.byref(info)), "awg_get_info")
+    d = {k: getattr(info, k) for k, _ in awg_info._fields_}
+    d["setup_ms"] = list(info.setup_ms)
+    return d
+
+
+def awg_apply(h, r, z, precision: int = FP64, stream=None):
+    nrhs = 1 if r.dim() == 1 else r.shape[0]
+    ld = r.shape[-1]
+    _check(load_library().awg_apply(h, precision, r.data_ptr(), z.data_ptr(), nrhs, ld,
+                                    _stream_ptr(stream)), "awg_apply")
+    return z
+
+
+def awg_apply_stage(h, which, x, y, precision: int = FP64, stream=None):
+    w = STAGE[which] if isinstance(which, str) else int(which)
+    _check(load_library().awg_apply_stage(h, w, precision, x.data_ptr(), y.data_ptr(),
+                                          _stream_ptr(stream)), "awg_apply_stage")
+    return y
+
+
+def awg_pcg(h, b, x, rtol: float = 1e-8, precision: int = FP64, stream=None, check=True):
+    nrhs = 1 if b.dim() == 1 else b.shape[0]
+    ld = b.shape[-1]
+    its = (ctypes.c_int * nrhs)()
+    rel = (ctypes.c_double * nrhs)()
+    st = load_library().awg_pcg(h, precision, b.data_ptr(), x.data_ptr(), nrhs, ld, float(rtol),
+                                its, rel, _stream_ptr(stream))
+    if check:
+        _check(st, "awg_pcg")
+    return st, list(its), list(rel)
+
+
+def awg_get_array(h, what: str, size: int) -> np.ndarray:
+    code, dt = ARRAY[what]
+    out = np.zeros(max(size, 1), dtype=dt)
+    _check(load_library().awg_get_array(h, code, out.ctypes.data_as(ctypes.c_void_p), size),
+           f"awg_get_array({what})")
+    return out[:size]
+
+
+# ------------------------------------------------------------- convenience class
+class AWGSolver:
+    """Owns one libawg handle built from host (NumPy) or device CSR arrays."""
+
+    def __init__(self, rowptr, colidx, val, partition, nparts: int, overlap: int, tau: float,
+                 device="cuda", **opts):
+        import torch
+        t = lambda a, dt: (a if isinstance(a, torch.Tensor) else torch.from_numpy(
+            np.ascontiguousarray(a))).to(device=device, dtype=dt).contiguous()
+        self.rowptr = t(rowptr, torch.int32)
+        self.colidx = t(colidx, torch.int32)
+        self.val = t(val, torch.float64)
+        part = t(partition, torch.int32)
+        self.n = self.rowptr.numel() - 1
+        self.device = device
+        self.h = awg_setup(self.rowptr, self.colidx, self.val, part, nparts, overlap, tau,
+                           default_options(**opts))
+        self.info = awg_get_info(self.h)
+
+    def close(self):
+        if self.h is not None:
+            awg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, r, precision: int = FP64, stage: Optional[str] = None):
+        import torch
+        z = torch.empty_like(r)
+        if stage is None:
+            return awg_apply(self.h, r, z, precision)
+        return awg_apply_stage(self.h, stage, r, z, precision)
+
+    def pcg(self, b, rtol: float = 1e-8, precision: int = FP64, check=True):
+        import torch
+        x = torch.zeros_like(b)
+        st, its, rel = awg_pcg(self.h, b, x, rtol, precision, check=check)
+        return x, its, rel, st
+
+    def array(self, what: str) -> np.ndarray:
+        i = self.info
+        size = {"ns": i["nparts"], "sub_idx": i["sum_ns"], "n_minus": i["nparts"],
+                "n_strict": i["nparts"], "modes": i["nparts"], "lam_minus": i["n_minus_all"],
+                "mmu": i["nnz"], "dvec": i["n"], "E": i["n0"] ** 2, "F": i["n_minus"] ** 2,
+                "W": i["n"] * i["n_minus"], "Z": i["n"] * i["n0"]}[what]
+        return awg_get_array(self.h, what, size)

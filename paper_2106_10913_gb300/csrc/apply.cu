@@ -1,0 +1,646 @@
+// Single-right-hand-side hot path: CSR SpMV, the AWG apply (H_3,ad, H_3,hyb,
+// H_3,inex over H_2 = H^NN_hyb(tau)) and PCG.
+//
+// Per apply of H_3,ad (Def. 10 with Thm. 4):
+//   y0 = Z^T r, w0 = W^T r             block-sparse gather-dot, tall-skinny pass 1
+//   c1 = E^-1 y0, d = F^-1 w0          dense coarse solves (explicit inverses)
+//   t  = r - A_+ Z c1                  Pi^T r  (A_+ x = A x + A_- x)
+//   u  = H^NN t                        batched local pseudo-inverse GEMVs
+//   c2 = E^-1 Z^T A_+ u
+//   z  = u + Z (c1 - c2) + W d         Pi H^NN Pi^T r + Z E^-1 Z^T r + W F^-1 W^T r
+// Every sum over subdomains is an owner-computes gather over the incidence
+// lists, every reduction a fixed-order tree: results are bitwise repeatable.
+
+#include "awg_common.cuh"
+#include "ops.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace awg {
+
+template <typename T> __device__ __forceinline__ float to_f(T v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) {
+    return __bfloat162float(v);
+}
+
+// ------------------------------------------------------------------ SpMV
+// y = A x; if pdot, also writes per-block partials of x^T y (fixed order).
+__global__ void __launch_bounds__(256) k_spmv(int n, const int* __restrict__ rp,
+                                              const int* __restrict__ ci,
+                                              const double* __restrict__ a,
+                                              const double* __restrict__ x, double* __restrict__ y,
+                                              double* pdot) {
+    __shared__ double red[32];
+    double part = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        const int e = rp[i + 1];
+        for (int k = rp[i]; k < e; k++) acc = fma(a[k], x[ci[k]], acc);
+        y[i] = acc;
+        part = fma(acc, x[i], part);
+    }
+    if (pdot) {
+        part = block_sum(part, red);
+        if (threadIdx.x == 0) pdot[blockIdx.x] = part;
+    }
+}
+
+// -------------------------------------------------------- block-sparse ops
+// c[colptr[s] + j] = sum_p B_s(p, j) x(idx_s(p)),  B_s column-major n^s x cols
+__global__ void __launch_bounds__(256) k_blk_tgemv(const int* __restrict__ sub_ptr,
+                                                   const int* __restrict__ sub_idx,
+                                                   const int* __restrict__ colptr,
+                                                   const int64_t* __restrict__ boff,
+                                                   const double* __restrict__ B,
+                                                   const double* __restrict__ x, double* c) {
+    extern __shared__ double xs[];
+    const int s = blockIdx.x;
+    const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
+    const int c0 = colptr[s], nc = colptr[s + 1] - c0;
+    if (nc == 0) return;
+    for (int p = threadIdx.x; p < m; p += blockDim.x) xs[p] = x[sub_idx[p0 + p]];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const double* Bs = B + boff[s];
+    for (int j = wid; j < nc; j += nw) {
+        const double* col = Bs + (size_t)j * m;
+        double acc = 0.0;
+        for (int p = lane; p < m; p += 32) acc = fma(col[p], xs[p], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) c[c0 + j] = acc;
+    }
+}
+
+// loc[sub_ptr[s] + p] = sum_j B_s(p, j) w_j c_j   (w optional)
+__global__ void __launch_bounds__(256) k_blk_gemv(const int* __restrict__ sub_ptr,
+                                                  const int* __restrict__ colptr,
+                                                  const int64_t* __restrict__ boff,
+                                                  const double* __restrict__ B,
+                                                  const double* __restrict__ c,
+                                                  const double* __restrict__ w, double wsign,
+                                                  double* loc) {
+    extern __shared__ double cs[];
+    const int s = blockIdx.x;
+    const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
+    const int c0 = colptr[s], nc = colptr[s + 1] - c0;
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) cs[j] = w ? wsign * w[c0 + j] * c[c0 + j] : c[c0 + j];
+    __syncthreads();
+    const double* Bs = B + boff[s];
+    for (int p = threadIdx.x; p < m; p += blockDim.x) {
+        double acc = 0.0;
+        for (int j = 0; j < nc; j++) acc = fma(Bs[p + (size_t)j * m], cs[j], acc);
+        loc[p0 + p] = acc;
+    }
+}
+
+// y = beta y + alpha sum_copies loc + gamma z
+__global__ void k_prolong1(int n, const int* __restrict__ inc_ptr, const int* __restrict__ inc_pos,
+                           const double* __restrict__ loc, double* y, double alpha, double beta,
+                           const double* z, double gamma) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = 0.0;
+    for (int e = inc_ptr[i]; e < inc_ptr[i + 1]; e++) acc += loc[inc_pos[e]];
+    double v = alpha * acc;
+    if (beta != 0.0) v = fma(beta, y[i], v);
+    if (z) v = fma(gamma, z[i], v);
+    y[i] = v;
+}
+
+// ------------------------------------------------------ local pseudo-inverse
+// loc[sub_ptr[s] + p] = sum_q G_s(p, q) x(idx_s(q)), G_s symmetric, full
+// column-major storage: row p is read as column p (contiguous).
+constexpr int LG_ROWS = 32;
+
+__global__ void __launch_bounds__(256) k_local_gemv64(const int* __restrict__ sub_ptr,
+                                                      const int* __restrict__ sub_idx,
+                                                      const int64_t* __restrict__ goff,
+                                                      const double* __restrict__ G,
+                                                      const double* __restrict__ x, double* loc) {
+    extern __shared__ double xs[];
+    const int s = blockIdx.x;
+    const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
+    const int r0 = blockIdx.y * LG_ROWS;
+    if (r0 >= m) return;
+    for (int q = threadIdx.x; q < m; q += blockDim.x) xs[q] = x[sub_idx[p0 + q]];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const double* Gs = G + goff[s];
+    const int r1 = min(m, r0 + LG_ROWS);
+    for (int p = r0 + wid; p < r1; p += nw) {
+        const double* col = Gs + (size_t)p * m;
+        double a0 = 0.0, a1 = 0.0;
+        int q = lane;
+        for (; q + 32 < m; q += 64) {
+            a0 = fma(col[q], xs[q], a0);
+            a1 = fma(col[q + 32], xs[q + 32], a1);
+        }
+        if (q < m) a0 = fma(col[q], xs[q], a0);
+        const double acc = warp_sum(a0 + a1);
+        if (lane == 0) loc[p0 + p] = acc;
+    }
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(256) k_local_gemv_lp(const int* __restrict__ sub_ptr,
+                                                       const int* __restrict__ sub_idx,
+                                                       const int64_t* __restrict__ goff,
+                                                       const TS* __restrict__ G,
+                                                       const double* __restrict__ x, double* loc) {
+    extern __shared__ float xf[];
+    const int s = blockIdx.x;
+    const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
+    const int r0 = blockIdx.y * LG_ROWS;
+    if (r0 >= m) return;
+    for (int q = threadIdx.x; q < m; q += blockDim.x) xf[q] = (float)x[sub_idx[p0 + q]];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const TS* Gs = G + goff[s];
+    const int r1 = min(m, r0 + LG_ROWS);
+    for (int p = r0 + wid; p < r1; p += nw) {
+        const TS* col = Gs + (size_t)p * m;
+        float a0 = 0.f, a1 = 0.f;
+        int q = lane;
+        for (; q + 32 < m; q += 64) {
+            a0 = fmaf(to_f(col[q]), xf[q], a0);
+            a1 = fmaf(to_f(col[q + 32]), xf[q + 32], a1);
+        }
+        if (q < m) a0 = fmaf(to_f(col[q]), xf[q], a0);
+        const float acc = warp_sumf(a0 + a1);
+        if (lane == 0) loc[p0 + p] = (double)acc;
+    }
+}
+
+// ------------------------------------------------------------ dense coarse
+// y = M x, M symmetric dim x dim (row p = column p), warp per row
+// y = alpha M x + beta sub  (sub optional; y must not alias x)
+__global__ void __launch_bounds__(256) k_dense_gemv(int dim, const double* __restrict__ M,
+                                                    const double* __restrict__ x, double* y,
+                                                    double alpha, const double* sub, double beta) {
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= dim) return;
+    const double* col = M + (size_t)row * dim;
+    double acc = 0.0;
+    for (int q = lane; q < dim; q += 32) acc = fma(col[q], x[q], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) y[row] = sub ? fma(beta, sub[row], alpha * acc) : alpha * acc;
+}
+
+// ------------------------------------------------- tall-skinny W (row-major)
+constexpr int WT_CPT = 16;  // columns per thread per chunk
+
+template <typename TS>
+__device__ __forceinline__ double wval(const TS* W, size_t i) { return (double)to_f(W[i]); }
+template <>
+__device__ __forceinline__ double wval<double>(const double* W, size_t i) { return W[i]; }
+
+// part[b*nm + c] = sum over the block's rows i of W(i, c) r(i)
+template <typename TS, typename TA>
+__global__ void __launch_bounds__(256) k_wt_partial(int n, int nm, int ldw, int rows,
+                                                    const TS* __restrict__ W,
+                                                    const double* __restrict__ r, double* part) {
+    const int i0 = blockIdx.x * rows;
+    const int i1 = min(n, i0 + rows);
+    for (int c0 = 0; c0 < nm; c0 += blockDim.x * WT_CPT) {
+        TA acc[WT_CPT];
+#pragma unroll
+        for (int u = 0; u < WT_CPT; u++) acc[u] = 0;
+        for (int i = i0; i < i1; i++) {
+            const TA ri = (TA)r[i];
+            const TS* row = W + (size_t)i * ldw;
+#pragma unroll
+            for (int u = 0; u < WT_CPT; u++) {
+                const int c = c0 + threadIdx.x + u * blockDim.x;
+                if (c < nm) acc[u] += (TA)wval<TS>(row, c) * ri;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < WT_CPT; u++) {
+            const int c = c0 + threadIdx.x + u * blockDim.x;
+            if (c < nm) part[(size_t)blockIdx.x * nm + c] = (double)acc[u];
+        }
+    }
+}
+
+__global__ void k_reduce_cols(int nb, int nm, const double* __restrict__ part, double* out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nm) return;
+    double acc = 0.0;
+    for (int b = 0; b < nb; b++) acc += part[(size_t)b * nm + c];
+    out[c] = acc;
+}
+
+// z(i) = v(i) + sum_c W(i, c) d(c)   (warp per row)
+template <typename TS, typename TA>
+__global__ void __launch_bounds__(256) k_w_d(int n, int nm, int ldw, const TS* __restrict__ W,
+                                             const double* __restrict__ d, const double* v,
+                                             double* z) {
+    extern __shared__ double ds[];
+    for (int c = threadIdx.x; c < nm; c += blockDim.x) ds[c] = d[c];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int nwb = blockDim.x >> 5;
+    for (int i = blockIdx.x * nwb + (threadIdx.x >> 5); i < n; i += gridDim.x * nwb) {
+        const TS* row = W + (size_t)i * ldw;
+        TA acc = 0;
+        for (int c = lane; c < nm; c += 32) acc += (TA)wval<TS>(row, c) * (TA)ds[c];
+        double a = (double)acc;
+        a = warp_sum(a);
+        if (lane == 0) z[i] = (v ? v[i] : 0.0) + a;
+    }
+}
+
+// -------------------------------------------------------------- vector ops
+__global__ void k_sub(int n, const double* a, const double* b, double* c) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) c[i] = a[i] - b[i];
+}
+
+__global__ void k_dot_partial(int n, const double* __restrict__ x, const double* __restrict__ y,
+                              double* part) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        acc = fma(x[i], y[i], acc);
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void k_final_sum(int nb, const double* __restrict__ part, double* out) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += part[b];
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) *out = acc;
+}
+
+// PCG scalars (device): 0 rz, 1 pq, 2 rr, 3 rz_new, 4 beta
+enum { S_RZ = 0, S_PQ = 1, S_RR = 2, S_RZN = 3, S_BETA = 4, S_BB = 5, S_TR = 6 };
+
+// x += alpha p, r -= alpha q with alpha = rz / pq; partials of r.r
+__global__ void k_pcg_xr(int n, const double* __restrict__ scal, const double* __restrict__ p,
+                         const double* __restrict__ q, double* x, double* r, double* part) {
+    __shared__ double red[32];
+    const double pq = scal[S_PQ];
+    const double alpha = (pq > 0.0) ? scal[S_RZ] / pq : 0.0;
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        acc = fma(ri, ri, acc);
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void k_pcg_beta(double* scal) {
+    const double rz = scal[S_RZ], rzn = scal[S_RZN];
+    scal[S_BETA] = (rz != 0.0) ? rzn / rz : 0.0;
+    scal[S_RZ] = rzn;
+}
+
+__global__ void k_pcg_p(int n, const double* __restrict__ scal, const double* __restrict__ z,
+                        double* p) {
+    const double beta = scal[S_BETA];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        p[i] = fma(beta, p[i], z[i]);
+}
+
+// ===================================================================== host
+struct Ws {
+    double *y0, *y2, *c1, *c2, *w0, *w1, *dd, *x1, *t, *u, *q, *loc, *loc2, *cm, *part, *wpart, *tmp, *tmp2;
+};
+
+static Ws ws_of(Handle* h) {
+    // carve the workspace (sizes fixed at setup, see ws_bytes)
+    Ws w;
+    double* p = (double*)h->ws.p;
+    const size_t n = h->n, n0 = std::max(1, h->n0), nm = std::max(1, h->n_minus);
+    auto take = [&](size_t len) { double* r = p; p += (len + 31) / 32 * 32; return r; };
+    w.y0 = take(n0); w.y2 = take(n0); w.c1 = take(n0); w.c2 = take(n0);
+    w.w0 = take(nm); w.w1 = take(nm); w.dd = take(nm);
+    w.x1 = take(n); w.t = take(n); w.u = take(n); w.q = take(n); w.tmp = take(n); w.tmp2 = take(n);
+    w.loc = take(h->sum_ns); w.loc2 = take(h->sum_ns);
+    w.cm = take(std::max(1, h->n_minus_all));
+    w.part = take(4096);
+    w.wpart = take((size_t)h->red_blocks * nm);
+    return w;
+}
+
+size_t ws_bytes(const Handle* h) {
+    const size_t n = h->n, n0 = std::max(1, h->n0), nm = std::max(1, h->n_minus);
+    auto r = [](size_t len) { return (len + 31) / 32 * 32; };
+    size_t tot = 4 * r(n0) + 3 * r(nm) + 6 * r(n) + 2 * r(h->sum_ns) +
+                 r(std::max(1, h->n_minus_all)) + r(4096) + r((size_t)h->red_blocks * nm);
+    return tot * sizeof(double);
+}
+
+static int grid_n(int n) { return std::min((n + 255) / 256, 152 * 8); }
+
+awg_status spmv1(Handle* h, const double* x, double* y, double* pdot, cudaStream_t s) {
+    k_spmv<<<grid_n(h->n), 256, 0, s>>>(h->n, (int*)h->rowptr.p, (int*)h->colidx.p,
+                                        (double*)h->val.p, x, y, pdot);
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
+static awg_status prolong1(Handle* h, const double* loc, double* y, double alpha, double beta,
+                           const double* z, double gamma, cudaStream_t s) {
+    k_prolong1<<<(h->n + 255) / 256, 256, 0, s>>>(h->n, (int*)h->inc_ptr.p, (int*)h->inc_pos.p, loc,
+                                                  y, alpha, beta, z, gamma);
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
+// y = A_- x, or y = yin + sign * A_- x
+static awg_status aminus1(Handle* h, const double* x, double* y, const double* yin, double sign,
+                          Ws& w, cudaStream_t s) {
+    if (h->n_minus_all == 0) {
+        if (yin) { if (yin != y) AWG_CUDA(cudaMemcpyAsync(y, yin, h->n * 8, cudaMemcpyDeviceToDevice, s)); }
+        else AWG_CUDA(cudaMemsetAsync(y, 0, h->n * 8, s));
+        return AWG_OK;
+    }
+    const size_t sm = (size_t)h->max_ns * 8;
+    k_blk_tgemv<<<h->N, 256, sm, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p, (int*)h->nm_ptr.p,
+                                      (int64_t*)h->vm_off.p, (double*)h->Vm.p, x, w.cm);
+    AWG_LAUNCH();
+    k_blk_gemv<<<h->N, 256, (size_t)std::max(1, *std::max_element(h->h_nm.begin(), h->h_nm.end())) * 8, s>>>(
+        (int*)h->sub_ptr.p, (int*)h->nm_ptr.p, (int64_t*)h->vm_off.p, (double*)h->Vm.p, w.cm,
+        (double*)h->lam_m.p, -1.0, w.loc2);
+    AWG_LAUNCH();
+    return prolong1(h, w.loc2, y, sign, 0.0, yin, 1.0, s);
+}
+
+// y = yin + sign * A_+ x
+static awg_status aplus1(Handle* h, const double* x, double* y, const double* yin, double sign,
+                         Ws& w, cudaStream_t s) {
+    AWG_TRY(spmv1(h, x, w.tmp2, nullptr, s));
+    // tmp2 = A x ; y = yin + sign*(A x + A_- x)
+    if (yin) {
+        k_sub<<<(h->n + 255) / 256, 256, 0, s>>>(h->n, yin, w.tmp2, w.tmp2);  // yin - A x
+        AWG_LAUNCH();
+        if (sign != -1.0) return AWG_ERR_INVALID_ARG;
+        return aminus1(h, x, y, w.tmp2, -1.0, w, s);
+    }
+    return aminus1(h, x, y, w.tmp2, sign, w, s);
+}
+
+static awg_status zt1(Handle* h, const double* x, double* c, cudaStream_t s) {
+    if (h->n0 == 0) return AWG_OK;
+    k_blk_tgemv<<<h->N, 256, (size_t)h->max_ns * 8, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p,
+                                                        (int*)h->mode_ptr.p, (int64_t*)h->z_off.p,
+                                                        (double*)h->Z.p, x, c);
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
+// loc = Z c (local slabs)
+static awg_status zloc1(Handle* h, const double* c, double* loc, cudaStream_t s) {
+    const int mx = std::max(1, *std::max_element(h->h_modes.begin(), h->h_modes.end()));
+    k_blk_gemv<<<h->N, 256, (size_t)mx * 8, s>>>((int*)h->sub_ptr.p, (int*)h->mode_ptr.p,
+                                                 (int64_t*)h->z_off.p, (double*)h->Z.p, c,
+                                                 nullptr, 1.0, loc);
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
+static awg_status dense_gemv(int dim, const double* M, const double* x, double* y, double alpha,
+                             const double* sub, double beta, cudaStream_t s) {
+    if (dim == 0) return AWG_OK;
+    k_dense_gemv<<<(dim + 7) / 8, 256, 0, s>>>(dim, M, x, y, alpha, sub, beta);
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
+static awg_status hnn1(Handle* h, int prec, const double* x, double* y, Ws& w, cudaStream_t s) {
+    dim3 g(h->N, (h->max_ns + LG_ROWS - 1) / LG_ROWS);
+    const PrecOps& P = h->prec[prec];
+    if (prec == AWG_FP64) {
+        k_local_gemv64<<<g, 256, (size_t)h->max_ns * 8, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p,
+                                                             (int64_t*)h->dense_off.p,
+                                                             (double*)P.G.p, x, w.loc);
+    } else if (prec == AWG_MIXED_FP32) {
+        k_local_gemv_lp<float><<<g, 256, (size_t)h->max_ns * 4, s>>>(
+            (int*)h->sub_ptr.p, (int*)h->sub_idx.p, (int64_t*)h->dense_off.p, (float*)P.G.p, x, w.loc);
+    } else {
+        k_local_gemv_lp<__nv_bfloat16><<<g, 256, (size_t)h->max_ns * 4, s>>>(
+            (int*)h->sub_ptr.p, (int*)h->sub_idx.p, (int64_t*)h->dense_off.p,
+            (__nv_bfloat16*)P.G.p, x, w.loc);
+    }
+    AWG_LAUNCH();
+    return prolong1(h, w.loc, y, 1.0, 0.0, nullptr, 0.0, s);
+}
+
+// c = E^-1 Z^T x
+static awg_status coarse_e(Handle* h, const double* x, double* y0, double* c, cudaStream_t s) {
+    AWG_TRY(zt1(h, x, y0, s));
+    return dense_gemv(h->n0, (double*)h->Einv.p, y0, c, 1.0, nullptr, 0.0, s);
+}
+
+// H_2 x = Pi H^NN Pi^T x + Z E^-1 Z^T x  (Thm. 4)
+static awg_status h2_1(Handle* h, int prec, const double* r, double* z, Ws& w, cudaStream_t s) {
+    if (h->n0 == 0) return hnn1(h, prec, r, z, w, s);
+    AWG_TRY(coarse_e(h, r, w.y0, w.c1, s));                 // c1 = E^-1 Z^T r
+    AWG_TRY(zloc1(h, w.c1, w.loc, s));
+    AWG_TRY(prolong1(h, w.loc, w.x1, 1.0, 0.0, nullptr, 0.0, s));  // x1 = Z c1
+    AWG_TRY(aplus1(h, w.x1, w.t, r, -1.0, w, s));           // t = r - A_+ x1
+    AWG_TRY(hnn1(h, prec, w.t, w.u, w, s));                 // u = H^NN t
+    AWG_TRY(aplus1(h, w.u, w.q, nullptr, 1.0, w, s));        // q = A_+ u
+    AWG_TRY(zt1(h, w.q, w.y2, s));
+    AWG_TRY(dense_gemv(h->n0, (double*)h->Einv.p, w.y2, w.c2, 1.0, w.c1, -1.0, s));  // c2 = E^-1 y2 - c1
+    AWG_TRY(zloc1(h, w.c2, w.loc, s));
+    return prolong1(h, w.loc, z, -1.0, 0.0, w.u, 1.0, s);   // z = u - Z (c2 - c1)
+}
+
+template <typename TS, typename TA>
+static awg_status wt_r_t(Handle* h, const void* W, const double* r, double* out, Ws& w,
+                         cudaStream_t s) {
+    const int nb = h->red_blocks;
+    const int rows = (h->n + nb - 1) / nb;
+    k_wt_partial<TS, TA><<<nb, 256, 0, s>>>(h->n, h->n_minus, h->ldw, rows, (const TS*)W, r, w.wpart);
+    AWG_LAUNCH();
+    k_reduce_cols<<<(h->n_minus + 255) / 256, 256, 0, s>>>(nb, h->n_minus, w.wpart, out);
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
+static awg_status wt_r(Handle* h, int prec, const double* r, double* out, Ws& w, cudaStream_t s) {
+    const void* W = h->prec[prec].W.p;
+    if (prec == AWG_FP64) return wt_r_t<double, double>(h, W, r, out, w, s);
+    if (prec == AWG_MIXED_FP32) return wt_r_t<float, float>(h, W, r, out, w, s);
+    return wt_r_t<__nv_bfloat16, float>(h, W, r, out, w, s);
+}
+
+static awg_status w_d(Handle* h, int prec, const double* d, const double* v, double* z,
+                      cudaStream_t s) {
+    const void* W = h->prec[prec].W.p;
+    const size_t sm = (size_t)h->n_minus * 8;
+    const int grid = std::min((h->n + 7) / 8, 152 * 16);
+    if (prec == AWG_FP64) {
+        k_w_d<double, double><<<grid, 256, sm, s>>>(h->n, h->n_minus, h->ldw, (const double*)W, d, v, z);
+    } else if (prec == AWG_MIXED_FP32) {
+        k_w_d<float, float><<<grid, 256, sm, s>>>(h->n, h->n_minus, h->ldw, (const float*)W, d, v, z);
+    } else {
+        k_w_d<__nv_bfloat16, float><<<grid, 256, sm, s>>>(h->n, h->n_minus, h->ldw,
+                                                          (const __nv_bfloat16*)W, d, v, z);
+    }
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
+awg_status set_smem_limits(Handle* h) {
+    const int mx = (int)std::max<size_t>((size_t)h->max_ns * 8, (size_t)std::max(1, h->n_minus) * 8);
+    if (mx > 48 * 1024) {
+        if (mx > 227 * 1024) return AWG_ERR_INVALID_ARG;
+        AWG_CUDA(cudaFuncSetAttribute(k_blk_tgemv, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        AWG_CUDA(cudaFuncSetAttribute(k_blk_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        AWG_CUDA(cudaFuncSetAttribute(k_local_gemv64, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        AWG_CUDA(cudaFuncSetAttribute(k_local_gemv_lp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        AWG_CUDA(cudaFuncSetAttribute(k_local_gemv_lp<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        AWG_CUDA(cudaFuncSetAttribute(k_w_d<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        AWG_CUDA(cudaFuncSetAttribute(k_w_d<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        AWG_CUDA(cudaFuncSetAttribute(k_w_d<__nv_bfloat16, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    }
+    return AWG_OK;
+}
+
+// One single-RHS apply of the selected stage (see awg_apply_stage).
+awg_status apply_stage(Handle* h, int which, int prec, const double* x, double* y, cudaStream_t s) {
+    if (prec < 0 || prec > 2 || !h->prec[prec].built) return AWG_ERR_INVALID_ARG;
+    Ws w = ws_of(h);
+    switch (which) {
+        case 0: return spmv1(h, x, y, nullptr, s);
+        case 1: return aplus1(h, x, y, nullptr, 1.0, w, s);
+        case 2: return hnn1(h, prec, x, y, w, s);
+        case 3: return h2_1(h, prec, x, y, w, s);
+        case 4: {  // H_3,ad = H_2 + W F^-1 W^T  (Def. 10)
+            if (h->n_minus == 0) return h2_1(h, prec, x, y, w, s);
+            AWG_TRY(wt_r(h, prec, x, w.w0, w, s));
+            AWG_TRY(dense_gemv(h->n_minus, (double*)h->prec[prec].Finv.p, w.w0, w.dd, 1.0, nullptr, 0, s));
+            AWG_TRY(h2_1(h, prec, x, w.tmp, w, s));
+            return w_d(h, prec, w.dd, w.tmp, y, s);
+        }
+        case 5: {  // H_3,hyb = Pi_3 H_2 Pi_3^T + W F^-1 W^T  (Def. 10)
+            if (h->n_minus == 0) return h2_1(h, prec, x, y, w, s);
+            const double* Finv = (double*)h->prec[prec].Finv.p;
+            AWG_TRY(wt_r(h, prec, x, w.w0, w, s));
+            AWG_TRY(dense_gemv(h->n_minus, Finv, w.w0, w.dd, 1.0, nullptr, 0, s));  // d = F^-1 W^T x
+            AWG_TRY(w_d(h, prec, w.dd, nullptr, w.tmp, s));                        // tmp = W d
+            AWG_TRY(spmv1(h, w.tmp, w.q, nullptr, s));
+            k_sub<<<(h->n + 255) / 256, 256, 0, s>>>(h->n, x, w.q, w.tmp);        // tmp = Pi_3^T x
+            AWG_LAUNCH();
+            AWG_TRY(h2_1(h, prec, w.tmp, y, w, s));                                // y = v = H_2 Pi_3^T x
+            AWG_TRY(spmv1(h, y, w.q, nullptr, s));                                 // q = A v
+            AWG_TRY(wt_r(h, prec, w.q, w.w0, w, s));
+            AWG_TRY(dense_gemv(h->n_minus, Finv, w.w0, w.w1, -1.0, w.dd, 1.0, s)); // w1 = d - F^-1 W^T A v
+            return w_d(h, prec, w.w1, y, y, s);                                     // z = v + W w1
+        }
+        case 6: {  // H_3,inex = H_2 + W (C^-1 - Vhat^T W)^-1 W^T  (Thm. 7)
+            if (h->n_minus == 0) return h2_1(h, prec, x, y, w, s);
+            AWG_TRY(wt_r(h, prec, x, w.w0, w, s));
+            AWG_TRY(dense_gemv(h->n_minus, (double*)h->prec[prec].inexInv.p, w.w0, w.dd, 1.0, nullptr, 0, s));
+            AWG_TRY(h2_1(h, prec, x, w.tmp, w, s));
+            return w_d(h, prec, w.dd, w.tmp, y, s);
+        }
+        default: return AWG_ERR_INVALID_ARG;
+    }
+}
+
+// ------------------------------------------------------------------- PCG
+static awg_status dot1(Handle* h, const double* x, const double* y, double* out, Ws& w,
+                       cudaStream_t s) {
+    const int nb = grid_n(h->n);
+    k_dot_partial<<<nb, 256, 0, s>>>(h->n, x, y, w.part);
+    AWG_LAUNCH();
+    k_final_sum<<<1, 256, 0, s>>>(nb, w.part, out);
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
+awg_status pcg1(Handle* h, int prec, int variant_stage, const double* b, double* x, double rtol,
+                int* iters, double* relres, cudaStream_t s) {
+    Ws w = ws_of(h);
+    const int n = h->n, nb = grid_n(n);
+    // partial buffer (4096 doubles): [0, 1216) and [1536, 2752) hold per-block
+    // partials (grid_n <= 1216 blocks), the device scalars live at [4000, 4016)
+    double* scal = w.part + 4000;
+    double *r, *p, *q, *z;
+    AWG_CUDA(cudaMallocAsync(&r, (size_t)n * 8, s));
+    AWG_CUDA(cudaMallocAsync(&p, (size_t)n * 8, s));
+    AWG_CUDA(cudaMallocAsync(&q, (size_t)n * 8, s));
+    AWG_CUDA(cudaMallocAsync(&z, (size_t)n * 8, s));
+    AWG_CUDA(cudaMemsetAsync(x, 0, (size_t)n * 8, s));
+    AWG_CUDA(cudaMemcpyAsync(r, b, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+    AWG_TRY(dot1(h, b, b, scal + S_BB, w, s));
+    AWG_TRY(apply_stage(h, variant_stage, prec, r, z, s));
+    AWG_TRY(dot1(h, r, z, scal + S_RZ, w, s));
+    AWG_CUDA(cudaMemcpyAsync(p, z, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+    AWG_CUDA(cudaMemcpyAsync(h->h_scal, scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    AWG_CUDA(cudaStreamSynchronize(s));
+    const double bnorm = sqrt(h->h_scal[S_BB]);
+    awg_status st = AWG_OK;
+    int it = 0;
+    double rel = (bnorm > 0) ? 1.0 : 0.0, true_rel = rel;
+    if (bnorm == 0.0) {
+        it = 0;
+    } else {
+        const int maxit = h->opt.maxit;
+        bool done = false;
+        while (!done) {
+            if (it >= maxit) { st = AWG_ERR_MAXIT; break; }
+            AWG_TRY(spmv1(h, p, q, w.part, s));                       // q = A p, partial p.q
+            k_final_sum<<<1, 256, 0, s>>>(nb, w.part, scal + S_PQ);
+            AWG_LAUNCH();
+            k_pcg_xr<<<nb, 256, 0, s>>>(n, scal, p, q, x, r, w.part + 1536);
+            AWG_LAUNCH();
+            k_final_sum<<<1, 256, 0, s>>>(nb, w.part + 1536, scal + S_RR);
+            AWG_LAUNCH();
+            it++;
+            AWG_CUDA(cudaMemcpyAsync(h->h_scal, scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            AWG_CUDA(cudaStreamSynchronize(s));
+            const double pq = h->h_scal[S_PQ];
+            if (!(pq > 0.0) || !std::isfinite(pq)) { st = AWG_ERR_BREAKDOWN; break; }
+            rel = sqrt(h->h_scal[S_RR]) / bnorm;
+            if (rel <= rtol) {
+                // confirm on the true residual b - A x
+                AWG_TRY(spmv1(h, x, q, nullptr, s));
+                k_sub<<<(n + 255) / 256, 256, 0, s>>>(n, b, q, q);
+                AWG_LAUNCH();
+                AWG_TRY(dot1(h, q, q, scal + S_TR, w, s));
+                AWG_CUDA(cudaMemcpyAsync(h->h_scal, scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+                AWG_CUDA(cudaStreamSynchronize(s));
+                true_rel = sqrt(h->h_scal[S_TR]) / bnorm;
+                if (true_rel <= rtol || rel <= 1e-6 * rtol) {
+                    if (true_rel > rtol) st = AWG_ERR_MAXIT;
+                    break;
+                }
+            }
+            AWG_TRY(apply_stage(h, variant_stage, prec, r, z, s));
+            AWG_TRY(dot1(h, r, z, scal + S_RZN, w, s));
+            k_pcg_beta<<<1, 1, 0, s>>>(scal);
+            AWG_LAUNCH();
+            k_pcg_p<<<nb, 256, 0, s>>>(n, scal, z, p);
+            AWG_LAUNCH();
+        }
+    }
+    if (st != AWG_OK || true_rel == rel) {
+        AWG_TRY(spmv1(h, x, q, nullptr, s));
+        k_sub<<<(n + 255) / 256, 256, 0, s>>>(n, b, q, q);
+        AWG_LAUNCH();
+        AWG_TRY(dot1(h, q, q, scal + S_TR, w, s));
+        AWG_CUDA(cudaMemcpyAsync(h->h_scal, scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        AWG_CUDA(cudaStreamSynchronize(s));
+        true_rel = bnorm > 0 ? sqrt(h->h_scal[S_TR]) / bnorm : 0.0;
+    }
+    for (double* ptr : {r, p, q, z}) AWG_CUDA(cudaFreeAsync(ptr, s));
+    AWG_CUDA(cudaStreamSynchronize(s));
+    if (iters) *iters = it;
+    if (relres) *relres = true_rel;
+    return st;
+}
+
+}  // namespace awg

@@ -1,0 +1,203 @@
+// Shared declarations of libawg's translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/awg.h"
+
+namespace awg {
+
+#define AWG_CUDA(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t err__ = (call);                                                       \
+        if (err__ != cudaSuccess) {                                                       \
+            if (err__ == cudaErrorMemoryAllocation) {                                     \
+                cudaGetLastError();                                                       \
+                return AWG_ERR_OOM;                                                       \
+            }                                                                             \
+            fprintf(stderr, "libawg: %s failed at %s:%d: %s\n", #call, __FILE__, __LINE__, \
+                    cudaGetErrorString(err__));                                           \
+            return AWG_ERR_CUDA;                                                          \
+        }                                                                                 \
+    } while (0)
+
+#define AWG_TRY(expr)                         \
+    do {                                      \
+        awg_status st__ = (expr);             \
+        if (st__ != AWG_OK) return st__;      \
+    } while (0)
+
+#define AWG_LAUNCH() AWG_CUDA(cudaGetLastError())
+
+// Bits of the device status word that kernels raise.
+enum : int {
+    FLAG_MIN_OVERLAP = 1,
+    FLAG_NOT_SPD = 2,
+    FLAG_EIG = 4,
+    FLAG_NOT_SYM = 8,
+    FLAG_BAD_CSR = 16,
+};
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// Storage of the apply for one precision (awg_precision).
+struct PrecOps {
+    bool built = false;
+    DevBuf G;         // local D^s (A^s_+)^+ D^s: float64 full n^s x n^s, or packed tiles
+    DevBuf W;         // second coarse basis, row-major n x ldw (float64/float32/bf16)
+    DevBuf Finv;      // (W^T A W)^-1 for this W, float64 n_- x n_-
+    DevBuf inexInv;   // (C^-1 - Vhat^T W)^-1 (H_3,inex), float64 n_- x n_-
+};
+
+struct Handle {
+    int n = 0, nnz = 0, N = 0, overlap = 0;
+    double tau = 0.1;
+    awg_options opt{};
+    cudaStream_t stream = nullptr;
+
+    DevBuf rowptr, colidx, val;          // A
+
+    // subdomains Omega^s (Def. 1), sizes n^s
+    std::vector<int> h_ns, h_sub_ptr;
+    int64_t sum_ns = 0;
+    int max_ns = 0;
+    DevBuf ns, sub_ptr, sub_idx;         // int32[N], int32[N+1], int32[sum_ns]
+    DevBuf inc_ptr, inc_pos, inc_sub;    // per dof i: positions (in the local arena)
+                                         // of its copies and their subdomain,
+                                         // ordered by subdomain
+    DevBuf pos_sub;                      // subdomain of each local-arena position
+    DevBuf dvec;                         // D (Def. 3): 1/multiplicity, float64[n]
+    DevBuf mmu, bval;                    // M_mu and B = A/M_mu per stored entry
+
+    // per-subdomain dense n^s x n^s blocks, column-major, ld = n^s
+    std::vector<int64_t> h_dense_off;
+    DevBuf dense_off;                    // int64[N+1]
+    int64_t dense_total = 0;
+
+    // eigen-split of B^s (Def. 6)
+    std::vector<int> h_nm, h_nstrict, h_nm_ptr;
+    std::vector<int64_t> h_vm_off;
+    DevBuf nm, nstrict, nm_ptr, vm_off;  // int32[N], int32[N], int32[N+1], int64[N+1]
+    DevBuf Vm, lam_m;                    // V^s_- (n^s x n^s_-), eigenvalues
+    DevBuf sigma;                        // shift of K^s per subdomain
+    int n_minus_all = 0;
+
+    // GenEO coarse space (Def. 9, Thm. 4)
+    std::vector<int> h_modes, h_mode_ptr;
+    std::vector<int64_t> h_z_off;
+    DevBuf modes, mode_ptr, z_off, Z;    // Z^s column-major n^s x m^s (M_B-normalised)
+    int n0 = 0;
+    DevBuf E, Einv;                      // n0 x n0, float64
+
+    // second coarse space (Def. 10)
+    int n_minus = 0, ldw = 0;
+    std::vector<int> h_wcol_ptr;         // prefix of the strict counts (N+1)
+    DevBuf wcol_ptr;
+    DevBuf Wcm;                          // W float64 column-major n x n_- (kept for checks)
+    DevBuf F64;                          // W^T A W of the float64 W
+    PrecOps prec[3];
+
+    // info
+    int w_iters = 0;
+    double w_relres = 0.0;
+    double setup_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    size_t device_bytes = 0;
+
+    // single right-hand-side workspace of the apply
+    DevBuf ws;
+    DevBuf flag;                         // int status word
+    DevBuf red;                          // partial-sum scratch
+    int red_blocks = 0;
+    int* h_flag = nullptr;               // pinned host mirror
+    double* h_scal = nullptr;            // pinned host scalars
+};
+
+awg_status dalloc(Handle* h, DevBuf& b, size_t bytes);
+void dfree(Handle* h, DevBuf& b);
+awg_status read_flag(Handle* h, int* out);
+awg_status upload(Handle* h, DevBuf& b, const void* src, size_t bytes);
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum in a fixed order (deterministic).  `sh` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    double t = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (wid == 0) t = warp_sum(t);
+    if (threadIdx.x == 0) sh[0] = t;
+    __syncthreads();
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// First position of `key` in the sorted int array a[0..len), or -1.
+__device__ __forceinline__ int bsearch_idx(const int* a, int len, int key) {
+    int lo = 0, hi = len - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int v = a[mid];
+        if (v == key) return mid;
+        if (v < key) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+// ------------------------------------------------------------------ cross-unit API
+// structure.cu
+awg_status setup_structure(Handle* h, const int* d_part);
+awg_status assemble_local(Handle* h, const double* d_vals, double* arena);
+
+// dense.cu : batched dense FP64 kernels over the per-subdomain blocks
+struct GemmDesc {
+    const double* A;
+    const double* B;
+    double* C;
+    int M, N, K, lda, ldb, ldc;
+    int transA, transB;
+    double alpha, beta;
+};
+awg_status gemm_batched(Handle* h, const std::vector<GemmDesc>& descs, cudaStream_t s);
+awg_status potrf_batched(Handle* h, double* arena, const int* d_m, const int64_t* d_off, int nb,
+                         int max_m, int* d_flag, cudaStream_t s);
+awg_status trtri_batched(Handle* h, double* arena, const int* d_m, const int64_t* d_off, int nb,
+                         int max_m, cudaStream_t s);
+// Selected eigenpairs of symmetric blocks (destroys the blocks).  mode 0: all
+// eigenvalues <= zero_rtol * max|lambda| (counts strictly negative ones too);
+// mode 1: all eigenvalues < tau.  Returns host counts and device arenas of the
+// eigenvectors (column-major n^s x count) and eigenvalues.
+awg_status eig_select_batched(Handle* h, double* arena, const int* d_m, const int64_t* d_off,
+                              const std::vector<int>& h_m, int nb, int max_m, int mode,
+                              double param, std::vector<int>& h_count,
+                              std::vector<int>& h_strict, DevBuf& vecs,
+                              std::vector<int64_t>& h_vec_off, DevBuf& vals,
+                              std::vector<int>& h_val_ptr, cudaStream_t s);
+
+// solve.cu
+awg_status apply_stage(Handle* h, int which, int prec, const double* x, double* y, cudaStream_t s);
+awg_status build_setup_numeric(Handle* h);
+
+}  // namespace awg

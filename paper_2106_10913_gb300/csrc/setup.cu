@@ -1,0 +1,709 @@
+// Numeric setup of the AWG preconditioner on the device (Sections 3-4):
+//   1. eigen-split of every B^s (Def. 6): selected eigenpairs lambda <= 0;
+//   2. local factors: K^s = B^s + V^s_-(sigma I - L^s_-)V^s_-^T = A^s_+ + sigma
+//      V^s_- V^s_-^T is SPD; (A^s_+)^+ = P K^s^-1 P with P = I - V^s_- V^s_-^T
+//      (Section 4.4 item 3) from the Cholesky factor of K^s, stored as the
+//      explicit symmetric D^s (A^s_+)^+ D^s;
+//   3. GenEO pencil (M_A, M_B) = (D^s^-1 A^s_+ D^s^-1, R^s A_+ R^sT) with M_B
+//      from Section 4.4 item 4; reduced by the Cholesky factor of M_B to a
+//      standard symmetric problem; eigenvectors with lambda < tau (Def. 9);
+//   4. E = Z^T A_+ Z (Thm. 4), Cholesky, explicit inverse;
+//   5. W = A_+^-1 [R^sT V^s_-] (strictly negative eigenvalues, Section 4.4
+//      items 1-2) by PCG preconditioned with H_2 on all columns at once;
+//   6. F = W^T A W (Def. 10), Cholesky, explicit inverse; the reduced-
+//      precision copies of W and of the local operators, each with its own F.
+
+#include "awg_common.cuh"
+#include "ops.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <numeric>
+
+namespace awg {
+
+size_t ws_bytes(const Handle* h);
+awg_status set_smem_limits(Handle* h);
+
+// K = B + V diag(sigma - lambda) V^T with sigma = mean of diag(B)
+__global__ void k_form_K(const int* __restrict__ ns, const int64_t* __restrict__ off,
+                         const int* __restrict__ nm_ptr, const int64_t* __restrict__ vm_off,
+                         const double* __restrict__ V, const double* __restrict__ lam, double* arena,
+                         double* sigma) {
+    __shared__ double red[32];
+    __shared__ double wsh[256];
+    const int s = blockIdx.x;
+    const int m = ns[s];
+    double* K = arena + off[s];
+    double tr = 0.0;
+    for (int p = threadIdx.x; p < m; p += blockDim.x) tr += K[p + (size_t)p * m];
+    tr = block_sum(tr, red);
+    const double sg = tr / m;
+    if (threadIdx.x == 0) sigma[s] = sg;
+    const int l0 = nm_ptr[s], nu = nm_ptr[s + 1] - l0;
+    const double* Vs = V + vm_off[s];
+    for (int k0 = 0; k0 < nu; k0 += 256) {
+        const int kk = min(256, nu - k0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < kk; k += blockDim.x) wsh[k] = sg - lam[l0 + k0 + k];
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+            const int p = (int)(e % m), q = (int)(e / m);
+            double acc = 0.0;
+            for (int k = 0; k < kk; k++)
+                acc = fma(Vs[p + (size_t)(k0 + k) * m] * wsh[k], Vs[q + (size_t)(k0 + k) * m], acc);
+            K[e] += acc;
+        }
+    }
+}
+
+// G = D (Kinv - V T^T - T V^T + U V^T) D, T = Kinv V, U = V (V^T T)
+__global__ void k_form_G(const int* __restrict__ ns, const int64_t* __restrict__ off,
+                         const int* __restrict__ sub_ptr, const int* __restrict__ sub_idx,
+                         const double* __restrict__ dvec, const int* __restrict__ nm_ptr,
+                         const int64_t* __restrict__ vm_off, const double* __restrict__ V,
+                         const double* __restrict__ T, const double* __restrict__ U, double* arena) {
+    const int s = blockIdx.x;
+    const int m = ns[s];
+    double* G = arena + off[s];
+    const int nu = nm_ptr[s + 1] - nm_ptr[s];
+    const double* Vs = V + vm_off[s];
+    const double* Ts = T + vm_off[s];
+    const double* Us = U + vm_off[s];
+    const int* idx = sub_idx + sub_ptr[s];
+    for (int64_t e = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)m * m;
+         e += (int64_t)gridDim.y * blockDim.x) {
+        const int p = (int)(e % m), q = (int)(e / m);
+        double acc = G[e];
+        for (int k = 0; k < nu; k++) {
+            const double vp = Vs[p + (size_t)k * m], vq = Vs[q + (size_t)k * m];
+            acc -= vp * Ts[q + (size_t)k * m] + Ts[p + (size_t)k * m] * vq;
+            acc = fma(Us[p + (size_t)k * m], vq, acc);
+        }
+        G[e] = acc * dvec[idx[p]] * dvec[idx[q]];
+    }
+}
+
+// M_A = D^-1 (B + V |L| V^T) D^-1 in place over B
+__global__ void k_form_MA(const int* __restrict__ ns, const int64_t* __restrict__ off,
+                          const int* __restrict__ sub_ptr, const int* __restrict__ sub_idx,
+                          const double* __restrict__ dvec, const int* __restrict__ nm_ptr,
+                          const int64_t* __restrict__ vm_off, const double* __restrict__ V,
+                          const double* __restrict__ lam, double* arena) {
+    const int s = blockIdx.x;
+    const int m = ns[s];
+    double* M = arena + off[s];
+    const int l0 = nm_ptr[s], nu = nm_ptr[s + 1] - l0;
+    const double* Vs = V + vm_off[s];
+    const int* idx = sub_idx + sub_ptr[s];
+    for (int64_t e = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)m * m;
+         e += (int64_t)gridDim.y * blockDim.x) {
+        const int p = (int)(e % m), q = (int)(e / m);
+        double acc = M[e];
+        for (int k = 0; k < nu; k++)
+            acc = fma(Vs[p + (size_t)k * m] * (-lam[l0 + k]), Vs[q + (size_t)k * m], acc);
+        M[e] = acc / (dvec[idx[p]] * dvec[idx[q]]);
+    }
+}
+
+// M_B += sum_t R^s R^tT V^t_- |L^t_-| V^t_-^T R^t R^sT  (Section 4.4 item 4)
+__global__ void k_add_nbr_MB(const int* __restrict__ ns, const int64_t* __restrict__ off,
+                             const int* __restrict__ sub_ptr, const int* __restrict__ sub_idx,
+                             const int* __restrict__ inc_ptr, const int* __restrict__ inc_pos,
+                             const int* __restrict__ inc_sub, const int* __restrict__ nm_ptr,
+                             const int64_t* __restrict__ vm_off, const double* __restrict__ V,
+                             const double* __restrict__ lam, double* arena) {
+    const int s = blockIdx.x;
+    const int m = ns[s];
+    double* M = arena + off[s];
+    const int* idx = sub_idx + sub_ptr[s];
+    for (int64_t e = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)m * m;
+         e += (int64_t)gridDim.y * blockDim.x) {
+        const int p = (int)(e % m), q = (int)(e / m);
+        const int ip = idx[p], iq = idx[q];
+        double acc = 0.0;
+        for (int e1 = inc_ptr[ip]; e1 < inc_ptr[ip + 1]; e1++) {
+            const int t = inc_sub[e1];
+            const int nu = nm_ptr[t + 1] - nm_ptr[t];
+            if (nu == 0) continue;
+            for (int e2 = inc_ptr[iq]; e2 < inc_ptr[iq + 1]; e2++) {
+                if (inc_sub[e2] != t) continue;
+                const int mt = ns[t];
+                const int pt = inc_pos[e1] - sub_ptr[t], qt = inc_pos[e2] - sub_ptr[t];
+                const double* Vt = V + vm_off[t];
+                const double* lt = lam + nm_ptr[t];
+                for (int k = 0; k < nu; k++)
+                    acc = fma(Vt[pt + (size_t)k * mt] * (-lt[k]), Vt[qt + (size_t)k * mt], acc);
+            }
+        }
+        M[e] += acc;
+    }
+}
+
+__global__ void k_symmetrize(const int* __restrict__ ns, const int64_t* __restrict__ off,
+                             double* arena) {
+    const int s = blockIdx.x;
+    const int m = ns[s];
+    double* C = arena + off[s];
+    for (int64_t e = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)m * m;
+         e += (int64_t)gridDim.y * blockDim.x) {
+        const int p = (int)(e % m), q = (int)(e / m);
+        if (p > q) {
+            const double v = 0.5 * (C[e] + C[q + (size_t)p * m]);
+            C[e] = v;
+            C[q + (size_t)p * m] = v;
+        }
+    }
+}
+
+// Y (n x k, column-major) gets, for every global column g = colptr[s] + j in
+// [c0, c0 + k), column g - c0 = R^sT B_s(:, j); other rows untouched.
+__global__ void k_scatter_cols(int n, const int* __restrict__ sub_ptr,
+                               const int* __restrict__ sub_idx, const int* __restrict__ colptr,
+                               const int64_t* __restrict__ boff, const double* __restrict__ B,
+                               double* Y, int c0, int k) {
+    const int s = blockIdx.x;
+    const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
+    const int g0 = colptr[s], nc = colptr[s + 1] - g0;
+    const int ja = max(0, c0 - g0), jb = min(nc, c0 + k - g0);
+    if (ja >= jb) return;
+    const double* Bs = B + boff[s];
+    for (int64_t e = (int64_t)ja * m + threadIdx.x; e < (int64_t)jb * m; e += blockDim.x) {
+        const int p = (int)(e % m), j = (int)(e / m);
+        Y[(size_t)(g0 + j - c0) * n + sub_idx[p0 + p]] = Bs[e];
+    }
+}
+
+// row-major copy of a column-major n x k block into ld columns, in TS
+template <typename TS>
+__global__ void k_to_rowmajor(int n, int k, int ld, const double* __restrict__ X, TS* Y) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * ld) return;
+    const int i = (int)(e / ld), c = (int)(e % ld);
+    const double v = (c < k) ? X[(size_t)c * n + i] : 0.0;
+    Y[e] = (TS)v;
+}
+template <>
+__global__ void k_to_rowmajor<__nv_bfloat16>(int n, int k, int ld, const double* __restrict__ X,
+                                             __nv_bfloat16* Y) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * ld) return;
+    const int i = (int)(e / ld), c = (int)(e % ld);
+    Y[e] = __double2bfloat16((c < k) ? X[(size_t)c * n + i] : 0.0);
+}
+
+// FP64 copy of a rounded column-major block (rounding through TS)
+__global__ void k_round_f32(size_t len, const double* __restrict__ X, double* Y) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < len) Y[e] = (double)(float)X[e];
+}
+__global__ void k_round_bf16(size_t len, const double* __restrict__ X, double* Y) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < len) Y[e] = (double)__bfloat162float(__double2bfloat16(X[e]));
+}
+__global__ void k_conv_f32(size_t len, const double* __restrict__ X, float* Y) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < len) Y[e] = (float)X[e];
+}
+__global__ void k_conv_bf16(size_t len, const double* __restrict__ X, __nv_bfloat16* Y) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < len) Y[e] = __double2bfloat16(X[e]);
+}
+
+// per-column PCG updates
+__global__ void k_col_axpy(int n, const double* __restrict__ alpha, const double* __restrict__ X,
+                           double* Y) {
+    const size_t c = blockIdx.y;
+    const double a = alpha[c];
+    if (a == 0.0) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        Y[c * n + i] = fma(a, X[c * n + i], Y[c * n + i]);
+}
+__global__ void k_col_xpby(int n, const double* __restrict__ beta, const double* __restrict__ Zb,
+                           double* P) {
+    const size_t c = blockIdx.y;
+    const double b = beta[c];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        P[c * n + i] = fma(b, P[c * n + i], Zb[c * n + i]);
+}
+
+__global__ void k_diag_minus(int dim, const double* __restrict__ dgl, double* M) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < dim) M[i + (size_t)i * dim] = dgl[i] - M[i + (size_t)i * dim];
+}
+__global__ void k_neg_offdiag(int dim, double* M) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)dim * dim) return;
+    const int i = (int)(e % dim), j = (int)(e / dim);
+    if (i != j) M[e] = -M[e];
+}
+
+static double now_ms() {
+    return std::chrono::duration<double, std::milli>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+static awg_status check_flag(Handle* h, int mask, awg_status err) {
+    int f = 0;
+    AWG_TRY(read_flag(h, &f));
+    return (f & mask) ? err : AWG_OK;
+}
+
+// Cholesky + explicit inverse of one dense SPD matrix M (dim x dim) into Minv.
+static awg_status spd_inverse(Handle* h, DevBuf& M, DevBuf& Minv, int dim) {
+    cudaStream_t s = h->stream;
+    if (dim == 0) return AWG_OK;
+    DevBuf L, dm, doff;
+    AWG_TRY(dalloc(h, L, (size_t)dim * dim * 8));
+    AWG_CUDA(cudaMemcpyAsync(L.p, M.p, (size_t)dim * dim * 8, cudaMemcpyDeviceToDevice, s));
+    int64_t zero = 0;
+    AWG_TRY(upload(h, dm, &dim, sizeof(int)));
+    AWG_TRY(upload(h, doff, &zero, sizeof(int64_t)));
+    AWG_CUDA(cudaMemsetAsync(h->flag.p, 0, sizeof(int), s));
+    AWG_TRY(potrf_batched(h, (double*)L.p, (int*)dm.p, (int64_t*)doff.p, 1, dim, (int*)h->flag.p, s));
+    AWG_TRY(check_flag(h, FLAG_NOT_SPD, AWG_ERR_NOT_SPD));
+    AWG_TRY(trtri_batched(h, (double*)L.p, (int*)dm.p, (int64_t*)doff.p, 1, dim, s));
+    if (!Minv.p) AWG_TRY(dalloc(h, Minv, (size_t)dim * dim * 8));
+    AWG_TRY(gemm_batched(h, {{(double*)L.p, (double*)L.p, (double*)Minv.p, dim, dim, dim, dim, dim,
+                              dim, 1, 0, 1.0, 0.0}}, s));
+    AWG_CUDA(cudaStreamSynchronize(s));
+    dfree(h, L);
+    dfree(h, dm);
+    dfree(h, doff);
+    return AWG_OK;
+}
+
+// ------------------------------------------------------------ W by PCG
+static awg_status build_W(Handle* h) {
+    cudaStream_t s = h->stream;
+    const int n = h->n, N = h->N, nm = h->n_minus;
+    // right-hand sides Vhat = [R^sT V^s_-(strict)]
+    AWG_TRY(dalloc(h, h->Wcm, (size_t)n * nm * 8));
+    double* Vhat = nullptr;
+    AWG_CUDA(cudaMallocAsync(&Vhat, (size_t)n * nm * 8, s));
+    AWG_CUDA(cudaMemsetAsync(Vhat, 0, (size_t)n * nm * 8, s));
+    k_scatter_cols<<<N, 256, 0, s>>>(n, (int*)h->sub_ptr.p, (int*)h->sub_idx.p, (int*)h->wcol_ptr.p,
+                                     (int64_t*)h->vm_off.p, (double*)h->Vm.p, Vhat, 0, nm);
+    AWG_LAUNCH();
+    // columns per chunk: about 10 n-vectors per column live at once
+    const size_t budget = (size_t)24 << 30;
+    int chunk = (int)std::max<size_t>(1, std::min<size_t>(nm, budget / ((size_t)n * 8 * 12)));
+    double *R, *Zb, *P, *Q, *dots;
+    AWG_CUDA(cudaMallocAsync(&R, (size_t)n * chunk * 8, s));
+    AWG_CUDA(cudaMallocAsync(&Zb, (size_t)n * chunk * 8, s));
+    AWG_CUDA(cudaMallocAsync(&P, (size_t)n * chunk * 8, s));
+    AWG_CUDA(cudaMallocAsync(&Q, (size_t)n * chunk * 8, s));
+    AWG_CUDA(cudaMallocAsync(&dots, (size_t)chunk * 5 * 8, s));
+    std::vector<double> hb(chunk), hrz(chunk), hpq(chunk), hrr(chunk), hrzn(chunk), ha(chunk), hbeta(chunk);
+    int max_it = 0;
+    double worst = 0.0;
+    for (int c0 = 0; c0 < nm; c0 += chunk) {
+        const int k = std::min(chunk, nm - c0);
+        const size_t nk = (size_t)n * k;
+        double* X = (double*)h->Wcm.p + (size_t)c0 * n;
+        const double* Bc = Vhat + (size_t)c0 * n;
+        AWG_CUDA(cudaMemsetAsync(X, 0, nk * 8, s));
+        AWG_CUDA(cudaMemcpyAsync(R, Bc, nk * 8, cudaMemcpyDeviceToDevice, s));
+        AWG_TRY(col_dot(h, Bc, Bc, dots, k, s));
+        AWG_TRY(blk_h2(h, R, Zb, k, s));
+        AWG_TRY(col_dot(h, R, Zb, dots + chunk, k, s));
+        AWG_CUDA(cudaMemcpyAsync(P, Zb, nk * 8, cudaMemcpyDeviceToDevice, s));
+        AWG_CUDA(cudaMemcpyAsync(hb.data(), dots, k * 8, cudaMemcpyDeviceToHost, s));
+        AWG_CUDA(cudaMemcpyAsync(hrz.data(), dots + chunk, k * 8, cudaMemcpyDeviceToHost, s));
+        AWG_CUDA(cudaStreamSynchronize(s));
+        std::vector<char> active(k, 1);
+        int it = 0;
+        dim3 gcol((unsigned)std::min((n + 255) / 256, 64), (unsigned)k);
+        for (;;) {
+            AWG_TRY(blk_aplus(h, P, Q, k, s));
+            AWG_TRY(col_dot(h, P, Q, dots, k, s));
+            AWG_CUDA(cudaMemcpyAsync(hpq.data(), dots, k * 8, cudaMemcpyDeviceToHost, s));
+            AWG_CUDA(cudaStreamSynchronize(s));
+            for (int c = 0; c < k; c++) {
+                ha[c] = (active[c] && hpq[c] > 0.0) ? hrz[c] / hpq[c] : 0.0;
+                if (active[c] && !(hpq[c] > 0.0)) active[c] = 0;  // exact solution reached
+            }
+            AWG_CUDA(cudaMemcpyAsync(dots + 2 * chunk, ha.data(), k * 8, cudaMemcpyHostToDevice, s));
+            k_col_axpy<<<gcol, 256, 0, s>>>(n, dots + 2 * chunk, P, X);
+            AWG_LAUNCH();
+            for (int c = 0; c < k; c++) ha[c] = -ha[c];
+            AWG_CUDA(cudaMemcpyAsync(dots + 3 * chunk, ha.data(), k * 8, cudaMemcpyHostToDevice, s));
+            k_col_axpy<<<gcol, 256, 0, s>>>(n, dots + 3 * chunk, Q, R);
+            AWG_LAUNCH();
+            AWG_TRY(col_dot(h, R, R, dots, k, s));
+            AWG_CUDA(cudaMemcpyAsync(hrr.data(), dots, k * 8, cudaMemcpyDeviceToHost, s));
+            AWG_CUDA(cudaStreamSynchronize(s));
+            it++;
+            int nact = 0;
+            double wst = 0.0;
+            for (int c = 0; c < k; c++) {
+                const double rel = sqrt(hrr[c] / hb[c]);
+                if (rel <= h->opt.w_rtol) active[c] = 0;
+                if (active[c]) nact++;
+                wst = std::max(wst, rel);
+            }
+            if (nact == 0 || it >= h->opt.w_maxit) { worst = std::max(worst, wst); break; }
+            AWG_TRY(blk_h2(h, R, Zb, k, s));
+            AWG_TRY(col_dot(h, R, Zb, dots, k, s));
+            AWG_CUDA(cudaMemcpyAsync(hrzn.data(), dots, k * 8, cudaMemcpyDeviceToHost, s));
+            AWG_CUDA(cudaStreamSynchronize(s));
+            for (int c = 0; c < k; c++) {
+                hbeta[c] = (hrz[c] != 0.0) ? hrzn[c] / hrz[c] : 0.0;
+                hrz[c] = hrzn[c];
+            }
+            AWG_CUDA(cudaMemcpyAsync(dots + 4 * chunk, hbeta.data(), k * 8, cudaMemcpyHostToDevice, s));
+            k_col_xpby<<<gcol, 256, 0, s>>>(n, dots + 4 * chunk, Zb, P);
+            AWG_LAUNCH();
+        }
+        max_it = std::max(max_it, it);
+        if (h->opt.verbose)
+            fprintf(stderr, "libawg: W columns %d..%d: %d iterations, max relres %.3e\n", c0,
+                    c0 + k, it, worst);
+    }
+    h->w_iters = max_it;
+    h->w_relres = worst;
+    for (double* p : {Vhat, R, Zb, P, Q, dots}) AWG_CUDA(cudaFreeAsync(p, s));
+    AWG_CUDA(cudaStreamSynchronize(s));
+    return AWG_OK;
+}
+
+// F = Wt^T A Wt for a column-major (rounded) W, its inverse into Finv
+static awg_status build_F(Handle* h, const double* Wt, DevBuf& Finv, DevBuf* keepF) {
+    cudaStream_t s = h->stream;
+    const int n = h->n, nm = h->n_minus;
+    double* AW = nullptr;
+    AWG_CUDA(cudaMallocAsync(&AW, (size_t)n * nm * 8, s));
+    AWG_TRY(blk_spmm(h, Wt, AW, nm, s));
+    DevBuf F;
+    AWG_TRY(dalloc(h, F, (size_t)nm * nm * 8));
+    AWG_TRY(gemm_batched(h, {{Wt, AW, (double*)F.p, nm, nm, n, n, n, nm, 1, 0, 1.0, 0.0}}, s));
+    AWG_CUDA(cudaFreeAsync(AW, s));
+    int one = 1;
+    int64_t zero = 0;
+    DevBuf dm, doff;
+    AWG_TRY(upload(h, dm, &nm, sizeof(int)));
+    AWG_TRY(upload(h, doff, &zero, sizeof(int64_t)));
+    k_symmetrize<<<dim3(1, 64), 256, 0, s>>>((int*)dm.p, (int64_t*)doff.p, (double*)F.p);
+    AWG_LAUNCH();
+    (void)one;
+    AWG_TRY(spd_inverse(h, F, Finv, nm));
+    dfree(h, dm);
+    dfree(h, doff);
+    if (keepF) { dfree(h, *keepF); *keepF = F; } else dfree(h, F);
+    return AWG_OK;
+}
+
+// (C^-1 - Vhat^T Wt)^-1 for H_3,inex (Thm. 7), C = diag|L^s_-| (strict)
+static awg_status build_inex(Handle* h, const double* Wt, DevBuf& out) {
+    cudaStream_t s = h->stream;
+    const int n = h->n, nm = h->n_minus, N = h->N;
+    double *Vhat = nullptr, *loc = nullptr;
+    AWG_CUDA(cudaMallocAsync(&loc, (size_t)h->sum_ns * nm * 8, s));
+    AWG_TRY(blk_gather(h, Wt, loc, nm, s));
+    DevBuf M;
+    AWG_TRY(dalloc(h, M, (size_t)nm * nm * 8));
+    std::vector<GemmDesc> d;
+    const double* V = (const double*)h->Vm.p;
+    for (int t = 0; t < N; t++) {
+        const int m = h->h_ns[t], k = h->h_nstrict[t];
+        if (k == 0) continue;
+        d.push_back({V + h->h_vm_off[t], loc + (int64_t)h->h_sub_ptr[t] * nm, (double*)M.p + h->h_wcol_ptr[t],
+                     k, nm, m, m, m, nm, 1, 0, 1.0, 0.0});
+    }
+    AWG_TRY(gemm_batched(h, d, s));
+    // diag of C^-1 in wcol order
+    std::vector<double> lam(h->n_minus_all);
+    AWG_CUDA(cudaMemcpyAsync(lam.data(), h->lam_m.p, lam.size() * 8, cudaMemcpyDeviceToHost, s));
+    AWG_CUDA(cudaStreamSynchronize(s));
+    std::vector<double> cinv(nm);
+    for (int t = 0; t < N; t++)
+        for (int j = 0; j < h->h_nstrict[t]; j++) cinv[h->h_wcol_ptr[t] + j] = -1.0 / lam[h->h_nm_ptr[t] + j];
+    double* dcinv = nullptr;
+    AWG_CUDA(cudaMallocAsync(&dcinv, (size_t)nm * 8, s));
+    AWG_CUDA(cudaMemcpyAsync(dcinv, cinv.data(), nm * 8, cudaMemcpyHostToDevice, s));
+    // M = C^-1 - Vhat^T W
+    k_neg_offdiag<<<(unsigned)(((size_t)nm * nm + 255) / 256), 256, 0, s>>>(nm, (double*)M.p);
+    AWG_LAUNCH();
+    k_diag_minus<<<(nm + 255) / 256, 256, 0, s>>>(nm, dcinv, (double*)M.p);
+    AWG_LAUNCH();
+    int64_t zero = 0;
+    DevBuf dm, doff;
+    AWG_TRY(upload(h, dm, &nm, sizeof(int)));
+    AWG_TRY(upload(h, doff, &zero, sizeof(int64_t)));
+    k_symmetrize<<<dim3(1, 64), 256, 0, s>>>((int*)dm.p, (int64_t*)doff.p, (double*)M.p);
+    AWG_LAUNCH();
+    AWG_TRY(spd_inverse(h, M, out, nm));
+    dfree(h, M);
+    dfree(h, dm);
+    dfree(h, doff);
+    AWG_CUDA(cudaFreeAsync(loc, s));
+    AWG_CUDA(cudaFreeAsync(dcinv, s));
+    (void)Vhat;
+    return AWG_OK;
+}
+
+awg_status build_setup_numeric(Handle* h) {
+    cudaStream_t s = h->stream;
+    const int N = h->N, n = h->n;
+    const int maxm = h->max_ns;
+    double t0 = now_ms();
+    const dim3 gblk(N, 16);
+    // ---------------------------------------------- 1. eigen-split of B^s
+    DevBuf A1;
+    AWG_TRY(dalloc(h, A1, (size_t)h->dense_total * 8));
+    AWG_TRY(assemble_local(h, (double*)h->bval.p, (double*)A1.p));
+    std::vector<int> cnt, strict, vptr;
+    std::vector<int64_t> voff;
+    AWG_CUDA(cudaMemsetAsync(h->flag.p, 0, sizeof(int), s));
+    AWG_TRY(eig_select_batched(h, (double*)A1.p, (int*)h->ns.p, (int64_t*)h->dense_off.p, h->h_ns, N,
+                               maxm, 0, h->opt.zero_rtol, cnt, strict, h->Vm, voff, h->lam_m, vptr, s));
+    AWG_TRY(check_flag(h, FLAG_EIG, AWG_ERR_EIG));
+    h->h_nm = cnt;
+    h->h_nstrict = strict;
+    h->h_nm_ptr = vptr;
+    h->h_vm_off = voff;
+    h->n_minus_all = vptr[N];
+    h->h_wcol_ptr.assign(N + 1, 0);
+    for (int t = 0; t < N; t++) h->h_wcol_ptr[t + 1] = h->h_wcol_ptr[t] + strict[t];
+    h->n_minus = h->h_wcol_ptr[N];
+    AWG_TRY(upload(h, h->nm, cnt.data(), N * sizeof(int)));
+    AWG_TRY(upload(h, h->nstrict, strict.data(), N * sizeof(int)));
+    AWG_TRY(upload(h, h->nm_ptr, vptr.data(), (N + 1) * sizeof(int)));
+    AWG_TRY(upload(h, h->vm_off, voff.data(), (N + 1) * sizeof(int64_t)));
+    AWG_TRY(upload(h, h->wcol_ptr, h->h_wcol_ptr.data(), (N + 1) * sizeof(int)));
+    AWG_CUDA(cudaStreamSynchronize(s));
+    double t1 = now_ms();
+    h->setup_ms[1] = t1 - t0;
+
+    // ---------------------------------------------- 2. local factors
+    AWG_TRY(assemble_local(h, (double*)h->bval.p, (double*)A1.p));
+    AWG_TRY(dalloc(h, h->sigma, N * 8));
+    k_form_K<<<N, 256, 0, s>>>((int*)h->ns.p, (int64_t*)h->dense_off.p, (int*)h->nm_ptr.p,
+                               (int64_t*)h->vm_off.p, (double*)h->Vm.p, (double*)h->lam_m.p,
+                               (double*)A1.p, (double*)h->sigma.p);
+    AWG_LAUNCH();
+    AWG_CUDA(cudaMemsetAsync(h->flag.p, 0, sizeof(int), s));
+    AWG_TRY(potrf_batched(h, (double*)A1.p, (int*)h->ns.p, (int64_t*)h->dense_off.p, N, maxm,
+                          (int*)h->flag.p, s));
+    AWG_TRY(check_flag(h, FLAG_NOT_SPD, AWG_ERR_NOT_SPD));
+    AWG_TRY(trtri_batched(h, (double*)A1.p, (int*)h->ns.p, (int64_t*)h->dense_off.p, N, maxm, s));
+    DevBuf& G = h->prec[AWG_FP64].G;
+    AWG_TRY(dalloc(h, G, (size_t)h->dense_total * 8));
+    {
+        std::vector<GemmDesc> d;
+        const double* L = (const double*)A1.p;
+        for (int t = 0; t < N; t++) {
+            const int m = h->h_ns[t];
+            d.push_back({L + h->h_dense_off[t], L + h->h_dense_off[t], (double*)G.p + h->h_dense_off[t],
+                         m, m, m, m, m, m, 1, 0, 1.0, 0.0});
+        }
+        AWG_TRY(gemm_batched(h, d, s));  // K^-1 = L^-T L^-1
+    }
+    if (h->n_minus_all > 0) {
+        const size_t vlen = (size_t)voff[N];
+        double *T = nullptr, *S = nullptr, *U = nullptr;
+        AWG_CUDA(cudaMallocAsync(&T, vlen * 8, s));
+        AWG_CUDA(cudaMallocAsync(&U, vlen * 8, s));
+        size_t slen = 0;
+        std::vector<size_t> soff(N + 1, 0);
+        for (int t = 0; t < N; t++) soff[t + 1] = soff[t] + (size_t)cnt[t] * cnt[t];
+        slen = soff[N];
+        AWG_CUDA(cudaMallocAsync(&S, std::max<size_t>(slen, 1) * 8, s));
+        std::vector<GemmDesc> d1, d2, d3;
+        const double* V = (const double*)h->Vm.p;
+        for (int t = 0; t < N; t++) {
+            const int m = h->h_ns[t], nu = cnt[t];
+            if (nu == 0) continue;
+            const double* Kinv = (const double*)G.p + h->h_dense_off[t];
+            d1.push_back({Kinv, V + voff[t], T + voff[t], m, nu, m, m, m, m, 0, 0, 1.0, 0.0});
+            d2.push_back({V + voff[t], T + voff[t], S + soff[t], nu, nu, m, m, m, nu, 1, 0, 1.0, 0.0});
+            d3.push_back({V + voff[t], S + soff[t], U + voff[t], m, nu, nu, m, nu, m, 0, 0, 1.0, 0.0});
+        }
+        AWG_TRY(gemm_batched(h, d1, s));
+        AWG_TRY(gemm_batched(h, d2, s));
+        AWG_TRY(gemm_batched(h, d3, s));
+        k_form_G<<<gblk, 256, 0, s>>>((int*)h->ns.p, (int64_t*)h->dense_off.p, (int*)h->sub_ptr.p,
+                                      (int*)h->sub_idx.p, (double*)h->dvec.p, (int*)h->nm_ptr.p,
+                                      (int64_t*)h->vm_off.p, V, T, U, (double*)G.p);
+        AWG_LAUNCH();
+        for (double* p : {T, S, U}) AWG_CUDA(cudaFreeAsync(p, s));
+    } else {
+        k_form_G<<<gblk, 256, 0, s>>>((int*)h->ns.p, (int64_t*)h->dense_off.p, (int*)h->sub_ptr.p,
+                                      (int*)h->sub_idx.p, (double*)h->dvec.p, (int*)h->nm_ptr.p,
+                                      (int64_t*)h->vm_off.p, (double*)h->Vm.p, nullptr, nullptr,
+                                      (double*)G.p);
+        AWG_LAUNCH();
+    }
+    h->prec[AWG_FP64].built = true;
+    AWG_CUDA(cudaStreamSynchronize(s));
+    double t2 = now_ms();
+    h->setup_ms[2] = t2 - t1;
+
+    // ---------------------------------------------- 3. GenEO
+    // A1 <- M_B = R^s A R^sT + neighbour terms; A2 <- M_A
+    DevBuf A2, A3;
+    AWG_TRY(assemble_local(h, (double*)h->val.p, (double*)A1.p));
+    if (h->n_minus_all > 0) {
+        k_add_nbr_MB<<<gblk, 256, 0, s>>>((int*)h->ns.p, (int64_t*)h->dense_off.p, (int*)h->sub_ptr.p,
+                                          (int*)h->sub_idx.p, (int*)h->inc_ptr.p, (int*)h->inc_pos.p,
+                                          (int*)h->inc_sub.p, (int*)h->nm_ptr.p, (int64_t*)h->vm_off.p,
+                                          (double*)h->Vm.p, (double*)h->lam_m.p, (double*)A1.p);
+        AWG_LAUNCH();
+    }
+    AWG_TRY(dalloc(h, A2, (size_t)h->dense_total * 8));
+    AWG_TRY(assemble_local(h, (double*)h->bval.p, (double*)A2.p));
+    k_form_MA<<<gblk, 256, 0, s>>>((int*)h->ns.p, (int64_t*)h->dense_off.p, (int*)h->sub_ptr.p,
+                                   (int*)h->sub_idx.p, (double*)h->dvec.p, (int*)h->nm_ptr.p,
+                                   (int64_t*)h->vm_off.p, (double*)h->Vm.p, (double*)h->lam_m.p,
+                                   (double*)A2.p);
+    AWG_LAUNCH();
+    AWG_CUDA(cudaMemsetAsync(h->flag.p, 0, sizeof(int), s));
+    AWG_TRY(potrf_batched(h, (double*)A1.p, (int*)h->ns.p, (int64_t*)h->dense_off.p, N, maxm,
+                          (int*)h->flag.p, s));
+    AWG_TRY(check_flag(h, FLAG_NOT_SPD, AWG_ERR_NOT_SPD));
+    AWG_TRY(trtri_batched(h, (double*)A1.p, (int*)h->ns.p, (int64_t*)h->dense_off.p, N, maxm, s));
+    AWG_TRY(dalloc(h, A3, (size_t)h->dense_total * 8));
+    {
+        std::vector<GemmDesc> d1, d2;
+        const double* Li = (const double*)A1.p;
+        for (int t = 0; t < N; t++) {
+            const int m = h->h_ns[t];
+            const int64_t o = h->h_dense_off[t];
+            d1.push_back({Li + o, (double*)A2.p + o, (double*)A3.p + o, m, m, m, m, m, m, 0, 0, 1.0, 0.0});
+            d2.push_back({(double*)A3.p + o, Li + o, (double*)A2.p + o, m, m, m, m, m, m, 0, 1, 1.0, 0.0});
+        }
+        AWG_TRY(gemm_batched(h, d1, s));  // A3 = L^-1 M_A
+        AWG_TRY(gemm_batched(h, d2, s));  // A2 = A3 L^-T
+    }
+    dfree(h, A3);
+    k_symmetrize<<<gblk, 256, 0, s>>>((int*)h->ns.p, (int64_t*)h->dense_off.p, (double*)A2.p);
+    AWG_LAUNCH();
+    {
+        std::vector<int> mc, mcs, mptr;
+        std::vector<int64_t> qoff;
+        DevBuf Q, qvals;
+        AWG_CUDA(cudaMemsetAsync(h->flag.p, 0, sizeof(int), s));
+        AWG_TRY(eig_select_batched(h, (double*)A2.p, (int*)h->ns.p, (int64_t*)h->dense_off.p, h->h_ns,
+                                   N, maxm, 1, h->tau, mc, mcs, Q, qoff, qvals, mptr, s));
+        AWG_TRY(check_flag(h, FLAG_EIG, AWG_ERR_EIG));
+        h->h_modes = mc;
+        h->h_mode_ptr = mptr;
+        h->h_z_off = qoff;
+        h->n0 = mptr[N];
+        AWG_TRY(upload(h, h->modes, mc.data(), N * sizeof(int)));
+        AWG_TRY(upload(h, h->mode_ptr, mptr.data(), (N + 1) * sizeof(int)));
+        AWG_TRY(upload(h, h->z_off, qoff.data(), (N + 1) * sizeof(int64_t)));
+        AWG_TRY(dalloc(h, h->Z, std::max<size_t>(8, (size_t)qoff[N] * 8)));
+        std::vector<GemmDesc> d;
+        const double* Li = (const double*)A1.p;
+        for (int t = 0; t < N; t++) {
+            const int m = h->h_ns[t], k = mc[t];
+            if (k == 0) continue;
+            d.push_back({Li + h->h_dense_off[t], (double*)Q.p + qoff[t], (double*)h->Z.p + qoff[t], m, k, m,
+                         m, m, m, 1, 0, 1.0, 0.0});  // Y = L^-T Q
+        }
+        AWG_TRY(gemm_batched(h, d, s));
+        AWG_CUDA(cudaStreamSynchronize(s));
+        dfree(h, Q);
+        dfree(h, qvals);
+    }
+    dfree(h, A1);
+    dfree(h, A2);
+    double t3 = now_ms();
+    h->setup_ms[3] = t3 - t2;
+
+    // ---------------------------------------------- 4. E = Z^T A_+ Z
+    const int n0 = h->n0;
+    if (n0 > 0) {
+        AWG_TRY(dalloc(h, h->E, (size_t)n0 * n0 * 8));
+        const size_t budget = (size_t)16 << 30;
+        const int chunk = (int)std::max<size_t>(1, std::min<size_t>(n0, budget / ((size_t)n * 8 * 4)));
+        double *Zc = nullptr, *Qc = nullptr;
+        AWG_CUDA(cudaMallocAsync(&Zc, (size_t)n * chunk * 8, s));
+        AWG_CUDA(cudaMallocAsync(&Qc, (size_t)n * chunk * 8, s));
+        for (int c0 = 0; c0 < n0; c0 += chunk) {
+            const int k = std::min(chunk, n0 - c0);
+            AWG_CUDA(cudaMemsetAsync(Zc, 0, (size_t)n * k * 8, s));
+            k_scatter_cols<<<N, 256, 0, s>>>(n, (int*)h->sub_ptr.p, (int*)h->sub_idx.p,
+                                             (int*)h->mode_ptr.p, (int64_t*)h->z_off.p,
+                                             (double*)h->Z.p, Zc, c0, k);
+            AWG_LAUNCH();
+            AWG_TRY(blk_aplus(h, Zc, Qc, k, s));
+            AWG_TRY(blk_zt(h, Qc, (double*)h->E.p + (size_t)c0 * n0, k, s));
+        }
+        AWG_CUDA(cudaFreeAsync(Zc, s));
+        AWG_CUDA(cudaFreeAsync(Qc, s));
+        int64_t zero = 0;
+        DevBuf dm, doff;
+        AWG_TRY(upload(h, dm, &n0, sizeof(int)));
+        AWG_TRY(upload(h, doff, &zero, sizeof(int64_t)));
+        k_symmetrize<<<dim3(1, 64), 256, 0, s>>>((int*)dm.p, (int64_t*)doff.p, (double*)h->E.p);
+        AWG_LAUNCH();
+        dfree(h, dm);
+        dfree(h, doff);
+        AWG_TRY(spd_inverse(h, h->E, h->Einv, n0));
+    }
+    // workspace of the single-RHS apply
+    h->red_blocks = std::min(1216, std::max(1, (n + 127) / 128));
+    AWG_TRY(dalloc(h, h->ws, ws_bytes(h)));
+    AWG_TRY(set_smem_limits(h));
+    AWG_CUDA(cudaStreamSynchronize(s));
+    double t4 = now_ms();
+    h->setup_ms[4] = t4 - t3;
+
+    // ---------------------------------------------- 5. W, 6. F
+    const int nm = h->n_minus;
+    h->ldw = nm;
+    if (nm > 0) {
+        AWG_TRY(build_W(h));
+        double t5 = now_ms();
+        h->setup_ms[5] = t5 - t4;
+        const double* W64 = (const double*)h->Wcm.p;
+        PrecOps& P64 = h->prec[AWG_FP64];
+        AWG_TRY(build_F(h, W64, P64.Finv, &h->F64));
+        const bool inex = (h->opt.variant == AWG_H3_INEX) || (n <= 200000 && nm <= 4096);
+        if (inex) AWG_TRY(build_inex(h, W64, P64.inexInv));
+        AWG_TRY(dalloc(h, P64.W, (size_t)n * nm * 8));
+        const unsigned gw = (unsigned)(((size_t)n * nm + 255) / 256);
+        k_to_rowmajor<double><<<gw, 256, 0, s>>>(n, nm, nm, W64, (double*)P64.W.p);
+        AWG_LAUNCH();
+        for (int p = 1; p <= 2; p++) {
+            if (!(h->opt.precisions & (1 << p))) continue;
+            PrecOps& P = h->prec[p];
+            double* Wr = nullptr;
+            AWG_CUDA(cudaMallocAsync(&Wr, (size_t)n * nm * 8, s));
+            const size_t len = (size_t)n * nm;
+            if (p == AWG_MIXED_FP32) k_round_f32<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, W64, Wr);
+            else k_round_bf16<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, W64, Wr);
+            AWG_LAUNCH();
+            AWG_TRY(build_F(h, Wr, P.Finv, nullptr));
+            if (inex) AWG_TRY(build_inex(h, Wr, P.inexInv));
+            AWG_TRY(dalloc(h, P.W, len * (p == AWG_MIXED_FP32 ? 4 : 2)));
+            if (p == AWG_MIXED_FP32) k_to_rowmajor<float><<<gw, 256, 0, s>>>(n, nm, nm, Wr, (float*)P.W.p);
+            else k_to_rowmajor<__nv_bfloat16><<<gw, 256, 0, s>>>(n, nm, nm, Wr, (__nv_bfloat16*)P.W.p);
+            AWG_LAUNCH();
+            AWG_CUDA(cudaFreeAsync(Wr, s));
+        }
+        AWG_CUDA(cudaStreamSynchronize(s));
+        h->setup_ms[6] = now_ms() - t5;
+    }
+    // reduced-precision local operators
+    for (int p = 1; p <= 2; p++) {
+        if (!(h->opt.precisions & (1 << p))) continue;
+        PrecOps& P = h->prec[p];
+        const size_t len = (size_t)h->dense_total;
+        AWG_TRY(dalloc(h, P.G, len * (p == AWG_MIXED_FP32 ? 4 : 2)));
+        if (p == AWG_MIXED_FP32)
+            k_conv_f32<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, (double*)G.p, (float*)P.G.p);
+        else
+            k_conv_bf16<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, (double*)G.p, (__nv_bfloat16*)P.G.p);
+        AWG_LAUNCH();
+        P.built = true;
+    }
+    AWG_CUDA(cudaStreamSynchronize(s));
+    return AWG_OK;
+}
+
+}  // namespace awg

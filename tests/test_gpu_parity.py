@@ -1,0 +1,133 @@
+"""GPU path against the CPU oracle on the same seeded inputs (through the
+C ABI).
+
+* integer/index results (subdomain index lists, pair multiplicities,
+  eigenvalue counts, GenEO mode counts) must be bit-exact;
+* floating point: every stage of the apply within 1e-11 relative (FP64
+  path), 1e-4 for the FP32 storage path; PCG relative residual <= 1e-8
+  and iteration count within 5 % of the oracle's.
+"""
+
+import numpy as np
+import pytest
+
+import awg_inputs as gi
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+APPLY_RTOL = 1e-11
+MIXED_RTOL = 1e-4
+
+
+def _cases():
+    return {
+        "poisson12": gi.poisson2d(12, qx=2, overlap=1, tau=0.1, seed=0),
+        "poisson10x9_ov2": gi.poisson2d(10, ny=9, qx=3, qy=2, overlap=2, tau=0.2, seed=1),
+        "channels24": gi.channels2d(24, q=3, nchan=3, contrast=1e3, seed=5, overlap=2, tau=0.1),
+        "random_spd60": gi.random_spd(60, nparts=4, density=0.06, seed=3, overlap=1, tau=0.1),
+        "config1": gi.config1(),
+        "channels64": gi.channels2d(64, q=2, nchan=3, contrast=1e6, seed=11, overlap=2, tau=0.1),
+    }
+
+
+CASES = _cases()
+_SOLVERS = {}
+
+
+def _pair(name):
+    if name not in _SOLVERS:
+        from paper_2106_10913_gb300 import AWGSolver
+        p = CASES[name]
+        sol = AWGSolver(p.rowptr, p.colidx, p.val, p.part, p.nparts, p.overlap, p.tau,
+                        precisions=0b011)
+        st = O.setup_problem(p, dense=p.n <= 6000)
+        _SOLVERS[name] = (p, sol, st)
+    return _SOLVERS[name]
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def pair(request):
+    return _pair(request.param)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_structure_exact(pair):
+    p, sol, st = pair
+    ns = sol.array("ns")
+    assert ns.tolist() == [len(s) for s in st.subs]
+    idx = sol.array("sub_idx")
+    assert np.array_equal(idx, np.concatenate(st.subs))
+    Mmu = O.pair_multiplicity(st.A, st.subs)
+    coo = st.A.tocoo()
+    ref = np.asarray(Mmu.tocsr()[coo.row, coo.col]).ravel()
+    assert np.array_equal(sol.array("mmu"), ref)
+    assert np.array_equal(sol.array("dvec"), st.d)
+
+
+def test_counts_exact(pair):
+    p, sol, st = pair
+    mm = O.minus_counts(st)
+    assert sol.array("n_minus").tolist() == mm[:, 0].tolist()
+    assert sol.array("n_strict").tolist() == mm[:, 1].tolist()
+    assert sol.array("modes").tolist() == O.mode_counts(st).tolist()
+    assert sol.info["n0"] == st.n0 and sol.info["n_minus"] == st.n_minus
+
+
+def test_eigenvalues_of_split(pair):
+    p, sol, st = pair
+    lam = sol.array("lam_minus")
+    ref = np.concatenate([s.L_minus for s in st.splits]) if st.n_minus else np.zeros(0)
+    scale = max(np.max(np.abs(s.lam)) for s in st.splits)
+    assert np.max(np.abs(lam - ref), initial=0.0) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("stage", ["spmv", "aplus", "hnn", "h2", "h3ad", "h3hyb", "h3inex"])
+def test_stage_parity(pair, stage):
+    p, sol, st = pair
+    rng = np.random.default_rng(123)
+    x = rng.standard_normal(p.n)
+    ref = {
+        "spmv": lambda v: st.A @ v,
+        "aplus": lambda v: O.A_plus_apply(st, v),
+        "hnn": lambda v: O.H_NN_apply(st, v),
+        "h2": lambda v: O.H2_apply(st, v),
+        "h3ad": lambda v: O.H3_ad_apply(st, v),
+        "h3hyb": lambda v: O.H3_hyb_apply(st, v),
+        "h3inex": lambda v: O.H3_inex_apply(st, v),
+    }[stage](x)
+    y = sol.apply(torch.from_numpy(x).cuda(), stage=stage).cpu().numpy()
+    assert _rel(y, ref) <= APPLY_RTOL
+
+
+def test_mixed_fp32_apply(pair):
+    p, sol, st = pair
+    from paper_2106_10913_gb300 import MIXED_FP32
+    x = np.random.default_rng(5).standard_normal(p.n)
+    y = sol.apply(torch.from_numpy(x).cuda(), precision=MIXED_FP32).cpu().numpy()
+    assert _rel(y, O.H3_ad_apply(st, x)) <= MIXED_RTOL
+
+
+def test_pcg_parity(pair):
+    p, sol, st = pair
+    b = p.b if p.b.ndim == 1 else p.b[0]
+    ref = O.pcg(lambda v: st.A @ v, b, lambda r: O.H3_ad_apply(st, r), rtol=1e-8)
+    x, its, rel, status = sol.pcg(torch.from_numpy(b).cuda(), rtol=1e-8)
+    assert status == 0
+    assert rel[0] <= 1e-8
+    assert abs(its[0] - ref.iters) <= max(1, round(0.05 * ref.iters))
+    xs = x.cpu().numpy()
+    assert np.linalg.norm(st.A @ xs - b) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-12)
+
+
+def test_apply_deterministic(pair):
+    """Two applies of the same vector are bitwise identical (fixed-order sums)."""
+    p, sol, st = pair
+    x = torch.from_numpy(np.random.default_rng(9).standard_normal(p.n)).cuda()
+    a = sol.apply(x)
+    b = sol.apply(x)
+    assert torch.equal(a, b)
