@@ -68,10 +68,13 @@ typedef enum { AWG_H3_AD = 0, AWG_H3_HYB = 1, AWG_H3_INEX = 2 } awg_variant;
 
 /* Storage/arithmetic of the two largest operators of the apply: the local
  * pseudo-inverses D^s (A^s_+)^+ D^s and the second coarse basis W.  FP64
- * keeps everything in float64.  MIXED_FP32 / MIXED_BF16 store both in
- * float32 / bfloat16 with float32 accumulation, keep the PCG recurrences,
- * both coarse factorisations and solves and the GenEO selection test in
- * float64, and assemble F from the same rounded W (so H_3 stays SPD). */
+ * keeps everything in float64.  MIXED_FP32 stores both in float32 with
+ * float32 accumulation; MIXED_BF16 stores W in bfloat16 and the local
+ * operators in float32 (the explicit local pseudo-inverses carry
+ * cond(A^s_+), far beyond 8 mantissa bits on high-contrast problems).  Both
+ * keep the PCG recurrences, both coarse factorisations and solves and the
+ * GenEO selection test in float64, and assemble F from the same rounded W
+ * (so H_3 stays SPD). */
 typedef enum { AWG_FP64 = 0, AWG_MIXED_FP32 = 1, AWG_MIXED_BF16 = 2 } awg_precision;
 
 typedef struct {
@@ -85,6 +88,10 @@ typedef struct {
     int w_maxit;            /* iteration cap of those solves; default 500      */
     int maxit;              /* iteration cap of awg_pcg; default 1000          */
     int verbose;            /* 1: print setup stage timings to stderr          */
+    int w_precision;        /* local operators of H_2 inside the W solve:
+                               AWG_MIXED_FP32 (default; the outer PCG, its
+                               residuals and A_+ products stay float64, so W
+                               still converges to w_rtol) or AWG_FP64          */
 } awg_options;
 
 /* Per-handle figures reported after setup (cf. Table 1 of the paper). */
@@ -191,6 +198,33 @@ awg_status awg_pcg(awg_handle h, int precision, const double* d_b, double* d_x,
  * is too small.
  */
 awg_status awg_get_array(awg_handle h, int what, void* h_out, size_t count);
+
+/* Kernel classes timed by awg_profile (index into the arrays it returns). */
+enum {
+    AWG_PROF_SPMV = 0,       /* CSR SpMV                                  */
+    AWG_PROF_LOCAL = 1,      /* batched local pseudo-inverse GEMV         */
+    AWG_PROF_WT = 2,         /* W^T r, first pass over W                  */
+    AWG_PROF_WD = 3,         /* W d, second pass over W                   */
+    AWG_PROF_COARSE = 4,     /* dense E^-1 / F^-1 GEMVs                   */
+    AWG_PROF_SUBDOMAIN = 5,  /* block-sparse Z / V^s_- products           */
+    AWG_PROF_PROLONG = 6,    /* prolongation gathers                      */
+    AWG_PROF_VECTOR = 7,     /* PCG vector updates and dot products       */
+    AWG_NPROF = 8
+};
+
+/*
+ * Profiling of the apply / PCG path, for benchmarks.  awg_profile(h, mask)
+ * with mask != 0 resets and starts: every kernel the apply and PCG launch
+ * is counted, and each launch of a kernel class k with bit (1 << k) set in
+ * mask is bracketed by two CUDA events recorded on its own stream (up to a
+ * pool of 65536 events).  awg_profile(h, 0) stops.
+ * awg_profile_read synchronises the handle's last stream, and writes the
+ * launch count to *h_launches and, per kernel class, the summed event time
+ * (ms) and the number of timed launches to the HOST arrays h_ms[AWG_NPROF]
+ * and h_count[AWG_NPROF] (either may be NULL).
+ */
+awg_status awg_profile(awg_handle h, int enable);
+awg_status awg_profile_read(awg_handle h, int64_t* h_launches, double* h_ms, int64_t* h_count);
 
 #ifdef __cplusplus
 }

@@ -579,6 +579,15 @@ def setup_problem(prob, **kw) -> Setup:
                  subsets=prob.subsets, **kw)
 
 
+def local_condition(st: Setup) -> float:
+    """max_s lambda_max(A^s_+) / lambda_min+(A^s_+): the condition number of
+    the local pseudo-inverses.  Any backward-stable evaluation of
+    (A^s_+)^+ t (this oracle's eigenvector form, or a Cholesky route) has a
+    forward error of order local_condition * eps, which bounds how closely
+    two correct implementations of H^NN can agree."""
+    return float(max(s.L_plus.max() / s.L_plus.min() for s in st.splits if s.L_plus.size))
+
+
 def mode_counts(st: Setup) -> np.ndarray:
     """Per-subdomain GenEO mode count m^s (columns of Y_L)."""
     return np.array([Y.shape[1] for Y in st.Y], dtype=np.int64)

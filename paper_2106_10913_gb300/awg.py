@@ -39,7 +39,8 @@ class AWGError(RuntimeError):
 class awg_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("precisions", ctypes.c_int),
                 ("zero_rtol", ctypes.c_double), ("w_rtol", ctypes.c_double),
-                ("w_maxit", ctypes.c_int), ("maxit", ctypes.c_int), ("verbose", ctypes.c_int)]
+                ("w_maxit", ctypes.c_int), ("maxit", ctypes.c_int), ("verbose", ctypes.c_int),
+                ("w_precision", ctypes.c_int)]
 
 
 class awg_info(ctypes.Structure):
@@ -51,7 +52,9 @@ class awg_info(ctypes.Structure):
 
 
 EXPORTED = ["awg_default_options", "awg_status_string", "awg_setup", "awg_destroy",
-            "awg_get_info", "awg_apply", "awg_apply_stage", "awg_pcg", "awg_get_array"]
+            "awg_get_info", "awg_apply", "awg_apply_stage", "awg_pcg", "awg_get_array",
+            "awg_profile", "awg_profile_read"]
+PROF_NAMES = ["spmv", "local", "wt", "wd", "coarse", "subdomain", "prolong", "vector"]
 
 _lib = None
 
@@ -85,6 +88,11 @@ def load_library(path: str = LIB_PATH):
     lib.awg_pcg.restype = I
     lib.awg_get_array.argtypes = [P, I, P, S]
     lib.awg_get_array.restype = I
+    lib.awg_profile.argtypes = [P, I]
+    lib.awg_profile.restype = I
+    lib.awg_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D),
+                                     ctypes.POINTER(ctypes.c_int64)]
+    lib.awg_profile_read.restype = I
     _lib = lib
     return lib
 
@@ -168,6 +176,23 @@ def awg_get_array(h, what: str, size: int) -> np.ndarray:
     _check(load_library().awg_get_array(h, code, out.ctypes.data_as(ctypes.c_void_p), size),
            f"awg_get_array({what})")
     return out[:size]
+
+
+def awg_profile(h, mask: int):
+    """Start (mask = bit set of kernel classes to time, 0xFF all) or stop (0)."""
+    _check(load_library().awg_profile(h, int(mask)), "awg_profile")
+
+
+def awg_profile_read(h) -> dict:
+    """Launch count and per-kernel-class event time (ms) and launch counts."""
+    n = len(PROF_NAMES)
+    launches = ctypes.c_int64()
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    _check(load_library().awg_profile_read(h, ctypes.byref(launches), ms, cnt), "awg_profile_read")
+    return {"launches": launches.value,
+            "ms": {k: ms[i] for i, k in enumerate(PROF_NAMES)},
+            "count": {k: cnt[i] for i, k in enumerate(PROF_NAMES)}}
 
 
 # ------------------------------------------------------------- convenience class

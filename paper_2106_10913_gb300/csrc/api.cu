@@ -64,6 +64,8 @@ static void free_all(Handle* h) {
         dfree(h, P.Finv);
         dfree(h, P.inexInv);
     }
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    h->ev_pool.clear();
     if (h->h_flag) cudaFreeHost(h->h_flag);
     if (h->h_scal) cudaFreeHost(h->h_scal);
     h->h_flag = nullptr;
@@ -91,6 +93,7 @@ void awg_default_options(awg_options* opt) {
     opt->w_maxit = 500;
     opt->maxit = 1000;
     opt->verbose = 0;
+    opt->w_precision = AWG_MIXED_FP32;
 }
 
 const char* awg_status_string(awg_status s) {
@@ -155,7 +158,7 @@ awg_status awg_setup(int n, int nnz, const int* d_rowptr, const int* d_colidx, c
     awg_default_options(&o);
     if (opt) o = *opt;
     if (o.variant < 0 || o.variant > 2 || !(o.zero_rtol >= 0.0) || !(o.w_rtol > 0.0) ||
-        o.w_maxit < 1 || o.maxit < 1)
+        o.w_maxit < 1 || o.maxit < 1 || (o.w_precision != AWG_FP64 && o.w_precision != AWG_MIXED_FP32))
         return AWG_ERR_INVALID_ARG;
     o.precisions |= 1 << AWG_FP64;
     Handle* h = new (std::nothrow) Handle();
@@ -295,6 +298,45 @@ awg_status awg_get_array(awg_handle hh, int what, void* h_out, size_t count) {
     if (!src) return AWG_ERR_STATE;
     AWG_CUDA(cudaStreamSynchronize(h->stream));
     AWG_CUDA(cudaMemcpy(h_out, src, len * esz, cudaMemcpyDeviceToHost));
+    return AWG_OK;
+}
+
+awg_status awg_profile(awg_handle hh, int enable) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return AWG_ERR_INVALID_ARG;
+    if (enable) {
+        AWG_CUDA(cudaStreamSynchronize(h->stream));
+        if (h->ev_pool.empty()) {
+            h->ev_pool.resize(65536);
+            for (auto& e : h->ev_pool) AWG_CUDA(cudaEventCreate(&e));
+        }
+        h->ev_used = 0;
+        h->ev_kernel.clear();
+        h->launches = 0;
+        for (int i = 0; i < AWG_NPROF; i++) { h->prof_ms[i] = 0.0; h->prof_cnt[i] = 0; }
+    }
+    h->prof = enable;
+    return AWG_OK;
+}
+
+awg_status awg_profile_read(awg_handle hh, int64_t* h_launches, double* h_ms, int64_t* h_count) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return AWG_ERR_INVALID_ARG;
+    // resolve the recorded event pairs
+    for (size_t k = 0; k < h->ev_kernel.size(); k++) {
+        AWG_CUDA(cudaEventSynchronize(h->ev_pool[2 * k + 1]));
+        float ms = 0.f;
+        AWG_CUDA(cudaEventElapsedTime(&ms, h->ev_pool[2 * k], h->ev_pool[2 * k + 1]));
+        h->prof_ms[h->ev_kernel[k]] += ms;
+        h->prof_cnt[h->ev_kernel[k]] += 1;
+    }
+    h->ev_kernel.clear();
+    h->ev_used = 0;
+    if (h_launches) *h_launches = h->launches;
+    for (int i = 0; i < AWG_NPROF; i++) {
+        if (h_ms) h_ms[i] = h->prof_ms[i];
+        if (h_count) h_count[i] = h->prof_cnt[i];
+    }
     return AWG_OK;
 }
 

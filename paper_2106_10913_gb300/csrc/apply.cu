@@ -190,64 +190,145 @@ __global__ void __launch_bounds__(256) k_dense_gemv(int dim, const double* __res
 }
 
 // ------------------------------------------------- tall-skinny W (row-major)
-constexpr int WT_CPT = 16;  // columns per thread per chunk
+// W is stored row-major with ldw a multiple of 8 (rows 16-byte aligned, the
+// padding columns zero).  Each thread moves 16 bytes per load (2 float64,
+// 4 float32 or 8 bfloat16) with the streaming cache hint (W is read once per
+// pass and is far larger than L2) and accumulates in the compute type of the
+// storage (float64 for float64; float32 for float32 and bfloat16), never
+// converting element by element through float64, whose pipe is narrow on
+// this GPU.
+template <typename TS> struct Vec;
+template <> struct Vec<double> {
+    static constexpr int V = 2;
+    using A = double;
+    __device__ __forceinline__ static void load(const double* p, double* o) {
+        const double2 t = __ldcs(reinterpret_cast<const double2*>(p));
+        o[0] = t.x; o[1] = t.y;
+    }
+};
+template <> struct Vec<float> {
+    static constexpr int V = 4;
+    using A = float;
+    __device__ __forceinline__ static void load(const float* p, float* o) {
+        const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    }
+};
+template <> struct Vec<__nv_bfloat16> {
+    static constexpr int V = 8;
+    using A = float;
+    __device__ __forceinline__ static void load(const __nv_bfloat16* p, float* o) {
+        const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
+        const unsigned w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            o[2 * k] = __uint_as_float(w[k] << 16);          // low half: element 2k
+            o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+        }
+    }
+};
 
-template <typename TS>
-__device__ __forceinline__ double wval(const TS* W, size_t i) { return (double)to_f(W[i]); }
-template <>
-__device__ __forceinline__ double wval<double>(const double* W, size_t i) { return W[i]; }
+// V consecutive values of a 16-byte aligned shared array, 16 bytes per load
+template <typename A, int V>
+__device__ __forceinline__ void lds_vec(const A* p, A* o) {
+    static_assert((V * sizeof(A)) % 16 == 0, "vector width");
+#pragma unroll
+    for (int k = 0; k < (int)(V * sizeof(A) / 16); k++) {
+        const float4 t = reinterpret_cast<const float4*>(p)[k];
+        reinterpret_cast<float4*>(o)[k] = t;
+    }
+}
 
-// part[b*nm + c] = sum over the block's rows i of W(i, c) r(i)
-template <typename TS, typename TA>
-__global__ void __launch_bounds__(256) k_wt_partial(int n, int nm, int ldw, int rows,
-                                                    const TS* __restrict__ W,
-                                                    const double* __restrict__ r, double* part) {
+constexpr int WT_THREADS = 256;
+
+// part[b*ldw + c] = sum over the block's rows i of W(i, c) r(i)
+template <typename TS, int UNR>
+__global__ void __launch_bounds__(WT_THREADS) k_wt_partial(int n, int ldw, int rows,
+                                                           const TS* __restrict__ W,
+                                                           const double* __restrict__ r,
+                                                           double* part) {
+    using A = typename Vec<TS>::A;
+    constexpr int V = Vec<TS>::V;
     const int i0 = blockIdx.x * rows;
     const int i1 = min(n, i0 + rows);
-    for (int c0 = 0; c0 < nm; c0 += blockDim.x * WT_CPT) {
-        TA acc[WT_CPT];
+    for (int c0 = 0; c0 < ldw; c0 += WT_THREADS * V * UNR) {
+        A acc[UNR][V];
 #pragma unroll
-        for (int u = 0; u < WT_CPT; u++) acc[u] = 0;
+        for (int u = 0; u < UNR; u++)
+#pragma unroll
+            for (int j = 0; j < V; j++) acc[u][j] = 0;
         for (int i = i0; i < i1; i++) {
-            const TA ri = (TA)r[i];
+            const A ri = (A)r[i];
             const TS* row = W + (size_t)i * ldw;
 #pragma unroll
-            for (int u = 0; u < WT_CPT; u++) {
-                const int c = c0 + threadIdx.x + u * blockDim.x;
-                if (c < nm) acc[u] += (TA)wval<TS>(row, c) * ri;
+            for (int u = 0; u < UNR; u++) {
+                const int c = c0 + (u * WT_THREADS + threadIdx.x) * V;
+                if (c < ldw) {
+                    A w[V];
+                    Vec<TS>::load(row + c, w);
+#pragma unroll
+                    for (int j = 0; j < V; j++) acc[u][j] = fma(w[j], ri, acc[u][j]);
+                }
             }
         }
 #pragma unroll
-        for (int u = 0; u < WT_CPT; u++) {
-            const int c = c0 + threadIdx.x + u * blockDim.x;
-            if (c < nm) part[(size_t)blockIdx.x * nm + c] = (double)acc[u];
+        for (int u = 0; u < UNR; u++) {
+            const int c = c0 + (u * WT_THREADS + threadIdx.x) * V;
+            if (c < ldw) {
+#pragma unroll
+                for (int j = 0; j < V; j++) part[(size_t)blockIdx.x * ldw + c + j] = (double)acc[u][j];
+            }
         }
     }
 }
 
-__global__ void k_reduce_cols(int nb, int nm, const double* __restrict__ part, double* out) {
+__global__ void k_reduce_cols(int nb, int nm, int ldp, const double* __restrict__ part, double* out) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nm) return;
     double acc = 0.0;
-    for (int b = 0; b < nb; b++) acc += part[(size_t)b * nm + c];
+    for (int b = 0; b < nb; b++) acc += part[(size_t)b * ldp + c];
     out[c] = acc;
 }
 
-// z(i) = v(i) + sum_c W(i, c) d(c)   (warp per row)
-template <typename TS, typename TA>
+// z(i) = v(i) + sum_c W(i, c) d(c)   (one warp per row, d staged in shared
+// memory in the compute type, zero-padded to ldw)
+template <typename TS>
 __global__ void __launch_bounds__(256) k_w_d(int n, int nm, int ldw, const TS* __restrict__ W,
                                              const double* __restrict__ d, const double* v,
                                              double* z) {
-    extern __shared__ double ds[];
-    for (int c = threadIdx.x; c < nm; c += blockDim.x) ds[c] = d[c];
+    using A = typename Vec<TS>::A;
+    constexpr int V = Vec<TS>::V;
+    extern __shared__ __align__(16) unsigned char wd_smem[];
+    A* ds = reinterpret_cast<A*>(wd_smem);
+    for (int c = threadIdx.x; c < ldw; c += blockDim.x) ds[c] = (c < nm) ? (A)d[c] : (A)0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int nwb = blockDim.x >> 5;
     for (int i = blockIdx.x * nwb + (threadIdx.x >> 5); i < n; i += gridDim.x * nwb) {
         const TS* row = W + (size_t)i * ldw;
-        TA acc = 0;
-        for (int c = lane; c < nm; c += 32) acc += (TA)wval<TS>(row, c) * (TA)ds[c];
-        double a = (double)acc;
+        A acc0 = 0, acc1 = 0;
+        int c = lane * V;
+        for (; c + 32 * V < ldw; c += 64 * V) {
+            A w0[V], w1[V];
+            Vec<TS>::load(row + c, w0);
+            Vec<TS>::load(row + c + 32 * V, w1);
+            A d0[V], d1[V];
+            lds_vec<A, V>(ds + c, d0);
+            lds_vec<A, V>(ds + c + 32 * V, d1);
+#pragma unroll
+            for (int j = 0; j < V; j++) {
+                acc0 = fma(w0[j], d0[j], acc0);
+                acc1 = fma(w1[j], d1[j], acc1);
+            }
+        }
+        if (c < ldw) {
+            A w0[V], d0[V];
+            Vec<TS>::load(row + c, w0);
+            lds_vec<A, V>(ds + c, d0);
+#pragma unroll
+            for (int j = 0; j < V; j++) acc0 = fma(w0[j], d0[j], acc0);
+        }
+        double a = (double)(acc0 + acc1);
         a = warp_sum(a);
         if (lane == 0) z[i] = (v ? v[i] : 0.0) + a;
     }
@@ -327,7 +408,7 @@ static Ws ws_of(Handle* h) {
     w.loc = take(h->sum_ns); w.loc2 = take(h->sum_ns);
     w.cm = take(std::max(1, h->n_minus_all));
     w.part = take(4096);
-    w.wpart = take((size_t)h->red_blocks * nm);
+    w.wpart = take((size_t)h->red_blocks * std::max(8, h->ldw));
     return w;
 }
 
@@ -335,23 +416,29 @@ size_t ws_bytes(const Handle* h) {
     const size_t n = h->n, n0 = std::max(1, h->n0), nm = std::max(1, h->n_minus);
     auto r = [](size_t len) { return (len + 31) / 32 * 32; };
     size_t tot = 4 * r(n0) + 3 * r(nm) + 6 * r(n) + 2 * r(h->sum_ns) +
-                 r(std::max(1, h->n_minus_all)) + r(4096) + r((size_t)h->red_blocks * nm);
+                 r(std::max(1, h->n_minus_all)) + r(4096) + r((size_t)h->red_blocks * std::max(8, h->ldw));
     return tot * sizeof(double);
 }
 
 static int grid_n(int n) { return std::min((n + 255) / 256, 152 * 8); }
 
 awg_status spmv1(Handle* h, const double* x, double* y, double* pdot, cudaStream_t s) {
-    k_spmv<<<grid_n(h->n), 256, 0, s>>>(h->n, (int*)h->rowptr.p, (int*)h->colidx.p,
-                                        (double*)h->val.p, x, y, pdot);
+    {
+        ProfScope ps_(h, AWG_PROF_SPMV, s);
+        k_spmv<<<grid_n(h->n), 256, 0, s>>>(h->n, (int*)h->rowptr.p, (int*)h->colidx.p,
+                                            (double*)h->val.p, x, y, pdot);
+    }
     AWG_LAUNCH();
     return AWG_OK;
 }
 
 static awg_status prolong1(Handle* h, const double* loc, double* y, double alpha, double beta,
                            const double* z, double gamma, cudaStream_t s) {
-    k_prolong1<<<(h->n + 255) / 256, 256, 0, s>>>(h->n, (int*)h->inc_ptr.p, (int*)h->inc_pos.p, loc,
-                                                  y, alpha, beta, z, gamma);
+    {
+        ProfScope ps_(h, AWG_PROF_PROLONG, s);
+        k_prolong1<<<(h->n + 255) / 256, 256, 0, s>>>(h->n, (int*)h->inc_ptr.p, (int*)h->inc_pos.p, loc,
+                                                      y, alpha, beta, z, gamma);
+    }
     AWG_LAUNCH();
     return AWG_OK;
 }
@@ -365,12 +452,18 @@ static awg_status aminus1(Handle* h, const double* x, double* y, const double* y
         return AWG_OK;
     }
     const size_t sm = (size_t)h->max_ns * 8;
-    k_blk_tgemv<<<h->N, 256, sm, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p, (int*)h->nm_ptr.p,
-                                      (int64_t*)h->vm_off.p, (double*)h->Vm.p, x, w.cm);
+    {
+        ProfScope ps_(h, AWG_PROF_SUBDOMAIN, s);
+        k_blk_tgemv<<<h->N, 256, sm, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p, (int*)h->nm_ptr.p,
+                                          (int64_t*)h->vm_off.p, (double*)h->Vm.p, x, w.cm);
+    }
     AWG_LAUNCH();
-    k_blk_gemv<<<h->N, 256, (size_t)std::max(1, *std::max_element(h->h_nm.begin(), h->h_nm.end())) * 8, s>>>(
-        (int*)h->sub_ptr.p, (int*)h->nm_ptr.p, (int64_t*)h->vm_off.p, (double*)h->Vm.p, w.cm,
-        (double*)h->lam_m.p, -1.0, w.loc2);
+    {
+        ProfScope ps_(h, AWG_PROF_SUBDOMAIN, s);
+        k_blk_gemv<<<h->N, 256, (size_t)std::max(1, *std::max_element(h->h_nm.begin(), h->h_nm.end())) * 8, s>>>(
+            (int*)h->sub_ptr.p, (int*)h->nm_ptr.p, (int64_t*)h->vm_off.p, (double*)h->Vm.p, w.cm,
+            (double*)h->lam_m.p, -1.0, w.loc2);
+    }
     AWG_LAUNCH();
     return prolong1(h, w.loc2, y, sign, 0.0, yin, 1.0, s);
 }
@@ -381,7 +474,10 @@ static awg_status aplus1(Handle* h, const double* x, double* y, const double* yi
     AWG_TRY(spmv1(h, x, w.tmp2, nullptr, s));
     // tmp2 = A x ; y = yin + sign*(A x + A_- x)
     if (yin) {
-        k_sub<<<(h->n + 255) / 256, 256, 0, s>>>(h->n, yin, w.tmp2, w.tmp2);  // yin - A x
+        {
+            ProfScope ps_(h, AWG_PROF_VECTOR, s);
+            k_sub<<<(h->n + 255) / 256, 256, 0, s>>>(h->n, yin, w.tmp2, w.tmp2);
+        }  // yin - A x
         AWG_LAUNCH();
         if (sign != -1.0) return AWG_ERR_INVALID_ARG;
         return aminus1(h, x, y, w.tmp2, -1.0, w, s);
@@ -391,9 +487,12 @@ static awg_status aplus1(Handle* h, const double* x, double* y, const double* yi
 
 static awg_status zt1(Handle* h, const double* x, double* c, cudaStream_t s) {
     if (h->n0 == 0) return AWG_OK;
-    k_blk_tgemv<<<h->N, 256, (size_t)h->max_ns * 8, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p,
-                                                        (int*)h->mode_ptr.p, (int64_t*)h->z_off.p,
-                                                        (double*)h->Z.p, x, c);
+    {
+        ProfScope ps_(h, AWG_PROF_SUBDOMAIN, s);
+        k_blk_tgemv<<<h->N, 256, (size_t)h->max_ns * 8, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p,
+                                                            (int*)h->mode_ptr.p, (int64_t*)h->z_off.p,
+                                                            (double*)h->Z.p, x, c);
+    }
     AWG_LAUNCH();
     return AWG_OK;
 }
@@ -401,16 +500,20 @@ static awg_status zt1(Handle* h, const double* x, double* c, cudaStream_t s) {
 // loc = Z c (local slabs)
 static awg_status zloc1(Handle* h, const double* c, double* loc, cudaStream_t s) {
     const int mx = std::max(1, *std::max_element(h->h_modes.begin(), h->h_modes.end()));
-    k_blk_gemv<<<h->N, 256, (size_t)mx * 8, s>>>((int*)h->sub_ptr.p, (int*)h->mode_ptr.p,
-                                                 (int64_t*)h->z_off.p, (double*)h->Z.p, c,
-                                                 nullptr, 1.0, loc);
+    {
+        ProfScope ps_(h, AWG_PROF_SUBDOMAIN, s);
+        k_blk_gemv<<<h->N, 256, (size_t)mx * 8, s>>>((int*)h->sub_ptr.p, (int*)h->mode_ptr.p,
+                                                     (int64_t*)h->z_off.p, (double*)h->Z.p, c,
+                                                     nullptr, 1.0, loc);
+    }
     AWG_LAUNCH();
     return AWG_OK;
 }
 
-static awg_status dense_gemv(int dim, const double* M, const double* x, double* y, double alpha,
-                             const double* sub, double beta, cudaStream_t s) {
+static awg_status dense_gemv(Handle* h, int dim, const double* M, const double* x, double* y,
+                             double alpha, const double* sub, double beta, cudaStream_t s) {
     if (dim == 0) return AWG_OK;
+    ProfScope ps(h, AWG_PROF_COARSE, s);
     k_dense_gemv<<<(dim + 7) / 8, 256, 0, s>>>(dim, M, x, y, alpha, sub, beta);
     AWG_LAUNCH();
     return AWG_OK;
@@ -418,18 +521,24 @@ static awg_status dense_gemv(int dim, const double* M, const double* x, double* 
 
 static awg_status hnn1(Handle* h, int prec, const double* x, double* y, Ws& w, cudaStream_t s) {
     dim3 g(h->N, (h->max_ns + LG_ROWS - 1) / LG_ROWS);
-    const PrecOps& P = h->prec[prec];
-    if (prec == AWG_FP64) {
-        k_local_gemv64<<<g, 256, (size_t)h->max_ns * 8, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p,
-                                                             (int64_t*)h->dense_off.p,
-                                                             (double*)P.G.p, x, w.loc);
-    } else if (prec == AWG_MIXED_FP32) {
-        k_local_gemv_lp<float><<<g, 256, (size_t)h->max_ns * 4, s>>>(
-            (int*)h->sub_ptr.p, (int*)h->sub_idx.p, (int64_t*)h->dense_off.p, (float*)P.G.p, x, w.loc);
+    // the bfloat16 form keeps float32 local operators: the explicit local
+    // pseudo-inverses carry cond(A^s_+), which 8 mantissa bits cannot hold on
+    // high-contrast problems; only W (whose accuracy PCG tolerates) is bf16
+    const int gp = (prec == AWG_MIXED_BF16) ? AWG_MIXED_FP32 : prec;
+    const PrecOps& P = h->prec[gp];
+    if (gp == AWG_FP64) {
+        {
+            ProfScope ps_(h, AWG_PROF_LOCAL, s);
+            k_local_gemv64<<<g, 256, (size_t)h->max_ns * 8, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p,
+                                                                 (int64_t*)h->dense_off.p,
+                                                                 (double*)P.G.p, x, w.loc);
+        }
     } else {
-        k_local_gemv_lp<__nv_bfloat16><<<g, 256, (size_t)h->max_ns * 4, s>>>(
-            (int*)h->sub_ptr.p, (int*)h->sub_idx.p, (int64_t*)h->dense_off.p,
-            (__nv_bfloat16*)P.G.p, x, w.loc);
+        {
+            ProfScope ps_(h, AWG_PROF_LOCAL, s);
+            k_local_gemv_lp<float><<<g, 256, (size_t)h->max_ns * 4, s>>>(
+                (int*)h->sub_ptr.p, (int*)h->sub_idx.p, (int64_t*)h->dense_off.p, (float*)P.G.p, x, w.loc);
+        }
     }
     AWG_LAUNCH();
     return prolong1(h, w.loc, y, 1.0, 0.0, nullptr, 0.0, s);
@@ -438,7 +547,7 @@ static awg_status hnn1(Handle* h, int prec, const double* x, double* y, Ws& w, c
 // c = E^-1 Z^T x
 static awg_status coarse_e(Handle* h, const double* x, double* y0, double* c, cudaStream_t s) {
     AWG_TRY(zt1(h, x, y0, s));
-    return dense_gemv(h->n0, (double*)h->Einv.p, y0, c, 1.0, nullptr, 0.0, s);
+    return dense_gemv(h, h->n0, (double*)h->Einv.p, y0, c, 1.0, nullptr, 0.0, s);
 }
 
 // H_2 x = Pi H^NN Pi^T x + Z E^-1 Z^T x  (Thm. 4)
@@ -451,59 +560,65 @@ static awg_status h2_1(Handle* h, int prec, const double* r, double* z, Ws& w, c
     AWG_TRY(hnn1(h, prec, w.t, w.u, w, s));                 // u = H^NN t
     AWG_TRY(aplus1(h, w.u, w.q, nullptr, 1.0, w, s));        // q = A_+ u
     AWG_TRY(zt1(h, w.q, w.y2, s));
-    AWG_TRY(dense_gemv(h->n0, (double*)h->Einv.p, w.y2, w.c2, 1.0, w.c1, -1.0, s));  // c2 = E^-1 y2 - c1
+    AWG_TRY(dense_gemv(h, h->n0, (double*)h->Einv.p, w.y2, w.c2, 1.0, w.c1, -1.0, s));  // c2 = E^-1 y2 - c1
     AWG_TRY(zloc1(h, w.c2, w.loc, s));
     return prolong1(h, w.loc, z, -1.0, 0.0, w.u, 1.0, s);   // z = u - Z (c2 - c1)
 }
 
-template <typename TS, typename TA>
+template <typename TS, int UNR>
 static awg_status wt_r_t(Handle* h, const void* W, const double* r, double* out, Ws& w,
                          cudaStream_t s) {
     const int nb = h->red_blocks;
     const int rows = (h->n + nb - 1) / nb;
-    k_wt_partial<TS, TA><<<nb, 256, 0, s>>>(h->n, h->n_minus, h->ldw, rows, (const TS*)W, r, w.wpart);
+    {
+        ProfScope ps_(h, AWG_PROF_WT, s);
+        k_wt_partial<TS, UNR><<<nb, WT_THREADS, 0, s>>>(h->n, h->ldw, rows, (const TS*)W, r, w.wpart);
+    }
     AWG_LAUNCH();
-    k_reduce_cols<<<(h->n_minus + 255) / 256, 256, 0, s>>>(nb, h->n_minus, w.wpart, out);
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        k_reduce_cols<<<(h->n_minus + 255) / 256, 256, 0, s>>>(nb, h->n_minus, h->ldw, w.wpart, out);
+    }
     AWG_LAUNCH();
     return AWG_OK;
 }
 
 static awg_status wt_r(Handle* h, int prec, const double* r, double* out, Ws& w, cudaStream_t s) {
     const void* W = h->prec[prec].W.p;
-    if (prec == AWG_FP64) return wt_r_t<double, double>(h, W, r, out, w, s);
-    if (prec == AWG_MIXED_FP32) return wt_r_t<float, float>(h, W, r, out, w, s);
-    return wt_r_t<__nv_bfloat16, float>(h, W, r, out, w, s);
+    if (prec == AWG_FP64) return wt_r_t<double, 4>(h, W, r, out, w, s);
+    if (prec == AWG_MIXED_FP32) return wt_r_t<float, 4>(h, W, r, out, w, s);
+    return wt_r_t<__nv_bfloat16, 2>(h, W, r, out, w, s);
 }
 
 static awg_status w_d(Handle* h, int prec, const double* d, const double* v, double* z,
                       cudaStream_t s) {
     const void* W = h->prec[prec].W.p;
-    const size_t sm = (size_t)h->n_minus * 8;
     const int grid = std::min((h->n + 7) / 8, 152 * 16);
-    if (prec == AWG_FP64) {
-        k_w_d<double, double><<<grid, 256, sm, s>>>(h->n, h->n_minus, h->ldw, (const double*)W, d, v, z);
-    } else if (prec == AWG_MIXED_FP32) {
-        k_w_d<float, float><<<grid, 256, sm, s>>>(h->n, h->n_minus, h->ldw, (const float*)W, d, v, z);
-    } else {
-        k_w_d<__nv_bfloat16, float><<<grid, 256, sm, s>>>(h->n, h->n_minus, h->ldw,
-                                                          (const __nv_bfloat16*)W, d, v, z);
+    {
+        ProfScope ps_(h, AWG_PROF_WD, s);
+        if (prec == AWG_FP64)
+            k_w_d<double><<<grid, 256, (size_t)h->ldw * 8, s>>>(h->n, h->n_minus, h->ldw, (const double*)W, d, v, z);
+        else if (prec == AWG_MIXED_FP32)
+            k_w_d<float><<<grid, 256, (size_t)h->ldw * 4, s>>>(h->n, h->n_minus, h->ldw, (const float*)W, d, v, z);
+        else
+            k_w_d<__nv_bfloat16><<<grid, 256, (size_t)h->ldw * 4, s>>>(h->n, h->n_minus, h->ldw,
+                                                                      (const __nv_bfloat16*)W, d, v, z);
     }
     AWG_LAUNCH();
     return AWG_OK;
 }
 
 awg_status set_smem_limits(Handle* h) {
-    const int mx = (int)std::max<size_t>((size_t)h->max_ns * 8, (size_t)std::max(1, h->n_minus) * 8);
+    const int mx = (int)std::max<size_t>((size_t)h->max_ns * 8, (size_t)std::max(1, h->ldw) * 8);
     if (mx > 48 * 1024) {
         if (mx > 227 * 1024) return AWG_ERR_INVALID_ARG;
         AWG_CUDA(cudaFuncSetAttribute(k_blk_tgemv, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         AWG_CUDA(cudaFuncSetAttribute(k_blk_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         AWG_CUDA(cudaFuncSetAttribute(k_local_gemv64, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         AWG_CUDA(cudaFuncSetAttribute(k_local_gemv_lp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-        AWG_CUDA(cudaFuncSetAttribute(k_local_gemv_lp<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-        AWG_CUDA(cudaFuncSetAttribute(k_w_d<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-        AWG_CUDA(cudaFuncSetAttribute(k_w_d<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-        AWG_CUDA(cudaFuncSetAttribute(k_w_d<__nv_bfloat16, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        AWG_CUDA(cudaFuncSetAttribute(k_w_d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        AWG_CUDA(cudaFuncSetAttribute(k_w_d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        AWG_CUDA(cudaFuncSetAttribute(k_w_d<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     }
     return AWG_OK;
 }
@@ -520,7 +635,7 @@ awg_status apply_stage(Handle* h, int which, int prec, const double* x, double* 
         case 4: {  // H_3,ad = H_2 + W F^-1 W^T  (Def. 10)
             if (h->n_minus == 0) return h2_1(h, prec, x, y, w, s);
             AWG_TRY(wt_r(h, prec, x, w.w0, w, s));
-            AWG_TRY(dense_gemv(h->n_minus, (double*)h->prec[prec].Finv.p, w.w0, w.dd, 1.0, nullptr, 0, s));
+            AWG_TRY(dense_gemv(h, h->n_minus, (double*)h->prec[prec].Finv.p, w.w0, w.dd, 1.0, nullptr, 0, s));
             AWG_TRY(h2_1(h, prec, x, w.tmp, w, s));
             return w_d(h, prec, w.dd, w.tmp, y, s);
         }
@@ -528,21 +643,24 @@ awg_status apply_stage(Handle* h, int which, int prec, const double* x, double* 
             if (h->n_minus == 0) return h2_1(h, prec, x, y, w, s);
             const double* Finv = (double*)h->prec[prec].Finv.p;
             AWG_TRY(wt_r(h, prec, x, w.w0, w, s));
-            AWG_TRY(dense_gemv(h->n_minus, Finv, w.w0, w.dd, 1.0, nullptr, 0, s));  // d = F^-1 W^T x
+            AWG_TRY(dense_gemv(h, h->n_minus, Finv, w.w0, w.dd, 1.0, nullptr, 0, s));  // d = F^-1 W^T x
             AWG_TRY(w_d(h, prec, w.dd, nullptr, w.tmp, s));                        // tmp = W d
             AWG_TRY(spmv1(h, w.tmp, w.q, nullptr, s));
-            k_sub<<<(h->n + 255) / 256, 256, 0, s>>>(h->n, x, w.q, w.tmp);        // tmp = Pi_3^T x
+            {
+                ProfScope ps_(h, AWG_PROF_VECTOR, s);
+                k_sub<<<(h->n + 255) / 256, 256, 0, s>>>(h->n, x, w.q, w.tmp);
+            }        // tmp = Pi_3^T x
             AWG_LAUNCH();
             AWG_TRY(h2_1(h, prec, w.tmp, y, w, s));                                // y = v = H_2 Pi_3^T x
             AWG_TRY(spmv1(h, y, w.q, nullptr, s));                                 // q = A v
             AWG_TRY(wt_r(h, prec, w.q, w.w0, w, s));
-            AWG_TRY(dense_gemv(h->n_minus, Finv, w.w0, w.w1, -1.0, w.dd, 1.0, s)); // w1 = d - F^-1 W^T A v
+            AWG_TRY(dense_gemv(h, h->n_minus, Finv, w.w0, w.w1, -1.0, w.dd, 1.0, s)); // w1 = d - F^-1 W^T A v
             return w_d(h, prec, w.w1, y, y, s);                                     // z = v + W w1
         }
         case 6: {  // H_3,inex = H_2 + W (C^-1 - Vhat^T W)^-1 W^T  (Thm. 7)
             if (h->n_minus == 0) return h2_1(h, prec, x, y, w, s);
             AWG_TRY(wt_r(h, prec, x, w.w0, w, s));
-            AWG_TRY(dense_gemv(h->n_minus, (double*)h->prec[prec].inexInv.p, w.w0, w.dd, 1.0, nullptr, 0, s));
+            AWG_TRY(dense_gemv(h, h->n_minus, (double*)h->prec[prec].inexInv.p, w.w0, w.dd, 1.0, nullptr, 0, s));
             AWG_TRY(h2_1(h, prec, x, w.tmp, w, s));
             return w_d(h, prec, w.dd, w.tmp, y, s);
         }
@@ -554,9 +672,15 @@ awg_status apply_stage(Handle* h, int which, int prec, const double* x, double* 
 static awg_status dot1(Handle* h, const double* x, const double* y, double* out, Ws& w,
                        cudaStream_t s) {
     const int nb = grid_n(h->n);
-    k_dot_partial<<<nb, 256, 0, s>>>(h->n, x, y, w.part);
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        k_dot_partial<<<nb, 256, 0, s>>>(h->n, x, y, w.part);
+    }
     AWG_LAUNCH();
-    k_final_sum<<<1, 256, 0, s>>>(nb, w.part, out);
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        k_final_sum<<<1, 256, 0, s>>>(nb, w.part, out);
+    }
     AWG_LAUNCH();
     return AWG_OK;
 }
@@ -593,11 +717,20 @@ awg_status pcg1(Handle* h, int prec, int variant_stage, const double* b, double*
         while (!done) {
             if (it >= maxit) { st = AWG_ERR_MAXIT; break; }
             AWG_TRY(spmv1(h, p, q, w.part, s));                       // q = A p, partial p.q
-            k_final_sum<<<1, 256, 0, s>>>(nb, w.part, scal + S_PQ);
+            {
+                ProfScope ps_(h, AWG_PROF_VECTOR, s);
+                k_final_sum<<<1, 256, 0, s>>>(nb, w.part, scal + S_PQ);
+            }
             AWG_LAUNCH();
-            k_pcg_xr<<<nb, 256, 0, s>>>(n, scal, p, q, x, r, w.part + 1536);
+            {
+                ProfScope ps_(h, AWG_PROF_VECTOR, s);
+                k_pcg_xr<<<nb, 256, 0, s>>>(n, scal, p, q, x, r, w.part + 1536);
+            }
             AWG_LAUNCH();
-            k_final_sum<<<1, 256, 0, s>>>(nb, w.part + 1536, scal + S_RR);
+            {
+                ProfScope ps_(h, AWG_PROF_VECTOR, s);
+                k_final_sum<<<1, 256, 0, s>>>(nb, w.part + 1536, scal + S_RR);
+            }
             AWG_LAUNCH();
             it++;
             AWG_CUDA(cudaMemcpyAsync(h->h_scal, scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -608,7 +741,10 @@ awg_status pcg1(Handle* h, int prec, int variant_stage, const double* b, double*
             if (rel <= rtol) {
                 // confirm on the true residual b - A x
                 AWG_TRY(spmv1(h, x, q, nullptr, s));
-                k_sub<<<(n + 255) / 256, 256, 0, s>>>(n, b, q, q);
+                {
+                    ProfScope ps_(h, AWG_PROF_VECTOR, s);
+                    k_sub<<<(n + 255) / 256, 256, 0, s>>>(n, b, q, q);
+                }
                 AWG_LAUNCH();
                 AWG_TRY(dot1(h, q, q, scal + S_TR, w, s));
                 AWG_CUDA(cudaMemcpyAsync(h->h_scal, scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -621,15 +757,24 @@ awg_status pcg1(Handle* h, int prec, int variant_stage, const double* b, double*
             }
             AWG_TRY(apply_stage(h, variant_stage, prec, r, z, s));
             AWG_TRY(dot1(h, r, z, scal + S_RZN, w, s));
-            k_pcg_beta<<<1, 1, 0, s>>>(scal);
+            {
+                ProfScope ps_(h, AWG_PROF_VECTOR, s);
+                k_pcg_beta<<<1, 1, 0, s>>>(scal);
+            }
             AWG_LAUNCH();
-            k_pcg_p<<<nb, 256, 0, s>>>(n, scal, z, p);
+            {
+                ProfScope ps_(h, AWG_PROF_VECTOR, s);
+                k_pcg_p<<<nb, 256, 0, s>>>(n, scal, z, p);
+            }
             AWG_LAUNCH();
         }
     }
     if (st != AWG_OK || true_rel == rel) {
         AWG_TRY(spmv1(h, x, q, nullptr, s));
-        k_sub<<<(n + 255) / 256, 256, 0, s>>>(n, b, q, q);
+        {
+            ProfScope ps_(h, AWG_PROF_VECTOR, s);
+            k_sub<<<(n + 255) / 256, 256, 0, s>>>(n, b, q, q);
+        }
         AWG_LAUNCH();
         AWG_TRY(dot1(h, q, q, scal + S_TR, w, s));
         AWG_CUDA(cudaMemcpyAsync(h->h_scal, scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -118,6 +118,38 @@ struct Handle {
     int red_blocks = 0;
     int* h_flag = nullptr;               // pinned host mirror
     double* h_scal = nullptr;            // pinned host scalars
+
+    // profiling (awg_profile): launch count of the apply/PCG path and CUDA
+    // event times of its heaviest kernels
+    int prof = 0;
+    int64_t launches = 0;
+    double prof_ms[AWG_NPROF] = {0};
+    int64_t prof_cnt[AWG_NPROF] = {0};
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_kernel;          // kernel id of each recorded pair
+    size_t ev_used = 0;
+};
+
+// Brackets one launch with CUDA events on its stream when profiling is on.
+struct ProfScope {
+    Handle* h;
+    int id;
+    cudaStream_t s;
+    bool on;
+    ProfScope(Handle* hh, int kid, cudaStream_t ss) : h(hh), id(kid), s(ss), on(false) {
+        h->launches += (h->prof != 0);
+        if ((h->prof >> id) & 1 && h->ev_used + 2 <= h->ev_pool.size()) {
+            cudaEventRecord(h->ev_pool[h->ev_used], s);
+            on = true;
+        }
+    }
+    ~ProfScope() {
+        if (on) {
+            cudaEventRecord(h->ev_pool[h->ev_used + 1], s);
+            h->ev_kernel.push_back(id);
+            h->ev_used += 2;
+        }
+    }
 };
 
 awg_status dalloc(Handle* h, DevBuf& b, size_t bytes);
@@ -181,6 +213,15 @@ struct GemmDesc {
     double alpha, beta;
 };
 awg_status gemm_batched(Handle* h, const std::vector<GemmDesc>& descs, cudaStream_t s);
+struct GemmDescF {
+    const float* A;
+    const double* B;
+    double* C;
+    int M, N, K, lda, ldb, ldc;
+    int transA;
+    double alpha, beta;
+};
+awg_status gemm_batched_f32(Handle* h, const std::vector<GemmDescF>& descs, cudaStream_t s);
 awg_status potrf_batched(Handle* h, double* arena, const int* d_m, const int64_t* d_off, int nb,
                          int max_m, int* d_flag, cudaStream_t s);
 awg_status trtri_batched(Handle* h, double* arena, const int* d_m, const int64_t* d_off, int nb,

@@ -106,6 +106,90 @@ awg_status gemm_batched(Handle* h, const std::vector<GemmDesc>& descs, cudaStrea
     return AWG_OK;
 }
 
+// ------------------------------------------- batched GEMM, FP32 operands
+// C (float64) = alpha op(A) B + beta C with A float32, B float64 rounded to
+// float32 on load, float32 products and accumulation (the reduced-precision
+// local operators inside the multi-RHS solves).
+__global__ void __launch_bounds__(256) k_gemm_f32(const GemmDescF* __restrict__ descs, int tilesM) {
+    const GemmDescF d = descs[blockIdx.y];
+    const int tm = blockIdx.x % tilesM, tn = blockIdx.x / tilesM;
+    const int m0 = tm * GBM, n0 = tn * GBN;
+    if (m0 >= d.M || n0 >= d.N) return;
+    __shared__ float As[GBK][GBM + 4];
+    __shared__ float Bs[GBK][GBN + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[r][c] = 0.f;
+    for (int k0 = 0; k0 < d.K; k0 += GBK) {
+        for (int e = threadIdx.x; e < GBM * GBK; e += 256) {
+            int i, k;
+            if (!d.transA) { i = e % GBM; k = e / GBM; } else { k = e % GBK; i = e / GBK; }
+            const int gi = m0 + i, gk = k0 + k;
+            float v = 0.f;
+            if (gi < d.M && gk < d.K)
+                v = d.transA ? d.A[gk + (size_t)gi * d.lda] : d.A[gi + (size_t)gk * d.lda];
+            As[k][i] = v;
+        }
+        for (int e = threadIdx.x; e < GBN * GBK; e += 256) {
+            const int k = e % GBK, j = e / GBK;
+            const int gj = n0 + j, gk = k0 + k;
+            Bs[k][j] = (gj < d.N && gk < d.K) ? (float)d.B[gk + (size_t)gj * d.ldb] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GBK; k++) {
+            float a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; r++) a[r] = As[k][tx + 16 * r];
+#pragma unroll
+            for (int c = 0; c < 4; c++) b[c] = Bs[k][ty + 16 * c];
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const int gj = n0 + ty + 16 * c;
+        if (gj >= d.N) continue;
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int gi = m0 + tx + 16 * r;
+            if (gi >= d.M) continue;
+            double* cp = d.C + gi + (size_t)gj * d.ldc;
+            const double v = d.alpha * (double)acc[r][c];
+            *cp = (d.beta == 0.0) ? v : fma(d.beta, *cp, v);
+        }
+    }
+}
+
+awg_status gemm_batched_f32(Handle* h, const std::vector<GemmDescF>& descs, cudaStream_t s) {
+    if (descs.empty()) return AWG_OK;
+    int maxM = 0, maxN = 0;
+    for (auto& d : descs) { maxM = std::max(maxM, d.M); maxN = std::max(maxN, d.N); }
+    if (maxM == 0 || maxN == 0) return AWG_OK;
+    const int tilesM = (maxM + GBM - 1) / GBM, tilesN = (maxN + GBN - 1) / GBN;
+    const size_t chunk = 65535;
+    for (size_t b0 = 0; b0 < descs.size(); b0 += chunk) {
+        const size_t nb = std::min(chunk, descs.size() - b0);
+        GemmDescF* d_desc = nullptr;
+        AWG_CUDA(cudaMallocAsync(&d_desc, nb * sizeof(GemmDescF), s));
+        AWG_CUDA(cudaMemcpyAsync(d_desc, descs.data() + b0, nb * sizeof(GemmDescF),
+                                 cudaMemcpyHostToDevice, s));
+        dim3 grid((unsigned)(tilesM * tilesN), (unsigned)nb);
+        k_gemm_f32<<<grid, 256, 0, s>>>(d_desc, tilesM);
+        AWG_LAUNCH();
+        AWG_CUDA(cudaFreeAsync(d_desc, s));
+    }
+    (void)h;
+    return AWG_OK;
+}
+
 // ========================================================= batched Cholesky
 // Lower Cholesky factor in place (right-looking).  A pivot that is not
 // positive (or not finite) raises FLAG_NOT_SPD and stops that block.

@@ -178,19 +178,31 @@ awg_status blk_z(Handle* h, const double* C, double* Y, int k, double alpha, dou
     return AWG_OK;
 }
 
-awg_status blk_hnn(Handle* h, const double* X, double* Y, int k, cudaStream_t s) {
+awg_status blk_hnn(Handle* h, const double* X, double* Y, int k, cudaStream_t s, int prec) {
     double *loc = nullptr, *out = nullptr;
     AWG_CUDA(cudaMallocAsync(&loc, (size_t)h->sum_ns * k * 8, s));
     AWG_CUDA(cudaMallocAsync(&out, (size_t)h->sum_ns * k * 8, s));
     AWG_TRY(blk_gather(h, X, loc, k, s));
-    std::vector<GemmDesc> d;
-    const double* G = (const double*)h->prec[AWG_FP64].G.p;
-    for (int t = 0; t < h->N; t++) {
-        const int m = h->h_ns[t];
-        d.push_back({G + h->h_dense_off[t], loc + (int64_t)h->h_sub_ptr[t] * k,
-                     out + (int64_t)h->h_sub_ptr[t] * k, m, k, m, m, m, m, 0, 0, 1.0, 0.0});
+    if (prec == AWG_MIXED_FP32) {
+        std::vector<GemmDescF> d;
+        const float* G = (const float*)h->prec[AWG_MIXED_FP32].G.p;
+        if (!G) return AWG_ERR_STATE;
+        for (int t = 0; t < h->N; t++) {
+            const int m = h->h_ns[t];
+            d.push_back({G + h->h_dense_off[t], loc + (int64_t)h->h_sub_ptr[t] * k,
+                         out + (int64_t)h->h_sub_ptr[t] * k, m, k, m, m, m, m, 0, 1.0, 0.0});
+        }
+        AWG_TRY(gemm_batched_f32(h, d, s));
+    } else {
+        std::vector<GemmDesc> d;
+        const double* G = (const double*)h->prec[AWG_FP64].G.p;
+        for (int t = 0; t < h->N; t++) {
+            const int m = h->h_ns[t];
+            d.push_back({G + h->h_dense_off[t], loc + (int64_t)h->h_sub_ptr[t] * k,
+                         out + (int64_t)h->h_sub_ptr[t] * k, m, k, m, m, m, m, 0, 0, 1.0, 0.0});
+        }
+        AWG_TRY(gemm_batched(h, d, s));
     }
-    AWG_TRY(gemm_batched(h, d, s));
     AWG_TRY(blk_prolong(h, out, Y, k, 1.0, 0.0, s));
     AWG_CUDA(cudaFreeAsync(loc, s));
     AWG_CUDA(cudaFreeAsync(out, s));
@@ -210,10 +222,10 @@ static awg_status axpby(size_t len, double a, const double* x, double b, double*
     return AWG_OK;
 }
 
-awg_status blk_h2(Handle* h, const double* X, double* Y, int k, cudaStream_t s) {
+awg_status blk_h2(Handle* h, const double* X, double* Y, int k, cudaStream_t s, int prec) {
     const size_t nk = (size_t)h->n * k;
     const int n0 = h->n0;
-    if (n0 == 0) return blk_hnn(h, X, Y, k, s);
+    if (n0 == 0) return blk_hnn(h, X, Y, k, s, prec);
     double *C0, *C1, *X1, *T, *U;
     AWG_CUDA(cudaMallocAsync(&C0, (size_t)n0 * k * 8, s));
     AWG_CUDA(cudaMallocAsync(&C1, (size_t)n0 * k * 8, s));
@@ -229,7 +241,7 @@ awg_status blk_h2(Handle* h, const double* X, double* Y, int k, cudaStream_t s) 
     AWG_TRY(blk_aplus(h, X1, T, k, s));
     AWG_TRY(axpby(nk, 1.0, X, -1.0, T, s));
     // U = H^NN T
-    AWG_TRY(blk_hnn(h, T, U, k, s));
+    AWG_TRY(blk_hnn(h, T, U, k, s, prec));
     // C0 = E^-1 Z^T A_+ U ; Y = U - Z C0 + Z C1
     AWG_TRY(blk_aplus(h, U, T, k, s));
     AWG_TRY(blk_zt(h, T, X1, k, s));  // X1 reused as n0 x k scratch

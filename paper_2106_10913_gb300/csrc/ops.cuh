@@ -23,10 +23,13 @@ awg_status blk_zt(Handle* h, const double* X, double* C, int k, cudaStream_t s);
 // Y = beta Y + alpha Z C
 awg_status blk_z(Handle* h, const double* C, double* Y, int k, double alpha, double beta,
                  cudaStream_t s);
-// Y = H^NN X (FP64 local pseudo-inverses)
-awg_status blk_hnn(Handle* h, const double* X, double* Y, int k, cudaStream_t s);
+// Y = H^NN X with the local pseudo-inverses of precision `prec`
+// (AWG_FP64: float64 GEMM; AWG_MIXED_FP32: float32 operands and accumulation)
+awg_status blk_hnn(Handle* h, const double* X, double* Y, int k, cudaStream_t s,
+                   int prec = AWG_FP64);
 // Y = H_2 X = Pi H^NN Pi^T X + Z E^-1 Z^T X
-awg_status blk_h2(Handle* h, const double* X, double* Y, int k, cudaStream_t s);
+awg_status blk_h2(Handle* h, const double* X, double* Y, int k, cudaStream_t s,
+                  int prec = AWG_FP64);
 
 // column-wise helpers (k columns of length n, ld = n)
 awg_status col_dot(Handle* h, const double* X, const double* Y, double* out, int k, cudaStream_t s);

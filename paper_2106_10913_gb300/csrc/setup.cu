@@ -206,10 +206,6 @@ __global__ void k_conv_f32(size_t len, const double* __restrict__ X, float* Y) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e < len) Y[e] = (float)X[e];
 }
-__global__ void k_conv_bf16(size_t len, const double* __restrict__ X, __nv_bfloat16* Y) {
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < len) Y[e] = __double2bfloat16(X[e]);
-}
 
 // per-column PCG updates
 __global__ void k_col_axpy(int n, const double* __restrict__ alpha, const double* __restrict__ X,
@@ -289,8 +285,10 @@ static awg_status build_W(Handle* h) {
     AWG_LAUNCH();
     // columns per chunk: about 10 n-vectors per column live at once
     const size_t budget = (size_t)24 << 30;
-    int chunk = (int)std::max<size_t>(1, std::min<size_t>(nm, budget / ((size_t)n * 8 * 12)));
-    double *R, *Zb, *P, *Q, *dots;
+    int chunk = (int)std::max<size_t>(1, std::min<size_t>(nm, budget / ((size_t)n * 8 * 13)));
+    const int wp = h->opt.w_precision;
+    double *R, *Zb, *Zo, *P, *Q, *dots;
+    AWG_CUDA(cudaMallocAsync(&Zo, (size_t)n * chunk * 8, s));
     AWG_CUDA(cudaMallocAsync(&R, (size_t)n * chunk * 8, s));
     AWG_CUDA(cudaMallocAsync(&Zb, (size_t)n * chunk * 8, s));
     AWG_CUDA(cudaMallocAsync(&P, (size_t)n * chunk * 8, s));
@@ -307,7 +305,7 @@ static awg_status build_W(Handle* h) {
         AWG_CUDA(cudaMemsetAsync(X, 0, nk * 8, s));
         AWG_CUDA(cudaMemcpyAsync(R, Bc, nk * 8, cudaMemcpyDeviceToDevice, s));
         AWG_TRY(col_dot(h, Bc, Bc, dots, k, s));
-        AWG_TRY(blk_h2(h, R, Zb, k, s));
+        AWG_TRY(blk_h2(h, R, Zb, k, s, wp));
         AWG_TRY(col_dot(h, R, Zb, dots + chunk, k, s));
         AWG_CUDA(cudaMemcpyAsync(P, Zb, nk * 8, cudaMemcpyDeviceToDevice, s));
         AWG_CUDA(cudaMemcpyAsync(hb.data(), dots, k * 8, cudaMemcpyDeviceToHost, s));
@@ -345,12 +343,17 @@ static awg_status build_W(Handle* h) {
                 wst = std::max(wst, rel);
             }
             if (nact == 0 || it >= h->opt.w_maxit) { worst = std::max(worst, wst); break; }
-            AWG_TRY(blk_h2(h, R, Zb, k, s));
+            // flexible (Polak-Ribiere) beta = r^T (z - z_old) / r_old^T z_old: the
+            // preconditioner may apply its local operators in float32
+            std::swap(Zb, Zo);
+            AWG_TRY(blk_h2(h, R, Zb, k, s, wp));
             AWG_TRY(col_dot(h, R, Zb, dots, k, s));
+            AWG_TRY(col_dot(h, R, Zo, dots + chunk, k, s));
             AWG_CUDA(cudaMemcpyAsync(hrzn.data(), dots, k * 8, cudaMemcpyDeviceToHost, s));
+            AWG_CUDA(cudaMemcpyAsync(hpq.data(), dots + chunk, k * 8, cudaMemcpyDeviceToHost, s));
             AWG_CUDA(cudaStreamSynchronize(s));
             for (int c = 0; c < k; c++) {
-                hbeta[c] = (hrz[c] != 0.0) ? hrzn[c] / hrz[c] : 0.0;
+                hbeta[c] = (hrz[c] != 0.0) ? (hrzn[c] - hpq[c]) / hrz[c] : 0.0;
                 hrz[c] = hrzn[c];
             }
             AWG_CUDA(cudaMemcpyAsync(dots + 4 * chunk, hbeta.data(), k * 8, cudaMemcpyHostToDevice, s));
@@ -364,7 +367,7 @@ static awg_status build_W(Handle* h) {
     }
     h->w_iters = max_it;
     h->w_relres = worst;
-    for (double* p : {Vhat, R, Zb, P, Q, dots}) AWG_CUDA(cudaFreeAsync(p, s));
+    for (double* p : {Vhat, R, Zb, Zo, P, Q, dots}) AWG_CUDA(cudaFreeAsync(p, s));
     AWG_CUDA(cudaStreamSynchronize(s));
     return AWG_OK;
 }
@@ -468,6 +471,7 @@ awg_status build_setup_numeric(Handle* h) {
     h->h_wcol_ptr.assign(N + 1, 0);
     for (int t = 0; t < N; t++) h->h_wcol_ptr[t + 1] = h->h_wcol_ptr[t] + strict[t];
     h->n_minus = h->h_wcol_ptr[N];
+    h->ldw = (h->n_minus + 7) / 8 * 8;  // W rows 16-byte aligned for vector loads
     AWG_TRY(upload(h, h->nm, cnt.data(), N * sizeof(int)));
     AWG_TRY(upload(h, h->nstrict, strict.data(), N * sizeof(int)));
     AWG_TRY(upload(h, h->nm_ptr, vptr.data(), (N + 1) * sizeof(int)));
@@ -653,9 +657,17 @@ awg_status build_setup_numeric(Handle* h) {
     double t4 = now_ms();
     h->setup_ms[4] = t4 - t3;
 
+    // float32 local operators: used by the float32 and bfloat16 apply forms
+    // (the bfloat16 form rounds only W) and by the W solve's preconditioner
+    if ((h->opt.precisions & 6) || h->opt.w_precision == AWG_MIXED_FP32) {
+        PrecOps& P = h->prec[AWG_MIXED_FP32];
+        const size_t len = (size_t)h->dense_total;
+        AWG_TRY(dalloc(h, P.G, len * 4));
+        k_conv_f32<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, (double*)G.p, (float*)P.G.p);
+        AWG_LAUNCH();
+    }
     // ---------------------------------------------- 5. W, 6. F
     const int nm = h->n_minus;
-    h->ldw = nm;
     if (nm > 0) {
         AWG_TRY(build_W(h));
         double t5 = now_ms();
@@ -665,9 +677,9 @@ awg_status build_setup_numeric(Handle* h) {
         AWG_TRY(build_F(h, W64, P64.Finv, &h->F64));
         const bool inex = (h->opt.variant == AWG_H3_INEX) || (n <= 200000 && nm <= 4096);
         if (inex) AWG_TRY(build_inex(h, W64, P64.inexInv));
-        AWG_TRY(dalloc(h, P64.W, (size_t)n * nm * 8));
-        const unsigned gw = (unsigned)(((size_t)n * nm + 255) / 256);
-        k_to_rowmajor<double><<<gw, 256, 0, s>>>(n, nm, nm, W64, (double*)P64.W.p);
+        AWG_TRY(dalloc(h, P64.W, (size_t)n * h->ldw * 8));
+        const unsigned gw = (unsigned)(((size_t)n * h->ldw + 255) / 256);
+        k_to_rowmajor<double><<<gw, 256, 0, s>>>(n, nm, h->ldw, W64, (double*)P64.W.p);
         AWG_LAUNCH();
         for (int p = 1; p <= 2; p++) {
             if (!(h->opt.precisions & (1 << p))) continue;
@@ -680,28 +692,17 @@ awg_status build_setup_numeric(Handle* h) {
             AWG_LAUNCH();
             AWG_TRY(build_F(h, Wr, P.Finv, nullptr));
             if (inex) AWG_TRY(build_inex(h, Wr, P.inexInv));
-            AWG_TRY(dalloc(h, P.W, len * (p == AWG_MIXED_FP32 ? 4 : 2)));
-            if (p == AWG_MIXED_FP32) k_to_rowmajor<float><<<gw, 256, 0, s>>>(n, nm, nm, Wr, (float*)P.W.p);
-            else k_to_rowmajor<__nv_bfloat16><<<gw, 256, 0, s>>>(n, nm, nm, Wr, (__nv_bfloat16*)P.W.p);
+            AWG_TRY(dalloc(h, P.W, (size_t)n * h->ldw * (p == AWG_MIXED_FP32 ? 4 : 2)));
+            if (p == AWG_MIXED_FP32) k_to_rowmajor<float><<<gw, 256, 0, s>>>(n, nm, h->ldw, Wr, (float*)P.W.p);
+            else k_to_rowmajor<__nv_bfloat16><<<gw, 256, 0, s>>>(n, nm, h->ldw, Wr, (__nv_bfloat16*)P.W.p);
             AWG_LAUNCH();
             AWG_CUDA(cudaFreeAsync(Wr, s));
         }
         AWG_CUDA(cudaStreamSynchronize(s));
         h->setup_ms[6] = now_ms() - t5;
     }
-    // reduced-precision local operators
-    for (int p = 1; p <= 2; p++) {
-        if (!(h->opt.precisions & (1 << p))) continue;
-        PrecOps& P = h->prec[p];
-        const size_t len = (size_t)h->dense_total;
-        AWG_TRY(dalloc(h, P.G, len * (p == AWG_MIXED_FP32 ? 4 : 2)));
-        if (p == AWG_MIXED_FP32)
-            k_conv_f32<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, (double*)G.p, (float*)P.G.p);
-        else
-            k_conv_bf16<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, (double*)G.p, (__nv_bfloat16*)P.G.p);
-        AWG_LAUNCH();
-        P.built = true;
-    }
+    for (int p = 1; p <= 2; p++)
+        if (h->opt.precisions & (1 << p)) h->prec[p].built = true;
     AWG_CUDA(cudaStreamSynchronize(s));
     return AWG_OK;
 }
