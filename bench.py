@@ -209,6 +209,7 @@ def run_awg(args):
         its, rels, sts = [], [], []
         with ClockSampler(local) as clk:
             barrier()
+            torch.cuda.nvtx.range_push(f"timed_{name}")
             ev0.record(stream)
             for _ in range(args.steps):
                 st, it, rel = awg_pcg(sol.h, b, x, RTOL, prec, check=False)
@@ -216,6 +217,7 @@ def run_awg(args):
                 rels.append(rel[0])
                 sts.append(st)
             ev1.record(stream)
+            torch.cuda.nvtx.range_pop()
             barrier()
         prof = awg_profile_read(sol.h)
         awg_profile(sol.h, 0)
