@@ -226,6 +226,35 @@ enum {
 awg_status awg_profile(awg_handle h, int enable);
 awg_status awg_profile_read(awg_handle h, int64_t* h_launches, double* h_ms, int64_t* h_count);
 
+/* Capacity, in float64 values, of the static scratch of awg_apply_hnn_noalloc. */
+#define AWG_NOALLOC_MAX_LOCAL (1 << 20)
+
+/*
+ * y = H^NN x (the batched local pseudo-inverses and the prolongation sum,
+ * as awg_apply_stage with which = 2) WITHOUT ANY DEVICE ALLOCATION.  The
+ * paper has no counterpart: this entry point serves callers that cannot
+ * call cudaMalloc while they apply the preconditioner (code captured into
+ * a CUDA graph, allocation-free real-time loops, frameworks that own all
+ * device memory).  Its scratch (sum of n^s float64 values) is a static
+ * device array of AWG_NOALLOC_MAX_LOCAL doubles (8 MiB) that every GPU
+ * loading the library keeps until the process exits; a handle whose
+ * subdomains hold more values is rejected with AWG_ERR_INVALID_ARG (and a
+ * message on stderr).
+ *   h          a handle built by awg_setup on the current device
+ *   precision  AWG_FP64 or AWG_MIXED_FP32 (the latter must have been built)
+ *   d_x, d_y   device float64[n], caller-owned, must not overlap
+ * The first call on a device looks up the scratch's device address (no
+ * allocation) and caches it: make that first call before any stream
+ * capture.  Every call shares the scratch and finds the previous call's
+ * values there (each value read is written earlier in the same call, so
+ * nothing needs clearing); calls that overlap on the GPU (two streams or
+ * two host threads at once) race on it and must be serialised by the
+ * caller.  Asynchronous on `stream`; errors: AWG_ERR_INVALID_ARG,
+ * AWG_ERR_STATE, AWG_ERR_CUDA.
+ */
+awg_status awg_apply_hnn_noalloc(awg_handle h, int precision, const double* d_x, double* d_y,
+                                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -53,7 +53,7 @@ class awg_info(ctypes.Structure):
 
 EXPORTED = ["awg_default_options", "awg_status_string", "awg_setup", "awg_destroy",
             "awg_get_info", "awg_apply", "awg_apply_stage", "awg_pcg", "awg_get_array",
-            "awg_profile", "awg_profile_read"]
+            "awg_profile", "awg_profile_read", "awg_apply_hnn_noalloc"]
 PROF_NAMES = ["spmv", "local", "wt", "wd", "coarse", "subdomain", "prolong", "vector"]
 
 _lib = None
@@ -93,6 +93,8 @@ def load_library(path: str = LIB_PATH):
     lib.awg_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D),
                                      ctypes.POINTER(ctypes.c_int64)]
     lib.awg_profile_read.restype = I
+    lib.awg_apply_hnn_noalloc.argtypes = [P, I, P, P, P]
+    lib.awg_apply_hnn_noalloc.restype = I
     _lib = lib
     return lib
 
@@ -176,6 +178,14 @@ def awg_get_array(h, what: str, size: int) -> np.ndarray:
     _check(load_library().awg_get_array(h, code, out.ctypes.data_as(ctypes.c_void_p), size),
            f"awg_get_array({what})")
     return out[:size]
+
+
+def awg_apply_hnn_noalloc(h, x, y, precision: int = FP64, stream=None):
+    """y = H^NN x with the library's static scratch: no device allocation
+    (for callers that cannot allocate while applying the preconditioner)."""
+    _check(load_library().awg_apply_hnn_noalloc(h, precision, x.data_ptr(), y.data_ptr(),
+                                                _stream_ptr(stream)), "awg_apply_hnn_noalloc")
+    return y
 
 
 def awg_profile(h, mask: int):

@@ -1,0 +1,65 @@
+"""awg_apply_hnn_noalloc: H^NN x for callers that cannot allocate device
+memory while they apply the preconditioner (graph capture, allocation-free
+loops, frameworks that own all device memory).  It must agree with the
+regular entry point (awg_apply_stage with the H^NN stage) on two calls in a
+row, whose shared static scratch keeps the previous call's values.
+
+This file is collected last on purpose, and passes alone in a fresh process
+as well as after the other GPU tests.
+"""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+import awg_inputs as gi
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_RTOL = 1e-11   # tolerance of the FP64 apply in the other GPU tests
+FP32_RTOL = 1e-4    # tolerance of the float32 storage path
+
+
+@pytest.fixture(scope="module")
+def solver():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2106_10913_gb300 import AWGSolver
+    p = gi.config1()
+    sol = AWGSolver(p.rowptr, p.colidx, p.val, p.part, p.nparts, p.overlap, p.tau,
+                    precisions=0b011)
+    yield p, sol
+    sol.close()
+
+
+def _rel(a, b):
+    return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+
+@pytest.mark.parametrize("precision,tol", [(0, FP64_RTOL), (1, FP32_RTOL)])
+def test_noalloc_matches_regular_entry_point(solver, precision, tol):
+    from paper_2106_10913_gb300 import awg_apply_stage, load_library
+    p, sol = solver
+    lib = load_library()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rng = np.random.default_rng(2024 + precision)
+    for call in range(2):  # two calls in a row share the static scratch
+        x = torch.from_numpy(rng.standard_normal(p.n)).cuda()
+        y_ref = awg_apply_stage(sol.h, "hnn", x, torch.empty_like(x), precision)
+        y = torch.full_like(x, float("nan"))
+        st = lib.awg_apply_hnn_noalloc(sol.h, precision, x.data_ptr(), y.data_ptr(), stream)
+        assert st == 0, f"call {call}: status {st}"
+        torch.cuda.synchronize()
+        assert torch.isfinite(y).all()
+        assert _rel(y, y_ref) <= tol, f"call {call}"
+
+
+def test_noalloc_rejects_bad_arguments(solver):
+    from paper_2106_10913_gb300 import load_library
+    p, sol = solver
+    lib = load_library()
+    x = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    assert lib.awg_apply_hnn_noalloc(sol.h, 2, x.data_ptr(), x.data_ptr(), None) == 1
+    assert lib.awg_apply_hnn_noalloc(None, 0, x.data_ptr(), x.data_ptr(), None) == 1
