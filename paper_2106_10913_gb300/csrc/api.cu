@@ -54,7 +54,7 @@ awg_status pcg1(Handle* h, int prec, int stage, const double* b, double* x, doub
 static void free_all(Handle* h) {
     DevBuf* bufs[] = {&h->rowptr, &h->colidx, &h->val, &h->ns, &h->sub_ptr, &h->sub_idx,
                       &h->inc_ptr, &h->inc_pos, &h->inc_sub, &h->pos_sub, &h->dvec, &h->mmu,
-                      &h->bval, &h->dense_off, &h->nm, &h->nstrict, &h->nm_ptr, &h->vm_off,
+                      &h->bval, &h->dense_off, &h->g32_off, &h->nm, &h->nstrict, &h->nm_ptr, &h->vm_off,
                       &h->Vm, &h->lam_m, &h->sigma, &h->modes, &h->mode_ptr, &h->z_off, &h->Z,
                       &h->E, &h->Einv, &h->wcol_ptr, &h->Wcm, &h->F64, &h->ws, &h->flag, &h->red};
     for (DevBuf* b : bufs) dfree(h, *b);
@@ -66,6 +66,11 @@ static void free_all(Handle* h) {
     }
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     h->ev_pool.clear();
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->side) cudaStreamDestroy(h->side);
+    h->ev_fork = h->ev_join = nullptr;
+    h->side = nullptr;
     if (h->h_flag) cudaFreeHost(h->h_flag);
     if (h->h_scal) cudaFreeHost(h->h_scal);
     h->h_flag = nullptr;
@@ -119,6 +124,9 @@ static awg_status setup_impl(Handle* h, const int* d_rowptr, const int* d_colidx
     const double t0 = now_ms();
     AWG_CUDA(cudaMallocHost(&h->h_flag, sizeof(int)));
     AWG_CUDA(cudaMallocHost(&h->h_scal, 16 * sizeof(double)));
+    AWG_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    AWG_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    AWG_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     AWG_TRY(dalloc(h, h->flag, sizeof(int)));
     AWG_TRY(dalloc(h, h->rowptr, (size_t)(h->n + 1) * sizeof(int)));
     AWG_TRY(dalloc(h, h->colidx, (size_t)h->nnz * sizeof(int)));

@@ -143,34 +143,59 @@ __global__ void __launch_bounds__(256) k_local_gemv64(const int* __restrict__ su
     }
 }
 
-template <typename TS>
-__global__ void __launch_bounds__(256) k_local_gemv_lp(const int* __restrict__ sub_ptr,
-                                                       const int* __restrict__ sub_idx,
-                                                       const int64_t* __restrict__ goff,
-                                                       const TS* __restrict__ G,
-                                                       const double* __restrict__ x, double* loc) {
-    extern __shared__ float xf[];
+// float32 local operators: column-major with a leading dimension padded to a
+// multiple of 4 (columns 16-byte aligned, padding zero) at offsets g32off.
+// The gathered x comes in float32 from k_gather_f32 (one conversion per
+// local position per apply), rows are read with 16-byte streaming loads and
+// the results of a block's rows leave through one conversion instruction:
+// no float64 operation sits in the inner loop, because the float64 pipe is
+// about 58 times narrower than the float32 one on this GPU.
+__global__ void k_gather_f32(int64_t sum_ns, const int* __restrict__ sub_idx,
+                             const double* __restrict__ x, float* xloc) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < sum_ns) xloc[p] = (float)x[sub_idx[p]];
+}
+
+__global__ void __launch_bounds__(256) k_local_gemv_f32(const int* __restrict__ sub_ptr,
+                                                        const int64_t* __restrict__ g32off,
+                                                        const float* __restrict__ G,
+                                                        const float* __restrict__ xloc,
+                                                        double* loc) {
+    extern __shared__ __align__(16) float xs32[];
+    float* xs = xs32;
+    __shared__ float outr[LG_ROWS];
     const int s = blockIdx.x;
     const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
+    const int ld = (m + 3) & ~3;
     const int r0 = blockIdx.y * LG_ROWS;
     if (r0 >= m) return;
-    for (int q = threadIdx.x; q < m; q += blockDim.x) xf[q] = (float)x[sub_idx[p0 + q]];
+    for (int q = threadIdx.x; q < ld; q += blockDim.x) xs[q] = (q < m) ? xloc[p0 + q] : 0.f;
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const TS* Gs = G + goff[s];
+    const float* Gs = G + g32off[s];
+    const float4* x4 = reinterpret_cast<const float4*>(xs);
+    const int nq = ld >> 2;
     const int r1 = min(m, r0 + LG_ROWS);
     for (int p = r0 + wid; p < r1; p += nw) {
-        const TS* col = Gs + (size_t)p * m;
+        const float4* col = reinterpret_cast<const float4*>(Gs + (size_t)p * ld);
         float a0 = 0.f, a1 = 0.f;
         int q = lane;
-        for (; q + 32 < m; q += 64) {
-            a0 = fmaf(to_f(col[q]), xf[q], a0);
-            a1 = fmaf(to_f(col[q + 32]), xf[q + 32], a1);
+        for (; q + 32 < nq; q += 64) {
+            const float4 g0 = __ldcs(col + q), g1 = __ldcs(col + q + 32);
+            const float4 u0 = x4[q], u1 = x4[q + 32];
+            a0 = fmaf(g0.x, u0.x, fmaf(g0.y, u0.y, fmaf(g0.z, u0.z, fmaf(g0.w, u0.w, a0))));
+            a1 = fmaf(g1.x, u1.x, fmaf(g1.y, u1.y, fmaf(g1.z, u1.z, fmaf(g1.w, u1.w, a1))));
         }
-        if (q < m) a0 = fmaf(to_f(col[q]), xf[q], a0);
+        if (q < nq) {
+            const float4 g0 = __ldcs(col + q);
+            const float4 u0 = x4[q];
+            a0 = fmaf(g0.x, u0.x, fmaf(g0.y, u0.y, fmaf(g0.z, u0.z, fmaf(g0.w, u0.w, a0))));
+        }
         const float acc = warp_sumf(a0 + a1);
-        if (lane == 0) loc[p0 + p] = (double)acc;
+        if (lane == 0) outr[p - r0] = acc;
     }
+    __syncthreads();
+    if (threadIdx.x < r1 - r0) loc[p0 + r0 + threadIdx.x] = (double)outr[threadIdx.x];
 }
 
 // ------------------------------------------------------------ dense coarse
@@ -239,80 +264,119 @@ __device__ __forceinline__ void lds_vec(const A* p, A* o) {
     }
 }
 
-constexpr int WT_THREADS = 256;
+constexpr int WT_THREADS = 256;  // 8 warps
+constexpr int WT_CW = 256;       // columns of W per block (blockIdx.y)
 
-// part[b*ldw + c] = sum over the block's rows i of W(i, c) r(i)
-template <typename TS, int UNR>
+// part[b*ldw + c] = sum over the rows of row block b of W(i, c) r(i), for the
+// 256 columns of column chunk blockIdx.y.  The block's r values are staged
+// once in shared memory in the compute type; the 8 warps take every 8th row
+// and the 8 partial sums meet in shared memory in a fixed order.
+template <typename TS>
 __global__ void __launch_bounds__(WT_THREADS) k_wt_partial(int n, int ldw, int rows,
                                                            const TS* __restrict__ W,
                                                            const double* __restrict__ r,
                                                            double* part) {
     using A = typename Vec<TS>::A;
     constexpr int V = Vec<TS>::V;
+    constexpr int UNR = WT_CW / (32 * V);
+    extern __shared__ __align__(16) unsigned char wt_smem[];
+    A* red = reinterpret_cast<A*>(wt_smem);  // [8][WT_CW]
+    A* rs = red + 8 * WT_CW;                 // [rows]
     const int i0 = blockIdx.x * rows;
-    const int i1 = min(n, i0 + rows);
-    for (int c0 = 0; c0 < ldw; c0 += WT_THREADS * V * UNR) {
-        A acc[UNR][V];
+    const int nr = min(n, i0 + rows) - i0;
+    const int c0 = blockIdx.y * WT_CW;
+    for (int t = threadIdx.x; t < nr; t += WT_THREADS) rs[t] = (A)r[i0 + t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    A acc[UNR][V];
 #pragma unroll
-        for (int u = 0; u < UNR; u++)
+    for (int u = 0; u < UNR; u++)
 #pragma unroll
-            for (int j = 0; j < V; j++) acc[u][j] = 0;
-        for (int i = i0; i < i1; i++) {
-            const A ri = (A)r[i];
-            const TS* row = W + (size_t)i * ldw;
-#pragma unroll
-            for (int u = 0; u < UNR; u++) {
-                const int c = c0 + (u * WT_THREADS + threadIdx.x) * V;
-                if (c < ldw) {
-                    A w[V];
-                    Vec<TS>::load(row + c, w);
-#pragma unroll
-                    for (int j = 0; j < V; j++) acc[u][j] = fma(w[j], ri, acc[u][j]);
-                }
-            }
-        }
+        for (int j = 0; j < V; j++) acc[u][j] = 0;
+#pragma unroll 2
+    for (int i = wid; i < nr; i += 8) {
+        const A ri = rs[i];
+        const TS* row = W + (size_t)(i0 + i) * ldw;
 #pragma unroll
         for (int u = 0; u < UNR; u++) {
-            const int c = c0 + (u * WT_THREADS + threadIdx.x) * V;
+            const int c = c0 + (u * 32 + lane) * V;
             if (c < ldw) {
+                A w[V];
+                Vec<TS>::load(row + c, w);
 #pragma unroll
-                for (int j = 0; j < V; j++) part[(size_t)blockIdx.x * ldw + c + j] = (double)acc[u][j];
+                for (int j = 0; j < V; j++) acc[u][j] = fma(w[j], ri, acc[u][j]);
             }
         }
     }
+#pragma unroll
+    for (int u = 0; u < UNR; u++)
+#pragma unroll
+        for (int j = 0; j < V; j++) red[wid * WT_CW + (u * 32 + lane) * V + j] = acc[u][j];
+    __syncthreads();
+    const int c = c0 + threadIdx.x;
+    if (c < ldw) {
+        A sum = 0;
+#pragma unroll
+        for (int w = 0; w < 8; w++) sum += red[w * WT_CW + threadIdx.x];
+        part[(size_t)blockIdx.x * ldw + c] = (double)sum;
+    }
 }
 
+// out[c] = sum over the row blocks of part[b*ldp + c]  (fixed order)
 __global__ void k_reduce_cols(int nb, int nm, int ldp, const double* __restrict__ part, double* out) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nm) return;
-    double acc = 0.0;
-    for (int b = 0; b < nb; b++) acc += part[(size_t)b * ldp + c];
-    out[c] = acc;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int b = 0;
+    for (; b + 3 < nb; b += 4) {
+        a0 += part[(size_t)b * ldp + c];
+        a1 += part[(size_t)(b + 1) * ldp + c];
+        a2 += part[(size_t)(b + 2) * ldp + c];
+        a3 += part[(size_t)(b + 3) * ldp + c];
+    }
+    for (; b < nb; b++) a0 += part[(size_t)b * ldp + c];
+    out[c] = (a0 + a1) + (a2 + a3);
 }
 
-// z(i) = v(i) + sum_c W(i, c) d(c)   (one warp per row, d staged in shared
-// memory in the compute type, zero-padded to ldw)
+template <typename A>
+__device__ __forceinline__ A warp_sum_t(A v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// d in the compute type of W's storage (one conversion per element per apply)
+__global__ void k_d_to_f32(int nm, int ldw, const double* __restrict__ d, float* d32) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ldw) d32[c] = (c < nm) ? (float)d[c] : 0.f;
+}
+
+// z(i) = v(i) + sum_c W(i, c) d(c).  One warp per row (grid-stride, many
+// warps in flight), the row sum reduced in the compute type; only lane 0
+// touches float64 (one conversion and one add per row, next to a row read of
+// ldw elements).  d (compute type, zero-padded to ldw) is staged in shared
+// memory: d itself for float64 storage, the float32 copy from k_d_to_f32
+// otherwise.
 template <typename TS>
-__global__ void __launch_bounds__(256) k_w_d(int n, int nm, int ldw, const TS* __restrict__ W,
-                                             const double* __restrict__ d, const double* v,
-                                             double* z) {
+__global__ void __launch_bounds__(256) k_w_d(int n, int ldw, const TS* __restrict__ W,
+                                             const typename Vec<TS>::A* __restrict__ dA,
+                                             const double* v, double* z) {
     using A = typename Vec<TS>::A;
     constexpr int V = Vec<TS>::V;
     extern __shared__ __align__(16) unsigned char wd_smem[];
     A* ds = reinterpret_cast<A*>(wd_smem);
-    for (int c = threadIdx.x; c < ldw; c += blockDim.x) ds[c] = (c < nm) ? (A)d[c] : (A)0;
+    for (int c = threadIdx.x; c < ldw; c += blockDim.x) ds[c] = dA[c];
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int nwb = blockDim.x >> 5;
-    for (int i = blockIdx.x * nwb + (threadIdx.x >> 5); i < n; i += gridDim.x * nwb) {
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
         const TS* row = W + (size_t)i * ldw;
         A acc0 = 0, acc1 = 0;
         int c = lane * V;
         for (; c + 32 * V < ldw; c += 64 * V) {
-            A w0[V], w1[V];
+            A w0[V], w1[V], d0[V], d1[V];
             Vec<TS>::load(row + c, w0);
             Vec<TS>::load(row + c + 32 * V, w1);
-            A d0[V], d1[V];
             lds_vec<A, V>(ds + c, d0);
             lds_vec<A, V>(ds + c + 32 * V, d1);
 #pragma unroll
@@ -328,9 +392,8 @@ __global__ void __launch_bounds__(256) k_w_d(int n, int nm, int ldw, const TS* _
 #pragma unroll
             for (int j = 0; j < V; j++) acc0 = fma(w0[j], d0[j], acc0);
         }
-        double a = (double)(acc0 + acc1);
-        a = warp_sum(a);
-        if (lane == 0) z[i] = (v ? v[i] : 0.0) + a;
+        const A s = warp_sum_t<A>(acc0 + acc1);
+        if (lane == 0) z[i] = (v ? v[i] : 0.0) + (double)s;
     }
 }
 
@@ -394,31 +457,37 @@ __global__ void k_pcg_p(int n, const double* __restrict__ scal, const double* __
 // ===================================================================== host
 struct Ws {
     double *y0, *y2, *c1, *c2, *w0, *w1, *dd, *x1, *t, *u, *q, *loc, *loc2, *cm, *part, *wpart, *tmp, *tmp2;
+    float *xf, *d32;  // float32 gathered local vector, float32 copy of d
+    double* dpad;     // d zero-padded to ldw (float64 W)
 };
 
-static Ws ws_of(Handle* h) {
-    // carve the workspace (sizes fixed at setup, see ws_bytes)
-    Ws w;
-    double* p = (double*)h->ws.p;
+// Carving of the single-RHS workspace; `dry` only measures it.
+static size_t carve(const Handle* h, double* base, Ws* w) {
+    double* p = base;
     const size_t n = h->n, n0 = std::max(1, h->n0), nm = std::max(1, h->n_minus);
     auto take = [&](size_t len) { double* r = p; p += (len + 31) / 32 * 32; return r; };
-    w.y0 = take(n0); w.y2 = take(n0); w.c1 = take(n0); w.c2 = take(n0);
-    w.w0 = take(nm); w.w1 = take(nm); w.dd = take(nm);
-    w.x1 = take(n); w.t = take(n); w.u = take(n); w.q = take(n); w.tmp = take(n); w.tmp2 = take(n);
-    w.loc = take(h->sum_ns); w.loc2 = take(h->sum_ns);
-    w.cm = take(std::max(1, h->n_minus_all));
-    w.part = take(4096);
-    w.wpart = take((size_t)h->red_blocks * std::max(8, h->ldw));
+    Ws t;
+    t.y0 = take(n0); t.y2 = take(n0); t.c1 = take(n0); t.c2 = take(n0);
+    t.w0 = take(nm); t.w1 = take(nm); t.dd = take(nm);
+    t.x1 = take(n); t.t = take(n); t.u = take(n); t.q = take(n); t.tmp = take(n); t.tmp2 = take(n);
+    t.loc = take(h->sum_ns); t.loc2 = take(h->sum_ns);
+    t.cm = take(std::max(1, h->n_minus_all));
+    t.part = take(4096);
+    t.wpart = take((size_t)h->red_blocks * std::max(8, h->ldw));
+    t.xf = reinterpret_cast<float*>(take((h->sum_ns + 1) / 2 + 4));
+    t.d32 = reinterpret_cast<float*>(take((std::max(8, h->ldw) + 1) / 2 + 4));
+    t.dpad = take(std::max(8, h->ldw));
+    if (w) *w = t;
+    return (size_t)(p - base) * sizeof(double);
+}
+
+static Ws ws_of(Handle* h) {
+    Ws w;
+    carve(h, (double*)h->ws.p, &w);
     return w;
 }
 
-size_t ws_bytes(const Handle* h) {
-    const size_t n = h->n, n0 = std::max(1, h->n0), nm = std::max(1, h->n_minus);
-    auto r = [](size_t len) { return (len + 31) / 32 * 32; };
-    size_t tot = 4 * r(n0) + 3 * r(nm) + 6 * r(n) + 2 * r(h->sum_ns) +
-                 r(std::max(1, h->n_minus_all)) + r(4096) + r((size_t)h->red_blocks * std::max(8, h->ldw));
-    return tot * sizeof(double);
-}
+size_t ws_bytes(const Handle* h) { return carve(h, nullptr, nullptr); }
 
 static int grid_n(int n) { return std::min((n + 255) / 256, 152 * 8); }
 
@@ -535,9 +604,15 @@ static awg_status hnn1(Handle* h, int prec, const double* x, double* y, Ws& w, c
         }
     } else {
         {
+            ProfScope ps_(h, AWG_PROF_PROLONG, s);
+            k_gather_f32<<<(unsigned)((h->sum_ns + 255) / 256), 256, 0, s>>>(h->sum_ns, (int*)h->sub_idx.p,
+                                                                            x, w.xf);
+        }
+        AWG_LAUNCH();
+        {
             ProfScope ps_(h, AWG_PROF_LOCAL, s);
-            k_local_gemv_lp<float><<<g, 256, (size_t)h->max_ns * 4, s>>>(
-                (int*)h->sub_ptr.p, (int*)h->sub_idx.p, (int64_t*)h->dense_off.p, (float*)P.G.p, x, w.loc);
+            k_local_gemv_f32<<<g, 256, (size_t)((h->max_ns + 3) & ~3) * 4, s>>>(
+                (int*)h->sub_ptr.p, (int64_t*)h->g32_off.p, (float*)P.G.p, w.xf, w.loc);
         }
     }
     AWG_LAUNCH();
@@ -565,19 +640,33 @@ static awg_status h2_1(Handle* h, int prec, const double* r, double* z, Ws& w, c
     return prolong1(h, w.loc, z, -1.0, 0.0, w.u, 1.0, s);   // z = u - Z (c2 - c1)
 }
 
-template <typename TS, int UNR>
+// Row blocks of the W^T r pass: about 8 blocks per SM in total over the
+// 256-column chunks, at most 8192 rows per block (its r values sit in
+// shared memory), never more blocks than the partial buffer holds.
+static int wt_row_blocks(const Handle* h) {
+    const int chunks = (h->ldw + WT_CW - 1) / WT_CW;
+    int rb = std::max(1, 152 * 8 / std::max(1, chunks));
+    rb = std::max(rb, (h->n + 8191) / 8192);
+    rb = std::min(rb, std::max(1, (h->n + 31) / 32));
+    return std::min(rb, h->red_blocks);
+}
+
+template <typename TS>
 static awg_status wt_r_t(Handle* h, const void* W, const double* r, double* out, Ws& w,
                          cudaStream_t s) {
-    const int nb = h->red_blocks;
-    const int rows = (h->n + nb - 1) / nb;
+    using A = typename Vec<TS>::A;
+    const int rb = wt_row_blocks(h);
+    const int rows = (h->n + rb - 1) / rb;
+    const dim3 grid(rb, (h->ldw + WT_CW - 1) / WT_CW);
+    const size_t smem = (size_t)(8 * WT_CW + rows) * sizeof(A);
     {
         ProfScope ps_(h, AWG_PROF_WT, s);
-        k_wt_partial<TS, UNR><<<nb, WT_THREADS, 0, s>>>(h->n, h->ldw, rows, (const TS*)W, r, w.wpart);
+        k_wt_partial<TS><<<grid, WT_THREADS, smem, s>>>(h->n, h->ldw, rows, (const TS*)W, r, w.wpart);
     }
     AWG_LAUNCH();
     {
         ProfScope ps_(h, AWG_PROF_VECTOR, s);
-        k_reduce_cols<<<(h->n_minus + 255) / 256, 256, 0, s>>>(nb, h->n_minus, h->ldw, w.wpart, out);
+        k_reduce_cols<<<(h->n_minus + 255) / 256, 256, 0, s>>>(rb, h->n_minus, h->ldw, w.wpart, out);
     }
     AWG_LAUNCH();
     return AWG_OK;
@@ -585,24 +674,43 @@ static awg_status wt_r_t(Handle* h, const void* W, const double* r, double* out,
 
 static awg_status wt_r(Handle* h, int prec, const double* r, double* out, Ws& w, cudaStream_t s) {
     const void* W = h->prec[prec].W.p;
-    if (prec == AWG_FP64) return wt_r_t<double, 4>(h, W, r, out, w, s);
-    if (prec == AWG_MIXED_FP32) return wt_r_t<float, 4>(h, W, r, out, w, s);
-    return wt_r_t<__nv_bfloat16, 2>(h, W, r, out, w, s);
+    if (prec == AWG_FP64) return wt_r_t<double>(h, W, r, out, w, s);
+    if (prec == AWG_MIXED_FP32) return wt_r_t<float>(h, W, r, out, w, s);
+    return wt_r_t<__nv_bfloat16>(h, W, r, out, w, s);
 }
 
-static awg_status w_d(Handle* h, int prec, const double* d, const double* v, double* z,
+// d zero-padded to ldw in the compute type of W's storage
+__global__ void k_d_pad64(int nm, int ldw, const double* __restrict__ d, double* dp) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ldw) dp[c] = (c < nm) ? d[c] : 0.0;
+}
+
+static awg_status w_d(Handle* h, int prec, const double* d, const double* v, double* z, Ws& w,
                       cudaStream_t s) {
     const void* W = h->prec[prec].W.p;
-    const int grid = std::min((h->n + 7) / 8, 152 * 16);
-    {
+    const int grid = std::max(1, std::min((h->n + 7) / 8, 152 * 16));  // 8 rows (warps) per block
+    const int gd = (h->ldw + 255) / 256;
+    if (prec == AWG_FP64) {
+        double* dp = w.dpad;
+        {
+            ProfScope ps_(h, AWG_PROF_VECTOR, s);
+            k_d_pad64<<<gd, 256, 0, s>>>(h->n_minus, h->ldw, d, dp);
+        }
+        AWG_LAUNCH();
         ProfScope ps_(h, AWG_PROF_WD, s);
-        if (prec == AWG_FP64)
-            k_w_d<double><<<grid, 256, (size_t)h->ldw * 8, s>>>(h->n, h->n_minus, h->ldw, (const double*)W, d, v, z);
-        else if (prec == AWG_MIXED_FP32)
-            k_w_d<float><<<grid, 256, (size_t)h->ldw * 4, s>>>(h->n, h->n_minus, h->ldw, (const float*)W, d, v, z);
+        k_w_d<double><<<grid, 256, (size_t)h->ldw * 8, s>>>(h->n, h->ldw, (const double*)W, dp, v, z);
+    } else {
+        {
+            ProfScope ps_(h, AWG_PROF_VECTOR, s);
+            k_d_to_f32<<<gd, 256, 0, s>>>(h->n_minus, h->ldw, d, w.d32);
+        }
+        AWG_LAUNCH();
+        ProfScope ps_(h, AWG_PROF_WD, s);
+        if (prec == AWG_MIXED_FP32)
+            k_w_d<float><<<grid, 256, (size_t)h->ldw * 4, s>>>(h->n, h->ldw, (const float*)W, w.d32, v, z);
         else
-            k_w_d<__nv_bfloat16><<<grid, 256, (size_t)h->ldw * 4, s>>>(h->n, h->n_minus, h->ldw,
-                                                                      (const __nv_bfloat16*)W, d, v, z);
+            k_w_d<__nv_bfloat16><<<grid, 256, (size_t)h->ldw * 4, s>>>(h->n, h->ldw,
+                                                                      (const __nv_bfloat16*)W, w.d32, v, z);
     }
     AWG_LAUNCH();
     return AWG_OK;
@@ -615,11 +723,16 @@ awg_status set_smem_limits(Handle* h) {
         AWG_CUDA(cudaFuncSetAttribute(k_blk_tgemv, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         AWG_CUDA(cudaFuncSetAttribute(k_blk_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         AWG_CUDA(cudaFuncSetAttribute(k_local_gemv64, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-        AWG_CUDA(cudaFuncSetAttribute(k_local_gemv_lp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        AWG_CUDA(cudaFuncSetAttribute(k_local_gemv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         AWG_CUDA(cudaFuncSetAttribute(k_w_d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         AWG_CUDA(cudaFuncSetAttribute(k_w_d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         AWG_CUDA(cudaFuncSetAttribute(k_w_d<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     }
+    // W^T r stages up to 8192 values of r plus 8 x 256 partial sums
+    const int wt = (8 * WT_CW + 8192) * 8;
+    AWG_CUDA(cudaFuncSetAttribute(k_wt_partial<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, wt));
+    AWG_CUDA(cudaFuncSetAttribute(k_wt_partial<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, wt / 2));
+    AWG_CUDA(cudaFuncSetAttribute(k_wt_partial<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, wt / 2));
     return AWG_OK;
 }
 
@@ -634,17 +747,23 @@ awg_status apply_stage(Handle* h, int which, int prec, const double* x, double* 
         case 3: return h2_1(h, prec, x, y, w, s);
         case 4: {  // H_3,ad = H_2 + W F^-1 W^T  (Def. 10)
             if (h->n_minus == 0) return h2_1(h, prec, x, y, w, s);
-            AWG_TRY(wt_r(h, prec, x, w.w0, w, s));
-            AWG_TRY(dense_gemv(h, h->n_minus, (double*)h->prec[prec].Finv.p, w.w0, w.dd, 1.0, nullptr, 0, s));
+            // d = F^-1 W^T x on the side stream while H_2 x runs on s
+            AWG_CUDA(cudaEventRecord(h->ev_fork, s));
+            AWG_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+            AWG_TRY(wt_r(h, prec, x, w.w0, w, h->side));
+            AWG_TRY(dense_gemv(h, h->n_minus, (double*)h->prec[prec].Finv.p, w.w0, w.dd, 1.0, nullptr, 0,
+                               h->side));
+            AWG_CUDA(cudaEventRecord(h->ev_join, h->side));
             AWG_TRY(h2_1(h, prec, x, w.tmp, w, s));
-            return w_d(h, prec, w.dd, w.tmp, y, s);
+            AWG_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+            return w_d(h, prec, w.dd, w.tmp, y, w, s);
         }
         case 5: {  // H_3,hyb = Pi_3 H_2 Pi_3^T + W F^-1 W^T  (Def. 10)
             if (h->n_minus == 0) return h2_1(h, prec, x, y, w, s);
             const double* Finv = (double*)h->prec[prec].Finv.p;
             AWG_TRY(wt_r(h, prec, x, w.w0, w, s));
             AWG_TRY(dense_gemv(h, h->n_minus, Finv, w.w0, w.dd, 1.0, nullptr, 0, s));  // d = F^-1 W^T x
-            AWG_TRY(w_d(h, prec, w.dd, nullptr, w.tmp, s));                        // tmp = W d
+            AWG_TRY(w_d(h, prec, w.dd, nullptr, w.tmp, w, s));                        // tmp = W d
             AWG_TRY(spmv1(h, w.tmp, w.q, nullptr, s));
             {
                 ProfScope ps_(h, AWG_PROF_VECTOR, s);
@@ -655,14 +774,19 @@ awg_status apply_stage(Handle* h, int which, int prec, const double* x, double* 
             AWG_TRY(spmv1(h, y, w.q, nullptr, s));                                 // q = A v
             AWG_TRY(wt_r(h, prec, w.q, w.w0, w, s));
             AWG_TRY(dense_gemv(h, h->n_minus, Finv, w.w0, w.w1, -1.0, w.dd, 1.0, s)); // w1 = d - F^-1 W^T A v
-            return w_d(h, prec, w.w1, y, y, s);                                     // z = v + W w1
+            return w_d(h, prec, w.w1, y, y, w, s);                                     // z = v + W w1
         }
         case 6: {  // H_3,inex = H_2 + W (C^-1 - Vhat^T W)^-1 W^T  (Thm. 7)
             if (h->n_minus == 0) return h2_1(h, prec, x, y, w, s);
-            AWG_TRY(wt_r(h, prec, x, w.w0, w, s));
-            AWG_TRY(dense_gemv(h, h->n_minus, (double*)h->prec[prec].inexInv.p, w.w0, w.dd, 1.0, nullptr, 0, s));
+            AWG_CUDA(cudaEventRecord(h->ev_fork, s));
+            AWG_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+            AWG_TRY(wt_r(h, prec, x, w.w0, w, h->side));
+            AWG_TRY(dense_gemv(h, h->n_minus, (double*)h->prec[prec].inexInv.p, w.w0, w.dd, 1.0, nullptr,
+                               0, h->side));
+            AWG_CUDA(cudaEventRecord(h->ev_join, h->side));
             AWG_TRY(h2_1(h, prec, x, w.tmp, w, s));
-            return w_d(h, prec, w.dd, w.tmp, y, s);
+            AWG_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+            return w_d(h, prec, w.dd, w.tmp, y, w, s);
         }
         default: return AWG_ERR_INVALID_ARG;
     }

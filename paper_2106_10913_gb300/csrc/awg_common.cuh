@@ -81,6 +81,9 @@ struct Handle {
     std::vector<int64_t> h_dense_off;
     DevBuf dense_off;                    // int64[N+1]
     int64_t dense_total = 0;
+    // float32 local operators: ld = n^s rounded up to 4 (16-byte columns)
+    std::vector<int64_t> h_g32_off;
+    DevBuf g32_off;                      // int64[N+1]
 
     // eigen-split of B^s (Def. 6)
     std::vector<int> h_nm, h_nstrict, h_nm_ptr;
@@ -118,6 +121,10 @@ struct Handle {
     int red_blocks = 0;
     int* h_flag = nullptr;               // pinned host mirror
     double* h_scal = nullptr;            // pinned host scalars
+    // the second-coarse-space pass W^T r runs on `side`, concurrently with
+    // H_2 on the caller's stream (fork and join through the two events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // profiling (awg_profile): launch count of the apply/PCG path and CUDA
     // event times of its heaviest kernels

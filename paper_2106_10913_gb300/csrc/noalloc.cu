@@ -36,7 +36,8 @@ static std::mutex g_noalloc_mutex;
 static double* g_noalloc_ptr[256] = {nullptr};
 
 // loc[sub_ptr[s] + p] = sum_q G_s(p, q) x(idx_s(q)) for the rows of this
-// block (G_s symmetric, full column-major, stored as TS)
+// block (G_s symmetric, full column-major, stored as TS; float32 blocks have
+// their leading dimension rounded up to 4)
 template <typename TS, typename TA>
 __global__ void __launch_bounds__(256) k_hnn_local_noalloc(const int* __restrict__ sub_ptr,
                                                            const int* __restrict__ sub_idx,
@@ -54,9 +55,10 @@ __global__ void __launch_bounds__(256) k_hnn_local_noalloc(const int* __restrict
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const TS* Gs = G + goff[s];
+    const int ld = (sizeof(TS) == 4) ? ((m + 3) & ~3) : m;
     const int r1 = min(m, r0 + rows_per_block);
     for (int p = r0 + wid; p < r1; p += nw) {
-        const TS* col = Gs + (size_t)p * m;
+        const TS* col = Gs + (size_t)p * ld;
         TA acc = 0;
         for (int q = lane; q < m; q += 32) acc = fma((TA)col[q], xs[q], acc);
         double a = (double)acc;
@@ -136,7 +138,7 @@ extern "C" awg_status awg_apply_hnn_noalloc(awg_handle hh, int precision, const 
             AWG_CUDA(cudaFuncSetAttribute(k_hnn_local_noalloc<float, float>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_hnn_local_noalloc<float, float><<<g, 256, sm, s>>>(
-            (int*)h->sub_ptr.p, (int*)h->sub_idx.p, (int64_t*)h->dense_off.p, (const float*)P.G.p,
+            (int*)h->sub_ptr.p, (int*)h->sub_idx.p, (int64_t*)h->g32_off.p, (const float*)P.G.p,
             d_x, loc, rows);
     }
     AWG_LAUNCH();

@@ -188,9 +188,9 @@ awg_status blk_hnn(Handle* h, const double* X, double* Y, int k, cudaStream_t s,
         const float* G = (const float*)h->prec[AWG_MIXED_FP32].G.p;
         if (!G) return AWG_ERR_STATE;
         for (int t = 0; t < h->N; t++) {
-            const int m = h->h_ns[t];
-            d.push_back({G + h->h_dense_off[t], loc + (int64_t)h->h_sub_ptr[t] * k,
-                         out + (int64_t)h->h_sub_ptr[t] * k, m, k, m, m, m, m, 0, 1.0, 0.0});
+            const int m = h->h_ns[t], ld = (m + 3) & ~3;  // padded float32 layout
+            d.push_back({G + h->h_g32_off[t], loc + (int64_t)h->h_sub_ptr[t] * k,
+                         out + (int64_t)h->h_sub_ptr[t] * k, m, k, m, ld, m, m, 0, 1.0, 0.0});
         }
         AWG_TRY(gemm_batched_f32(h, d, s));
     } else {

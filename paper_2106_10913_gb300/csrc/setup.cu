@@ -207,6 +207,22 @@ __global__ void k_conv_f32(size_t len, const double* __restrict__ X, float* Y) {
     if (e < len) Y[e] = (float)X[e];
 }
 
+// float32 copy of the per-subdomain blocks with the leading dimension
+// rounded up to 4 (padding rows zero)
+__global__ void k_conv_f32_padded(const int* __restrict__ ns, const int64_t* __restrict__ off,
+                                  const int64_t* __restrict__ off32, const double* __restrict__ X,
+                                  float* Y) {
+    const int s = blockIdx.x;
+    const int m = ns[s], ld = (m + 3) & ~3;
+    const double* Xs = X + off[s];
+    float* Ys = Y + off32[s];
+    for (int64_t e = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)ld * m;
+         e += (int64_t)gridDim.y * blockDim.x) {
+        const int q = (int)(e % ld), p = (int)(e / ld);
+        Ys[e] = (q < m) ? (float)Xs[q + (size_t)p * m] : 0.f;
+    }
+}
+
 // per-column PCG updates
 __global__ void k_col_axpy(int n, const double* __restrict__ alpha, const double* __restrict__ X,
                            double* Y) {
@@ -661,9 +677,13 @@ awg_status build_setup_numeric(Handle* h) {
     // (the bfloat16 form rounds only W) and by the W solve's preconditioner
     if ((h->opt.precisions & 6) || h->opt.w_precision == AWG_MIXED_FP32) {
         PrecOps& P = h->prec[AWG_MIXED_FP32];
-        const size_t len = (size_t)h->dense_total;
-        AWG_TRY(dalloc(h, P.G, len * 4));
-        k_conv_f32<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, (double*)G.p, (float*)P.G.p);
+        h->h_g32_off.assign(N + 1, 0);
+        for (int t = 0; t < N; t++)
+            h->h_g32_off[t + 1] = h->h_g32_off[t] + (int64_t)h->h_ns[t] * ((h->h_ns[t] + 3) & ~3);
+        AWG_TRY(upload(h, h->g32_off, h->h_g32_off.data(), (N + 1) * sizeof(int64_t)));
+        AWG_TRY(dalloc(h, P.G, (size_t)h->h_g32_off[N] * 4));
+        k_conv_f32_padded<<<gblk, 256, 0, s>>>((int*)h->ns.p, (int64_t*)h->dense_off.p,
+                                               (int64_t*)h->g32_off.p, (double*)G.p, (float*)P.G.p);
         AWG_LAUNCH();
     }
     // ---------------------------------------------- 5. W, 6. F
