@@ -92,6 +92,23 @@ typedef struct {
                                AWG_MIXED_FP32 (default; the outer PCG, its
                                residuals and A_+ products stay float64, so W
                                still converges to w_rtol) or AWG_FP64          */
+    int geneo_solver;       /* eigensolver of the GenEO pencils (Def. 9):
+                               0 (default) dense: Cholesky of M_B, Householder
+                               tridiagonalisation, bisection, inverse iteration;
+                               1 block inverse iteration with Rayleigh-Ritz from
+                               a pseudo-random start block, each subdomain
+                               accepted only under an inertia certificate
+                               (Sylvester's law) that no eigenvalue below tau
+                               was missed; pencils it cannot certify within
+                               geneo_maxit steps go to the dense solver;
+                               2 as 1, start block from the learned network
+                               (learned_params)                                 */
+    int geneo_block;        /* block width b of solvers 1-2, 2..16; default 8.
+                               A subdomain with b or more extra modes (beyond
+                               the kernel D^s V^s_-) goes to the dense solver  */
+    int geneo_maxit;        /* step cap of solvers 1-2; default 60             */
+    const double* learned_params; /* host float64[AWG_LEARNED_NPARAM], read
+                               during awg_setup only (solver 2)                */
 } awg_options;
 
 /* Per-handle figures reported after setup (cf. Table 1 of the paper). */
@@ -108,6 +125,10 @@ typedef struct {
     double setup_ms[8];     /* stage times: subdomains, split, local factors,
                                GenEO, E, W, F, total                            */
     size_t device_bytes;    /* device memory held by the handle                 */
+    int geneo_its_max;      /* block solver: most steps taken by a subdomain    */
+    int64_t geneo_its_sum;  /* block solver: steps summed over subdomains       */
+    int geneo_dense;        /* subdomains whose pencil went through the dense
+                               eigensolver (all of them with geneo_solver 0)    */
 } awg_info;
 
 /* Fill *opt with the defaults above. */
@@ -254,6 +275,57 @@ awg_status awg_profile_read(awg_handle h, int64_t* h_launches, double* h_ms, int
  */
 awg_status awg_apply_hnn_noalloc(awg_handle h, int precision, const double* d_x, double* d_y,
                                  void* stream);
+
+/* ------------------------------------------------------------------------
+ * Learned start block of the GenEO block solver.  The paper has no
+ * counterpart: it names iterative eigensolvers for the GenEO pencils
+ * (remark after Def. 9) without fixing their start.  A 5-16-16-1 network
+ * (tanh, tanh, sigmoid) maps per-node features of a subdomain, computed
+ * from A, to the predicted normalised leverage of the subdomain's extra
+ * modes (GenEO eigenvectors with eigenvalue in (0, tau)).  Parameters are
+ * float64[AWG_LEARNED_NPARAM]: W1[16x5] row-major, b1[16], W2[16x16]
+ * row-major, b2[16], w3[16], b3.  Features are float64[P x 5], row-major:
+ *   f0 = (log10 A_pp - mean over the subdomain of log10 A_qq) / 6
+ *   f1 = (multiplicity of p - 1) / 3
+ *   f2 = mean of f0 over the neighbours of p inside the subdomain (0 if none)
+ *   f3 = largest f0 over those neighbours (f0_p if none)
+ *   f4 = (sum of the stored row of A) / A_pp
+ * The functions below are asynchronous on `stream` except awg_learned_train,
+ * which returns after the last step.
+ */
+#define AWG_LEARNED_NPARAM 385
+#define AWG_LEARNED_NFEAT 5
+
+/* Features (d_features, device float64[sum_ns x 5], row k = k-th entry of
+ * the concatenated subdomain index lists) and training targets (d_targets,
+ * device float64[sum_ns]: per subdomain, the diagonal of the orthogonal
+ * projector onto the span of its extra modes, divided by its maximum; zero
+ * where a subdomain has none; at most 16 extra modes enter) of a built
+ * handle.  Either pointer may be NULL.  Errors: AWG_ERR_INVALID_ARG,
+ * AWG_ERR_CUDA. */
+awg_status awg_learned_data(awg_handle h, double* d_features, double* d_targets, void* stream);
+
+/* d_out[p] = network(d_features row p), p < P, in float64 (precision
+ * AWG_FP64) or float32 (AWG_MIXED_FP32) arithmetic.  d_params is device
+ * float64[AWG_LEARNED_NPARAM].  Errors: AWG_ERR_INVALID_ARG, AWG_ERR_CUDA. */
+awg_status awg_learned_forward(int P, const double* d_features, const double* d_params, double* d_out,
+                               int precision, void* stream);
+
+/* Gradient of the mean squared error L = (1/P) sum_p (out_p - t_p)^2 with
+ * respect to the parameters: d_grad (device float64[AWG_LEARNED_NPARAM + 1])
+ * receives the gradient, then L.  Sums are taken in a fixed order (the
+ * result does not depend on scheduling).  Allocates scratch on `stream`.
+ * Errors: AWG_ERR_INVALID_ARG, AWG_ERR_OOM, AWG_ERR_CUDA. */
+awg_status awg_learned_grad(int P, const double* d_features, const double* d_targets,
+                            const double* d_params, double* d_grad, int precision, void* stream);
+
+/* `steps` full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, step
+ * size lr) on L, all on the device.  h_params (host float64[NPARAM]) holds
+ * the start on entry and the result on return; h_loss (host float64[steps]
+ * or NULL) receives L before each step.  Synchronous.  Errors:
+ * AWG_ERR_INVALID_ARG, AWG_ERR_OOM, AWG_ERR_CUDA. */
+awg_status awg_learned_train(int P, const double* d_features, const double* d_targets, double* h_params,
+                             int steps, double lr, int precision, double* h_loss, void* stream);
 
 #ifdef __cplusplus
 }

@@ -40,7 +40,9 @@ class awg_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("precisions", ctypes.c_int),
                 ("zero_rtol", ctypes.c_double), ("w_rtol", ctypes.c_double),
                 ("w_maxit", ctypes.c_int), ("maxit", ctypes.c_int), ("verbose", ctypes.c_int),
-                ("w_precision", ctypes.c_int)]
+                ("w_precision", ctypes.c_int), ("geneo_solver", ctypes.c_int),
+                ("geneo_block", ctypes.c_int), ("geneo_maxit", ctypes.c_int),
+                ("learned_params", ctypes.c_void_p)]
 
 
 class awg_info(ctypes.Structure):
@@ -48,12 +50,17 @@ class awg_info(ctypes.Structure):
                 ("sum_ns", ctypes.c_int64), ("max_ns", ctypes.c_int), ("n0", ctypes.c_int),
                 ("n_minus", ctypes.c_int), ("n_minus_all", ctypes.c_int),
                 ("w_iters", ctypes.c_int), ("w_relres", ctypes.c_double),
-                ("setup_ms", ctypes.c_double * 8), ("device_bytes", ctypes.c_size_t)]
+                ("setup_ms", ctypes.c_double * 8), ("device_bytes", ctypes.c_size_t),
+                ("geneo_its_max", ctypes.c_int), ("geneo_its_sum", ctypes.c_int64),
+                ("geneo_dense", ctypes.c_int)]
 
 
 EXPORTED = ["awg_default_options", "awg_status_string", "awg_setup", "awg_destroy",
             "awg_get_info", "awg_apply", "awg_apply_stage", "awg_pcg", "awg_get_array",
-            "awg_profile", "awg_profile_read", "awg_apply_hnn_noalloc"]
+            "awg_profile", "awg_profile_read", "awg_apply_hnn_noalloc", "awg_learned_data",
+            "awg_learned_forward", "awg_learned_grad", "awg_learned_train"]
+LEARNED_NPARAM, LEARNED_NFEAT = 385, 5
+GENEO_DENSE, GENEO_BLOCK, GENEO_LEARNED = 0, 1, 2
 PROF_NAMES = ["spmv", "local", "wt", "wd", "coarse", "subdomain", "prolong", "vector"]
 
 _lib = None
@@ -95,6 +102,14 @@ def load_library(path: str = LIB_PATH):
     lib.awg_profile_read.restype = I
     lib.awg_apply_hnn_noalloc.argtypes = [P, I, P, P, P]
     lib.awg_apply_hnn_noalloc.restype = I
+    lib.awg_learned_data.argtypes = [P, P, P, P]
+    lib.awg_learned_data.restype = I
+    lib.awg_learned_forward.argtypes = [I, P, P, P, I, P]
+    lib.awg_learned_forward.restype = I
+    lib.awg_learned_grad.argtypes = [I, P, P, P, P, I, P]
+    lib.awg_learned_grad.restype = I
+    lib.awg_learned_train.argtypes = [I, P, P, P, I, D, I, P, P]
+    lib.awg_learned_train.restype = I
     _lib = lib
     return lib
 
@@ -111,9 +126,18 @@ def _stream_ptr(stream) -> ctypes.c_void_p:
 
 
 def default_options(**kw) -> awg_options:
+    """Defaults of the library with the given fields replaced.  A NumPy
+    `learned_params` array is passed by pointer and kept alive on the
+    returned structure."""
     o = awg_options()
     load_library().awg_default_options(ctypes.byref(o))
     for k, v in kw.items():
+        if k == "learned_params" and v is not None and not isinstance(v, int):
+            arr = np.ascontiguousarray(v, dtype=np.float64)
+            if arr.size != LEARNED_NPARAM:
+                raise ValueError(f"learned_params needs {LEARNED_NPARAM} values")
+            o._learned_keep = arr
+            v = arr.ctypes.data
         setattr(o, k, v)
     return o
 
@@ -186,6 +210,42 @@ def awg_apply_hnn_noalloc(h, x, y, precision: int = FP64, stream=None):
     _check(load_library().awg_apply_hnn_noalloc(h, precision, x.data_ptr(), y.data_ptr(),
                                                 _stream_ptr(stream)), "awg_apply_hnn_noalloc")
     return y
+
+
+def awg_learned_data(h, features=None, targets=None, stream=None):
+    """Per-node features (sum_ns x 5) and leverage targets (sum_ns) of a
+    built handle into caller-owned float64 CUDA tensors (either may be None)."""
+    _check(load_library().awg_learned_data(
+        h, None if features is None else features.data_ptr(),
+        None if targets is None else targets.data_ptr(), _stream_ptr(stream)), "awg_learned_data")
+
+
+def awg_learned_forward(features, params, out, precision: int = FP64, stream=None):
+    _check(load_library().awg_learned_forward(features.shape[0], features.data_ptr(),
+                                              params.data_ptr(), out.data_ptr(), precision,
+                                              _stream_ptr(stream)), "awg_learned_forward")
+    return out
+
+
+def awg_learned_grad(features, targets, params, grad, precision: int = FP64, stream=None):
+    """grad (NPARAM + 1 float64 on the device): gradient of the mean squared
+    error, then the loss."""
+    _check(load_library().awg_learned_grad(features.shape[0], features.data_ptr(),
+                                           targets.data_ptr(), params.data_ptr(), grad.data_ptr(),
+                                           precision, _stream_ptr(stream)), "awg_learned_grad")
+    return grad
+
+
+def awg_learned_train(features, targets, params: np.ndarray, steps: int, lr: float = 1e-2,
+                      precision: int = FP64, stream=None):
+    """Full-batch Adam on the device; returns (new params, loss per step)."""
+    th = np.array(params, dtype=np.float64, copy=True)
+    loss = np.zeros(max(steps, 1))
+    _check(load_library().awg_learned_train(features.shape[0], features.data_ptr(),
+                                            targets.data_ptr(), th.ctypes.data, int(steps),
+                                            float(lr), precision, loss.ctypes.data,
+                                            _stream_ptr(stream)), "awg_learned_train")
+    return th, loss[:steps]
 
 
 def awg_profile(h, mask: int):

@@ -99,6 +99,10 @@ void awg_default_options(awg_options* opt) {
     opt->maxit = 1000;
     opt->verbose = 0;
     opt->w_precision = AWG_MIXED_FP32;
+    opt->geneo_solver = 0;
+    opt->geneo_block = 8;
+    opt->geneo_maxit = 60;
+    opt->learned_params = nullptr;
 }
 
 const char* awg_status_string(awg_status s) {
@@ -151,6 +155,9 @@ static awg_status setup_impl(Handle* h, const int* d_rowptr, const int* d_colidx
                 h->setup_ms[1], h->setup_ms[2], h->setup_ms[3], h->setup_ms[4], h->setup_ms[5],
                 h->setup_ms[6], h->setup_ms[7], h->n0, h->n_minus, h->n_minus_all, h->w_iters,
                 h->w_relres);
+    if (h->opt.verbose && h->opt.geneo_solver)
+        fprintf(stderr, "libawg: GenEO block solver: steps max %d, sum %lld; dense fallback %d of %d\n",
+                h->geneo_its_max, (long long)h->geneo_its_sum, h->geneo_dense, h->N);
     return AWG_OK;
 }
 
@@ -166,7 +173,9 @@ awg_status awg_setup(int n, int nnz, const int* d_rowptr, const int* d_colidx, c
     awg_default_options(&o);
     if (opt) o = *opt;
     if (o.variant < 0 || o.variant > 2 || !(o.zero_rtol >= 0.0) || !(o.w_rtol > 0.0) ||
-        o.w_maxit < 1 || o.maxit < 1 || (o.w_precision != AWG_FP64 && o.w_precision != AWG_MIXED_FP32))
+        o.w_maxit < 1 || o.maxit < 1 || (o.w_precision != AWG_FP64 && o.w_precision != AWG_MIXED_FP32) ||
+        o.geneo_solver < 0 || o.geneo_solver > 2 || o.geneo_block < 2 || o.geneo_block > 16 ||
+        o.geneo_maxit < 1 || (o.geneo_solver == 2 && !o.learned_params))
         return AWG_ERR_INVALID_ARG;
     o.precisions |= 1 << AWG_FP64;
     Handle* h = new (std::nothrow) Handle();
@@ -177,6 +186,8 @@ awg_status awg_setup(int n, int nnz, const int* d_rowptr, const int* d_colidx, c
     h->overlap = overlap;
     h->tau = tau;
     h->opt = o;
+    if (o.geneo_solver == 2) h->h_learned.assign(o.learned_params, o.learned_params + AWG_LEARNED_NPARAM);
+    h->opt.learned_params = nullptr;  // the caller's array is read during setup only
     h->stream = (cudaStream_t)stream;
     awg_status st = setup_impl(h, d_rowptr, d_colidx, d_val, d_partition);
     if (st != AWG_OK) {
@@ -212,6 +223,9 @@ awg_status awg_get_info(awg_handle hh, awg_info* info) {
     info->w_relres = h->w_relres;
     for (int i = 0; i < 8; i++) info->setup_ms[i] = h->setup_ms[i];
     info->device_bytes = h->device_bytes;
+    info->geneo_its_max = h->geneo_its_max;
+    info->geneo_its_sum = h->geneo_its_sum;
+    info->geneo_dense = h->geneo_dense;
     return AWG_OK;
 }
 

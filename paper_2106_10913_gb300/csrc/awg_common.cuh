@@ -108,6 +108,13 @@ struct Handle {
     DevBuf F64;                          // W^T A W of the float64 W
     PrecOps prec[3];
 
+    // GenEO block solver (awg_options.geneo_solver): network parameters of
+    // the learned start and per-setup iteration figures
+    std::vector<double> h_learned;
+    int geneo_its_max = 0;
+    int64_t geneo_its_sum = 0;
+    int geneo_dense = 0;
+
     // info
     int w_iters = 0;
     double w_relres = 0.0;
@@ -229,8 +236,10 @@ struct GemmDescF {
     double alpha, beta;
 };
 awg_status gemm_batched_f32(Handle* h, const std::vector<GemmDescF>& descs, cudaStream_t s);
+// Lower Cholesky factor in place of every block; a non-positive pivot raises
+// FLAG_NOT_SPD in *d_flag (if given) and sets d_status[block] = 1 (if given).
 awg_status potrf_batched(Handle* h, double* arena, const int* d_m, const int64_t* d_off, int nb,
-                         int max_m, int* d_flag, cudaStream_t s);
+                         int max_m, int* d_flag, cudaStream_t s, int* d_status = nullptr);
 awg_status trtri_batched(Handle* h, double* arena, const int* d_m, const int64_t* d_off, int nb,
                          int max_m, cudaStream_t s);
 // Selected eigenpairs of symmetric blocks (destroys the blocks).  mode 0: all
@@ -247,5 +256,35 @@ awg_status eig_select_batched(Handle* h, double* arena, const int* d_m, const in
 // solve.cu
 awg_status apply_stage(Handle* h, int which, int prec, const double* x, double* y, cudaStream_t s);
 awg_status build_setup_numeric(Handle* h);
+
+// learned.cu : features, network and start block of the GenEO block solver
+constexpr int LEARNED_NF = 5;
+constexpr int LEARNED_NPARAM = 385;
+awg_status learned_features(Handle* h, double* d_F, cudaStream_t s);
+awg_status learned_forward(int P, const double* d_F, const double* d_params, double* d_out, int prec,
+                           cudaStream_t s);
+// gradient (LEARNED_NPARAM values) then the loss into d_g; d_part holds
+// nblocks x (LEARNED_NPARAM + 1) partial sums
+awg_status learned_grad(int P, const double* d_F, const double* d_t, const double* d_params,
+                        double* d_g, double* d_part, int nblocks, int prec, cudaStream_t s);
+awg_status learned_adam(int t, double lr, const double* d_g, double* d_th, double* d_m, double* d_v,
+                        cudaStream_t s);
+awg_status learned_targets(Handle* h, double* d_t, cudaStream_t s);
+awg_status learned_start_block(Handle* h, const int64_t* d_xoff, int b, const double* d_g, double* d_X0,
+                               cudaStream_t s);
+
+// geneo_iter.cu : certified block eigensolver of the GenEO pencils
+struct GeneoIter {
+    int b = 0;
+    std::vector<int> ecount;   // extra modes per subdomain, -1: not certified
+    std::vector<int> its;      // iterations per subdomain
+    std::vector<int64_t> hx;   // offsets of the m x b blocks
+    DevBuf xoff, X, BX, Kq, MBKq;
+};
+awg_status geneo_block_solve(Handle* h, const double* MA, const double* MB, const double* d_params,
+                             int b, int maxit, double tol, GeneoIter& r);
+// writes [Kq_s | X_s(:, 0..e_s)] of every certified subdomain at Z + zoff[s]
+awg_status geneo_block_pack(Handle* h, GeneoIter& r, const int64_t* d_zoff, double* Z);
+void geneo_block_free(Handle* h, GeneoIter& r);
 
 }  // namespace awg

@@ -194,7 +194,8 @@ awg_status gemm_batched_f32(Handle* h, const std::vector<GemmDescF>& descs, cuda
 // Lower Cholesky factor in place (right-looking).  A pivot that is not
 // positive (or not finite) raises FLAG_NOT_SPD and stops that block.
 __global__ void __launch_bounds__(512) k_potrf(double* arena, const int* __restrict__ ms,
-                                               const int64_t* __restrict__ offs, int* flag) {
+                                               const int64_t* __restrict__ offs, int* flag,
+                                               int* status) {
     extern __shared__ double col[];
     __shared__ int bad;
     const int s = blockIdx.x;
@@ -228,7 +229,8 @@ __global__ void __launch_bounds__(512) k_potrf(double* arena, const int* __restr
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0 && bad) atomicOr(flag, FLAG_NOT_SPD);
+    if (threadIdx.x == 0 && bad && flag) atomicOr(flag, FLAG_NOT_SPD);
+    if (threadIdx.x == 0 && status) status[s] = bad;
     // zero the strict upper triangle so that the block is a plain lower matrix
     if (!bad) {
         for (int c = 1 + wid; c < m; c += nw) {
@@ -239,13 +241,13 @@ __global__ void __launch_bounds__(512) k_potrf(double* arena, const int* __restr
 }
 
 awg_status potrf_batched(Handle* h, double* arena, const int* d_m, const int64_t* d_off, int nb,
-                         int max_m, int* d_flag, cudaStream_t s) {
+                         int max_m, int* d_flag, cudaStream_t s, int* d_status) {
     if (nb == 0) return AWG_OK;
     const size_t smem = (size_t)max_m * sizeof(double);
     if (smem > 48 * 1024)
         AWG_CUDA(cudaFuncSetAttribute(k_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-    k_potrf<<<nb, 512, smem, s>>>(arena, d_m, d_off, d_flag);
+    k_potrf<<<nb, 512, smem, s>>>(arena, d_m, d_off, d_flag, d_status);
     AWG_LAUNCH();
     (void)h;
     return AWG_OK;

@@ -579,55 +579,103 @@ awg_status build_setup_numeric(Handle* h) {
                                    (int64_t*)h->vm_off.p, (double*)h->Vm.p, (double*)h->lam_m.p,
                                    (double*)A2.p);
     AWG_LAUNCH();
-    AWG_CUDA(cudaMemsetAsync(h->flag.p, 0, sizeof(int), s));
-    AWG_TRY(potrf_batched(h, (double*)A1.p, (int*)h->ns.p, (int64_t*)h->dense_off.p, N, maxm,
-                          (int*)h->flag.p, s));
-    AWG_TRY(check_flag(h, FLAG_NOT_SPD, AWG_ERR_NOT_SPD));
-    AWG_TRY(trtri_batched(h, (double*)A1.p, (int*)h->ns.p, (int64_t*)h->dense_off.p, N, maxm, s));
-    AWG_TRY(dalloc(h, A3, (size_t)h->dense_total * 8));
-    {
-        std::vector<GemmDesc> d1, d2;
-        const double* Li = (const double*)A1.p;
+    // Block eigensolver first (it reads M_A and M_B and keeps them); the
+    // pencils it does not certify go to the dense eigensolver below.
+    GeneoIter gi;
+    std::vector<int> sel;
+    h->geneo_its_max = 0;
+    h->geneo_its_sum = 0;
+    if (h->opt.geneo_solver != 0) {
+        DevBuf prm;
+        if (h->opt.geneo_solver == 2)
+            AWG_TRY(upload(h, prm, h->h_learned.data(), LEARNED_NPARAM * sizeof(double)));
+        AWG_TRY(geneo_block_solve(h, (double*)A2.p, (double*)A1.p, (double*)prm.p, h->opt.geneo_block,
+                                  h->opt.geneo_maxit, 1e-13, gi));
+        dfree(h, prm);
         for (int t = 0; t < N; t++) {
-            const int m = h->h_ns[t];
-            const int64_t o = h->h_dense_off[t];
-            d1.push_back({Li + o, (double*)A2.p + o, (double*)A3.p + o, m, m, m, m, m, m, 0, 0, 1.0, 0.0});
-            d2.push_back({(double*)A3.p + o, Li + o, (double*)A2.p + o, m, m, m, m, m, m, 0, 1, 1.0, 0.0});
+            if (gi.ecount[t] < 0) sel.push_back(t);
+            h->geneo_its_max = std::max(h->geneo_its_max, gi.its[t]);
+            h->geneo_its_sum += gi.its[t];
         }
-        AWG_TRY(gemm_batched(h, d1, s));  // A3 = L^-1 M_A
-        AWG_TRY(gemm_batched(h, d2, s));  // A2 = A3 L^-T
+    } else {
+        for (int t = 0; t < N; t++) sel.push_back(t);
     }
-    dfree(h, A3);
-    k_symmetrize<<<gblk, 256, 0, s>>>((int*)h->ns.p, (int64_t*)h->dense_off.p, (double*)A2.p);
-    AWG_LAUNCH();
-    {
-        std::vector<int> mc, mcs, mptr;
-        std::vector<int64_t> qoff;
-        DevBuf Q, qvals;
+    h->geneo_dense = (int)sel.size();
+    // dense eigensolver on that subset: M_B = L L^T, eigenpairs of
+    // L^-1 M_A L^-T below tau, Y = L^-T Q
+    const int nsel = (int)sel.size();
+    std::vector<int> mc_sel;
+    std::vector<int64_t> qoff;
+    DevBuf Q, qvals, dms, dos;
+    if (nsel > 0) {
+        std::vector<int> hms(nsel);
+        std::vector<int64_t> hos(nsel);
+        int maxsel = 1;
+        for (int k = 0; k < nsel; k++) {
+            hms[k] = h->h_ns[sel[k]];
+            hos[k] = h->h_dense_off[sel[k]];
+            maxsel = std::max(maxsel, hms[k]);
+        }
+        AWG_TRY(upload(h, dms, hms.data(), nsel * sizeof(int)));
+        AWG_TRY(upload(h, dos, hos.data(), nsel * sizeof(int64_t)));
         AWG_CUDA(cudaMemsetAsync(h->flag.p, 0, sizeof(int), s));
-        AWG_TRY(eig_select_batched(h, (double*)A2.p, (int*)h->ns.p, (int64_t*)h->dense_off.p, h->h_ns,
-                                   N, maxm, 1, h->tau, mc, mcs, Q, qoff, qvals, mptr, s));
+        AWG_TRY(potrf_batched(h, (double*)A1.p, (int*)dms.p, (int64_t*)dos.p, nsel, maxsel, (int*)h->flag.p, s));
+        AWG_TRY(check_flag(h, FLAG_NOT_SPD, AWG_ERR_NOT_SPD));
+        AWG_TRY(trtri_batched(h, (double*)A1.p, (int*)dms.p, (int64_t*)dos.p, nsel, maxsel, s));
+        AWG_TRY(dalloc(h, A3, (size_t)h->dense_total * 8));
+        {
+            std::vector<GemmDesc> d1, d2;
+            const double* Li = (const double*)A1.p;
+            for (int t : sel) {
+                const int m = h->h_ns[t];
+                const int64_t o = h->h_dense_off[t];
+                d1.push_back({Li + o, (double*)A2.p + o, (double*)A3.p + o, m, m, m, m, m, m, 0, 0, 1.0, 0.0});
+                d2.push_back({(double*)A3.p + o, Li + o, (double*)A2.p + o, m, m, m, m, m, m, 0, 1, 1.0, 0.0});
+            }
+            AWG_TRY(gemm_batched(h, d1, s));  // A3 = L^-1 M_A
+            AWG_TRY(gemm_batched(h, d2, s));  // A2 = A3 L^-T
+        }
+        dfree(h, A3);
+        k_symmetrize<<<dim3(nsel, 16), 256, 0, s>>>((int*)dms.p, (int64_t*)dos.p, (double*)A2.p);
+        AWG_LAUNCH();
+        std::vector<int> mcs, mptr;
+        AWG_CUDA(cudaMemsetAsync(h->flag.p, 0, sizeof(int), s));
+        AWG_TRY(eig_select_batched(h, (double*)A2.p, (int*)dms.p, (int64_t*)dos.p, hms, nsel, maxsel, 1,
+                                   h->tau, mc_sel, mcs, Q, qoff, qvals, mptr, s));
         AWG_TRY(check_flag(h, FLAG_EIG, AWG_ERR_EIG));
+    }
+    {
+        std::vector<int> mc(N, 0);
+        for (int t = 0; t < N; t++)
+            if (h->opt.geneo_solver != 0 && gi.ecount[t] >= 0) mc[t] = h->h_nm[t] + gi.ecount[t];
+        for (int k = 0; k < nsel; k++) mc[sel[k]] = mc_sel[k];
         h->h_modes = mc;
-        h->h_mode_ptr = mptr;
-        h->h_z_off = qoff;
-        h->n0 = mptr[N];
+        h->h_mode_ptr.assign(N + 1, 0);
+        h->h_z_off.assign(N + 1, 0);
+        for (int t = 0; t < N; t++) {
+            h->h_mode_ptr[t + 1] = h->h_mode_ptr[t] + mc[t];
+            h->h_z_off[t + 1] = h->h_z_off[t] + (int64_t)h->h_ns[t] * mc[t];
+        }
+        h->n0 = h->h_mode_ptr[N];
         AWG_TRY(upload(h, h->modes, mc.data(), N * sizeof(int)));
-        AWG_TRY(upload(h, h->mode_ptr, mptr.data(), (N + 1) * sizeof(int)));
-        AWG_TRY(upload(h, h->z_off, qoff.data(), (N + 1) * sizeof(int64_t)));
-        AWG_TRY(dalloc(h, h->Z, std::max<size_t>(8, (size_t)qoff[N] * 8)));
+        AWG_TRY(upload(h, h->mode_ptr, h->h_mode_ptr.data(), (N + 1) * sizeof(int)));
+        AWG_TRY(upload(h, h->z_off, h->h_z_off.data(), (N + 1) * sizeof(int64_t)));
+        AWG_TRY(dalloc(h, h->Z, std::max<size_t>(8, (size_t)h->h_z_off[N] * 8)));
+        if (h->opt.geneo_solver != 0) {
+            AWG_TRY(geneo_block_pack(h, gi, (int64_t*)h->z_off.p, (double*)h->Z.p));
+            geneo_block_free(h, gi);
+        }
         std::vector<GemmDesc> d;
         const double* Li = (const double*)A1.p;
-        for (int t = 0; t < N; t++) {
-            const int m = h->h_ns[t], k = mc[t];
-            if (k == 0) continue;
-            d.push_back({Li + h->h_dense_off[t], (double*)Q.p + qoff[t], (double*)h->Z.p + qoff[t], m, k, m,
+        for (int k = 0; k < nsel; k++) {
+            const int t = sel[k], m = h->h_ns[t], c = mc_sel[k];
+            if (c == 0) continue;
+            d.push_back({Li + h->h_dense_off[t], (double*)Q.p + qoff[k], (double*)h->Z.p + h->h_z_off[t], m, c, m,
                          m, m, m, 1, 0, 1.0, 0.0});  // Y = L^-T Q
         }
         AWG_TRY(gemm_batched(h, d, s));
         AWG_CUDA(cudaStreamSynchronize(s));
-        dfree(h, Q);
-        dfree(h, qvals);
+        for (DevBuf* bb : {&Q, &qvals, &dms, &dos}) dfree(h, *bb);
     }
     dfree(h, A1);
     dfree(h, A2);

@@ -1,0 +1,212 @@
+"""GPU path of the GenEO block eigensolver and its learned start block
+against the oracle (oracle/learned.py, oracle/awg_oracle.py), through the
+C ABI.
+
+* network forward and gradient: float64 within 1e-12 relative, float32
+  within 1e-4;
+* features: within 1e-13; training targets (normalised leverage of the extra
+  modes, a function of their span only): within 1e-8;
+* Adam on the device against the oracle's Adam steps: within 1e-9;
+* block solver (random and learned start): GenEO mode counts bit-exact, every
+  subdomain certified, the apply within the tolerance of the dense-eigensolver
+  path, PCG iteration counts within 5 % of the oracle's.
+"""
+
+import numpy as np
+import pytest
+
+import awg_inputs as gi
+import oracle as O
+import oracle.learned as L
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+APPLY_RTOL = 1e-11
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _net_inputs(P=3000, seed=0):
+    rng = np.random.default_rng(seed)
+    F = rng.standard_normal((P, L.NF))
+    t = rng.uniform(0.0, 1.0, P)
+    th = L.init_params(seed + 1) + 0.2 * rng.standard_normal(L.NPARAM)
+    return F, t, th
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("P", [1, 127, 3000])
+def test_forward_parity(P):
+    from paper_2106_10913_gb300 import FP64, MIXED_FP32, awg_learned_forward
+    F, _, th = _net_inputs(P, seed=P)
+    ref, _ = L.forward(th, F)
+    for prec, tol in ((FP64, 1e-12), (MIXED_FP32, 1e-4)):
+        out = torch.zeros(P, dtype=torch.float64, device="cuda")
+        awg_learned_forward(_cuda(F), _cuda(th), out, precision=prec)
+        assert _rel(out.cpu().numpy(), ref) <= tol
+
+
+@pytest.mark.parametrize("P", [1, 128, 129, 5000, 100000])
+def test_gradient_parity(P):
+    """Gradient and loss; sizes span a partial tile, whole tiles and more
+    tiles than blocks (each block then loops over several tiles)."""
+    from paper_2106_10913_gb300 import FP64, MIXED_FP32, awg_learned_grad
+    F, t, th = _net_inputs(P, seed=7)
+    loss, g = L.loss_and_grad(th, F, t)
+    for prec, tol in ((FP64, 1e-12), (MIXED_FP32, 1e-4)):
+        out = torch.zeros(L.NPARAM + 1, dtype=torch.float64, device="cuda")
+        awg_learned_grad(_cuda(F), _cuda(t), _cuda(th), out, precision=prec)
+        o = out.cpu().numpy()
+        assert _rel(o[:L.NPARAM], g) <= tol
+        assert abs(o[L.NPARAM] - loss) <= tol * loss
+
+
+def test_gradient_is_deterministic():
+    from paper_2106_10913_gb300 import FP64, awg_learned_grad
+    F, t, th = _net_inputs(20000, seed=3)
+    a = torch.zeros(L.NPARAM + 1, dtype=torch.float64, device="cuda")
+    b = torch.zeros_like(a)
+    awg_learned_grad(_cuda(F), _cuda(t), _cuda(th), a, precision=FP64)
+    awg_learned_grad(_cuda(F), _cuda(t), _cuda(th), b, precision=FP64)
+    assert torch.equal(a, b)
+
+
+def test_adam_training_parity():
+    """Full-batch Adam on the device against the oracle's steps."""
+    from paper_2106_10913_gb300 import FP64, awg_learned_train
+    F, t, th0 = _net_inputs(2000, seed=11)
+    steps, lr = 25, 1e-2
+    th, m, v = th0.copy(), np.zeros(L.NPARAM), np.zeros(L.NPARAM)
+    losses = []
+    for k in range(1, steps + 1):
+        loss, g = L.loss_and_grad(th, F, t)
+        losses.append(loss)
+        th, m, v = L.adam_step(th, g, m, v, k, lr=lr)
+    got, gl = awg_learned_train(_cuda(F), _cuda(t), th0, steps, lr, precision=FP64)
+    assert np.max(np.abs(got - th)) <= 1e-9
+    assert np.allclose(gl, losses, rtol=1e-10, atol=0)
+    assert gl[-1] < gl[0]
+
+
+# ------------------------------------------------------------ setup-based tests
+CASES = {
+    "channels24": gi.channels2d(24, q=3, nchan=3, contrast=1e3, seed=5, overlap=2, tau=0.1),
+    "config1": gi.config1(),
+    "channels48": gi.channels2d(48, q=3, nchan=4, contrast=1e4, seed=9, overlap=2, tau=0.1),
+    "channels64": gi.channels2d(64, q=2, nchan=3, contrast=1e6, seed=11, overlap=2, tau=0.1),
+}
+_ORACLE = {}
+
+
+def _oracle(name):
+    if name not in _ORACLE:
+        p = CASES[name]
+        _ORACLE[name] = (p, O.setup_problem(p, dense=p.n <= 6000))
+    return _ORACLE[name]
+
+
+def _solver(p, **opts):
+    from paper_2106_10913_gb300 import AWGSolver
+    return AWGSolver(p.rowptr, p.colidx, p.val, p.part, p.nparts, p.overlap, p.tau, **opts)
+
+
+@pytest.mark.parametrize("name", ["channels24", "config1", "channels48"])
+def test_features_and_targets(name):
+    from paper_2106_10913_gb300 import awg_learned_data
+    p, st = _oracle(name)
+    sol = _solver(p)
+    S = sol.info["sum_ns"]
+    F = torch.zeros((S, L.NF), dtype=torch.float64, device="cuda")
+    t = torch.zeros(S, dtype=torch.float64, device="cuda")
+    awg_learned_data(sol.h, F, t)
+    torch.cuda.synchronize()
+    mult = 1.0 / st.d
+    Fref = np.vstack([L.node_features(st.A, idx, mult) for idx in st.subs])
+    tref = np.concatenate([L.leverage(L.extra_modes(st, s)) for s in range(st.N)])
+    assert np.max(np.abs(F.cpu().numpy() - Fref)) <= 1e-13
+    assert np.max(np.abs(t.cpu().numpy() - tref)) <= 1e-8
+    sol.close()
+
+
+def _trained_params():
+    """Network trained on the device on the features and targets of one
+    channel instance (seed 9); used on other instances."""
+    from paper_2106_10913_gb300 import MIXED_FP32, awg_learned_data, awg_learned_train
+    p, _ = _oracle("channels48")
+    sol = _solver(p)
+    S = sol.info["sum_ns"]
+    F = torch.zeros((S, L.NF), dtype=torch.float64, device="cuda")
+    t = torch.zeros(S, dtype=torch.float64, device="cuda")
+    awg_learned_data(sol.h, F, t)
+    th, loss = awg_learned_train(F, t, L.init_params(0), 300, 1e-2, precision=MIXED_FP32)
+    sol.close()
+    assert loss[-1] < loss[0]
+    return th
+
+
+@pytest.fixture(scope="module")
+def trained():
+    return _trained_params()
+
+
+@pytest.mark.parametrize("solver", [1, 2])
+@pytest.mark.parametrize("name", ["channels24", "config1", "channels64"])
+def test_block_solver_parity(name, solver, trained):
+    """Same coarse space as the dense eigensolver: exact mode counts, apply
+    and PCG parity with the oracle, every subdomain certified."""
+    p, st = _oracle(name)
+    opts = dict(geneo_solver=solver)
+    if solver == 2:
+        opts["learned_params"] = trained
+    sol = _solver(p, **opts)
+    assert sol.array("modes").tolist() == O.mode_counts(st).tolist()
+    assert sol.info["n0"] == st.n0
+    assert sol.info["geneo_dense"] == 0
+    assert sol.info["geneo_its_max"] >= 1
+    x = np.random.default_rng(123).standard_normal(p.n)
+    tol = max(APPLY_RTOL, O.local_condition(st) * np.finfo(float).eps)
+    for stage, ref in (("hnn", O.H_NN_apply), ("h3ad", O.H3_ad_apply)):
+        y = sol.apply(torch.from_numpy(x).cuda(), stage=stage).cpu().numpy()
+        assert _rel(y, ref(st, x)) <= tol, stage
+    bv = p.b if p.b.ndim == 1 else p.b[0]
+    xs, its, rel, status = sol.pcg(torch.from_numpy(bv).cuda(), rtol=1e-8)
+    ref = O.pcg(lambda v: st.A @ v, bv, lambda r: O.H3_ad_apply(st, r), rtol=1e-8)
+    assert status == 0 and rel[0] <= 1e-8
+    assert abs(its[0] - ref.iters) <= max(1, round(0.05 * ref.iters))
+    sol.close()
+
+
+def test_block_width_too_small_falls_back():
+    """With b = 2 a subdomain with two or more extra modes cannot be held by
+    the block: it goes to the dense eigensolver, and the result is unchanged."""
+    p, st = _oracle("config1")
+    sol = _solver(p, geneo_solver=1, geneo_block=2)
+    extra = [L.extra_modes(st, s).shape[1] for s in range(st.N)]
+    assert sol.info["geneo_dense"] >= sum(e >= 2 for e in extra)
+    assert sol.array("modes").tolist() == O.mode_counts(st).tolist()
+    x = np.random.default_rng(1).standard_normal(p.n)
+    y = sol.apply(torch.from_numpy(x).cuda(), stage="h3ad").cpu().numpy()
+    assert _rel(y, O.H3_ad_apply(st, x)) <= max(APPLY_RTOL, O.local_condition(st) * 2.3e-16)
+    sol.close()
+
+
+def test_learned_start_iterations(trained, capsys):
+    """Block-solver steps from the learned start against the random start on
+    an instance the network was not trained on (reported; both certified)."""
+    p = gi.channels2d(64, q=2, nchan=4, contrast=1e4, seed=21, overlap=2, tau=0.1)
+    r = _solver(p, geneo_solver=1)
+    l = _solver(p, geneo_solver=2, learned_params=trained)
+    assert r.info["geneo_dense"] == 0 and l.info["geneo_dense"] == 0
+    assert r.array("modes").tolist() == l.array("modes").tolist()
+    with capsys.disabled():
+        print(f"\n[learned start] steps sum random {r.info['geneo_its_sum']} learned "
+              f"{l.info['geneo_its_sum']}; max random {r.info['geneo_its_max']} learned "
+              f"{l.info['geneo_its_max']}")
+    r.close()
+    l.close()

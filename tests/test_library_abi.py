@@ -45,6 +45,8 @@ def test_host_only_calls(lib):
     import paper_2106_10913_gb300 as pkg
     o = pkg.default_options()
     assert o.variant == 0 and o.precisions == 1 and o.zero_rtol == 1e-12 and o.maxit == 1000
+    assert o.geneo_solver == 0 and o.geneo_block == 8 and o.geneo_maxit == 60
+    assert not o.learned_params
     assert lib.awg_status_string(0) == b"AWG_OK"
     assert lib.awg_status_string(2) == b"AWG_ERR_MIN_OVERLAP"
     # argument errors are rejected before any CUDA call
@@ -52,6 +54,15 @@ def test_host_only_calls(lib):
     st = lib.awg_setup(0, 0, None, None, None, None, 1, 1, 0.1, None, None, ctypes.byref(h))
     assert st == 1 and not h.value
     assert lib.awg_get_info(None, None) == 1
+    # the learned start needs its parameters; the network calls check sizes
+    o = pkg.default_options(geneo_solver=2)
+    st = lib.awg_setup(4, 4, 1, 1, 1, 1, 1, 1, 0.1, ctypes.byref(o), None, ctypes.byref(h))
+    assert st == 1 and not h.value
+    assert lib.awg_learned_forward(-1, None, None, None, 0, None) == 1
+    assert lib.awg_learned_grad(0, None, None, None, None, 0, None) == 1
+    assert lib.awg_learned_train(1, None, None, None, 1, 1e-2, 0, None, None) == 1
+    assert lib.awg_learned_data(None, None, None, None) == 1
+    assert ctypes.sizeof(pkg.awg.awg_options) == 64
 
 
 def test_product_does_not_import_oracle():
