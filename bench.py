@@ -188,9 +188,15 @@ def run_awg(args):
         torch.cuda.synchronize()
 
     p = _problem(args.config)
+    geneo_opts, train = {}, None
+    if args.geneo == "learned":
+        params, train = train_start_network()
+        geneo_opts = {"geneo_solver": 2, "learned_params": params}
+    elif args.geneo == "block":
+        geneo_opts = {"geneo_solver": 1}
     t0 = time.perf_counter()
     sol = AWGSolver(p.rowptr, p.colidx, p.val, p.part, p.nparts, p.overlap, p.tau,
-                    precisions=0b111, verbose=int(args.verbose))
+                    precisions=0b111, verbose=int(args.verbose), **geneo_opts)
     setup_s = time.perf_counter() - t0
     info = dict(sol.info)
     info["dense_total"] = int(np.sum(sol.array("ns").astype(np.int64) ** 2))
@@ -303,6 +309,11 @@ def run_awg(args):
                        "n0": info["n0"], "n_minus": info["n_minus"], "iters": best["iters"],
                        "l2": "inputs larger than L2 (W and local operators are GBs)",
                        "setup_s": round(setup_s, 2),
+                       "setup_ms": dict(zip(("structure", "split", "local", "geneo", "E", "W", "F",
+                                             "total"), (round(v, 1) for v in info["setup_ms"]))),
+                       "geneo": {"solver": args.geneo, "block_steps_max": info["geneo_its_max"],
+                                 "block_steps_sum": info["geneo_its_sum"],
+                                 "dense_subdomains": info["geneo_dense"], "training": train},
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "forms": {k: {"value": v["value"], "ms_per_step": v["ms_per_step"], "iters": v["iters"],
                           "relres": v["relres"], "ok": v["ok"]} for k, v in forms.items()},
@@ -320,6 +331,42 @@ def run_awg(args):
         dist.destroy_process_group()
 
 
+def train_start_network(seeds=(3, 4, 5), steps=400, lr=1e-2):
+    """Trains the start-block network on the device: features and leverage
+    targets of three 128 x 128 channel instances (4 x 4 subdomains of the
+    same 32 x 32 boxes as the benchmark problem, other seeds), full-batch
+    Adam in float32 kernels.  Returns (params, summary)."""
+    import torch
+    import awg_inputs as gi
+    from paper_2106_10913_gb300 import (AWGSolver, LEARNED_NFEAT, MIXED_FP32, awg_learned_data,
+                                        awg_learned_train)
+    t0 = time.perf_counter()
+    Fs, ts = [], []
+    for sd in seeds:
+        q = gi.channels2d(128, q=4, nchan=5, contrast=1e6, seed=sd, overlap=2, tau=0.1)
+        sol = AWGSolver(q.rowptr, q.colidx, q.val, q.part, q.nparts, q.overlap, q.tau)
+        S = sol.info["sum_ns"]
+        F = torch.zeros((S, LEARNED_NFEAT), dtype=torch.float64, device="cuda")
+        t = torch.zeros(S, dtype=torch.float64, device="cuda")
+        awg_learned_data(sol.h, F, t)
+        torch.cuda.synchronize()
+        sol.close()
+        Fs.append(F)
+        ts.append(t)
+    F, t = torch.cat(Fs), torch.cat(ts)
+    rng = np.random.default_rng(0)
+    th0 = np.zeros(385)
+    o = 0
+    for fo, fi in ((16, 5), (16, 16), (1, 16)):  # Glorot-uniform weights, zero biases
+        lim = np.sqrt(6.0 / (fi + fo))
+        th0[o:o + fo * fi] = rng.uniform(-lim, lim, fo * fi)
+        o += fo * fi + fo
+    th, loss = awg_learned_train(F, t, th0, steps, lr, precision=MIXED_FP32)
+    return th, {"instances": ["channels128 seed %d" % sd for sd in seeds], "samples": int(F.shape[0]),
+                "steps": steps, "loss_first": float(loss[0]), "loss_last": float(loss[-1]),
+                "seconds": round(time.perf_counter() - t0, 2)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -329,6 +376,10 @@ def main():
     ap.add_argument("--config", default="config2")
     ap.add_argument("--verbose", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--geneo", default="learned", choices=["learned", "block", "dense"],
+                    help="GenEO eigensolver of the setup: block solver from the learned start "
+                         "(network trained on the device on smaller instances), from a random "
+                         "start, or the dense eigensolver")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
