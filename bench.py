@@ -156,15 +156,18 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------- GPU arm
-def algorithmic_bytes(info, prec_bytes):
-    """Minimum bytes per launch of each kernel class."""
+def algorithmic_bytes(info, w_bytes, g_bytes, scaled):
+    """Minimum bytes per launch of each kernel class: W stored with w_bytes
+    per element (plus float32 row/column scales when `scaled`), the local
+    operators with g_bytes per element."""
     n, nm = info["n"], info["n_minus"]
     sum_ns = info["sum_ns"]
     dense = info["dense_total"]
+    sc = 4 if scaled else 0
     return {
-        "wt": n * nm * prec_bytes + 8 * n,
-        "wd": n * nm * prec_bytes + 16 * n + 8 * nm,
-        "local": dense * prec_bytes + 16 * sum_ns,
+        "wt": n * nm * w_bytes + 8 * n + sc * n,
+        "wd": n * nm * w_bytes + 16 * n + 8 * nm + sc * n,
+        "local": dense * g_bytes + 16 * sum_ns,
         "spmv": 12 * info["nnz"] + 4 * (n + 1) + 16 * n,
     }
 
@@ -172,7 +175,7 @@ def algorithmic_bytes(info, prec_bytes):
 def run_awg(args):
     import torch
     import torch.distributed as dist
-    from paper_2106_10913_gb300 import (AWGSolver, FP64, MIXED_BF16, MIXED_FP32, awg_pcg,
+    from paper_2106_10913_gb300 import (AWGSolver, FP64, MIXED_BF16, MIXED_FP16, MIXED_FP32, awg_pcg,
                                         awg_profile, awg_profile_read)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -196,7 +199,7 @@ def run_awg(args):
         geneo_opts = {"geneo_solver": 1}
     t0 = time.perf_counter()
     sol = AWGSolver(p.rowptr, p.colidx, p.val, p.part, p.nparts, p.overlap, p.tau,
-                    precisions=0b111, verbose=int(args.verbose), **geneo_opts)
+                    precisions=0b1111, verbose=int(args.verbose), **geneo_opts)
     setup_s = time.perf_counter() - t0
     info = dict(sol.info)
     info["dense_total"] = int(np.sum(sol.array("ns").astype(np.int64) ** 2))
@@ -206,7 +209,8 @@ def run_awg(args):
 
     forms = {}
     timed_mask = (1 << 2) | (1 << 3) | (1 << 1) | (1 << 0)  # wt, wd, local, spmv
-    for name, prec in (("fp64", FP64), ("mixed_fp32", MIXED_FP32), ("mixed_bf16", MIXED_BF16)):
+    for name, prec in (("fp64", FP64), ("mixed_fp32", MIXED_FP32), ("mixed_bf16", MIXED_BF16),
+                       ("mixed_fp16", MIXED_FP16)):
         for _ in range(args.warmup):
             awg_pcg(sol.h, b, x, RTOL, prec, check=False)
         barrier()
@@ -240,11 +244,12 @@ def run_awg(args):
     best = max((f for f in forms.values() if f["ok"]), key=lambda f: f["value"],
                default=forms["fp64"])
     best_name = [k for k, v in forms.items() if v is best][0]
-    pbytes = {FP64: 8, MIXED_FP32: 4, MIXED_BF16: 2}[best["prec"]]
+    wbytes = {FP64: 8, MIXED_FP32: 4, MIXED_BF16: 2, MIXED_FP16: 2}[best["prec"]]
+    gbytes = 8 if best["prec"] == FP64 else 4
 
     # roofline of the dominant kernel class of the headline form
     prof = best["prof"]
-    abytes = algorithmic_bytes(info, pbytes)
+    abytes = algorithmic_bytes(info, wbytes, gbytes, best["prec"] == MIXED_FP16)
     cand = {k: prof["ms"][k] for k in abytes if prof["count"][k] > 0}
     dom = max(cand, key=cand.get)
     per_launch_ms = prof["ms"][dom] / prof["count"][dom]
@@ -302,7 +307,8 @@ def run_awg(args):
             "metric": METRIC, "value": best["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {FP64: "f64", MIXED_FP32: "f32+f64", MIXED_BF16: "bf16+f32+f64"}[best["prec"]],
+            "dtype": {FP64: "f64", MIXED_FP32: "f32+f64", MIXED_BF16: "bf16+f32+f64",
+                      MIXED_FP16: "f16+f32+f64"}[best["prec"]],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "form": best_name, "n": p.n, "nparts": p.nparts,
                        "overlap": p.overlap, "tau": p.tau, "rtol": RTOL,

@@ -71,11 +71,14 @@ typedef enum { AWG_H3_AD = 0, AWG_H3_HYB = 1, AWG_H3_INEX = 2 } awg_variant;
  * keeps everything in float64.  MIXED_FP32 stores both in float32 with
  * float32 accumulation; MIXED_BF16 stores W in bfloat16 and the local
  * operators in float32 (the explicit local pseudo-inverses carry
- * cond(A^s_+), far beyond 8 mantissa bits on high-contrast problems).  Both
- * keep the PCG recurrences, both coarse factorisations and solves and the
- * GenEO selection test in float64, and assemble F from the same rounded W
- * (so H_3 stays SPD). */
-typedef enum { AWG_FP64 = 0, AWG_MIXED_FP32 = 1, AWG_MIXED_BF16 = 2 } awg_precision;
+ * cond(A^s_+), far beyond 8 mantissa bits on high-contrast problems);
+ * MIXED_FP16 stores W as float16 values times power-of-two row and column
+ * scales (W = S_r What S_c, every row of What with largest magnitude in
+ * [1/2, 1); 11 significant bits, 3 more than bfloat16) and the local
+ * operators in float32.  All keep the PCG recurrences, both coarse
+ * factorisations and solves and the GenEO selection test in float64, and
+ * assemble F from the same rounded W (so H_3 stays SPD). */
+typedef enum { AWG_FP64 = 0, AWG_MIXED_FP32 = 1, AWG_MIXED_BF16 = 2, AWG_MIXED_FP16 = 3 } awg_precision;
 
 typedef struct {
     int variant;            /* awg_variant, default AWG_H3_AD                  */

@@ -63,6 +63,8 @@ static void free_all(Handle* h) {
         dfree(h, P.W);
         dfree(h, P.Finv);
         dfree(h, P.inexInv);
+        dfree(h, P.rscale);
+        dfree(h, P.cscale);
     }
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     h->ev_pool.clear();
@@ -234,7 +236,7 @@ static int variant_stage(const Handle* h) { return 4 + h->opt.variant; }
 awg_status awg_apply(awg_handle hh, int precision, const double* d_r, double* d_z, int nrhs, int ld,
                      void* stream) {
     Handle* h = reinterpret_cast<Handle*>(hh);
-    if (!h || !d_r || !d_z || nrhs < 0 || ld < h->n || precision < 0 || precision > 2)
+    if (!h || !d_r || !d_z || nrhs < 0 || ld < h->n || precision < 0 || precision >= AWG_NPREC)
         return AWG_ERR_INVALID_ARG;
     if (!h->prec[precision].built) return AWG_ERR_STATE;
     for (int c = 0; c < nrhs; c++)
@@ -246,7 +248,7 @@ awg_status awg_apply(awg_handle hh, int precision, const double* d_r, double* d_
 awg_status awg_apply_stage(awg_handle hh, int which, int precision, const double* d_x, double* d_y,
                            void* stream) {
     Handle* h = reinterpret_cast<Handle*>(hh);
-    if (!h || !d_x || !d_y || which < 0 || which > 6 || precision < 0 || precision > 2)
+    if (!h || !d_x || !d_y || which < 0 || which > 6 || precision < 0 || precision >= AWG_NPREC)
         return AWG_ERR_INVALID_ARG;
     if (!h->prec[precision].built) return AWG_ERR_STATE;
     if (which == 6 && h->n_minus > 0 && !h->prec[precision].inexInv.p) return AWG_ERR_STATE;
@@ -256,7 +258,7 @@ awg_status awg_apply_stage(awg_handle hh, int which, int precision, const double
 awg_status awg_pcg(awg_handle hh, int precision, const double* d_b, double* d_x, int nrhs, int ld,
                    double rtol, int* h_iters, double* h_relres, void* stream) {
     Handle* h = reinterpret_cast<Handle*>(hh);
-    if (!h || !d_b || !d_x || nrhs < 0 || ld < h->n || !(rtol > 0.0) || precision < 0 || precision > 2)
+    if (!h || !d_b || !d_x || nrhs < 0 || ld < h->n || !(rtol > 0.0) || precision < 0 || precision >= AWG_NPREC)
         return AWG_ERR_INVALID_ARG;
     if (!h->prec[precision].built) return AWG_ERR_STATE;
     awg_status worst = AWG_OK;

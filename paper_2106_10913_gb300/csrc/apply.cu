@@ -253,6 +253,21 @@ template <> struct Vec<__nv_bfloat16> {
     }
 };
 
+template <> struct Vec<__half> {
+    static constexpr int V = 8;
+    using A = float;
+    __device__ __forceinline__ static void load(const __half* p, float* o) {
+        const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
+        const __half2* hv = reinterpret_cast<const __half2*>(&t);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float2 f = __half22float2(hv[k]);  // .x: element 2k
+            o[2 * k] = f.x;
+            o[2 * k + 1] = f.y;
+        }
+    }
+};
+
 // V consecutive values of a 16-byte aligned shared array, 16 bytes per load
 template <typename A, int V>
 __device__ __forceinline__ void lds_vec(const A* p, A* o) {
@@ -269,12 +284,14 @@ constexpr int WT_CW = 256;       // columns of W per block (blockIdx.y)
 
 // part[b*ldw + c] = sum over the rows of row block b of W(i, c) r(i), for the
 // 256 columns of column chunk blockIdx.y.  The block's r values are staged
-// once in shared memory in the compute type; the 8 warps take every 8th row
-// and the 8 partial sums meet in shared memory in a fixed order.
+// once in shared memory in the compute type (times the row scale of a scaled
+// float16 W); the 8 warps take every 8th row and the 8 partial sums meet in
+// shared memory in a fixed order.
 template <typename TS>
 __global__ void __launch_bounds__(WT_THREADS) k_wt_partial(int n, int ldw, int rows,
                                                            const TS* __restrict__ W,
                                                            const double* __restrict__ r,
+                                                           const float* __restrict__ rscale,
                                                            double* part) {
     using A = typename Vec<TS>::A;
     constexpr int V = Vec<TS>::V;
@@ -285,7 +302,10 @@ __global__ void __launch_bounds__(WT_THREADS) k_wt_partial(int n, int ldw, int r
     const int i0 = blockIdx.x * rows;
     const int nr = min(n, i0 + rows) - i0;
     const int c0 = blockIdx.y * WT_CW;
-    for (int t = threadIdx.x; t < nr; t += WT_THREADS) rs[t] = (A)r[i0 + t];
+    if (rscale)
+        for (int t = threadIdx.x; t < nr; t += WT_THREADS) rs[t] = (A)r[i0 + t] * rscale[i0 + t];
+    else
+        for (int t = threadIdx.x; t < nr; t += WT_THREADS) rs[t] = (A)r[i0 + t];
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     A acc[UNR][V];
@@ -322,8 +342,10 @@ __global__ void __launch_bounds__(WT_THREADS) k_wt_partial(int n, int ldw, int r
     }
 }
 
-// out[c] = sum over the row blocks of part[b*ldp + c]  (fixed order)
-__global__ void k_reduce_cols(int nb, int nm, int ldp, const double* __restrict__ part, double* out) {
+// out[c] = sum over the row blocks of part[b*ldp + c]  (fixed order), times
+// the column scale of a scaled float16 W
+__global__ void k_reduce_cols(int nb, int nm, int ldp, const double* __restrict__ part,
+                              const float* __restrict__ cscale, double* out) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nm) return;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
@@ -335,7 +357,8 @@ __global__ void k_reduce_cols(int nb, int nm, int ldp, const double* __restrict_
         a3 += part[(size_t)(b + 3) * ldp + c];
     }
     for (; b < nb; b++) a0 += part[(size_t)b * ldp + c];
-    out[c] = (a0 + a1) + (a2 + a3);
+    const double v = (a0 + a1) + (a2 + a3);
+    out[c] = cscale ? v * (double)cscale[c] : v;
 }
 
 template <typename A>
@@ -345,10 +368,12 @@ __device__ __forceinline__ A warp_sum_t(A v) {
     return v;
 }
 
-// d in the compute type of W's storage (one conversion per element per apply)
-__global__ void k_d_to_f32(int nm, int ldw, const double* __restrict__ d, float* d32) {
+// d in the compute type of W's storage (one conversion per element per
+// apply), times the column scale of a scaled float16 W
+__global__ void k_d_to_f32(int nm, int ldw, const double* __restrict__ d, const float* __restrict__ cscale,
+                           float* d32) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < ldw) d32[c] = (c < nm) ? (float)d[c] : 0.f;
+    if (c < ldw) d32[c] = (c < nm) ? (cscale ? (float)(d[c] * (double)cscale[c]) : (float)d[c]) : 0.f;
 }
 
 // z(i) = v(i) + sum_c W(i, c) d(c).  One warp per row (grid-stride, many
@@ -360,7 +385,8 @@ __global__ void k_d_to_f32(int nm, int ldw, const double* __restrict__ d, float*
 template <typename TS>
 __global__ void __launch_bounds__(256) k_w_d(int n, int ldw, const TS* __restrict__ W,
                                              const typename Vec<TS>::A* __restrict__ dA,
-                                             const double* v, double* z) {
+                                             const float* __restrict__ rscale, const double* v,
+                                             double* z) {
     using A = typename Vec<TS>::A;
     constexpr int V = Vec<TS>::V;
     extern __shared__ __align__(16) unsigned char wd_smem[];
@@ -392,8 +418,11 @@ __global__ void __launch_bounds__(256) k_w_d(int n, int ldw, const TS* __restric
 #pragma unroll
             for (int j = 0; j < V; j++) acc0 = fma(w0[j], d0[j], acc0);
         }
-        const A s = warp_sum_t<A>(acc0 + acc1);
-        if (lane == 0) z[i] = (v ? v[i] : 0.0) + (double)s;
+        A s = warp_sum_t<A>(acc0 + acc1);
+        if (lane == 0) {
+            if (rscale) s *= rscale[i];
+            z[i] = (v ? v[i] : 0.0) + (double)s;
+        }
     }
 }
 
@@ -590,10 +619,11 @@ static awg_status dense_gemv(Handle* h, int dim, const double* M, const double* 
 
 static awg_status hnn1(Handle* h, int prec, const double* x, double* y, Ws& w, cudaStream_t s) {
     dim3 g(h->N, (h->max_ns + LG_ROWS - 1) / LG_ROWS);
-    // the bfloat16 form keeps float32 local operators: the explicit local
-    // pseudo-inverses carry cond(A^s_+), which 8 mantissa bits cannot hold on
-    // high-contrast problems; only W (whose accuracy PCG tolerates) is bf16
-    const int gp = (prec == AWG_MIXED_BF16) ? AWG_MIXED_FP32 : prec;
+    // the bfloat16 and float16 forms keep float32 local operators: the
+    // explicit local pseudo-inverses carry cond(A^s_+), which 8 or 11
+    // significant bits cannot hold on high-contrast problems; only W (whose
+    // accuracy PCG tolerates) is rounded further
+    const int gp = (prec == AWG_MIXED_BF16 || prec == AWG_MIXED_FP16) ? AWG_MIXED_FP32 : prec;
     const PrecOps& P = h->prec[gp];
     if (gp == AWG_FP64) {
         {
@@ -652,8 +682,11 @@ static int wt_row_blocks(const Handle* h) {
 }
 
 template <typename TS>
-static awg_status wt_r_t(Handle* h, const void* W, const double* r, double* out, Ws& w,
+static awg_status wt_r_t(Handle* h, const PrecOps& P, const double* r, double* out, Ws& w,
                          cudaStream_t s) {
+    const void* W = P.W.p;
+    const float* rsc = (const float*)P.rscale.p;
+    const float* csc = (const float*)P.cscale.p;
     using A = typename Vec<TS>::A;
     const int rb = wt_row_blocks(h);
     const int rows = (h->n + rb - 1) / rb;
@@ -661,22 +694,23 @@ static awg_status wt_r_t(Handle* h, const void* W, const double* r, double* out,
     const size_t smem = (size_t)(8 * WT_CW + rows) * sizeof(A);
     {
         ProfScope ps_(h, AWG_PROF_WT, s);
-        k_wt_partial<TS><<<grid, WT_THREADS, smem, s>>>(h->n, h->ldw, rows, (const TS*)W, r, w.wpart);
+        k_wt_partial<TS><<<grid, WT_THREADS, smem, s>>>(h->n, h->ldw, rows, (const TS*)W, r, rsc, w.wpart);
     }
     AWG_LAUNCH();
     {
         ProfScope ps_(h, AWG_PROF_VECTOR, s);
-        k_reduce_cols<<<(h->n_minus + 255) / 256, 256, 0, s>>>(rb, h->n_minus, h->ldw, w.wpart, out);
+        k_reduce_cols<<<(h->n_minus + 255) / 256, 256, 0, s>>>(rb, h->n_minus, h->ldw, w.wpart, csc, out);
     }
     AWG_LAUNCH();
     return AWG_OK;
 }
 
 static awg_status wt_r(Handle* h, int prec, const double* r, double* out, Ws& w, cudaStream_t s) {
-    const void* W = h->prec[prec].W.p;
-    if (prec == AWG_FP64) return wt_r_t<double>(h, W, r, out, w, s);
-    if (prec == AWG_MIXED_FP32) return wt_r_t<float>(h, W, r, out, w, s);
-    return wt_r_t<__nv_bfloat16>(h, W, r, out, w, s);
+    const PrecOps& P = h->prec[prec];
+    if (prec == AWG_FP64) return wt_r_t<double>(h, P, r, out, w, s);
+    if (prec == AWG_MIXED_FP32) return wt_r_t<float>(h, P, r, out, w, s);
+    if (prec == AWG_MIXED_FP16) return wt_r_t<__half>(h, P, r, out, w, s);
+    return wt_r_t<__nv_bfloat16>(h, P, r, out, w, s);
 }
 
 // d zero-padded to ldw in the compute type of W's storage
@@ -687,7 +721,8 @@ __global__ void k_d_pad64(int nm, int ldw, const double* __restrict__ d, double*
 
 static awg_status w_d(Handle* h, int prec, const double* d, const double* v, double* z, Ws& w,
                       cudaStream_t s) {
-    const void* W = h->prec[prec].W.p;
+    const PrecOps& P = h->prec[prec];
+    const void* W = P.W.p;
     const int grid = std::max(1, std::min((h->n + 7) / 8, 152 * 16));  // 8 rows (warps) per block
     const int gd = (h->ldw + 255) / 256;
     if (prec == AWG_FP64) {
@@ -698,19 +733,22 @@ static awg_status w_d(Handle* h, int prec, const double* d, const double* v, dou
         }
         AWG_LAUNCH();
         ProfScope ps_(h, AWG_PROF_WD, s);
-        k_w_d<double><<<grid, 256, (size_t)h->ldw * 8, s>>>(h->n, h->ldw, (const double*)W, dp, v, z);
+        k_w_d<double><<<grid, 256, (size_t)h->ldw * 8, s>>>(h->n, h->ldw, (const double*)W, dp, nullptr, v, z);
     } else {
+        const float* rsc = (const float*)P.rscale.p;
         {
             ProfScope ps_(h, AWG_PROF_VECTOR, s);
-            k_d_to_f32<<<gd, 256, 0, s>>>(h->n_minus, h->ldw, d, w.d32);
+            k_d_to_f32<<<gd, 256, 0, s>>>(h->n_minus, h->ldw, d, (const float*)P.cscale.p, w.d32);
         }
         AWG_LAUNCH();
         ProfScope ps_(h, AWG_PROF_WD, s);
+        const size_t sm = (size_t)h->ldw * 4;
         if (prec == AWG_MIXED_FP32)
-            k_w_d<float><<<grid, 256, (size_t)h->ldw * 4, s>>>(h->n, h->ldw, (const float*)W, w.d32, v, z);
+            k_w_d<float><<<grid, 256, sm, s>>>(h->n, h->ldw, (const float*)W, w.d32, rsc, v, z);
+        else if (prec == AWG_MIXED_FP16)
+            k_w_d<__half><<<grid, 256, sm, s>>>(h->n, h->ldw, (const __half*)W, w.d32, rsc, v, z);
         else
-            k_w_d<__nv_bfloat16><<<grid, 256, (size_t)h->ldw * 4, s>>>(h->n, h->ldw,
-                                                                      (const __nv_bfloat16*)W, w.d32, v, z);
+            k_w_d<__nv_bfloat16><<<grid, 256, sm, s>>>(h->n, h->ldw, (const __nv_bfloat16*)W, w.d32, rsc, v, z);
     }
     AWG_LAUNCH();
     return AWG_OK;
@@ -727,18 +765,20 @@ awg_status set_smem_limits(Handle* h) {
         AWG_CUDA(cudaFuncSetAttribute(k_w_d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         AWG_CUDA(cudaFuncSetAttribute(k_w_d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         AWG_CUDA(cudaFuncSetAttribute(k_w_d<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        AWG_CUDA(cudaFuncSetAttribute(k_w_d<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     }
     // W^T r stages up to 8192 values of r plus 8 x 256 partial sums
     const int wt = (8 * WT_CW + 8192) * 8;
     AWG_CUDA(cudaFuncSetAttribute(k_wt_partial<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, wt));
     AWG_CUDA(cudaFuncSetAttribute(k_wt_partial<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, wt / 2));
     AWG_CUDA(cudaFuncSetAttribute(k_wt_partial<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, wt / 2));
+    AWG_CUDA(cudaFuncSetAttribute(k_wt_partial<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, wt / 2));
     return AWG_OK;
 }
 
 // One single-RHS apply of the selected stage (see awg_apply_stage).
 awg_status apply_stage(Handle* h, int which, int prec, const double* x, double* y, cudaStream_t s) {
-    if (prec < 0 || prec > 2 || !h->prec[prec].built) return AWG_ERR_INVALID_ARG;
+    if (prec < 0 || prec >= AWG_NPREC || !h->prec[prec].built) return AWG_ERR_INVALID_ARG;
     Ws w = ws_of(h);
     switch (which) {
         case 0: return spmv1(h, x, y, nullptr, s);

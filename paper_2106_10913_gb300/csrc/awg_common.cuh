@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -55,7 +56,10 @@ struct PrecOps {
     DevBuf W;         // second coarse basis, row-major n x ldw (float64/float32/bf16)
     DevBuf Finv;      // (W^T A W)^-1 for this W, float64 n_- x n_-
     DevBuf inexInv;   // (C^-1 - Vhat^T W)^-1 (H_3,inex), float64 n_- x n_-
+    DevBuf rscale;    // float16 W: power-of-two row scales, float32[n]
+    DevBuf cscale;    // float16 W: power-of-two column scales, float32[ldw] (0 on padding)
 };
+constexpr int AWG_NPREC = 4;
 
 struct Handle {
     int n = 0, nnz = 0, N = 0, overlap = 0;
@@ -106,7 +110,7 @@ struct Handle {
     DevBuf wcol_ptr;
     DevBuf Wcm;                          // W float64 column-major n x n_- (kept for checks)
     DevBuf F64;                          // W^T A W of the float64 W
-    PrecOps prec[3];
+    PrecOps prec[AWG_NPREC];
 
     // GenEO block solver (awg_options.geneo_solver): network parameters of
     // the learned start and per-setup iteration figures

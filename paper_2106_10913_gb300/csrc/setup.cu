@@ -202,6 +202,54 @@ __global__ void k_round_bf16(size_t len, const double* __restrict__ X, double* Y
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e < len) Y[e] = (double)__bfloat162float(__double2bfloat16(X[e]));
 }
+// ---- float16 W with power-of-two row and column scales: W = S_r What S_c
+// 2^e with |x| < 2^e <= 2|x| (1 for x = 0), within the normal float32 range;
+// built from the exponent bits, so the scaling itself is exact
+__device__ __forceinline__ float pow2_above(double x) {
+    if (!(x > 0.0)) return 1.f;
+    int e;
+    (void)frexp(x, &e);  // x = f 2^e, f in [1/2, 1)
+    e = max(-126, min(127, e));
+    return __int_as_float((e + 127) << 23);
+}
+__global__ void k_w16_cscale(int n, const double* __restrict__ W, float* cs) {
+    __shared__ double red[32];
+    const int j = blockIdx.x;
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(W[(size_t)j * n + i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t = fmax(t, red[w]);
+        cs[j] = pow2_above(t);
+    }
+}
+__global__ void k_w16_rscale(int n, int nm, const double* __restrict__ W, const float* __restrict__ cs,
+                             float* rs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double m = 0.0;
+    for (int j = 0; j < nm; j++) m = fmax(m, fabs(W[(size_t)j * n + i]) / (double)cs[j]);
+    rs[i] = pow2_above(m);
+}
+// float64 copy of the rounded W (column-major), for F
+__global__ void k_round_fp16(int n, size_t len, const double* __restrict__ X, const float* __restrict__ rs,
+                             const float* __restrict__ cs, double* Y) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= len) return;
+    const double sc = (double)rs[e % n] * (double)cs[e / n];
+    Y[e] = sc * (double)__half2float(__double2half(X[e] / sc));
+}
+__global__ void k_to_rowmajor_fp16(int n, int k, int ld, const double* __restrict__ X,
+                                   const float* __restrict__ rs, const float* __restrict__ cs, __half* Y) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * ld) return;
+    const int i = (int)(e / ld), c = (int)(e % ld);
+    Y[e] = __double2half((c < k) ? X[(size_t)c * n + i] / ((double)rs[i] * (double)cs[c]) : 0.0);
+}
+
 __global__ void k_conv_f32(size_t len, const double* __restrict__ X, float* Y) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e < len) Y[e] = (float)X[e];
@@ -723,7 +771,7 @@ awg_status build_setup_numeric(Handle* h) {
 
     // float32 local operators: used by the float32 and bfloat16 apply forms
     // (the bfloat16 form rounds only W) and by the W solve's preconditioner
-    if ((h->opt.precisions & 6) || h->opt.w_precision == AWG_MIXED_FP32) {
+    if ((h->opt.precisions & 14) || h->opt.w_precision == AWG_MIXED_FP32) {
         PrecOps& P = h->prec[AWG_MIXED_FP32];
         h->h_g32_off.assign(N + 1, 0);
         for (int t = 0; t < N; t++)
@@ -749,27 +797,45 @@ awg_status build_setup_numeric(Handle* h) {
         const unsigned gw = (unsigned)(((size_t)n * h->ldw + 255) / 256);
         k_to_rowmajor<double><<<gw, 256, 0, s>>>(n, nm, h->ldw, W64, (double*)P64.W.p);
         AWG_LAUNCH();
-        for (int p = 1; p <= 2; p++) {
+        for (int p = 1; p < AWG_NPREC; p++) {
             if (!(h->opt.precisions & (1 << p))) continue;
             PrecOps& P = h->prec[p];
             double* Wr = nullptr;
             AWG_CUDA(cudaMallocAsync(&Wr, (size_t)n * nm * 8, s));
             const size_t len = (size_t)n * nm;
-            if (p == AWG_MIXED_FP32) k_round_f32<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, W64, Wr);
-            else k_round_bf16<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, W64, Wr);
+            const unsigned gl = (unsigned)((len + 255) / 256);
+            if (p == AWG_MIXED_FP16) {
+                AWG_TRY(dalloc(h, P.rscale, (size_t)n * 4));
+                AWG_TRY(dalloc(h, P.cscale, (size_t)h->ldw * 4));
+                AWG_CUDA(cudaMemsetAsync(P.cscale.p, 0, (size_t)h->ldw * 4, s));
+                k_w16_cscale<<<nm, 256, 0, s>>>(n, W64, (float*)P.cscale.p);
+                AWG_LAUNCH();
+                k_w16_rscale<<<(n + 255) / 256, 256, 0, s>>>(n, nm, W64, (float*)P.cscale.p, (float*)P.rscale.p);
+                AWG_LAUNCH();
+                k_round_fp16<<<gl, 256, 0, s>>>(n, len, W64, (float*)P.rscale.p, (float*)P.cscale.p, Wr);
+            } else if (p == AWG_MIXED_FP32) {
+                k_round_f32<<<gl, 256, 0, s>>>(len, W64, Wr);
+            } else {
+                k_round_bf16<<<gl, 256, 0, s>>>(len, W64, Wr);
+            }
             AWG_LAUNCH();
             AWG_TRY(build_F(h, Wr, P.Finv, nullptr));
             if (inex) AWG_TRY(build_inex(h, Wr, P.inexInv));
             AWG_TRY(dalloc(h, P.W, (size_t)n * h->ldw * (p == AWG_MIXED_FP32 ? 4 : 2)));
-            if (p == AWG_MIXED_FP32) k_to_rowmajor<float><<<gw, 256, 0, s>>>(n, nm, h->ldw, Wr, (float*)P.W.p);
-            else k_to_rowmajor<__nv_bfloat16><<<gw, 256, 0, s>>>(n, nm, h->ldw, Wr, (__nv_bfloat16*)P.W.p);
+            if (p == AWG_MIXED_FP32)
+                k_to_rowmajor<float><<<gw, 256, 0, s>>>(n, nm, h->ldw, Wr, (float*)P.W.p);
+            else if (p == AWG_MIXED_FP16)  // from the float64 W: the scaled values round once
+                k_to_rowmajor_fp16<<<gw, 256, 0, s>>>(n, nm, h->ldw, W64, (float*)P.rscale.p,
+                                                     (float*)P.cscale.p, (__half*)P.W.p);
+            else
+                k_to_rowmajor<__nv_bfloat16><<<gw, 256, 0, s>>>(n, nm, h->ldw, Wr, (__nv_bfloat16*)P.W.p);
             AWG_LAUNCH();
             AWG_CUDA(cudaFreeAsync(Wr, s));
         }
         AWG_CUDA(cudaStreamSynchronize(s));
         h->setup_ms[6] = now_ms() - t5;
     }
-    for (int p = 1; p <= 2; p++)
+    for (int p = 1; p < AWG_NPREC; p++)
         if (h->opt.precisions & (1 << p)) h->prec[p].built = true;
     AWG_CUDA(cudaStreamSynchronize(s));
     return AWG_OK;

@@ -44,7 +44,7 @@ def _pair(name):
         from paper_2106_10913_gb300 import AWGSolver
         p = CASES[name]
         sol = AWGSolver(p.rowptr, p.colidx, p.val, p.part, p.nparts, p.overlap, p.tau,
-                        precisions=0b011)
+                        precisions=0b1111)
         st = O.setup_problem(p, dense=p.n <= 6000)
         _SOLVERS[name] = (p, sol, st)
     return _SOLVERS[name]
@@ -114,6 +114,39 @@ def test_mixed_fp32_apply(pair):
     x = np.random.default_rng(5).standard_normal(p.n)
     y = sol.apply(torch.from_numpy(x).cuda(), precision=MIXED_FP32).cpu().numpy()
     assert _rel(y, O.H3_ad_apply(st, x)) <= MIXED_RTOL
+
+
+# Apply error of the forms that round W below float32, against the float64
+# oracle.  The rounded W spans a slightly different second coarse space, so
+# the error is that of the storage unit roundoff u (float16 2^-11, bfloat16
+# 2^-8) amplified by the coarse problem; the bounds are 64 u.
+REDUCED_RTOL = {"fp16": 64 * 2.0 ** -11, "bf16": 64 * 2.0 ** -8}
+
+
+@pytest.mark.parametrize("form", ["fp16", "bf16"])
+def test_reduced_w_apply_error(pair, form, capsys):
+    p, sol, st = pair
+    from paper_2106_10913_gb300 import MIXED_BF16, MIXED_FP16
+    prec = {"fp16": MIXED_FP16, "bf16": MIXED_BF16}[form]
+    x = np.random.default_rng(5).standard_normal(p.n)
+    y = sol.apply(torch.from_numpy(x).cuda(), precision=prec).cpu().numpy()
+    err = _rel(y, O.H3_ad_apply(st, x))
+    with capsys.disabled():
+        print(f" [{form} W apply error {err:.2e}]", end="")
+    assert err <= REDUCED_RTOL[form]
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp16", "bf16"])
+def test_reduced_forms_converge(pair, form):
+    """Every reduced form still reaches the 1e-8 true relative residual."""
+    p, sol, st = pair
+    from paper_2106_10913_gb300 import MIXED_BF16, MIXED_FP16, MIXED_FP32
+    prec = {"fp32": MIXED_FP32, "fp16": MIXED_FP16, "bf16": MIXED_BF16}[form]
+    b = p.b if p.b.ndim == 1 else p.b[0]
+    x, its, rel, status = sol.pcg(torch.from_numpy(b).cuda(), rtol=1e-8, precision=prec)
+    assert status == 0 and rel[0] <= 1e-8
+    xs = x.cpu().numpy()
+    assert np.linalg.norm(st.A @ xs - b) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-12)
 
 
 def test_pcg_parity(pair):
