@@ -209,8 +209,10 @@ def run_awg(args):
 
     forms = {}
     timed_mask = (1 << 2) | (1 << 3) | (1 << 1) | (1 << 0)  # wt, wd, local, spmv
-    for name, prec in (("fp64", FP64), ("mixed_fp32", MIXED_FP32), ("mixed_bf16", MIXED_BF16),
-                       ("mixed_fp16", MIXED_FP16)):
+    all_forms = {"fp64": FP64, "mixed_fp32": MIXED_FP32, "mixed_bf16": MIXED_BF16,
+                 "mixed_fp16": MIXED_FP16}
+    for name in args.forms.split(","):
+        prec = all_forms[name]
         for _ in range(args.warmup):
             awg_pcg(sol.h, b, x, RTOL, prec, check=False)
         barrier()
@@ -242,7 +244,7 @@ def run_awg(args):
                        "ok": ok, "prof": prof, "clocks": clk.summary()}
 
     best = max((f for f in forms.values() if f["ok"]), key=lambda f: f["value"],
-               default=forms["fp64"])
+               default=next(iter(forms.values())))
     best_name = [k for k, v in forms.items() if v is best][0]
     wbytes = {FP64: 8, MIXED_FP32: 4, MIXED_BF16: 2, MIXED_FP16: 2}[best["prec"]]
     gbytes = 8 if best["prec"] == FP64 else 4
@@ -382,6 +384,8 @@ def main():
     ap.add_argument("--config", default="config2")
     ap.add_argument("--verbose", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forms", default="fp64,mixed_fp32,mixed_bf16,mixed_fp16",
+                    help="comma-separated storage forms to time")
     ap.add_argument("--geneo", default="learned", choices=["learned", "block", "dense"],
                     help="GenEO eigensolver of the setup: block solver from the learned start "
                          "(network trained on the device on smaller instances), from a random "

@@ -74,8 +74,9 @@ typedef enum { AWG_H3_AD = 0, AWG_H3_HYB = 1, AWG_H3_INEX = 2 } awg_variant;
  * cond(A^s_+), far beyond 8 mantissa bits on high-contrast problems);
  * MIXED_FP16 stores W as float16 values times power-of-two row and column
  * scales (W = S_r What S_c, every row of What with largest magnitude in
- * [1/2, 1); 11 significant bits, 3 more than bfloat16) and the local
- * operators in float32.  All keep the PCG recurrences, both coarse
+ * [1/2, 1); 11 significant bits, 3 more than bfloat16) plus a sparse
+ * float32 correction of its largest entries (awg_options.w16_keep), and the
+ * local operators in float32.  All keep the PCG recurrences, both coarse
  * factorisations and solves and the GenEO selection test in float64, and
  * assemble F from the same rounded W (so H_3 stays SPD). */
 typedef enum { AWG_FP64 = 0, AWG_MIXED_FP32 = 1, AWG_MIXED_BF16 = 2, AWG_MIXED_FP16 = 3 } awg_precision;
@@ -112,6 +113,17 @@ typedef struct {
     int geneo_maxit;        /* step cap of solvers 1-2; default 60             */
     const double* learned_params; /* host float64[AWG_LEARNED_NPARAM], read
                                during awg_setup only (solver 2)                */
+    int autotune;           /* 1 (default): at the end of setup, time the apply
+                               of every built form over a few grid sizes of the
+                               two W passes (they run beside the H_2 chain on
+                               a second stream) and keep the fastest; 0: fixed
+                               defaults                                         */
+    double w16_keep;        /* MIXED_FP16: entries with |W_ij| >= w16_keep *
+                               max_i |W_ij| also keep a float32 correction of
+                               their float16 rounding (a sparse term added in
+                               both W passes; the largest ~1 % of W carry most
+                               of each column, so this restores nearly the
+                               float32 iteration count); 0 disables; 0.1       */
 } awg_options;
 
 /* Per-handle figures reported after setup (cf. Table 1 of the paper). */
@@ -132,6 +144,8 @@ typedef struct {
     int64_t geneo_its_sum;  /* block solver: steps summed over subdomains       */
     int geneo_dense;        /* subdomains whose pencil went through the dense
                                eigensolver (all of them with geneo_solver 0)    */
+    int wt_blocks[4];       /* per awg_precision form: blocks of the W^T r and  */
+    int wd_blocks[4];       /* W d passes (autotuned; 0 if the form is unbuilt) */
 } awg_info;
 
 /* Fill *opt with the defaults above. */
@@ -249,6 +263,18 @@ enum {
  */
 awg_status awg_profile(awg_handle h, int enable);
 awg_status awg_profile_read(awg_handle h, int64_t* h_launches, double* h_ms, int64_t* h_count);
+
+/*
+ * Trace of the launches timed since awg_profile started (call before
+ * awg_profile_read, which clears them): for up to `cap` launches in the
+ * order they were issued, the kernel class (h_class, int32), and the start
+ * and end (h_t0, h_t1, ms) relative to the first timed launch's start, on
+ * the device clock shared by all streams; launches on the side stream
+ * overlap those on the main stream where the GPU ran them concurrently.
+ * Returns the number of launches written in *h_count.  Synchronises.
+ */
+awg_status awg_profile_trace(awg_handle h, int cap, int* h_class, double* h_t0, double* h_t1,
+                             int* h_count);
 
 /* Capacity, in float64 values, of the static scratch of awg_apply_hnn_noalloc. */
 #define AWG_NOALLOC_MAX_LOCAL (1 << 20)

@@ -42,7 +42,8 @@ class awg_options(ctypes.Structure):
                 ("w_maxit", ctypes.c_int), ("maxit", ctypes.c_int), ("verbose", ctypes.c_int),
                 ("w_precision", ctypes.c_int), ("geneo_solver", ctypes.c_int),
                 ("geneo_block", ctypes.c_int), ("geneo_maxit", ctypes.c_int),
-                ("learned_params", ctypes.c_void_p)]
+                ("learned_params", ctypes.c_void_p), ("autotune", ctypes.c_int),
+                ("w16_keep", ctypes.c_double)]
 
 
 class awg_info(ctypes.Structure):
@@ -52,13 +53,14 @@ class awg_info(ctypes.Structure):
                 ("w_iters", ctypes.c_int), ("w_relres", ctypes.c_double),
                 ("setup_ms", ctypes.c_double * 8), ("device_bytes", ctypes.c_size_t),
                 ("geneo_its_max", ctypes.c_int), ("geneo_its_sum", ctypes.c_int64),
-                ("geneo_dense", ctypes.c_int)]
+                ("geneo_dense", ctypes.c_int), ("wt_blocks", ctypes.c_int * 4),
+                ("wd_blocks", ctypes.c_int * 4)]
 
 
 EXPORTED = ["awg_default_options", "awg_status_string", "awg_setup", "awg_destroy",
             "awg_get_info", "awg_apply", "awg_apply_stage", "awg_pcg", "awg_get_array",
             "awg_profile", "awg_profile_read", "awg_apply_hnn_noalloc", "awg_learned_data",
-            "awg_learned_forward", "awg_learned_grad", "awg_learned_train"]
+            "awg_learned_forward", "awg_learned_grad", "awg_learned_train", "awg_profile_trace"]
 LEARNED_NPARAM, LEARNED_NFEAT = 385, 5
 GENEO_DENSE, GENEO_BLOCK, GENEO_LEARNED = 0, 1, 2
 PROF_NAMES = ["spmv", "local", "wt", "wd", "coarse", "subdomain", "prolong", "vector"]
@@ -100,6 +102,8 @@ def load_library(path: str = LIB_PATH):
     lib.awg_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D),
                                      ctypes.POINTER(ctypes.c_int64)]
     lib.awg_profile_read.restype = I
+    lib.awg_profile_trace.argtypes = [P, I, P, P, P, ctypes.POINTER(I)]
+    lib.awg_profile_trace.restype = I
     lib.awg_apply_hnn_noalloc.argtypes = [P, I, P, P, P]
     lib.awg_apply_hnn_noalloc.restype = I
     lib.awg_learned_data.argtypes = [P, P, P, P]
@@ -166,6 +170,8 @@ def awg_get_info(h) -> dict:
     _check(load_library().awg_get_info(h, ctypes.byref(info)), "awg_get_info")
     d = {k: getattr(info, k) for k, _ in awg_info._fields_}
     d["setup_ms"] = list(info.setup_ms)
+    d["wt_blocks"] = list(info.wt_blocks)
+    d["wd_blocks"] = list(info.wd_blocks)
     return d
 
 
@@ -263,6 +269,19 @@ def awg_profile_read(h) -> dict:
     return {"launches": launches.value,
             "ms": {k: ms[i] for i, k in enumerate(PROF_NAMES)},
             "count": {k: cnt[i] for i, k in enumerate(PROF_NAMES)}}
+
+
+def awg_profile_trace(h, cap: int = 65536):
+    """(class names, start ms, end ms) of the launches timed so far, on the
+    device clock shared by all streams."""
+    cls = np.zeros(cap, dtype=np.int32)
+    t0 = np.zeros(cap)
+    t1 = np.zeros(cap)
+    cnt = ctypes.c_int()
+    _check(load_library().awg_profile_trace(h, cap, cls.ctypes.data, t0.ctypes.data, t1.ctypes.data,
+                                            ctypes.byref(cnt)), "awg_profile_trace")
+    k = cnt.value
+    return [PROF_NAMES[c] for c in cls[:k]], t0[:k], t1[:k]
 
 
 # ------------------------------------------------------------- convenience class

@@ -65,14 +65,19 @@ static void free_all(Handle* h) {
         dfree(h, P.inexInv);
         dfree(h, P.rscale);
         dfree(h, P.cscale);
+        for (DevBuf* b : {&P.corr_rowptr, &P.corr_col, &P.corr_val, &P.corr_colptr, &P.corr_row, &P.corr_cval})
+            dfree(h, *b);
     }
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     h->ev_pool.clear();
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->side) cudaStreamDestroy(h->side);
-    h->ev_fork = h->ev_join = nullptr;
-    h->side = nullptr;
+    if (h->hp) cudaStreamDestroy(h->hp);
+    h->ev_fork = h->ev_join = h->ev_in = h->ev_out = nullptr;
+    h->side = h->hp = nullptr;
     if (h->h_flag) cudaFreeHost(h->h_flag);
     if (h->h_scal) cudaFreeHost(h->h_scal);
     h->h_flag = nullptr;
@@ -105,6 +110,8 @@ void awg_default_options(awg_options* opt) {
     opt->geneo_block = 8;
     opt->geneo_maxit = 60;
     opt->learned_params = nullptr;
+    opt->autotune = 1;
+    opt->w16_keep = 0.1;
 }
 
 const char* awg_status_string(awg_status s) {
@@ -130,9 +137,14 @@ static awg_status setup_impl(Handle* h, const int* d_rowptr, const int* d_colidx
     const double t0 = now_ms();
     AWG_CUDA(cudaMallocHost(&h->h_flag, sizeof(int)));
     AWG_CUDA(cudaMallocHost(&h->h_scal, 16 * sizeof(double)));
-    AWG_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    int prio_least = 0, prio_greatest = 0;
+    AWG_CUDA(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+    AWG_CUDA(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_least));
+    AWG_CUDA(cudaStreamCreateWithPriority(&h->hp, cudaStreamNonBlocking, prio_greatest));
     AWG_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     AWG_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    AWG_CUDA(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    AWG_CUDA(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
     AWG_TRY(dalloc(h, h->flag, sizeof(int)));
     AWG_TRY(dalloc(h, h->rowptr, (size_t)(h->n + 1) * sizeof(int)));
     AWG_TRY(dalloc(h, h->colidx, (size_t)h->nnz * sizeof(int)));
@@ -177,7 +189,8 @@ awg_status awg_setup(int n, int nnz, const int* d_rowptr, const int* d_colidx, c
     if (o.variant < 0 || o.variant > 2 || !(o.zero_rtol >= 0.0) || !(o.w_rtol > 0.0) ||
         o.w_maxit < 1 || o.maxit < 1 || (o.w_precision != AWG_FP64 && o.w_precision != AWG_MIXED_FP32) ||
         o.geneo_solver < 0 || o.geneo_solver > 2 || o.geneo_block < 2 || o.geneo_block > 16 ||
-        o.geneo_maxit < 1 || (o.geneo_solver == 2 && !o.learned_params))
+        o.geneo_maxit < 1 || (o.geneo_solver == 2 && !o.learned_params) || !(o.w16_keep >= 0.0) ||
+        o.w16_keep > 1.0)
         return AWG_ERR_INVALID_ARG;
     o.precisions |= 1 << AWG_FP64;
     Handle* h = new (std::nothrow) Handle();
@@ -228,6 +241,10 @@ awg_status awg_get_info(awg_handle hh, awg_info* info) {
     info->geneo_its_max = h->geneo_its_max;
     info->geneo_its_sum = h->geneo_its_sum;
     info->geneo_dense = h->geneo_dense;
+    for (int p = 0; p < 4; p++) {
+        info->wt_blocks[p] = h->prec[p].built ? h->prec[p].wt_blocks : 0;
+        info->wd_blocks[p] = h->prec[p].built ? h->prec[p].wd_blocks : 0;
+    }
     return AWG_OK;
 }
 
@@ -239,10 +256,15 @@ awg_status awg_apply(awg_handle hh, int precision, const double* d_r, double* d_
     if (!h || !d_r || !d_z || nrhs < 0 || ld < h->n || precision < 0 || precision >= AWG_NPREC)
         return AWG_ERR_INVALID_ARG;
     if (!h->prec[precision].built) return AWG_ERR_STATE;
-    for (int c = 0; c < nrhs; c++)
-        AWG_TRY(apply_stage(h, variant_stage(h), precision, d_r + (size_t)c * ld, d_z + (size_t)c * ld,
-                            (cudaStream_t)stream));
-    return AWG_OK;
+    cudaStream_t us = (cudaStream_t)stream;
+    AWG_CUDA(cudaEventRecord(h->ev_in, us));
+    AWG_CUDA(cudaStreamWaitEvent(h->hp, h->ev_in, 0));
+    awg_status st = AWG_OK;
+    for (int c = 0; c < nrhs && st == AWG_OK; c++)
+        st = apply_stage(h, variant_stage(h), precision, d_r + (size_t)c * ld, d_z + (size_t)c * ld, h->hp);
+    AWG_CUDA(cudaEventRecord(h->ev_out, h->hp));
+    AWG_CUDA(cudaStreamWaitEvent(us, h->ev_out, 0));
+    return st;
 }
 
 awg_status awg_apply_stage(awg_handle hh, int which, int precision, const double* d_x, double* d_y,
@@ -262,16 +284,21 @@ awg_status awg_pcg(awg_handle hh, int precision, const double* d_b, double* d_x,
         return AWG_ERR_INVALID_ARG;
     if (!h->prec[precision].built) return AWG_ERR_STATE;
     awg_status worst = AWG_OK;
+    cudaStream_t us = (cudaStream_t)stream;
+    AWG_CUDA(cudaEventRecord(h->ev_in, us));
+    AWG_CUDA(cudaStreamWaitEvent(h->hp, h->ev_in, 0));
     for (int c = 0; c < nrhs; c++) {
         int it = 0;
         double rr = 0.0;
         awg_status st = pcg1(h, precision, variant_stage(h), d_b + (size_t)c * ld, d_x + (size_t)c * ld,
-                             rtol, &it, &rr, (cudaStream_t)stream);
+                             rtol, &it, &rr, h->hp);
         if (h_iters) h_iters[c] = it;
         if (h_relres) h_relres[c] = rr;
         if (st != AWG_OK && (worst == AWG_OK || st == AWG_ERR_CUDA)) worst = st;
         if (st == AWG_ERR_CUDA) break;
     }
+    AWG_CUDA(cudaEventRecord(h->ev_out, h->hp));
+    AWG_CUDA(cudaStreamWaitEvent(us, h->ev_out, 0));
     return worst;
 }
 
@@ -340,6 +367,24 @@ awg_status awg_profile(awg_handle hh, int enable) {
         for (int i = 0; i < AWG_NPROF; i++) { h->prof_ms[i] = 0.0; h->prof_cnt[i] = 0; }
     }
     h->prof = enable;
+    return AWG_OK;
+}
+
+awg_status awg_profile_trace(awg_handle hh, int cap, int* h_class, double* h_t0, double* h_t1,
+                             int* h_count) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || cap < 0 || !h_count || (cap > 0 && (!h_class || !h_t0 || !h_t1))) return AWG_ERR_INVALID_ARG;
+    const int k = (int)std::min<size_t>((size_t)cap, h->ev_kernel.size());
+    for (int i = 0; i < k; i++) {
+        AWG_CUDA(cudaEventSynchronize(h->ev_pool[2 * i + 1]));
+        float a = 0.f, b = 0.f;
+        AWG_CUDA(cudaEventElapsedTime(&a, h->ev_pool[0], h->ev_pool[2 * i]));
+        AWG_CUDA(cudaEventElapsedTime(&b, h->ev_pool[0], h->ev_pool[2 * i + 1]));
+        h_class[i] = h->ev_kernel[i];
+        h_t0[i] = a;
+        h_t1[i] = b;
+    }
+    *h_count = k;
     return AWG_OK;
 }
 

@@ -25,13 +25,37 @@ template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v
     return __bfloat162float(v);
 }
 
+// Finish of a grid-wide sum in one launch: every block stores its block sum
+// v in part[blockIdx.x]; the last block to arrive (ticket counter) adds the
+// partials in block order, exactly as a separate one-block kernel would, writes
+// *out and resets the counter.  The result does not depend on scheduling.
+__device__ __forceinline__ void grid_sum_finish(double v, double* part, unsigned* counter, double* out,
+                                                double* red) {
+    __shared__ unsigned ticket;
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = v;
+        __threadfence();
+        ticket = atomicAdd(counter, 1u);
+    }
+    __syncthreads();
+    if (ticket != gridDim.x - 1) return;
+    __threadfence();
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) acc += __ldcg(part + b);
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) {
+        *out = acc;
+        *counter = 0u;
+    }
+}
+
 // ------------------------------------------------------------------ SpMV
-// y = A x; if pdot, also writes per-block partials of x^T y (fixed order).
+// y = A x; if pdot, also the sum x^T y into *dot (grid_sum_finish).
 __global__ void __launch_bounds__(256) k_spmv(int n, const int* __restrict__ rp,
                                               const int* __restrict__ ci,
                                               const double* __restrict__ a,
                                               const double* __restrict__ x, double* __restrict__ y,
-                                              double* pdot) {
+                                              double* pdot, unsigned* counter, double* dot) {
     __shared__ double red[32];
     double part = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -43,56 +67,196 @@ __global__ void __launch_bounds__(256) k_spmv(int n, const int* __restrict__ rp,
     }
     if (pdot) {
         part = block_sum(part, red);
-        if (threadIdx.x == 0) pdot[blockIdx.x] = part;
+        grid_sum_finish(part, pdot, counter, dot, red);
     }
 }
 
 // -------------------------------------------------------- block-sparse ops
-// c[colptr[s] + j] = sum_p B_s(p, j) x(idx_s(p)),  B_s column-major n^s x cols
-__global__ void __launch_bounds__(256) k_blk_tgemv(const int* __restrict__ sub_ptr,
-                                                   const int* __restrict__ sub_idx,
-                                                   const int* __restrict__ colptr,
-                                                   const int64_t* __restrict__ boff,
-                                                   const double* __restrict__ B,
-                                                   const double* __restrict__ x, double* c) {
-    extern __shared__ double xs[];
+// c[colptr[s] + j] = wsign w_j sum_p B_s(p, j) x(idx_s(p))  (w optional):
+// every thread takes rows p = t, t + blockDim, ... and keeps one accumulator
+// per column (all loads independent and coalesced along p), then the
+// per-warp sums meet in shared memory in a fixed order.
+constexpr int TG_MAXC = 16;
+__global__ void __launch_bounds__(256) k_blk_tgemv2(const int* __restrict__ sub_ptr,
+                                                    const int* __restrict__ sub_idx,
+                                                    const int* __restrict__ colptr,
+                                                    const int64_t* __restrict__ boff,
+                                                    const double* __restrict__ B,
+                                                    const double* __restrict__ x,
+                                                    const double* __restrict__ w, double wsign,
+                                                    double* c) {
+    __shared__ double red[8][TG_MAXC];
     const int s = blockIdx.x;
     const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
     const int c0 = colptr[s], nc = colptr[s + 1] - c0;
-    if (nc == 0) return;
-    for (int p = threadIdx.x; p < m; p += blockDim.x) xs[p] = x[sub_idx[p0 + p]];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double* Bs = B + boff[s];
-    for (int j = wid; j < nc; j += nw) {
-        const double* col = Bs + (size_t)j * m;
-        double acc = 0.0;
-        for (int p = lane; p < m; p += 32) acc = fma(col[p], xs[p], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) c[c0 + j] = acc;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int cb = 0; cb < nc; cb += TG_MAXC) {
+        const int k = min(TG_MAXC, nc - cb);
+        double acc[TG_MAXC];
+#pragma unroll
+        for (int j = 0; j < TG_MAXC; j++) acc[j] = 0.0;
+        for (int q = threadIdx.x; q < m; q += blockDim.x) {
+            const double xv = x[sub_idx[p0 + q]];
+            const double* col = Bs + (size_t)cb * m + q;
+#pragma unroll
+            for (int j = 0; j < TG_MAXC; j++)
+                if (j < k) acc[j] = fma(col[(size_t)j * m], xv, acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < TG_MAXC; j++) {
+            if (j >= k) break;
+            const double v = warp_sum(acc[j]);
+            if (lane == 0) red[wid][j] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < k) {
+            double v = 0.0;
+#pragma unroll
+            for (int q = 0; q < 8; q++) v += red[q][threadIdx.x];
+            const int cj = c0 + cb + threadIdx.x;
+            c[cj] = w ? wsign * w[cj] * v : v;
+        }
+        __syncthreads();
     }
 }
 
-// loc[sub_ptr[s] + p] = sum_j B_s(p, j) w_j c_j   (w optional)
-__global__ void __launch_bounds__(256) k_blk_gemv(const int* __restrict__ sub_ptr,
-                                                  const int* __restrict__ colptr,
-                                                  const int64_t* __restrict__ boff,
-                                                  const double* __restrict__ B,
-                                                  const double* __restrict__ c,
-                                                  const double* __restrict__ w, double wsign,
-                                                  double* loc) {
-    extern __shared__ double cs[];
-    const int s = blockIdx.x;
+// Same product with the rows of a subdomain split over blockIdx.y (256 rows
+// per block, one per thread, so every load of a block is in flight at once):
+// block (s, y) leaves its column sums in part[(s * gridDim.y + y) * TG_MAXC],
+// and the last block of subdomain s to finish (ticket counter cnt[s]) adds
+// them in block order and resets the counter.  At most TG_MAXC columns per
+// subdomain.
+__global__ void __launch_bounds__(256) k_blk_tgemv3(const int* __restrict__ sub_ptr,
+                                                    const int* __restrict__ sub_idx,
+                                                    const int* __restrict__ colptr,
+                                                    const int64_t* __restrict__ boff,
+                                                    const double* __restrict__ B,
+                                                    const double* __restrict__ x,
+                                                    const double* __restrict__ w, double wsign,
+                                                    double* part, unsigned* cnt, double* c) {
+    __shared__ double red[8][TG_MAXC];
+    __shared__ unsigned ticket;
+    const int s = blockIdx.x, yb = blockIdx.y;
     const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
+    const int nsplit = (m + 255) >> 8;
+    if (yb >= nsplit) return;
     const int c0 = colptr[s], nc = colptr[s + 1] - c0;
-    for (int j = threadIdx.x; j < nc; j += blockDim.x) cs[j] = w ? wsign * w[c0 + j] * c[c0 + j] : c[c0 + j];
-    __syncthreads();
-    const double* Bs = B + boff[s];
-    for (int p = threadIdx.x; p < m; p += blockDim.x) {
-        double acc = 0.0;
-        for (int j = 0; j < nc; j++) acc = fma(Bs[p + (size_t)j * m], cs[j], acc);
-        loc[p0 + p] = acc;
+    if (nc == 0) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int q = (yb << 8) + threadIdx.x;
+    double acc[TG_MAXC];
+    if (q < m) {
+        const double xv = x[sub_idx[p0 + q]];
+        const double* col = B + boff[s] + q;
+        double bv[TG_MAXC];
+#pragma unroll
+        for (int j = 0; j < TG_MAXC; j++) bv[j] = (j < nc) ? col[(size_t)j * m] : 0.0;
+#pragma unroll
+        for (int j = 0; j < TG_MAXC; j++) acc[j] = bv[j] * xv;
+    } else {
+#pragma unroll
+        for (int j = 0; j < TG_MAXC; j++) acc[j] = 0.0;
     }
+#pragma unroll
+    for (int j = 0; j < TG_MAXC; j++) {
+        if (j >= nc) break;
+        const double v = warp_sum(acc[j]);
+        if (lane == 0) red[wid][j] = v;
+    }
+    __syncthreads();
+    double* ps = part + (size_t)s * gridDim.y * TG_MAXC;
+    if (threadIdx.x < nc) {
+        double v = 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; k++) v += red[k][threadIdx.x];
+        ps[yb * TG_MAXC + threadIdx.x] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) ticket = atomicAdd(cnt + s, 1u);
+    __syncthreads();
+    if (ticket != (unsigned)(nsplit - 1)) return;
+    __threadfence();
+    if (threadIdx.x < nc) {
+        double v = 0.0;
+        for (int k = 0; k < nsplit; k++) v += __ldcg(ps + k * TG_MAXC + threadIdx.x);
+        const int cj = c0 + threadIdx.x;
+        c[cj] = w ? wsign * w[cj] * v : v;
+    }
+    if (threadIdx.x == 0) cnt[s] = 0u;
+}
+
+// y(i) = beta y(i) + alpha sum over the copies (s, p) of i of
+// sum_j B_s(p, j) c[colptr[s] + j] + gamma z(i): block-sparse GEMV and
+// prolongation in one owner-computes pass (copies in subdomain order)
+__global__ void k_blk_prolong(int n, const int* __restrict__ inc_ptr, const int* __restrict__ inc_pos,
+                              const int* __restrict__ inc_sub, const int* __restrict__ sub_ptr,
+                              const int* __restrict__ colptr, const int64_t* __restrict__ boff,
+                              const double* __restrict__ B, const double* __restrict__ c, double* y,
+                              double alpha, double beta, const double* z, double gamma,
+                              const double* __restrict__ z2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = 0.0;
+    for (int e = inc_ptr[i]; e < inc_ptr[i + 1]; e++) {
+        const int s = inc_sub[e];
+        const int ps = sub_ptr[s], m = sub_ptr[s + 1] - ps;
+        const int c0 = colptr[s], nc = colptr[s + 1] - c0;
+        const double* b = B + boff[s] + (inc_pos[e] - ps);
+        int j = 0;
+        for (; j + 8 <= nc; j += 8) {  // eight loads in flight, then the FMAs
+            double bv[8], cv[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) { bv[k] = b[(size_t)(j + k) * m]; cv[k] = c[c0 + j + k]; }
+#pragma unroll
+            for (int k = 0; k < 8; k++) acc = fma(bv[k], cv[k], acc);
+        }
+        for (; j < nc; j++) acc = fma(b[(size_t)j * m], c[c0 + j], acc);
+    }
+    double v = alpha * acc;
+    if (beta != 0.0) v = fma(beta, y[i], v);
+    if (z) v = fma(gamma, z[i], v);
+    if (z2) v += z2[i];
+    y[i] = v;
+}
+
+__global__ void k_add(int n, const double* __restrict__ a, double* y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] += a[i];
+}
+
+// y(i) = yin(i) + sign (A x + A_- x)(i), with cm = |Lambda_-| V_-^T R x per
+// subdomain from k_blk_tgemv2: one row of A and the copies of i in one pass
+__global__ void k_aplus_row(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                            const double* __restrict__ a, const double* __restrict__ x,
+                            const int* __restrict__ inc_ptr, const int* __restrict__ inc_pos,
+                            const int* __restrict__ inc_sub, const int* __restrict__ sub_ptr,
+                            const int* __restrict__ colptr, const int64_t* __restrict__ boff,
+                            const double* __restrict__ V, const double* __restrict__ cm,
+                            const double* yin, double sign, double* y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; k++) acc = fma(a[k], x[ci[k]], acc);
+    if (cm) {
+        for (int e = inc_ptr[i]; e < inc_ptr[i + 1]; e++) {
+            const int s = inc_sub[e];
+            const int ps = sub_ptr[s], m = sub_ptr[s + 1] - ps;
+            const int c0 = colptr[s], nc = colptr[s + 1] - c0;
+            const double* b = V + boff[s] + (inc_pos[e] - ps);
+            int j = 0;
+            for (; j + 8 <= nc; j += 8) {
+                double bv[8], cv[8];
+#pragma unroll
+                for (int k = 0; k < 8; k++) { bv[k] = b[(size_t)(j + k) * m]; cv[k] = cm[c0 + j + k]; }
+#pragma unroll
+                for (int k = 0; k < 8; k++) acc = fma(bv[k], cv[k], acc);
+            }
+            for (; j < nc; j++) acc = fma(b[(size_t)j * m], cm[c0 + j], acc);
+        }
+    }
+    y[i] = yin ? fma(sign, acc, yin[i]) : sign * acc;
 }
 
 // y = beta y + alpha sum_copies loc + gamma z
@@ -292,7 +456,7 @@ __global__ void __launch_bounds__(WT_THREADS) k_wt_partial(int n, int ldw, int r
                                                            const TS* __restrict__ W,
                                                            const double* __restrict__ r,
                                                            const float* __restrict__ rscale,
-                                                           double* part) {
+                                                           double* part, float* rf) {
     using A = typename Vec<TS>::A;
     constexpr int V = Vec<TS>::V;
     constexpr int UNR = WT_CW / (32 * V);
@@ -302,9 +466,11 @@ __global__ void __launch_bounds__(WT_THREADS) k_wt_partial(int n, int ldw, int r
     const int i0 = blockIdx.x * rows;
     const int nr = min(n, i0 + rows) - i0;
     const int c0 = blockIdx.y * WT_CW;
-    if (rscale)
+    if (rscale) {
         for (int t = threadIdx.x; t < nr; t += WT_THREADS) rs[t] = (A)r[i0 + t] * rscale[i0 + t];
-    else
+        if (rf && blockIdx.y == 0)  // S_r r in float32 for the sparse correction
+            for (int t = threadIdx.x; t < nr; t += WT_THREADS) rf[i0 + t] = (float)rs[t];
+    } else
         for (int t = threadIdx.x; t < nr; t += WT_THREADS) rs[t] = (A)r[i0 + t];
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -313,8 +479,32 @@ __global__ void __launch_bounds__(WT_THREADS) k_wt_partial(int n, int ldw, int r
     for (int u = 0; u < UNR; u++)
 #pragma unroll
         for (int j = 0; j < V; j++) acc[u][j] = 0;
-#pragma unroll 2
-    for (int i = wid; i < nr; i += 8) {
+    // four rows per step: their loads are issued before the first FMA
+    int i = wid;
+    for (; i + 24 < nr; i += 32) {
+        A wv[4][UNR][V];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const TS* row = W + (size_t)(i0 + i + 8 * k) * ldw;
+#pragma unroll
+            for (int u = 0; u < UNR; u++) {
+                const int c = c0 + (u * 32 + lane) * V;
+                if (c < ldw) Vec<TS>::load(row + c, wv[k][u]);
+                else
+#pragma unroll
+                    for (int j = 0; j < V; j++) wv[k][u][j] = 0;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const A ri = rs[i + 8 * k];
+#pragma unroll
+            for (int u = 0; u < UNR; u++)
+#pragma unroll
+                for (int j = 0; j < V; j++) acc[u][j] = fma(wv[k][u][j], ri, acc[u][j]);
+        }
+    }
+    for (; i < nr; i += 8) {
         const A ri = rs[i];
         const TS* row = W + (size_t)(i0 + i) * ldw;
 #pragma unroll
@@ -361,6 +551,25 @@ __global__ void k_reduce_cols(int nb, int nm, int ldp, const double* __restrict_
     out[c] = cscale ? v * (double)cscale[c] : v;
 }
 
+// out[c] = cscale[c] (sum of the partials + sum_i C_ic (S_r r)_i): the
+// float16 form's column sums plus its sparse correction (CSC, one block per
+// column; fixed order)
+__global__ void __launch_bounds__(256) k_reduce_cols_corr(int nb, int ldp, const double* __restrict__ part,
+                                                          const float* __restrict__ cscale,
+                                                          const int* __restrict__ ccp,
+                                                          const int* __restrict__ crow,
+                                                          const float* __restrict__ cval,
+                                                          const float* __restrict__ rf, double* out) {
+    __shared__ double red[32];
+    const int c = blockIdx.x;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += part[(size_t)b * ldp + c];
+    float fc = 0.f;
+    for (int k = ccp[c] + threadIdx.x; k < ccp[c + 1]; k += blockDim.x) fc = fmaf(cval[k], rf[crow[k]], fc);
+    acc = block_sum(acc + (double)fc, red);
+    if (threadIdx.x == 0) out[c] = acc * (double)cscale[c];
+}
+
 template <typename A>
 __device__ __forceinline__ A warp_sum_t(A v) {
 #pragma unroll
@@ -385,8 +594,9 @@ __global__ void k_d_to_f32(int nm, int ldw, const double* __restrict__ d, const 
 template <typename TS>
 __global__ void __launch_bounds__(256) k_w_d(int n, int ldw, const TS* __restrict__ W,
                                              const typename Vec<TS>::A* __restrict__ dA,
-                                             const float* __restrict__ rscale, const double* v,
-                                             double* z) {
+                                             const float* __restrict__ rscale, const int* __restrict__ crp,
+                                             const int* __restrict__ ccol, const float* __restrict__ cval,
+                                             const double* v, double* z) {
     using A = typename Vec<TS>::A;
     constexpr int V = Vec<TS>::V;
     extern __shared__ __align__(16) unsigned char wd_smem[];
@@ -397,28 +607,33 @@ __global__ void __launch_bounds__(256) k_w_d(int n, int ldw, const TS* __restric
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
         const TS* row = W + (size_t)i * ldw;
-        A acc0 = 0, acc1 = 0;
+        // four 16-byte loads in flight per lane: a grid of a few blocks per
+        // SM still covers the memory latency (the pass shares the GPU with
+        // the H_2 chain)
+        A acc[4] = {0, 0, 0, 0};
         int c = lane * V;
-        for (; c + 32 * V < ldw; c += 64 * V) {
-            A w0[V], w1[V], d0[V], d1[V];
-            Vec<TS>::load(row + c, w0);
-            Vec<TS>::load(row + c + 32 * V, w1);
-            lds_vec<A, V>(ds + c, d0);
-            lds_vec<A, V>(ds + c + 32 * V, d1);
+        for (; c + 96 * V < ldw; c += 128 * V) {
+            A wv[4][V];
 #pragma unroll
-            for (int j = 0; j < V; j++) {
-                acc0 = fma(w0[j], d0[j], acc0);
-                acc1 = fma(w1[j], d1[j], acc1);
+            for (int u = 0; u < 4; u++) Vec<TS>::load(row + c + u * 32 * V, wv[u]);
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                A dv[V];
+                lds_vec<A, V>(ds + c + u * 32 * V, dv);
+#pragma unroll
+                for (int j = 0; j < V; j++) acc[u] = fma(wv[u][j], dv[j], acc[u]);
             }
         }
-        if (c < ldw) {
+        for (; c < ldw; c += 32 * V) {
             A w0[V], d0[V];
             Vec<TS>::load(row + c, w0);
             lds_vec<A, V>(ds + c, d0);
 #pragma unroll
-            for (int j = 0; j < V; j++) acc0 = fma(w0[j], d0[j], acc0);
+            for (int j = 0; j < V; j++) acc[0] = fma(w0[j], d0[j], acc[0]);
         }
-        A s = warp_sum_t<A>(acc0 + acc1);
+        if (crp)  // sparse correction of the row (scaled units, d staged scaled)
+            for (int k = crp[i] + lane; k < crp[i + 1]; k += 32) acc[1] = fma((A)cval[k], ds[ccol[k]], acc[1]);
+        A s = warp_sum_t<A>((acc[0] + acc[1]) + (acc[2] + acc[3]));
         if (lane == 0) {
             if (rscale) s *= rscale[i];
             z[i] = (v ? v[i] : 0.0) + (double)s;
@@ -432,30 +647,23 @@ __global__ void k_sub(int n, const double* a, const double* b, double* c) {
     if (i < n) c[i] = a[i] - b[i];
 }
 
-__global__ void k_dot_partial(int n, const double* __restrict__ x, const double* __restrict__ y,
-                              double* part) {
+// *out = x^T y
+__global__ void k_dot(int n, const double* __restrict__ x, const double* __restrict__ y, double* part,
+                      unsigned* counter, double* out) {
     __shared__ double red[32];
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         acc = fma(x[i], y[i], acc);
     acc = block_sum(acc, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    grid_sum_finish(acc, part, counter, out, red);
 }
 
-__global__ void k_final_sum(int nb, const double* __restrict__ part, double* out) {
-    __shared__ double red[32];
-    double acc = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += part[b];
-    acc = block_sum(acc, red);
-    if (threadIdx.x == 0) *out = acc;
-}
+// PCG scalars (device): 0 rz, 1 pq, 2 rr, 3 rz_new, 5 b.b, 6 true residual
+enum { S_RZ = 0, S_PQ = 1, S_RR = 2, S_RZN = 3, S_BB = 5, S_TR = 6 };
 
-// PCG scalars (device): 0 rz, 1 pq, 2 rr, 3 rz_new, 4 beta
-enum { S_RZ = 0, S_PQ = 1, S_RR = 2, S_RZN = 3, S_BETA = 4, S_BB = 5, S_TR = 6 };
-
-// x += alpha p, r -= alpha q with alpha = rz / pq; partials of r.r
-__global__ void k_pcg_xr(int n, const double* __restrict__ scal, const double* __restrict__ p,
-                         const double* __restrict__ q, double* x, double* r, double* part) {
+// x += alpha p, r -= alpha q with alpha = rz / pq; scal[S_RR] = r.r
+__global__ void k_pcg_xr(int n, double* scal, const double* __restrict__ p, const double* __restrict__ q,
+                         double* x, double* r, double* part, unsigned* counter) {
     __shared__ double red[32];
     const double pq = scal[S_PQ];
     const double alpha = (pq > 0.0) ? scal[S_RZ] / pq : 0.0;
@@ -467,26 +675,37 @@ __global__ void k_pcg_xr(int n, const double* __restrict__ scal, const double* _
         acc = fma(ri, ri, acc);
     }
     acc = block_sum(acc, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    grid_sum_finish(acc, part, counter, scal + S_RR, red);
 }
 
-__global__ void k_pcg_beta(double* scal) {
+// p = z + beta p with beta = rz_new / rz; the last block then moves rz_new
+// into rz (every block has read both by then)
+__global__ void k_pcg_p(int n, double* scal, const double* __restrict__ z, double* p, unsigned* counter) {
+    __shared__ unsigned ticket;
     const double rz = scal[S_RZ], rzn = scal[S_RZN];
-    scal[S_BETA] = (rz != 0.0) ? rzn / rz : 0.0;
-    scal[S_RZ] = rzn;
-}
-
-__global__ void k_pcg_p(int n, const double* __restrict__ scal, const double* __restrict__ z,
-                        double* p) {
-    const double beta = scal[S_BETA];
+    const double beta = (rz != 0.0) ? rzn / rz : 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         p[i] = fma(beta, p[i], z[i]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        ticket = atomicAdd(counter, 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && ticket == gridDim.x - 1) {
+        scal[S_RZ] = rzn;
+        *counter = 0u;
+    }
 }
 
 // ===================================================================== host
 struct Ws {
     double *y0, *y2, *c1, *c2, *w0, *w1, *dd, *x1, *t, *u, *q, *loc, *loc2, *cm, *part, *wpart, *tmp, *tmp2;
+    unsigned* cnt;    // ticket counters of the one-launch grid sums (zero between launches)
+    double* tgpart;   // k_blk_tgemv3 partial column sums, N x splits x TG_MAXC
+    unsigned* tgcnt;  // k_blk_tgemv3 ticket counter per subdomain (zero between launches)
     float *xf, *d32;  // float32 gathered local vector, float32 copy of d
+    float* rf;        // S_r r in float32 (sparse correction of the float16 W)
     double* dpad;     // d zero-padded to ldw (float64 W)
 };
 
@@ -502,9 +721,13 @@ static size_t carve(const Handle* h, double* base, Ws* w) {
     t.loc = take(h->sum_ns); t.loc2 = take(h->sum_ns);
     t.cm = take(std::max(1, h->n_minus_all));
     t.part = take(4096);
+    t.cnt = reinterpret_cast<unsigned*>(t.part + 4064);
+    t.tgpart = take((size_t)h->N * ((h->max_ns + 255) / 256) * TG_MAXC);
+    t.tgcnt = reinterpret_cast<unsigned*>(take(((size_t)h->N + 1) / 2));
     t.wpart = take((size_t)h->red_blocks * std::max(8, h->ldw));
     t.xf = reinterpret_cast<float*>(take((h->sum_ns + 1) / 2 + 4));
     t.d32 = reinterpret_cast<float*>(take((std::max(8, h->ldw) + 1) / 2 + 4));
+    t.rf = reinterpret_cast<float*>(take((n + 1) / 2 + 4));
     t.dpad = take(std::max(8, h->ldw));
     if (w) *w = t;
     return (size_t)(p - base) * sizeof(double);
@@ -521,10 +744,13 @@ size_t ws_bytes(const Handle* h) { return carve(h, nullptr, nullptr); }
 static int grid_n(int n) { return std::min((n + 255) / 256, 152 * 8); }
 
 awg_status spmv1(Handle* h, const double* x, double* y, double* pdot, cudaStream_t s) {
+    // pdot: x^T y into *pdot (scratch and ticket counter in the workspace)
+    Ws w = ws_of(h);
     {
         ProfScope ps_(h, AWG_PROF_SPMV, s);
         k_spmv<<<grid_n(h->n), 256, 0, s>>>(h->n, (int*)h->rowptr.p, (int*)h->colidx.p,
-                                            (double*)h->val.p, x, y, pdot);
+                                            (double*)h->val.p, x, y, pdot ? w.part : nullptr,
+                                            w.cnt, pdot);
     }
     AWG_LAUNCH();
     return AWG_OK;
@@ -541,68 +767,66 @@ static awg_status prolong1(Handle* h, const double* loc, double* y, double alpha
     return AWG_OK;
 }
 
-// y = A_- x, or y = yin + sign * A_- x
-static awg_status aminus1(Handle* h, const double* x, double* y, const double* yin, double sign,
-                          Ws& w, cudaStream_t s) {
-    if (h->n_minus_all == 0) {
-        if (yin) { if (yin != y) AWG_CUDA(cudaMemcpyAsync(y, yin, h->n * 8, cudaMemcpyDeviceToDevice, s)); }
-        else AWG_CUDA(cudaMemsetAsync(y, 0, h->n * 8, s));
-        return AWG_OK;
-    }
-    const size_t sm = (size_t)h->max_ns * 8;
-    {
-        ProfScope ps_(h, AWG_PROF_SUBDOMAIN, s);
-        k_blk_tgemv<<<h->N, 256, sm, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p, (int*)h->nm_ptr.p,
-                                          (int64_t*)h->vm_off.p, (double*)h->Vm.p, x, w.cm);
-    }
-    AWG_LAUNCH();
-    {
-        ProfScope ps_(h, AWG_PROF_SUBDOMAIN, s);
-        k_blk_gemv<<<h->N, 256, (size_t)std::max(1, *std::max_element(h->h_nm.begin(), h->h_nm.end())) * 8, s>>>(
-            (int*)h->sub_ptr.p, (int*)h->nm_ptr.p, (int64_t*)h->vm_off.p, (double*)h->Vm.p, w.cm,
-            (double*)h->lam_m.p, -1.0, w.loc2);
-    }
-    AWG_LAUNCH();
-    return prolong1(h, w.loc2, y, sign, 0.0, yin, 1.0, s);
-}
-
-// y = yin + sign * A_+ x
-static awg_status aplus1(Handle* h, const double* x, double* y, const double* yin, double sign,
-                         Ws& w, cudaStream_t s) {
-    AWG_TRY(spmv1(h, x, w.tmp2, nullptr, s));
-    // tmp2 = A x ; y = yin + sign*(A x + A_- x)
-    if (yin) {
-        {
-            ProfScope ps_(h, AWG_PROF_VECTOR, s);
-            k_sub<<<(h->n + 255) / 256, 256, 0, s>>>(h->n, yin, w.tmp2, w.tmp2);
-        }  // yin - A x
-        AWG_LAUNCH();
-        if (sign != -1.0) return AWG_ERR_INVALID_ARG;
-        return aminus1(h, x, y, w.tmp2, -1.0, w, s);
-    }
-    return aminus1(h, x, y, w.tmp2, sign, w, s);
-}
-
-static awg_status zt1(Handle* h, const double* x, double* c, cudaStream_t s) {
-    if (h->n0 == 0) return AWG_OK;
-    {
-        ProfScope ps_(h, AWG_PROF_SUBDOMAIN, s);
-        k_blk_tgemv<<<h->N, 256, (size_t)h->max_ns * 8, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p,
-                                                            (int*)h->mode_ptr.p, (int64_t*)h->z_off.p,
-                                                            (double*)h->Z.p, x, c);
+// cm = |Lambda_-| V_-^T R x per subdomain (the middle of A_- x, Thm. 2)
+// c_s = wsign w .* (B_s^T x|Omega^s) for every subdomain: the split-row
+// kernel when every block has at most TG_MAXC columns, else one block per
+// subdomain
+static awg_status blk_tgemv(Handle* h, const int* colptr, const int64_t* boff, const double* B,
+                            int maxc, const double* x, const double* wv, double wsign, double* c,
+                            cudaStream_t s) {
+    ProfScope ps_(h, AWG_PROF_SUBDOMAIN, s);
+    if (maxc <= TG_MAXC) {
+        Ws w = ws_of(h);
+        const dim3 g(h->N, (h->max_ns + 255) / 256);
+        k_blk_tgemv3<<<g, 256, 0, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p, colptr, boff, B, x, wv, wsign,
+                                       w.tgpart, w.tgcnt, c);
+    } else {
+        k_blk_tgemv2<<<h->N, 256, 0, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p, colptr, boff, B, x, wv,
+                                          wsign, c);
     }
     AWG_LAUNCH();
     return AWG_OK;
 }
 
-// loc = Z c (local slabs)
-static awg_status zloc1(Handle* h, const double* c, double* loc, cudaStream_t s) {
-    const int mx = std::max(1, *std::max_element(h->h_modes.begin(), h->h_modes.end()));
+static awg_status vmt1(Handle* h, const double* x, double* cm, cudaStream_t s) {
+    const int maxc = *std::max_element(h->h_nm.begin(), h->h_nm.end());
+    return blk_tgemv(h, (int*)h->nm_ptr.p, (int64_t*)h->vm_off.p, (double*)h->Vm.p, maxc, x,
+                     (double*)h->lam_m.p, -1.0, cm, s);
+}
+
+// y = yin + sign * A_+ x  (A_+ = A + A_-, Thm. 2)
+static awg_status aplus1(Handle* h, const double* x, double* y, const double* yin, double sign,
+                         Ws& w, cudaStream_t s) {
+    const bool vm = h->n_minus_all > 0;
+    if (vm) AWG_TRY(vmt1(h, x, w.cm, s));
     {
-        ProfScope ps_(h, AWG_PROF_SUBDOMAIN, s);
-        k_blk_gemv<<<h->N, 256, (size_t)mx * 8, s>>>((int*)h->sub_ptr.p, (int*)h->mode_ptr.p,
-                                                     (int64_t*)h->z_off.p, (double*)h->Z.p, c,
-                                                     nullptr, 1.0, loc);
+        ProfScope ps_(h, AWG_PROF_SPMV, s);
+        k_aplus_row<<<(h->n + 255) / 256, 256, 0, s>>>(
+            h->n, (int*)h->rowptr.p, (int*)h->colidx.p, (double*)h->val.p, x, (int*)h->inc_ptr.p,
+            (int*)h->inc_pos.p, (int*)h->inc_sub.p, (int*)h->sub_ptr.p, (int*)h->nm_ptr.p,
+            (int64_t*)h->vm_off.p, (double*)h->Vm.p, vm ? w.cm : nullptr, yin, sign, y);
+    }
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
+// c = Z^T x (block-sparse, Thm. 4)
+static awg_status zt1(Handle* h, const double* x, double* c, cudaStream_t s) {
+    if (h->n0 == 0) return AWG_OK;
+    const int maxc = *std::max_element(h->h_modes.begin(), h->h_modes.end());
+    return blk_tgemv(h, (int*)h->mode_ptr.p, (int64_t*)h->z_off.p, (double*)h->Z.p, maxc, x, nullptr, 1.0,
+                     c, s);
+}
+
+// y = beta y + alpha Z c + gamma v (+ v2)
+static awg_status zc1(Handle* h, const double* c, double* y, double alpha, double beta, const double* v,
+                      double gamma, cudaStream_t s, const double* v2 = nullptr) {
+    {
+        ProfScope ps_(h, AWG_PROF_PROLONG, s);
+        k_blk_prolong<<<(h->n + 255) / 256, 256, 0, s>>>(h->n, (int*)h->inc_ptr.p, (int*)h->inc_pos.p,
+                                                         (int*)h->inc_sub.p, (int*)h->sub_ptr.p,
+                                                         (int*)h->mode_ptr.p, (int64_t*)h->z_off.p,
+                                                         (double*)h->Z.p, c, y, alpha, beta, v, gamma, v2);
     }
     AWG_LAUNCH();
     return AWG_OK;
@@ -656,26 +880,37 @@ static awg_status coarse_e(Handle* h, const double* x, double* y0, double* c, cu
 }
 
 // H_2 x = Pi H^NN Pi^T x + Z E^-1 Z^T x  (Thm. 4)
-static awg_status h2_1(Handle* h, int prec, const double* r, double* z, Ws& w, cudaStream_t s) {
-    if (h->n0 == 0) return hnn1(h, prec, r, z, w, s);
+// z = H_2 r (+ add, once the event `wait` has completed)
+static awg_status h2_1(Handle* h, int prec, const double* r, double* z, Ws& w, cudaStream_t s,
+                       const double* add = nullptr, cudaEvent_t wait = nullptr) {
+    if (h->n0 == 0) {
+        AWG_TRY(hnn1(h, prec, r, z, w, s));
+        if (add) {
+            if (wait) AWG_CUDA(cudaStreamWaitEvent(s, wait, 0));
+            ProfScope ps_(h, AWG_PROF_VECTOR, s);
+            k_add<<<(h->n + 255) / 256, 256, 0, s>>>(h->n, add, z);
+            AWG_LAUNCH();
+        }
+        return AWG_OK;
+    }
     AWG_TRY(coarse_e(h, r, w.y0, w.c1, s));                 // c1 = E^-1 Z^T r
-    AWG_TRY(zloc1(h, w.c1, w.loc, s));
-    AWG_TRY(prolong1(h, w.loc, w.x1, 1.0, 0.0, nullptr, 0.0, s));  // x1 = Z c1
+    AWG_TRY(zc1(h, w.c1, w.x1, 1.0, 0.0, nullptr, 0.0, s));  // x1 = Z c1
     AWG_TRY(aplus1(h, w.x1, w.t, r, -1.0, w, s));           // t = r - A_+ x1
     AWG_TRY(hnn1(h, prec, w.t, w.u, w, s));                 // u = H^NN t
     AWG_TRY(aplus1(h, w.u, w.q, nullptr, 1.0, w, s));        // q = A_+ u
     AWG_TRY(zt1(h, w.q, w.y2, s));
     AWG_TRY(dense_gemv(h, h->n0, (double*)h->Einv.p, w.y2, w.c2, 1.0, w.c1, -1.0, s));  // c2 = E^-1 y2 - c1
-    AWG_TRY(zloc1(h, w.c2, w.loc, s));
-    return prolong1(h, w.loc, z, -1.0, 0.0, w.u, 1.0, s);   // z = u - Z (c2 - c1)
+    if (wait) AWG_CUDA(cudaStreamWaitEvent(s, wait, 0));
+    return zc1(h, w.c2, z, -1.0, 0.0, w.u, 1.0, s, add);    // z = u - Z (c2 - c1) (+ add)
 }
 
-// Row blocks of the W^T r pass: about 8 blocks per SM in total over the
-// 256-column chunks, at most 8192 rows per block (its r values sit in
-// shared memory), never more blocks than the partial buffer holds.
-static int wt_row_blocks(const Handle* h) {
+// Row blocks of the W^T r pass: about 3 blocks per SM in total over the
+// 256-column chunks (the pass shares the GPU with the H_2 chain), at most
+// 8192 rows per block (its r values sit in shared memory), never more blocks
+// than the partial buffer holds.
+static int wt_row_blocks(const Handle* h, const PrecOps& P) {
     const int chunks = (h->ldw + WT_CW - 1) / WT_CW;
-    int rb = std::max(1, 152 * 8 / std::max(1, chunks));
+    int rb = std::max(1, (P.wt_blocks > 0 ? P.wt_blocks : 152 * 3) / std::max(1, chunks));
     rb = std::max(rb, (h->n + 8191) / 8192);
     rb = std::min(rb, std::max(1, (h->n + 31) / 32));
     return std::min(rb, h->red_blocks);
@@ -688,18 +923,23 @@ static awg_status wt_r_t(Handle* h, const PrecOps& P, const double* r, double* o
     const float* rsc = (const float*)P.rscale.p;
     const float* csc = (const float*)P.cscale.p;
     using A = typename Vec<TS>::A;
-    const int rb = wt_row_blocks(h);
+    const int rb = wt_row_blocks(h, P);
     const int rows = (h->n + rb - 1) / rb;
     const dim3 grid(rb, (h->ldw + WT_CW - 1) / WT_CW);
     const size_t smem = (size_t)(8 * WT_CW + rows) * sizeof(A);
     {
         ProfScope ps_(h, AWG_PROF_WT, s);
-        k_wt_partial<TS><<<grid, WT_THREADS, smem, s>>>(h->n, h->ldw, rows, (const TS*)W, r, rsc, w.wpart);
+        k_wt_partial<TS><<<grid, WT_THREADS, smem, s>>>(h->n, h->ldw, rows, (const TS*)W, r, rsc, w.wpart,
+                                                        P.corr_nnz > 0 ? w.rf : nullptr);
     }
     AWG_LAUNCH();
     {
         ProfScope ps_(h, AWG_PROF_VECTOR, s);
-        k_reduce_cols<<<(h->n_minus + 255) / 256, 256, 0, s>>>(rb, h->n_minus, h->ldw, w.wpart, csc, out);
+        if (P.corr_nnz > 0)
+            k_reduce_cols_corr<<<h->n_minus, 256, 0, s>>>(rb, h->ldw, w.wpart, csc, (int*)P.corr_colptr.p,
+                                                          (int*)P.corr_row.p, (float*)P.corr_cval.p, w.rf, out);
+        else
+            k_reduce_cols<<<(h->n_minus + 255) / 256, 256, 0, s>>>(rb, h->n_minus, h->ldw, w.wpart, csc, out);
     }
     AWG_LAUNCH();
     return AWG_OK;
@@ -723,7 +963,9 @@ static awg_status w_d(Handle* h, int prec, const double* d, const double* v, dou
                       cudaStream_t s) {
     const PrecOps& P = h->prec[prec];
     const void* W = P.W.p;
-    const int grid = std::max(1, std::min((h->n + 7) / 8, 152 * 16));  // 8 rows (warps) per block
+    // 8 rows (warps) per block, grid-stride; the pass runs after H_2 has
+    // issued its bandwidth-heavy part, so it takes the whole GPU
+    const int grid = std::max(1, std::min((h->n + 7) / 8, P.wd_blocks > 0 ? P.wd_blocks : 152 * 16));
     const int gd = (h->ldw + 255) / 256;
     if (prec == AWG_FP64) {
         double* dp = w.dpad;
@@ -733,7 +975,8 @@ static awg_status w_d(Handle* h, int prec, const double* d, const double* v, dou
         }
         AWG_LAUNCH();
         ProfScope ps_(h, AWG_PROF_WD, s);
-        k_w_d<double><<<grid, 256, (size_t)h->ldw * 8, s>>>(h->n, h->ldw, (const double*)W, dp, nullptr, v, z);
+        k_w_d<double><<<grid, 256, (size_t)h->ldw * 8, s>>>(h->n, h->ldw, (const double*)W, dp, nullptr, nullptr,
+                                                            nullptr, nullptr, v, z);
     } else {
         const float* rsc = (const float*)P.rscale.p;
         {
@@ -743,12 +986,17 @@ static awg_status w_d(Handle* h, int prec, const double* d, const double* v, dou
         AWG_LAUNCH();
         ProfScope ps_(h, AWG_PROF_WD, s);
         const size_t sm = (size_t)h->ldw * 4;
+        const bool cor = P.corr_nnz > 0;
+        const int* crp = cor ? (const int*)P.corr_rowptr.p : nullptr;
+        const int* ccol = cor ? (const int*)P.corr_col.p : nullptr;
+        const float* cval = cor ? (const float*)P.corr_val.p : nullptr;
         if (prec == AWG_MIXED_FP32)
-            k_w_d<float><<<grid, 256, sm, s>>>(h->n, h->ldw, (const float*)W, w.d32, rsc, v, z);
+            k_w_d<float><<<grid, 256, sm, s>>>(h->n, h->ldw, (const float*)W, w.d32, rsc, crp, ccol, cval, v, z);
         else if (prec == AWG_MIXED_FP16)
-            k_w_d<__half><<<grid, 256, sm, s>>>(h->n, h->ldw, (const __half*)W, w.d32, rsc, v, z);
+            k_w_d<__half><<<grid, 256, sm, s>>>(h->n, h->ldw, (const __half*)W, w.d32, rsc, crp, ccol, cval, v, z);
         else
-            k_w_d<__nv_bfloat16><<<grid, 256, sm, s>>>(h->n, h->ldw, (const __nv_bfloat16*)W, w.d32, rsc, v, z);
+            k_w_d<__nv_bfloat16><<<grid, 256, sm, s>>>(h->n, h->ldw, (const __nv_bfloat16*)W, w.d32, rsc, crp,
+                                                       ccol, cval, v, z);
     }
     AWG_LAUNCH();
     return AWG_OK;
@@ -758,8 +1006,6 @@ awg_status set_smem_limits(Handle* h) {
     const int mx = (int)std::max<size_t>((size_t)h->max_ns * 8, (size_t)std::max(1, h->ldw) * 8);
     if (mx > 48 * 1024) {
         if (mx > 227 * 1024) return AWG_ERR_INVALID_ARG;
-        AWG_CUDA(cudaFuncSetAttribute(k_blk_tgemv, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-        AWG_CUDA(cudaFuncSetAttribute(k_blk_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         AWG_CUDA(cudaFuncSetAttribute(k_local_gemv64, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         AWG_CUDA(cudaFuncSetAttribute(k_local_gemv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         AWG_CUDA(cudaFuncSetAttribute(k_w_d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
@@ -787,16 +1033,16 @@ awg_status apply_stage(Handle* h, int which, int prec, const double* x, double* 
         case 3: return h2_1(h, prec, x, y, w, s);
         case 4: {  // H_3,ad = H_2 + W F^-1 W^T  (Def. 10)
             if (h->n_minus == 0) return h2_1(h, prec, x, y, w, s);
-            // d = F^-1 W^T x on the side stream while H_2 x runs on s
+            // W F^-1 W^T x on the side stream while H_2 x runs on s; the two
+            // meet in the last kernel of H_2
             AWG_CUDA(cudaEventRecord(h->ev_fork, s));
             AWG_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
             AWG_TRY(wt_r(h, prec, x, w.w0, w, h->side));
             AWG_TRY(dense_gemv(h, h->n_minus, (double*)h->prec[prec].Finv.p, w.w0, w.dd, 1.0, nullptr, 0,
                                h->side));
+            AWG_TRY(w_d(h, prec, w.dd, nullptr, w.tmp2, w, h->side));
             AWG_CUDA(cudaEventRecord(h->ev_join, h->side));
-            AWG_TRY(h2_1(h, prec, x, w.tmp, w, s));
-            AWG_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
-            return w_d(h, prec, w.dd, w.tmp, y, w, s);
+            return h2_1(h, prec, x, y, w, s, w.tmp2, h->ev_join);
         }
         case 5: {  // H_3,hyb = Pi_3 H_2 Pi_3^T + W F^-1 W^T  (Def. 10)
             if (h->n_minus == 0) return h2_1(h, prec, x, y, w, s);
@@ -823,28 +1069,94 @@ awg_status apply_stage(Handle* h, int which, int prec, const double* x, double* 
             AWG_TRY(wt_r(h, prec, x, w.w0, w, h->side));
             AWG_TRY(dense_gemv(h, h->n_minus, (double*)h->prec[prec].inexInv.p, w.w0, w.dd, 1.0, nullptr,
                                0, h->side));
+            AWG_TRY(w_d(h, prec, w.dd, nullptr, w.tmp2, w, h->side));
             AWG_CUDA(cudaEventRecord(h->ev_join, h->side));
-            AWG_TRY(h2_1(h, prec, x, w.tmp, w, s));
-            AWG_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
-            return w_d(h, prec, w.dd, w.tmp, y, w, s);
+            return h2_1(h, prec, x, y, w, s, w.tmp2, h->ev_join);
         }
         default: return AWG_ERR_INVALID_ARG;
     }
 }
 
+// ------------------------------------------------------------- autotuner
+__global__ void k_fill_unit(int n, double* x) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t v = (uint32_t)i * 0x9e3779b1u + 0x7f4a7c15u;
+    v ^= v >> 15; v *= 0x2c1b3c6du; v ^= v >> 12; v *= 0x297a2d39u; v ^= v >> 15;
+    x[i] = (double)(v & 0xffffff) / 16777216.0 - 0.5;
+}
+
+awg_status autotune_apply(Handle* h) {
+    if (h->n_minus == 0) return AWG_OK;
+    cudaStream_t s = h->hp;
+    double *x = nullptr, *y = nullptr;
+    AWG_CUDA(cudaMallocAsync(&x, (size_t)h->n * 8, s));
+    AWG_CUDA(cudaMallocAsync(&y, (size_t)h->n * 8, s));
+    k_fill_unit<<<(h->n + 255) / 256, 256, 0, s>>>(h->n, x);
+    AWG_LAUNCH();
+    cudaEvent_t e0, e1;
+    AWG_CUDA(cudaEventCreate(&e0));
+    AWG_CUDA(cudaEventCreate(&e1));
+    const int stage = 4 + h->opt.variant;
+    auto timed = [&](int p, float* ms) -> awg_status {
+        AWG_TRY(apply_stage(h, stage, p, x, y, s));
+        AWG_CUDA(cudaEventRecord(e0, s));
+        for (int k = 0; k < 3; k++) AWG_TRY(apply_stage(h, stage, p, x, y, s));
+        AWG_CUDA(cudaEventRecord(e1, s));
+        AWG_CUDA(cudaEventSynchronize(e1));
+        AWG_CUDA(cudaEventElapsedTime(ms, e0, e1));
+        return AWG_OK;
+    };
+    awg_status st = AWG_OK;
+    for (int p = 0; p < AWG_NPREC && st == AWG_OK; p++) {
+        PrecOps& P = h->prec[p];
+        if (!P.built) continue;
+        const int wt_c[] = {2, 3, 4, 6, 8}, wd_c[] = {4, 8, 16};
+        float best = 1e30f;
+        int bwt = 152 * 3, bwd = 152 * 16;
+        P.wd_blocks = bwd;
+        for (int c : wt_c) {
+            P.wt_blocks = 152 * c;
+            float ms = 0.f;
+            if ((st = timed(p, &ms)) != AWG_OK) break;
+            if (ms < best) { best = ms; bwt = P.wt_blocks; }
+        }
+        P.wt_blocks = bwt;
+        for (int c : wd_c) {
+            if (st != AWG_OK) break;
+            P.wd_blocks = 152 * c;
+            float ms = 0.f;
+            if ((st = timed(p, &ms)) != AWG_OK) break;
+            if (ms < best) { best = ms; bwd = P.wd_blocks; }
+        }
+        P.wd_blocks = bwd;
+        if (h->opt.verbose)
+            fprintf(stderr, "libawg: autotune form %d: W^T r %d blocks, W d %d blocks, apply %.3f ms\n", p,
+                    P.wt_blocks, P.wd_blocks, best / 3.0f);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    AWG_CUDA(cudaFreeAsync(x, s));
+    AWG_CUDA(cudaFreeAsync(y, s));
+    AWG_CUDA(cudaStreamSynchronize(s));
+    return st;
+}
+
 // ------------------------------------------------------------------- PCG
 static awg_status dot1(Handle* h, const double* x, const double* y, double* out, Ws& w,
                        cudaStream_t s) {
-    const int nb = grid_n(h->n);
-    {
-        ProfScope ps_(h, AWG_PROF_VECTOR, s);
-        k_dot_partial<<<nb, 256, 0, s>>>(h->n, x, y, w.part);
-    }
+    ProfScope ps_(h, AWG_PROF_VECTOR, s);
+    k_dot<<<grid_n(h->n), 256, 0, s>>>(h->n, x, y, w.part, w.cnt, out);
     AWG_LAUNCH();
-    {
-        ProfScope ps_(h, AWG_PROF_VECTOR, s);
-        k_final_sum<<<1, 256, 0, s>>>(nb, w.part, out);
-    }
+    return AWG_OK;
+}
+
+// q = b - A x
+static awg_status resid1(Handle* h, const double* b, const double* x, double* q, cudaStream_t s) {
+    ProfScope ps_(h, AWG_PROF_SPMV, s);
+    k_aplus_row<<<(h->n + 255) / 256, 256, 0, s>>>(h->n, (int*)h->rowptr.p, (int*)h->colidx.p,
+                                                   (double*)h->val.p, x, nullptr, nullptr, nullptr, nullptr,
+                                                   nullptr, nullptr, nullptr, nullptr, b, -1.0, q);
     AWG_LAUNCH();
     return AWG_OK;
 }
@@ -853,8 +1165,9 @@ awg_status pcg1(Handle* h, int prec, int variant_stage, const double* b, double*
                 int* iters, double* relres, cudaStream_t s) {
     Ws w = ws_of(h);
     const int n = h->n, nb = grid_n(n);
-    // partial buffer (4096 doubles): [0, 1216) and [1536, 2752) hold per-block
-    // partials (grid_n <= 1216 blocks), the device scalars live at [4000, 4016)
+    // partial buffer (4096 doubles): [0, 1216) holds per-block partials
+    // (grid_n <= 1216 blocks), the device scalars live at [4000, 4016), the
+    // ticket counters at [4064, 4068)
     double* scal = w.part + 4000;
     double *r, *p, *q, *z;
     AWG_CUDA(cudaMallocAsync(&r, (size_t)n * 8, s));
@@ -880,20 +1193,10 @@ awg_status pcg1(Handle* h, int prec, int variant_stage, const double* b, double*
         bool done = false;
         while (!done) {
             if (it >= maxit) { st = AWG_ERR_MAXIT; break; }
-            AWG_TRY(spmv1(h, p, q, w.part, s));                       // q = A p, partial p.q
+            AWG_TRY(spmv1(h, p, q, scal + S_PQ, s));                  // q = A p, p.q
             {
                 ProfScope ps_(h, AWG_PROF_VECTOR, s);
-                k_final_sum<<<1, 256, 0, s>>>(nb, w.part, scal + S_PQ);
-            }
-            AWG_LAUNCH();
-            {
-                ProfScope ps_(h, AWG_PROF_VECTOR, s);
-                k_pcg_xr<<<nb, 256, 0, s>>>(n, scal, p, q, x, r, w.part + 1536);
-            }
-            AWG_LAUNCH();
-            {
-                ProfScope ps_(h, AWG_PROF_VECTOR, s);
-                k_final_sum<<<1, 256, 0, s>>>(nb, w.part + 1536, scal + S_RR);
+                k_pcg_xr<<<nb, 256, 0, s>>>(n, scal, p, q, x, r, w.part, w.cnt);  // x, r, r.r
             }
             AWG_LAUNCH();
             it++;
@@ -904,12 +1207,7 @@ awg_status pcg1(Handle* h, int prec, int variant_stage, const double* b, double*
             rel = sqrt(h->h_scal[S_RR]) / bnorm;
             if (rel <= rtol) {
                 // confirm on the true residual b - A x
-                AWG_TRY(spmv1(h, x, q, nullptr, s));
-                {
-                    ProfScope ps_(h, AWG_PROF_VECTOR, s);
-                    k_sub<<<(n + 255) / 256, 256, 0, s>>>(n, b, q, q);
-                }
-                AWG_LAUNCH();
+                AWG_TRY(resid1(h, b, x, q, s));
                 AWG_TRY(dot1(h, q, q, scal + S_TR, w, s));
                 AWG_CUDA(cudaMemcpyAsync(h->h_scal, scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
                 AWG_CUDA(cudaStreamSynchronize(s));
@@ -923,23 +1221,13 @@ awg_status pcg1(Handle* h, int prec, int variant_stage, const double* b, double*
             AWG_TRY(dot1(h, r, z, scal + S_RZN, w, s));
             {
                 ProfScope ps_(h, AWG_PROF_VECTOR, s);
-                k_pcg_beta<<<1, 1, 0, s>>>(scal);
-            }
-            AWG_LAUNCH();
-            {
-                ProfScope ps_(h, AWG_PROF_VECTOR, s);
-                k_pcg_p<<<nb, 256, 0, s>>>(n, scal, z, p);
+                k_pcg_p<<<nb, 256, 0, s>>>(n, scal, z, p, w.cnt);  // beta, p, rz <- rz_new
             }
             AWG_LAUNCH();
         }
     }
     if (st != AWG_OK || true_rel == rel) {
-        AWG_TRY(spmv1(h, x, q, nullptr, s));
-        {
-            ProfScope ps_(h, AWG_PROF_VECTOR, s);
-            k_sub<<<(n + 255) / 256, 256, 0, s>>>(n, b, q, q);
-        }
-        AWG_LAUNCH();
+        AWG_TRY(resid1(h, b, x, q, s));
         AWG_TRY(dot1(h, q, q, scal + S_TR, w, s));
         AWG_CUDA(cudaMemcpyAsync(h->h_scal, scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
         AWG_CUDA(cudaStreamSynchronize(s));

@@ -58,6 +58,16 @@ struct PrecOps {
     DevBuf inexInv;   // (C^-1 - Vhat^T W)^-1 (H_3,inex), float64 n_- x n_-
     DevBuf rscale;    // float16 W: power-of-two row scales, float32[n]
     DevBuf cscale;    // float16 W: power-of-two column scales, float32[ldw] (0 on padding)
+    // float16 W: sparse float32 correction of the largest entries (|W_ij| >=
+    // w16_keep * max_i |W_ij|), in the scaled units of What: the exact value
+    // minus its float16 rounding.  Rows (CSR, for W d) and columns (CSC, for
+    // W^T r), indices ascending.
+    int64_t corr_nnz = 0;
+    DevBuf corr_rowptr, corr_col, corr_val;   // int32[n+1], int32[nnz], float32[nnz]
+    DevBuf corr_colptr, corr_row, corr_cval;  // int32[n_-+1], int32[nnz], float32[nnz]
+    // grid sizes of the W^T r and W d passes (0: defaults), set by the
+    // autotuner at the end of setup
+    int wt_blocks = 0, wd_blocks = 0;
 };
 constexpr int AWG_NPREC = 4;
 
@@ -136,6 +146,13 @@ struct Handle {
     // H_2 on the caller's stream (fork and join through the two events)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // awg_pcg and awg_apply run on `hp`, created with the highest stream
+    // priority (`side` has the lowest): blocks of the H_2 chain, the critical
+    // path, are dispatched ahead of the bandwidth-bound W^T r pass, which
+    // fills the SMs they leave free.  Fork and join with the caller's stream
+    // through ev_in / ev_out.
+    cudaStream_t hp = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 
     // profiling (awg_profile): launch count of the apply/PCG path and CUDA
     // event times of its heaviest kernels
@@ -257,8 +274,11 @@ awg_status eig_select_batched(Handle* h, double* arena, const int* d_m, const in
                               std::vector<int64_t>& h_vec_off, DevBuf& vals,
                               std::vector<int>& h_val_ptr, cudaStream_t s);
 
-// solve.cu
+// apply.cu
 awg_status apply_stage(Handle* h, int which, int prec, const double* x, double* y, cudaStream_t s);
+// times the apply of every built form over a few grid sizes of the two W
+// passes (which share the GPU with the H_2 chain) and keeps the fastest
+awg_status autotune_apply(Handle* h);
 awg_status build_setup_numeric(Handle* h);
 
 // learned.cu : features, network and start block of the GenEO block solver

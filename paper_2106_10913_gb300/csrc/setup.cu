@@ -212,7 +212,7 @@ __device__ __forceinline__ float pow2_above(double x) {
     e = max(-126, min(127, e));
     return __int_as_float((e + 127) << 23);
 }
-__global__ void k_w16_cscale(int n, const double* __restrict__ W, float* cs) {
+__global__ void k_w16_cscale(int n, const double* __restrict__ W, float* cs, double* cmax) {
     __shared__ double red[32];
     const int j = blockIdx.x;
     double m = 0.0;
@@ -224,6 +224,35 @@ __global__ void k_w16_cscale(int n, const double* __restrict__ W, float* cs) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) t = fmax(t, red[w]);
         cs[j] = pow2_above(t);
+        cmax[j] = t;
+    }
+}
+// entries kept exact: |W_ij| >= keep * max_i |W_ij| (and nonzero)
+__device__ __forceinline__ bool w16_kept(double v, double cmax, double keep) {
+    return keep > 0.0 && v != 0.0 && fabs(v) >= keep * cmax;
+}
+__global__ void k_w16_corr_count(int n, int nm, const double* __restrict__ W, const double* __restrict__ cmax,
+                                 double keep, int* cnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = 0;
+    for (int j = 0; j < nm; j++) c += w16_kept(W[(size_t)j * n + i], cmax[j], keep);
+    cnt[i] = c;
+}
+// CSR of the correction (scaled units): What_ij exact minus its float16 rounding
+__global__ void k_w16_corr_fill(int n, int nm, const double* __restrict__ W, const double* __restrict__ cmax,
+                                double keep, const float* __restrict__ rs, const float* __restrict__ cs,
+                                const int* __restrict__ rowptr, int* col, float* val) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int k = rowptr[i];
+    for (int j = 0; j < nm; j++) {
+        const double v = W[(size_t)j * n + i];
+        if (!w16_kept(v, cmax[j], keep)) continue;
+        const double sv = v / ((double)rs[i] * (double)cs[j]);
+        col[k] = j;
+        val[k] = (float)(sv - (double)__half2float(__double2half(sv)));
+        k++;
     }
 }
 __global__ void k_w16_rscale(int n, int nm, const double* __restrict__ W, const float* __restrict__ cs,
@@ -235,12 +264,17 @@ __global__ void k_w16_rscale(int n, int nm, const double* __restrict__ W, const 
     rs[i] = pow2_above(m);
 }
 // float64 copy of the rounded W (column-major), for F
+// float64 copy of the stored W (float16 value plus the float32 correction
+// where kept), column-major, for F
 __global__ void k_round_fp16(int n, size_t len, const double* __restrict__ X, const float* __restrict__ rs,
-                             const float* __restrict__ cs, double* Y) {
+                             const float* __restrict__ cs, const double* __restrict__ cmax, double keep,
+                             double* Y) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= len) return;
     const double sc = (double)rs[e % n] * (double)cs[e / n];
-    Y[e] = sc * (double)__half2float(__double2half(X[e] / sc));
+    const double sv = X[e] / sc;
+    const double h = (double)__half2float(__double2half(sv));
+    Y[e] = w16_kept(X[e], cmax[e / n], keep) ? sc * (h + (double)(float)(sv - h)) : sc * h;
 }
 __global__ void k_to_rowmajor_fp16(int n, int k, int ld, const double* __restrict__ X,
                                    const float* __restrict__ rs, const float* __restrict__ cs, __half* Y) {
@@ -511,6 +545,58 @@ static awg_status build_inex(Handle* h, const double* Wt, DevBuf& out) {
     return AWG_OK;
 }
 
+// Sparse correction of the float16 W (rows on the device, columns by a
+// stable transpose on the host: setup-time only)
+static awg_status build_w16_correction(Handle* h, PrecOps& P, const double* W64, const double* cmax,
+                                       double keep) {
+    cudaStream_t s = h->stream;
+    const int n = h->n, nm = h->n_minus;
+    AWG_TRY(dalloc(h, P.corr_rowptr, (size_t)(n + 1) * 4));
+    AWG_TRY(dalloc(h, P.corr_colptr, (size_t)(nm + 1) * 4));
+    std::vector<int> cnt(n), rp(n + 1, 0);
+    if (keep > 0.0) {
+        k_w16_corr_count<<<(n + 255) / 256, 256, 0, s>>>(n, nm, W64, cmax, keep, (int*)P.corr_rowptr.p);
+        AWG_LAUNCH();
+        AWG_CUDA(cudaMemcpyAsync(cnt.data(), P.corr_rowptr.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+        AWG_CUDA(cudaStreamSynchronize(s));
+        int64_t tot = 0;
+        for (int i = 0; i < n; i++) tot += cnt[i];
+        if (tot > INT32_MAX) return AWG_ERR_INVALID_ARG;
+        for (int i = 0; i < n; i++) rp[i + 1] = rp[i] + cnt[i];
+    }
+    const int64_t nnz = rp[n];
+    P.corr_nnz = nnz;
+    AWG_CUDA(cudaMemcpyAsync(P.corr_rowptr.p, rp.data(), (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, s));
+    for (DevBuf* b : {&P.corr_col, &P.corr_row}) AWG_TRY(dalloc(h, *b, (size_t)std::max<int64_t>(1, nnz) * 4));
+    for (DevBuf* b : {&P.corr_val, &P.corr_cval}) AWG_TRY(dalloc(h, *b, (size_t)std::max<int64_t>(1, nnz) * 4));
+    std::vector<int> cp(nm + 1, 0);
+    if (nnz > 0) {
+        k_w16_corr_fill<<<(n + 255) / 256, 256, 0, s>>>(n, nm, W64, cmax, keep, (float*)P.rscale.p,
+                                                         (float*)P.cscale.p, (int*)P.corr_rowptr.p,
+                                                         (int*)P.corr_col.p, (float*)P.corr_val.p);
+        AWG_LAUNCH();
+        std::vector<int> col(nnz), row(nnz);
+        std::vector<float> val(nnz), cval(nnz);
+        AWG_CUDA(cudaMemcpyAsync(col.data(), P.corr_col.p, (size_t)nnz * 4, cudaMemcpyDeviceToHost, s));
+        AWG_CUDA(cudaMemcpyAsync(val.data(), P.corr_val.p, (size_t)nnz * 4, cudaMemcpyDeviceToHost, s));
+        AWG_CUDA(cudaStreamSynchronize(s));
+        for (int64_t k = 0; k < nnz; k++) cp[col[k] + 1]++;
+        for (int j = 0; j < nm; j++) cp[j + 1] += cp[j];
+        std::vector<int> next(cp.begin(), cp.end() - 1);
+        for (int i = 0; i < n; i++)  // rows ascending within each column
+            for (int k = rp[i]; k < rp[i + 1]; k++) {
+                const int t = next[col[k]]++;
+                row[t] = i;
+                cval[t] = val[k];
+            }
+        AWG_CUDA(cudaMemcpyAsync(P.corr_row.p, row.data(), (size_t)nnz * 4, cudaMemcpyHostToDevice, s));
+        AWG_CUDA(cudaMemcpyAsync(P.corr_cval.p, cval.data(), (size_t)nnz * 4, cudaMemcpyHostToDevice, s));
+    }
+    AWG_CUDA(cudaMemcpyAsync(P.corr_colptr.p, cp.data(), (size_t)(nm + 1) * 4, cudaMemcpyHostToDevice, s));
+    AWG_CUDA(cudaStreamSynchronize(s));
+    return AWG_OK;
+}
+
 awg_status build_setup_numeric(Handle* h) {
     cudaStream_t s = h->stream;
     const int N = h->N, n = h->n;
@@ -764,6 +850,7 @@ awg_status build_setup_numeric(Handle* h) {
     // workspace of the single-RHS apply
     h->red_blocks = std::min(1216, std::max(1, (n + 127) / 128));
     AWG_TRY(dalloc(h, h->ws, ws_bytes(h)));
+    AWG_CUDA(cudaMemsetAsync(h->ws.p, 0, ws_bytes(h), s));  // ticket counters start at zero
     AWG_TRY(set_smem_limits(h));
     AWG_CUDA(cudaStreamSynchronize(s));
     double t4 = now_ms();
@@ -808,11 +895,19 @@ awg_status build_setup_numeric(Handle* h) {
                 AWG_TRY(dalloc(h, P.rscale, (size_t)n * 4));
                 AWG_TRY(dalloc(h, P.cscale, (size_t)h->ldw * 4));
                 AWG_CUDA(cudaMemsetAsync(P.cscale.p, 0, (size_t)h->ldw * 4, s));
-                k_w16_cscale<<<nm, 256, 0, s>>>(n, W64, (float*)P.cscale.p);
+                DevBuf cmax;
+                AWG_TRY(dalloc(h, cmax, (size_t)nm * 8));
+                k_w16_cscale<<<nm, 256, 0, s>>>(n, W64, (float*)P.cscale.p, (double*)cmax.p);
                 AWG_LAUNCH();
                 k_w16_rscale<<<(n + 255) / 256, 256, 0, s>>>(n, nm, W64, (float*)P.cscale.p, (float*)P.rscale.p);
                 AWG_LAUNCH();
-                k_round_fp16<<<gl, 256, 0, s>>>(n, len, W64, (float*)P.rscale.p, (float*)P.cscale.p, Wr);
+                const double keep = h->opt.w16_keep;
+                AWG_TRY(build_w16_correction(h, P, W64, (double*)cmax.p, keep));
+                k_round_fp16<<<gl, 256, 0, s>>>(n, len, W64, (float*)P.rscale.p, (float*)P.cscale.p,
+                                                (double*)cmax.p, keep, Wr);
+                AWG_LAUNCH();
+                AWG_CUDA(cudaStreamSynchronize(s));
+                dfree(h, cmax);
             } else if (p == AWG_MIXED_FP32) {
                 k_round_f32<<<gl, 256, 0, s>>>(len, W64, Wr);
             } else {
@@ -838,6 +933,7 @@ awg_status build_setup_numeric(Handle* h) {
     for (int p = 1; p < AWG_NPREC; p++)
         if (h->opt.precisions & (1 << p)) h->prec[p].built = true;
     AWG_CUDA(cudaStreamSynchronize(s));
+    if (h->opt.autotune) AWG_TRY(autotune_apply(h));
     return AWG_OK;
 }
 

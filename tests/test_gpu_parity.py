@@ -118,9 +118,11 @@ def test_mixed_fp32_apply(pair):
 
 # Apply error of the forms that round W below float32, against the float64
 # oracle.  The rounded W spans a slightly different second coarse space, so
-# the error is that of the storage unit roundoff u (float16 2^-11, bfloat16
-# 2^-8) amplified by the coarse problem; the bounds are 64 u.
-REDUCED_RTOL = {"fp16": 64 * 2.0 ** -11, "bf16": 64 * 2.0 ** -8}
+# the error is that of the storage unit roundoff u amplified by the coarse
+# problem: bfloat16 (u = 2^-8) is bounded by 64 u; the float16 form keeps
+# its largest entries exact to float32 and meets the reduced-precision
+# target of 1e-4 like the float32 form.
+REDUCED_RTOL = {"fp16": MIXED_RTOL, "bf16": 64 * 2.0 ** -8}
 
 
 @pytest.mark.parametrize("form", ["fp16", "bf16"])

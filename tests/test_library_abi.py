@@ -45,7 +45,7 @@ def test_host_only_calls(lib):
     import paper_2106_10913_gb300 as pkg
     o = pkg.default_options()
     assert o.variant == 0 and o.precisions == 1 and o.zero_rtol == 1e-12 and o.maxit == 1000
-    assert o.geneo_solver == 0 and o.geneo_block == 8 and o.geneo_maxit == 60
+    assert o.geneo_solver == 0 and o.geneo_block == 8 and o.geneo_maxit == 60 and o.autotune == 1
     assert not o.learned_params
     assert lib.awg_status_string(0) == b"AWG_OK"
     assert lib.awg_status_string(2) == b"AWG_ERR_MIN_OVERLAP"
@@ -62,7 +62,8 @@ def test_host_only_calls(lib):
     assert lib.awg_learned_grad(0, None, None, None, None, 0, None) == 1
     assert lib.awg_learned_train(1, None, None, None, 1, 1e-2, 0, None, None) == 1
     assert lib.awg_learned_data(None, None, None, None) == 1
-    assert ctypes.sizeof(pkg.awg.awg_options) == 64
+    assert ctypes.sizeof(pkg.awg.awg_options) == 80
+    assert o.w16_keep == 0.1
 
 
 def test_product_does_not_import_oracle():
