@@ -124,6 +124,10 @@ typedef struct {
                                both W passes; the largest ~1 % of W carry most
                                of each column, so this restores nearly the
                                float32 iteration count); 0 disables; 0.1       */
+    int block_tensor_cores; /* awg_apply_block / awg_pcg_block with
+                               AWG_MIXED_FP16 or AWG_MIXED_BF16: 1 (default)
+                               the two passes over W on the tensor cores
+                               (tcgen05.mma fed by TMA); 0 on the CUDA cores   */
 } awg_options;
 
 /* Per-handle figures reported after setup (cf. Table 1 of the paper). */
@@ -275,6 +279,34 @@ awg_status awg_profile_read(awg_handle h, int64_t* h_launches, double* h_ms, int
  */
 awg_status awg_profile_trace(awg_handle h, int cap, int* h_class, double* h_t0, double* h_t1,
                              int* h_count);
+
+/*
+ * Multi-right-hand-side ("block") forms of awg_apply_stage and awg_pcg: the
+ * nrhs columns are processed together, so every pass over an operator (the
+ * local pseudo-inverses, W, Z, V^s_-, E^-1, F^-1, A) serves all of them; the
+ * GEMV-shaped steps of the single-RHS path become GEMMs.  Each column keeps
+ * its own PCG recurrence (Section 1: alpha, beta and the stopping test per
+ * column), so column c of a block solve follows the single-RHS solve of
+ * column c.  `precision`: AWG_FP64 computes every step in float64; the
+ * mixed forms keep the preconditioner's internal vectors and arithmetic in
+ * float32 (with their stored W: float32 on the CUDA cores, float16 or
+ * bfloat16 on the tensor cores, see awg_options.block_tensor_cores) and the
+ * coarse solves E^-1, F^-1 and all PCG recurrences in float64.
+ *   d_x, d_y / d_b, d_x   device float64, nrhs columns of length n with
+ *                         leading dimension ld >= n (column-major)
+ * awg_apply_block: which = 0 (A), 1 (A_+), 2 (H^NN), 3 (H_2), 4 (H_3,ad);
+ * 1 <= nrhs <= 64; asynchronous on `stream` (allocates its workspace on the
+ * handle's first block call).
+ * awg_pcg_block: H_3,ad (the handle's variant must be AWG_H3_AD), any
+ * nrhs >= 1 (groups of up to 64 columns), x_0 = 0; synchronises `stream`;
+ * h_iters / h_relres as awg_pcg.  Errors: AWG_ERR_INVALID_ARG,
+ * AWG_ERR_STATE, AWG_ERR_MAXIT, AWG_ERR_BREAKDOWN, AWG_ERR_OOM,
+ * AWG_ERR_CUDA (also when a tensor-core pass reports a timed-out wait).
+ */
+awg_status awg_apply_block(awg_handle h, int which, int precision, const double* d_x, double* d_y, int nrhs,
+                           int ld, void* stream);
+awg_status awg_pcg_block(awg_handle h, int precision, const double* d_b, double* d_x, int nrhs, int ld,
+                         double rtol, int* h_iters, double* h_relres, void* stream);
 
 /* Capacity, in float64 values, of the static scratch of awg_apply_hnn_noalloc. */
 #define AWG_NOALLOC_MAX_LOCAL (1 << 20)

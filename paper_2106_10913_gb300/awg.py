@@ -43,7 +43,7 @@ class awg_options(ctypes.Structure):
                 ("w_precision", ctypes.c_int), ("geneo_solver", ctypes.c_int),
                 ("geneo_block", ctypes.c_int), ("geneo_maxit", ctypes.c_int),
                 ("learned_params", ctypes.c_void_p), ("autotune", ctypes.c_int),
-                ("w16_keep", ctypes.c_double)]
+                ("w16_keep", ctypes.c_double), ("block_tensor_cores", ctypes.c_int)]
 
 
 class awg_info(ctypes.Structure):
@@ -60,7 +60,8 @@ class awg_info(ctypes.Structure):
 EXPORTED = ["awg_default_options", "awg_status_string", "awg_setup", "awg_destroy",
             "awg_get_info", "awg_apply", "awg_apply_stage", "awg_pcg", "awg_get_array",
             "awg_profile", "awg_profile_read", "awg_apply_hnn_noalloc", "awg_learned_data",
-            "awg_learned_forward", "awg_learned_grad", "awg_learned_train", "awg_profile_trace"]
+            "awg_learned_forward", "awg_learned_grad", "awg_learned_train", "awg_profile_trace",
+            "awg_apply_block", "awg_pcg_block"]
 LEARNED_NPARAM, LEARNED_NFEAT = 385, 5
 GENEO_DENSE, GENEO_BLOCK, GENEO_LEARNED = 0, 1, 2
 PROF_NAMES = ["spmv", "local", "wt", "wd", "coarse", "subdomain", "prolong", "vector"]
@@ -104,6 +105,10 @@ def load_library(path: str = LIB_PATH):
     lib.awg_profile_read.restype = I
     lib.awg_profile_trace.argtypes = [P, I, P, P, P, ctypes.POINTER(I)]
     lib.awg_profile_trace.restype = I
+    lib.awg_apply_block.argtypes = [P, I, I, P, P, I, I, P]
+    lib.awg_apply_block.restype = I
+    lib.awg_pcg_block.argtypes = [P, I, P, P, I, I, D, ctypes.POINTER(I), ctypes.POINTER(D), P]
+    lib.awg_pcg_block.restype = I
     lib.awg_apply_hnn_noalloc.argtypes = [P, I, P, P, P]
     lib.awg_apply_hnn_noalloc.restype = I
     lib.awg_learned_data.argtypes = [P, P, P, P]
@@ -199,6 +204,28 @@ def awg_pcg(h, b, x, rtol: float = 1e-8, precision: int = FP64, stream=None, che
                                 its, rel, _stream_ptr(stream))
     if check:
         _check(st, "awg_pcg")
+    return st, list(its), list(rel)
+
+
+def awg_apply_block(h, which, x, y, precision: int = FP64, stream=None):
+    """y = stage(x) for the rows of x (nrhs x n, one right-hand side per row,
+    nrhs <= 64) at once; `which` as awg_apply_stage, stages 0-4."""
+    w = STAGE[which] if isinstance(which, str) else int(which)
+    _check(load_library().awg_apply_block(h, w, precision, x.data_ptr(), y.data_ptr(), x.shape[0],
+                                          x.shape[-1], _stream_ptr(stream)), "awg_apply_block")
+    return y
+
+
+def awg_pcg_block(h, b, x, rtol: float = 1e-8, precision: int = FP64, stream=None, check=True):
+    """PCG for the rows of b (nrhs x n) together: one pass over each
+    operator per iteration for all of them, one recurrence per row."""
+    nrhs = b.shape[0]
+    its = (ctypes.c_int * nrhs)()
+    rel = (ctypes.c_double * nrhs)()
+    st = load_library().awg_pcg_block(h, precision, b.data_ptr(), x.data_ptr(), nrhs, b.shape[-1],
+                                      float(rtol), its, rel, _stream_ptr(stream))
+    if check:
+        _check(st, "awg_pcg_block")
     return st, list(its), list(rel)
 
 

@@ -3,6 +3,7 @@
 
 #include "awg_common.cuh"
 #include "ops.cuh"
+#include "block.cuh"
 
 #include <algorithm>
 #include <chrono>
@@ -56,7 +57,8 @@ static void free_all(Handle* h) {
                       &h->inc_ptr, &h->inc_pos, &h->inc_sub, &h->pos_sub, &h->dvec, &h->mmu,
                       &h->bval, &h->dense_off, &h->g32_off, &h->nm, &h->nstrict, &h->nm_ptr, &h->vm_off,
                       &h->Vm, &h->lam_m, &h->sigma, &h->modes, &h->mode_ptr, &h->z_off, &h->Z,
-                      &h->E, &h->Einv, &h->wcol_ptr, &h->Wcm, &h->F64, &h->ws, &h->flag, &h->red};
+                      &h->E, &h->Einv, &h->wcol_ptr, &h->Wcm, &h->F64, &h->ws, &h->flag, &h->red,
+                      &h->bws, &h->bval32, &h->bvm32, &h->blam32, &h->blam64, &h->bz32};
     for (DevBuf* b : bufs) dfree(h, *b);
     for (auto& P : h->prec) {
         dfree(h, P.G);
@@ -112,6 +114,7 @@ void awg_default_options(awg_options* opt) {
     opt->learned_params = nullptr;
     opt->autotune = 1;
     opt->w16_keep = 0.1;
+    opt->block_tensor_cores = 1;
 }
 
 const char* awg_status_string(awg_status s) {
@@ -300,6 +303,42 @@ awg_status awg_pcg(awg_handle hh, int precision, const double* d_b, double* d_x,
     AWG_CUDA(cudaEventRecord(h->ev_out, h->hp));
     AWG_CUDA(cudaStreamWaitEvent(us, h->ev_out, 0));
     return worst;
+}
+
+awg_status awg_apply_block(awg_handle hh, int which, int precision, const double* d_x, double* d_y, int nrhs,
+                           int ld, void* stream) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !d_x || !d_y || which < 0 || which > 4 || nrhs < 1 || nrhs > 64 || ld < h->n || precision < 0 ||
+        precision >= AWG_NPREC)
+        return AWG_ERR_INVALID_ARG;
+    // the mixed block forms apply the float32 local pseudo-inverses
+    if (!h->prec[precision].built || (precision != AWG_FP64 && !h->prec[AWG_MIXED_FP32].G.p)) return AWG_ERR_STATE;
+    cudaStream_t us = (cudaStream_t)stream;
+    AWG_CUDA(cudaEventRecord(h->ev_in, us));
+    AWG_CUDA(cudaStreamWaitEvent(h->hp, h->ev_in, 0));
+    const awg_status st = block_apply(h, which, precision, d_x, d_y, nrhs, ld, h->hp);
+    AWG_CUDA(cudaEventRecord(h->ev_out, h->hp));
+    AWG_CUDA(cudaStreamWaitEvent(us, h->ev_out, 0));
+    return st;
+}
+
+awg_status awg_pcg_block(awg_handle hh, int precision, const double* d_b, double* d_x, int nrhs, int ld,
+                         double rtol, int* h_iters, double* h_relres, void* stream) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !d_b || !d_x || nrhs < 0 || ld < h->n || !(rtol > 0.0) || precision < 0 || precision >= AWG_NPREC)
+        return AWG_ERR_INVALID_ARG;
+    // the mixed block forms apply the float32 local pseudo-inverses
+    if (!h->prec[precision].built || (precision != AWG_FP64 && !h->prec[AWG_MIXED_FP32].G.p)) return AWG_ERR_STATE;
+    if (h->opt.variant != AWG_H3_AD) return AWG_ERR_STATE;
+    if (nrhs == 0) return AWG_OK;
+    cudaStream_t us = (cudaStream_t)stream;
+    AWG_CUDA(cudaEventRecord(h->ev_in, us));
+    AWG_CUDA(cudaStreamWaitEvent(h->hp, h->ev_in, 0));
+    const awg_status st = block_pcg(h, precision, d_b, d_x, nrhs, ld, rtol, h_iters, h_relres, h->hp);
+    AWG_CUDA(cudaEventRecord(h->ev_out, h->hp));
+    AWG_CUDA(cudaStreamWaitEvent(us, h->ev_out, 0));
+    AWG_CUDA(cudaStreamSynchronize(us));
+    return st;
 }
 
 awg_status awg_get_array(awg_handle hh, int what, void* h_out, size_t count) {

@@ -137,6 +137,10 @@ struct Handle {
 
     // single right-hand-side workspace of the apply
     DevBuf ws;
+    // multi-right-hand-side (block) path: workspace and float32 copies of
+    // A's values, V^s_-, |Lambda^s_-| and Z (built on the first block call),
+    // |Lambda^s_-| in float64
+    DevBuf bws, bval32, bvm32, blam32, blam64, bz32;
     DevBuf flag;                         // int status word
     DevBuf red;                          // partial-sum scratch
     int red_blocks = 0;

@@ -1,0 +1,1459 @@
+// Multi-right-hand-side hot path: the AWG apply and PCG for K columns at
+// once (K = 16, 32 or 64; nrhs <= 64 columns padded with zero columns).
+//
+// Every column runs its own PCG recurrence (its own alpha, beta and stopping
+// test, Section 1 PCG), so each column's iterates are those of a
+// single-right-hand-side solve; what the columns share is one pass over each
+// operator per iteration.  The local pseudo-inverses, W and the GenEO / V_-
+// blocks are then read once for K right-hand sides instead of K times, which
+// turns the bandwidth-bound GEMVs of the single-RHS path into GEMMs.
+//
+// Precision of a block apply (awg_precision):
+//   FP64        every step in float64 (the parity form);
+//   MIXED_*     the preconditioner's internal block vectors and arithmetic
+//               in float32 (local pseudo-inverses float32; W float32, or
+//               float16 / bfloat16 on the tensor cores, umma.cu), the two
+//               coarse solves E^-1, F^-1 in float64; the PCG recurrences
+//               (dot products, x, r, p updates, stopping test) always float64.
+// Layout: block vectors row-major X[i * K + c]; local arenas row-major per
+// local position loc[P * K + c], P in the concatenated subdomain lists.
+
+#include "block.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+
+namespace awg {
+
+// Thread-to-(row, column) map of the row kernels: TPR threads cover the K
+// columns of one row, CPT columns each (cl, cl + TPR, ...), RPW rows per warp.
+template <int K>
+struct RM {
+    static constexpr int TPR = K < 32 ? K : 32;
+    static constexpr int CPT = K / TPR;
+    static constexpr int RPW = 32 / TPR;
+    static constexpr int RPB = 8 * RPW;  // rows per 256-thread block
+};
+
+template <typename T> struct Acc { using type = float; };
+template <> struct Acc<double> { using type = double; };
+
+// Per-column sums of a 256-thread block (thread partials acc[j] belong to
+// column cl + TPR * j), then over the grid: block partials go to
+// part[b * K + c] and the last block to arrive (ticket) adds them in block
+// order.  Deterministic for a given grid.
+template <int K>
+__device__ __forceinline__ void colsum_grid(const double* acc, double* part, unsigned* cnt, double* out) {
+    using M = RM<K>;
+    __shared__ double red[8 * M::RPW][K];
+    __shared__ unsigned ticket;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int rw = lane / M::TPR, cl = lane % M::TPR;
+#pragma unroll
+    for (int j = 0; j < M::CPT; j++) red[w * M::RPW + rw][cl + M::TPR * j] = acc[j];
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double v = 0.0;
+        for (int r = 0; r < 8 * M::RPW; r++) v += red[r][threadIdx.x];
+        part[(size_t)blockIdx.x * K + threadIdx.x] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) ticket = atomicAdd(cnt, 1u);
+    __syncthreads();
+    if (ticket != gridDim.x - 1) return;
+    __threadfence();
+    if (threadIdx.x < K) {
+        double v = 0.0;
+        for (int b = 0; b < (int)gridDim.x; b++) v += __ldcg(part + (size_t)b * K + threadIdx.x);
+        out[threadIdx.x] = v;
+    }
+    if (threadIdx.x == 0) *cnt = 0u;
+}
+
+#define ROW_LOOP(K_)                                                                     \
+    using M = RM<K_>;                                                                    \
+    const int lane_ = threadIdx.x & 31, w_ = threadIdx.x >> 5;                           \
+    const int rw_ = lane_ / M::TPR, cl = lane_ % M::TPR;                                 \
+    (void)rw_;                                                                           \
+    for (int i = blockIdx.x * M::RPB + w_ * M::RPW + rw_; i < n; i += gridDim.x * M::RPB)
+
+// ------------------------------------------------------------- PCG (float64)
+// PCG scalars of a block solve, K values each: rz, pq, rr, rz_new, b.b,
+// true residual, active flag (1.0 / 0.0)
+enum { B_RZ = 0, B_PQ = 1, B_RR = 2, B_RZN = 3, B_BB = 4, B_TR = 5, B_ACT = 6, B_NSC = 7 };
+
+// Y = A X and, if dot, the column sums of X .* Y
+template <int K>
+__global__ void __launch_bounds__(256) kb_spmv_dot(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                   const double* __restrict__ a, const double* __restrict__ X,
+                                                   double* __restrict__ Y, double* part, unsigned* cnt,
+                                                   double* dot) {
+    double acc[RM<K>::CPT] = {};
+    ROW_LOOP(K) {
+        double y[M::CPT] = {};
+        for (int k = rp[i]; k < rp[i + 1]; k++) {
+            const double av = a[k];
+            const double* xr = X + (size_t)ci[k] * K + cl;
+#pragma unroll
+            for (int j = 0; j < M::CPT; j++) y[j] = fma(av, xr[M::TPR * j], y[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < M::CPT; j++) {
+            Y[(size_t)i * K + cl + M::TPR * j] = y[j];
+            acc[j] = fma(y[j], X[(size_t)i * K + cl + M::TPR * j], acc[j]);
+        }
+    }
+    if (dot) colsum_grid<K>(acc, part, cnt, dot);
+}
+
+// Q = B - A X
+template <int K>
+__global__ void __launch_bounds__(256) kb_resid(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                const double* __restrict__ a, const double* __restrict__ B,
+                                                const double* __restrict__ X, double* __restrict__ Q) {
+    ROW_LOOP(K) {
+        double y[M::CPT] = {};
+        for (int k = rp[i]; k < rp[i + 1]; k++) {
+            const double av = a[k];
+            const double* xr = X + (size_t)ci[k] * K + cl;
+#pragma unroll
+            for (int j = 0; j < M::CPT; j++) y[j] = fma(av, xr[M::TPR * j], y[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < M::CPT; j++) {
+            const size_t e = (size_t)i * K + cl + M::TPR * j;
+            Q[e] = B[e] - y[j];
+        }
+    }
+}
+
+// out[c] = sum_i X(i, c) Y(i, c)
+template <int K>
+__global__ void __launch_bounds__(256) kb_coldot(int n, const double* __restrict__ X, const double* __restrict__ Y,
+                                                 double* part, unsigned* cnt, double* out) {
+    double acc[RM<K>::CPT] = {};
+    ROW_LOOP(K) {
+#pragma unroll
+        for (int j = 0; j < M::CPT; j++) {
+            const size_t e = (size_t)i * K + cl + M::TPR * j;
+            acc[j] = fma(X[e], Y[e], acc[j]);
+        }
+    }
+    colsum_grid<K>(acc, part, cnt, out);
+}
+
+// per column c: alpha = rz / pq (0 for inactive columns or pq <= 0);
+// X += alpha P, R -= alpha Q, rr = R . R
+template <int K>
+__global__ void __launch_bounds__(256) kb_pcg_xr(int n, double* sc, const double* __restrict__ P,
+                                                 const double* __restrict__ Q, double* X, double* R,
+                                                 double* part, unsigned* cnt) {
+    double alpha[RM<K>::CPT], acc[RM<K>::CPT] = {};
+    {
+        const int cl0 = (threadIdx.x & 31) % RM<K>::TPR;
+#pragma unroll
+        for (int j = 0; j < RM<K>::CPT; j++) {
+            const int c = cl0 + RM<K>::TPR * j;
+            const double pq = sc[B_PQ * K + c];
+            alpha[j] = (sc[B_ACT * K + c] != 0.0 && pq > 0.0) ? sc[B_RZ * K + c] / pq : 0.0;
+        }
+    }
+    ROW_LOOP(K) {
+#pragma unroll
+        for (int j = 0; j < M::CPT; j++) {
+            const size_t e = (size_t)i * K + cl + M::TPR * j;
+            X[e] = fma(alpha[j], P[e], X[e]);
+            const double r = fma(-alpha[j], Q[e], R[e]);
+            R[e] = r;
+            acc[j] = fma(r, r, acc[j]);
+        }
+    }
+    colsum_grid<K>(acc, part, cnt, sc + B_RR * K);
+}
+
+// per active column: beta = rz_new / rz, P = Z + beta P; the last block
+// then moves rz_new into rz
+template <int K>
+__global__ void __launch_bounds__(256) kb_pcg_p(int n, double* sc, const double* __restrict__ Z, double* P,
+                                                unsigned* cnt) {
+    __shared__ unsigned ticket;
+    double beta[RM<K>::CPT];
+    bool act[RM<K>::CPT];
+    {
+        const int cl0 = (threadIdx.x & 31) % RM<K>::TPR;
+#pragma unroll
+        for (int j = 0; j < RM<K>::CPT; j++) {
+            const int c = cl0 + RM<K>::TPR * j;
+            const double rz = sc[B_RZ * K + c];
+            act[j] = sc[B_ACT * K + c] != 0.0;
+            beta[j] = (rz != 0.0) ? sc[B_RZN * K + c] / rz : 0.0;
+        }
+    }
+    ROW_LOOP(K) {
+#pragma unroll
+        for (int j = 0; j < M::CPT; j++) {
+            const size_t e = (size_t)i * K + cl + M::TPR * j;
+            if (act[j]) P[e] = fma(beta[j], P[e], Z[e]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        ticket = atomicAdd(cnt, 1u);
+    }
+    __syncthreads();
+    if (ticket == gridDim.x - 1) {
+        if (threadIdx.x < K && sc[B_ACT * K + threadIdx.x] != 0.0)
+            sc[B_RZ * K + threadIdx.x] = sc[B_RZN * K + threadIdx.x];
+        if (threadIdx.x == 0) *cnt = 0u;
+    }
+}
+
+// --------------------------------------------------------- layout / types
+// dst (n x K row-major) from nrhs columns of src (column-major, ld), zero
+// columns beyond nrhs; 32 x 32 tiles through shared memory
+template <typename TD>
+__global__ void kb_from_cols(int n, int nrhs, int ld, int K, const double* __restrict__ src, TD* __restrict__ dst) {
+    __shared__ double t[32][33];
+    const int i0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int c = c0 + r, i = i0 + threadIdx.x;
+        t[r][threadIdx.x] = (c < nrhs && i < n) ? src[(size_t)c * ld + i] : 0.0;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int i = i0 + r, c = c0 + threadIdx.x;
+        if (i < n && c < K) dst[(size_t)i * K + c] = (TD)t[threadIdx.x][r];
+    }
+}
+
+// nrhs columns of dst (column-major, ld) from src (n x K row-major)
+template <typename TS>
+__global__ void kb_to_cols(int n, int nrhs, int ld, int K, const TS* __restrict__ src, double* __restrict__ dst) {
+    __shared__ double t[32][33];
+    const int i0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int i = i0 + r, c = c0 + threadIdx.x;
+        t[r][threadIdx.x] = (i < n && c < K) ? (double)src[(size_t)i * K + c] : 0.0;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int c = c0 + r, i = i0 + threadIdx.x;
+        if (c < nrhs && i < n) dst[(size_t)c * ld + i] = t[threadIdx.x][r];
+    }
+}
+
+template <typename T>
+__global__ void kb_add(size_t len, const T* __restrict__ a, T* y) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < len) y[e] += a[e];
+}
+
+template <typename TI, typename TO>
+__global__ void kb_cvt(size_t len, const TI* __restrict__ a, TO* __restrict__ b) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < len) b[e] = (TO)a[e];
+}
+
+// ------------------------------------------------------ preconditioner ops
+// Y = Yin + sign (A X + sum over the copies (s, q) of i of V_s(q, :) cm_s)
+// (A_+ = A + A_-, Thm. 2), cm_s = |Lambda^s_-| V^s_-^T R^s X from kb_tgemv
+template <typename T, int K>
+__global__ void __launch_bounds__(256) kb_aplus(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                const T* __restrict__ a, const T* __restrict__ X,
+                                                const int* __restrict__ inc_ptr, const int* __restrict__ inc_pos,
+                                                const int* __restrict__ inc_sub, const int* __restrict__ sub_ptr,
+                                                const int* __restrict__ colptr, const int64_t* __restrict__ boff,
+                                                const T* __restrict__ V, const T* __restrict__ cm,
+                                                const T* Yin, T sign, T* Y) {
+    ROW_LOOP(K) {
+        T y[M::CPT] = {};
+        for (int k = rp[i]; k < rp[i + 1]; k++) {
+            const T av = a[k];
+            const T* xr = X + (size_t)ci[k] * K + cl;
+#pragma unroll
+            for (int j = 0; j < M::CPT; j++) y[j] = fma(av, xr[M::TPR * j], y[j]);
+        }
+        if (cm) {
+            for (int e = inc_ptr[i]; e < inc_ptr[i + 1]; e++) {
+                const int s = inc_sub[e];
+                const int ps = sub_ptr[s], m = sub_ptr[s + 1] - ps;
+                const int c0 = colptr[s], nc = colptr[s + 1] - c0;
+                const T* b = V + boff[s] + (inc_pos[e] - ps);
+                for (int q = 0; q < nc; q++) {
+                    const T bv = b[(size_t)q * m];
+                    const T* cr = cm + (size_t)(c0 + q) * K + cl;
+#pragma unroll
+                    for (int j = 0; j < M::CPT; j++) y[j] = fma(bv, cr[M::TPR * j], y[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < M::CPT; j++) {
+            const size_t e = (size_t)i * K + cl + M::TPR * j;
+            Y[e] = Yin ? fma(sign, y[j], Yin[e]) : sign * y[j];
+        }
+    }
+}
+
+// C_s(q, :) = wsign w_q sum_p B_s(p, q) X(idx_s(p), :) for the columns q of
+// subdomain s in chunk blockIdx.y (16 per chunk): 4 warps take every 4th
+// local position, their sums meet in shared memory in a fixed order.
+constexpr int KB_TG_C = 16;
+template <typename T, int K>
+__global__ void __launch_bounds__(128) kb_tgemv(const int* __restrict__ sub_ptr, const int* __restrict__ sub_idx,
+                                                const int* __restrict__ colptr, const int64_t* __restrict__ boff,
+                                                const T* __restrict__ B, const T* __restrict__ X,
+                                                const T* __restrict__ w, T wsign, T* C) {
+    using M = RM<K>;
+    __shared__ T red[4 * M::RPW][KB_TG_C][K];
+    const int s = blockIdx.x, cb = blockIdx.y * KB_TG_C;
+    const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
+    const int c0 = colptr[s], nc = colptr[s + 1] - c0;
+    if (cb >= nc) return;
+    const int kc = min(KB_TG_C, nc - cb);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int rw = lane / M::TPR, cl = lane % M::TPR;
+    T acc[KB_TG_C][M::CPT];
+#pragma unroll
+    for (int q = 0; q < KB_TG_C; q++)
+#pragma unroll
+        for (int j = 0; j < M::CPT; j++) acc[q][j] = 0;
+    const T* Bs = B + boff[s] + (size_t)cb * m;
+    for (int p = wid * M::RPW + rw; p < m; p += 4 * M::RPW) {
+        T x[M::CPT];
+        const T* xr = X + (size_t)sub_idx[p0 + p] * K + cl;
+#pragma unroll
+        for (int j = 0; j < M::CPT; j++) x[j] = xr[M::TPR * j];
+#pragma unroll
+        for (int q = 0; q < KB_TG_C; q++) {
+            if (q < kc) {
+                const T bv = Bs[(size_t)q * m + p];
+#pragma unroll
+                for (int j = 0; j < M::CPT; j++) acc[q][j] = fma(bv, x[j], acc[q][j]);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < KB_TG_C; q++)
+#pragma unroll
+        for (int j = 0; j < M::CPT; j++) red[wid * M::RPW + rw][q][cl + M::TPR * j] = acc[q][j];
+    __syncthreads();
+    for (int e = threadIdx.x; e < kc * K; e += blockDim.x) {
+        const int q = e / K, c = e % K;
+        T v = 0;
+        for (int r = 0; r < 4 * M::RPW; r++) v += red[r][q][c];
+        const int cq = c0 + cb + q;
+        C[(size_t)cq * K + c] = w ? wsign * w[cq] * v : v;
+    }
+}
+
+// Y(i, :) = beta Y(i, :) + alpha sum over the copies (s, p) of i of
+// sum_q B_s(p, q) C(colptr[s] + q, :) + gamma V(i, :) (+ V2(i, :))
+template <typename T, int K>
+__global__ void __launch_bounds__(256) kb_blk_prolong(int n, const int* __restrict__ inc_ptr,
+                                                      const int* __restrict__ inc_pos,
+                                                      const int* __restrict__ inc_sub,
+                                                      const int* __restrict__ sub_ptr,
+                                                      const int* __restrict__ colptr,
+                                                      const int64_t* __restrict__ boff, const T* __restrict__ B,
+                                                      const T* __restrict__ C, T* Y, T alpha, T beta,
+                                                      const T* V, T gamma, const T* V2) {
+    ROW_LOOP(K) {
+        T y[M::CPT] = {};
+        for (int e = inc_ptr[i]; e < inc_ptr[i + 1]; e++) {
+            const int s = inc_sub[e];
+            const int ps = sub_ptr[s], m = sub_ptr[s + 1] - ps;
+            const int c0 = colptr[s], nc = colptr[s + 1] - c0;
+            const T* b = B + boff[s] + (inc_pos[e] - ps);
+            for (int q = 0; q < nc; q++) {
+                const T bv = b[(size_t)q * m];
+                const T* cr = C + (size_t)(c0 + q) * K + cl;
+#pragma unroll
+                for (int j = 0; j < M::CPT; j++) y[j] = fma(bv, cr[M::TPR * j], y[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < M::CPT; j++) {
+            const size_t e = (size_t)i * K + cl + M::TPR * j;
+            T v = alpha * y[j];
+            if (beta != (T)0) v = fma(beta, Y[e], v);
+            if (V) v = fma(gamma, V[e], v);
+            if (V2) v += V2[e];
+            Y[e] = v;
+        }
+    }
+}
+
+// Y(i, :) = beta Y(i, :) + alpha sum over the copies of i of loc(pos, :) + gamma V(i, :)
+template <typename T, int K>
+__global__ void __launch_bounds__(256) kb_prolong(int n, const int* __restrict__ inc_ptr,
+                                                  const int* __restrict__ inc_pos, const T* __restrict__ loc,
+                                                  T* Y, T alpha, T beta, const T* V, T gamma) {
+    ROW_LOOP(K) {
+        T y[M::CPT] = {};
+        for (int e = inc_ptr[i]; e < inc_ptr[i + 1]; e++) {
+            const T* lr = loc + (size_t)inc_pos[e] * K + cl;
+#pragma unroll
+            for (int j = 0; j < M::CPT; j++) y[j] += lr[M::TPR * j];
+        }
+#pragma unroll
+        for (int j = 0; j < M::CPT; j++) {
+            const size_t e = (size_t)i * K + cl + M::TPR * j;
+            T v = alpha * y[j];
+            if (beta != (T)0) v = fma(beta, Y[e], v);
+            if (V) v = fma(gamma, V[e], v);
+            Y[e] = v;
+        }
+    }
+}
+
+// loc(P, :) = X(sub_idx[P], :)
+template <typename T, int K>
+__global__ void kb_gather(int64_t sum_ns, const int* __restrict__ sub_idx, const T* __restrict__ X,
+                          T* __restrict__ loc) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= sum_ns * K) return;
+    const int64_t P = e / K;
+    const int c = (int)(e % K);
+    loc[e] = X[(size_t)sub_idx[P] * K + c];
+}
+
+// out_s = G_s loc_s for every subdomain s: G_s symmetric n^s x n^s stored
+// column-major with leading dimension ld_s (n^s for float64; n^s rounded up
+// to 4, zero padded, for float32), so row r of G_s is read as column r.
+// Each thread owns RT consecutive rows and all K columns (RT * K = 64
+// accumulators): per step q one load of RT values of column q of G_s, the
+// K values of loc_s(q, :) from shared memory (broadcast), RT * K FMAs.
+template <typename T, int K>
+struct LG {
+    static constexpr int RT = 64 / K;            // rows per thread: 4, 2, 1
+    static constexpr int ROWS = 128 * RT;        // rows per 128-thread block
+    static constexpr int JC = 64;                // staged local positions
+};
+
+template <typename T, int RT> struct LoadRT;
+template <> struct LoadRT<float, 1> {
+    __device__ static void ld(const float* p, float* o) { o[0] = __ldcs(p); }
+};
+template <> struct LoadRT<float, 2> {
+    __device__ static void ld(const float* p, float* o) {
+        const float2 v = __ldcs(reinterpret_cast<const float2*>(p));
+        o[0] = v.x; o[1] = v.y;
+    }
+};
+template <> struct LoadRT<float, 4> {
+    __device__ static void ld(const float* p, float* o) {
+        const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+};
+template <int RT> struct LoadRT<double, RT> {
+    __device__ static void ld(const double* p, double* o) {
+#pragma unroll
+        for (int r = 0; r < RT; r++) o[r] = __ldcs(p + r);
+    }
+};
+
+template <typename T, int K>
+__global__ void __launch_bounds__(128) kb_local_gemm(const int* __restrict__ sub_ptr, const int64_t* __restrict__ goff,
+                                                     const T* __restrict__ G, int pad4,
+                                                     const T* __restrict__ loc, T* __restrict__ out) {
+    using L = LG<T, K>;
+    constexpr int RT = L::RT;
+    __shared__ __align__(16) T xs[L::JC][K];
+    const int s = blockIdx.x;
+    const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
+    const int ld = pad4 ? ((m + 3) & ~3) : m;
+    const int r0 = blockIdx.y * L::ROWS;
+    if (r0 >= m) return;
+    const int rb = r0 + threadIdx.x * RT;          // first row of this thread
+    const bool live = rb < m;
+    const T* Gs = G + goff[s] + rb;
+    T acc[RT][K];
+#pragma unroll
+    for (int r = 0; r < RT; r++)
+#pragma unroll
+        for (int c = 0; c < K; c++) acc[r][c] = 0;
+    const T* ls = loc + (size_t)p0 * K;
+    for (int q0 = 0; q0 < m; q0 += L::JC) {
+        const int qn = min(L::JC, m - q0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < qn * K; e += blockDim.x) (&xs[0][0])[e] = ls[(size_t)q0 * K + e];
+        __syncthreads();
+        if (live) {
+            int q = 0;
+            for (; q + 4 <= qn; q += 4) {
+                T g[4][RT];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    if (pad4 || rb + RT <= m) LoadRT<T, RT>::ld(Gs + (size_t)(q0 + q + u) * ld, g[u]);
+                    else
+#pragma unroll
+                        for (int r = 0; r < RT; r++) g[u][r] = (rb + r < m) ? Gs[(size_t)(q0 + q + u) * ld + r] : (T)0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+#pragma unroll
+                    for (int c = 0; c < K; c++) {
+                        const T xv = xs[q + u][c];
+#pragma unroll
+                        for (int r = 0; r < RT; r++) acc[r][c] = fma(g[u][r], xv, acc[r][c]);
+                    }
+            }
+            for (; q < qn; q++) {
+                T g[RT];
+                if (pad4 || rb + RT <= m) LoadRT<T, RT>::ld(Gs + (size_t)(q0 + q) * ld, g);
+                else
+#pragma unroll
+                    for (int r = 0; r < RT; r++) g[r] = (rb + r < m) ? Gs[(size_t)(q0 + q) * ld + r] : (T)0;
+#pragma unroll
+                for (int c = 0; c < K; c++) {
+                    const T xv = xs[q][c];
+#pragma unroll
+                    for (int r = 0; r < RT; r++) acc[r][c] = fma(g[r], xv, acc[r][c]);
+                }
+            }
+        }
+    }
+    if (!live) return;
+#pragma unroll
+    for (int r = 0; r < RT; r++) {
+        if (rb + r >= m) break;
+        T* o = out + (size_t)(p0 + rb + r) * K;
+#pragma unroll
+        for (int c = 0; c < K; c++) o[c] = acc[r][c];
+    }
+}
+
+// Y = alpha M X + beta Sub in float64, M symmetric dim x dim (row p read as
+// column p), X, Y, Sub dim x K row-major: 16 rows per block, 4 columns per
+// thread, 64-wide chunks of M and X staged in shared memory
+constexpr int DG_RB = 16, DG_JC = 64;
+template <int K>
+__global__ void __launch_bounds__(4 * K) kb_dense_gemm(int dim, const double* __restrict__ Mx,
+                                                       const double* __restrict__ X, double* Y, double alpha,
+                                                       const double* Sub, double beta) {
+    __shared__ double ms[DG_RB][DG_JC + 1];
+    __shared__ __align__(16) double xs[DG_JC][K];
+    const int r0 = blockIdx.x * DG_RB;
+    const int cg = threadIdx.x % (K / 4), r = threadIdx.x / (K / 4);
+    double acc[4] = {0, 0, 0, 0};
+    for (int j0 = 0; j0 < dim; j0 += DG_JC) {
+        const int jn = min(DG_JC, dim - j0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < DG_RB * DG_JC; e += blockDim.x) {
+            const int rr = e / DG_JC, jj = e % DG_JC;
+            ms[rr][jj] = (r0 + rr < dim && jj < jn) ? Mx[(size_t)(r0 + rr) * dim + j0 + jj] : 0.0;
+        }
+        for (int e = threadIdx.x; e < DG_JC * K; e += blockDim.x)
+            (&xs[0][0])[e] = (e / K < jn) ? X[(size_t)j0 * K + e] : 0.0;
+        __syncthreads();
+#pragma unroll 4
+        for (int jj = 0; jj < DG_JC; jj++) {
+            const double mv = ms[r][jj];
+            const double2 x01 = *reinterpret_cast<const double2*>(&xs[jj][cg * 4]);
+            const double2 x23 = *reinterpret_cast<const double2*>(&xs[jj][cg * 4 + 2]);
+            acc[0] = fma(mv, x01.x, acc[0]);
+            acc[1] = fma(mv, x01.y, acc[1]);
+            acc[2] = fma(mv, x23.x, acc[2]);
+            acc[3] = fma(mv, x23.y, acc[3]);
+        }
+    }
+    if (r0 + r >= dim) return;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const size_t e = (size_t)(r0 + r) * K + cg * 4 + c;
+        Y[e] = Sub ? fma(beta, Sub[e], alpha * acc[c]) : alpha * acc[c];
+    }
+}
+
+// ------------------------------------------- W passes on the CUDA cores
+template <typename TS> __device__ __forceinline__ typename Acc<TS>::type wval(TS v) {
+    return (typename Acc<TS>::type)v;
+}
+template <> __device__ __forceinline__ float wval<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float wval<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// part[b][c * K + j] = sum over the rows i of row block b of W(i, c) Xs(i, j),
+// Xs = S_r X (rscale) or X; one column of W per thread, 32-row chunks of Xs
+// in shared memory.  Block (b, 0) also stores Xs (for the sparse correction).
+template <typename TS, typename A, int K>
+__global__ void __launch_bounds__(256) kb_wt_partial(int n, int ldw, int rows, const TS* __restrict__ W,
+                                                     const A* __restrict__ X, const float* __restrict__ rscale,
+                                                     A* part, A* xs_out) {
+    __shared__ __align__(16) A xs[32][K];
+    const int i0 = blockIdx.x * rows, i1 = min(n, i0 + rows);
+    const int c = blockIdx.y * 256 + threadIdx.x;
+    A acc[K];
+#pragma unroll
+    for (int j = 0; j < K; j++) acc[j] = 0;
+    for (int ib = i0; ib < i1; ib += 32) {
+        const int nr = min(32, i1 - ib);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nr * K; e += 256) {
+            const int r = e / K;
+            A v = X[(size_t)(ib + r) * K + (e % K)];
+            if (rscale) v *= (A)rscale[ib + r];
+            (&xs[0][0])[e] = v;
+            if (xs_out && blockIdx.y == 0) xs_out[(size_t)ib * K + e] = v;
+        }
+        __syncthreads();
+        if (c < ldw) {
+            for (int r = 0; r < nr; r++) {
+                const A wv = wval<TS>(W[(size_t)(ib + r) * ldw + c]);
+#pragma unroll
+                for (int j = 0; j < K; j++) acc[j] = fma(wv, xs[r][j], acc[j]);
+            }
+        }
+    }
+    if (c < ldw) {
+        A* o = part + ((size_t)blockIdx.x * ldw + c) * K;
+#pragma unroll
+        for (int j = 0; j < K; j++) o[j] = acc[j];
+    }
+}
+
+// out(c, j) = cscale_c (sum_b part[b][c * K + j] + sum_k C_kc Xs(k, j)) in
+// float64 (the input of the F^-1 solve); C is the sparse float32 correction
+// of a float16 W (CSC)
+template <typename A, int K>
+__global__ void kb_wt_reduce(int nb, int ldw, int nm, const A* __restrict__ part, const float* __restrict__ cscale,
+                             const int* __restrict__ ccp, const int* __restrict__ crow,
+                             const float* __restrict__ cval, const A* __restrict__ xs, double* out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nm * K) return;
+    const int c = e / K, j = e % K;
+    A v = 0;
+    for (int b = 0; b < nb; b++) v += part[((size_t)b * ldw + c) * K + j];
+    if (ccp)
+        for (int k = ccp[c]; k < ccp[c + 1]; k++) v = fma((A)cval[k], xs[(size_t)crow[k] * K + j], v);
+    out[e] = cscale ? (double)v * (double)cscale[c] : (double)v;
+}
+
+// Ds(c, j) = cscale_c D(c, j) in the compute type, zero on the padding
+// columns c >= nm (c < ldw)
+template <typename A, int K>
+__global__ void kb_d_scaled(int nm, int ldw, const double* __restrict__ D, const float* __restrict__ cscale, A* Ds) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ldw * K) return;
+    const int c = e / K;
+    Ds[e] = (c < nm) ? (A)(cscale ? D[e] * (double)cscale[c] : D[e]) : (A)0;
+}
+
+// out(i, :) = (V(i, :)) + rscale_i (sum_c W(i, c) Ds(c, :) + sum_k C_ik Ds(col_k, :)):
+// 32 rows of W and 32-column chunks staged in shared memory; thread (r, g)
+// computes row r, columns g*K/8 .. g*K/8 + K/8 - 1.
+template <typename TS, typename A, int K>
+__global__ void __launch_bounds__(256) kb_w_d(int n, int ldw, const TS* __restrict__ W, const A* __restrict__ Ds,
+                                              const float* __restrict__ rscale, const int* __restrict__ crp,
+                                              const int* __restrict__ ccol, const float* __restrict__ cval,
+                                              const A* V, A* out) {
+    constexpr int CG = K / 8, CC = 32;
+    __shared__ A ws[32][CC + 1];
+    __shared__ __align__(16) A dsm[CC][K];
+    const int i0 = blockIdx.x * 32;
+    const int r = threadIdx.x / 8, g = threadIdx.x % 8;
+    A acc[CG];
+#pragma unroll
+    for (int q = 0; q < CG; q++) acc[q] = 0;
+    for (int c0 = 0; c0 < ldw; c0 += CC) {
+        const int cn = min(CC, ldw - c0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * CC; e += 256) {
+            const int rr = e / CC, cc = e % CC;
+            ws[rr][cc] = (i0 + rr < n && cc < cn) ? wval<TS>(W[(size_t)(i0 + rr) * ldw + c0 + cc]) : (A)0;
+        }
+        for (int e = threadIdx.x; e < CC * K; e += 256)
+            (&dsm[0][0])[e] = (e / K < cn) ? Ds[(size_t)c0 * K + e] : (A)0;
+        __syncthreads();
+#pragma unroll 4
+        for (int cc = 0; cc < CC; cc++) {
+            const A wv = ws[r][cc];
+#pragma unroll
+            for (int q = 0; q < CG; q++) acc[q] = fma(wv, dsm[cc][g * CG + q], acc[q]);
+        }
+    }
+    const int i = i0 + r;
+    if (i >= n) return;
+    if (crp)
+        for (int k = crp[i]; k < crp[i + 1]; k++) {
+            const A cv = (A)cval[k];
+            const A* dr = Ds + (size_t)ccol[k] * K + g * CG;
+#pragma unroll
+            for (int q = 0; q < CG; q++) acc[q] = fma(cv, dr[q], acc[q]);
+        }
+    const A sc = rscale ? (A)rscale[i] : (A)1;
+#pragma unroll
+    for (int q = 0; q < CG; q++) {
+        const size_t e = (size_t)i * K + g * CG + q;
+        out[e] = (V ? V[e] : (A)0) + sc * acc[q];
+    }
+}
+
+// ---------------------------------------------- tensor-core operand prep
+// Bt (2K x n, 16-bit, n contiguous, row stride ldb): rows j < K the high part, rows K + j
+// the low part of Xs(:, j) = S_r X(:, j) 2^-e_j, where 2^e_j >= max_i
+// |Xs(i, j)| (a power of two from the column maxima colmax, so the scaled
+// values lie in [-1, 1] and the low parts stay in the normal range of
+// float16 down to 2^-14 of the column maximum)
+__device__ __forceinline__ float pow2_ceil_inv(float mx) {
+    if (!(mx > 0.f)) return 1.f;
+    int e;
+    frexpf(mx, &e);        // mx = f 2^e, f in [0.5, 1)
+    return ldexpf(1.f, -e);
+}
+
+// max |S_r X(:, j)| per column as float bits (non-negative floats order
+// like their bit patterns): block maxima in shared memory, one atomic per
+// block and column
+template <int K>
+__global__ void __launch_bounds__(256) kb_colmax(int n, const float* __restrict__ X, const float* __restrict__ rscale,
+                                                 unsigned* mx) {
+    __shared__ unsigned bm[K];
+    if (threadIdx.x < K) bm[threadIdx.x] = 0u;
+    __syncthreads();
+    float tm[RM<K>::CPT] = {};
+    ROW_LOOP(K) {
+#pragma unroll
+        for (int j = 0; j < M::CPT; j++) {
+            float v = fabsf(X[(size_t)i * K + cl + M::TPR * j]);
+            if (rscale) v *= rscale[i];
+            tm[j] = fmaxf(tm[j], v);
+        }
+    }
+    {
+        const int cl0 = (threadIdx.x & 31) % RM<K>::TPR;
+#pragma unroll
+        for (int j = 0; j < RM<K>::CPT; j++) atomicMax(bm + cl0 + RM<K>::TPR * j, __float_as_uint(tm[j]));
+    }
+    __syncthreads();
+    if (threadIdx.x < K) atomicMax(mx + threadIdx.x, bm[threadIdx.x]);
+}
+
+template <typename H, int K>
+__global__ void kb_split16(int n, int ldb, const float* __restrict__ X, const float* __restrict__ rscale,
+                           const unsigned* __restrict__ mx, H* __restrict__ Bt) {
+    __shared__ float t[32][K + 1];
+    const int i0 = blockIdx.x * 32;
+    for (int e = threadIdx.x; e < 32 * K; e += blockDim.x) {
+        const int r = e / K, c = e % K, i = i0 + r;
+        float v = 0.f;
+        if (i < n) {
+            v = X[(size_t)i * K + c] * pow2_ceil_inv(__uint_as_float(mx[c]));
+            if (rscale) v *= rscale[i];
+        }
+        t[r][c] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * K; e += blockDim.x) {
+        const int c = e / 32, r = e % 32, i = i0 + r;
+        if (i >= n) continue;
+        const float v = t[r][c];
+        H hi, lo;
+        if constexpr (std::is_same<H, __half>::value) {
+            hi = __float2half_rn(v);
+            lo = __float2half_rn(v - __half2float(hi));
+        } else {
+            hi = __float2bfloat16_rn(v);
+            lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+        }
+        Bt[(size_t)c * ldb + i] = hi;
+        Bt[(size_t)(K + c) * ldb + i] = lo;
+    }
+}
+
+// Dt (2K x ldw) from Ds (ldw x K float32, cscale applied, zero padding
+// columns): Ds 2^-f_j split in two 16-bit parts.  One block; also stores 2^f_j.
+template <typename H, int K>
+__global__ void kb_split16_d(int ldw, const float* __restrict__ Ds, H* __restrict__ Dt, float* __restrict__ dscale) {
+    __shared__ unsigned cmx[K];
+    if (threadIdx.x < K) cmx[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int e = threadIdx.x; e < ldw * K; e += blockDim.x) atomicMax(cmx + (e % K), __float_as_uint(fabsf(Ds[e])));
+    __syncthreads();
+    for (int e = threadIdx.x; e < ldw * K; e += blockDim.x) {
+        const int j = e / ldw, c = e % ldw;
+        const float v = Ds[(size_t)c * K + j] * pow2_ceil_inv(__uint_as_float(cmx[j]));
+        H hi, lo;
+        if constexpr (std::is_same<H, __half>::value) {
+            hi = __float2half_rn(v);
+            lo = __float2half_rn(v - __half2float(hi));
+        } else {
+            hi = __float2bfloat16_rn(v);
+            lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+        }
+        Dt[(size_t)j * ldw + c] = hi;
+        Dt[(size_t)(K + j) * ldw + c] = lo;
+    }
+    if (threadIdx.x < K) dscale[threadIdx.x] = 1.f / pow2_ceil_inv(__uint_as_float(cmx[threadIdx.x]));
+}
+
+// out(c, j) = 2^e_j cscale_c (sum_b part[b][c * K + j]) + correction, float64
+template <int K>
+__global__ void kb_wt_reduce_umma(int nb, int ldw, int nm, const float* __restrict__ part,
+                                  const unsigned* __restrict__ mx, const float* __restrict__ cscale,
+                                  const int* __restrict__ ccp, const int* __restrict__ crow,
+                                  const float* __restrict__ cval, const float* __restrict__ X,
+                                  const float* __restrict__ rscale, double* out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nm * K) return;
+    const int c = e / K, j = e % K;
+    float v = 0.f;
+    for (int b = 0; b < nb; b++) v += part[((size_t)b * ldw + c) * K + j];
+    v *= 1.f / pow2_ceil_inv(__uint_as_float(mx[j]));
+    if (ccp)
+        for (int k = ccp[c]; k < ccp[c + 1]; k++) {
+            const int i = crow[k];
+            v = fmaf(cval[k], X[(size_t)i * K + j] * (rscale ? rscale[i] : 1.f), v);
+        }
+    out[e] = cscale ? (double)v * (double)cscale[c] : (double)v;
+}
+
+// out(i, :) = V(i, :) + rscale_i (2^f_j acc(i, j) + sum_k C_ik Ds(col_k, j))
+template <int K>
+__global__ void __launch_bounds__(256) kb_wd_finish_umma(int n, const float* __restrict__ acc,
+                                                         const float* __restrict__ dscale,
+                                                         const float* __restrict__ rscale, const int* __restrict__ crp,
+                                                         const int* __restrict__ ccol, const float* __restrict__ cval,
+                                                         const float* __restrict__ Ds, const float* V, float* out) {
+    ROW_LOOP(K) {
+#pragma unroll
+        for (int j = 0; j < M::CPT; j++) {
+            const int c = cl + M::TPR * j;
+            const size_t e = (size_t)i * K + c;
+            float v = acc[e] * dscale[c];
+            if (crp)
+                for (int k = crp[i]; k < crp[i + 1]; k++) v = fmaf(cval[k], Ds[(size_t)ccol[k] * K + c], v);
+            if (rscale) v *= rscale[i];
+            out[e] = (V ? V[e] : 0.f) + v;
+        }
+    }
+}
+
+// ===================================================================== host
+namespace {
+
+template <typename T>
+struct BView {
+    // preconditioner block vectors (n x K), local arenas (sum_ns x K)
+    T *rin, *x1, *t, *u, *q, *out, *tmpw, *loc, *loc2, *cm, *cf;
+    // coarse vectors, float64 (n0 x K, n_- x K)
+    double *y0, *y2, *c1, *c2, *w0, *dd, *w1, *y0d;
+    // W passes
+    void* part;    // row-block partials (compute type)
+    void* xs;      // S_r X (compute type), n x K
+    void* ds;      // S_c D (compute type), ldw x K
+    void* bt;      // 16-bit split operands: 2K x n
+    void* dt;      //                        2K x ldw
+    float* wacc;   // tensor-core W d accumulators, n x K
+    float* dscale;
+    unsigned* mx;  // column maxima (float bits)
+    int* err;
+    // PCG (float64, n x K)
+    double *pb, *px, *pr, *pp, *pq, *pz;
+    double *sc, *red;
+    unsigned* cnt;
+};
+
+constexpr int WT_SPLITS_MAX = 64;
+
+size_t carve_block(const Handle* h, char* base, BView<double>* vd, BView<float>* vf) {
+    // one layout serves both element types: every region is sized for the
+    // float64 form (the float32 form uses the first half of each)
+    char* p = base;
+    auto take = [&](size_t bytes) { char* r = p; p += (bytes + 255) / 256 * 256; return r; };
+    const size_t K = BLK_KMAX;
+    const size_t n = h->n, n0 = std::max(1, h->n0), nm = std::max(1, h->n_minus);
+    const size_t ldw = std::max(8, h->ldw);
+    BView<double> d{};
+    d.rin = (double*)take(n * K * 8); d.x1 = (double*)take(n * K * 8); d.t = (double*)take(n * K * 8);
+    d.u = (double*)take(n * K * 8); d.q = (double*)take(n * K * 8); d.out = (double*)take(n * K * 8);
+    d.tmpw = (double*)take(n * K * 8);
+    d.loc = (double*)take((size_t)h->sum_ns * K * 8); d.loc2 = (double*)take((size_t)h->sum_ns * K * 8);
+    d.cm = (double*)take((size_t)std::max(1, h->n_minus_all) * K * 8);
+    d.cf = (double*)take(std::max(n0, nm) * K * 8);
+    d.y0 = (double*)take(n0 * K * 8); d.y2 = (double*)take(n0 * K * 8); d.c1 = (double*)take(n0 * K * 8);
+    d.c2 = (double*)take(n0 * K * 8); d.y0d = (double*)take(std::max(n0, nm) * K * 8);
+    d.w0 = (double*)take(nm * K * 8); d.dd = (double*)take(nm * K * 8); d.w1 = (double*)take(nm * K * 8);
+    d.part = take((size_t)WT_SPLITS_MAX * ldw * K * 8);
+    d.xs = take(n * K * 8);
+    d.ds = take(ldw * K * 8);
+    d.bt = take(2 * K * ((n + 63) / 64 * 64) * 2);
+    d.dt = take(2 * K * ldw * 2);
+    d.wacc = (float*)take(n * K * 4);
+    d.dscale = (float*)take(K * 4);
+    d.mx = (unsigned*)take(K * 4);
+    d.err = (int*)take(64);
+    d.pb = (double*)take(n * K * 8); d.px = (double*)take(n * K * 8); d.pr = (double*)take(n * K * 8);
+    d.pp = (double*)take(n * K * 8); d.pq = (double*)take(n * K * 8); d.pz = (double*)take(n * K * 8);
+    d.sc = (double*)take(B_NSC * K * 8);
+    d.red = (double*)take((size_t)1216 * K * 8);
+    d.cnt = (unsigned*)take(64);
+    if (vd) *vd = d;
+    if (vf) {
+        BView<float> f{};
+        f.rin = (float*)d.rin; f.x1 = (float*)d.x1; f.t = (float*)d.t; f.u = (float*)d.u; f.q = (float*)d.q;
+        f.out = (float*)d.out; f.tmpw = (float*)d.tmpw; f.loc = (float*)d.loc; f.loc2 = (float*)d.loc2;
+        f.cm = (float*)d.cm; f.cf = (float*)d.cf;
+        f.y0 = d.y0; f.y2 = d.y2; f.c1 = d.c1; f.c2 = d.c2; f.y0d = d.y0d; f.w0 = d.w0; f.dd = d.dd; f.w1 = d.w1;
+        f.part = d.part; f.xs = d.xs; f.ds = d.ds; f.bt = d.bt; f.dt = d.dt; f.wacc = d.wacc;
+        f.dscale = d.dscale; f.mx = d.mx; f.err = d.err;
+        f.pb = d.pb; f.px = d.px; f.pr = d.pr; f.pp = d.pp; f.pq = d.pq; f.pz = d.pz;
+        f.sc = d.sc; f.red = d.red; f.cnt = d.cnt;
+        *vf = f;
+    }
+    return (size_t)(p - base);
+}
+
+template <typename T> T* fl(const DevBuf& d64, const DevBuf& d32);
+template <> double* fl<double>(const DevBuf& d64, const DevBuf&) { return (double*)d64.p; }
+template <> float* fl<float>(const DevBuf&, const DevBuf& d32) { return (float*)d32.p; }
+
+int grid_rows(int n, int rpb) { return std::max(1, std::min((n + rpb - 1) / rpb, 152 * 8)); }
+
+}  // namespace
+
+// Float32 copies of the small operators the float32 block apply reads (A's
+// values, V^s_-, |Lambda^s_-|, Z), the workspace, and the side stream's
+// error word: built on the first block call of a handle.
+awg_status block_prepare(Handle* h) {
+    if (h->bws.p) return AWG_OK;
+    cudaStream_t s = h->stream;
+    auto cvt = [&](DevBuf& dst, const DevBuf& src, size_t len, bool neg) -> awg_status {
+        AWG_TRY(dalloc(h, dst, std::max<size_t>(len, 1) * 4));
+        if (len == 0) return AWG_OK;
+        std::vector<double> hv(len);
+        std::vector<float> fv(len);
+        AWG_CUDA(cudaMemcpy(hv.data(), src.p, len * 8, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < len; i++) fv[i] = (float)(neg ? -hv[i] : hv[i]);
+        AWG_CUDA(cudaMemcpy(dst.p, fv.data(), len * 4, cudaMemcpyHostToDevice));
+        return AWG_OK;
+    };
+    AWG_TRY(cvt(h->bval32, h->val, (size_t)h->nnz, false));
+    AWG_TRY(cvt(h->bvm32, h->Vm, (size_t)(h->h_vm_off.empty() ? 0 : h->h_vm_off[h->N]), false));
+    AWG_TRY(cvt(h->blam32, h->lam_m, (size_t)h->n_minus_all, true));   // |Lambda_-| = -Lambda_-
+    AWG_TRY(dalloc(h, h->blam64, (size_t)std::max(1, h->n_minus_all) * 8));
+    if (h->n_minus_all > 0) {
+        std::vector<double> hv(h->n_minus_all);
+        AWG_CUDA(cudaMemcpy(hv.data(), h->lam_m.p, hv.size() * 8, cudaMemcpyDeviceToHost));
+        for (double& v : hv) v = -v;
+        AWG_CUDA(cudaMemcpy(h->blam64.p, hv.data(), hv.size() * 8, cudaMemcpyHostToDevice));
+    }
+    AWG_TRY(cvt(h->bz32, h->Z, (size_t)(h->h_z_off.empty() ? 0 : h->h_z_off[h->N]), false));
+    const size_t bytes = carve_block(h, nullptr, nullptr, nullptr);
+    AWG_TRY(dalloc(h, h->bws, bytes));
+    AWG_CUDA(cudaMemset(h->bws.p, 0, bytes));
+    (void)s;
+    return AWG_OK;
+}
+
+namespace {
+
+template <typename T, int K>
+struct BlockApply {
+    Handle* h;
+    BView<T> v;
+    using A = T;
+
+    static dim3 rows_grid(int n) { return dim3(grid_rows(n, RM<K>::RPB)); }
+
+    const T* aval() const { return fl<T>(h->val, h->bval32); }
+    const T* vm() const { return fl<T>(h->Vm, h->bvm32); }
+    const T* lam() const { return fl<T>(h->blam64, h->blam32); }
+    const T* zb() const { return fl<T>(h->Z, h->bz32); }
+
+    awg_status cvt_d2t(const double* a, T* b, size_t len, cudaStream_t s) {
+        if (len == 0) return AWG_OK;
+        kb_cvt<double, T><<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, a, b);
+        AWG_LAUNCH();
+        return AWG_OK;
+    }
+    awg_status cvt_t2d(const T* a, double* b, size_t len, cudaStream_t s) {
+        if (len == 0) return AWG_OK;
+        kb_cvt<T, double><<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, a, b);
+        AWG_LAUNCH();
+        return AWG_OK;
+    }
+
+    // C = wsign w .* (B^T X) per subdomain
+    awg_status tgemv(const int* colptr, const int64_t* boff, const T* B, int maxc, const T* X, const T* w,
+                     T wsign, T* C, cudaStream_t s) {
+        if (maxc == 0) return AWG_OK;
+        ProfScope ps_(h, AWG_PROF_SUBDOMAIN, s);
+        const dim3 g(h->N, (maxc + KB_TG_C - 1) / KB_TG_C);
+        kb_tgemv<T, K><<<g, 128, 0, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p, colptr, boff, B, X, w, wsign, C);
+        AWG_LAUNCH();
+        return AWG_OK;
+    }
+
+    // Y = Yin + sign A_+ X
+    awg_status aplus(const T* X, T* Y, const T* Yin, T sign, cudaStream_t s) {
+        const bool vmb = h->n_minus_all > 0;
+        if (vmb) {
+            const int maxc = *std::max_element(h->h_nm.begin(), h->h_nm.end());
+            AWG_TRY(tgemv((int*)h->nm_ptr.p, (int64_t*)h->vm_off.p, vm(), maxc, X, lam(), (T)1, v.cm, s));
+        }
+        ProfScope ps_(h, AWG_PROF_SPMV, s);
+        kb_aplus<T, K><<<rows_grid(h->n), 256, 0, s>>>(
+            h->n, (int*)h->rowptr.p, (int*)h->colidx.p, aval(), X, (int*)h->inc_ptr.p, (int*)h->inc_pos.p,
+            (int*)h->inc_sub.p, (int*)h->sub_ptr.p, (int*)h->nm_ptr.p, (int64_t*)h->vm_off.p, vm(),
+            vmb ? v.cm : nullptr, Yin, sign, Y);
+        AWG_LAUNCH();
+        return AWG_OK;
+    }
+
+    // c (float64, n0 x K) = Z^T X
+    awg_status zt(const T* X, double* c, cudaStream_t s) {
+        const int maxc = *std::max_element(h->h_modes.begin(), h->h_modes.end());
+        if constexpr (std::is_same<T, double>::value) {
+            return tgemv((int*)h->mode_ptr.p, (int64_t*)h->z_off.p, zb(), maxc, X, nullptr, (T)1, c, s);
+        } else {
+            AWG_TRY(tgemv((int*)h->mode_ptr.p, (int64_t*)h->z_off.p, zb(), maxc, X, nullptr, (T)1, v.cf, s));
+            return cvt_t2d(v.cf, c, (size_t)h->n0 * K, s);
+        }
+    }
+
+    // Y = beta Y + alpha Z c + gamma V (+ V2), c float64
+    awg_status zc(const double* c, T* Y, T alpha, T beta, const T* V, T gamma, const T* V2, cudaStream_t s) {
+        const T* cc;
+        if constexpr (std::is_same<T, double>::value) {
+            cc = c;
+        } else {
+            AWG_TRY(cvt_d2t(c, v.cf, (size_t)h->n0 * K, s));
+            cc = v.cf;
+        }
+        ProfScope ps_(h, AWG_PROF_PROLONG, s);
+        kb_blk_prolong<T, K><<<rows_grid(h->n), 256, 0, s>>>(
+            h->n, (int*)h->inc_ptr.p, (int*)h->inc_pos.p, (int*)h->inc_sub.p, (int*)h->sub_ptr.p,
+            (int*)h->mode_ptr.p, (int64_t*)h->z_off.p, zb(), cc, Y, alpha, beta, V, gamma, V2);
+        AWG_LAUNCH();
+        return AWG_OK;
+    }
+
+    awg_status dense(int dim, const double* Mx, const double* X, double* Y, double alpha, const double* Sub,
+                     double beta, cudaStream_t s) {
+        if (dim == 0) return AWG_OK;
+        ProfScope ps_(h, AWG_PROF_COARSE, s);
+        kb_dense_gemm<K><<<(dim + DG_RB - 1) / DG_RB, 4 * K, 0, s>>>(dim, Mx, X, Y, alpha, Sub, beta);
+        AWG_LAUNCH();
+        return AWG_OK;
+    }
+
+    // Y = H^NN X
+    awg_status hnn(int prec, const T* X, T* Y, cudaStream_t s) {
+        {
+            ProfScope ps_(h, AWG_PROF_PROLONG, s);
+            const int64_t len = h->sum_ns * K;
+            kb_gather<T, K><<<(unsigned)((len + 255) / 256), 256, 0, s>>>(h->sum_ns, (int*)h->sub_idx.p, X, v.loc);
+        }
+        AWG_LAUNCH();
+        {
+            ProfScope ps_(h, AWG_PROF_LOCAL, s);
+            const dim3 g(h->N, (h->max_ns + LG<T, K>::ROWS - 1) / LG<T, K>::ROWS);
+            if constexpr (std::is_same<T, double>::value) {
+                kb_local_gemm<double, K><<<g, 128, 0, s>>>((int*)h->sub_ptr.p, (int64_t*)h->dense_off.p,
+                                                           (double*)h->prec[AWG_FP64].G.p, 0, v.loc, v.loc2);
+            } else {
+                (void)prec;
+                kb_local_gemm<float, K><<<g, 128, 0, s>>>((int*)h->sub_ptr.p, (int64_t*)h->g32_off.p,
+                                                          (float*)h->prec[AWG_MIXED_FP32].G.p, 1, v.loc, v.loc2);
+            }
+        }
+        AWG_LAUNCH();
+        ProfScope ps_(h, AWG_PROF_PROLONG, s);
+        kb_prolong<T, K><<<rows_grid(h->n), 256, 0, s>>>(h->n, (int*)h->inc_ptr.p, (int*)h->inc_pos.p, v.loc2, Y,
+                                                        (T)1, (T)0, nullptr, (T)0);
+        AWG_LAUNCH();
+        return AWG_OK;
+    }
+
+    // Y = H_2 X (+ V2 after the event `wait`)
+    awg_status h2(int prec, const T* X, T* Y, cudaStream_t s, const T* V2 = nullptr, cudaEvent_t wait = nullptr) {
+        if (h->n0 == 0) {
+            AWG_TRY(hnn(prec, X, Y, s));
+            if (V2) {
+                if (wait) AWG_CUDA(cudaStreamWaitEvent(s, wait, 0));
+                ProfScope ps_(h, AWG_PROF_VECTOR, s);
+                const size_t len = (size_t)h->n * K;
+                kb_add<T><<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, V2, Y);
+                AWG_LAUNCH();
+            }
+            return AWG_OK;
+        }
+        const int n0 = h->n0;
+        AWG_TRY(zt(X, v.y0, s));                                                   // y0 = Z^T X
+        AWG_TRY(dense(n0, (double*)h->Einv.p, v.y0, v.c1, 1.0, nullptr, 0.0, s));  // c1 = E^-1 y0
+        AWG_TRY(zc(v.c1, v.x1, (T)1, (T)0, nullptr, (T)0, nullptr, s));            // x1 = Z c1
+        AWG_TRY(aplus(v.x1, v.t, X, (T)-1, s));                                    // t = X - A_+ x1
+        AWG_TRY(hnn(prec, v.t, v.u, s));                                           // u = H^NN t
+        AWG_TRY(aplus(v.u, v.q, nullptr, (T)1, s));                                // q = A_+ u
+        AWG_TRY(zt(v.q, v.y2, s));
+        AWG_TRY(dense(n0, (double*)h->Einv.p, v.y2, v.c2, 1.0, v.c1, -1.0, s));    // c2 = E^-1 y2 - c1
+        if (wait) AWG_CUDA(cudaStreamWaitEvent(s, wait, 0));
+        return zc(v.c2, Y, (T)-1, (T)0, v.u, (T)1, V2, s);                         // Y = u - Z c2 (+ V2)
+    }
+
+    // w0 (float64, n_- x K) = W^T X
+    awg_status wt(int prec, const T* X, double* w0, cudaStream_t s) {
+        const PrecOps& P = h->prec[prec];
+        const int n = h->n, ldw = h->ldw, nm = h->n_minus;
+        const bool cor = P.corr_nnz > 0;
+        const float* rsc = (const float*)P.rscale.p;
+        const float* csc = (const float*)P.cscale.p;
+        if constexpr (std::is_same<T, float>::value) {
+            if ((prec == AWG_MIXED_FP16 || prec == AWG_MIXED_BF16) && h->opt.block_tensor_cores &&
+                umma_available()) {
+                const unsigned gr = grid_rows(n, RM<K>::RPB);
+                {
+                    ProfScope ps_(h, AWG_PROF_VECTOR, s);
+                    AWG_CUDA(cudaMemsetAsync(v.mx, 0, K * 4, s));
+                    kb_colmax<K><<<gr, 256, 0, s>>>(n, X, rsc, v.mx);
+                    AWG_LAUNCH();
+                    if (prec == AWG_MIXED_FP16)
+                        kb_split16<__half, K><<<(n + 31) / 32, 256, 0, s>>>(n, ldb(), X, rsc, v.mx, (__half*)v.bt);
+                    else
+                        kb_split16<__nv_bfloat16, K><<<(n + 31) / 32, 256, 0, s>>>(n, ldb(), X, rsc, v.mx,
+                                                                                  (__nv_bfloat16*)v.bt);
+                    AWG_LAUNCH();
+                }
+                UmmaW u;
+                u.W = P.W.p; u.n = n; u.ldw = ldw; u.nm = nm; u.bf16 = (prec == AWG_MIXED_BF16);
+                const int splits = wt_splits();
+                {
+                    ProfScope ps_(h, AWG_PROF_WT, s);
+                    AWG_TRY(umma_wt(u, K, v.bt, ldb(), (float*)v.part, splits, v.err, s));
+                }
+                ProfScope ps_(h, AWG_PROF_VECTOR, s);
+                kb_wt_reduce_umma<K><<<(nm * K + 255) / 256, 256, 0, s>>>(
+                    splits, ldw, nm, (float*)v.part, v.mx, csc, cor ? (int*)P.corr_colptr.p : nullptr,
+                    cor ? (int*)P.corr_row.p : nullptr, cor ? (float*)P.corr_cval.p : nullptr, X, rsc, w0);
+                AWG_LAUNCH();
+                return AWG_OK;
+            }
+        }
+        const int rb = std::max(1, std::min(WT_SPLITS_MAX, (n + 2047) / 2048));
+        const int rows = (n + rb - 1) / rb;
+        const dim3 g(rb, (ldw + 255) / 256);
+        {
+            ProfScope ps_(h, AWG_PROF_WT, s);
+            if constexpr (std::is_same<T, double>::value) {
+                kb_wt_partial<double, double, K><<<g, 256, 0, s>>>(n, ldw, rows, (const double*)P.W.p, X, nullptr,
+                                                                  (double*)v.part, nullptr);
+            } else {
+                float* xo = cor ? (float*)v.xs : nullptr;
+                if (prec == AWG_MIXED_FP32)
+                    kb_wt_partial<float, float, K><<<g, 256, 0, s>>>(n, ldw, rows, (const float*)P.W.p, X, rsc,
+                                                                    (float*)v.part, xo);
+                else if (prec == AWG_MIXED_FP16)
+                    kb_wt_partial<__half, float, K><<<g, 256, 0, s>>>(n, ldw, rows, (const __half*)P.W.p, X, rsc,
+                                                                     (float*)v.part, xo);
+                else
+                    kb_wt_partial<__nv_bfloat16, float, K><<<g, 256, 0, s>>>(
+                        n, ldw, rows, (const __nv_bfloat16*)P.W.p, X, rsc, (float*)v.part, xo);
+            }
+        }
+        AWG_LAUNCH();
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        kb_wt_reduce<A, K><<<(nm * K + 255) / 256, 256, 0, s>>>(
+            rb, ldw, nm, (const A*)v.part, csc, cor ? (int*)P.corr_colptr.p : nullptr,
+            cor ? (int*)P.corr_row.p : nullptr, cor ? (float*)P.corr_cval.p : nullptr, (const A*)v.xs, w0);
+        AWG_LAUNCH();
+        return AWG_OK;
+    }
+
+    int ldb() const { return (h->n + 63) / 64 * 64; }
+
+    int wt_splits() const {
+        // about two CTAs per SM over the 128-column tiles of W
+        const int tiles = (h->ldw + 127) / 128;
+        return umma_wt_splits(h->n, std::max(1, std::min(WT_SPLITS_MAX, (2 * 152 + tiles - 1) / tiles)));
+    }
+
+    // out = W d (+ V), d float64 n_- x K
+    awg_status wd(int prec, const double* d, T* out, const T* V, cudaStream_t s) {
+        const PrecOps& P = h->prec[prec];
+        const int n = h->n, ldw = h->ldw, nm = h->n_minus;
+        const bool cor = P.corr_nnz > 0;
+        const float* rsc = (const float*)P.rscale.p;
+        const float* csc = (const float*)P.cscale.p;
+        if constexpr (std::is_same<T, float>::value) {
+            if ((prec == AWG_MIXED_FP16 || prec == AWG_MIXED_BF16) && h->opt.block_tensor_cores &&
+                umma_available()) {
+                {
+                    ProfScope ps_(h, AWG_PROF_VECTOR, s);
+                    kb_d_scaled<float, K><<<(ldw * K + 255) / 256, 256, 0, s>>>(nm, ldw, d, csc, (float*)v.ds);
+                    AWG_LAUNCH();
+                    if (prec == AWG_MIXED_FP16)
+                        kb_split16_d<__half, K><<<1, 1024, 0, s>>>(ldw, (float*)v.ds, (__half*)v.dt, v.dscale);
+                    else
+                        kb_split16_d<__nv_bfloat16, K><<<1, 1024, 0, s>>>(ldw, (float*)v.ds, (__nv_bfloat16*)v.dt,
+                                                                         v.dscale);
+                    AWG_LAUNCH();
+                }
+                UmmaW u;
+                u.W = P.W.p; u.n = n; u.ldw = ldw; u.nm = nm; u.bf16 = (prec == AWG_MIXED_BF16);
+                {
+                    ProfScope ps_(h, AWG_PROF_WD, s);
+                    AWG_TRY(umma_wd(u, K, v.dt, v.wacc, v.err, s));
+                }
+                ProfScope ps_(h, AWG_PROF_VECTOR, s);
+                kb_wd_finish_umma<K><<<grid_rows(n, RM<K>::RPB), 256, 0, s>>>(
+                    n, v.wacc, v.dscale, rsc, cor ? (int*)P.corr_rowptr.p : nullptr,
+                    cor ? (int*)P.corr_col.p : nullptr, cor ? (float*)P.corr_val.p : nullptr, (float*)v.ds, V, out);
+                AWG_LAUNCH();
+                return AWG_OK;
+            }
+        }
+        {
+            ProfScope ps_(h, AWG_PROF_VECTOR, s);
+            kb_d_scaled<A, K><<<(ldw * K + 255) / 256, 256, 0, s>>>(nm, ldw, d, csc, (A*)v.ds);
+            AWG_LAUNCH();
+        }
+        ProfScope ps_(h, AWG_PROF_WD, s);
+        const unsigned g = (n + 31) / 32;
+        const int* crp = cor ? (int*)P.corr_rowptr.p : nullptr;
+        const int* ccol = cor ? (int*)P.corr_col.p : nullptr;
+        const float* cval = cor ? (float*)P.corr_val.p : nullptr;
+        if constexpr (std::is_same<T, double>::value) {
+            kb_w_d<double, double, K><<<g, 256, 0, s>>>(n, ldw, (const double*)P.W.p, (const double*)v.ds, nullptr,
+                                                        nullptr, nullptr, nullptr, V, out);
+        } else {
+            if (prec == AWG_MIXED_FP32)
+                kb_w_d<float, float, K><<<g, 256, 0, s>>>(n, ldw, (const float*)P.W.p, (const float*)v.ds, rsc, crp,
+                                                          ccol, cval, V, out);
+            else if (prec == AWG_MIXED_FP16)
+                kb_w_d<__half, float, K><<<g, 256, 0, s>>>(n, ldw, (const __half*)P.W.p, (const float*)v.ds, rsc,
+                                                           crp, ccol, cval, V, out);
+            else
+                kb_w_d<__nv_bfloat16, float, K><<<g, 256, 0, s>>>(n, ldw, (const __nv_bfloat16*)P.W.p,
+                                                                  (const float*)v.ds, rsc, crp, ccol, cval, V, out);
+        }
+        AWG_LAUNCH();
+        return AWG_OK;
+    }
+
+    // Y = stage(X) on preconditioner block vectors (X may be v.rin)
+    awg_status stage(int which, int prec, const T* X, T* Y, cudaStream_t s) {
+        switch (which) {
+            case 0: {
+                ProfScope ps_(h, AWG_PROF_SPMV, s);
+                kb_aplus<T, K><<<rows_grid(h->n), 256, 0, s>>>(
+                    h->n, (int*)h->rowptr.p, (int*)h->colidx.p, aval(), X, nullptr, nullptr, nullptr, nullptr,
+                    nullptr, nullptr, nullptr, nullptr, nullptr, (T)1, Y);
+                AWG_LAUNCH();
+                return AWG_OK;
+            }
+            case 1: return aplus(X, Y, nullptr, (T)1, s);
+            case 2: return hnn(prec, X, Y, s);
+            case 3: return h2(prec, X, Y, s);
+            case 4: {  // H_3,ad = H_2 + W F^-1 W^T (Def. 10); the W branch on the side stream
+                if (h->n_minus == 0) return h2(prec, X, Y, s);
+                AWG_CUDA(cudaEventRecord(h->ev_fork, s));
+                AWG_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+                AWG_TRY(wt(prec, X, v.w0, h->side));
+                AWG_TRY(dense(h->n_minus, (double*)h->prec[prec].Finv.p, v.w0, v.dd, 1.0, nullptr, 0.0, h->side));
+                AWG_TRY(wd(prec, v.dd, v.tmpw, nullptr, h->side));
+                AWG_CUDA(cudaEventRecord(h->ev_join, h->side));
+                return h2(prec, X, Y, s, v.tmpw, h->ev_join);
+            }
+            default: return AWG_ERR_INVALID_ARG;
+        }
+    }
+
+    // float64 in, float64 out (row-major n x K): conversions around the
+    // float32 internal vectors of the mixed forms
+    awg_status apply64(int which, int prec, const double* X, double* Y, cudaStream_t s) {
+        if constexpr (std::is_same<T, double>::value) {
+            return stage(which, prec, X, Y, s);
+        } else {
+            const size_t len = (size_t)h->n * K;
+            {
+                ProfScope ps_(h, AWG_PROF_VECTOR, s);
+                AWG_TRY(cvt_d2t(X, v.rin, len, s));
+            }
+            AWG_TRY(stage(which, prec, v.rin, v.out, s));
+            ProfScope ps_(h, AWG_PROF_VECTOR, s);
+            return cvt_t2d(v.out, Y, len, s);
+        }
+    }
+};
+
+template <int K>
+awg_status apply64_k(Handle* h, int which, int prec, const double* X, double* Y, cudaStream_t s) {
+    if (prec == AWG_FP64) {
+        BlockApply<double, K> b{h, {}};
+        carve_block(h, (char*)h->bws.p, &b.v, nullptr);
+        return b.apply64(which, prec, X, Y, s);
+    }
+    BlockApply<float, K> b{h, {}};
+    carve_block(h, (char*)h->bws.p, nullptr, &b.v);
+    return b.apply64(which, prec, X, Y, s);
+}
+
+awg_status apply64_any(Handle* h, int K, int which, int prec, const double* X, double* Y, cudaStream_t s) {
+    if (K == 16) return apply64_k<16>(h, which, prec, X, Y, s);
+    if (K == 32) return apply64_k<32>(h, which, prec, X, Y, s);
+    return apply64_k<64>(h, which, prec, X, Y, s);
+}
+
+int pick_k(int nrhs) { return nrhs <= 16 ? 16 : (nrhs <= 32 ? 32 : 64); }
+
+template <int K>
+awg_status pcg_k(Handle* h, int prec, const double* b, double* x, int nrhs, int ld, double rtol, int* iters,
+                 double* relres, cudaStream_t s) {
+    BView<double> v;
+    carve_block(h, (char*)h->bws.p, &v, nullptr);
+    const int n = h->n;
+    const dim3 tg((n + 31) / 32, (K + 31) / 32), tb(32, 8);
+    const unsigned gr = grid_rows(n, RM<K>::RPB);
+    double* sc = v.sc;
+    const size_t len = (size_t)n * K;
+    auto prof_vec = [&](auto&& f) -> awg_status {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        f();
+        AWG_LAUNCH();
+        return AWG_OK;
+    };
+    AWG_TRY(prof_vec([&] { kb_from_cols<double><<<tg, tb, 0, s>>>(n, nrhs, ld, K, b, v.pb); }));
+    AWG_CUDA(cudaMemsetAsync(v.px, 0, len * 8, s));
+    AWG_CUDA(cudaMemcpyAsync(v.pr, v.pb, len * 8, cudaMemcpyDeviceToDevice, s));
+    AWG_TRY(prof_vec([&] { kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pb, v.pb, v.red, v.cnt, sc + B_BB * K); }));
+    AWG_TRY(apply64_any(h, K, 4, prec, v.pr, v.pz, s));
+    AWG_TRY(prof_vec([&] { kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, sc + B_RZ * K); }));
+    AWG_CUDA(cudaMemcpyAsync(v.pp, v.pz, len * 8, cudaMemcpyDeviceToDevice, s));
+    std::vector<double> hs(B_NSC * K);
+    AWG_CUDA(cudaMemcpyAsync(hs.data(), sc, B_NSC * K * 8, cudaMemcpyDeviceToHost, s));
+    AWG_CUDA(cudaStreamSynchronize(s));
+    std::vector<double> bnorm(K), act(K, 0.0), rel(K, 1.0), trel(K, -1.0);
+    std::vector<int> its(K, 0);
+    int nact = 0;
+    for (int c = 0; c < K; c++) {
+        bnorm[c] = sqrt(hs[B_BB * K + c]);
+        if (c < nrhs && bnorm[c] > 0.0) { act[c] = 1.0; nact++; }
+        else trel[c] = 0.0;
+    }
+    awg_status st = AWG_OK;
+    int it = 0;
+    auto upload_act = [&]() -> awg_status {
+        AWG_CUDA(cudaMemcpyAsync(sc + B_ACT * K, act.data(), K * 8, cudaMemcpyHostToDevice, s));
+        return AWG_OK;
+    };
+    AWG_TRY(upload_act());
+    auto true_resid = [&]() -> awg_status {
+        AWG_TRY(prof_vec([&] {
+            kb_resid<K><<<gr, 256, 0, s>>>(n, (int*)h->rowptr.p, (int*)h->colidx.p, (double*)h->val.p, v.pb, v.px,
+                                           v.pq);
+        }));
+        AWG_TRY(prof_vec([&] { kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pq, v.pq, v.red, v.cnt, sc + B_TR * K); }));
+        AWG_CUDA(cudaMemcpyAsync(hs.data() + B_TR * K, sc + B_TR * K, K * 8, cudaMemcpyDeviceToHost, s));
+        AWG_CUDA(cudaStreamSynchronize(s));
+        return AWG_OK;
+    };
+    while (nact > 0) {
+        if (it >= h->opt.maxit) { st = AWG_ERR_MAXIT; break; }
+        {
+            ProfScope ps_(h, AWG_PROF_SPMV, s);
+            kb_spmv_dot<K><<<gr, 256, 0, s>>>(n, (int*)h->rowptr.p, (int*)h->colidx.p, (double*)h->val.p, v.pp, v.pq,
+                                              v.red, v.cnt, sc + B_PQ * K);
+        }
+        AWG_LAUNCH();
+        AWG_TRY(prof_vec([&] { kb_pcg_xr<K><<<gr, 256, 0, s>>>(n, sc, v.pp, v.pq, v.px, v.pr, v.red, v.cnt); }));
+        it++;
+        AWG_CUDA(cudaMemcpyAsync(hs.data(), sc, 3 * K * 8, cudaMemcpyDeviceToHost, s));
+        AWG_CUDA(cudaStreamSynchronize(s));
+        bool cand = false, changed = false;
+        for (int c = 0; c < K; c++) {
+            if (act[c] == 0.0) continue;
+            const double pq = hs[B_PQ * K + c];
+            if (!(pq > 0.0) || !std::isfinite(pq)) {
+                act[c] = 0.0; nact--; changed = true; its[c] = it; st = AWG_ERR_BREAKDOWN;
+                continue;
+            }
+            rel[c] = sqrt(hs[B_RR * K + c]) / bnorm[c];
+            if (rel[c] <= rtol) cand = true;
+        }
+        if (cand) {
+            AWG_TRY(true_resid());
+            for (int c = 0; c < K; c++) {
+                if (act[c] == 0.0 || rel[c] > rtol) continue;
+                const double tr = sqrt(hs[B_TR * K + c]) / bnorm[c];
+                if (tr <= rtol || rel[c] <= 1e-6 * rtol) {
+                    if (tr > rtol) st = AWG_ERR_MAXIT;
+                    act[c] = 0.0; nact--; changed = true; its[c] = it; trel[c] = tr;
+                }
+            }
+        }
+        if (nact == 0) break;
+        if (changed) AWG_TRY(upload_act());
+        AWG_TRY(apply64_any(h, K, 4, prec, v.pr, v.pz, s));
+        AWG_TRY(prof_vec([&] { kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, sc + B_RZN * K); }));
+        AWG_TRY(prof_vec([&] { kb_pcg_p<K><<<gr, 256, 0, s>>>(n, sc, v.pz, v.pp, v.cnt); }));
+    }
+    bool need = false;
+    for (int c = 0; c < nrhs; c++)
+        if (trel[c] < 0.0) { need = true; its[c] = it; }
+    if (need) {
+        AWG_TRY(true_resid());
+        for (int c = 0; c < nrhs; c++)
+            if (trel[c] < 0.0) trel[c] = sqrt(hs[B_TR * K + c]) / bnorm[c];
+    }
+    AWG_TRY(prof_vec([&] { kb_to_cols<double><<<tg, tb, 0, s>>>(n, nrhs, ld, K, v.px, x); }));
+    AWG_CUDA(cudaStreamSynchronize(s));
+    int herr = 0;
+    AWG_CUDA(cudaMemcpy(&herr, v.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) {
+        fprintf(stderr, "libawg: tensor-core W pass reported error %d\n", herr);
+        AWG_CUDA(cudaMemset(v.err, 0, sizeof(int)));
+        return AWG_ERR_CUDA;
+    }
+    for (int c = 0; c < nrhs; c++) {
+        if (iters) iters[c] = its[c];
+        if (relres) relres[c] = trel[c];
+    }
+    return st;
+}
+
+}  // namespace
+
+awg_status block_apply(Handle* h, int which, int prec, const double* x, double* y, int nrhs, int ld,
+                       cudaStream_t s) {
+    if (nrhs < 1 || nrhs > BLK_KMAX) return AWG_ERR_INVALID_ARG;
+    AWG_TRY(block_prepare(h));
+    const int K = pick_k(nrhs);
+    BView<double> v;
+    carve_block(h, (char*)h->bws.p, &v, nullptr);
+    const int n = h->n;
+    const dim3 tg((n + 31) / 32, (K + 31) / 32), tb(32, 8);
+    kb_from_cols<double><<<tg, tb, 0, s>>>(n, nrhs, ld, K, x, v.pb);
+    AWG_LAUNCH();
+    AWG_TRY(apply64_any(h, K, which, prec, v.pb, v.pz, s));
+    kb_to_cols<double><<<tg, tb, 0, s>>>(n, nrhs, ld, K, v.pz, y);
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
+awg_status block_pcg(Handle* h, int prec, const double* b, double* x, int nrhs, int ld, double rtol, int* iters,
+                     double* relres, cudaStream_t s) {
+    AWG_TRY(block_prepare(h));
+    awg_status worst = AWG_OK;
+    for (int c0 = 0; c0 < nrhs; c0 += BLK_KMAX) {
+        const int k = std::min(BLK_KMAX, nrhs - c0);
+        const int K = pick_k(k);
+        awg_status st;
+        const double* bc = b + (size_t)c0 * ld;
+        double* xc = x + (size_t)c0 * ld;
+        int* ic = iters ? iters + c0 : nullptr;
+        double* rc = relres ? relres + c0 : nullptr;
+        if (K == 16) st = pcg_k<16>(h, prec, bc, xc, k, ld, rtol, ic, rc, s);
+        else if (K == 32) st = pcg_k<32>(h, prec, bc, xc, k, ld, rtol, ic, rc, s);
+        else st = pcg_k<64>(h, prec, bc, xc, k, ld, rtol, ic, rc, s);
+        if (st != AWG_OK && (worst == AWG_OK || st == AWG_ERR_CUDA)) worst = st;
+        if (st == AWG_ERR_CUDA) break;
+    }
+    return worst;
+}
+
+}  // namespace awg

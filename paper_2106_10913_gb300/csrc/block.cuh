@@ -1,0 +1,48 @@
+// Multi-right-hand-side ("block") hot path: declarations shared by block.cu
+// (CUDA-core kernels, block apply and block PCG) and umma.cu (tensor-core
+// passes over W).  Not part of the C ABI.
+//
+// A block vector holds K columns (K = 16, 32 or 64; the caller's nrhs
+// columns padded with zero columns) stored row by row: X[i * K + c].  Every
+// warp then reads whole rows, so the gathers through index lists (CSR
+// columns, subdomain index lists, incidence lists) move K contiguous values
+// per index instead of one.
+#pragma once
+
+#include "awg_common.cuh"
+
+namespace awg {
+
+constexpr int BLK_KMAX = 64;
+
+// Block apply of one stage (0 A, 1 A_+, 2 H^NN, 3 H_2, 4 H_3,ad) to nrhs <=
+// 64 columns (column-major, ld), and block PCG with H_3,ad (groups of up to
+// 64 columns), on stream s.
+awg_status block_apply(Handle* h, int which, int prec, const double* x, double* y, int nrhs, int ld,
+                       cudaStream_t s);
+awg_status block_pcg(Handle* h, int prec, const double* b, double* x, int nrhs, int ld, double rtol, int* iters,
+                     double* relres, cudaStream_t s);
+
+// Tensor-core passes over a 16-bit W (float16 or bfloat16), row-major
+// n x ldw.  All pointers are device pointers.
+struct UmmaW {
+    const void* W = nullptr;      // n x ldw, 16-bit
+    int n = 0, ldw = 0, nm = 0;   // rows, stride (multiple of 8), used columns
+    int bf16 = 0;                 // 1: bfloat16 storage, 0: float16
+};
+
+// part[split][c * K + j] = sum over rows i of split of W(i, c) * Bt(j, i) (hi + lo)
+// Bt: 2K x n 16-bit with row stride ldb (a multiple of 8), row j (< K) the
+// high part of column j of the scaled right-hand side, row K + j its low
+// part.  Returns AWG_ERR_INVALID_ARG for unsupported sizes.
+awg_status umma_wt(const UmmaW& u, int K, const void* Bt, int ldb, float* part, int splits, int* d_err,
+                   cudaStream_t s);
+// out(i, j) = sum_c W(i, c) * Dt(j, c) (hi + lo), fp32 n x K row-major;
+// Dt: 2K x ldw 16-bit (row stride ldw)
+awg_status umma_wd(const UmmaW& u, int K, const void* Dt, float* out, int* d_err, cudaStream_t s);
+// Whether the tensor-core passes are available (driver entry point found).
+bool umma_available();
+// Number of row splits umma_wt uses when asked for `want` (no empty split).
+int umma_wt_splits(int n, int want);
+
+}  // namespace awg

@@ -1,0 +1,475 @@
+// Tensor-core passes over the 16-bit second coarse basis W (float16 with
+// power-of-two row and column scales, or bfloat16) for K right-hand sides at
+// once: W^T B (first projection of Def. 10) and W D (prolongation of the
+// second coarse correction).  With K columns the two passes are GEMMs of
+// shape (ldw x n) x (n x K) and (n x ldw) x (ldw x K), bound by the bytes of
+// W; on the CUDA cores their K FMAs per element of W would bound them
+// instead.
+//
+// Both kernels: one CTA per 128-row tile of the product (M = 128), the K
+// right-hand sides as N, the reduction in 64-deep chunks.  W tiles and the
+// right-hand-side tiles come through TMA (cp.async.bulk.tensor, 128-byte
+// swizzle) into a 4-stage shared-memory ring guarded by mbarriers; one
+// thread issues tcgen05.mma (kind::f16, float32 accumulation in tensor
+// memory); the four warps read the accumulator back with tcgen05.ld.  The
+// right-hand sides enter as two 16-bit parts (high and low: about 22
+// significant bits for float16), accumulated into the same tensor-memory
+// tile, so the products carry the rounding of W alone.
+//
+// Every wait is bounded (about two seconds): a wait that gives up records a
+// code in *d_err and the CTA winds down (waits for its copies in flight,
+// frees its tensor memory) instead of hanging.
+
+#include "block.cuh"
+
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstdint>
+
+namespace awg {
+
+namespace {
+
+constexpr int UM_BM = 128;     // rows of the product per CTA (MMA M)
+constexpr int UM_BK = 64;      // reduction depth per stage (128 bytes of 16-bit)
+constexpr int UM_STAGES = 4;
+constexpr int UM_THREADS = 128;
+constexpr long long UM_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+
+enum : int { ERR_WAIT_EMPTY = 1, ERR_WAIT_FULL = 2, ERR_WAIT_DONE = 4 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of parity `parity` of *bar; false (and *err |= code)
+// after about two seconds.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+    if (mbar_test(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_test(bar, parity)) return true;
+        if (clock64() - t0 > UM_WAIT_CYCLES) {
+            atomicOr(err, code);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* holder, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(holder)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (float16 or bfloat16 inputs,
+// float32 accumulation)
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// arrive on *bar once every tcgen05.mma issued so far by this thread is done
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+// 16 consecutive 32-bit columns of this warp's 32 tensor-memory lanes
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor of a tcgen05.mma operand in the 128-byte
+// swizzled canonical layout: start address, leading and stride byte offsets
+// (16-byte units), descriptor version 1, swizzle mode 2 (128 B).  K-major
+// operand: rows of 128 bytes (64 16-bit values along the reduction), 8-row
+// groups 1024 bytes apart (stride offset); MN-major operand: rows of 128
+// bytes along M, 8-row groups along the reduction 1024 bytes apart (stride
+// offset), 64-wide M groups `lbo` bytes apart (leading offset).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: float32 accumulator, A and B of the
+// same 16-bit type, A K-major or MN-major, B K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int bf16, int a_mn) {
+    return (1u << 4) | ((uint32_t)bf16 << 7) | ((uint32_t)bf16 << 10) | ((uint32_t)a_mn << 15) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int K>
+struct UmCfg {
+    static constexpr int A_BYTES = UM_BM * UM_BK * 2;            // 16 KB
+    static constexpr int B_BYTES = 2 * K * UM_BK * 2;            // hi + lo parts
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int SMEM = UM_STAGES * STAGE + 1024;        // + alignment slack
+    static constexpr int TMEM_COLS = K < 32 ? 32 : K;
+};
+
+struct UmShared {
+    uint64_t full[UM_STAGES];
+    uint64_t empty[UM_STAGES];
+    uint64_t done;
+    uint32_t tmem;
+    int fail;
+};
+
+// Shared prologue: 1024-aligned stage ring, barriers, tensor memory.
+template <int K>
+__device__ __forceinline__ uint8_t* um_setup(uint8_t* raw, UmShared& sh) {
+    const uint32_t base = smem_u32(raw);
+    uint8_t* ring = raw + ((1024u - (base & 1023u)) & 1023u);
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < UM_STAGES; s++) {
+            mbar_init(&sh.full[s], 1);
+            mbar_init(&sh.empty[s], 1);
+        }
+        mbar_init(&sh.done, 1);
+        sh.fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 2) {
+        tmem_alloc(&sh.tmem, UmCfg<K>::TMEM_COLS);
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    return ring;
+}
+
+// Producer / MMA issue over nk chunks; the two callbacks issue one stage's
+// TMA loads and return its shared-memory descriptors' bases.
+// LoadF(stage_ptr, bar, kb); MmaF(a_base, b_base, first)
+template <int K, typename LoadF, typename MmaF>
+__device__ __forceinline__ void um_mainloop(uint8_t* ring, UmShared& sh, int nk, int* d_err, LoadF load,
+                                            MmaF mma) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    using C = UmCfg<K>;
+    if (warp == 0 && lane == 0) {
+        int kb = 0;
+        for (; kb < nk; kb++) {
+            const int st = kb % UM_STAGES;
+            if (kb >= UM_STAGES && !mbar_wait(&sh.empty[st], ((kb / UM_STAGES) - 1) & 1, d_err, ERR_WAIT_EMPTY)) {
+                sh.fail = 1;
+                break;
+            }
+            if (*(volatile int*)&sh.fail) break;
+            uint8_t* sp = ring + st * C::STAGE;
+            mbar_expect_tx(&sh.full[st], C::STAGE);
+            load(sp, &sh.full[st], kb);
+        }
+        // copies in flight: wait for the last load of every stage (bounded)
+        for (int j = (kb > UM_STAGES ? kb - UM_STAGES : 0); j < kb; j++)
+            mbar_wait(&sh.full[j % UM_STAGES], (j / UM_STAGES) & 1, d_err, ERR_WAIT_FULL);
+    } else if (warp == 1 && lane == 0) {
+        bool ok = true;
+        for (int kb = 0; kb < nk; kb++) {
+            const int st = kb % UM_STAGES;
+            if (!mbar_wait(&sh.full[st], (kb / UM_STAGES) & 1, d_err, ERR_WAIT_FULL) || *(volatile int*)&sh.fail) {
+                sh.fail = 1;
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t sp = smem_u32(ring + st * C::STAGE);
+            mma(sp, sp + C::A_BYTES, kb == 0);
+            umma_commit(&sh.empty[st]);  // the stage is free once these MMAs are done
+        }
+        (void)ok;
+        umma_commit(&sh.done);
+    }
+    __syncwarp();
+}
+
+// W D: out(i, :) = sum_c W(i, c) (Dt_hi(:, c) + Dt_lo(:, c)) for the 128 rows
+// of this CTA.  A = W tile (K-major: rows of W, 64 columns per stage), B =
+// Dt tile (K-major: 2K rows, 64 columns of W per stage).
+template <int K, int BF16>
+__global__ void __launch_bounds__(UM_THREADS) k_umma_wd(const __grid_constant__ CUtensorMap tmW,
+                                                        const __grid_constant__ CUtensorMap tmD, int n, int ldw,
+                                                        float* __restrict__ out, int* d_err) {
+    extern __shared__ uint8_t um_raw[];
+    __shared__ UmShared sh;
+    using C = UmCfg<K>;
+    uint8_t* ring = um_setup<K>(um_raw, sh);
+    const uint32_t taddr = sh.tmem;
+    const int m0 = blockIdx.x * UM_BM;
+    const int nk = (ldw + UM_BK - 1) / UM_BK;
+    constexpr uint32_t idesc = idesc_f16(UM_BM, K, BF16, 0);
+    um_mainloop<K>(
+        ring, sh, nk, d_err,
+        [&](uint8_t* sp, uint64_t* bar, int kb) {
+            tma_load_2d(sp, &tmW, bar, kb * UM_BK, m0);
+            tma_load_2d(sp + C::A_BYTES, &tmD, bar, kb * UM_BK, 0);
+        },
+        [&](uint32_t a, uint32_t b, bool first) {
+#pragma unroll
+            for (int kk = 0; kk < UM_BK / 16; kk++) {
+                const uint64_t ad = sdesc(a + kk * 32, 16, 1024);
+                const uint64_t bh = sdesc(b + kk * 32, 16, 1024);
+                const uint64_t bl = sdesc(b + K * 128 + kk * 32, 16, 1024);
+                umma_f16(taddr, ad, bh, idesc, (first && kk == 0) ? 0u : 1u);
+                umma_f16(taddr, ad, bl, idesc, 1u);
+            }
+        });
+    // epilogue: warp w holds rows m0 + 32 w + lane
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    bool ok = mbar_wait(&sh.done, 0, d_err, ERR_WAIT_DONE);
+    ok = __syncthreads_and(ok && !*(volatile int*)&sh.fail);  // uniform: tcgen05.ld is warp-collective
+    tc_fence_after();
+    const int row = m0 + warp * 32 + lane;
+    if (ok) {
+#pragma unroll
+        for (int c0 = 0; c0 < K; c0 += 16) {
+            float v[16];
+            tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (row < n) {
+                float4* o = reinterpret_cast<float4*>(out + (size_t)row * K + c0);
+#pragma unroll
+                for (int q = 0; q < 4; q++) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 2) tmem_dealloc(taddr, C::TMEM_COLS);
+}
+
+// W^T B: part(split, c, :) = sum over the rows i of this split of W(i, c)
+// (Bt_hi(:, i) + Bt_lo(:, i)) for the 128 columns c of this CTA.  A = W^T
+// tile (MN-major: two 64-column boxes of W side by side, 64 rows per stage),
+// B = Bt tile (K-major: 2K rows, 64 rows of W per stage).
+template <int K, int BF16>
+__global__ void __launch_bounds__(UM_THREADS) k_umma_wt(const __grid_constant__ CUtensorMap tmW,
+                                                        const __grid_constant__ CUtensorMap tmB, int n, int ldw,
+                                                        int rows_per_split, float* __restrict__ part, int* d_err) {
+    extern __shared__ uint8_t um_raw[];
+    __shared__ UmShared sh;
+    using C = UmCfg<K>;
+    uint8_t* ring = um_setup<K>(um_raw, sh);
+    const uint32_t taddr = sh.tmem;
+    const int c0 = blockIdx.x * UM_BM;
+    const int i0 = blockIdx.y * rows_per_split;
+    const int i1 = min(n, i0 + rows_per_split);
+    const int nk = i1 > i0 ? (i1 - i0 + UM_BK - 1) / UM_BK : 0;
+    constexpr uint32_t idesc = idesc_f16(UM_BM, K, BF16, 1);
+    um_mainloop<K>(
+        ring, sh, nk, d_err,
+        [&](uint8_t* sp, uint64_t* bar, int kb) {
+            const int i = i0 + kb * UM_BK;
+            tma_load_2d(sp, &tmW, bar, c0, i);
+            tma_load_2d(sp + C::A_BYTES / 2, &tmW, bar, c0 + 64, i);
+            tma_load_2d(sp + C::A_BYTES, &tmB, bar, i, 0);
+        },
+        [&](uint32_t a, uint32_t b, bool first) {
+#pragma unroll
+            for (int kk = 0; kk < UM_BK / 16; kk++) {
+                // 16 rows of W per MMA: two 8-row groups, 2048 bytes further
+                const uint64_t ad = sdesc(a + kk * 2048, C::A_BYTES / 2, 1024);
+                const uint64_t bh = sdesc(b + kk * 32, 16, 1024);
+                const uint64_t bl = sdesc(b + K * 128 + kk * 32, 16, 1024);
+                umma_f16(taddr, ad, bh, idesc, (first && kk == 0) ? 0u : 1u);
+                umma_f16(taddr, ad, bl, idesc, 1u);
+            }
+        });
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    bool ok = nk > 0 && mbar_wait(&sh.done, 0, d_err, ERR_WAIT_DONE);
+    ok = __syncthreads_and(ok && !*(volatile int*)&sh.fail);  // uniform: tcgen05.ld is warp-collective
+    tc_fence_after();
+    const int c = c0 + warp * 32 + lane;
+    float* o = part + ((size_t)blockIdx.y * ldw + c) * K;
+#pragma unroll
+    for (int j0 = 0; j0 < K; j0 += 16) {
+        float v[16];
+        if (ok) tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)j0, v);
+        else
+#pragma unroll
+            for (int q = 0; q < 16; q++) v[q] = 0.f;
+        if (c < ldw) {
+            float4* o4 = reinterpret_cast<float4*>(o + j0);
+#pragma unroll
+            for (int q = 0; q < 4; q++) o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 2) tmem_dealloc(taddr, C::TMEM_COLS);
+}
+
+// ----------------------------------------------------------------- host
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2D tensor map of a row-major 16-bit matrix (rows x cols, row stride ld
+// elements, a multiple of 8), box of box_cols x box_rows, 128-byte swizzle,
+// zero fill outside
+bool make_map(CUtensorMap* m, const void* ptr, int bf16, uint64_t rows, uint64_t cols, uint64_t ld,
+              uint32_t box_cols, uint32_t box_rows) {
+    EncodeTiledFn enc = encoder();
+    if (!enc || ((uintptr_t)ptr & 15) || (ld % 8)) return false;
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {ld * 2};
+    const cuuint32_t box[2] = {box_cols, box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                           const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// rows per split of W^T B: a multiple of the 64-row stage
+int split_rows(int n, int splits) {
+    const int rps = (n + splits - 1) / splits;
+    return (rps + UM_BK - 1) / UM_BK * UM_BK;
+}
+
+template <int K, int BF16>
+awg_status launch_wd(const UmmaW& u, const void* Dt, float* out, int* d_err, cudaStream_t s) {
+    CUtensorMap mW, mD;
+    if (!make_map(&mW, u.W, BF16, u.n, u.ldw, u.ldw, UM_BK, UM_BM) ||
+        !make_map(&mD, Dt, BF16, 2 * K, u.ldw, u.ldw, UM_BK, 2 * K))
+        return AWG_ERR_INVALID_ARG;
+    auto kern = k_umma_wd<K, BF16>;
+    static bool attr = false;
+    if (!attr) {
+        AWG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, UmCfg<K>::SMEM));
+        attr = true;
+    }
+    kern<<<(u.n + UM_BM - 1) / UM_BM, UM_THREADS, UmCfg<K>::SMEM, s>>>(mW, mD, u.n, u.ldw, out, d_err);
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
+template <int K, int BF16>
+awg_status launch_wt(const UmmaW& u, const void* Bt, int ldb, float* part, int splits, int* d_err,
+                     cudaStream_t s) {
+    CUtensorMap mW, mB;
+    if (!make_map(&mW, u.W, BF16, u.n, u.ldw, u.ldw, 64, UM_BK) ||
+        !make_map(&mB, Bt, BF16, 2 * K, u.n, ldb, UM_BK, 2 * K))
+        return AWG_ERR_INVALID_ARG;
+    auto kern = k_umma_wt<K, BF16>;
+    static bool attr = false;
+    if (!attr) {
+        AWG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, UmCfg<K>::SMEM));
+        attr = true;
+    }
+    const int rps = split_rows(u.n, splits);
+    const dim3 grid((u.ldw + UM_BM - 1) / UM_BM, (u.n + rps - 1) / rps);
+    kern<<<grid, UM_THREADS, UmCfg<K>::SMEM, s>>>(mW, mB, u.n, u.ldw, rps, part, d_err);
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
+}  // namespace
+
+bool umma_available() { return encoder() != nullptr; }
+
+int umma_wt_splits(int n, int want) {
+    const int rps = split_rows(n, std::max(1, want));
+    return (n + rps - 1) / rps;
+}
+
+awg_status umma_wd(const UmmaW& u, int K, const void* Dt, float* out, int* d_err, cudaStream_t s) {
+    if (u.n < 1 || u.ldw < 8 || (u.ldw % 8)) return AWG_ERR_INVALID_ARG;
+    if (K == 16) return u.bf16 ? launch_wd<16, 1>(u, Dt, out, d_err, s) : launch_wd<16, 0>(u, Dt, out, d_err, s);
+    if (K == 32) return u.bf16 ? launch_wd<32, 1>(u, Dt, out, d_err, s) : launch_wd<32, 0>(u, Dt, out, d_err, s);
+    if (K == 64) return u.bf16 ? launch_wd<64, 1>(u, Dt, out, d_err, s) : launch_wd<64, 0>(u, Dt, out, d_err, s);
+    return AWG_ERR_INVALID_ARG;
+}
+
+awg_status umma_wt(const UmmaW& u, int K, const void* Bt, int ldb, float* part, int splits, int* d_err,
+                   cudaStream_t s) {
+    if (u.n < 1 || u.ldw < 8 || (u.ldw % 8) || (ldb % 8) || splits < 1) return AWG_ERR_INVALID_ARG;
+    if (K == 16)
+        return u.bf16 ? launch_wt<16, 1>(u, Bt, ldb, part, splits, d_err, s)
+                      : launch_wt<16, 0>(u, Bt, ldb, part, splits, d_err, s);
+    if (K == 32)
+        return u.bf16 ? launch_wt<32, 1>(u, Bt, ldb, part, splits, d_err, s)
+                      : launch_wt<32, 0>(u, Bt, ldb, part, splits, d_err, s);
+    if (K == 64)
+        return u.bf16 ? launch_wt<64, 1>(u, Bt, ldb, part, splits, d_err, s)
+                      : launch_wt<64, 0>(u, Bt, ldb, part, splits, d_err, s);
+    return AWG_ERR_INVALID_ARG;
+}
+
+}  // namespace awg

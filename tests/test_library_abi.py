@@ -62,7 +62,7 @@ def test_host_only_calls(lib):
     assert lib.awg_learned_grad(0, None, None, None, None, 0, None) == 1
     assert lib.awg_learned_train(1, None, None, None, 1, 1e-2, 0, None, None) == 1
     assert lib.awg_learned_data(None, None, None, None) == 1
-    assert ctypes.sizeof(pkg.awg.awg_options) == 80
+    assert ctypes.sizeof(pkg.awg.awg_options) == 88
     assert o.w16_keep == 0.1
 
 
