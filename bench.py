@@ -4,10 +4,15 @@ Workload (default): 2D heterogeneous diffusion, 512 x 512 cells (n = 262144),
 coefficient 1 with 20 seeded horizontal channels of width 2 at 1e6, 16 x 16
 box subdomains grown by 2 layers, GenEO threshold tau = 0.1, b ~ N(0, 1).
 One step = one full PCG solve (x_0 = 0, stop at ||b - A x|| <= 1e-8 ||b||)
-preconditioned by H_3,ad with H_2 = H^NN_hyb(0.1); the setup runs once before
-the timed region.  The storage forms timed: FP64 (plain) and FP32-stored local
-operators and W with FP64 recurrences and coarse solves (mixed); `value` is
-the fastest form that reaches 1e-8.
+preconditioned by H_3,ad with H_2 = H^NN_hyb(0.1); the setup (GenEO block
+eigensolver from the learned start, network trained on the device on other
+instances) runs once before the timed region.  Forms timed: FP64 (plain),
+the mixed storage forms (float32 local operators; W in float32, bfloat16 or
+scaled float16; float64 recurrences and coarse solves), and the batched
+forms (suffix _block): one step = one block PCG solve of --nrhs right-hand
+sides (default 32), each column with its own recurrence to 1e-8, W passes of
+the float16 form on the tensor cores.  `value` is the fastest form, in
+solves (right-hand sides brought to 1e-8) per second.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl awg|reference]
 Under torchrun (N > 1) every rank solves its own copy of the problem
@@ -156,26 +161,85 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------- GPU arm
-def algorithmic_bytes(info, w_bytes, g_bytes, scaled):
-    """Minimum bytes per launch of each kernel class: W stored with w_bytes
-    per element (plus float32 row/column scales when `scaled`), the local
-    operators with g_bytes per element."""
-    n, nm = info["n"], info["n_minus"]
-    sum_ns = info["sum_ns"]
-    dense = info["dense_total"]
-    sc = 4 if scaled else 0
-    return {
-        "wt": n * nm * w_bytes + 8 * n + sc * n,
-        "wd": n * nm * w_bytes + 16 * n + 8 * nm + sc * n,
-        "local": dense * g_bytes + 16 * sum_ns,
-        "spmv": 12 * info["nnz"] + 4 * (n + 1) + 16 * n,
-    }
+FP64_TFLOPS = 1.197  # measured float64 FMA rate of this GPU (TFLOP/s)
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def roofline_of(form, info):
+    """Roofline of the dominant kernel class of a timed form (largest summed
+    CUDA-event time): algorithmic bytes (or flops) per launch over the
+    average event-timed launch.  Algorithmic bytes are the minimum traffic of
+    one launch: the operator read once (W with w bytes per element, the
+    local pseudo-inverses with g bytes), its input and output vectors once.
+    Float64 passes with one FMA per 8-byte element, and the float64 coarse
+    GEMMs of the block form, are bound by the float64 pipes, not by HBM."""
+    n, nm, nnz = info["n"], info["n_minus"], info["nnz"]
+    n0, sum_ns, dense = info["n0"], info["sum_ns"], info["dense_total"]
+    ldw = (nm + 7) // 8 * 8
+    prec = form["prec"]
+    from paper_2106_10913_gb300 import FP64, MIXED_BF16, MIXED_FP16, MIXED_FP32
+    w = {FP64: 8, MIXED_FP32: 4, MIXED_BF16: 2, MIXED_FP16: 2}[prec]
+    g = 8 if prec == FP64 else 4
+    sc = 4 if prec == MIXED_FP16 else 0
+    prof = form["prof"]
+    peaks = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    cls = {}
+    if not form["block"]:
+        cls["wt"] = ("k_wt_partial (W^T r)", "bytes", n * ldw * w + 8 * n + sc * n)
+        cls["wd"] = ("k_w_d (W d)", "bytes", n * ldw * w + 16 * n + 8 * nm + sc * n)
+        cls["local"] = ("k_local_gemv (batched local pseudo-inverses)", "bytes", dense * g + 16 * sum_ns)
+        cls["spmv"] = ("k_spmv", "bytes", 12 * nnz + 4 * (n + 1) + 16 * n)
+    else:
+        K = form["nrhs"]
+        K = 16 if K <= 16 else (32 if K <= 32 else 64)
+        v = 8 if prec == FP64 else 4  # internal block vectors
+        tc = prec in (MIXED_FP16, MIXED_BF16)
+        cls["wt"] = ("k_umma_wt (tcgen05 W^T B)" if tc else "kb_wt_partial (W^T B)", "bytes",
+                     n * ldw * w + (2 * K * n * 2 if tc else n * K * v) + ldw * K * 4)
+        cls["wd"] = ("k_umma_wd (tcgen05 W D)" if tc else "kb_w_d (W D)", "bytes",
+                     n * ldw * w + (2 * K * ldw * 2 if tc else ldw * K * v) + n * K * 4)
+        cls["local"] = ("kb_local_gemm (batched local pseudo-inverses, K columns)", "bytes",
+                        dense * g + 2 * sum_ns * K * v)
+        # E^-1 twice and F^-1 once per apply: average float64 flops per launch
+        cls["coarse"] = ("kb_dense_gemm (float64 E^-1, F^-1 on K columns)", "flops",
+                         2 * K * (2 * n0 * n0 + nm * nm) / 3.0)
+    cand = {k: prof["ms"][k] for k in cls if prof["count"][k] > 0}
+    dom = max(cand, key=cand.get)
+    name, kind, units = cls[dom]
+    per_launch_ms = prof["ms"][dom] / prof["count"][dom]
+    out = {"kernel": name, "avg_launch_ms": per_launch_ms, "launches": prof["count"][dom],
+           "kernel_share_of_step": prof["ms"][dom] / form["ms"], "traffic": None}
+    if kind == "flops":
+        achieved = units / (per_launch_ms / 1000.0) / 1e12
+        out.update({"bound": "alu", "achieved": achieved, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_TFLOPS, "algorithmic_flops_per_launch": units,
+                    "peak_source": "measured float64 FMA rate 1.197 TFLOP/s"})
+        return out
+    achieved = units / (per_launch_ms / 1000.0) / 1e9
+    out.update({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "algorithmic_bytes_per_launch": units, "peak_source": hbm_src})
+    if prec == FP64 and dom in ("wt", "wd", "local"):
+        # one float64 FMA per 8-byte element (per K columns in the block form)
+        kk = form["nrhs"] if form["block"] else 1
+        out["bound"] = "alu"
+        out["peak"] = FP64_TFLOPS * 1e3 * 8 / 2 / kk
+        out["frac"] = achieved / out["peak"]
+        out["peak_source"] = "measured float64 FMA rate 1.197 TFLOP/s x 4 bytes/flop / columns"
+    return out
 
 
 def run_awg(args):
     import torch
     import torch.distributed as dist
-    from paper_2106_10913_gb300 import (AWGSolver, FP64, MIXED_BF16, MIXED_FP16, MIXED_FP32, awg_pcg,
+    from paper_2106_10913_gb300 import (AWGSolver, FP64, MIXED_BF16, MIXED_FP16, MIXED_FP32, awg_pcg, awg_pcg_block,
                                         awg_profile, awg_profile_read)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -198,8 +262,12 @@ def run_awg(args):
     elif args.geneo == "block":
         geneo_opts = {"geneo_solver": 1}
     t0 = time.perf_counter()
+    # storage forms to build: float64 always, plus those of the timed forms
+    pmask = 1
+    for nm_ in args.forms.split(","):
+        pmask |= 1 << {"fp64": 0, "mixed_fp32": 1, "mixed_bf16": 2, "mixed_fp16": 3}[nm_.replace("_block", "")]
     sol = AWGSolver(p.rowptr, p.colidx, p.val, p.part, p.nparts, p.overlap, p.tau,
-                    precisions=0b1111, verbose=int(args.verbose), **geneo_opts)
+                    precisions=pmask, verbose=int(args.verbose), **geneo_opts)
     setup_s = time.perf_counter() - t0
     info = dict(sol.info)
     info["dense_total"] = int(np.sum(sol.array("ns").astype(np.int64) ** 2))
@@ -208,13 +276,23 @@ def run_awg(args):
     stream = torch.cuda.current_stream()
 
     forms = {}
-    timed_mask = (1 << 2) | (1 << 3) | (1 << 1) | (1 << 0)  # wt, wd, local, spmv
+    timed_mask = 0xFF  # every kernel class
     all_forms = {"fp64": FP64, "mixed_fp32": MIXED_FP32, "mixed_bf16": MIXED_BF16,
                  "mixed_fp16": MIXED_FP16}
+    K = args.nrhs
+    # batched forms: K right-hand sides per block solve, column 0 the
+    # benchmark's b, the others seeded N(0, 1)
+    B = np.concatenate([p.b[None, :], np.random.default_rng(1).standard_normal((K - 1, p.n))])
+    bB = torch.from_numpy(B).cuda()
+    xB = torch.zeros_like(bB)
     for name in args.forms.split(","):
-        prec = all_forms[name]
+        block = name.endswith("_block")
+        prec = all_forms[name[:-6] if block else name]
+        solve = ((lambda: awg_pcg_block(sol.h, bB, xB, RTOL, prec, check=False)) if block else
+                 (lambda: awg_pcg(sol.h, b, x, RTOL, prec, check=False)))
+        per_step = K if block else 1
         for _ in range(args.warmup):
-            awg_pcg(sol.h, b, x, RTOL, prec, check=False)
+            solve()
         barrier()
         awg_profile(sol.h, timed_mask)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -224,9 +302,9 @@ def run_awg(args):
             torch.cuda.nvtx.range_push(f"timed_{name}")
             ev0.record(stream)
             for _ in range(args.steps):
-                st, it, rel = awg_pcg(sol.h, b, x, RTOL, prec, check=False)
-                its.append(it[0])
-                rels.append(rel[0])
+                st, it, rel = solve()
+                its.append(max(it))
+                rels.append(max(rel))
                 sts.append(st)
             ev1.record(stream)
             torch.cuda.nvtx.range_pop()
@@ -239,69 +317,41 @@ def run_awg(args):
             dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
         ms = float(tmax.item())
         ok = all(s == 0 for s in sts) and max(rels) <= RTOL
-        forms[name] = {"prec": prec, "ms": ms, "value": world * args.steps / (ms / 1000.0),
+        forms[name] = {"prec": prec, "block": block, "nrhs": per_step, "ms": ms,
+                       "value": world * args.steps * per_step / (ms / 1000.0),
                        "ms_per_step": ms / args.steps, "iters": its[0], "relres": max(rels),
                        "ok": ok, "prof": prof, "clocks": clk.summary()}
 
     best = max((f for f in forms.values() if f["ok"]), key=lambda f: f["value"],
                default=next(iter(forms.values())))
     best_name = [k for k, v in forms.items() if v is best][0]
-    wbytes = {FP64: 8, MIXED_FP32: 4, MIXED_BF16: 2, MIXED_FP16: 2}[best["prec"]]
-    gbytes = 8 if best["prec"] == FP64 else 4
-
-    # roofline of the dominant kernel class of the headline form
-    prof = best["prof"]
-    abytes = algorithmic_bytes(info, wbytes, gbytes, best["prec"] == MIXED_FP16)
-    cand = {k: prof["ms"][k] for k in abytes if prof["count"][k] > 0}
-    dom = max(cand, key=cand.get)
-    per_launch_ms = prof["ms"][dom] / prof["count"][dom]
-    achieved = abytes[dom] / (per_launch_ms / 1000.0) / 1e9
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    peak = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    roofline = {"kernel": {"wt": "k_wt_partial (W^T r)", "wd": "k_w_d (W d)",
-                           "local": "k_local_gemv (batched local pseudo-inverses)",
-                           "spmv": "k_spmv"}[dom],
-                "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": abytes[dom],
-                "avg_launch_ms": per_launch_ms, "traffic": None,
-                "kernel_share_of_step": prof["ms"][dom] / best["ms"]}
-    if best["prec"] == FP64 and dom in ("wt", "wd", "local"):
-        # one FP64 FMA per 8-byte element: bound by the FP64 pipes on GB300
-        roofline["bound"] = "alu"
-        roofline["peak"] = 1.197e3 * 8 / 2  # GB/s at which the FP64 FMA rate is reached
-        roofline["unit"] = "GB/s"
-        roofline["frac"] = achieved / roofline["peak"]
-        roofline["peak_source"] = "measured FP64 FMA rate 1.197 TFLOP/s x 4 bytes/flop"
+    roofline = roofline_of(best, info)
 
     # end to end: host buffers through the public API (H2D b, solve, D2H x)
-    e2e = None
-    if True:
-        hb = torch.from_numpy(p.b).pin_memory()
-        hx = torch.empty_like(hb).pin_memory()
-        db = torch.empty_like(b)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            db.copy_(hb, non_blocking=True)
-            awg_pcg(sol.h, db, x, RTOL, best["prec"], check=False)
-            hx.copy_(x, non_blocking=True)
-            stream.synchronize()
-        e1.record(stream)
-        barrier()
-        ems = e0.elapsed_time(e1)
-        et = torch.tensor([ems], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(et, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * args.steps / (float(et.item()) / 1000.0), "unit": UNIT,
-               "h2d_bytes_per_step": int(hb.numel() * 8), "d2h_bytes_per_step": int(hx.numel() * 8),
-               "form": best_name}
+    hb = torch.from_numpy(B if best["block"] else p.b).pin_memory()
+    hx = torch.empty_like(hb).pin_memory()
+    db = torch.empty_like(hb, device="cuda")
+    dx = torch.zeros_like(db)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        db.copy_(hb, non_blocking=True)
+        if best["block"]:
+            awg_pcg_block(sol.h, db, dx, RTOL, best["prec"], check=False)
+        else:
+            awg_pcg(sol.h, db, dx, RTOL, best["prec"], check=False)
+        hx.copy_(dx, non_blocking=True)
+        stream.synchronize()
+    e1.record(stream)
+    barrier()
+    ems = e0.elapsed_time(e1)
+    et = torch.tensor([ems], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(et, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * args.steps * best["nrhs"] / (float(et.item()) / 1000.0), "unit": UNIT,
+           "h2d_bytes_per_step": int(hb.numel() * 8), "d2h_bytes_per_step": int(hx.numel() * 8),
+           "form": best_name}
 
     if rank == 0:
         cb = oracle_sample(1) if (world == 1 and not args.no_cpu_baseline) else None
@@ -312,7 +362,10 @@ def run_awg(args):
             "dtype": {FP64: "f64", MIXED_FP32: "f32+f64", MIXED_BF16: "bf16+f32+f64",
                       MIXED_FP16: "f16+f32+f64"}[best["prec"]],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "form": best_name, "n": p.n, "nparts": p.nparts,
+            "config": {"workload": WORKLOAD + (f"; batched form: {best['nrhs']} right-hand sides per block "
+                                               "solve (column 0 the benchmark b, the rest seeded N(0,1)), "
+                                               "each column its own PCG to 1e-8" if best["block"] else ""),
+                       "form": best_name, "nrhs_per_step": best["nrhs"], "n": p.n, "nparts": p.nparts,
                        "overlap": p.overlap, "tau": p.tau, "rtol": RTOL,
                        "n0": info["n0"], "n_minus": info["n_minus"], "iters": best["iters"],
                        "l2": "inputs larger than L2 (W and local operators are GBs)",
@@ -323,8 +376,11 @@ def run_awg(args):
                                  "block_steps_sum": info["geneo_its_sum"],
                                  "dense_subdomains": info["geneo_dense"], "training": train},
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "forms": {k: {"value": v["value"], "ms_per_step": v["ms_per_step"], "iters": v["iters"],
-                          "relres": v["relres"], "ok": v["ok"]} for k, v in forms.items()},
+            "forms": {k: {"value": v["value"], "ms_per_step": v["ms_per_step"], "nrhs": v["nrhs"],
+                          "iters": v["iters"], "relres": v["relres"], "ok": v["ok"],
+                          "kernel_ms": {c: round(t, 3) for c, t in v["prof"]["ms"].items()},
+                          "launches": v["prof"]["launches"]} for k, v in forms.items()},
+            "speedup_vs_plain_fp64": (best["value"] / forms["fp64"]["value"]) if "fp64" in forms else None,
             "roofline": roofline,
             "cpu_baseline": ({k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
                              if cb else None),
@@ -384,8 +440,10 @@ def main():
     ap.add_argument("--config", default="config2")
     ap.add_argument("--verbose", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default="fp64,mixed_fp32,mixed_bf16,mixed_fp16",
-                    help="comma-separated storage forms to time")
+    ap.add_argument("--nrhs", type=int, default=32, help="right-hand sides per step of the batched forms")
+    ap.add_argument("--forms", default="fp64,mixed_fp32,mixed_bf16,mixed_fp16,mixed_fp32_block,mixed_fp16_block",
+                    help="comma-separated storage forms to time; a _block suffix times the "
+                         "batched (multi-right-hand-side) solve of --nrhs columns")
     ap.add_argument("--geneo", default="learned", choices=["learned", "block", "dense"],
                     help="GenEO eigensolver of the setup: block solver from the learned start "
                          "(network trained on the device on smaller instances), from a random "

@@ -26,12 +26,13 @@
 
 namespace awg {
 
-// Thread-to-(row, column) map of the row kernels: TPR threads cover the K
-// columns of one row, CPT columns each (cl, cl + TPR, ...), RPW rows per warp.
-template <int K>
+// Thread-to-(row, column) map of the row kernels: every thread moves 16
+// bytes of a row (V = 4 float32 or 2 float64 consecutive columns, from
+// column c0), TPR = K / V threads cover a row, RPW rows per warp.
+template <typename T, int K>
 struct RM {
-    static constexpr int TPR = K < 32 ? K : 32;
-    static constexpr int CPT = K / TPR;
+    static constexpr int V = 16 / sizeof(T);
+    static constexpr int TPR = K / V;
     static constexpr int RPW = 32 / TPR;
     static constexpr int RPB = 8 * RPW;  // rows per 256-thread block
 };
@@ -39,19 +40,34 @@ struct RM {
 template <typename T> struct Acc { using type = float; };
 template <> struct Acc<double> { using type = double; };
 
-// Per-column sums of a 256-thread block (thread partials acc[j] belong to
-// column cl + TPR * j), then over the grid: block partials go to
-// part[b * K + c] and the last block to arrive (ticket) adds them in block
-// order.  Deterministic for a given grid.
+__device__ __forceinline__ void ldv(const float* p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ldv(const double* p, double (&v)[2]) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    v[0] = t.x; v[1] = t.y;
+}
+__device__ __forceinline__ void stv(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void stv(double* p, const double (&v)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+}
+
+// Per-column sums of a 256-thread block of float64 row kernels (thread
+// partials acc[j] belong to column c0 + j), then over the grid: block
+// partials go to part[b * K + c] and the last block to arrive (ticket) adds
+// them in block order.  Deterministic for a given grid.
 template <int K>
-__device__ __forceinline__ void colsum_grid(const double* acc, double* part, unsigned* cnt, double* out) {
-    using M = RM<K>;
+__device__ __forceinline__ void colsum_grid(const double (&acc)[2], double* part, unsigned* cnt, double* out) {
+    using M = RM<double, K>;
     __shared__ double red[8 * M::RPW][K];
     __shared__ unsigned ticket;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int rw = lane / M::TPR, cl = lane % M::TPR;
-#pragma unroll
-    for (int j = 0; j < M::CPT; j++) red[w * M::RPW + rw][cl + M::TPR * j] = acc[j];
+    const int rw = lane / M::TPR, c0 = (lane % M::TPR) * 2;
+    red[w * M::RPW + rw][c0] = acc[0];
+    red[w * M::RPW + rw][c0 + 1] = acc[1];
     __syncthreads();
     if (threadIdx.x < K) {
         double v = 0.0;
@@ -72,11 +88,10 @@ __device__ __forceinline__ void colsum_grid(const double* acc, double* part, uns
     if (threadIdx.x == 0) *cnt = 0u;
 }
 
-#define ROW_LOOP(K_)                                                                     \
-    using M = RM<K_>;                                                                    \
+#define ROW_LOOP(T_, K_)                                                                 \
+    using M = RM<T_, K_>;                                                                \
     const int lane_ = threadIdx.x & 31, w_ = threadIdx.x >> 5;                           \
-    const int rw_ = lane_ / M::TPR, cl = lane_ % M::TPR;                                 \
-    (void)rw_;                                                                           \
+    const int rw_ = lane_ / M::TPR, c0 = (lane_ % M::TPR) * M::V;                        \
     for (int i = blockIdx.x * M::RPB + w_ * M::RPW + rw_; i < n; i += gridDim.x * M::RPB)
 
 // ------------------------------------------------------------- PCG (float64)
@@ -90,20 +105,22 @@ __global__ void __launch_bounds__(256) kb_spmv_dot(int n, const int* __restrict_
                                                    const double* __restrict__ a, const double* __restrict__ X,
                                                    double* __restrict__ Y, double* part, unsigned* cnt,
                                                    double* dot) {
-    double acc[RM<K>::CPT] = {};
-    ROW_LOOP(K) {
-        double y[M::CPT] = {};
-        for (int k = rp[i]; k < rp[i + 1]; k++) {
+    double acc[2] = {0.0, 0.0};
+    ROW_LOOP(double, K) {
+        double y[2] = {0.0, 0.0};
+        const int e1 = rp[i + 1];
+        for (int k = rp[i]; k < e1; k++) {
+            double xv[2];
+            ldv(X + (size_t)ci[k] * K + c0, xv);
             const double av = a[k];
-            const double* xr = X + (size_t)ci[k] * K + cl;
-#pragma unroll
-            for (int j = 0; j < M::CPT; j++) y[j] = fma(av, xr[M::TPR * j], y[j]);
+            y[0] = fma(av, xv[0], y[0]);
+            y[1] = fma(av, xv[1], y[1]);
         }
-#pragma unroll
-        for (int j = 0; j < M::CPT; j++) {
-            Y[(size_t)i * K + cl + M::TPR * j] = y[j];
-            acc[j] = fma(y[j], X[(size_t)i * K + cl + M::TPR * j], acc[j]);
-        }
+        stv(Y + (size_t)i * K + c0, y);
+        double xi[2];
+        ldv(X + (size_t)i * K + c0, xi);
+        acc[0] = fma(y[0], xi[0], acc[0]);
+        acc[1] = fma(y[1], xi[1], acc[1]);
     }
     if (dot) colsum_grid<K>(acc, part, cnt, dot);
 }
@@ -113,19 +130,18 @@ template <int K>
 __global__ void __launch_bounds__(256) kb_resid(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                 const double* __restrict__ a, const double* __restrict__ B,
                                                 const double* __restrict__ X, double* __restrict__ Q) {
-    ROW_LOOP(K) {
-        double y[M::CPT] = {};
+    ROW_LOOP(double, K) {
+        double y[2] = {0.0, 0.0};
         for (int k = rp[i]; k < rp[i + 1]; k++) {
-            const double av = a[k];
-            const double* xr = X + (size_t)ci[k] * K + cl;
-#pragma unroll
-            for (int j = 0; j < M::CPT; j++) y[j] = fma(av, xr[M::TPR * j], y[j]);
+            double xv[2];
+            ldv(X + (size_t)ci[k] * K + c0, xv);
+            y[0] = fma(a[k], xv[0], y[0]);
+            y[1] = fma(a[k], xv[1], y[1]);
         }
-#pragma unroll
-        for (int j = 0; j < M::CPT; j++) {
-            const size_t e = (size_t)i * K + cl + M::TPR * j;
-            Q[e] = B[e] - y[j];
-        }
+        double b[2];
+        ldv(B + (size_t)i * K + c0, b);
+        const double q[2] = {b[0] - y[0], b[1] - y[1]};
+        stv(Q + (size_t)i * K + c0, q);
     }
 }
 
@@ -133,13 +149,13 @@ __global__ void __launch_bounds__(256) kb_resid(int n, const int* __restrict__ r
 template <int K>
 __global__ void __launch_bounds__(256) kb_coldot(int n, const double* __restrict__ X, const double* __restrict__ Y,
                                                  double* part, unsigned* cnt, double* out) {
-    double acc[RM<K>::CPT] = {};
-    ROW_LOOP(K) {
-#pragma unroll
-        for (int j = 0; j < M::CPT; j++) {
-            const size_t e = (size_t)i * K + cl + M::TPR * j;
-            acc[j] = fma(X[e], Y[e], acc[j]);
-        }
+    double acc[2] = {0.0, 0.0};
+    ROW_LOOP(double, K) {
+        double x[2], y[2];
+        ldv(X + (size_t)i * K + c0, x);
+        ldv(Y + (size_t)i * K + c0, y);
+        acc[0] = fma(x[0], y[0], acc[0]);
+        acc[1] = fma(x[1], y[1], acc[1]);
     }
     colsum_grid<K>(acc, part, cnt, out);
 }
@@ -150,25 +166,31 @@ template <int K>
 __global__ void __launch_bounds__(256) kb_pcg_xr(int n, double* sc, const double* __restrict__ P,
                                                  const double* __restrict__ Q, double* X, double* R,
                                                  double* part, unsigned* cnt) {
-    double alpha[RM<K>::CPT], acc[RM<K>::CPT] = {};
+    double alpha[2], acc[2] = {0.0, 0.0};
     {
-        const int cl0 = (threadIdx.x & 31) % RM<K>::TPR;
+        const int cc = ((threadIdx.x & 31) % RM<double, K>::TPR) * 2;
 #pragma unroll
-        for (int j = 0; j < RM<K>::CPT; j++) {
-            const int c = cl0 + RM<K>::TPR * j;
+        for (int j = 0; j < 2; j++) {
+            const int c = cc + j;
             const double pq = sc[B_PQ * K + c];
             alpha[j] = (sc[B_ACT * K + c] != 0.0 && pq > 0.0) ? sc[B_RZ * K + c] / pq : 0.0;
         }
     }
-    ROW_LOOP(K) {
+    ROW_LOOP(double, K) {
+        const size_t e = (size_t)i * K + c0;
+        double p[2], q[2], x[2], r[2];
+        ldv(P + e, p);
+        ldv(Q + e, q);
+        ldv(X + e, x);
+        ldv(R + e, r);
 #pragma unroll
-        for (int j = 0; j < M::CPT; j++) {
-            const size_t e = (size_t)i * K + cl + M::TPR * j;
-            X[e] = fma(alpha[j], P[e], X[e]);
-            const double r = fma(-alpha[j], Q[e], R[e]);
-            R[e] = r;
-            acc[j] = fma(r, r, acc[j]);
+        for (int j = 0; j < 2; j++) {
+            x[j] = fma(alpha[j], p[j], x[j]);
+            r[j] = fma(-alpha[j], q[j], r[j]);
+            acc[j] = fma(r[j], r[j], acc[j]);
         }
+        stv(X + e, x);
+        stv(R + e, r);
     }
     colsum_grid<K>(acc, part, cnt, sc + B_RR * K);
 }
@@ -179,24 +201,27 @@ template <int K>
 __global__ void __launch_bounds__(256) kb_pcg_p(int n, double* sc, const double* __restrict__ Z, double* P,
                                                 unsigned* cnt) {
     __shared__ unsigned ticket;
-    double beta[RM<K>::CPT];
-    bool act[RM<K>::CPT];
+    double beta[2];
     {
-        const int cl0 = (threadIdx.x & 31) % RM<K>::TPR;
+        const int cc = ((threadIdx.x & 31) % RM<double, K>::TPR) * 2;
 #pragma unroll
-        for (int j = 0; j < RM<K>::CPT; j++) {
-            const int c = cl0 + RM<K>::TPR * j;
+        for (int j = 0; j < 2; j++) {
+            const int c = cc + j;
             const double rz = sc[B_RZ * K + c];
-            act[j] = sc[B_ACT * K + c] != 0.0;
-            beta[j] = (rz != 0.0) ? sc[B_RZN * K + c] / rz : 0.0;
+            // inactive columns keep P: beta = 1 and Z replaced by 0 below
+            beta[j] = (sc[B_ACT * K + c] == 0.0) ? 1.0 : ((rz != 0.0) ? sc[B_RZN * K + c] / rz : 0.0);
         }
     }
-    ROW_LOOP(K) {
-#pragma unroll
-        for (int j = 0; j < M::CPT; j++) {
-            const size_t e = (size_t)i * K + cl + M::TPR * j;
-            if (act[j]) P[e] = fma(beta[j], P[e], Z[e]);
-        }
+    const int cc = ((threadIdx.x & 31) % RM<double, K>::TPR) * 2;
+    const bool a0 = sc[B_ACT * K + cc] != 0.0, a1 = sc[B_ACT * K + cc + 1] != 0.0;
+    ROW_LOOP(double, K) {
+        const size_t e = (size_t)i * K + c0;
+        double z[2], pv[2];
+        ldv(Z + e, z);
+        ldv(P + e, pv);
+        pv[0] = a0 ? fma(beta[0], pv[0], z[0]) : pv[0];
+        pv[1] = a1 ? fma(beta[1], pv[1], z[1]) : pv[1];
+        stv(P + e, pv);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -268,86 +293,111 @@ __global__ void __launch_bounds__(256) kb_aplus(int n, const int* __restrict__ r
                                                 const int* __restrict__ colptr, const int64_t* __restrict__ boff,
                                                 const T* __restrict__ V, const T* __restrict__ cm,
                                                 const T* Yin, T sign, T* Y) {
-    ROW_LOOP(K) {
-        T y[M::CPT] = {};
-        for (int k = rp[i]; k < rp[i + 1]; k++) {
+    ROW_LOOP(T, K) {
+        T y[M::V] = {};
+        const int k1 = rp[i + 1];
+        for (int k = rp[i]; k < k1; k++) {
+            T xv[M::V];
+            ldv(X + (size_t)ci[k] * K + c0, xv);
             const T av = a[k];
-            const T* xr = X + (size_t)ci[k] * K + cl;
 #pragma unroll
-            for (int j = 0; j < M::CPT; j++) y[j] = fma(av, xr[M::TPR * j], y[j]);
+            for (int j = 0; j < M::V; j++) y[j] = fma(av, xv[j], y[j]);
         }
         if (cm) {
             for (int e = inc_ptr[i]; e < inc_ptr[i + 1]; e++) {
                 const int s = inc_sub[e];
                 const int ps = sub_ptr[s], m = sub_ptr[s + 1] - ps;
-                const int c0 = colptr[s], nc = colptr[s + 1] - c0;
+                const int cq = colptr[s], nc = colptr[s + 1] - cq;
                 const T* b = V + boff[s] + (inc_pos[e] - ps);
+#pragma unroll 4
                 for (int q = 0; q < nc; q++) {
+                    T cv[M::V];
+                    ldv(cm + (size_t)(cq + q) * K + c0, cv);
                     const T bv = b[(size_t)q * m];
-                    const T* cr = cm + (size_t)(c0 + q) * K + cl;
 #pragma unroll
-                    for (int j = 0; j < M::CPT; j++) y[j] = fma(bv, cr[M::TPR * j], y[j]);
+                    for (int j = 0; j < M::V; j++) y[j] = fma(bv, cv[j], y[j]);
                 }
             }
         }
+        const size_t e = (size_t)i * K + c0;
+        T o[M::V];
+        if (Yin) {
+            ldv(Yin + e, o);
 #pragma unroll
-        for (int j = 0; j < M::CPT; j++) {
-            const size_t e = (size_t)i * K + cl + M::TPR * j;
-            Y[e] = Yin ? fma(sign, y[j], Yin[e]) : sign * y[j];
+            for (int j = 0; j < M::V; j++) o[j] = fma(sign, y[j], o[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < M::V; j++) o[j] = sign * y[j];
         }
+        stv(Y + e, o);
     }
 }
 
-// C_s(q, :) = wsign w_q sum_p B_s(p, q) X(idx_s(p), :) for the columns q of
-// subdomain s in chunk blockIdx.y (16 per chunk): 4 warps take every 4th
-// local position, their sums meet in shared memory in a fixed order.
-constexpr int KB_TG_C = 16;
+// C_s(q, :) = wsign w_q sum_p B_s(p, q) X(idx_s(p), :) for every subdomain s
+// (B_s n^s x nc_s column-major; block-sparse Z^T X and V_-^T X).  Block
+// (s, qc, ps) takes the columns q of chunk qc (16 per chunk) and the local
+// positions of split ps, in chunks of 64 staged in shared memory (B_s rows
+// coalesced along p, X rows gathered whole); each thread owns K / 16
+// outputs (q, c).  Partial sums go to part[ps][colptr[s] + q][c];
+// kb_tg_sum adds the TG_PS splits in order.
+constexpr int KB_TG_C = 16, TG_PC = 64, TG_PS = 4;
 template <typename T, int K>
-__global__ void __launch_bounds__(128) kb_tgemv(const int* __restrict__ sub_ptr, const int* __restrict__ sub_idx,
+__global__ void __launch_bounds__(256) kb_tgemv(const int* __restrict__ sub_ptr, const int* __restrict__ sub_idx,
                                                 const int* __restrict__ colptr, const int64_t* __restrict__ boff,
-                                                const T* __restrict__ B, const T* __restrict__ X,
-                                                const T* __restrict__ w, T wsign, T* C) {
-    using M = RM<K>;
-    __shared__ T red[4 * M::RPW][KB_TG_C][K];
-    const int s = blockIdx.x, cb = blockIdx.y * KB_TG_C;
+                                                const T* __restrict__ B, const T* __restrict__ X, int ncol_total,
+                                                T* __restrict__ part) {
+    __shared__ T bs[TG_PC][KB_TG_C + 1];
+    __shared__ __align__(16) T xs[TG_PC][K];
+    constexpr int U = K / 16;
+    const int s = blockIdx.x, cb = blockIdx.y * KB_TG_C, ps = blockIdx.z;
     const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
     const int c0 = colptr[s], nc = colptr[s + 1] - c0;
     if (cb >= nc) return;
     const int kc = min(KB_TG_C, nc - cb);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int rw = lane / M::TPR, cl = lane % M::TPR;
-    T acc[KB_TG_C][M::CPT];
-#pragma unroll
-    for (int q = 0; q < KB_TG_C; q++)
-#pragma unroll
-        for (int j = 0; j < M::CPT; j++) acc[q][j] = 0;
+    const int plen = (m + TG_PS - 1) / TG_PS;
+    const int pa = ps * plen, pb = min(m, pa + plen);
     const T* Bs = B + boff[s] + (size_t)cb * m;
-    for (int p = wid * M::RPW + rw; p < m; p += 4 * M::RPW) {
-        T x[M::CPT];
-        const T* xr = X + (size_t)sub_idx[p0 + p] * K + cl;
+    T acc[U];
 #pragma unroll
-        for (int j = 0; j < M::CPT; j++) x[j] = xr[M::TPR * j];
+    for (int u = 0; u < U; u++) acc[u] = 0;
+    for (int q0 = pa; q0 < pb; q0 += TG_PC) {
+        const int pn = min(TG_PC, pb - q0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < KB_TG_C * TG_PC; e += 256) {
+            const int q = e / TG_PC, pp = e % TG_PC;
+            bs[pp][q] = (q < kc && pp < pn) ? Bs[(size_t)q * m + q0 + pp] : (T)0;
+        }
+        for (int e = threadIdx.x; e < TG_PC * K; e += 256) {
+            const int pp = e / K;
+            (&xs[0][0])[e] = (pp < pn) ? X[(size_t)sub_idx[p0 + q0 + pp] * K + (e % K)] : (T)0;
+        }
+        __syncthreads();
 #pragma unroll
-        for (int q = 0; q < KB_TG_C; q++) {
-            if (q < kc) {
-                const T bv = Bs[(size_t)q * m + p];
-#pragma unroll
-                for (int j = 0; j < M::CPT; j++) acc[q][j] = fma(bv, x[j], acc[q][j]);
-            }
+        for (int u = 0; u < U; u++) {
+            const int o = threadIdx.x + 256 * u, q = o / K, c = o % K;
+            T a = acc[u];
+#pragma unroll 8
+            for (int pp = 0; pp < TG_PC; pp++) a = fma(bs[pp][q], xs[pp][c], a);
+            acc[u] = a;
         }
     }
 #pragma unroll
-    for (int q = 0; q < KB_TG_C; q++)
-#pragma unroll
-        for (int j = 0; j < M::CPT; j++) red[wid * M::RPW + rw][q][cl + M::TPR * j] = acc[q][j];
-    __syncthreads();
-    for (int e = threadIdx.x; e < kc * K; e += blockDim.x) {
-        const int q = e / K, c = e % K;
-        T v = 0;
-        for (int r = 0; r < 4 * M::RPW; r++) v += red[r][q][c];
-        const int cq = c0 + cb + q;
-        C[(size_t)cq * K + c] = w ? wsign * w[cq] * v : v;
+    for (int u = 0; u < U; u++) {
+        const int o = threadIdx.x + 256 * u, q = o / K, c = o % K;
+        if (q < kc) part[((size_t)ps * ncol_total + c0 + cb + q) * K + c] = acc[u];
     }
+}
+
+// C(j, c) = wsign w_j sum_ps part[ps][j][c]  (fixed order)
+template <typename T, int K>
+__global__ void kb_tg_sum(int ncol_total, const T* __restrict__ part, const T* __restrict__ w, T wsign, T* C) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t len = (size_t)ncol_total * K;
+    if (e >= len) return;
+    T v = 0;
+#pragma unroll
+    for (int ps = 0; ps < TG_PS; ps++) v += part[(size_t)ps * len + e];
+    C[e] = w ? wsign * w[e / K] * v : v;
 }
 
 // Y(i, :) = beta Y(i, :) + alpha sum over the copies (s, p) of i of
@@ -361,29 +411,42 @@ __global__ void __launch_bounds__(256) kb_blk_prolong(int n, const int* __restri
                                                       const int64_t* __restrict__ boff, const T* __restrict__ B,
                                                       const T* __restrict__ C, T* Y, T alpha, T beta,
                                                       const T* V, T gamma, const T* V2) {
-    ROW_LOOP(K) {
-        T y[M::CPT] = {};
+    ROW_LOOP(T, K) {
+        T y[M::V] = {};
         for (int e = inc_ptr[i]; e < inc_ptr[i + 1]; e++) {
             const int s = inc_sub[e];
             const int ps = sub_ptr[s], m = sub_ptr[s + 1] - ps;
-            const int c0 = colptr[s], nc = colptr[s + 1] - c0;
+            const int cq = colptr[s], nc = colptr[s + 1] - cq;
             const T* b = B + boff[s] + (inc_pos[e] - ps);
+#pragma unroll 4
             for (int q = 0; q < nc; q++) {
+                T cv[M::V];
+                ldv(C + (size_t)(cq + q) * K + c0, cv);
                 const T bv = b[(size_t)q * m];
-                const T* cr = C + (size_t)(c0 + q) * K + cl;
 #pragma unroll
-                for (int j = 0; j < M::CPT; j++) y[j] = fma(bv, cr[M::TPR * j], y[j]);
+                for (int j = 0; j < M::V; j++) y[j] = fma(bv, cv[j], y[j]);
             }
         }
+        const size_t e = (size_t)i * K + c0;
+        T o[M::V], t[M::V];
 #pragma unroll
-        for (int j = 0; j < M::CPT; j++) {
-            const size_t e = (size_t)i * K + cl + M::TPR * j;
-            T v = alpha * y[j];
-            if (beta != (T)0) v = fma(beta, Y[e], v);
-            if (V) v = fma(gamma, V[e], v);
-            if (V2) v += V2[e];
-            Y[e] = v;
+        for (int j = 0; j < M::V; j++) o[j] = alpha * y[j];
+        if (beta != (T)0) {
+            ldv(Y + e, t);
+#pragma unroll
+            for (int j = 0; j < M::V; j++) o[j] = fma(beta, t[j], o[j]);
         }
+        if (V) {
+            ldv(V + e, t);
+#pragma unroll
+            for (int j = 0; j < M::V; j++) o[j] = fma(gamma, t[j], o[j]);
+        }
+        if (V2) {
+            ldv(V2 + e, t);
+#pragma unroll
+            for (int j = 0; j < M::V; j++) o[j] += t[j];
+        }
+        stv(Y + e, o);
     }
 }
 
@@ -392,21 +455,29 @@ template <typename T, int K>
 __global__ void __launch_bounds__(256) kb_prolong(int n, const int* __restrict__ inc_ptr,
                                                   const int* __restrict__ inc_pos, const T* __restrict__ loc,
                                                   T* Y, T alpha, T beta, const T* V, T gamma) {
-    ROW_LOOP(K) {
-        T y[M::CPT] = {};
+    ROW_LOOP(T, K) {
+        T y[M::V] = {};
         for (int e = inc_ptr[i]; e < inc_ptr[i + 1]; e++) {
-            const T* lr = loc + (size_t)inc_pos[e] * K + cl;
+            T lv[M::V];
+            ldv(loc + (size_t)inc_pos[e] * K + c0, lv);
 #pragma unroll
-            for (int j = 0; j < M::CPT; j++) y[j] += lr[M::TPR * j];
+            for (int j = 0; j < M::V; j++) y[j] += lv[j];
         }
+        const size_t e = (size_t)i * K + c0;
+        T o[M::V], t[M::V];
 #pragma unroll
-        for (int j = 0; j < M::CPT; j++) {
-            const size_t e = (size_t)i * K + cl + M::TPR * j;
-            T v = alpha * y[j];
-            if (beta != (T)0) v = fma(beta, Y[e], v);
-            if (V) v = fma(gamma, V[e], v);
-            Y[e] = v;
+        for (int j = 0; j < M::V; j++) o[j] = alpha * y[j];
+        if (beta != (T)0) {
+            ldv(Y + e, t);
+#pragma unroll
+            for (int j = 0; j < M::V; j++) o[j] = fma(beta, t[j], o[j]);
         }
+        if (V) {
+            ldv(V + e, t);
+#pragma unroll
+            for (int j = 0; j < M::V; j++) o[j] = fma(gamma, t[j], o[j]);
+        }
+        stv(Y + e, o);
     }
 }
 
@@ -457,12 +528,20 @@ template <int RT> struct LoadRT<double, RT> {
     }
 };
 
+// 16 bytes of a 16-byte aligned shared array in one load
+template <typename T>
+__device__ __forceinline__ void lds16(const T* p, T* o) {
+    *reinterpret_cast<float4*>(o) = *reinterpret_cast<const float4*>(p);
+}
+
 template <typename T, int K>
 __global__ void __launch_bounds__(128) kb_local_gemm(const int* __restrict__ sub_ptr, const int64_t* __restrict__ goff,
                                                      const T* __restrict__ G, int pad4,
                                                      const T* __restrict__ loc, T* __restrict__ out) {
     using L = LG<T, K>;
     constexpr int RT = L::RT;
+    constexpr int QG = sizeof(T) == 4 ? 8 : 4;     // columns of G per step
+    constexpr int V = 16 / sizeof(T);              // values per 16-byte shared load
     __shared__ __align__(16) T xs[L::JC][K];
     const int s = blockIdx.x;
     const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
@@ -471,51 +550,56 @@ __global__ void __launch_bounds__(128) kb_local_gemm(const int* __restrict__ sub
     if (r0 >= m) return;
     const int rb = r0 + threadIdx.x * RT;          // first row of this thread
     const bool live = rb < m;
+    const bool vec = pad4 || rb + RT <= m;         // whole RT rows inside the column
     const T* Gs = G + goff[s] + rb;
     T acc[RT][K];
 #pragma unroll
     for (int r = 0; r < RT; r++)
 #pragma unroll
         for (int c = 0; c < K; c++) acc[r][c] = 0;
+    // the RT values of columns q .. q + QG - 1 (zero past column m - 1)
+    auto load_group = [&](int q, T (&g)[QG][RT]) {
+#pragma unroll
+        for (int u = 0; u < QG; u++) {
+            if (live && q + u < m) {
+                if (vec) LoadRT<T, RT>::ld(Gs + (size_t)(q + u) * ld, g[u]);
+                else
+#pragma unroll
+                    for (int r = 0; r < RT; r++) g[u][r] = (rb + r < m) ? Gs[(size_t)(q + u) * ld + r] : (T)0;
+            } else {
+#pragma unroll
+                for (int r = 0; r < RT; r++) g[u][r] = (T)0;
+            }
+        }
+    };
+    // software pipeline: the loads of the next QG columns are in flight
+    // while the current ones are multiplied
+    T gc[QG][RT], gn[QG][RT];
+    load_group(0, gc);
     const T* ls = loc + (size_t)p0 * K;
     for (int q0 = 0; q0 < m; q0 += L::JC) {
         const int qn = min(L::JC, m - q0);
         __syncthreads();
-        for (int e = threadIdx.x; e < qn * K; e += blockDim.x) (&xs[0][0])[e] = ls[(size_t)q0 * K + e];
+        for (int e = threadIdx.x; e < L::JC * K; e += blockDim.x)
+            (&xs[0][0])[e] = (e / K < qn) ? ls[(size_t)q0 * K + e] : (T)0;
         __syncthreads();
-        if (live) {
-            int q = 0;
-            for (; q + 4 <= qn; q += 4) {
-                T g[4][RT];
+        for (int q = 0; q < qn; q += QG) {
+            load_group(q0 + q + QG, gn);
 #pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    if (pad4 || rb + RT <= m) LoadRT<T, RT>::ld(Gs + (size_t)(q0 + q + u) * ld, g[u]);
-                    else
+            for (int u = 0; u < QG; u++)
 #pragma unroll
-                        for (int r = 0; r < RT; r++) g[u][r] = (rb + r < m) ? Gs[(size_t)(q0 + q + u) * ld + r] : (T)0;
+                for (int c = 0; c < K; c += V) {
+                    T xv[V];
+                    lds16(&xs[q + u][c], xv);
+#pragma unroll
+                    for (int cc = 0; cc < V; cc++)
+#pragma unroll
+                        for (int r = 0; r < RT; r++) acc[r][c + cc] = fma(gc[u][r], xv[cc], acc[r][c + cc]);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; u++)
+            for (int u = 0; u < QG; u++)
 #pragma unroll
-                    for (int c = 0; c < K; c++) {
-                        const T xv = xs[q + u][c];
-#pragma unroll
-                        for (int r = 0; r < RT; r++) acc[r][c] = fma(g[u][r], xv, acc[r][c]);
-                    }
-            }
-            for (; q < qn; q++) {
-                T g[RT];
-                if (pad4 || rb + RT <= m) LoadRT<T, RT>::ld(Gs + (size_t)(q0 + q) * ld, g);
-                else
-#pragma unroll
-                    for (int r = 0; r < RT; r++) g[r] = (rb + r < m) ? Gs[(size_t)(q0 + q) * ld + r] : (T)0;
-#pragma unroll
-                for (int c = 0; c < K; c++) {
-                    const T xv = xs[q][c];
-#pragma unroll
-                    for (int r = 0; r < RT; r++) acc[r][c] = fma(g[r], xv, acc[r][c]);
-                }
-            }
+                for (int r = 0; r < RT; r++) gc[u][r] = gn[u][r];
         }
     }
     if (!live) return;
@@ -524,25 +608,34 @@ __global__ void __launch_bounds__(128) kb_local_gemm(const int* __restrict__ sub
         if (rb + r >= m) break;
         T* o = out + (size_t)(p0 + rb + r) * K;
 #pragma unroll
-        for (int c = 0; c < K; c++) o[c] = acc[r][c];
+        for (int c = 0; c < K; c += V) {
+            if constexpr (sizeof(T) == 4)
+                *reinterpret_cast<float4*>(o + c) = make_float4(acc[r][c], acc[r][c + 1], acc[r][c + 2], acc[r][c + 3]);
+            else
+                *reinterpret_cast<double2*>(o + c) = make_double2(acc[r][c], acc[r][c + 1]);
+        }
     }
 }
 
 // Y = alpha M X + beta Sub in float64, M symmetric dim x dim (row p read as
-// column p), X, Y, Sub dim x K row-major: 16 rows per block, 4 columns per
-// thread, 64-wide chunks of M and X staged in shared memory
-constexpr int DG_RB = 16, DG_JC = 64;
+// column p), X, Y, Sub dim x K row-major.  The float64 pipes of this GPU
+// are its narrowest unit, so the product is spread over about four blocks
+// per SM: block (t, sp) multiplies rows 32 t .. 32 t + 31 of M by the rows
+// jlen sp .. jlen (sp + 1) - 1 of X into part[sp] (each thread 2 rows x 4
+// columns, chunks of 32 staged in shared memory); kb_dense_sum adds the
+// splits in order.
+constexpr int DG_RB = 32, DG_JC = 32, DG_SMAX = 16;
 template <int K>
-__global__ void __launch_bounds__(4 * K) kb_dense_gemm(int dim, const double* __restrict__ Mx,
-                                                       const double* __restrict__ X, double* Y, double alpha,
-                                                       const double* Sub, double beta) {
+__global__ void __launch_bounds__(4 * K) kb_dense_part(int dim, int jlen, const double* __restrict__ Mx,
+                                                       const double* __restrict__ X, double* __restrict__ part) {
     __shared__ double ms[DG_RB][DG_JC + 1];
     __shared__ __align__(16) double xs[DG_JC][K];
     const int r0 = blockIdx.x * DG_RB;
-    const int cg = threadIdx.x % (K / 4), r = threadIdx.x / (K / 4);
-    double acc[4] = {0, 0, 0, 0};
-    for (int j0 = 0; j0 < dim; j0 += DG_JC) {
-        const int jn = min(DG_JC, dim - j0);
+    const int j0s = blockIdx.y * jlen, j1s = min(dim, j0s + jlen);
+    const int cg = threadIdx.x % (K / 4), rp = threadIdx.x / (K / 4);  // rp < 16
+    double acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    for (int j0 = j0s; j0 < j1s; j0 += DG_JC) {
+        const int jn = min(DG_JC, j1s - j0);
         __syncthreads();
         for (int e = threadIdx.x; e < DG_RB * DG_JC; e += blockDim.x) {
             const int rr = e / DG_JC, jj = e % DG_JC;
@@ -551,23 +644,40 @@ __global__ void __launch_bounds__(4 * K) kb_dense_gemm(int dim, const double* __
         for (int e = threadIdx.x; e < DG_JC * K; e += blockDim.x)
             (&xs[0][0])[e] = (e / K < jn) ? X[(size_t)j0 * K + e] : 0.0;
         __syncthreads();
-#pragma unroll 4
+#pragma unroll 8
         for (int jj = 0; jj < DG_JC; jj++) {
-            const double mv = ms[r][jj];
+            const double m0 = ms[2 * rp][jj], m1 = ms[2 * rp + 1][jj];
             const double2 x01 = *reinterpret_cast<const double2*>(&xs[jj][cg * 4]);
             const double2 x23 = *reinterpret_cast<const double2*>(&xs[jj][cg * 4 + 2]);
-            acc[0] = fma(mv, x01.x, acc[0]);
-            acc[1] = fma(mv, x01.y, acc[1]);
-            acc[2] = fma(mv, x23.x, acc[2]);
-            acc[3] = fma(mv, x23.y, acc[3]);
+            acc[0][0] = fma(m0, x01.x, acc[0][0]);
+            acc[0][1] = fma(m0, x01.y, acc[0][1]);
+            acc[0][2] = fma(m0, x23.x, acc[0][2]);
+            acc[0][3] = fma(m0, x23.y, acc[0][3]);
+            acc[1][0] = fma(m1, x01.x, acc[1][0]);
+            acc[1][1] = fma(m1, x01.y, acc[1][1]);
+            acc[1][2] = fma(m1, x23.x, acc[1][2]);
+            acc[1][3] = fma(m1, x23.y, acc[1][3]);
         }
     }
-    if (r0 + r >= dim) return;
 #pragma unroll
-    for (int c = 0; c < 4; c++) {
-        const size_t e = (size_t)(r0 + r) * K + cg * 4 + c;
-        Y[e] = Sub ? fma(beta, Sub[e], alpha * acc[c]) : alpha * acc[c];
+    for (int u = 0; u < 2; u++) {
+        const int row = r0 + 2 * rp + u;
+        if (row >= dim) continue;
+        double* o = part + ((size_t)blockIdx.y * dim + row) * K + cg * 4;
+        *reinterpret_cast<double2*>(o) = make_double2(acc[u][0], acc[u][1]);
+        *reinterpret_cast<double2*>(o + 2) = make_double2(acc[u][2], acc[u][3]);
     }
+}
+
+template <int K>
+__global__ void kb_dense_sum(int dim, int S, const double* __restrict__ part, double* Y, double alpha,
+                             const double* Sub, double beta) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t len = (size_t)dim * K;
+    if (e >= len) return;
+    double v = 0.0;
+    for (int sp = 0; sp < S; sp++) v += part[(size_t)sp * len + e];
+    Y[e] = Sub ? fma(beta, Sub[e], alpha * v) : alpha * v;
 }
 
 // ------------------------------------------- W passes on the CUDA cores
@@ -715,19 +825,21 @@ __global__ void __launch_bounds__(256) kb_colmax(int n, const float* __restrict_
     __shared__ unsigned bm[K];
     if (threadIdx.x < K) bm[threadIdx.x] = 0u;
     __syncthreads();
-    float tm[RM<K>::CPT] = {};
-    ROW_LOOP(K) {
+    float tm[4] = {0.f, 0.f, 0.f, 0.f};
+    int cc = 0;
+    ROW_LOOP(float, K) {
+        float v[4];
+        ldv(X + (size_t)i * K + c0, v);
+        const float sc = rscale ? rscale[i] : 1.f;
 #pragma unroll
-        for (int j = 0; j < M::CPT; j++) {
-            float v = fabsf(X[(size_t)i * K + cl + M::TPR * j]);
-            if (rscale) v *= rscale[i];
-            tm[j] = fmaxf(tm[j], v);
-        }
+        for (int j = 0; j < 4; j++) tm[j] = fmaxf(tm[j], fabsf(v[j]) * sc);
+        cc = c0;
     }
     {
-        const int cl0 = (threadIdx.x & 31) % RM<K>::TPR;
+        const int cl = ((threadIdx.x & 31) % RM<float, K>::TPR) * 4;
+        (void)cc;
 #pragma unroll
-        for (int j = 0; j < RM<K>::CPT; j++) atomicMax(bm + cl0 + RM<K>::TPR * j, __float_as_uint(tm[j]));
+        for (int j = 0; j < 4; j++) atomicMax(bm + cl + j, __float_as_uint(tm[j]));
     }
     __syncthreads();
     if (threadIdx.x < K) atomicMax(mx + threadIdx.x, bm[threadIdx.x]);
@@ -766,50 +878,69 @@ __global__ void kb_split16(int n, int ldb, const float* __restrict__ X, const fl
 }
 
 // Dt (2K x ldw) from Ds (ldw x K float32, cscale applied, zero padding
-// columns): Ds 2^-f_j split in two 16-bit parts.  One block; also stores 2^f_j.
+// columns): Ds 2^-f_j split in two 16-bit parts, 2^f_j >= max_c |Ds(c, j)|
+// from the column maxima mx (kb_colmax over Ds); also stores 2^f_j.
 template <typename H, int K>
-__global__ void kb_split16_d(int ldw, const float* __restrict__ Ds, H* __restrict__ Dt, float* __restrict__ dscale) {
-    __shared__ unsigned cmx[K];
-    if (threadIdx.x < K) cmx[threadIdx.x] = 0u;
-    __syncthreads();
-    for (int e = threadIdx.x; e < ldw * K; e += blockDim.x) atomicMax(cmx + (e % K), __float_as_uint(fabsf(Ds[e])));
-    __syncthreads();
-    for (int e = threadIdx.x; e < ldw * K; e += blockDim.x) {
-        const int j = e / ldw, c = e % ldw;
-        const float v = Ds[(size_t)c * K + j] * pow2_ceil_inv(__uint_as_float(cmx[j]));
-        H hi, lo;
-        if constexpr (std::is_same<H, __half>::value) {
-            hi = __float2half_rn(v);
-            lo = __float2half_rn(v - __half2float(hi));
-        } else {
-            hi = __float2bfloat16_rn(v);
-            lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-        }
-        Dt[(size_t)j * ldw + c] = hi;
-        Dt[(size_t)(K + j) * ldw + c] = lo;
+__global__ void kb_split16_d(int ldw, const float* __restrict__ Ds, const unsigned* __restrict__ mx,
+                             H* __restrict__ Dt, float* __restrict__ dscale) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ldw * K) return;
+    const int j = e / ldw, c = e % ldw;
+    const float inv = pow2_ceil_inv(__uint_as_float(mx[j]));
+    const float v = Ds[(size_t)c * K + j] * inv;
+    H hi, lo;
+    if constexpr (std::is_same<H, __half>::value) {
+        hi = __float2half_rn(v);
+        lo = __float2half_rn(v - __half2float(hi));
+    } else {
+        hi = __float2bfloat16_rn(v);
+        lo = __float2bfloat16_rn(v - __bfloat162float(hi));
     }
-    if (threadIdx.x < K) dscale[threadIdx.x] = 1.f / pow2_ceil_inv(__uint_as_float(cmx[threadIdx.x]));
+    Dt[(size_t)j * ldw + c] = hi;
+    Dt[(size_t)(K + j) * ldw + c] = lo;
+    if (c == 0) dscale[j] = 1.f / inv;
 }
 
-// out(c, j) = 2^e_j cscale_c (sum_b part[b][c * K + j]) + correction, float64
+// out(c, j) = cscale_c (2^e_j sum_b part[b][c * K + j] + sum_k C_kc S_r X(k, j)),
+// float64: one block per column c; the column's correction entries are
+// spread over the block (K / 4 threads per entry, 16 bytes of X each) and
+// their sums meet in shared memory in a fixed order
 template <int K>
-__global__ void kb_wt_reduce_umma(int nb, int ldw, int nm, const float* __restrict__ part,
-                                  const unsigned* __restrict__ mx, const float* __restrict__ cscale,
-                                  const int* __restrict__ ccp, const int* __restrict__ crow,
-                                  const float* __restrict__ cval, const float* __restrict__ X,
-                                  const float* __restrict__ rscale, double* out) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nm * K) return;
-    const int c = e / K, j = e % K;
-    float v = 0.f;
-    for (int b = 0; b < nb; b++) v += part[((size_t)b * ldw + c) * K + j];
-    v *= 1.f / pow2_ceil_inv(__uint_as_float(mx[j]));
-    if (ccp)
-        for (int k = ccp[c]; k < ccp[c + 1]; k++) {
+__global__ void __launch_bounds__(256) kb_wt_reduce_umma(int nb, int ldw, int nm, const float* __restrict__ part,
+                                                         const unsigned* __restrict__ mx,
+                                                         const float* __restrict__ cscale,
+                                                         const int* __restrict__ ccp, const int* __restrict__ crow,
+                                                         const float* __restrict__ cval, const float* __restrict__ X,
+                                                         const float* __restrict__ rscale, double* out) {
+    constexpr int TPE = K / 4, EPB = 256 / TPE;
+    __shared__ float red[EPB][K];
+    const int c = blockIdx.x;
+    const int slot = threadIdx.x / TPE, j0 = (threadIdx.x % TPE) * 4;
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    if (ccp) {
+        const int k1 = ccp[c + 1];
+        for (int k = ccp[c] + slot; k < k1; k += EPB) {
             const int i = crow[k];
-            v = fmaf(cval[k], X[(size_t)i * K + j] * (rscale ? rscale[i] : 1.f), v);
+            const float cv = cval[k] * (rscale ? rscale[i] : 1.f);
+            float xv[4];
+            ldv(X + (size_t)i * K + j0, xv);
+#pragma unroll
+            for (int j = 0; j < 4; j++) a[j] = fmaf(cv, xv[j], a[j]);
         }
-    out[e] = cscale ? (double)v * (double)cscale[c] : (double)v;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++) red[slot][j0 + j] = a[j];
+    __syncthreads();
+    if (threadIdx.x < K) {
+        const int j = threadIdx.x;
+        float v = 0.f;
+        for (int b = 0; b < nb; b++) v += part[((size_t)b * ldw + c) * K + j];
+        v *= 1.f / pow2_ceil_inv(__uint_as_float(mx[j]));
+        float corr = 0.f;
+        for (int t = 0; t < EPB; t++) corr += red[t][j];
+        v += corr;
+        out[(size_t)c * K + j] = cscale ? (double)v * (double)cscale[c] : (double)v;
+    }
 }
 
 // out(i, :) = V(i, :) + rscale_i (2^f_j acc(i, j) + sum_k C_ik Ds(col_k, j))
@@ -819,17 +950,33 @@ __global__ void __launch_bounds__(256) kb_wd_finish_umma(int n, const float* __r
                                                          const float* __restrict__ rscale, const int* __restrict__ crp,
                                                          const int* __restrict__ ccol, const float* __restrict__ cval,
                                                          const float* __restrict__ Ds, const float* V, float* out) {
-    ROW_LOOP(K) {
+    ROW_LOOP(float, K) {
+        const size_t e = (size_t)i * K + c0;
+        float v[4], d[4];
+        ldv(acc + e, v);
+        ldv(dscale + c0, d);
 #pragma unroll
-        for (int j = 0; j < M::CPT; j++) {
-            const int c = cl + M::TPR * j;
-            const size_t e = (size_t)i * K + c;
-            float v = acc[e] * dscale[c];
-            if (crp)
-                for (int k = crp[i]; k < crp[i + 1]; k++) v = fmaf(cval[k], Ds[(size_t)ccol[k] * K + c], v);
-            if (rscale) v *= rscale[i];
-            out[e] = (V ? V[e] : 0.f) + v;
+        for (int j = 0; j < 4; j++) v[j] *= d[j];
+        if (crp)
+            for (int k = crp[i]; k < crp[i + 1]; k++) {
+                float dv[4];
+                ldv(Ds + (size_t)ccol[k] * K + c0, dv);
+                const float cv = cval[k];
+#pragma unroll
+                for (int j = 0; j < 4; j++) v[j] = fmaf(cv, dv[j], v[j]);
+            }
+        if (rscale) {
+            const float r = rscale[i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) v[j] *= r;
         }
+        if (V) {
+            float t[4];
+            ldv(V + e, t);
+#pragma unroll
+            for (int j = 0; j < 4; j++) v[j] += t[j];
+        }
+        stv(out + e, v);
     }
 }
 
@@ -842,6 +989,8 @@ struct BView {
     T *rin, *x1, *t, *u, *q, *out, *tmpw, *loc, *loc2, *cm, *cf;
     // coarse vectors, float64 (n0 x K, n_- x K)
     double *y0, *y2, *c1, *c2, *w0, *dd, *w1, *y0d;
+    double *dpm, *dps;  // split partials of the float64 coarse GEMMs (main, side stream)
+    T* tgp;             // p-split partials of the block-sparse transposed products
     // W passes
     void* part;    // row-block partials (compute type)
     void* xs;      // S_r X (compute type), n x K
@@ -850,7 +999,8 @@ struct BView {
     void* dt;      //                        2K x ldw
     float* wacc;   // tensor-core W d accumulators, n x K
     float* dscale;
-    unsigned* mx;  // column maxima (float bits)
+    unsigned* mx;  // column maxima (float bits) of S_r X
+    unsigned* mx2; //                             of S_c D
     int* err;
     // PCG (float64, n x K)
     double *pb, *px, *pr, *pp, *pq, *pz;
@@ -878,6 +1028,9 @@ size_t carve_block(const Handle* h, char* base, BView<double>* vd, BView<float>*
     d.y0 = (double*)take(n0 * K * 8); d.y2 = (double*)take(n0 * K * 8); d.c1 = (double*)take(n0 * K * 8);
     d.c2 = (double*)take(n0 * K * 8); d.y0d = (double*)take(std::max(n0, nm) * K * 8);
     d.w0 = (double*)take(nm * K * 8); d.dd = (double*)take(nm * K * 8); d.w1 = (double*)take(nm * K * 8);
+    d.dpm = (double*)take((size_t)DG_SMAX * n0 * K * 8);
+    d.dps = (double*)take((size_t)DG_SMAX * nm * K * 8);
+    d.tgp = (double*)take((size_t)TG_PS * std::max<size_t>(n0, std::max(1, h->n_minus_all)) * K * 8);
     d.part = take((size_t)WT_SPLITS_MAX * ldw * K * 8);
     d.xs = take(n * K * 8);
     d.ds = take(ldw * K * 8);
@@ -886,6 +1039,7 @@ size_t carve_block(const Handle* h, char* base, BView<double>* vd, BView<float>*
     d.wacc = (float*)take(n * K * 4);
     d.dscale = (float*)take(K * 4);
     d.mx = (unsigned*)take(K * 4);
+    d.mx2 = (unsigned*)take(K * 4);
     d.err = (int*)take(64);
     d.pb = (double*)take(n * K * 8); d.px = (double*)take(n * K * 8); d.pr = (double*)take(n * K * 8);
     d.pp = (double*)take(n * K * 8); d.pq = (double*)take(n * K * 8); d.pz = (double*)take(n * K * 8);
@@ -899,8 +1053,9 @@ size_t carve_block(const Handle* h, char* base, BView<double>* vd, BView<float>*
         f.out = (float*)d.out; f.tmpw = (float*)d.tmpw; f.loc = (float*)d.loc; f.loc2 = (float*)d.loc2;
         f.cm = (float*)d.cm; f.cf = (float*)d.cf;
         f.y0 = d.y0; f.y2 = d.y2; f.c1 = d.c1; f.c2 = d.c2; f.y0d = d.y0d; f.w0 = d.w0; f.dd = d.dd; f.w1 = d.w1;
+        f.dpm = d.dpm; f.dps = d.dps; f.tgp = (float*)d.tgp;
         f.part = d.part; f.xs = d.xs; f.ds = d.ds; f.bt = d.bt; f.dt = d.dt; f.wacc = d.wacc;
-        f.dscale = d.dscale; f.mx = d.mx; f.err = d.err;
+        f.dscale = d.dscale; f.mx = d.mx; f.mx2 = d.mx2; f.err = d.err;
         f.pb = d.pb; f.px = d.px; f.pr = d.pr; f.pp = d.pp; f.pq = d.pq; f.pz = d.pz;
         f.sc = d.sc; f.red = d.red; f.cnt = d.cnt;
         *vf = f;
@@ -958,7 +1113,7 @@ struct BlockApply {
     BView<T> v;
     using A = T;
 
-    static dim3 rows_grid(int n) { return dim3(grid_rows(n, RM<K>::RPB)); }
+    static dim3 rows_grid(int n) { return dim3(grid_rows(n, RM<T, K>::RPB)); }
 
     const T* aval() const { return fl<T>(h->val, h->bval32); }
     const T* vm() const { return fl<T>(h->Vm, h->bvm32); }
@@ -978,13 +1133,17 @@ struct BlockApply {
         return AWG_OK;
     }
 
-    // C = wsign w .* (B^T X) per subdomain
-    awg_status tgemv(const int* colptr, const int64_t* boff, const T* B, int maxc, const T* X, const T* w,
-                     T wsign, T* C, cudaStream_t s) {
-        if (maxc == 0) return AWG_OK;
+    // C = wsign w .* (B^T X) per subdomain (ncol_total columns in all)
+    awg_status tgemv(const int* colptr, const int64_t* boff, const T* B, int maxc, int ncol_total, const T* X,
+                     const T* w, T wsign, T* C, cudaStream_t s) {
+        if (maxc == 0 || ncol_total == 0) return AWG_OK;
         ProfScope ps_(h, AWG_PROF_SUBDOMAIN, s);
-        const dim3 g(h->N, (maxc + KB_TG_C - 1) / KB_TG_C);
-        kb_tgemv<T, K><<<g, 128, 0, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p, colptr, boff, B, X, w, wsign, C);
+        const dim3 g(h->N, (maxc + KB_TG_C - 1) / KB_TG_C, TG_PS);
+        kb_tgemv<T, K><<<g, 256, 0, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p, colptr, boff, B, X, ncol_total,
+                                         v.tgp);
+        AWG_LAUNCH();
+        const size_t len = (size_t)ncol_total * K;
+        kb_tg_sum<T, K><<<(unsigned)((len + 255) / 256), 256, 0, s>>>(ncol_total, v.tgp, w, wsign, C);
         AWG_LAUNCH();
         return AWG_OK;
     }
@@ -994,7 +1153,8 @@ struct BlockApply {
         const bool vmb = h->n_minus_all > 0;
         if (vmb) {
             const int maxc = *std::max_element(h->h_nm.begin(), h->h_nm.end());
-            AWG_TRY(tgemv((int*)h->nm_ptr.p, (int64_t*)h->vm_off.p, vm(), maxc, X, lam(), (T)1, v.cm, s));
+            AWG_TRY(tgemv((int*)h->nm_ptr.p, (int64_t*)h->vm_off.p, vm(), maxc, h->n_minus_all, X, lam(), (T)1,
+                          v.cm, s));
         }
         ProfScope ps_(h, AWG_PROF_SPMV, s);
         kb_aplus<T, K><<<rows_grid(h->n), 256, 0, s>>>(
@@ -1009,9 +1169,9 @@ struct BlockApply {
     awg_status zt(const T* X, double* c, cudaStream_t s) {
         const int maxc = *std::max_element(h->h_modes.begin(), h->h_modes.end());
         if constexpr (std::is_same<T, double>::value) {
-            return tgemv((int*)h->mode_ptr.p, (int64_t*)h->z_off.p, zb(), maxc, X, nullptr, (T)1, c, s);
+            return tgemv((int*)h->mode_ptr.p, (int64_t*)h->z_off.p, zb(), maxc, h->n0, X, nullptr, (T)1, c, s);
         } else {
-            AWG_TRY(tgemv((int*)h->mode_ptr.p, (int64_t*)h->z_off.p, zb(), maxc, X, nullptr, (T)1, v.cf, s));
+            AWG_TRY(tgemv((int*)h->mode_ptr.p, (int64_t*)h->z_off.p, zb(), maxc, h->n0, X, nullptr, (T)1, v.cf, s));
             return cvt_t2d(v.cf, c, (size_t)h->n0 * K, s);
         }
     }
@@ -1033,11 +1193,21 @@ struct BlockApply {
         return AWG_OK;
     }
 
+    // Y = alpha M X + beta Sub (float64); part: the partial buffer of the
+    // stream s (the main and side streams each own one)
     awg_status dense(int dim, const double* Mx, const double* X, double* Y, double alpha, const double* Sub,
-                     double beta, cudaStream_t s) {
+                     double beta, double* part, cudaStream_t s) {
         if (dim == 0) return AWG_OK;
         ProfScope ps_(h, AWG_PROF_COARSE, s);
-        kb_dense_gemm<K><<<(dim + DG_RB - 1) / DG_RB, 4 * K, 0, s>>>(dim, Mx, X, Y, alpha, Sub, beta);
+        const int tiles = (dim + DG_RB - 1) / DG_RB;
+        int S = std::max(1, std::min(DG_SMAX, (4 * 152 + tiles - 1) / tiles));
+        int jlen = (dim + S - 1) / S;
+        jlen = (jlen + DG_JC - 1) / DG_JC * DG_JC;
+        S = (dim + jlen - 1) / jlen;
+        kb_dense_part<K><<<dim3(tiles, S), 4 * K, 0, s>>>(dim, jlen, Mx, X, part);
+        AWG_LAUNCH();
+        const size_t len = (size_t)dim * K;
+        kb_dense_sum<K><<<(unsigned)((len + 255) / 256), 256, 0, s>>>(dim, S, part, Y, alpha, Sub, beta);
         AWG_LAUNCH();
         return AWG_OK;
     }
@@ -1085,13 +1255,13 @@ struct BlockApply {
         }
         const int n0 = h->n0;
         AWG_TRY(zt(X, v.y0, s));                                                   // y0 = Z^T X
-        AWG_TRY(dense(n0, (double*)h->Einv.p, v.y0, v.c1, 1.0, nullptr, 0.0, s));  // c1 = E^-1 y0
+        AWG_TRY(dense(n0, (double*)h->Einv.p, v.y0, v.c1, 1.0, nullptr, 0.0, v.dpm, s));  // c1 = E^-1 y0
         AWG_TRY(zc(v.c1, v.x1, (T)1, (T)0, nullptr, (T)0, nullptr, s));            // x1 = Z c1
         AWG_TRY(aplus(v.x1, v.t, X, (T)-1, s));                                    // t = X - A_+ x1
         AWG_TRY(hnn(prec, v.t, v.u, s));                                           // u = H^NN t
         AWG_TRY(aplus(v.u, v.q, nullptr, (T)1, s));                                // q = A_+ u
         AWG_TRY(zt(v.q, v.y2, s));
-        AWG_TRY(dense(n0, (double*)h->Einv.p, v.y2, v.c2, 1.0, v.c1, -1.0, s));    // c2 = E^-1 y2 - c1
+        AWG_TRY(dense(n0, (double*)h->Einv.p, v.y2, v.c2, 1.0, v.c1, -1.0, v.dpm, s));    // c2 = E^-1 y2 - c1
         if (wait) AWG_CUDA(cudaStreamWaitEvent(s, wait, 0));
         return zc(v.c2, Y, (T)-1, (T)0, v.u, (T)1, V2, s);                         // Y = u - Z c2 (+ V2)
     }
@@ -1106,7 +1276,7 @@ struct BlockApply {
         if constexpr (std::is_same<T, float>::value) {
             if ((prec == AWG_MIXED_FP16 || prec == AWG_MIXED_BF16) && h->opt.block_tensor_cores &&
                 umma_available()) {
-                const unsigned gr = grid_rows(n, RM<K>::RPB);
+                const unsigned gr = grid_rows(n, RM<float, K>::RPB);
                 {
                     ProfScope ps_(h, AWG_PROF_VECTOR, s);
                     AWG_CUDA(cudaMemsetAsync(v.mx, 0, K * 4, s));
@@ -1127,7 +1297,7 @@ struct BlockApply {
                     AWG_TRY(umma_wt(u, K, v.bt, ldb(), (float*)v.part, splits, v.err, s));
                 }
                 ProfScope ps_(h, AWG_PROF_VECTOR, s);
-                kb_wt_reduce_umma<K><<<(nm * K + 255) / 256, 256, 0, s>>>(
+                kb_wt_reduce_umma<K><<<nm, 256, 0, s>>>(
                     splits, ldw, nm, (float*)v.part, v.mx, csc, cor ? (int*)P.corr_colptr.p : nullptr,
                     cor ? (int*)P.corr_row.p : nullptr, cor ? (float*)P.corr_cval.p : nullptr, X, rsc, w0);
                 AWG_LAUNCH();
@@ -1186,11 +1356,15 @@ struct BlockApply {
                     ProfScope ps_(h, AWG_PROF_VECTOR, s);
                     kb_d_scaled<float, K><<<(ldw * K + 255) / 256, 256, 0, s>>>(nm, ldw, d, csc, (float*)v.ds);
                     AWG_LAUNCH();
+                    AWG_CUDA(cudaMemsetAsync(v.mx2, 0, K * 4, s));
+                    kb_colmax<K><<<grid_rows(ldw, RM<float, K>::RPB), 256, 0, s>>>(ldw, (float*)v.ds, nullptr, v.mx2);
+                    AWG_LAUNCH();
+                    const unsigned gs = (ldw * K + 255) / 256;
                     if (prec == AWG_MIXED_FP16)
-                        kb_split16_d<__half, K><<<1, 1024, 0, s>>>(ldw, (float*)v.ds, (__half*)v.dt, v.dscale);
+                        kb_split16_d<__half, K><<<gs, 256, 0, s>>>(ldw, (float*)v.ds, v.mx2, (__half*)v.dt, v.dscale);
                     else
-                        kb_split16_d<__nv_bfloat16, K><<<1, 1024, 0, s>>>(ldw, (float*)v.ds, (__nv_bfloat16*)v.dt,
-                                                                         v.dscale);
+                        kb_split16_d<__nv_bfloat16, K><<<gs, 256, 0, s>>>(ldw, (float*)v.ds, v.mx2,
+                                                                         (__nv_bfloat16*)v.dt, v.dscale);
                     AWG_LAUNCH();
                 }
                 UmmaW u;
@@ -1200,7 +1374,7 @@ struct BlockApply {
                     AWG_TRY(umma_wd(u, K, v.dt, v.wacc, v.err, s));
                 }
                 ProfScope ps_(h, AWG_PROF_VECTOR, s);
-                kb_wd_finish_umma<K><<<grid_rows(n, RM<K>::RPB), 256, 0, s>>>(
+                kb_wd_finish_umma<K><<<grid_rows(n, RM<float, K>::RPB), 256, 0, s>>>(
                     n, v.wacc, v.dscale, rsc, cor ? (int*)P.corr_rowptr.p : nullptr,
                     cor ? (int*)P.corr_col.p : nullptr, cor ? (float*)P.corr_val.p : nullptr, (float*)v.ds, V, out);
                 AWG_LAUNCH();
@@ -1254,7 +1428,8 @@ struct BlockApply {
                 AWG_CUDA(cudaEventRecord(h->ev_fork, s));
                 AWG_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
                 AWG_TRY(wt(prec, X, v.w0, h->side));
-                AWG_TRY(dense(h->n_minus, (double*)h->prec[prec].Finv.p, v.w0, v.dd, 1.0, nullptr, 0.0, h->side));
+                AWG_TRY(dense(h->n_minus, (double*)h->prec[prec].Finv.p, v.w0, v.dd, 1.0, nullptr, 0.0, v.dps,
+                               h->side));
                 AWG_TRY(wd(prec, v.dd, v.tmpw, nullptr, h->side));
                 AWG_CUDA(cudaEventRecord(h->ev_join, h->side));
                 return h2(prec, X, Y, s, v.tmpw, h->ev_join);
@@ -1308,7 +1483,7 @@ awg_status pcg_k(Handle* h, int prec, const double* b, double* x, int nrhs, int 
     carve_block(h, (char*)h->bws.p, &v, nullptr);
     const int n = h->n;
     const dim3 tg((n + 31) / 32, (K + 31) / 32), tb(32, 8);
-    const unsigned gr = grid_rows(n, RM<K>::RPB);
+    const unsigned gr = grid_rows(n, RM<double, K>::RPB);
     double* sc = v.sc;
     const size_t len = (size_t)n * K;
     auto prof_vec = [&](auto&& f) -> awg_status {
