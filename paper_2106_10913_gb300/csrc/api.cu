@@ -58,7 +58,8 @@ static void free_all(Handle* h) {
                       &h->bval, &h->dense_off, &h->g32_off, &h->nm, &h->nstrict, &h->nm_ptr, &h->vm_off,
                       &h->Vm, &h->lam_m, &h->sigma, &h->modes, &h->mode_ptr, &h->z_off, &h->Z,
                       &h->E, &h->Einv, &h->wcol_ptr, &h->Wcm, &h->F64, &h->ws, &h->flag, &h->red,
-                      &h->bws, &h->bval32, &h->bvm32, &h->blam32, &h->blam64, &h->bz32};
+                      &h->bws, &h->bval32, &h->bvm32, &h->blam32, &h->blam64, &h->bz32,
+                      &h->ul_gt, &h->ul_gtoff, &h->ul_kcpre, &h->ul_tsub, &h->ul_trt};
     for (DevBuf* b : bufs) dfree(h, *b);
     for (auto& P : h->prec) {
         dfree(h, P.G);
@@ -74,11 +75,12 @@ static void free_all(Handle* h) {
     h->ev_pool.clear();
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_mid) cudaEventDestroy(h->ev_mid);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->side) cudaStreamDestroy(h->side);
     if (h->hp) cudaStreamDestroy(h->hp);
-    h->ev_fork = h->ev_join = h->ev_in = h->ev_out = nullptr;
+    h->ev_fork = h->ev_join = h->ev_mid = h->ev_in = h->ev_out = nullptr;
     h->side = h->hp = nullptr;
     if (h->h_flag) cudaFreeHost(h->h_flag);
     if (h->h_scal) cudaFreeHost(h->h_scal);
@@ -146,6 +148,7 @@ static awg_status setup_impl(Handle* h, const int* d_rowptr, const int* d_colidx
     AWG_CUDA(cudaStreamCreateWithPriority(&h->hp, cudaStreamNonBlocking, prio_greatest));
     AWG_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     AWG_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    AWG_CUDA(cudaEventCreateWithFlags(&h->ev_mid, cudaEventDisableTiming));
     AWG_CUDA(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
     AWG_CUDA(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
     AWG_TRY(dalloc(h, h->flag, sizeof(int)));

@@ -141,6 +141,10 @@ struct Handle {
     // A's values, V^s_-, |Lambda^s_-| and Z (built on the first block call),
     // |Lambda^s_-| in float64
     DevBuf bws, bval32, bvm32, blam32, blam64, bz32;
+    // tensor-core local solves of the block path: 16 KB images of the
+    // float32 local pseudo-inverses and their tables (ul_ntiles = 0: not built)
+    DevBuf ul_gt, ul_gtoff, ul_kcpre, ul_tsub, ul_trt;
+    int ul_ntiles = 0, ul_maxkc = 0, ul_maxtiles = 0;
     DevBuf flag;                         // int status word
     DevBuf red;                          // partial-sum scratch
     int red_blocks = 0;
@@ -150,6 +154,10 @@ struct Handle {
     // H_2 on the caller's stream (fork and join through the two events)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // block path: recorded after the first E^-1 of H_2 on the main stream;
+    // the side stream's F^-1 waits for it, so the two float64 GEMMs do not
+    // share the FP64 pipes
+    cudaEvent_t ev_mid = nullptr;
     // awg_pcg and awg_apply run on `hp`, created with the highest stream
     // priority (`side` has the lowest): blocks of the H_2 chain, the critical
     // path, are dispatched ahead of the bandwidth-bound W^T r pass, which
@@ -190,6 +198,9 @@ struct ProfScope {
         }
     }
 };
+
+// Kernels launched inside one ProfScope beyond its first (launch count).
+inline void extra_launches(Handle* h, int k) { h->launches += (h->prof != 0) * k; }
 
 awg_status dalloc(Handle* h, DevBuf& b, size_t bytes);
 void dfree(Handle* h, DevBuf& b);

@@ -998,6 +998,7 @@ struct BView {
     void* bt;      // 16-bit split operands: 2K x n
     void* dt;      //                        2K x ldw
     float* wacc;   // tensor-core W d accumulators, n x K
+    float* lt;     // tensor-core local solves: TF32 hi / lo right-hand-side images
     float* dscale;
     unsigned* mx;  // column maxima (float bits) of S_r X
     unsigned* mx2; //                             of S_c D
@@ -1041,6 +1042,11 @@ size_t carve_block(const Handle* h, char* base, BView<double>* vd, BView<float>*
     d.mx = (unsigned*)take(K * 4);
     d.mx2 = (unsigned*)take(K * 4);
     d.err = (int*)take(64);
+    {
+        int64_t kcs = 0;
+        for (int t = 0; t < h->N; t++) kcs += (h->h_ns[t] + 31) / 32;
+        d.lt = (float*)take((size_t)kcs * 2 * K * 32 * 4);
+    }
     d.pb = (double*)take(n * K * 8); d.px = (double*)take(n * K * 8); d.pr = (double*)take(n * K * 8);
     d.pp = (double*)take(n * K * 8); d.pq = (double*)take(n * K * 8); d.pz = (double*)take(n * K * 8);
     d.sc = (double*)take(B_NSC * K * 8);
@@ -1054,7 +1060,7 @@ size_t carve_block(const Handle* h, char* base, BView<double>* vd, BView<float>*
         f.cm = (float*)d.cm; f.cf = (float*)d.cf;
         f.y0 = d.y0; f.y2 = d.y2; f.c1 = d.c1; f.c2 = d.c2; f.y0d = d.y0d; f.w0 = d.w0; f.dd = d.dd; f.w1 = d.w1;
         f.dpm = d.dpm; f.dps = d.dps; f.tgp = (float*)d.tgp;
-        f.part = d.part; f.xs = d.xs; f.ds = d.ds; f.bt = d.bt; f.dt = d.dt; f.wacc = d.wacc;
+        f.part = d.part; f.xs = d.xs; f.ds = d.ds; f.bt = d.bt; f.dt = d.dt; f.wacc = d.wacc; f.lt = d.lt;
         f.dscale = d.dscale; f.mx = d.mx; f.mx2 = d.mx2; f.err = d.err;
         f.pb = d.pb; f.px = d.px; f.pr = d.pr; f.pp = d.pp; f.pq = d.pq; f.pz = d.pz;
         f.sc = d.sc; f.red = d.red; f.cnt = d.cnt;
@@ -1070,6 +1076,22 @@ template <> float* fl<float>(const DevBuf&, const DevBuf& d32) { return (float*)
 int grid_rows(int n, int rpb) { return std::max(1, std::min((n + rpb - 1) / rpb, 152 * 8)); }
 
 }  // namespace
+
+UmmaLocal ul_of(const Handle* h) {
+    UmmaLocal u;
+    u.N = h->N;
+    u.ntiles = h->ul_ntiles;
+    u.max_kc = h->ul_maxkc;
+    u.max_tiles_sub = h->ul_maxtiles;
+    u.sub_ptr = (const int*)h->sub_ptr.p;
+    u.sub_idx = (const int*)h->sub_idx.p;
+    u.Gt = (const float*)h->ul_gt.p;
+    u.gt_off = (const int64_t*)h->ul_gtoff.p;
+    u.kc_prefix = (const int64_t*)h->ul_kcpre.p;
+    u.tile_sub = (const int*)h->ul_tsub.p;
+    u.tile_rt = (const int*)h->ul_trt.p;
+    return u;
+}
 
 // Float32 copies of the small operators the float32 block apply reads (A's
 // values, V^s_-, |Lambda^s_-|, Z), the workspace, and the side stream's
@@ -1098,6 +1120,33 @@ awg_status block_prepare(Handle* h) {
         AWG_CUDA(cudaMemcpy(h->blam64.p, hv.data(), hv.size() * 8, cudaMemcpyHostToDevice));
     }
     AWG_TRY(cvt(h->bz32, h->Z, (size_t)(h->h_z_off.empty() ? 0 : h->h_z_off[h->N]), false));
+    if (h->prec[AWG_MIXED_FP32].G.p && h->opt.block_tensor_cores && umma_available()) {
+        // 16 KB images of G_s, 128-row tiles by 32-column chunks
+        const int N = h->N;
+        std::vector<int64_t> gtoff(N), kcpre(N + 1, 0);
+        std::vector<int> tsub, trt;
+        int64_t tiles = 0;
+        int maxkc = 0, maxtiles = 0;
+        for (int t = 0; t < N; t++) {
+            const int m = h->h_ns[t], RT = (m + 127) / 128, KC = (m + 31) / 32;
+            gtoff[t] = tiles;
+            tiles += (int64_t)RT * KC;
+            kcpre[t + 1] = kcpre[t] + KC;
+            maxkc = std::max(maxkc, KC);
+            maxtiles = std::max(maxtiles, RT * KC);
+            for (int r = 0; r < RT; r++) { tsub.push_back(t); trt.push_back(r); }
+        }
+        AWG_TRY(dalloc(h, h->ul_gt, (size_t)tiles * 16384));
+        AWG_TRY(upload(h, h->ul_gtoff, gtoff.data(), N * 8));
+        AWG_TRY(upload(h, h->ul_kcpre, kcpre.data(), (N + 1) * 8));
+        AWG_TRY(upload(h, h->ul_tsub, tsub.data(), tsub.size() * 4));
+        AWG_TRY(upload(h, h->ul_trt, trt.data(), trt.size() * 4));
+        h->ul_ntiles = (int)tsub.size();
+        h->ul_maxkc = maxkc;
+        h->ul_maxtiles = maxtiles;
+        AWG_TRY(umma_local_tiles(ul_of(h), (int64_t*)h->g32_off.p, (float*)h->prec[AWG_MIXED_FP32].G.p, s));
+        AWG_CUDA(cudaStreamSynchronize(s));
+    }
     const size_t bytes = carve_block(h, nullptr, nullptr, nullptr);
     AWG_TRY(dalloc(h, h->bws, bytes));
     AWG_CUDA(cudaMemset(h->bws.p, 0, bytes));
@@ -1145,6 +1194,7 @@ struct BlockApply {
         const size_t len = (size_t)ncol_total * K;
         kb_tg_sum<T, K><<<(unsigned)((len + 255) / 256), 256, 0, s>>>(ncol_total, v.tgp, w, wsign, C);
         AWG_LAUNCH();
+        extra_launches(h, 1);
         return AWG_OK;
     }
 
@@ -1172,6 +1222,7 @@ struct BlockApply {
             return tgemv((int*)h->mode_ptr.p, (int64_t*)h->z_off.p, zb(), maxc, h->n0, X, nullptr, (T)1, c, s);
         } else {
             AWG_TRY(tgemv((int*)h->mode_ptr.p, (int64_t*)h->z_off.p, zb(), maxc, h->n0, X, nullptr, (T)1, v.cf, s));
+            ProfScope ps_(h, AWG_PROF_VECTOR, s);
             return cvt_t2d(v.cf, c, (size_t)h->n0 * K, s);
         }
     }
@@ -1182,6 +1233,7 @@ struct BlockApply {
         if constexpr (std::is_same<T, double>::value) {
             cc = c;
         } else {
+            ProfScope pc_(h, AWG_PROF_VECTOR, s);
             AWG_TRY(cvt_d2t(c, v.cf, (size_t)h->n0 * K, s));
             cc = v.cf;
         }
@@ -1209,11 +1261,26 @@ struct BlockApply {
         const size_t len = (size_t)dim * K;
         kb_dense_sum<K><<<(unsigned)((len + 255) / 256), 256, 0, s>>>(dim, S, part, Y, alpha, Sub, beta);
         AWG_LAUNCH();
+        extra_launches(h, 1);
         return AWG_OK;
     }
 
     // Y = H^NN X
     awg_status hnn(int prec, const T* X, T* Y, cudaStream_t s) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (h->ul_ntiles > 0) {  // tensor cores: gather + TF32 split, then the tile GEMMs
+                {
+                    ProfScope ps_(h, AWG_PROF_LOCAL, s);
+                    AWG_TRY(umma_local(ul_of(h), K, X, v.lt, v.loc2, v.err, s));
+                    extra_launches(h, 1);
+                }
+                ProfScope ps_(h, AWG_PROF_PROLONG, s);
+                kb_prolong<T, K><<<rows_grid(h->n), 256, 0, s>>>(h->n, (int*)h->inc_ptr.p, (int*)h->inc_pos.p, v.loc2,
+                                                                Y, (T)1, (T)0, nullptr, (T)0);
+                AWG_LAUNCH();
+                return AWG_OK;
+            }
+        }
         {
             ProfScope ps_(h, AWG_PROF_PROLONG, s);
             const int64_t len = h->sum_ns * K;
@@ -1240,8 +1307,15 @@ struct BlockApply {
         return AWG_OK;
     }
 
-    // Y = H_2 X (+ V2 after the event `wait`)
-    awg_status h2(int prec, const T* X, T* Y, cudaStream_t s, const T* V2 = nullptr, cudaEvent_t wait = nullptr) {
+    // H_2 X = Pi H^NN Pi^T X + Z E^-1 Z^T X (Thm. 4) in two parts, so that
+    // another stream's work can be issued between them: h2a computes
+    // c1 = E^-1 Z^T X, h2b the rest (+ V2 once the event `wait` completed)
+    awg_status h2a(const T* X, cudaStream_t s) {
+        if (h->n0 == 0) return AWG_OK;
+        AWG_TRY(zt(X, v.y0, s));                                                          // y0 = Z^T X
+        return dense(h->n0, (double*)h->Einv.p, v.y0, v.c1, 1.0, nullptr, 0.0, v.dpm, s);  // c1 = E^-1 y0
+    }
+    awg_status h2b(int prec, const T* X, T* Y, cudaStream_t s, const T* V2 = nullptr, cudaEvent_t wait = nullptr) {
         if (h->n0 == 0) {
             AWG_TRY(hnn(prec, X, Y, s));
             if (V2) {
@@ -1254,16 +1328,18 @@ struct BlockApply {
             return AWG_OK;
         }
         const int n0 = h->n0;
-        AWG_TRY(zt(X, v.y0, s));                                                   // y0 = Z^T X
-        AWG_TRY(dense(n0, (double*)h->Einv.p, v.y0, v.c1, 1.0, nullptr, 0.0, v.dpm, s));  // c1 = E^-1 y0
         AWG_TRY(zc(v.c1, v.x1, (T)1, (T)0, nullptr, (T)0, nullptr, s));            // x1 = Z c1
         AWG_TRY(aplus(v.x1, v.t, X, (T)-1, s));                                    // t = X - A_+ x1
         AWG_TRY(hnn(prec, v.t, v.u, s));                                           // u = H^NN t
         AWG_TRY(aplus(v.u, v.q, nullptr, (T)1, s));                                // q = A_+ u
         AWG_TRY(zt(v.q, v.y2, s));
-        AWG_TRY(dense(n0, (double*)h->Einv.p, v.y2, v.c2, 1.0, v.c1, -1.0, v.dpm, s));    // c2 = E^-1 y2 - c1
+        AWG_TRY(dense(n0, (double*)h->Einv.p, v.y2, v.c2, 1.0, v.c1, -1.0, v.dpm, s));  // c2 = E^-1 y2 - c1
         if (wait) AWG_CUDA(cudaStreamWaitEvent(s, wait, 0));
         return zc(v.c2, Y, (T)-1, (T)0, v.u, (T)1, V2, s);                         // Y = u - Z c2 (+ V2)
+    }
+    awg_status h2(int prec, const T* X, T* Y, cudaStream_t s) {
+        AWG_TRY(h2a(X, s));
+        return h2b(prec, X, Y, s);
     }
 
     // w0 (float64, n_- x K) = W^T X
@@ -1288,6 +1364,7 @@ struct BlockApply {
                         kb_split16<__nv_bfloat16, K><<<(n + 31) / 32, 256, 0, s>>>(n, ldb(), X, rsc, v.mx,
                                                                                   (__nv_bfloat16*)v.bt);
                     AWG_LAUNCH();
+                    extra_launches(h, 1);
                 }
                 UmmaW u;
                 u.W = P.W.p; u.n = n; u.ldw = ldw; u.nm = nm; u.bf16 = (prec == AWG_MIXED_BF16);
@@ -1365,6 +1442,7 @@ struct BlockApply {
                     else
                         kb_split16_d<__nv_bfloat16, K><<<gs, 256, 0, s>>>(ldw, (float*)v.ds, v.mx2,
                                                                          (__nv_bfloat16*)v.dt, v.dscale);
+                    extra_launches(h, 2);
                     AWG_LAUNCH();
                 }
                 UmmaW u;
@@ -1427,12 +1505,18 @@ struct BlockApply {
                 if (h->n_minus == 0) return h2(prec, X, Y, s);
                 AWG_CUDA(cudaEventRecord(h->ev_fork, s));
                 AWG_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+                // side stream: W^T X (HBM) beside the first E^-1 (FP64 pipes),
+                // then F^-1 (FP64) after it, beside the local solves (FP32),
+                // and W d beside the second E^-1
                 AWG_TRY(wt(prec, X, v.w0, h->side));
+                AWG_TRY(h2a(X, s));
+                AWG_CUDA(cudaEventRecord(h->ev_mid, s));
+                AWG_CUDA(cudaStreamWaitEvent(h->side, h->ev_mid, 0));
                 AWG_TRY(dense(h->n_minus, (double*)h->prec[prec].Finv.p, v.w0, v.dd, 1.0, nullptr, 0.0, v.dps,
                                h->side));
                 AWG_TRY(wd(prec, v.dd, v.tmpw, nullptr, h->side));
                 AWG_CUDA(cudaEventRecord(h->ev_join, h->side));
-                return h2(prec, X, Y, s, v.tmpw, h->ev_join);
+                return h2b(prec, X, Y, s, v.tmpw, h->ev_join);
             }
             default: return AWG_ERR_INVALID_ARG;
         }

@@ -40,6 +40,25 @@ awg_status umma_wt(const UmmaW& u, int K, const void* Bt, int ldb, float* part, 
 // out(i, j) = sum_c W(i, c) * Dt(j, c) (hi + lo), fp32 n x K row-major;
 // Dt: 2K x ldw 16-bit (row stride ldw)
 awg_status umma_wd(const UmmaW& u, int K, const void* Dt, float* out, int* d_err, cudaStream_t s);
+// Tensor-core local solves with the float32 local pseudo-inverses (TF32,
+// three products of high and low parts): tables built once per handle.
+struct UmmaLocal {
+    int N = 0, ntiles = 0, max_kc = 0, max_tiles_sub = 0;
+    const int* sub_ptr = nullptr;     // int32[N+1]
+    const int* sub_idx = nullptr;     // int32[sum_ns]
+    const float* Gt = nullptr;        // 16 KB G images, sum over s of RT_s * KC_s
+    const int64_t* gt_off = nullptr;  // int64[N]: first image of subdomain s
+    const int64_t* kc_prefix = nullptr;  // int64[N+1]: prefix of KC_s = ceil(n^s / 32)
+    const int* tile_sub = nullptr;    // int32[ntiles]: subdomain of CTA tile t
+    const int* tile_rt = nullptr;     // int32[ntiles]: 128-row tile of CTA tile t
+};
+// Gt from the float32 local pseudo-inverses (column-major, ld = n^s rounded up to 4)
+awg_status umma_local_tiles(const UmmaLocal& u, const int64_t* g32off, const float* G, cudaStream_t s);
+// out(P, :) (row-major sum_ns x K) = G_s X_s for every subdomain, X row-major
+// n x K; lt: scratch of kc_prefix[N] * 2 * K * 32 floats
+awg_status umma_local(const UmmaLocal& u, int K, const float* X, float* lt, float* out, int* d_err,
+                      cudaStream_t s);
+
 // Whether the tensor-core passes are available (driver entry point found).
 bool umma_available();
 // Number of row splits umma_wt uses when asked for `want` (no empty split).

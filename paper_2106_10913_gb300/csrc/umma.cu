@@ -357,6 +357,256 @@ __global__ void __launch_bounds__(UM_THREADS) k_umma_wt(const __grid_constant__ 
     if (warp == 2) tmem_dealloc(taddr, C::TMEM_COLS);
 }
 
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::tf32 (float32 operands read as
+// TF32, float32 accumulation)
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Instruction descriptor of kind::tf32: float32 accumulator, A and B TF32,
+// both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Position (float index) of element (r, q), q < 32, of a 128-byte-row tile in
+// the 128-byte swizzled layout: 16-byte chunk q / 4 of row r is stored at
+// chunk (q / 4) ^ (r % 8).
+__device__ __forceinline__ int sw128_f32(int r, int q) { return r * 32 + ((((q >> 2) ^ (r & 7))) << 2) + (q & 3); }
+
+// Tiles of the float32 local pseudo-inverses G_s for the tensor cores: tile
+// (rt, kc) of subdomain s holds G_s(rt*128 + r, kc*32 + q), r < 128, q < 32
+// (zero outside n^s x n^s), as a 16 KB image in the 128-byte swizzled
+// K-major layout.  G_s is symmetric, so its rows are read as its columns.
+__global__ void __launch_bounds__(256) k_tile_g(const int* __restrict__ sub_ptr, const int64_t* __restrict__ g32off,
+                                                const float* __restrict__ G, const int64_t* __restrict__ gt_off,
+                                                float* __restrict__ Gt) {
+    const int s = blockIdx.y;
+    const int m = sub_ptr[s + 1] - sub_ptr[s];
+    const int ld = (m + 3) & ~3;
+    const int RT = (m + 127) / 128, KC = (m + 31) / 32;
+    const int t = blockIdx.x;
+    if (t >= RT * KC) return;
+    const int rt = t / KC, kc = t % KC;
+    const float* Gs = G + g32off[s];
+    float* img = Gt + (size_t)(gt_off[s] + t) * 4096;
+    for (int e = threadIdx.x; e < 4096; e += 256) {
+        const int r = e / 32, q = e % 32;
+        const int i = rt * 128 + r, j = kc * 32 + q;
+        img[sw128_f32(r, q)] = (i < m && j < m) ? Gs[(size_t)i * ld + j] : 0.f;
+    }
+}
+
+// Right-hand-side images of the tensor-core local solves: for subdomain s
+// and chunk kc, the TF32 high and low parts (round to nearest: hi =
+// tf32(x), lo = tf32(x - hi)) of X(idx_s(kc*32 + jj), c) as two K x 32
+// images (row c) in the 128-byte swizzled layout, at
+// lt + (kc_prefix[s] + kc) * 2 * K * 32 floats.
+template <int K>
+__global__ void __launch_bounds__(256) k_local_bimg(const int* __restrict__ sub_ptr, const int* __restrict__ sub_idx,
+                                                    const int64_t* __restrict__ kc_prefix,
+                                                    const float* __restrict__ X, float* __restrict__ lt) {
+    __shared__ float xs[32][K + 1];
+    const int s = blockIdx.y, kc = blockIdx.x;
+    const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
+    if (kc * 32 >= m) return;
+    for (int e = threadIdx.x; e < 32 * K; e += 256) {
+        const int jj = e / K, c = e % K, p = kc * 32 + jj;
+        xs[jj][c] = (p < m) ? X[(size_t)sub_idx[p0 + p] * K + c] : 0.f;
+    }
+    __syncthreads();
+    float* hi = lt + (size_t)(kc_prefix[s] + kc) * 2 * K * 32;
+    float* lo = hi + K * 32;
+    for (int e = threadIdx.x; e < 32 * K; e += 256) {
+        const int c = e / 32, q = e % 32;
+        const float x = xs[q][c];
+        const float h = tf32_rna(x);
+        hi[sw128_f32(c, q)] = h;
+        lo[sw128_f32(c, q)] = tf32_rna(x - h);
+    }
+}
+
+// U_s(rt*128 + r, :) = sum over kc of G_s tile (rt, kc) times X_s chunk kc,
+// with G = G_hi + G_lo and X = X_hi + X_lo split in TF32 and the three
+// products hi*hi + hi*lo + lo*hi accumulated in float32 in tensor memory
+// (error about 2^-22 of each product, the float32 level).  One CTA per
+// 128-row tile (flattened list tile_sub / tile_rt); 6 warps: warp 0 issues
+// the bulk copies (one 16 KB G image and the two right-hand-side images per
+// stage), warp 1 the MMAs, warps 2-5 split the G images in shared memory
+// (hi in place, lo beside it) and read the accumulator back.
+constexpr int UL_STAGES = 4;
+constexpr int UL_THREADS = 192;
+template <int K>
+struct UlCfg {
+    static constexpr int A_BYTES = 128 * 32 * 4;          // 16 KB G image
+    static constexpr int B_BYTES = 2 * K * 32 * 4;        // hi + lo right-hand-side images
+    static constexpr int STAGE = 2 * A_BYTES + B_BYTES;   // G hi, G lo, B
+    static constexpr int SMEM = UL_STAGES * STAGE + 1024;
+    static constexpr int TMEM_COLS = K < 32 ? 32 : K;
+};
+
+struct UlShared {
+    uint64_t full[UL_STAGES];
+    uint64_t ready[UL_STAGES];
+    uint64_t empty[UL_STAGES];
+    uint64_t done;
+    uint32_t tmem;
+    int fail;
+};
+
+template <int K>
+__global__ void __launch_bounds__(UL_THREADS) k_umma_local(const int* __restrict__ sub_ptr,
+                                                           const int* __restrict__ tile_sub,
+                                                           const int* __restrict__ tile_rt,
+                                                           const int64_t* __restrict__ gt_off,
+                                                           const int64_t* __restrict__ kc_prefix,
+                                                           const float* __restrict__ Gt, const float* __restrict__ lt,
+                                                           float* __restrict__ out, int* d_err) {
+    extern __shared__ uint8_t ul_raw[];
+    __shared__ UlShared sh;
+    using C = UlCfg<K>;
+    const uint32_t base = smem_u32(ul_raw);
+    uint8_t* ring = ul_raw + ((1024u - (base & 1023u)) & 1023u);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = tile_sub[blockIdx.x], rt = tile_rt[blockIdx.x];
+    const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
+    const int KC = (m + 31) / 32;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < UL_STAGES; i++) {
+            mbar_init(&sh.full[i], 1);
+            mbar_init(&sh.ready[i], 128);
+            mbar_init(&sh.empty[i], 1);
+        }
+        mbar_init(&sh.done, 1);
+        sh.fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 2) {
+        tmem_alloc(&sh.tmem, C::TMEM_COLS);
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = sh.tmem;
+    const float* gsrc = Gt + (size_t)(gt_off[s] + (int64_t)rt * KC) * 4096;
+    const float* bsrc = lt + (size_t)kc_prefix[s] * 2 * K * 32;
+    if (warp == 0) {
+        if (lane == 0) {
+            int kc = 0;
+            for (; kc < KC; kc++) {
+                const int st = kc % UL_STAGES;
+                if (kc >= UL_STAGES &&
+                    !mbar_wait(&sh.empty[st], ((kc / UL_STAGES) - 1) & 1, d_err, ERR_WAIT_EMPTY)) {
+                    sh.fail = 1;
+                    break;
+                }
+                if (*(volatile int*)&sh.fail) break;
+                uint8_t* sp = ring + st * C::STAGE;
+                mbar_expect_tx(&sh.full[st], C::A_BYTES + C::B_BYTES);
+                bulk_load(sp, gsrc + (size_t)kc * 4096, C::A_BYTES, &sh.full[st]);
+                bulk_load(sp + 2 * C::A_BYTES, bsrc + (size_t)kc * 2 * K * 32, C::B_BYTES, &sh.full[st]);
+            }
+            for (int j = (kc > UL_STAGES ? kc - UL_STAGES : 0); j < kc; j++)
+                mbar_wait(&sh.full[j % UL_STAGES], (j / UL_STAGES) & 1, d_err, ERR_WAIT_FULL);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_tf32(128, K);
+            for (int kc = 0; kc < KC; kc++) {
+                const int st = kc % UL_STAGES;
+                if (!mbar_wait(&sh.ready[st], (kc / UL_STAGES) & 1, d_err, ERR_WAIT_FULL) ||
+                    *(volatile int*)&sh.fail) {
+                    sh.fail = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a = smem_u32(ring + st * C::STAGE);
+                const uint32_t al = a + C::A_BYTES, b = a + 2 * C::A_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < 4; kk++) {  // 8 TF32 values (32 bytes) per MMA
+                    const uint64_t ah = sdesc(a + kk * 32, 16, 1024), alo = sdesc(al + kk * 32, 16, 1024);
+                    const uint64_t bh = sdesc(b + kk * 32, 16, 1024), blo = sdesc(b + K * 128 + kk * 32, 16, 1024);
+                    umma_tf32(taddr, ah, bh, idesc, (kc == 0 && kk == 0) ? 0u : 1u);
+                    umma_tf32(taddr, ah, blo, idesc, 1u);
+                    umma_tf32(taddr, alo, bh, idesc, 1u);
+                }
+                umma_commit(&sh.empty[st]);
+            }
+            umma_commit(&sh.done);
+        }
+    } else {
+        // split the G image of every stage: hi = tf32(g) in place, lo = tf32(g - hi)
+        const int t = threadIdx.x - 64;
+        for (int kc = 0; kc < KC; kc++) {
+            const int st = kc % UL_STAGES;
+            if (!mbar_wait(&sh.full[st], (kc / UL_STAGES) & 1, d_err, ERR_WAIT_FULL)) {
+                sh.fail = 1;
+                break;
+            }
+            float4* a4 = reinterpret_cast<float4*>(ring + st * C::STAGE);
+            float4* l4 = reinterpret_cast<float4*>(ring + st * C::STAGE + C::A_BYTES);
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const float4 g = a4[t + 128 * u];
+                float4 h, l;
+                h.x = tf32_rna(g.x); l.x = tf32_rna(g.x - h.x);
+                h.y = tf32_rna(g.y); l.y = tf32_rna(g.y - h.y);
+                h.z = tf32_rna(g.z); l.z = tf32_rna(g.z - h.z);
+                h.w = tf32_rna(g.w); l.w = tf32_rna(g.w - h.w);
+                a4[t + 128 * u] = h;
+                l4[t + 128 * u] = l;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+            mbar_arrive(&sh.ready[st]);
+        }
+    }
+    __syncwarp();
+    bool ok = mbar_wait(&sh.done, 0, d_err, ERR_WAIT_DONE);
+    ok = __syncthreads_and(ok && !*(volatile int*)&sh.fail);
+    tc_fence_after();
+    if (warp >= 2 && ok) {
+        const int q = warp & 3;  // tensor-memory lanes 32 q .. 32 q + 31
+        const int row = rt * 128 + q * 32 + lane;
+#pragma unroll
+        for (int c0 = 0; c0 < K; c0 += 16) {
+            float v[16];
+            tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+            if (row < m) {
+                float4* o = reinterpret_cast<float4*>(out + (size_t)(p0 + row) * K + c0);
+#pragma unroll
+                for (int u = 0; u < 4; u++) o[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 2) tmem_dealloc(taddr, C::TMEM_COLS);
+}
+
 // ----------------------------------------------------------------- host
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -440,7 +690,37 @@ awg_status launch_wt(const UmmaW& u, const void* Bt, int ldb, float* part, int s
     return AWG_OK;
 }
 
+template <int K>
+awg_status launch_local(const UmmaLocal& u, const float* X, float* lt, float* out, int* d_err, cudaStream_t s) {
+    k_local_bimg<K><<<dim3(u.max_kc, u.N), 256, 0, s>>>(u.sub_ptr, u.sub_idx, u.kc_prefix, X, lt);
+    AWG_LAUNCH();
+    auto kern = k_umma_local<K>;
+    static bool attr = false;
+    if (!attr) {
+        AWG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, UlCfg<K>::SMEM));
+        attr = true;
+    }
+    kern<<<u.ntiles, UL_THREADS, UlCfg<K>::SMEM, s>>>(u.sub_ptr, u.tile_sub, u.tile_rt, u.gt_off, u.kc_prefix, u.Gt,
+                                                       lt, out, d_err);
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
 }  // namespace
+
+awg_status umma_local_tiles(const UmmaLocal& u, const int64_t* g32off, const float* G, cudaStream_t s) {
+    k_tile_g<<<dim3(u.max_tiles_sub, u.N), 256, 0, s>>>(u.sub_ptr, g32off, G, u.gt_off, const_cast<float*>(u.Gt));
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
+awg_status umma_local(const UmmaLocal& u, int K, const float* X, float* lt, float* out, int* d_err,
+                      cudaStream_t s) {
+    if (K == 16) return launch_local<16>(u, X, lt, out, d_err, s);
+    if (K == 32) return launch_local<32>(u, X, lt, out, d_err, s);
+    if (K == 64) return launch_local<64>(u, X, lt, out, d_err, s);
+    return AWG_ERR_INVALID_ARG;
+}
 
 bool umma_available() { return encoder() != nullptr; }
 
