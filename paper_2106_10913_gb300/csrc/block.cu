@@ -88,10 +88,12 @@ __device__ __forceinline__ void colsum_grid(const double (&acc)[2], double* part
     if (threadIdx.x == 0) *cnt = 0u;
 }
 
+// (unrolled by 4: the loads of four rows are in flight together)
 #define ROW_LOOP(T_, K_)                                                                 \
     using M = RM<T_, K_>;                                                                \
     const int lane_ = threadIdx.x & 31, w_ = threadIdx.x >> 5;                           \
     const int rw_ = lane_ / M::TPR, c0 = (lane_ % M::TPR) * M::V;                        \
+    _Pragma("unroll 4")                                                                  \
     for (int i = blockIdx.x * M::RPB + w_ * M::RPW + rw_; i < n; i += gridDim.x * M::RPB)
 
 // ------------------------------------------------------------- PCG (float64)
@@ -919,6 +921,7 @@ __global__ void __launch_bounds__(256) kb_wt_reduce_umma(int nb, int ldw, int nm
     float a[4] = {0.f, 0.f, 0.f, 0.f};
     if (ccp) {
         const int k1 = ccp[c + 1];
+#pragma unroll 4
         for (int k = ccp[c] + slot; k < k1; k += EPB) {
             const int i = crow[k];
             const float cv = cval[k] * (rscale ? rscale[i] : 1.f);
