@@ -240,6 +240,7 @@ def run_awg(args):
     import torch
     import torch.distributed as dist
     from paper_2106_10913_gb300 import (AWGSolver, FP64, MIXED_BF16, MIXED_FP16, MIXED_FP32, awg_pcg, awg_pcg_block,
+                                        awg_pcg_block_async,
                                         awg_profile, awg_profile_read)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -265,7 +266,8 @@ def run_awg(args):
     # storage forms to build: float64 always, plus those of the timed forms
     pmask = 1
     for nm_ in args.forms.split(","):
-        pmask |= 1 << {"fp64": 0, "mixed_fp32": 1, "mixed_bf16": 2, "mixed_fp16": 3}[nm_.replace("_block", "")]
+        pmask |= 1 << {"fp64": 0, "mixed_fp32": 1, "mixed_bf16": 2,
+                       "mixed_fp16": 3}[nm_.replace("_block", "").replace("_graph", "")]
     sol = AWGSolver(p.rowptr, p.colidx, p.val, p.part, p.nparts, p.overlap, p.tau,
                     precisions=pmask, verbose=int(args.verbose), **geneo_opts)
     setup_s = time.perf_counter() - t0
@@ -285,11 +287,26 @@ def run_awg(args):
     B = np.concatenate([p.b[None, :], np.random.default_rng(1).standard_normal((K - 1, p.n))])
     bB = torch.from_numpy(B).cuda()
     xB = torch.zeros_like(bB)
+    g_its = torch.zeros(K, dtype=torch.int32, device="cuda")
+    g_rel = torch.zeros(K, dtype=torch.float64, device="cuda")
+    g_st = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    def graph_solve(prec):
+        # enqueued without a host synchronisation; results read after the step
+        awg_pcg_block_async(sol.h, bB, xB, g_its, g_rel, g_st, RTOL, precision=prec)
+        return None
+
     for name in args.forms.split(","):
-        block = name.endswith("_block")
-        prec = all_forms[name[:-6] if block else name]
-        solve = ((lambda: awg_pcg_block(sol.h, bB, xB, RTOL, prec, check=False)) if block else
-                 (lambda: awg_pcg(sol.h, b, x, RTOL, prec, check=False)))
+        graph = name.endswith("_graph")
+        block = name.endswith("_block") or graph
+        base = name.rsplit("_", 1)[0] if block else name
+        prec = all_forms[base]
+        if graph:
+            solve = lambda: graph_solve(prec)
+        elif block:
+            solve = lambda: awg_pcg_block(sol.h, bB, xB, RTOL, prec, check=False)
+        else:
+            solve = lambda: awg_pcg(sol.h, b, x, RTOL, prec, check=False)
         per_step = K if block else 1
         for _ in range(args.warmup):
             solve()
@@ -302,10 +319,12 @@ def run_awg(args):
             torch.cuda.nvtx.range_push(f"timed_{name}")
             ev0.record(stream)
             for _ in range(args.steps):
-                st, it, rel = solve()
-                its.append(max(it))
-                rels.append(max(rel))
-                sts.append(st)
+                r = solve()
+                if r is not None:
+                    st, it, rel = r
+                    its.append(max(it))
+                    rels.append(max(rel))
+                    sts.append(st)
             ev1.record(stream)
             torch.cuda.nvtx.range_pop()
             barrier()
@@ -316,8 +335,12 @@ def run_awg(args):
         if world > 1:
             dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
         ms = float(tmax.item())
+        if not its:  # graph-driven solves: device results of the last step
+            its = [int(g_its.max().item())]
+            rels = [float(g_rel.max().item())]
+            sts = [int(g_st.item())]
         ok = all(s == 0 for s in sts) and max(rels) <= RTOL
-        forms[name] = {"prec": prec, "block": block, "nrhs": per_step, "ms": ms,
+        forms[name] = {"prec": prec, "block": block, "graph": graph, "nrhs": per_step, "ms": ms,
                        "value": world * args.steps * per_step / (ms / 1000.0),
                        "ms_per_step": ms / args.steps, "iters": its[0], "relres": max(rels),
                        "ok": ok, "prof": prof, "clocks": clk.summary()}
@@ -325,7 +348,12 @@ def run_awg(args):
     best = max((f for f in forms.values() if f["ok"]), key=lambda f: f["value"],
                default=next(iter(forms.values())))
     best_name = [k for k, v in forms.items() if v is best][0]
-    roofline = roofline_of(best, info)
+    # kernels inside a graph loop are not event-timed: the roofline of a
+    # graph-driven form comes from the host-driven run of the same kernels
+    rform = forms.get(best_name.replace("_graph", "_block"), best) if best["graph"] else best
+    roofline = roofline_of(rform, info)
+    if rform is not best:
+        roofline["timed_in"] = best_name.replace("_graph", "_block")
 
     # end to end: host buffers through the public API (H2D b, solve, D2H x)
     hb = torch.from_numpy(B if best["block"] else p.b).pin_memory()
@@ -337,7 +365,9 @@ def run_awg(args):
     e0.record(stream)
     for _ in range(args.steps):
         db.copy_(hb, non_blocking=True)
-        if best["block"]:
+        if best["graph"]:
+            awg_pcg_block_async(sol.h, db, dx, g_its, g_rel, g_st, RTOL, precision=best["prec"])
+        elif best["block"]:
             awg_pcg_block(sol.h, db, dx, RTOL, best["prec"], check=False)
         else:
             awg_pcg(sol.h, db, dx, RTOL, best["prec"], check=False)
@@ -352,6 +382,8 @@ def run_awg(args):
     e2e = {"value": world * args.steps * best["nrhs"] / (float(et.item()) / 1000.0), "unit": UNIT,
            "h2d_bytes_per_step": int(hb.numel() * 8), "d2h_bytes_per_step": int(hx.numel() * 8),
            "form": best_name}
+
+    batch = batched_problems(args, barrier) if args.batch_problems > 0 else None
 
     if rank == 0:
         cb = oracle_sample(1) if (world == 1 and not args.no_cpu_baseline) else None
@@ -381,6 +413,7 @@ def run_awg(args):
                           "kernel_ms": {c: round(t, 3) for c, t in v["prof"]["ms"].items()},
                           "launches": v["prof"]["launches"]} for k, v in forms.items()},
             "speedup_vs_plain_fp64": (best["value"] / forms["fp64"]["value"]) if "fp64" in forms else None,
+            "batched_problems": batch,
             "roofline": roofline,
             "cpu_baseline": ({k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
                              if cb else None),
@@ -393,6 +426,77 @@ def run_awg(args):
     sol.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def batched_problems(args, barrier):
+    """Independent problems solved together (the batched-problem workload at
+    reduced size): P channel problems of the batch generator (side L drawn
+    from [Lmin, Lmax], q x q boxes, contrast 10^U(4,6), one right-hand side
+    each), every one with its own handle.  Plain: one float64 single-RHS
+    solve after the other.  Batched: the mixed float16 graph-driven solves of
+    all problems enqueued from one host thread (each handle on its own
+    streams, no host synchronisation until the last), then one wait."""
+    import torch
+    import awg_inputs as gi
+    from paper_2106_10913_gb300 import AWGSolver, FP64, MIXED_FP16, awg_pcg, awg_pcg_block_async
+    lo, hi = (int(v) for v in args.batch_sides.split(","))
+    probs = gi.batch_channels(args.batch_problems, Lmin=lo, Lmax=hi)
+    t0 = time.perf_counter()
+    sols = [AWGSolver(q.rowptr, q.colidx, q.val, q.part, q.nparts, q.overlap, q.tau, precisions=0b1001)
+            for q in probs]
+    setup_s = time.perf_counter() - t0
+    bs = [torch.from_numpy(q.b).cuda() for q in probs]
+    xs = [torch.zeros_like(v) for v in bs]
+    B2 = [v[None, :].contiguous() for v in bs]
+    X2 = [torch.zeros_like(v) for v in B2]
+    its = [torch.zeros(1, dtype=torch.int32, device="cuda") for _ in probs]
+    rel = [torch.zeros(1, dtype=torch.float64, device="cuda") for _ in probs]
+    sts = [torch.zeros(1, dtype=torch.int32, device="cuda") for _ in probs]
+    stream = torch.cuda.current_stream()
+
+    def plain():
+        out = []
+        for s_, v, x_ in zip(sols, bs, xs):
+            out.append(awg_pcg(s_.h, v, x_, RTOL, FP64, check=False))
+        return out
+
+    streams = [torch.cuda.Stream() for _ in probs]
+
+    def batched():
+        # one stream per problem: the solves overlap on the device
+        for j, s_ in enumerate(sols):
+            streams[j].wait_stream(stream)
+            awg_pcg_block_async(s_.h, B2[j], X2[j], its[j], rel[j], sts[j], RTOL, precision=MIXED_FP16,
+                                stream=streams[j])
+        for sj in streams:
+            stream.wait_stream(sj)
+
+    res = {}
+    for name, fn in (("plain_fp64", plain), ("batched_mixed_fp16_graph", batched)):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            r = fn()
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if name == "plain_fp64":
+            ok = all(st == 0 and rr[0] <= RTOL for st, _, rr in r)
+            iters = [it[0] for _, it, _ in r]
+        else:
+            ok = all(int(t.item()) == 0 for t in sts) and max(float(t.item()) for t in rel) <= RTOL
+            iters = [int(t.item()) for t in its]
+        res[name] = {"value": args.steps * len(probs) / (ms / 1000.0), "unit": UNIT,
+                     "ms_per_batch": ms / args.steps, "ok": ok, "iters": iters}
+    for s_ in sols:
+        s_.close()
+    res["problems"] = [q.name for q in probs]
+    res["setup_s"] = round(setup_s, 2)
+    res["speedup"] = res["batched_mixed_fp16_graph"]["value"] / res["plain_fp64"]["value"]
+    return res
 
 
 def train_start_network(seeds=(3, 4, 5), steps=400, lr=1e-2):
@@ -441,9 +545,14 @@ def main():
     ap.add_argument("--verbose", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nrhs", type=int, default=32, help="right-hand sides per step of the batched forms")
-    ap.add_argument("--forms", default="fp64,mixed_fp32,mixed_bf16,mixed_fp16,mixed_fp32_block,mixed_fp16_block",
+    ap.add_argument("--batch-problems", type=int, default=8,
+                    help="independent problems of the batched-problem measurement (0: skip)")
+    ap.add_argument("--batch-sides", default="128,256", help="range of their grid sides")
+    ap.add_argument("--forms", default="fp64,mixed_fp32,mixed_bf16,mixed_fp16,mixed_fp32_block,mixed_fp16_block,"
+                                      "mixed_fp16_graph",
                     help="comma-separated storage forms to time; a _block suffix times the "
-                         "batched (multi-right-hand-side) solve of --nrhs columns")
+                         "batched (multi-right-hand-side) solve of --nrhs columns, _graph the same "
+                         "solve as one CUDA graph launch with a device-side loop")
     ap.add_argument("--geneo", default="learned", choices=["learned", "block", "dense"],
                     help="GenEO eigensolver of the setup: block solver from the learned start "
                          "(network trained on the device on smaller instances), from a random "

@@ -308,6 +308,29 @@ awg_status awg_apply_block(awg_handle h, int which, int precision, const double*
 awg_status awg_pcg_block(awg_handle h, int precision, const double* d_b, double* d_x, int nrhs, int ld,
                          double rtol, int* h_iters, double* h_relres, void* stream);
 
+/*
+ * Asynchronous block PCG (H_3,ad, 1 <= nrhs <= 64 columns, x_0 = 0): the
+ * iterations run as one CUDA graph launch, a conditional while node whose
+ * body is one iteration captured from the handle's two streams, with the
+ * stopping test (per column, recurrence residual <= rtol ||b||, Section 1)
+ * evaluated on the device.  No host synchronisation: the call returns once
+ * the work is enqueued on `stream`, so one host thread can keep several
+ * handles (independent problems) solving at the same time.  The loop graph
+ * of each (precision, nrhs width 16/32/64) is captured on first use (make
+ * that first call outside any stream capture).  DEVICE outputs, written
+ * when the work completes: d_iters int32[nrhs] (iterations per column),
+ * d_relres float64[nrhs] (recurrence relative residual at exit), d_status
+ * int32[1] (AWG_OK, AWG_ERR_BREAKDOWN or AWG_ERR_MAXIT); any may be NULL.
+ * With nrhs = 1 the loop body is the single-right-hand-side apply (the
+ * GEMV-shaped passes of awg_pcg), otherwise the block apply of
+ * awg_pcg_block.  The true residual is not re-checked (awg_pcg_block does
+ * that).
+ * Errors returned: AWG_ERR_INVALID_ARG, AWG_ERR_STATE, AWG_ERR_OOM,
+ * AWG_ERR_CUDA.
+ */
+awg_status awg_pcg_block_async(awg_handle h, int precision, const double* d_b, double* d_x, int nrhs, int ld,
+                               double rtol, int* d_iters, double* d_relres, int* d_status, void* stream);
+
 /* Capacity, in float64 values, of the static scratch of awg_apply_hnn_noalloc. */
 #define AWG_NOALLOC_MAX_LOCAL (1 << 20)
 

@@ -61,7 +61,7 @@ EXPORTED = ["awg_default_options", "awg_status_string", "awg_setup", "awg_destro
             "awg_get_info", "awg_apply", "awg_apply_stage", "awg_pcg", "awg_get_array",
             "awg_profile", "awg_profile_read", "awg_apply_hnn_noalloc", "awg_learned_data",
             "awg_learned_forward", "awg_learned_grad", "awg_learned_train", "awg_profile_trace",
-            "awg_apply_block", "awg_pcg_block"]
+            "awg_apply_block", "awg_pcg_block", "awg_pcg_block_async"]
 LEARNED_NPARAM, LEARNED_NFEAT = 385, 5
 GENEO_DENSE, GENEO_BLOCK, GENEO_LEARNED = 0, 1, 2
 PROF_NAMES = ["spmv", "local", "wt", "wd", "coarse", "subdomain", "prolong", "vector"]
@@ -109,6 +109,8 @@ def load_library(path: str = LIB_PATH):
     lib.awg_apply_block.restype = I
     lib.awg_pcg_block.argtypes = [P, I, P, P, I, I, D, ctypes.POINTER(I), ctypes.POINTER(D), P]
     lib.awg_pcg_block.restype = I
+    lib.awg_pcg_block_async.argtypes = [P, I, P, P, I, I, D, P, P, P, P]
+    lib.awg_pcg_block_async.restype = I
     lib.awg_apply_hnn_noalloc.argtypes = [P, I, P, P, P]
     lib.awg_apply_hnn_noalloc.restype = I
     lib.awg_learned_data.argtypes = [P, P, P, P]
@@ -227,6 +229,17 @@ def awg_pcg_block(h, b, x, rtol: float = 1e-8, precision: int = FP64, stream=Non
     if check:
         _check(st, "awg_pcg_block")
     return st, list(its), list(rel)
+
+
+def awg_pcg_block_async(h, b, x, iters, relres, status, rtol: float = 1e-8, precision: int = FP64,
+                        stream=None):
+    """Enqueue a graph-driven block PCG for the rows of b (nrhs <= 64):
+    iters (int32[nrhs]), relres (float64[nrhs]) and status (int32[1]) are
+    CUDA tensors filled when the work completes."""
+    ptr = lambda t: None if t is None else t.data_ptr()
+    _check(load_library().awg_pcg_block_async(h, precision, b.data_ptr(), x.data_ptr(), b.shape[0], b.shape[-1],
+                                              float(rtol), ptr(iters), ptr(relres), ptr(status),
+                                              _stream_ptr(stream)), "awg_pcg_block_async")
 
 
 def awg_get_array(h, what: str, size: int) -> np.ndarray:

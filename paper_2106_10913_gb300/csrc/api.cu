@@ -59,7 +59,7 @@ static void free_all(Handle* h) {
                       &h->Vm, &h->lam_m, &h->sigma, &h->modes, &h->mode_ptr, &h->z_off, &h->Z,
                       &h->E, &h->Einv, &h->wcol_ptr, &h->Wcm, &h->F64, &h->ws, &h->flag, &h->red,
                       &h->bws, &h->bval32, &h->bvm32, &h->blam32, &h->blam64, &h->bz32,
-                      &h->ul_gt, &h->ul_gtoff, &h->ul_kcpre, &h->ul_tsub, &h->ul_trt};
+                      &h->ul_gt, &h->ul_gtoff, &h->ul_kcpre, &h->ul_tsub, &h->ul_trt, &h->g1buf, &h->g1cnt};
     for (DevBuf* b : bufs) dfree(h, *b);
     for (auto& P : h->prec) {
         dfree(h, P.G);
@@ -70,6 +70,18 @@ static void free_all(Handle* h) {
         dfree(h, P.cscale);
         for (DevBuf* b : {&P.corr_rowptr, &P.corr_col, &P.corr_val, &P.corr_colptr, &P.corr_row, &P.corr_cval})
             dfree(h, *b);
+    }
+    for (int g = 0; g < 4; g++) {
+        if (h->g1_exec[g]) cudaGraphExecDestroy(h->g1_exec[g]);
+        if (h->g1_graph[g]) cudaGraphDestroy(h->g1_graph[g]);
+        h->g1_exec[g] = nullptr;
+        h->g1_graph[g] = nullptr;
+    }
+    for (int g = 0; g < 12; g++) {
+        if (h->bg_exec[g]) cudaGraphExecDestroy(h->bg_exec[g]);
+        if (h->bg_graph[g]) cudaGraphDestroy(h->bg_graph[g]);
+        h->bg_exec[g] = nullptr;
+        h->bg_graph[g] = nullptr;
     }
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     h->ev_pool.clear();
@@ -344,6 +356,26 @@ awg_status awg_pcg_block(awg_handle hh, int precision, const double* d_b, double
     return st;
 }
 
+awg_status awg_pcg_block_async(awg_handle hh, int precision, const double* d_b, double* d_x, int nrhs, int ld,
+                               double rtol, int* d_iters, double* d_relres, int* d_status, void* stream) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !d_b || !d_x || nrhs < 1 || nrhs > 64 || ld < h->n || !(rtol > 0.0) || precision < 0 ||
+        precision >= AWG_NPREC)
+        return AWG_ERR_INVALID_ARG;
+    if (!h->prec[precision].built || (precision != AWG_FP64 && !h->prec[AWG_MIXED_FP32].G.p)) return AWG_ERR_STATE;
+    if (h->opt.variant != AWG_H3_AD) return AWG_ERR_STATE;
+    cudaStream_t us = (cudaStream_t)stream;
+    AWG_CUDA(cudaEventRecord(h->ev_in, us));
+    AWG_CUDA(cudaStreamWaitEvent(h->hp, h->ev_in, 0));
+    // one right-hand side: the single-RHS apply (GEMV passes) in the loop graph
+    const awg_status st =
+        nrhs == 1 ? pcg1_async(h, precision, variant_stage(h), d_b, d_x, rtol, d_iters, d_relres, d_status, h->hp)
+                  : block_pcg_async(h, precision, d_b, d_x, nrhs, ld, rtol, d_iters, d_relres, d_status, h->hp);
+    AWG_CUDA(cudaEventRecord(h->ev_out, h->hp));
+    AWG_CUDA(cudaStreamWaitEvent(us, h->ev_out, 0));
+    return st;
+}
+
 awg_status awg_get_array(awg_handle hh, int what, void* h_out, size_t count) {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h || !h_out) return AWG_ERR_INVALID_ARG;
@@ -406,6 +438,9 @@ awg_status awg_profile(awg_handle hh, int enable) {
         h->ev_used = 0;
         h->ev_kernel.clear();
         h->launches = 0;
+        AWG_CUDA(cudaStreamSynchronize(h->hp));
+        block_graph_launches(h);  // drop the graph-loop kernels counted so far
+        pcg1_graph_launches(h);
         for (int i = 0; i < AWG_NPROF; i++) { h->prof_ms[i] = 0.0; h->prof_cnt[i] = 0; }
     }
     h->prof = enable;
@@ -443,6 +478,8 @@ awg_status awg_profile_read(awg_handle hh, int64_t* h_launches, double* h_ms, in
     }
     h->ev_kernel.clear();
     h->ev_used = 0;
+    AWG_CUDA(cudaStreamSynchronize(h->hp));
+    h->launches += block_graph_launches(h) + pcg1_graph_launches(h);  // kernels run inside graph loops
     if (h_launches) *h_launches = h->launches;
     for (int i = 0; i < AWG_NPROF; i++) {
         if (h_ms) h_ms[i] = h->prof_ms[i];

@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 namespace awg {
 
@@ -1238,6 +1239,195 @@ awg_status pcg1(Handle* h, int prec, int variant_stage, const double* b, double*
     if (iters) *iters = it;
     if (relres) *relres = true_rel;
     return st;
+}
+
+// ------------------------------------------------- graph-driven PCG, one RHS
+// Control words next to the PCG scalars: [8] iterations done, [9] rtol,
+// [10] maxit, [11] status, [12] active (1/0), [13] relative residual and
+// [14] iterations at exit.
+enum { C_IT = 8, C_RTOL = 9, C_MAXIT = 10, C_ST = 11, C_ACT = 12, C_REL = 13, C_ITS = 14 };
+
+__global__ void k_pcg1_init(double* scal, double rtol, double maxit) {
+    if (threadIdx.x == 0) {
+        scal[C_IT] = 0.0;
+        scal[C_RTOL] = rtol;
+        scal[C_MAXIT] = maxit;
+        scal[C_ST] = 0.0;
+        scal[C_ACT] = scal[S_BB] > 0.0 ? 1.0 : 0.0;
+        scal[C_REL] = 0.0;
+        scal[C_ITS] = 0.0;
+    }
+}
+
+// after an x, r update: stop on breakdown, convergence (recurrence residual
+// <= rtol ||b||) or the iteration cap; with `set`, the loop condition
+__global__ void k_pcg1_cond(double* scal, cudaGraphConditionalHandle hc, int set, unsigned long long* launches,
+                            int add) {
+    if (threadIdx.x != 0) return;
+    bool go = false;
+    if (scal[C_ACT] != 0.0) {
+        const int it = (int)scal[C_IT] + 1;
+        scal[C_IT] = it;
+        const double pq = scal[S_PQ];
+        const double rel = sqrt(scal[S_RR] / scal[S_BB]);
+        scal[C_REL] = rel;
+        scal[C_ITS] = it;
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            scal[C_ST] = AWG_ERR_BREAKDOWN;
+        } else if (rel <= scal[C_RTOL]) {
+        } else if (it >= (int)scal[C_MAXIT]) {
+            scal[C_ST] = AWG_ERR_MAXIT;
+        } else {
+            go = true;
+        }
+        if (!go) scal[C_ACT] = 0.0;
+    }
+    if (set) cudaGraphSetConditional(hc, go ? 1u : 0u);
+    if (launches && add) atomicAdd(launches, (unsigned long long)add);
+}
+
+__global__ void k_pcg1_fini(const double* scal, int* d_it, double* d_rel, int* d_st) {
+    if (threadIdx.x != 0) return;
+    if (d_it) *d_it = (int)scal[C_ITS];
+    if (d_rel) *d_rel = scal[C_REL];
+    if (d_st) *d_st = (int)scal[C_ST];
+}
+
+namespace {
+struct G1 {
+    double *b, *x, *r, *p, *q, *z;
+};
+G1 g1_of(Handle* h) {
+    double* base = (double*)h->g1buf.p;
+    const size_t n = (size_t)h->n;
+    return {base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n};
+}
+
+// one iteration: z = H r, rz_new, p = z + beta p, q = A p (p.q), x, r (r.r), stop test
+awg_status pcg1_body(Handle* h, int prec, int stage, const G1& g, double* scal, Ws& w, cudaStream_t s,
+                     cudaGraphConditionalHandle hc, int set, unsigned long long* launches, int add) {
+    const int n = h->n, nb = grid_n(n);
+    AWG_TRY(apply_stage(h, stage, prec, g.r, g.z, s));
+    AWG_TRY(dot1(h, g.r, g.z, scal + S_RZN, w, s));
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        k_pcg_p<<<nb, 256, 0, s>>>(n, scal, g.z, g.p, w.cnt);
+    }
+    AWG_LAUNCH();
+    AWG_TRY(spmv1(h, g.p, g.q, scal + S_PQ, s));
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        k_pcg_xr<<<nb, 256, 0, s>>>(n, scal, g.p, g.q, g.x, g.r, w.part, w.cnt);
+    }
+    AWG_LAUNCH();
+    ProfScope ps_(h, AWG_PROF_VECTOR, s);
+    k_pcg1_cond<<<1, 32, 0, s>>>(scal, hc, set, launches, add);
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+}  // namespace
+
+awg_status pcg1_async(Handle* h, int prec, int stage, const double* b, double* x, double rtol, int* d_it,
+                      double* d_rel, int* d_st, cudaStream_t s) {
+    Ws w = ws_of(h);
+    const int n = h->n, nb = grid_n(n);
+    if (!h->g1buf.p) AWG_TRY(dalloc(h, h->g1buf, (size_t)n * 6 * 8));
+    if (!h->g1cnt.p) {
+        AWG_TRY(dalloc(h, h->g1cnt, 8));
+        AWG_CUDA(cudaMemset(h->g1cnt.p, 0, 8));
+    }
+    const G1 g = g1_of(h);
+    double* scal = w.part + 4000;
+    unsigned long long* gl = (unsigned long long*)h->g1cnt.p;
+    AWG_CUDA(cudaMemcpyAsync(g.b, b, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+    AWG_CUDA(cudaMemsetAsync(g.x, 0, (size_t)n * 8, s));
+    AWG_CUDA(cudaMemcpyAsync(g.r, g.b, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+    AWG_TRY(dot1(h, g.b, g.b, scal + S_BB, w, s));
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        k_pcg1_init<<<1, 32, 0, s>>>(scal, rtol, (double)h->opt.maxit);
+    }
+    AWG_LAUNCH();
+    // first iteration: z = H r, rz, p = z, q = A p, x, r
+    AWG_TRY(apply_stage(h, stage, prec, g.r, g.z, s));
+    AWG_TRY(dot1(h, g.r, g.z, scal + S_RZ, w, s));
+    AWG_CUDA(cudaMemcpyAsync(g.p, g.z, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+    AWG_TRY(spmv1(h, g.p, g.q, scal + S_PQ, s));
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        k_pcg_xr<<<nb, 256, 0, s>>>(n, scal, g.p, g.q, g.x, g.r, w.part, w.cnt);
+    }
+    AWG_LAUNCH();
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        k_pcg1_cond<<<1, 32, 0, s>>>(scal, 0, 0, nullptr, 0);
+    }
+    AWG_LAUNCH();
+    // the loop graph of this precision (captured once, after the first
+    // iteration has been issued)
+    if (!h->g1_exec[prec]) {
+        cudaGraph_t gr = nullptr;
+        AWG_CUDA(cudaGraphCreate(&gr, 0));
+        cudaGraphConditionalHandle hc;
+        AWG_CUDA(cudaGraphConditionalHandleCreate(&hc, gr, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = hc;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        AWG_CUDA(cudaGraphAddNode(&node, gr, nullptr, nullptr, 0, &np));
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        const int prof = h->prof;
+        const int64_t l0 = h->launches;
+        h->prof = 1 << 30;  // count, do not time, while capturing
+        // one body to count its kernels, then the captured one with that count
+        AWG_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        awg_status st = pcg1_body(h, prec, stage, g, scal, w, s, hc, 1, gl, 0);
+        cudaGraph_t cap = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(s, &cap);
+        const int add = (int)(h->launches - l0);
+        h->prof = prof;
+        h->launches = l0;
+        if (st != AWG_OK || ce != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphDestroy(gr);
+            return st != AWG_OK ? st : AWG_ERR_CUDA;
+        }
+        size_t nn = 0;
+        AWG_CUDA(cudaGraphGetNodes(body, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        AWG_CUDA(cudaGraphGetNodes(body, nodes.data(), &nn));
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            AWG_CUDA(cudaGraphNodeGetType(nd, &t));
+            if (t != cudaGraphNodeTypeKernel) continue;
+            cudaKernelNodeParams kp;
+            AWG_CUDA(cudaGraphKernelNodeGetParams(nd, &kp));
+            if (kp.func != (void*)k_pcg1_cond) continue;
+            *(int*)kp.kernelParams[4] = add;
+            AWG_CUDA(cudaGraphKernelNodeSetParams(nd, &kp));
+        }
+        cudaGraphExec_t ex = nullptr;
+        AWG_CUDA(cudaGraphInstantiate(&ex, gr, cudaGraphInstantiateFlagUseNodePriority));
+        h->g1_graph[prec] = gr;
+        h->g1_exec[prec] = ex;
+    }
+    AWG_CUDA(cudaGraphLaunch(h->g1_exec[prec], s));
+    AWG_CUDA(cudaMemcpyAsync(x, g.x, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+    ProfScope ps_(h, AWG_PROF_VECTOR, s);
+    k_pcg1_fini<<<1, 32, 0, s>>>(scal, d_it, d_rel, d_st);
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
+// kernels launched by single-RHS graph loop bodies since the last call (reset)
+int64_t pcg1_graph_launches(Handle* h) {
+    if (!h->g1cnt.p) return 0;
+    unsigned long long c = 0;
+    if (cudaMemcpy(&c, h->g1cnt.p, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+    cudaMemset(h->g1cnt.p, 0, 8);
+    return (int64_t)c;
 }
 
 }  // namespace awg

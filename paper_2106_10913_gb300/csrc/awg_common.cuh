@@ -145,6 +145,14 @@ struct Handle {
     // float32 local pseudo-inverses and their tables (ul_ntiles = 0: not built)
     DevBuf ul_gt, ul_gtoff, ul_kcpre, ul_tsub, ul_trt;
     int ul_ntiles = 0, ul_maxkc = 0, ul_maxtiles = 0;
+    // graph-driven block PCG: loop graph per (precision, K in 16/32/64)
+    cudaGraph_t bg_graph[12] = {};
+    cudaGraphExec_t bg_exec[12] = {};
+    // graph-driven single-RHS PCG: loop graph per precision, its vectors
+    // (b, x, r, p, q, z) and the graph-loop kernel counter
+    cudaGraph_t g1_graph[4] = {};
+    cudaGraphExec_t g1_exec[4] = {};
+    DevBuf g1buf, g1cnt;
     DevBuf flag;                         // int status word
     DevBuf red;                          // partial-sum scratch
     int red_blocks = 0;
@@ -295,6 +303,10 @@ awg_status apply_stage(Handle* h, int which, int prec, const double* x, double* 
 // passes (which share the GPU with the H_2 chain) and keeps the fastest
 awg_status autotune_apply(Handle* h);
 awg_status build_setup_numeric(Handle* h);
+// PCG of one right-hand side as one CUDA graph launch (device-side loop)
+awg_status pcg1_async(Handle* h, int prec, int stage, const double* b, double* x, double rtol, int* d_it,
+                      double* d_rel, int* d_st, cudaStream_t s);
+int64_t pcg1_graph_launches(Handle* h);
 
 // learned.cu : features, network and start block of the GenEO block solver
 constexpr int LEARNED_NF = 5;

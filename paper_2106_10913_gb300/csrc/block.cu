@@ -983,6 +983,87 @@ __global__ void __launch_bounds__(256) kb_wd_finish_umma(int n, const float* __r
     }
 }
 
+// ------------------------------------------------ device-driven PCG control
+// Control words of a graph-driven block PCG: ctl[0] iterations done,
+// ctl[1] rtol, ctl[2] maxit, ctl[3] status (0, AWG_ERR_BREAKDOWN,
+// AWG_ERR_MAXIT); its[c] / rel[c] the iteration at which column c stopped
+// and its recurrence relative residual.
+template <int K>
+__global__ void kb_pcg_init(int nrhs, double* sc, double* ctl, double rtol, double maxit, int* its, double* rel) {
+    const int c = threadIdx.x;
+    if (c < K) {
+        const double bb = sc[B_BB * K + c];
+        const bool a = c < nrhs && bb > 0.0;
+        sc[B_ACT * K + c] = a ? 1.0 : 0.0;
+        its[c] = 0;
+        rel[c] = 0.0;
+    }
+    if (c == 0) {
+        ctl[0] = 0.0;
+        ctl[1] = rtol;
+        ctl[2] = maxit;
+        ctl[3] = 0.0;
+    }
+}
+
+// After an x, r update: one more iteration; an active column whose p^T A p
+// is not positive (breakdown) or whose recurrence residual reached rtol
+// stops.  With `set`, the loop condition of the enclosing graph becomes
+// "some column active and iterations < maxit"; `add` kernels per loop body
+// go to *launches (profiling).
+template <int K>
+__global__ void kb_pcg_cond(double* sc, double* ctl, int* its, double* rel, cudaGraphConditionalHandle hc, int set,
+                            unsigned long long* launches, int add) {
+    const int c = threadIdx.x;
+    const int it = (int)ctl[0] + 1;
+    const double rtol = ctl[1];
+    const int maxit = (int)ctl[2];
+    bool active = false;
+    int status = 0;
+    if (c < K && sc[B_ACT * K + c] != 0.0) {
+        const double pq = sc[B_PQ * K + c];
+        const double r = sqrt(sc[B_RR * K + c] / sc[B_BB * K + c]);
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            sc[B_ACT * K + c] = 0.0;
+            its[c] = it;
+            rel[c] = r;
+            status = AWG_ERR_BREAKDOWN;
+        } else if (r <= rtol) {
+            sc[B_ACT * K + c] = 0.0;
+            its[c] = it;
+            rel[c] = r;
+        } else if (it >= maxit) {
+            its[c] = it;
+            rel[c] = r;
+            status = AWG_ERR_MAXIT;
+            active = true;
+        } else {
+            active = true;
+        }
+    }
+    const int any = __syncthreads_or(active && it < maxit);
+    const int st = __syncthreads_or(status == AWG_ERR_BREAKDOWN) ? AWG_ERR_BREAKDOWN
+                   : (__syncthreads_or(status == AWG_ERR_MAXIT) ? AWG_ERR_MAXIT : 0);
+    if (c == 0) {
+        ctl[0] = (double)it;
+        if (st && ctl[3] == 0.0) ctl[3] = (double)st;
+        if (set) cudaGraphSetConditional(hc, any ? 1u : 0u);
+        if (launches && add) atomicAdd(launches, (unsigned long long)add);
+    }
+}
+
+// iterations and residuals of the nrhs columns and the status to the
+// caller's arrays
+__global__ void kb_pcg_fini(int nrhs, const int* __restrict__ its, const double* __restrict__ rel,
+                            const double* __restrict__ ctl, int* d_its, double* d_rel, int* d_status) {
+    const int c = threadIdx.x;
+    if (c < nrhs) {
+        if (d_its) d_its[c] = its[c];
+        if (d_rel) d_rel[c] = rel[c];
+    }
+    if (c == 0 && d_status) *d_status = (int)ctl[3];
+}
+
 // ===================================================================== host
 namespace {
 
@@ -1010,6 +1091,12 @@ struct BView {
     double *pb, *px, *pr, *pp, *pq, *pz;
     double *sc, *red;
     unsigned* cnt;
+    // graph-driven PCG: iteration, rtol, maxit, status; per-column iterations
+    // and residuals; kernels launched by graph loop bodies (profiling)
+    double* ctl;
+    int* gits;
+    double* grel;
+    unsigned long long* glaunch;
 };
 
 constexpr int WT_SPLITS_MAX = 64;
@@ -1055,6 +1142,10 @@ size_t carve_block(const Handle* h, char* base, BView<double>* vd, BView<float>*
     d.sc = (double*)take(B_NSC * K * 8);
     d.red = (double*)take((size_t)1216 * K * 8);
     d.cnt = (unsigned*)take(64);
+    d.ctl = (double*)take(8 * 8);
+    d.gits = (int*)take(K * 4);
+    d.grel = (double*)take(K * 8);
+    d.glaunch = (unsigned long long*)take(64);
     if (vd) *vd = d;
     if (vf) {
         BView<float> f{};
@@ -1067,6 +1158,7 @@ size_t carve_block(const Handle* h, char* base, BView<double>* vd, BView<float>*
         f.dscale = d.dscale; f.mx = d.mx; f.mx2 = d.mx2; f.err = d.err;
         f.pb = d.pb; f.px = d.px; f.pr = d.pr; f.pp = d.pp; f.pq = d.pq; f.pz = d.pz;
         f.sc = d.sc; f.red = d.red; f.cnt = d.cnt;
+        f.ctl = d.ctl; f.gits = d.gits; f.grel = d.grel; f.glaunch = d.glaunch;
         *vf = f;
     }
     return (size_t)(p - base);
@@ -1679,6 +1771,193 @@ awg_status pcg_k(Handle* h, int prec, const double* b, double* x, int nrhs, int 
 }
 
 }  // namespace
+
+// One PCG iteration of K columns issued on the handle's streams (the body of
+// the graph loop): z = H r, rz_new, p update, q = A p, x and r update, stop test.
+template <int K>
+awg_status pcg_body_k(Handle* h, int prec, const BView<double>& v, cudaStream_t s, cudaGraphConditionalHandle hc,
+                      int set, int add) {
+    const int n = h->n;
+    const unsigned gr = grid_rows(n, RM<double, K>::RPB);
+    AWG_TRY(apply64_any(h, K, 4, prec, v.pr, v.pz, s));
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, v.sc + B_RZN * K);
+        AWG_LAUNCH();
+    }
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        kb_pcg_p<K><<<gr, 256, 0, s>>>(n, v.sc, v.pz, v.pp, v.cnt);
+        AWG_LAUNCH();
+    }
+    {
+        ProfScope ps_(h, AWG_PROF_SPMV, s);
+        kb_spmv_dot<K><<<gr, 256, 0, s>>>(n, (int*)h->rowptr.p, (int*)h->colidx.p, (double*)h->val.p, v.pp, v.pq,
+                                          v.red, v.cnt, v.sc + B_PQ * K);
+        AWG_LAUNCH();
+    }
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        kb_pcg_xr<K><<<gr, 256, 0, s>>>(n, v.sc, v.pp, v.pq, v.px, v.pr, v.red, v.cnt);
+        AWG_LAUNCH();
+    }
+    ProfScope ps_(h, AWG_PROF_VECTOR, s);
+    kb_pcg_cond<K><<<1, K, 0, s>>>(v.sc, v.ctl, v.gits, v.grel, hc, set, v.glaunch, add);
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
+// The loop graph of (prec, K): a conditional while node whose body is one
+// PCG iteration captured from the handle's streams; built on first use.
+template <int K>
+awg_status pcg_graph_k(Handle* h, int prec, const BView<double>& v, cudaGraphExec_t* out) {
+    const int slot = prec * 3 + (K == 16 ? 0 : (K == 32 ? 1 : 2));
+    if (h->bg_exec[slot]) {
+        *out = (cudaGraphExec_t)h->bg_exec[slot];
+        return AWG_OK;
+    }
+    cudaGraph_t g = nullptr;
+    AWG_CUDA(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle hc;
+    AWG_CUDA(cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hc;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    AWG_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    // capture one iteration; kernels are counted (not timed) while capturing
+    const int prof = h->prof;
+    const int64_t l0 = h->launches;
+    h->prof = 1 << 30;
+    AWG_CUDA(cudaStreamBeginCaptureToGraph(h->hp, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    awg_status st = pcg_body_k<K>(h, prec, v, h->hp, hc, 1, 0);
+    cudaGraph_t cap = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(h->hp, &cap);
+    const int body_launches = (int)(h->launches - l0);
+    h->prof = prof;
+    h->launches = l0;
+    if (st != AWG_OK || ce != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        return st != AWG_OK ? st : AWG_ERR_CUDA;
+    }
+    // the counting argument of the body's last kernel: patch it now that the
+    // number of kernels per body is known
+    {
+        size_t nn = 0;
+        AWG_CUDA(cudaGraphGetNodes(body, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        AWG_CUDA(cudaGraphGetNodes(body, nodes.data(), &nn));
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            AWG_CUDA(cudaGraphNodeGetType(nd, &t));
+            if (t != cudaGraphNodeTypeKernel) continue;
+            cudaKernelNodeParams kp;
+            AWG_CUDA(cudaGraphKernelNodeGetParams(nd, &kp));
+            if (kp.func != (void*)kb_pcg_cond<K>) continue;
+            int* addp = (int*)kp.kernelParams[7];
+            *addp = body_launches;
+            AWG_CUDA(cudaGraphKernelNodeSetParams(nd, &kp));
+        }
+    }
+    cudaGraphExec_t exec = nullptr;
+    // keep the capture-time stream priorities (H_2 chain ahead of the W passes)
+    AWG_CUDA(cudaGraphInstantiate(&exec, g, cudaGraphInstantiateFlagUseNodePriority));
+    h->bg_graph[slot] = g;
+    h->bg_exec[slot] = exec;
+    *out = exec;
+    return AWG_OK;
+}
+
+template <int K>
+awg_status pcg_async_k(Handle* h, int prec, const double* b, double* x, int nrhs, int ld, double rtol, int* d_iters,
+                       double* d_relres, int* d_status, cudaStream_t s) {
+    BView<double> v;
+    carve_block(h, (char*)h->bws.p, &v, nullptr);
+    const int n = h->n;
+    const dim3 tg((n + 31) / 32, (K + 31) / 32), tb(32, 8);
+    const unsigned gr = grid_rows(n, RM<double, K>::RPB);
+    const size_t len = (size_t)n * K;
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        kb_from_cols<double><<<tg, tb, 0, s>>>(n, nrhs, ld, K, b, v.pb);
+        AWG_LAUNCH();
+    }
+    AWG_CUDA(cudaMemsetAsync(v.px, 0, len * 8, s));
+    AWG_CUDA(cudaMemcpyAsync(v.pr, v.pb, len * 8, cudaMemcpyDeviceToDevice, s));
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pb, v.pb, v.red, v.cnt, v.sc + B_BB * K);
+        AWG_LAUNCH();
+    }
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        kb_pcg_init<K><<<1, K, 0, s>>>(nrhs, v.sc, v.ctl, rtol, (double)h->opt.maxit, v.gits, v.grel);
+        AWG_LAUNCH();
+    }
+    // first iteration with z = H r, p = z (then the loop's iterations)
+    AWG_TRY(apply64_any(h, K, 4, prec, v.pr, v.pz, s));
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, v.sc + B_RZ * K);
+        AWG_LAUNCH();
+    }
+    AWG_CUDA(cudaMemcpyAsync(v.pp, v.pz, len * 8, cudaMemcpyDeviceToDevice, s));
+    {
+        ProfScope ps_(h, AWG_PROF_SPMV, s);
+        kb_spmv_dot<K><<<gr, 256, 0, s>>>(n, (int*)h->rowptr.p, (int*)h->colidx.p, (double*)h->val.p, v.pp, v.pq,
+                                          v.red, v.cnt, v.sc + B_PQ * K);
+        AWG_LAUNCH();
+    }
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        kb_pcg_xr<K><<<gr, 256, 0, s>>>(n, v.sc, v.pp, v.pq, v.px, v.pr, v.red, v.cnt);
+        AWG_LAUNCH();
+    }
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        kb_pcg_cond<K><<<1, K, 0, s>>>(v.sc, v.ctl, v.gits, v.grel, 0, 0, nullptr, 0);
+        AWG_LAUNCH();
+    }
+    // the loop graph is captured after the first iteration has been issued
+    // (every kernel attribute and tensor-map entry point is set up by then)
+    cudaGraphExec_t exec;
+    AWG_TRY(pcg_graph_k<K>(h, prec, v, &exec));
+    AWG_CUDA(cudaGraphLaunch(exec, s));
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        kb_to_cols<double><<<tg, tb, 0, s>>>(n, nrhs, ld, K, v.px, x);
+        AWG_LAUNCH();
+    }
+    ProfScope ps_(h, AWG_PROF_VECTOR, s);
+    kb_pcg_fini<<<1, 64, 0, s>>>(nrhs, v.gits, v.grel, v.ctl, d_iters, d_relres, d_status);
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
+awg_status block_pcg_async(Handle* h, int prec, const double* b, double* x, int nrhs, int ld, double rtol,
+                           int* d_iters, double* d_relres, int* d_status, cudaStream_t s) {
+    if (nrhs < 1 || nrhs > BLK_KMAX) return AWG_ERR_INVALID_ARG;
+    AWG_TRY(block_prepare(h));
+    const int K = pick_k(nrhs);
+    if (K == 16) return pcg_async_k<16>(h, prec, b, x, nrhs, ld, rtol, d_iters, d_relres, d_status, s);
+    if (K == 32) return pcg_async_k<32>(h, prec, b, x, nrhs, ld, rtol, d_iters, d_relres, d_status, s);
+    return pcg_async_k<64>(h, prec, b, x, nrhs, ld, rtol, d_iters, d_relres, d_status, s);
+}
+
+// kernels launched by graph loop bodies since the last call (reset)
+int64_t block_graph_launches(Handle* h) {
+    if (!h->bws.p) return 0;
+    BView<double> v;
+    carve_block(h, (char*)h->bws.p, &v, nullptr);
+    unsigned long long c = 0;
+    if (cudaMemcpy(&c, v.glaunch, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+    cudaMemset(v.glaunch, 0, 8);
+    return (int64_t)c;
+}
 
 awg_status block_apply(Handle* h, int which, int prec, const double* x, double* y, int nrhs, int ld,
                        cudaStream_t s) {

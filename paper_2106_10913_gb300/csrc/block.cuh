@@ -23,6 +23,13 @@ awg_status block_apply(Handle* h, int which, int prec, const double* x, double* 
 awg_status block_pcg(Handle* h, int prec, const double* b, double* x, int nrhs, int ld, double rtol, int* iters,
                      double* relres, cudaStream_t s);
 
+// Block PCG whose iterations run as one CUDA graph launch (conditional
+// while node, device-side stopping test); asynchronous on s.
+awg_status block_pcg_async(Handle* h, int prec, const double* b, double* x, int nrhs, int ld, double rtol,
+                           int* d_iters, double* d_relres, int* d_status, cudaStream_t s);
+// kernels launched by graph loop bodies since the last call (reset)
+int64_t block_graph_launches(Handle* h);
+
 // Tensor-core passes over a 16-bit W (float16 or bfloat16), row-major
 // n x ldw.  All pointers are device pointers.
 struct UmmaW {

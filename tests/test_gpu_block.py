@@ -193,3 +193,75 @@ def test_block_apply_rejects_bad_sizes():
         awg_apply_block(sol.h, "h3ad", x, x.clone(), precision=FP64)
     with pytest.raises(AWGError):
         awg_apply_block(sol.h, 7, x[:2], x[:2].clone(), precision=FP64)
+
+
+def _async_solve(sol, B, prec, stream=None):
+    from paper_2106_10913_gb300 import awg_pcg_block_async
+    b = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+    x = torch.full_like(b, 3.0)
+    its = torch.zeros(B.shape[0], dtype=torch.int32, device="cuda")
+    rel = torch.zeros(B.shape[0], dtype=torch.float64, device="cuda")
+    st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    awg_pcg_block_async(sol.h, b, x, its, rel, st, 1e-8, precision=prec, stream=stream)
+    return x, its, rel, st
+
+
+@pytest.mark.parametrize("form", ["fp64", "fp16"])
+def test_block_pcg_async_matches_sync(pair, form):
+    """The graph-driven solve (device-side loop and stopping test) takes the
+    iterations of the host-driven block solve and reaches 1e-8 on every
+    column; a second call reuses the captured loop graph."""
+    p, sol, st = pair
+    from paper_2106_10913_gb300 import FP64, MIXED_FP16, awg_pcg_block
+    prec = {"fp64": FP64, "fp16": MIXED_FP16}[form]
+    for seed in (31, 32):
+        B = np.random.default_rng(seed).standard_normal((5, p.n))
+        x, its, rel, status = _async_solve(sol, B, prec)
+        torch.cuda.synchronize()
+        xs = torch.zeros((5, p.n), dtype=torch.float64, device="cuda")
+        _, its_s, _ = awg_pcg_block(sol.h, torch.from_numpy(B).cuda(), xs, 1e-8, precision=prec)
+        X = x.cpu().numpy()
+        assert int(status.item()) == 0
+        for c in range(5):
+            assert abs(int(its[c].item()) - its_s[c]) <= 1
+            assert float(rel[c].item()) <= 1e-8
+            assert np.linalg.norm(st.A @ X[c] - B[c]) <= 2e-8 * np.linalg.norm(B[c])
+
+
+def test_block_pcg_async_concurrent_problems():
+    """Two handles (independent problems) enqueued on two streams from one
+    host thread (their solves overlap on the device) reach 1e-8 each."""
+    from paper_2106_10913_gb300 import MIXED_FP16
+    pa, sa, sta = _pair("channels64")
+    pb, sb, stb = _pair("config1")
+    Ba = np.random.default_rng(41).standard_normal((3, pa.n))
+    Bb = np.random.default_rng(42).standard_normal((20, pb.n))
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    xa, ia, ra, sa_ = _async_solve(sa, Ba, MIXED_FP16, stream=s1)
+    xb, ib, rb, sb_ = _async_solve(sb, Bb, MIXED_FP16, stream=s2)
+    torch.cuda.synchronize()
+    assert int(sa_.item()) == 0 and int(sb_.item()) == 0
+    for (p, st, B, x) in ((pa, sta, Ba, xa), (pb, stb, Bb, xb)):
+        X = x.cpu().numpy()
+        for c in range(B.shape[0]):
+            assert np.linalg.norm(st.A @ X[c] - B[c]) <= 2e-8 * np.linalg.norm(B[c])
+
+
+@pytest.mark.parametrize("form", ["fp64", "fp16"])
+def test_pcg_async_single_rhs(pair, form):
+    """One right-hand side through the graph-driven loop (single-RHS apply in
+    the body): the iterations of awg_pcg and a 1e-8 residual."""
+    p, sol, st = pair
+    from paper_2106_10913_gb300 import FP64, MIXED_FP16, awg_pcg
+    prec = {"fp64": FP64, "fp16": MIXED_FP16}[form]
+    B = np.random.default_rng(51).standard_normal((1, p.n))
+    x, its, rel, status = _async_solve(sol, B, prec)
+    torch.cuda.synchronize()
+    x1 = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    _, its1, _ = awg_pcg(sol.h, torch.from_numpy(B[0]).cuda(), x1, 1e-8, precision=prec)
+    assert int(status.item()) == 0
+    assert abs(int(its[0].item()) - its1[0]) <= 1
+    assert float(rel[0].item()) <= 1e-8
+    X = x.cpu().numpy()
+    assert np.linalg.norm(st.A @ X[0] - B[0]) <= 2e-8 * np.linalg.norm(B[0])
