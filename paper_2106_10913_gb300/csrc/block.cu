@@ -238,6 +238,46 @@ __global__ void __launch_bounds__(256) kb_pcg_p(int n, double* sc, const double*
     }
 }
 
+// flexible (Polak-Ribiere) update for a preconditioner applied in lower
+// precision: per active column beta = (r.z - r.z_old) / rz_old with r.z in
+// B_RZN and r.z_old in B_TR, P = Z + beta P; the last block moves rz_new
+// into rz
+template <int K>
+__global__ void __launch_bounds__(256) kb_pcg_p_flex(int n, double* sc, const double* __restrict__ Z, double* P,
+                                                     unsigned* cnt) {
+    __shared__ unsigned ticket;
+    const int cc = ((threadIdx.x & 31) % RM<double, K>::TPR) * 2;
+    double beta[2];
+    bool act[2];
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+        const int c = cc + j;
+        const double rz = sc[B_RZ * K + c];
+        act[j] = sc[B_ACT * K + c] != 0.0;
+        beta[j] = (rz != 0.0) ? (sc[B_RZN * K + c] - sc[B_TR * K + c]) / rz : 0.0;
+    }
+    ROW_LOOP(double, K) {
+        const size_t e = (size_t)i * K + c0;
+        double z[2], pv[2];
+        ldv(Z + e, z);
+        ldv(P + e, pv);
+        pv[0] = act[0] ? fma(beta[0], pv[0], z[0]) : pv[0];
+        pv[1] = act[1] ? fma(beta[1], pv[1], z[1]) : pv[1];
+        stv(P + e, pv);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        ticket = atomicAdd(cnt, 1u);
+    }
+    __syncthreads();
+    if (ticket == gridDim.x - 1) {
+        if (threadIdx.x < K && sc[B_ACT * K + threadIdx.x] != 0.0)
+            sc[B_RZ * K + threadIdx.x] = sc[B_RZN * K + threadIdx.x];
+        if (threadIdx.x == 0) *cnt = 0u;
+    }
+}
+
 // --------------------------------------------------------- layout / types
 // dst (n x K row-major) from nrhs columns of src (column-major, ld), zero
 // columns beyond nrhs; 32 x 32 tiles through shared memory
@@ -1957,6 +1997,110 @@ int64_t block_graph_launches(Handle* h) {
     if (cudaMemcpy(&c, v.glaunch, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
     cudaMemset(v.glaunch, 0, 8);
     return (int64_t)c;
+}
+
+// W columns c0 .. c0 + k - 1: A_+ X = B by flexible block PCG (K = 64
+// columns per group) with H_2 in the precision wprec (Section 4.4 items 1-2):
+// the A_+ products and every recurrence in float64, the preconditioner in
+// float32 for the mixed forms (its local solves on the tensor cores).
+// Columns stop at ||b - A_+ x|| <= rtol ||b|| (recurrence residual) or
+// breakdown; *its and *worst report the group's iterations and largest
+// final relative residual.
+template <int K>
+awg_status wsolve_k(Handle* h, int wprec, const double* B, double* X, int k, double rtol, int maxit, int* its,
+                    double* worst, cudaStream_t s) {
+    BView<double> v;
+    carve_block(h, (char*)h->bws.p, &v, nullptr);
+    BlockApply<double, K> bd{h, v};
+    const int n = h->n;
+    const dim3 tg((n + 31) / 32, (K + 31) / 32), tb(32, 8);
+    const unsigned gr = grid_rows(n, RM<double, K>::RPB);
+    const size_t len = (size_t)n * K;
+    double* sc = v.sc;
+    double* z = v.pz;
+    double* zo = v.tmpw;  // previous z (float64 view of the W-pass output, unused by H_2)
+    kb_from_cols<double><<<tg, tb, 0, s>>>(n, k, n, K, B, v.pb);
+    AWG_LAUNCH();
+    AWG_CUDA(cudaMemsetAsync(v.px, 0, len * 8, s));
+    AWG_CUDA(cudaMemcpyAsync(v.pr, v.pb, len * 8, cudaMemcpyDeviceToDevice, s));
+    kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pb, v.pb, v.red, v.cnt, sc + B_BB * K);
+    AWG_LAUNCH();
+    AWG_TRY(apply64_any(h, K, 3, wprec, v.pr, z, s));
+    kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, z, v.red, v.cnt, sc + B_RZ * K);
+    AWG_LAUNCH();
+    AWG_CUDA(cudaMemcpyAsync(v.pp, z, len * 8, cudaMemcpyDeviceToDevice, s));
+    std::vector<double> hs(B_NSC * K), act(K, 0.0);
+    AWG_CUDA(cudaMemcpyAsync(hs.data(), sc, B_NSC * K * 8, cudaMemcpyDeviceToHost, s));
+    AWG_CUDA(cudaStreamSynchronize(s));
+    int nact = 0;
+    for (int c = 0; c < k; c++)
+        if (hs[B_BB * K + c] > 0.0) { act[c] = 1.0; nact++; }
+    AWG_CUDA(cudaMemcpyAsync(sc + B_ACT * K, act.data(), K * 8, cudaMemcpyHostToDevice, s));
+    int it = 0;
+    double wst = 0.0;
+    while (nact > 0) {
+        AWG_TRY(bd.aplus(v.pp, v.pq, nullptr, 1.0, s));  // q = A_+ p
+        kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pp, v.pq, v.red, v.cnt, sc + B_PQ * K);
+        AWG_LAUNCH();
+        kb_pcg_xr<K><<<gr, 256, 0, s>>>(n, sc, v.pp, v.pq, v.px, v.pr, v.red, v.cnt);
+        AWG_LAUNCH();
+        AWG_CUDA(cudaMemcpyAsync(hs.data(), sc, 3 * K * 8, cudaMemcpyDeviceToHost, s));
+        AWG_CUDA(cudaStreamSynchronize(s));
+        it++;
+        bool changed = false;
+        wst = 0.0;
+        for (int c = 0; c < k; c++) {
+            const double rel = sqrt(hs[B_RR * K + c] / hs[B_BB * K + c]);
+            if (hs[B_BB * K + c] > 0.0) wst = std::max(wst, rel);
+            if (act[c] == 0.0) continue;
+            if (!(hs[B_PQ * K + c] > 0.0) || rel <= rtol) {  // exact solution reached, or converged
+                act[c] = 0.0;
+                nact--;
+                changed = true;
+            }
+        }
+        if (nact == 0 || it >= maxit) break;
+        if (changed) AWG_CUDA(cudaMemcpyAsync(sc + B_ACT * K, act.data(), K * 8, cudaMemcpyHostToDevice, s));
+        std::swap(z, zo);
+        AWG_TRY(apply64_any(h, K, 3, wprec, v.pr, z, s));  // z = H_2 r
+        kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, z, v.red, v.cnt, sc + B_RZN * K);
+        AWG_LAUNCH();
+        kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, zo, v.red, v.cnt, sc + B_TR * K);
+        AWG_LAUNCH();
+        kb_pcg_p_flex<K><<<gr, 256, 0, s>>>(n, sc, z, v.pp, v.cnt);
+        AWG_LAUNCH();
+    }
+    kb_to_cols<double><<<tg, tb, 0, s>>>(n, k, n, K, v.px, X);
+    AWG_LAUNCH();
+    AWG_CUDA(cudaStreamSynchronize(s));
+    *its = it;
+    *worst = wst;
+    return AWG_OK;
+}
+
+awg_status block_solve_w(Handle* h, int wprec, const double* Vhat, double* W, int nm, double rtol, int maxit,
+                         int* its_max, double* worst, cudaStream_t s) {
+    AWG_TRY(block_prepare(h));
+    *its_max = 0;
+    *worst = 0.0;
+    for (int c0 = 0; c0 < nm; c0 += BLK_KMAX) {
+        const int k = std::min(BLK_KMAX, nm - c0);
+        int it = 0;
+        double w = 0.0;
+        const double* Bc = Vhat + (size_t)c0 * h->n;
+        double* Xc = W + (size_t)c0 * h->n;
+        const int K = pick_k(k);
+        awg_status st;
+        if (K == 16) st = wsolve_k<16>(h, wprec, Bc, Xc, k, rtol, maxit, &it, &w, s);
+        else if (K == 32) st = wsolve_k<32>(h, wprec, Bc, Xc, k, rtol, maxit, &it, &w, s);
+        else st = wsolve_k<64>(h, wprec, Bc, Xc, k, rtol, maxit, &it, &w, s);
+        AWG_TRY(st);
+        *its_max = std::max(*its_max, it);
+        *worst = std::max(*worst, w);
+        if (h->opt.verbose)
+            fprintf(stderr, "libawg: W columns %d..%d: %d iterations, max relres %.3e\n", c0, c0 + k, it, w);
+    }
+    return AWG_OK;
 }
 
 awg_status block_apply(Handle* h, int which, int prec, const double* x, double* y, int nrhs, int ld,

@@ -29,6 +29,10 @@ awg_status block_pcg_async(Handle* h, int prec, const double* b, double* x, int 
                            int* d_iters, double* d_relres, int* d_status, cudaStream_t s);
 // kernels launched by graph loop bodies since the last call (reset)
 int64_t block_graph_launches(Handle* h);
+// W = A_+^-1 Vhat (n x nm column-major, ld = n) by flexible block PCG with
+// H_2 in precision wprec, groups of 64 columns
+awg_status block_solve_w(Handle* h, int wprec, const double* Vhat, double* W, int nm, double rtol, int maxit,
+                         int* its_max, double* worst, cudaStream_t s);
 
 // Tensor-core passes over a 16-bit W (float16 or bfloat16), row-major
 // n x ldw.  All pointers are device pointers.

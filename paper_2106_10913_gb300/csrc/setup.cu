@@ -15,6 +15,7 @@
 
 #include "awg_common.cuh"
 #include "ops.cuh"
+#include "block.cuh"
 
 #include <algorithm>
 #include <chrono>
@@ -381,6 +382,19 @@ static awg_status build_W(Handle* h) {
     k_scatter_cols<<<N, 256, 0, s>>>(n, (int*)h->sub_ptr.p, (int*)h->sub_idx.p, (int*)h->wcol_ptr.p,
                                      (int64_t*)h->vm_off.p, (double*)h->Vm.p, Vhat, 0, nm);
     AWG_LAUNCH();
+    // the block path: groups of 64 columns through the block kernels (local
+    // solves on the tensor cores for the float32 preconditioner)
+    if (h->opt.block_tensor_cores) {
+        int its = 0;
+        double worst = 0.0;
+        AWG_TRY(block_solve_w(h, h->opt.w_precision, Vhat, (double*)h->Wcm.p, nm, h->opt.w_rtol, h->opt.w_maxit,
+                              &its, &worst, s));
+        h->w_iters = its;
+        h->w_relres = worst;
+        AWG_CUDA(cudaFreeAsync(Vhat, s));
+        AWG_CUDA(cudaStreamSynchronize(s));
+        return AWG_OK;
+    }
     // columns per chunk: about 10 n-vectors per column live at once
     const size_t budget = (size_t)24 << 30;
     int chunk = (int)std::max<size_t>(1, std::min<size_t>(nm, budget / ((size_t)n * 8 * 13)));
