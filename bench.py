@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -267,7 +268,7 @@ def run_awg(args):
     pmask = 1
     for nm_ in args.forms.split(","):
         pmask |= 1 << {"fp64": 0, "mixed_fp32": 1, "mixed_bf16": 2,
-                       "mixed_fp16": 3}[nm_.replace("_block", "").replace("_graph", "")]
+                       "mixed_fp16": 3}[re.sub(r"_(block|graph)\d*$", "", nm_)]
     sol = AWGSolver(p.rowptr, p.colidx, p.val, p.part, p.nparts, p.overlap, p.tau,
                     precisions=pmask, verbose=int(args.verbose), **geneo_opts)
     setup_s = time.perf_counter() - t0
@@ -281,32 +282,33 @@ def run_awg(args):
     timed_mask = 0xFF  # every kernel class
     all_forms = {"fp64": FP64, "mixed_fp32": MIXED_FP32, "mixed_bf16": MIXED_BF16,
                  "mixed_fp16": MIXED_FP16}
-    K = args.nrhs
     # batched forms: K right-hand sides per block solve, column 0 the
-    # benchmark's b, the others seeded N(0, 1)
-    B = np.concatenate([p.b[None, :], np.random.default_rng(1).standard_normal((K - 1, p.n))])
-    bB = torch.from_numpy(B).cuda()
-    xB = torch.zeros_like(bB)
-    g_its = torch.zeros(K, dtype=torch.int32, device="cuda")
-    g_rel = torch.zeros(K, dtype=torch.float64, device="cuda")
+    # benchmark's b, the others seeded N(0, 1); a width suffix (e.g.
+    # mixed_fp16_block32) overrides --nrhs
+    Kmax = max([args.nrhs] + [int(m.group(3)) for m in (re.match(r"(.*)_(block|graph)(\d+)$", f)
+                                                         for f in args.forms.split(",")) if m])
+    Ball = np.concatenate([p.b[None, :], np.random.default_rng(1).standard_normal((Kmax - 1, p.n))])
+    bAll = torch.from_numpy(Ball).cuda()
+    xAll = torch.zeros_like(bAll)
+    g_its = torch.zeros(Kmax, dtype=torch.int32, device="cuda")
+    g_rel = torch.zeros(Kmax, dtype=torch.float64, device="cuda")
     g_st = torch.zeros(1, dtype=torch.int32, device="cuda")
 
-    def graph_solve(prec):
-        # enqueued without a host synchronisation; results read after the step
-        awg_pcg_block_async(sol.h, bB, xB, g_its, g_rel, g_st, RTOL, precision=prec)
-        return None
-
     for name in args.forms.split(","):
-        graph = name.endswith("_graph")
-        block = name.endswith("_block") or graph
-        base = name.rsplit("_", 1)[0] if block else name
+        m = re.match(r"(.*)_(block|graph)(\d*)$", name)
+        graph = bool(m) and m.group(2) == "graph"
+        block = bool(m)
+        base = m.group(1) if m else name
+        K = (int(m.group(3)) if m.group(3) else args.nrhs) if m else 1
         prec = all_forms[base]
+        bB, xB = bAll[:K], xAll[:K]
         if graph:
-            solve = lambda: graph_solve(prec)
+            solve = (lambda prec=prec, bB=bB, xB=xB, K=K:
+                     awg_pcg_block_async(sol.h, bB, xB, g_its[:K], g_rel[:K], g_st, RTOL, precision=prec))
         elif block:
-            solve = lambda: awg_pcg_block(sol.h, bB, xB, RTOL, prec, check=False)
+            solve = lambda prec=prec, bB=bB, xB=xB: awg_pcg_block(sol.h, bB, xB, RTOL, prec, check=False)
         else:
-            solve = lambda: awg_pcg(sol.h, b, x, RTOL, prec, check=False)
+            solve = lambda prec=prec: awg_pcg(sol.h, b, x, RTOL, prec, check=False)
         per_step = K if block else 1
         for _ in range(args.warmup):
             solve()
@@ -336,8 +338,8 @@ def run_awg(args):
             dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
         ms = float(tmax.item())
         if not its:  # graph-driven solves: device results of the last step
-            its = [int(g_its.max().item())]
-            rels = [float(g_rel.max().item())]
+            its = [int(g_its[:K].max().item())]
+            rels = [float(g_rel[:K].max().item())]
             sts = [int(g_st.item())]
         ok = all(s == 0 for s in sts) and max(rels) <= RTOL
         forms[name] = {"prec": prec, "block": block, "graph": graph, "nrhs": per_step, "ms": ms,
@@ -350,13 +352,18 @@ def run_awg(args):
     best_name = [k for k, v in forms.items() if v is best][0]
     # kernels inside a graph loop are not event-timed: the roofline of a
     # graph-driven form comes from the host-driven run of the same kernels
-    rform = forms.get(best_name.replace("_graph", "_block"), best) if best["graph"] else best
+    rform = best
+    if best["graph"]:
+        base = re.sub(r"_graph\d*$", "", best_name)
+        twins = [k for k, v in forms.items() if not v["graph"] and v["block"] and k.startswith(base + "_block")]
+        if twins:
+            rform = forms[max(twins, key=lambda k: forms[k]["nrhs"])]
     roofline = roofline_of(rform, info)
     if rform is not best:
-        roofline["timed_in"] = best_name.replace("_graph", "_block")
+        roofline["timed_in"] = [k for k, v in forms.items() if v is rform][0]
 
     # end to end: host buffers through the public API (H2D b, solve, D2H x)
-    hb = torch.from_numpy(B if best["block"] else p.b).pin_memory()
+    hb = torch.from_numpy(np.ascontiguousarray(Ball[:best["nrhs"]]) if best["block"] else p.b).pin_memory()
     hx = torch.empty_like(hb).pin_memory()
     db = torch.empty_like(hb, device="cuda")
     dx = torch.zeros_like(db)
@@ -366,7 +373,8 @@ def run_awg(args):
     for _ in range(args.steps):
         db.copy_(hb, non_blocking=True)
         if best["graph"]:
-            awg_pcg_block_async(sol.h, db, dx, g_its, g_rel, g_st, RTOL, precision=best["prec"])
+            awg_pcg_block_async(sol.h, db, dx, g_its[:best["nrhs"]], g_rel[:best["nrhs"]], g_st, RTOL,
+                                precision=best["prec"])
         elif best["block"]:
             awg_pcg_block(sol.h, db, dx, RTOL, best["prec"], check=False)
         else:
@@ -544,12 +552,14 @@ def main():
     ap.add_argument("--config", default="config2")
     ap.add_argument("--verbose", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--nrhs", type=int, default=32, help="right-hand sides per step of the batched forms")
+    ap.add_argument("--nrhs", type=int, default=64,
+                    help="right-hand sides per step of the batched forms without a width suffix (<= 64 for "
+                         "_block, <= 128 for _graph)")
     ap.add_argument("--batch-problems", type=int, default=8,
                     help="independent problems of the batched-problem measurement (0: skip)")
     ap.add_argument("--batch-sides", default="128,256", help="range of their grid sides")
-    ap.add_argument("--forms", default="fp64,mixed_fp32,mixed_bf16,mixed_fp16,mixed_fp32_block,mixed_fp16_block,"
-                                      "mixed_fp16_graph",
+    ap.add_argument("--forms", default="fp64,mixed_fp32,mixed_bf16,mixed_fp16,mixed_fp16_block32,mixed_fp16_block,"
+                                      "mixed_fp16_graph128",
                     help="comma-separated storage forms to time; a _block suffix times the "
                          "batched (multi-right-hand-side) solve of --nrhs columns, _graph the same "
                          "solve as one CUDA graph launch with a device-side loop")

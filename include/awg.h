@@ -309,7 +309,7 @@ awg_status awg_pcg_block(awg_handle h, int precision, const double* d_b, double*
                          double rtol, int* h_iters, double* h_relres, void* stream);
 
 /*
- * Asynchronous block PCG (H_3,ad, 1 <= nrhs <= 64 columns, x_0 = 0): the
+ * Asynchronous block PCG (H_3,ad, 1 <= nrhs <= 128 columns, x_0 = 0): the
  * iterations run as one CUDA graph launch, a conditional while node whose
  * body is one iteration captured from the handle's two streams, with the
  * stopping test (per column, recurrence residual <= rtol ||b||, Section 1)
@@ -323,7 +323,10 @@ awg_status awg_pcg_block(awg_handle h, int precision, const double* d_b, double*
  * int32[1] (AWG_OK, AWG_ERR_BREAKDOWN or AWG_ERR_MAXIT); any may be NULL.
  * With nrhs = 1 the loop body is the single-right-hand-side apply (the
  * GEMV-shaped passes of awg_pcg), otherwise the block apply of
- * awg_pcg_block.  The true residual is not re-checked (awg_pcg_block does
+ * awg_pcg_block; more than 64 columns run as two groups (64 and the rest)
+ * side by side on the handle's two block slots (own workspace, stream pair
+ * and loop graphs), so one group's float64 coarse GEMMs overlap the other's
+ * bandwidth-bound passes.  The true residual is not re-checked (awg_pcg_block does
  * that).
  * Errors returned: AWG_ERR_INVALID_ARG, AWG_ERR_STATE, AWG_ERR_OOM,
  * AWG_ERR_CUDA.

@@ -233,7 +233,7 @@ def awg_pcg_block(h, b, x, rtol: float = 1e-8, precision: int = FP64, stream=Non
 
 def awg_pcg_block_async(h, b, x, iters, relres, status, rtol: float = 1e-8, precision: int = FP64,
                         stream=None):
-    """Enqueue a graph-driven block PCG for the rows of b (nrhs <= 64):
+    """Enqueue a graph-driven block PCG for the rows of b (nrhs <= 128):
     iters (int32[nrhs]), relres (float64[nrhs]) and status (int32[1]) are
     CUDA tensors filled when the work completes."""
     ptr = lambda t: None if t is None else t.data_ptr()

@@ -59,7 +59,8 @@ static void free_all(Handle* h) {
                       &h->Vm, &h->lam_m, &h->sigma, &h->modes, &h->mode_ptr, &h->z_off, &h->Z,
                       &h->E, &h->Einv, &h->wcol_ptr, &h->Wcm, &h->F64, &h->ws, &h->flag, &h->red,
                       &h->bws, &h->bval32, &h->bvm32, &h->blam32, &h->blam64, &h->bz32,
-                      &h->ul_gt, &h->ul_gtoff, &h->ul_kcpre, &h->ul_tsub, &h->ul_trt, &h->g1buf, &h->g1cnt};
+                      &h->ul_gt, &h->ul_gtoff, &h->ul_kcpre, &h->ul_tsub, &h->ul_trt, &h->g1buf, &h->g1cnt,
+                      &h->bws2};
     for (DevBuf* b : bufs) dfree(h, *b);
     for (auto& P : h->prec) {
         dfree(h, P.G);
@@ -77,6 +78,19 @@ static void free_all(Handle* h) {
         h->g1_exec[g] = nullptr;
         h->g1_graph[g] = nullptr;
     }
+    for (int g = 0; g < 12; g++) {
+        if (h->bg2_exec[g]) cudaGraphExecDestroy(h->bg2_exec[g]);
+        if (h->bg2_graph[g]) cudaGraphDestroy(h->bg2_graph[g]);
+        h->bg2_exec[g] = nullptr;
+        h->bg2_graph[g] = nullptr;
+    }
+    for (cudaEvent_t* e : {&h->ev2_fork, &h->ev2_mid, &h->ev2_join, &h->ev2_in, &h->ev2_out}) {
+        if (*e) cudaEventDestroy(*e);
+        *e = nullptr;
+    }
+    if (h->side2) cudaStreamDestroy(h->side2);
+    if (h->hp2) cudaStreamDestroy(h->hp2);
+    h->side2 = h->hp2 = nullptr;
     for (int g = 0; g < 12; g++) {
         if (h->bg_exec[g]) cudaGraphExecDestroy(h->bg_exec[g]);
         if (h->bg_graph[g]) cudaGraphDestroy(h->bg_graph[g]);
@@ -359,7 +373,7 @@ awg_status awg_pcg_block(awg_handle hh, int precision, const double* d_b, double
 awg_status awg_pcg_block_async(awg_handle hh, int precision, const double* d_b, double* d_x, int nrhs, int ld,
                                double rtol, int* d_iters, double* d_relres, int* d_status, void* stream) {
     Handle* h = reinterpret_cast<Handle*>(hh);
-    if (!h || !d_b || !d_x || nrhs < 1 || nrhs > 64 || ld < h->n || !(rtol > 0.0) || precision < 0 ||
+    if (!h || !d_b || !d_x || nrhs < 1 || nrhs > 128 || ld < h->n || !(rtol > 0.0) || precision < 0 ||
         precision >= AWG_NPREC)
         return AWG_ERR_INVALID_ARG;
     if (!h->prec[precision].built || (precision != AWG_FP64 && !h->prec[AWG_MIXED_FP32].G.p)) return AWG_ERR_STATE;

@@ -148,6 +148,15 @@ struct Handle {
     // graph-driven block PCG: loop graph per (precision, K in 16/32/64)
     cudaGraph_t bg_graph[12] = {};
     cudaGraphExec_t bg_exec[12] = {};
+    // a second block slot (workspace, stream pair, events, loop graphs): the
+    // two column groups of a wide graph-driven solve run side by side, so
+    // one group's float64 coarse GEMMs overlap the other's bandwidth-bound
+    // passes
+    DevBuf bws2;
+    cudaStream_t hp2 = nullptr, side2 = nullptr;
+    cudaEvent_t ev2_fork = nullptr, ev2_mid = nullptr, ev2_join = nullptr, ev2_in = nullptr, ev2_out = nullptr;
+    cudaGraph_t bg2_graph[12] = {};
+    cudaGraphExec_t bg2_exec[12] = {};
     // graph-driven single-RHS PCG: loop graph per precision, its vectors
     // (b, x, r, p, q, z) and the graph-loop kernel counter
     cudaGraph_t g1_graph[4] = {};

@@ -1212,6 +1212,23 @@ int grid_rows(int n, int rpb) { return std::max(1, std::min((n + rpb - 1) / rpb,
 
 }  // namespace
 
+// A block slot: workspace, the side stream and events of its apply, and
+// its cache of loop graphs.  Slot 0 is the handle's main set; slot 1 the
+// second set used by wide graph-driven solves.
+struct Slot {
+    char* ws;
+    cudaStream_t main, side;
+    cudaEvent_t fork, mid, join;
+    cudaGraph_t* graph;
+    cudaGraphExec_t* exec;
+};
+Slot slot0(Handle* h) {
+    return {(char*)h->bws.p, h->hp, h->side, h->ev_fork, h->ev_mid, h->ev_join, h->bg_graph, h->bg_exec};
+}
+Slot slot1(Handle* h) {
+    return {(char*)h->bws2.p, h->hp2, h->side2, h->ev2_fork, h->ev2_mid, h->ev2_join, h->bg2_graph, h->bg2_exec};
+}
+
 UmmaLocal ul_of(const Handle* h) {
     UmmaLocal u;
     u.N = h->N;
@@ -1295,6 +1312,7 @@ template <typename T, int K>
 struct BlockApply {
     Handle* h;
     BView<T> v;
+    Slot sl;
     using A = T;
 
     static dim3 rows_grid(int n) { return dim3(grid_rows(n, RM<T, K>::RPB)); }
@@ -1638,20 +1656,20 @@ struct BlockApply {
             case 3: return h2(prec, X, Y, s);
             case 4: {  // H_3,ad = H_2 + W F^-1 W^T (Def. 10); the W branch on the side stream
                 if (h->n_minus == 0) return h2(prec, X, Y, s);
-                AWG_CUDA(cudaEventRecord(h->ev_fork, s));
-                AWG_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+                AWG_CUDA(cudaEventRecord(sl.fork, s));
+                AWG_CUDA(cudaStreamWaitEvent(sl.side, sl.fork, 0));
                 // side stream: W^T X (HBM) beside the first E^-1 (FP64 pipes),
                 // then F^-1 (FP64) after it, beside the local solves (FP32),
                 // and W d beside the second E^-1
-                AWG_TRY(wt(prec, X, v.w0, h->side));
+                AWG_TRY(wt(prec, X, v.w0, sl.side));
                 AWG_TRY(h2a(X, s));
-                AWG_CUDA(cudaEventRecord(h->ev_mid, s));
-                AWG_CUDA(cudaStreamWaitEvent(h->side, h->ev_mid, 0));
+                AWG_CUDA(cudaEventRecord(sl.mid, s));
+                AWG_CUDA(cudaStreamWaitEvent(sl.side, sl.mid, 0));
                 AWG_TRY(dense(h->n_minus, (double*)h->prec[prec].Finv.p, v.w0, v.dd, 1.0, nullptr, 0.0, v.dps,
-                               h->side));
-                AWG_TRY(wd(prec, v.dd, v.tmpw, nullptr, h->side));
-                AWG_CUDA(cudaEventRecord(h->ev_join, h->side));
-                return h2b(prec, X, Y, s, v.tmpw, h->ev_join);
+                               sl.side));
+                AWG_TRY(wd(prec, v.dd, v.tmpw, nullptr, sl.side));
+                AWG_CUDA(cudaEventRecord(sl.join, sl.side));
+                return h2b(prec, X, Y, s, v.tmpw, sl.join);
             }
             default: return AWG_ERR_INVALID_ARG;
         }
@@ -1676,21 +1694,22 @@ struct BlockApply {
 };
 
 template <int K>
-awg_status apply64_k(Handle* h, int which, int prec, const double* X, double* Y, cudaStream_t s) {
+awg_status apply64_k(Handle* h, int which, int prec, const double* X, double* Y, cudaStream_t s, const Slot& sl) {
     if (prec == AWG_FP64) {
-        BlockApply<double, K> b{h, {}};
-        carve_block(h, (char*)h->bws.p, &b.v, nullptr);
+        BlockApply<double, K> b{h, {}, sl};
+        carve_block(h, sl.ws, &b.v, nullptr);
         return b.apply64(which, prec, X, Y, s);
     }
-    BlockApply<float, K> b{h, {}};
-    carve_block(h, (char*)h->bws.p, nullptr, &b.v);
+    BlockApply<float, K> b{h, {}, sl};
+    carve_block(h, sl.ws, nullptr, &b.v);
     return b.apply64(which, prec, X, Y, s);
 }
 
-awg_status apply64_any(Handle* h, int K, int which, int prec, const double* X, double* Y, cudaStream_t s) {
-    if (K == 16) return apply64_k<16>(h, which, prec, X, Y, s);
-    if (K == 32) return apply64_k<32>(h, which, prec, X, Y, s);
-    return apply64_k<64>(h, which, prec, X, Y, s);
+awg_status apply64_any(Handle* h, int K, int which, int prec, const double* X, double* Y, cudaStream_t s,
+                       const Slot& sl) {
+    if (K == 16) return apply64_k<16>(h, which, prec, X, Y, s, sl);
+    if (K == 32) return apply64_k<32>(h, which, prec, X, Y, s, sl);
+    return apply64_k<64>(h, which, prec, X, Y, s, sl);
 }
 
 int pick_k(int nrhs) { return nrhs <= 16 ? 16 : (nrhs <= 32 ? 32 : 64); }
@@ -1715,7 +1734,7 @@ awg_status pcg_k(Handle* h, int prec, const double* b, double* x, int nrhs, int 
     AWG_CUDA(cudaMemsetAsync(v.px, 0, len * 8, s));
     AWG_CUDA(cudaMemcpyAsync(v.pr, v.pb, len * 8, cudaMemcpyDeviceToDevice, s));
     AWG_TRY(prof_vec([&] { kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pb, v.pb, v.red, v.cnt, sc + B_BB * K); }));
-    AWG_TRY(apply64_any(h, K, 4, prec, v.pr, v.pz, s));
+    AWG_TRY(apply64_any(h, K, 4, prec, v.pr, v.pz, s, slot0(h)));
     AWG_TRY(prof_vec([&] { kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, sc + B_RZ * K); }));
     AWG_CUDA(cudaMemcpyAsync(v.pp, v.pz, len * 8, cudaMemcpyDeviceToDevice, s));
     std::vector<double> hs(B_NSC * K);
@@ -1782,7 +1801,7 @@ awg_status pcg_k(Handle* h, int prec, const double* b, double* x, int nrhs, int 
         }
         if (nact == 0) break;
         if (changed) AWG_TRY(upload_act());
-        AWG_TRY(apply64_any(h, K, 4, prec, v.pr, v.pz, s));
+        AWG_TRY(apply64_any(h, K, 4, prec, v.pr, v.pz, s, slot0(h)));
         AWG_TRY(prof_vec([&] { kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, sc + B_RZN * K); }));
         AWG_TRY(prof_vec([&] { kb_pcg_p<K><<<gr, 256, 0, s>>>(n, sc, v.pz, v.pp, v.cnt); }));
     }
@@ -1816,10 +1835,10 @@ awg_status pcg_k(Handle* h, int prec, const double* b, double* x, int nrhs, int 
 // the graph loop): z = H r, rz_new, p update, q = A p, x and r update, stop test.
 template <int K>
 awg_status pcg_body_k(Handle* h, int prec, const BView<double>& v, cudaStream_t s, cudaGraphConditionalHandle hc,
-                      int set, int add) {
+                      int set, int add, const Slot& sl) {
     const int n = h->n;
     const unsigned gr = grid_rows(n, RM<double, K>::RPB);
-    AWG_TRY(apply64_any(h, K, 4, prec, v.pr, v.pz, s));
+    AWG_TRY(apply64_any(h, K, 4, prec, v.pr, v.pz, s, sl));
     {
         ProfScope ps_(h, AWG_PROF_VECTOR, s);
         kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, v.sc + B_RZN * K);
@@ -1850,10 +1869,10 @@ awg_status pcg_body_k(Handle* h, int prec, const BView<double>& v, cudaStream_t 
 // The loop graph of (prec, K): a conditional while node whose body is one
 // PCG iteration captured from the handle's streams; built on first use.
 template <int K>
-awg_status pcg_graph_k(Handle* h, int prec, const BView<double>& v, cudaGraphExec_t* out) {
+awg_status pcg_graph_k(Handle* h, int prec, const BView<double>& v, cudaGraphExec_t* out, const Slot& sl) {
     const int slot = prec * 3 + (K == 16 ? 0 : (K == 32 ? 1 : 2));
-    if (h->bg_exec[slot]) {
-        *out = (cudaGraphExec_t)h->bg_exec[slot];
+    if (sl.exec[slot]) {
+        *out = sl.exec[slot];
         return AWG_OK;
     }
     cudaGraph_t g = nullptr;
@@ -1872,10 +1891,10 @@ awg_status pcg_graph_k(Handle* h, int prec, const BView<double>& v, cudaGraphExe
     const int prof = h->prof;
     const int64_t l0 = h->launches;
     h->prof = 1 << 30;
-    AWG_CUDA(cudaStreamBeginCaptureToGraph(h->hp, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    awg_status st = pcg_body_k<K>(h, prec, v, h->hp, hc, 1, 0);
+    AWG_CUDA(cudaStreamBeginCaptureToGraph(sl.main, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    awg_status st = pcg_body_k<K>(h, prec, v, sl.main, hc, 1, 0, sl);
     cudaGraph_t cap = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(h->hp, &cap);
+    const cudaError_t ce = cudaStreamEndCapture(sl.main, &cap);
     const int body_launches = (int)(h->launches - l0);
     h->prof = prof;
     h->launches = l0;
@@ -1906,17 +1925,18 @@ awg_status pcg_graph_k(Handle* h, int prec, const BView<double>& v, cudaGraphExe
     cudaGraphExec_t exec = nullptr;
     // keep the capture-time stream priorities (H_2 chain ahead of the W passes)
     AWG_CUDA(cudaGraphInstantiate(&exec, g, cudaGraphInstantiateFlagUseNodePriority));
-    h->bg_graph[slot] = g;
-    h->bg_exec[slot] = exec;
+    sl.graph[slot] = g;
+    sl.exec[slot] = exec;
     *out = exec;
     return AWG_OK;
 }
 
 template <int K>
 awg_status pcg_async_k(Handle* h, int prec, const double* b, double* x, int nrhs, int ld, double rtol, int* d_iters,
-                       double* d_relres, int* d_status, cudaStream_t s) {
+                       double* d_relres, int* d_status, const Slot& sl) {
+    const cudaStream_t s = sl.main;
     BView<double> v;
-    carve_block(h, (char*)h->bws.p, &v, nullptr);
+    carve_block(h, sl.ws, &v, nullptr);
     const int n = h->n;
     const dim3 tg((n + 31) / 32, (K + 31) / 32), tb(32, 8);
     const unsigned gr = grid_rows(n, RM<double, K>::RPB);
@@ -1939,7 +1959,7 @@ awg_status pcg_async_k(Handle* h, int prec, const double* b, double* x, int nrhs
         AWG_LAUNCH();
     }
     // first iteration with z = H r, p = z (then the loop's iterations)
-    AWG_TRY(apply64_any(h, K, 4, prec, v.pr, v.pz, s));
+    AWG_TRY(apply64_any(h, K, 4, prec, v.pr, v.pz, s, sl));
     {
         ProfScope ps_(h, AWG_PROF_VECTOR, s);
         kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, v.sc + B_RZ * K);
@@ -1965,7 +1985,7 @@ awg_status pcg_async_k(Handle* h, int prec, const double* b, double* x, int nrhs
     // the loop graph is captured after the first iteration has been issued
     // (every kernel attribute and tensor-map entry point is set up by then)
     cudaGraphExec_t exec;
-    AWG_TRY(pcg_graph_k<K>(h, prec, v, &exec));
+    AWG_TRY(pcg_graph_k<K>(h, prec, v, &exec, sl));
     AWG_CUDA(cudaGraphLaunch(exec, s));
     {
         ProfScope ps_(h, AWG_PROF_VECTOR, s);
@@ -1978,25 +1998,74 @@ awg_status pcg_async_k(Handle* h, int prec, const double* b, double* x, int nrhs
     return AWG_OK;
 }
 
+awg_status pcg_async_group(Handle* h, int prec, const double* b, double* x, int nrhs, int ld, double rtol,
+                           int* d_iters, double* d_relres, int* d_status, const Slot& sl) {
+    const int K = pick_k(nrhs);
+    if (K == 16) return pcg_async_k<16>(h, prec, b, x, nrhs, ld, rtol, d_iters, d_relres, d_status, sl);
+    if (K == 32) return pcg_async_k<32>(h, prec, b, x, nrhs, ld, rtol, d_iters, d_relres, d_status, sl);
+    return pcg_async_k<64>(h, prec, b, x, nrhs, ld, rtol, d_iters, d_relres, d_status, sl);
+}
+
+// the second slot: its workspace, streams (the priorities of the first) and events
+awg_status slot1_prepare(Handle* h) {
+    if (h->bws2.p) return AWG_OK;
+    int lo = 0, hi = 0;
+    AWG_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    AWG_CUDA(cudaStreamCreateWithPriority(&h->hp2, cudaStreamNonBlocking, hi));
+    AWG_CUDA(cudaStreamCreateWithPriority(&h->side2, cudaStreamNonBlocking, lo));
+    for (cudaEvent_t* e : {&h->ev2_fork, &h->ev2_mid, &h->ev2_join, &h->ev2_in, &h->ev2_out})
+        AWG_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    const size_t bytes = carve_block(h, nullptr, nullptr, nullptr);
+    AWG_TRY(dalloc(h, h->bws2, bytes));
+    AWG_CUDA(cudaMemset(h->bws2.p, 0, bytes));
+    return AWG_OK;
+}
+
+// status of two groups into *d_status: breakdown before maxit before ok
+__global__ void kb_status_merge(const double* ctl_a, const double* ctl_b, int* d_status) {
+    if (threadIdx.x != 0 || !d_status) return;
+    const int a = (int)ctl_a[3], b = (int)ctl_b[3];
+    *d_status = (a == AWG_ERR_BREAKDOWN || b == AWG_ERR_BREAKDOWN) ? AWG_ERR_BREAKDOWN : (a ? a : b);
+}
+
 awg_status block_pcg_async(Handle* h, int prec, const double* b, double* x, int nrhs, int ld, double rtol,
                            int* d_iters, double* d_relres, int* d_status, cudaStream_t s) {
-    if (nrhs < 1 || nrhs > BLK_KMAX) return AWG_ERR_INVALID_ARG;
+    if (nrhs < 1 || nrhs > 2 * BLK_KMAX) return AWG_ERR_INVALID_ARG;
     AWG_TRY(block_prepare(h));
-    const int K = pick_k(nrhs);
-    if (K == 16) return pcg_async_k<16>(h, prec, b, x, nrhs, ld, rtol, d_iters, d_relres, d_status, s);
-    if (K == 32) return pcg_async_k<32>(h, prec, b, x, nrhs, ld, rtol, d_iters, d_relres, d_status, s);
-    return pcg_async_k<64>(h, prec, b, x, nrhs, ld, rtol, d_iters, d_relres, d_status, s);
+    if (nrhs <= BLK_KMAX)
+        return pcg_async_group(h, prec, b, x, nrhs, ld, rtol, d_iters, d_relres, d_status, slot0(h));
+    // two groups side by side: columns [0, 64) on slot 0, the rest on slot 1
+    AWG_TRY(slot1_prepare(h));
+    const int ka = BLK_KMAX, kb = nrhs - BLK_KMAX;
+    AWG_CUDA(cudaEventRecord(h->ev2_in, s));
+    AWG_CUDA(cudaStreamWaitEvent(h->hp2, h->ev2_in, 0));
+    AWG_TRY(pcg_async_group(h, prec, b, x, ka, ld, rtol, d_iters, d_relres, nullptr, slot0(h)));
+    AWG_TRY(pcg_async_group(h, prec, b + (size_t)ka * ld, x + (size_t)ka * ld, kb, ld, rtol,
+                            d_iters ? d_iters + ka : nullptr, d_relres ? d_relres + ka : nullptr, nullptr, slot1(h)));
+    AWG_CUDA(cudaEventRecord(h->ev2_out, h->hp2));
+    AWG_CUDA(cudaStreamWaitEvent(s, h->ev2_out, 0));
+    BView<double> va, vb;
+    carve_block(h, (char*)h->bws.p, &va, nullptr);
+    carve_block(h, (char*)h->bws2.p, &vb, nullptr);
+    kb_status_merge<<<1, 32, 0, s>>>(va.ctl, vb.ctl, d_status);
+    AWG_LAUNCH();
+    extra_launches(h, 1);
+    return AWG_OK;
 }
 
 // kernels launched by graph loop bodies since the last call (reset)
 int64_t block_graph_launches(Handle* h) {
-    if (!h->bws.p) return 0;
-    BView<double> v;
-    carve_block(h, (char*)h->bws.p, &v, nullptr);
-    unsigned long long c = 0;
-    if (cudaMemcpy(&c, v.glaunch, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
-    cudaMemset(v.glaunch, 0, 8);
-    return (int64_t)c;
+    int64_t total = 0;
+    for (DevBuf* ws : {&h->bws, &h->bws2}) {
+        if (!ws->p) continue;
+        BView<double> v;
+        carve_block(h, (char*)ws->p, &v, nullptr);
+        unsigned long long c = 0;
+        if (cudaMemcpy(&c, v.glaunch, 8, cudaMemcpyDeviceToHost) != cudaSuccess) continue;
+        cudaMemset(v.glaunch, 0, 8);
+        total += (int64_t)c;
+    }
+    return total;
 }
 
 // W columns c0 .. c0 + k - 1: A_+ X = B by flexible block PCG (K = 64
@@ -2011,7 +2080,7 @@ awg_status wsolve_k(Handle* h, int wprec, const double* B, double* X, int k, dou
                     double* worst, cudaStream_t s) {
     BView<double> v;
     carve_block(h, (char*)h->bws.p, &v, nullptr);
-    BlockApply<double, K> bd{h, v};
+    BlockApply<double, K> bd{h, v, slot0(h)};
     const int n = h->n;
     const dim3 tg((n + 31) / 32, (K + 31) / 32), tb(32, 8);
     const unsigned gr = grid_rows(n, RM<double, K>::RPB);
@@ -2025,7 +2094,7 @@ awg_status wsolve_k(Handle* h, int wprec, const double* B, double* X, int k, dou
     AWG_CUDA(cudaMemcpyAsync(v.pr, v.pb, len * 8, cudaMemcpyDeviceToDevice, s));
     kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pb, v.pb, v.red, v.cnt, sc + B_BB * K);
     AWG_LAUNCH();
-    AWG_TRY(apply64_any(h, K, 3, wprec, v.pr, z, s));
+    AWG_TRY(apply64_any(h, K, 3, wprec, v.pr, z, s, slot0(h)));
     kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, z, v.red, v.cnt, sc + B_RZ * K);
     AWG_LAUNCH();
     AWG_CUDA(cudaMemcpyAsync(v.pp, z, len * 8, cudaMemcpyDeviceToDevice, s));
@@ -2062,7 +2131,7 @@ awg_status wsolve_k(Handle* h, int wprec, const double* B, double* X, int k, dou
         if (nact == 0 || it >= maxit) break;
         if (changed) AWG_CUDA(cudaMemcpyAsync(sc + B_ACT * K, act.data(), K * 8, cudaMemcpyHostToDevice, s));
         std::swap(z, zo);
-        AWG_TRY(apply64_any(h, K, 3, wprec, v.pr, z, s));  // z = H_2 r
+        AWG_TRY(apply64_any(h, K, 3, wprec, v.pr, z, s, slot0(h)));  // z = H_2 r
         kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, z, v.red, v.cnt, sc + B_RZN * K);
         AWG_LAUNCH();
         kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, zo, v.red, v.cnt, sc + B_TR * K);
@@ -2114,7 +2183,7 @@ awg_status block_apply(Handle* h, int which, int prec, const double* x, double* 
     const dim3 tg((n + 31) / 32, (K + 31) / 32), tb(32, 8);
     kb_from_cols<double><<<tg, tb, 0, s>>>(n, nrhs, ld, K, x, v.pb);
     AWG_LAUNCH();
-    AWG_TRY(apply64_any(h, K, which, prec, v.pb, v.pz, s));
+    AWG_TRY(apply64_any(h, K, which, prec, v.pb, v.pz, s, slot0(h)));
     kb_to_cols<double><<<tg, tb, 0, s>>>(n, nrhs, ld, K, v.pz, y);
     AWG_LAUNCH();
     return AWG_OK;

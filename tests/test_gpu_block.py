@@ -265,3 +265,26 @@ def test_pcg_async_single_rhs(pair, form):
     assert float(rel[0].item()) <= 1e-8
     X = x.cpu().numpy()
     assert np.linalg.norm(st.A @ X[0] - B[0]) <= 2e-8 * np.linalg.norm(B[0])
+
+
+def test_block_pcg_async_two_groups(pair):
+    """More than 64 columns: two column groups solve side by side on the
+    handle's two slots (own workspace, streams and loop graphs); every
+    column takes the host-driven solve's iterations and reaches 1e-8."""
+    p, sol, st = pair
+    from paper_2106_10913_gb300 import MIXED_FP16, awg_pcg_block
+    B = np.random.default_rng(61).standard_normal((77, p.n))
+    B[70] = 0.0
+    x, its, rel, status = _async_solve(sol, B, MIXED_FP16)
+    torch.cuda.synchronize()
+    xs = torch.zeros((77, p.n), dtype=torch.float64, device="cuda")
+    _, its_s, _ = awg_pcg_block(sol.h, torch.from_numpy(B).cuda(), xs, 1e-8, precision=MIXED_FP16)
+    assert int(status.item()) == 0
+    X = x.cpu().numpy()
+    assert int(its[70].item()) == 0 and np.all(X[70] == 0.0)
+    for c in range(77):
+        if c == 70:
+            continue
+        assert abs(int(its[c].item()) - its_s[c]) <= 1
+        assert float(rel[c].item()) <= 1e-8
+        assert np.linalg.norm(st.A @ X[c] - B[c]) <= 2e-8 * np.linalg.norm(B[c])
