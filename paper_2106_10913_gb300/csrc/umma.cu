@@ -452,12 +452,13 @@ __global__ void __launch_bounds__(256) k_local_bimg(const int* __restrict__ sub_
 // U_s(rt*128 + r, :) = sum over kc of G_s tile (rt, kc) times X_s chunk kc,
 // with G = G_hi + G_lo and X = X_hi + X_lo split in TF32 and the three
 // products hi*hi + hi*lo + lo*hi accumulated in float32 in tensor memory
+// (two MMAs per step: G_hi against the stacked [X_hi; X_lo], G_lo against X_hi)
 // (error about 2^-22 of each product, the float32 level).  One CTA per
 // 128-row tile (flattened list tile_sub / tile_rt); 6 warps: warp 0 issues
 // the bulk copies (one 16 KB G image and the two right-hand-side images per
 // stage), warp 1 the MMAs, warps 2-5 split the G images in shared memory
 // (hi in place, lo beside it) and read the accumulator back.
-constexpr int UL_STAGES = 4;
+constexpr int UL_STAGES = 2;  // 2 stages: two CTAs share an SM
 constexpr int UL_THREADS = 192;
 template <int K>
 struct UlCfg {
@@ -465,7 +466,7 @@ struct UlCfg {
     static constexpr int B_BYTES = 2 * K * 32 * 4;        // hi + lo right-hand-side images
     static constexpr int STAGE = 2 * A_BYTES + B_BYTES;   // G hi, G lo, B
     static constexpr int SMEM = UL_STAGES * STAGE + 1024;
-    static constexpr int TMEM_COLS = K < 32 ? 32 : K;
+    static constexpr int TMEM_COLS = 2 * K < 32 ? 32 : 2 * K;  // [hi*hi + lo*hi | hi*lo]
 };
 
 struct UlShared {
@@ -535,7 +536,10 @@ __global__ void __launch_bounds__(UL_THREADS) k_umma_local(const int* __restrict
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_tf32(128, K);
+            // columns [0, K): G_hi X_hi + G_lo X_hi; [K, 2K): G_hi X_lo (one
+            // MMA over the hi and lo right-hand-side images stacked as 2K rows)
+            constexpr uint32_t idesc2 = idesc_tf32(128, 2 * K);
+            constexpr uint32_t idesc1 = idesc_tf32(128, K);
             for (int kc = 0; kc < KC; kc++) {
                 const int st = kc % UL_STAGES;
                 if (!mbar_wait(&sh.ready[st], (kc / UL_STAGES) & 1, d_err, ERR_WAIT_FULL) ||
@@ -549,10 +553,9 @@ __global__ void __launch_bounds__(UL_THREADS) k_umma_local(const int* __restrict
 #pragma unroll
                 for (int kk = 0; kk < 4; kk++) {  // 8 TF32 values (32 bytes) per MMA
                     const uint64_t ah = sdesc(a + kk * 32, 16, 1024), alo = sdesc(al + kk * 32, 16, 1024);
-                    const uint64_t bh = sdesc(b + kk * 32, 16, 1024), blo = sdesc(b + K * 128 + kk * 32, 16, 1024);
-                    umma_tf32(taddr, ah, bh, idesc, (kc == 0 && kk == 0) ? 0u : 1u);
-                    umma_tf32(taddr, ah, blo, idesc, 1u);
-                    umma_tf32(taddr, alo, bh, idesc, 1u);
+                    const uint64_t bb = sdesc(b + kk * 32, 16, 1024);
+                    umma_tf32(taddr, ah, bb, idesc2, (kc == 0 && kk == 0) ? 0u : 1u);
+                    umma_tf32(taddr, alo, bb, idesc1, 1u);
                 }
                 umma_commit(&sh.empty[st]);
             }
@@ -593,8 +596,11 @@ __global__ void __launch_bounds__(UL_THREADS) k_umma_local(const int* __restrict
         const int row = rt * 128 + q * 32 + lane;
 #pragma unroll
         for (int c0 = 0; c0 < K; c0 += 16) {
-            float v[16];
+            float v[16], w[16];
             tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+            tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(K + c0), w);
+#pragma unroll
+            for (int u = 0; u < 16; u++) v[u] += w[u];
             if (row < m) {
                 float4* o = reinterpret_cast<float4*>(out + (size_t)(p0 + row) * K + c0);
 #pragma unroll
