@@ -161,7 +161,9 @@ struct UmCfg {
     static constexpr int A_BYTES = UM_BM * UM_BK * 2;            // 16 KB
     static constexpr int B_BYTES = 2 * K * UM_BK * 2;            // hi + lo parts
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int SMEM = UM_STAGES * STAGE + 1024;        // + alignment slack
+    // 4 stages up to 32 columns, 3 at 64 (2 x 97 KB: two CTAs per SM)
+    static constexpr int STAGES = K < 64 ? UM_STAGES : 3;
+    static constexpr int SMEM = STAGES * STAGE + 1024;           // + alignment slack
     static constexpr int TMEM_COLS = K < 32 ? 32 : K;
 };
 
@@ -209,8 +211,8 @@ __device__ __forceinline__ void um_mainloop(uint8_t* ring, UmShared& sh, int nk,
     if (warp == 0 && lane == 0) {
         int kb = 0;
         for (; kb < nk; kb++) {
-            const int st = kb % UM_STAGES;
-            if (kb >= UM_STAGES && !mbar_wait(&sh.empty[st], ((kb / UM_STAGES) - 1) & 1, d_err, ERR_WAIT_EMPTY)) {
+            const int st = kb % C::STAGES;
+            if (kb >= C::STAGES && !mbar_wait(&sh.empty[st], ((kb / C::STAGES) - 1) & 1, d_err, ERR_WAIT_EMPTY)) {
                 sh.fail = 1;
                 break;
             }
@@ -220,13 +222,13 @@ __device__ __forceinline__ void um_mainloop(uint8_t* ring, UmShared& sh, int nk,
             load(sp, &sh.full[st], kb);
         }
         // copies in flight: wait for the last load of every stage (bounded)
-        for (int j = (kb > UM_STAGES ? kb - UM_STAGES : 0); j < kb; j++)
-            mbar_wait(&sh.full[j % UM_STAGES], (j / UM_STAGES) & 1, d_err, ERR_WAIT_FULL);
+        for (int j = (kb > C::STAGES ? kb - C::STAGES : 0); j < kb; j++)
+            mbar_wait(&sh.full[j % C::STAGES], (j / C::STAGES) & 1, d_err, ERR_WAIT_FULL);
     } else if (warp == 1 && lane == 0) {
         bool ok = true;
         for (int kb = 0; kb < nk; kb++) {
-            const int st = kb % UM_STAGES;
-            if (!mbar_wait(&sh.full[st], (kb / UM_STAGES) & 1, d_err, ERR_WAIT_FULL) || *(volatile int*)&sh.fail) {
+            const int st = kb % C::STAGES;
+            if (!mbar_wait(&sh.full[st], (kb / C::STAGES) & 1, d_err, ERR_WAIT_FULL) || *(volatile int*)&sh.fail) {
                 sh.fail = 1;
                 ok = false;
                 break;
