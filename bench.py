@@ -391,6 +391,10 @@ def run_awg(args):
            "h2d_bytes_per_step": int(hb.numel() * 8), "d2h_bytes_per_step": int(hx.numel() * 8),
            "form": best_name}
 
+    from paper_2106_10913_gb300 import awg_get_info
+    tuned = awg_get_info(sol.h)
+    autotune = {"widths": [16, 32, 64], "wt_ctas_per_sm": tuned["block_wt_ctas"],
+                "dense_blocks_per_sm": tuned["block_dense_bps"]}
     batch = batched_problems(args, barrier) if args.batch_problems > 0 else None
 
     if rank == 0:
@@ -415,7 +419,8 @@ def run_awg(args):
                        "geneo": {"solver": args.geneo, "block_steps_max": info["geneo_its_max"],
                                  "block_steps_sum": info["geneo_its_sum"],
                                  "dense_subdomains": info["geneo_dense"], "training": train},
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "block_autotune": autotune},
             "forms": {k: {"value": v["value"], "ms_per_step": v["ms_per_step"], "nrhs": v["nrhs"],
                           "iters": v["iters"], "relres": v["relres"], "ok": v["ok"],
                           "kernel_ms": {c: round(t, 3) for c, t in v["prof"]["ms"].items()},

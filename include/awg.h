@@ -150,6 +150,10 @@ typedef struct {
                                eigensolver (all of them with geneo_solver 0)    */
     int wt_blocks[4];       /* per awg_precision form: blocks of the W^T r and  */
     int wd_blocks[4];       /* W d passes (autotuned; 0 if the form is unbuilt) */
+    int block_wt_ctas[3];   /* block path, widths 16 / 32 / 64: CTAs per SM of
+                               the tensor-core W^T B pass and blocks per SM of  */
+    int block_dense_bps[3]; /* the float64 coarse GEMM (autotuned on the first
+                               H_3 apply of that width; 0 before)              */
 } awg_info;
 
 /* Fill *opt with the defaults above. */

@@ -54,7 +54,8 @@ class awg_info(ctypes.Structure):
                 ("setup_ms", ctypes.c_double * 8), ("device_bytes", ctypes.c_size_t),
                 ("geneo_its_max", ctypes.c_int), ("geneo_its_sum", ctypes.c_int64),
                 ("geneo_dense", ctypes.c_int), ("wt_blocks", ctypes.c_int * 4),
-                ("wd_blocks", ctypes.c_int * 4)]
+                ("wd_blocks", ctypes.c_int * 4), ("block_wt_ctas", ctypes.c_int * 3),
+                ("block_dense_bps", ctypes.c_int * 3)]
 
 
 EXPORTED = ["awg_default_options", "awg_status_string", "awg_setup", "awg_destroy",
@@ -179,6 +180,8 @@ def awg_get_info(h) -> dict:
     d["setup_ms"] = list(info.setup_ms)
     d["wt_blocks"] = list(info.wt_blocks)
     d["wd_blocks"] = list(info.wd_blocks)
+    d["block_wt_ctas"] = list(info.block_wt_ctas)
+    d["block_dense_bps"] = list(info.block_dense_bps)
     return d
 
 

@@ -277,6 +277,10 @@ awg_status awg_get_info(awg_handle hh, awg_info* info) {
         info->wt_blocks[p] = h->prec[p].built ? h->prec[p].wt_blocks : 0;
         info->wd_blocks[p] = h->prec[p].built ? h->prec[p].wd_blocks : 0;
     }
+    for (int k = 0; k < 3; k++) {
+        info->block_wt_ctas[k] = h->bt_wt[k];
+        info->block_dense_bps[k] = h->bt_dense[k];
+    }
     return AWG_OK;
 }
 

@@ -153,6 +153,12 @@ struct Handle {
     // one group's float64 coarse GEMMs overlap the other's bandwidth-bound
     // passes
     DevBuf bws2;
+    // block-path tunables per width (16, 32, 64), set by the block
+    // autotuner on the first H_3 apply of that width: CTAs per SM of the
+    // tensor-core W^T B pass (split-K) and blocks per SM of the float64
+    // coarse GEMM (split-j); 0 = not tuned yet (defaults 2 and 4)
+    int bt_wt[3] = {0, 0, 0};
+    int bt_dense[3] = {0, 0, 0};
     cudaStream_t hp2 = nullptr, side2 = nullptr;
     cudaEvent_t ev2_fork = nullptr, ev2_mid = nullptr, ev2_join = nullptr, ev2_in = nullptr, ev2_out = nullptr;
     cudaGraph_t bg2_graph[12] = {};

@@ -1405,7 +1405,8 @@ struct BlockApply {
         if (dim == 0) return AWG_OK;
         ProfScope ps_(h, AWG_PROF_COARSE, s);
         const int tiles = (dim + DG_RB - 1) / DG_RB;
-        int S = std::max(1, std::min(DG_SMAX, (4 * 152 + tiles - 1) / tiles));
+        const int bps = h->bt_dense[kidx] > 0 ? h->bt_dense[kidx] : 4;  // (autotuned) blocks per SM
+        int S = std::max(1, std::min(DG_SMAX, (bps * 152 + tiles - 1) / tiles));
         int jlen = (dim + S - 1) / S;
         jlen = (jlen + DG_JC - 1) / DG_JC * DG_JC;
         S = (dim + jlen - 1) / jlen;
@@ -1566,10 +1567,13 @@ struct BlockApply {
 
     int ldb() const { return (h->n + 63) / 64 * 64; }
 
+    static constexpr int kidx = K == 16 ? 0 : (K == 32 ? 1 : 2);
+
     int wt_splits() const {
-        // about two CTAs per SM over the 128-column tiles of W
+        // (autotuned) CTAs per SM over the 128-column tiles of W; default 2
+        const int per_sm = h->bt_wt[kidx] > 0 ? h->bt_wt[kidx] : 2;
         const int tiles = (h->ldw + 127) / 128;
-        return umma_wt_splits(h->n, std::max(1, std::min(WT_SPLITS_MAX, (2 * 152 + tiles - 1) / tiles)));
+        return umma_wt_splits(h->n, std::max(1, std::min(WT_SPLITS_MAX, (per_sm * 152 + tiles - 1) / tiles)));
     }
 
     // out = W d (+ V), d float64 n_- x K
@@ -1694,7 +1698,16 @@ struct BlockApply {
 };
 
 template <int K>
+awg_status tune_k(Handle* h, int prec, const double* X, double* Y, cudaStream_t s, const Slot& sl);
+
+template <int K>
 awg_status apply64_k(Handle* h, int which, int prec, const double* X, double* Y, cudaStream_t s, const Slot& sl) {
+    constexpr int kidx = K == 16 ? 0 : (K == 32 ? 1 : 2);
+    if (which == 4 && h->opt.autotune && h->bt_wt[kidx] == 0 && h->n_minus > 0) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        AWG_CUDA(cudaStreamIsCapturing(s, &cs));
+        if (cs == cudaStreamCaptureStatusNone) AWG_TRY(tune_k<K>(h, prec, X, Y, s, sl));
+    }
     if (prec == AWG_FP64) {
         BlockApply<double, K> b{h, {}, sl};
         carve_block(h, sl.ws, &b.v, nullptr);
@@ -1710,6 +1723,57 @@ awg_status apply64_any(Handle* h, int K, int which, int prec, const double* X, d
     if (K == 16) return apply64_k<16>(h, which, prec, X, Y, s, sl);
     if (K == 32) return apply64_k<32>(h, which, prec, X, Y, s, sl);
     return apply64_k<64>(h, which, prec, X, Y, s, sl);
+}
+
+// Block autotuner: on the first H_3 apply of width K, time the apply (on
+// the caller's X, Y) for CTAs per SM of the W^T B pass in {1, 2, 4} and
+// blocks per SM of the float64 coarse GEMM in {2, 4, 8}, keep the fastest
+// pair (two timed applies each, after one warm-up).
+template <int K>
+awg_status tune_k(Handle* h, int prec, const double* X, double* Y, cudaStream_t s, const Slot& sl) {
+    constexpr int kidx = K == 16 ? 0 : (K == 32 ? 1 : 2);
+    const int prof = h->prof;
+    const int64_t l0 = h->launches;
+    h->prof = 0;
+    cudaEvent_t e0, e1;
+    AWG_CUDA(cudaEventCreate(&e0));
+    AWG_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bw = 2, bd = 4;
+    awg_status st = AWG_OK;
+    for (int w : {1, 2, 4}) {
+        for (int d : {2, 4, 8}) {
+            h->bt_wt[kidx] = w;
+            h->bt_dense[kidx] = d;
+            float ms = 0.f;
+            for (int rep = 0; rep < 3 && st == AWG_OK; rep++) {
+                if (rep == 1) cudaEventRecord(e0, s);
+                if (prec == AWG_FP64) {
+                    BlockApply<double, K> b{h, {}, sl};
+                    carve_block(h, sl.ws, &b.v, nullptr);
+                    st = b.apply64(4, prec, X, Y, s);
+                } else {
+                    BlockApply<float, K> b{h, {}, sl};
+                    carve_block(h, sl.ws, nullptr, &b.v);
+                    st = b.apply64(4, prec, X, Y, s);
+                }
+            }
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (st == AWG_OK && ms < best) { best = ms; bw = w; bd = d; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->bt_wt[kidx] = bw;
+    h->bt_dense[kidx] = bd;
+    h->prof = prof;
+    h->launches = l0;
+    if (h->opt.verbose)
+        fprintf(stderr, "libawg: block autotune K=%d: W^T B %d CTAs/SM, coarse GEMM %d blocks/SM (%.3f ms/apply)\n",
+                K, bw, bd, best / 2);
+    return st;
 }
 
 int pick_k(int nrhs) { return nrhs <= 16 ? 16 : (nrhs <= 32 ? 32 : 64); }

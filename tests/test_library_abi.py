@@ -64,6 +64,12 @@ def test_host_only_calls(lib):
     assert lib.awg_learned_data(None, None, None, None) == 1
     assert ctypes.sizeof(pkg.awg.awg_options) == 88
     assert o.w16_keep == 0.1
+    assert pkg.default_options().block_tensor_cores == 1
+    # the block and graph-driven entry points reject bad arguments before
+    # touching the device
+    assert lib.awg_apply_block(None, 4, 0, None, None, 1, 1, None) == 1
+    assert lib.awg_pcg_block(None, 0, None, None, 1, 1, 1e-8, None, None, None) == 1
+    assert lib.awg_pcg_block_async(None, 0, None, None, 1, 1, 1e-8, None, None, None, None) == 1
 
 
 def test_product_does_not_import_oracle():
