@@ -312,6 +312,11 @@ awg_status eig_select_batched(Handle* h, double* arena, const int* d_m, const in
                               std::vector<int64_t>& h_vec_off, DevBuf& vals,
                               std::vector<int>& h_val_ptr, cudaStream_t s);
 
+// coarse.cu : blocked float64 Cholesky (lower factor in place; the strict
+// upper blocks keep their input) and inverse of its triangular factor
+awg_status chol_blocked(Handle* h, double* A, int dim, int* d_flag, cudaStream_t s);
+awg_status trtri_blocked(Handle* h, const double* L, double* Li, int dim, cudaStream_t s);
+
 // apply.cu
 awg_status apply_stage(Handle* h, int which, int prec, const double* x, double* y, cudaStream_t s);
 // times the apply of every built form over a few grid sizes of the two W

@@ -347,26 +347,27 @@ static awg_status check_flag(Handle* h, int mask, awg_status err) {
 }
 
 // Cholesky + explicit inverse of one dense SPD matrix M (dim x dim) into Minv.
+static awg_status atb_sym(Handle* h, int n, int m, const double* A, const double* B, double* C, cudaStream_t s);
+
+// Minv = M^-1 for an SPD coarse matrix (E or F): blocked Cholesky M = L L^T
+// over the whole GPU, L^-1 by block rows, then M^-1 = L^-T L^-1 by the
+// symmetric A^T B kernel (float64 throughout).
 static awg_status spd_inverse(Handle* h, DevBuf& M, DevBuf& Minv, int dim) {
     cudaStream_t s = h->stream;
     if (dim == 0) return AWG_OK;
-    DevBuf L, dm, doff;
+    DevBuf L, Li;
     AWG_TRY(dalloc(h, L, (size_t)dim * dim * 8));
+    AWG_TRY(dalloc(h, Li, (size_t)dim * dim * 8));
     AWG_CUDA(cudaMemcpyAsync(L.p, M.p, (size_t)dim * dim * 8, cudaMemcpyDeviceToDevice, s));
-    int64_t zero = 0;
-    AWG_TRY(upload(h, dm, &dim, sizeof(int)));
-    AWG_TRY(upload(h, doff, &zero, sizeof(int64_t)));
     AWG_CUDA(cudaMemsetAsync(h->flag.p, 0, sizeof(int), s));
-    AWG_TRY(potrf_batched(h, (double*)L.p, (int*)dm.p, (int64_t*)doff.p, 1, dim, (int*)h->flag.p, s));
+    AWG_TRY(chol_blocked(h, (double*)L.p, dim, (int*)h->flag.p, s));
     AWG_TRY(check_flag(h, FLAG_NOT_SPD, AWG_ERR_NOT_SPD));
-    AWG_TRY(trtri_batched(h, (double*)L.p, (int*)dm.p, (int64_t*)doff.p, 1, dim, s));
+    AWG_TRY(trtri_blocked(h, (double*)L.p, (double*)Li.p, dim, s));
     if (!Minv.p) AWG_TRY(dalloc(h, Minv, (size_t)dim * dim * 8));
-    AWG_TRY(gemm_batched(h, {{(double*)L.p, (double*)L.p, (double*)Minv.p, dim, dim, dim, dim, dim,
-                              dim, 1, 0, 1.0, 0.0}}, s));
+    AWG_TRY(atb_sym(h, dim, dim, (double*)Li.p, (double*)Li.p, (double*)Minv.p, s));
     AWG_CUDA(cudaStreamSynchronize(s));
     dfree(h, L);
-    dfree(h, dm);
-    dfree(h, doff);
+    dfree(h, Li);
     return AWG_OK;
 }
 
@@ -484,6 +485,87 @@ static awg_status build_W(Handle* h) {
     return AWG_OK;
 }
 
+// C = A^T B for A, B n x m column-major (ld n), C m x m symmetric: the
+// float64 contraction of F = W^T (A W) (Def. 10).  Only the tiles on and
+// above the diagonal are formed (64 x 64 per block, each thread 4 x 4, the
+// reduction over n in 16-row chunks staged in shared memory, split over
+// blockIdx.y into part[sp]); k_atb_sum adds the splits in order and mirrors
+// the upper triangle, so C is exactly symmetric.
+constexpr int AT_T = 64, AT_KC = 16;
+__global__ void __launch_bounds__(256) k_atb_part(int n, int m, int klen, const double* __restrict__ A,
+                                                  const double* __restrict__ B, double* __restrict__ part) {
+    __shared__ double as[AT_KC][AT_T + 1];
+    __shared__ double bs[AT_KC][AT_T + 1];
+    __shared__ int tij[2];
+    const int nt = (m + AT_T - 1) / AT_T;
+    if (threadIdx.x == 0) {  // blockIdx.x -> (ti, tj), ti <= tj, row by row
+        int t = blockIdx.x, ti = 0;
+        while (t >= nt - ti) { t -= nt - ti; ti++; }
+        tij[0] = ti;
+        tij[1] = ti + t;
+    }
+    __syncthreads();
+    const int i0 = tij[0] * AT_T, j0 = tij[1] * AT_T;
+    const int k0s = blockIdx.y * klen, k1s = min(n, k0s + klen);
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4] = {};
+    for (int k0 = k0s; k0 < k1s; k0 += AT_KC) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < AT_KC * AT_T; e += 256) {
+            const int c = e / AT_KC, kk = e % AT_KC, k = k0 + kk;
+            const bool kin = k < k1s;
+            as[kk][c] = (kin && i0 + c < m) ? A[(size_t)(i0 + c) * n + k] : 0.0;
+            bs[kk][c] = (kin && j0 + c < m) ? B[(size_t)(j0 + c) * n + k] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < AT_KC; kk++) {
+            double a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) { a[u] = as[kk][ty * 4 + u]; b[u] = bs[kk][tx * 4 + u]; }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+#pragma unroll
+                for (int v = 0; v < 4; v++) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        }
+    }
+    double* P = part + (size_t)blockIdx.y * m * m;
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+            const int i = i0 + ty * 4 + u, j = j0 + tx * 4 + v;
+            if (i < m && j < m) P[(size_t)j * m + i] = acc[u][v];
+        }
+}
+
+__global__ void k_atb_sum(int m, int S, const double* __restrict__ part, double* __restrict__ C) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)m * m) return;
+    const int i = (int)(e % m), j = (int)(e / m);
+    const size_t src = (i <= j) ? e : (size_t)i * m + j;  // (j, i) above the diagonal
+    double v = 0.0;
+    for (int sp = 0; sp < S; sp++) v += part[(size_t)sp * m * m + src];
+    C[e] = v;
+}
+
+static awg_status atb_sym(Handle* h, int n, int m, const double* A, const double* B, double* C, cudaStream_t s) {
+    if (m == 0) return AWG_OK;
+    const int nt = (m + AT_T - 1) / AT_T;
+    const int tiles = nt * (nt + 1) / 2;
+    const int S = std::max(1, std::min(16, (8 * 152 + tiles - 1) / tiles));
+    const int klen = ((n + S - 1) / S + AT_KC - 1) / AT_KC * AT_KC;
+    double* part = nullptr;
+    AWG_CUDA(cudaMallocAsync(&part, (size_t)S * m * m * 8, s));
+    k_atb_part<<<dim3(tiles, S), 256, 0, s>>>(n, m, klen, A, B, part);
+    AWG_LAUNCH();
+    const size_t len = (size_t)m * m;
+    k_atb_sum<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(m, S, part, C);
+    AWG_LAUNCH();
+    AWG_CUDA(cudaFreeAsync(part, s));
+    return AWG_OK;
+}
+
 // F = Wt^T A Wt for a column-major (rounded) W, its inverse into Finv
 static awg_status build_F(Handle* h, const double* Wt, DevBuf& Finv, DevBuf* keepF) {
     cudaStream_t s = h->stream;
@@ -493,19 +575,15 @@ static awg_status build_F(Handle* h, const double* Wt, DevBuf& Finv, DevBuf* kee
     AWG_TRY(blk_spmm(h, Wt, AW, nm, s));
     DevBuf F;
     AWG_TRY(dalloc(h, F, (size_t)nm * nm * 8));
-    AWG_TRY(gemm_batched(h, {{Wt, AW, (double*)F.p, nm, nm, n, n, n, nm, 1, 0, 1.0, 0.0}}, s));
+    const double t0 = now_ms();
+    AWG_TRY(atb_sym(h, n, nm, Wt, AW, (double*)F.p, s));  // F = W^T (A W), exactly symmetric
     AWG_CUDA(cudaFreeAsync(AW, s));
-    int one = 1;
-    int64_t zero = 0;
-    DevBuf dm, doff;
-    AWG_TRY(upload(h, dm, &nm, sizeof(int)));
-    AWG_TRY(upload(h, doff, &zero, sizeof(int64_t)));
-    k_symmetrize<<<dim3(1, 64), 256, 0, s>>>((int*)dm.p, (int64_t*)doff.p, (double*)F.p);
-    AWG_LAUNCH();
-    (void)one;
+    AWG_CUDA(cudaStreamSynchronize(s));
+    const double t1 = now_ms();
     AWG_TRY(spd_inverse(h, F, Finv, nm));
-    dfree(h, dm);
-    dfree(h, doff);
+    if (h->opt.verbose)
+        fprintf(stderr, "libawg: F (%d x %d): W^T A W %.1f ms, Cholesky inverse %.1f ms\n", nm, nm, t1 - t0,
+                now_ms() - t1);
     if (keepF) { dfree(h, *keepF); *keepF = F; } else dfree(h, F);
     return AWG_OK;
 }
@@ -859,7 +937,12 @@ awg_status build_setup_numeric(Handle* h) {
         AWG_LAUNCH();
         dfree(h, dm);
         dfree(h, doff);
+        AWG_CUDA(cudaStreamSynchronize(s));
+        const double te = now_ms();
         AWG_TRY(spd_inverse(h, h->E, h->Einv, n0));
+        if (h->opt.verbose)
+            fprintf(stderr, "libawg: E (%d x %d): Z^T A_+ Z %.1f ms, Cholesky inverse %.1f ms\n", n0, n0,
+                    te - t3, now_ms() - te);
     }
     // workspace of the single-RHS apply
     h->red_blocks = std::min(1216, std::max(1, (n + 127) / 128));
