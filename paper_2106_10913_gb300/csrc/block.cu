@@ -379,10 +379,10 @@ __global__ void __launch_bounds__(256) kb_aplus(int n, const int* __restrict__ r
 // (B_s n^s x nc_s column-major; block-sparse Z^T X and V_-^T X).  Block
 // (s, qc, ps) takes the columns q of chunk qc (16 per chunk) and the local
 // positions of split ps, in chunks of 64 staged in shared memory (B_s rows
-// coalesced along p, X rows gathered whole); each thread owns K / 16
-// outputs (q, c).  Partial sums go to part[ps][colptr[s] + q][c];
+// coalesced along p, X rows gathered whole with 16-byte loads); each thread
+// owns K / 16 outputs (q, c).  Partial sums go to part[ps][colptr[s] + q][c];
 // kb_tg_sum adds the TG_PS splits in order.
-constexpr int KB_TG_C = 16, TG_PC = 64, TG_PS = 4;
+constexpr int KB_TG_C = 16, TG_PC = 64, TG_PS = 8;
 template <typename T, int K>
 __global__ void __launch_bounds__(256) kb_tgemv(const int* __restrict__ sub_ptr, const int* __restrict__ sub_idx,
                                                 const int* __restrict__ colptr, const int64_t* __restrict__ boff,
@@ -409,9 +409,13 @@ __global__ void __launch_bounds__(256) kb_tgemv(const int* __restrict__ sub_ptr,
             const int q = e / TG_PC, pp = e % TG_PC;
             bs[pp][q] = (q < kc && pp < pn) ? Bs[(size_t)q * m + q0 + pp] : (T)0;
         }
-        for (int e = threadIdx.x; e < TG_PC * K; e += 256) {
-            const int pp = e / K;
-            (&xs[0][0])[e] = (pp < pn) ? X[(size_t)sub_idx[p0 + q0 + pp] * K + (e % K)] : (T)0;
+        // whole rows of X, 16 bytes per load
+        constexpr int V4 = K * (int)sizeof(T) / 16;
+        for (int e = threadIdx.x; e < TG_PC * V4; e += 256) {
+            const int pp = e / V4, cc = e % V4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (pp < pn) v = reinterpret_cast<const float4*>(X + (size_t)sub_idx[p0 + q0 + pp] * K)[cc];
+            reinterpret_cast<float4*>(&xs[pp][0])[cc] = v;
         }
         __syncthreads();
 #pragma unroll
