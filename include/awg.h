@@ -298,10 +298,11 @@ awg_status awg_profile_trace(awg_handle h, int cap, int* h_class, double* h_t0, 
  * coarse solves E^-1, F^-1 and all PCG recurrences in float64.
  *   d_x, d_y / d_b, d_x   device float64, nrhs columns of length n with
  *                         leading dimension ld >= n (column-major)
- * awg_apply_block: which = 0 (A), 1 (A_+), 2 (H^NN), 3 (H_2), 4 (H_3,ad);
- * 1 <= nrhs <= 64; asynchronous on `stream` (allocates its workspace on the
- * handle's first block call).
- * awg_pcg_block: H_3,ad (the handle's variant must be AWG_H3_AD), any
+ * awg_apply_block: which = 0 (A), 1 (A_+), 2 (H^NN), 3 (H_2), 4 (H_3,ad),
+ * 5 (H_3,hyb), 6 (H_3,inex: AWG_ERR_STATE unless its matrix was built, as
+ * for awg_apply_stage); 1 <= nrhs <= 64; asynchronous on `stream`
+ * (allocates its workspace on the handle's first block call).
+ * awg_pcg_block: the handle's variant (H_3,ad, H_3,hyb or H_3,inex), any
  * nrhs >= 1 (groups of up to 64 columns), x_0 = 0; synchronises `stream`;
  * h_iters / h_relres as awg_pcg.  Errors: AWG_ERR_INVALID_ARG,
  * AWG_ERR_STATE, AWG_ERR_MAXIT, AWG_ERR_BREAKDOWN, AWG_ERR_OOM,
@@ -313,7 +314,8 @@ awg_status awg_pcg_block(awg_handle h, int precision, const double* d_b, double*
                          double rtol, int* h_iters, double* h_relres, void* stream);
 
 /*
- * Asynchronous block PCG (H_3,ad, 1 <= nrhs <= 128 columns, x_0 = 0): the
+ * Asynchronous block PCG (the handle's variant, 1 <= nrhs <= 128 columns,
+ * x_0 = 0): the
  * iterations run as one CUDA graph launch, a conditional while node whose
  * body is one iteration captured from the handle's two streams, with the
  * stopping test (per column, recurrence residual <= rtol ||b||, Section 1)

@@ -214,7 +214,7 @@ def awg_pcg(h, b, x, rtol: float = 1e-8, precision: int = FP64, stream=None, che
 
 def awg_apply_block(h, which, x, y, precision: int = FP64, stream=None):
     """y = stage(x) for the rows of x (nrhs x n, one right-hand side per row,
-    nrhs <= 64) at once; `which` as awg_apply_stage, stages 0-4."""
+    nrhs <= 64) at once; `which` as awg_apply_stage, stages 0-6."""
     w = STAGE[which] if isinstance(which, str) else int(which)
     _check(load_library().awg_apply_block(h, w, precision, x.data_ptr(), y.data_ptr(), x.shape[0],
                                           x.shape[-1], _stream_ptr(stream)), "awg_apply_block")

@@ -341,11 +341,12 @@ awg_status awg_pcg(awg_handle hh, int precision, const double* d_b, double* d_x,
 awg_status awg_apply_block(awg_handle hh, int which, int precision, const double* d_x, double* d_y, int nrhs,
                            int ld, void* stream) {
     Handle* h = reinterpret_cast<Handle*>(hh);
-    if (!h || !d_x || !d_y || which < 0 || which > 4 || nrhs < 1 || nrhs > 64 || ld < h->n || precision < 0 ||
+    if (!h || !d_x || !d_y || which < 0 || which > 6 || nrhs < 1 || nrhs > 64 || ld < h->n || precision < 0 ||
         precision >= AWG_NPREC)
         return AWG_ERR_INVALID_ARG;
     // the mixed block forms apply the float32 local pseudo-inverses
     if (!h->prec[precision].built || (precision != AWG_FP64 && !h->prec[AWG_MIXED_FP32].G.p)) return AWG_ERR_STATE;
+    if (which == 6 && h->n_minus > 0 && !h->prec[precision].inexInv.p) return AWG_ERR_STATE;
     cudaStream_t us = (cudaStream_t)stream;
     AWG_CUDA(cudaEventRecord(h->ev_in, us));
     AWG_CUDA(cudaStreamWaitEvent(h->hp, h->ev_in, 0));
@@ -362,7 +363,6 @@ awg_status awg_pcg_block(awg_handle hh, int precision, const double* d_b, double
         return AWG_ERR_INVALID_ARG;
     // the mixed block forms apply the float32 local pseudo-inverses
     if (!h->prec[precision].built || (precision != AWG_FP64 && !h->prec[AWG_MIXED_FP32].G.p)) return AWG_ERR_STATE;
-    if (h->opt.variant != AWG_H3_AD) return AWG_ERR_STATE;
     if (nrhs == 0) return AWG_OK;
     cudaStream_t us = (cudaStream_t)stream;
     AWG_CUDA(cudaEventRecord(h->ev_in, us));
@@ -381,7 +381,6 @@ awg_status awg_pcg_block_async(awg_handle hh, int precision, const double* d_b, 
         precision >= AWG_NPREC)
         return AWG_ERR_INVALID_ARG;
     if (!h->prec[precision].built || (precision != AWG_FP64 && !h->prec[AWG_MIXED_FP32].G.p)) return AWG_ERR_STATE;
-    if (h->opt.variant != AWG_H3_AD) return AWG_ERR_STATE;
     cudaStream_t us = (cudaStream_t)stream;
     AWG_CUDA(cudaEventRecord(h->ev_in, us));
     AWG_CUDA(cudaStreamWaitEvent(h->hp, h->ev_in, 0));

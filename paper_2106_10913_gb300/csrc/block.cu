@@ -313,6 +313,12 @@ __global__ void kb_to_cols(int n, int nrhs, int ld, int K, const TS* __restrict_
 }
 
 template <typename T>
+__global__ void kb_sub(size_t len, const T* __restrict__ a, const T* __restrict__ b, T* c) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < len) c[e] = a[e] - b[e];
+}
+
+template <typename T>
 __global__ void kb_add(size_t len, const T* __restrict__ a, T* y) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e < len) y[e] += a[e];
@@ -1662,22 +1668,42 @@ struct BlockApply {
             case 1: return aplus(X, Y, nullptr, (T)1, s);
             case 2: return hnn(prec, X, Y, s);
             case 3: return h2(prec, X, Y, s);
-            case 4: {  // H_3,ad = H_2 + W F^-1 W^T (Def. 10); the W branch on the side stream
+            case 4:    // H_3,ad = H_2 + W F^-1 W^T (Def. 10)
+            case 6: {  // H_3,inex = H_2 + W (C^-1 - Vhat^T W)^-1 W^T (Thm. 7)
                 if (h->n_minus == 0) return h2(prec, X, Y, s);
+                const double* coarse = (double*)(which == 4 ? h->prec[prec].Finv.p : h->prec[prec].inexInv.p);
                 AWG_CUDA(cudaEventRecord(sl.fork, s));
                 AWG_CUDA(cudaStreamWaitEvent(sl.side, sl.fork, 0));
                 // side stream: W^T X (HBM) beside the first E^-1 (FP64 pipes),
-                // then F^-1 (FP64) after it, beside the local solves (FP32),
-                // and W d beside the second E^-1
+                // then the second coarse solve (FP64) after it, beside the
+                // local solves (FP32), and W d beside the second E^-1
                 AWG_TRY(wt(prec, X, v.w0, sl.side));
                 AWG_TRY(h2a(X, s));
                 AWG_CUDA(cudaEventRecord(sl.mid, s));
                 AWG_CUDA(cudaStreamWaitEvent(sl.side, sl.mid, 0));
-                AWG_TRY(dense(h->n_minus, (double*)h->prec[prec].Finv.p, v.w0, v.dd, 1.0, nullptr, 0.0, v.dps,
-                               sl.side));
+                AWG_TRY(dense(h->n_minus, coarse, v.w0, v.dd, 1.0, nullptr, 0.0, v.dps, sl.side));
                 AWG_TRY(wd(prec, v.dd, v.tmpw, nullptr, sl.side));
                 AWG_CUDA(cudaEventRecord(sl.join, sl.side));
                 return h2b(prec, X, Y, s, v.tmpw, sl.join);
+            }
+            case 5: {  // H_3,hyb = Pi_3 H_2 Pi_3^T + W F^-1 W^T (Def. 10), in order on s
+                if (h->n_minus == 0) return h2(prec, X, Y, s);
+                const double* Finv = (double*)h->prec[prec].Finv.p;
+                const size_t len = (size_t)h->n * K;
+                AWG_TRY(wt(prec, X, v.w0, s));
+                AWG_TRY(dense(h->n_minus, Finv, v.w0, v.dd, 1.0, nullptr, 0.0, v.dpm, s));  // d = F^-1 W^T X
+                AWG_TRY(wd(prec, v.dd, v.tmpw, nullptr, s));                                   // W d
+                AWG_TRY(stage(0, prec, v.tmpw, v.q, s));                                       // A W d
+                {
+                    ProfScope ps_(h, AWG_PROF_VECTOR, s);
+                    kb_sub<T><<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, X, v.q, v.tmpw);  // Pi_3^T X
+                    AWG_LAUNCH();
+                }
+                AWG_TRY(h2(prec, v.tmpw, Y, s));                                                // y = H_2 Pi_3^T X
+                AWG_TRY(stage(0, prec, Y, v.q, s));                                             // A y
+                AWG_TRY(wt(prec, v.q, v.w0, s));
+                AWG_TRY(dense(h->n_minus, Finv, v.w0, v.w1, -1.0, v.dd, 1.0, v.dpm, s));      // d - F^-1 W^T A y
+                return wd(prec, v.w1, Y, Y, s);                                                 // Y = y + W w1
             }
             default: return AWG_ERR_INVALID_ARG;
         }
@@ -1707,7 +1733,7 @@ awg_status tune_k(Handle* h, int prec, const double* X, double* Y, cudaStream_t 
 template <int K>
 awg_status apply64_k(Handle* h, int which, int prec, const double* X, double* Y, cudaStream_t s, const Slot& sl) {
     constexpr int kidx = K == 16 ? 0 : (K == 32 ? 1 : 2);
-    if (which == 4 && h->opt.autotune && h->bt_wt[kidx] == 0 && h->n_minus > 0) {
+    if (which >= 4 && h->opt.autotune && h->bt_wt[kidx] == 0 && h->n_minus > 0) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         AWG_CUDA(cudaStreamIsCapturing(s, &cs));
         if (cs == cudaStreamCaptureStatusNone) AWG_TRY(tune_k<K>(h, prec, X, Y, s, sl));
@@ -1755,11 +1781,11 @@ awg_status tune_k(Handle* h, int prec, const double* X, double* Y, cudaStream_t 
                 if (prec == AWG_FP64) {
                     BlockApply<double, K> b{h, {}, sl};
                     carve_block(h, sl.ws, &b.v, nullptr);
-                    st = b.apply64(4, prec, X, Y, s);
+                    st = b.apply64(4 + h->opt.variant, prec, X, Y, s);
                 } else {
                     BlockApply<float, K> b{h, {}, sl};
                     carve_block(h, sl.ws, nullptr, &b.v);
-                    st = b.apply64(4, prec, X, Y, s);
+                    st = b.apply64(4 + h->opt.variant, prec, X, Y, s);
                 }
             }
             cudaEventRecord(e1, s);
@@ -1802,7 +1828,7 @@ awg_status pcg_k(Handle* h, int prec, const double* b, double* x, int nrhs, int 
     AWG_CUDA(cudaMemsetAsync(v.px, 0, len * 8, s));
     AWG_CUDA(cudaMemcpyAsync(v.pr, v.pb, len * 8, cudaMemcpyDeviceToDevice, s));
     AWG_TRY(prof_vec([&] { kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pb, v.pb, v.red, v.cnt, sc + B_BB * K); }));
-    AWG_TRY(apply64_any(h, K, 4, prec, v.pr, v.pz, s, slot0(h)));
+    AWG_TRY(apply64_any(h, K, 4 + h->opt.variant, prec, v.pr, v.pz, s, slot0(h)));
     AWG_TRY(prof_vec([&] { kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, sc + B_RZ * K); }));
     AWG_CUDA(cudaMemcpyAsync(v.pp, v.pz, len * 8, cudaMemcpyDeviceToDevice, s));
     std::vector<double> hs(B_NSC * K);
@@ -1869,7 +1895,7 @@ awg_status pcg_k(Handle* h, int prec, const double* b, double* x, int nrhs, int 
         }
         if (nact == 0) break;
         if (changed) AWG_TRY(upload_act());
-        AWG_TRY(apply64_any(h, K, 4, prec, v.pr, v.pz, s, slot0(h)));
+        AWG_TRY(apply64_any(h, K, 4 + h->opt.variant, prec, v.pr, v.pz, s, slot0(h)));
         AWG_TRY(prof_vec([&] { kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, sc + B_RZN * K); }));
         AWG_TRY(prof_vec([&] { kb_pcg_p<K><<<gr, 256, 0, s>>>(n, sc, v.pz, v.pp, v.cnt); }));
     }
@@ -1906,7 +1932,7 @@ awg_status pcg_body_k(Handle* h, int prec, const BView<double>& v, cudaStream_t 
                       int set, int add, const Slot& sl) {
     const int n = h->n;
     const unsigned gr = grid_rows(n, RM<double, K>::RPB);
-    AWG_TRY(apply64_any(h, K, 4, prec, v.pr, v.pz, s, sl));
+    AWG_TRY(apply64_any(h, K, 4 + h->opt.variant, prec, v.pr, v.pz, s, sl));
     {
         ProfScope ps_(h, AWG_PROF_VECTOR, s);
         kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, v.sc + B_RZN * K);
@@ -2027,7 +2053,7 @@ awg_status pcg_async_k(Handle* h, int prec, const double* b, double* x, int nrhs
         AWG_LAUNCH();
     }
     // first iteration with z = H r, p = z (then the loop's iterations)
-    AWG_TRY(apply64_any(h, K, 4, prec, v.pr, v.pz, s, sl));
+    AWG_TRY(apply64_any(h, K, 4 + h->opt.variant, prec, v.pr, v.pz, s, sl));
     {
         ProfScope ps_(h, AWG_PROF_VECTOR, s);
         kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, v.sc + B_RZ * K);

@@ -1,7 +1,8 @@
 """Multi-right-hand-side (block) path against the CPU oracle, column by column
 (through the C ABI: awg_apply_block, awg_pcg_block).
 
-* every stage of the block apply (A, A_+, H^NN, H_2, H_3,ad) for 3, 20 and
+* every stage of the block apply (A, A_+, H^NN, H_2 and the three H_3
+  variants: H_3,ad, H_3,hyb of Def. 10, H_3,inex of Thm. 7) for 3, 20 and
   40 columns (the 16-, 32- and 64-wide kernels; padding columns included)
   matches the oracle's single-vector operator on each column to the FP64
   apply tolerance (1e-11, or kappa_loc * eps on ill-conditioned local
@@ -11,7 +12,7 @@
   tolerances of the single-RHS forms, and the tensor-core W passes agree
   with the CUDA-core ones;
 * block PCG: per column, true relative residual <= 1e-8 and iteration count
-  within 5 % of the oracle's PCG on the same column.
+  within 5 % of the oracle's PCG on the same column, for every variant.
 """
 
 import numpy as np
@@ -62,6 +63,8 @@ def _ref_op(st, stage):
         "hnn": lambda v: O.H_NN_apply(st, v),
         "h2": lambda v: O.H2_apply(st, v),
         "h3ad": lambda v: O.H3_ad_apply(st, v),
+        "h3hyb": lambda v: O.H3_hyb_apply(st, v),
+        "h3inex": lambda v: O.H3_inex_apply(st, v),
     }[stage]
 
 
@@ -75,7 +78,7 @@ def _block_apply(sol, stage, X, prec):
 
 
 @pytest.mark.parametrize("nrhs", [3, 20, 40])
-@pytest.mark.parametrize("stage", ["spmv", "aplus", "hnn", "h2", "h3ad"])
+@pytest.mark.parametrize("stage", ["spmv", "aplus", "hnn", "h2", "h3ad", "h3hyb", "h3inex"])
 def test_block_stage_parity_fp64(pair, stage, nrhs):
     p, sol, st = pair
     from paper_2106_10913_gb300 import FP64
@@ -85,6 +88,77 @@ def test_block_stage_parity_fp64(pair, stage, nrhs):
     tol = max(APPLY_RTOL, O.local_condition(st) * np.finfo(float).eps)
     errs = [_rel(Y[c], op(X[c])) for c in range(nrhs)]
     assert max(errs) <= tol, f"worst column error {max(errs):.3e}"
+
+
+# float16 W in H_3,hyb / H_3,inex: every W pass and the coarse matrices built
+# from the stored W carry its rounding (u16 = 2^-11); with every entry of W
+# rounded uniformly at random in the oracle, the applies of these workloads
+# move by at most 6.3 u16 (H_3,inex on random_spd60; H_3,ad at most 2.8 u16)
+VARIANT_FP16_RTOL = 8 * 2.0 ** -11
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp16"])
+@pytest.mark.parametrize("stage", ["h3hyb", "h3inex"])
+def test_block_mixed_apply_variants(pair, stage, form):
+    """H_3,hyb and H_3,inex in the mixed block forms (float32 vectors, W in
+    float32 / float16 on the tensor cores)."""
+    p, sol, st = pair
+    from paper_2106_10913_gb300 import MIXED_FP16, MIXED_FP32
+    prec = {"fp32": MIXED_FP32, "fp16": MIXED_FP16}[form]
+    X = np.random.default_rng(17).standard_normal((40, p.n))
+    Y = _block_apply(sol, stage, X, prec)
+    op = _ref_op(st, stage)
+    errs = [_rel(Y[c], op(X[c])) for c in range(X.shape[0])]
+    assert max(errs) <= (MIXED_RTOL if form == "fp32" else VARIANT_FP16_RTOL), f"worst column error {max(errs):.3e}"
+
+
+_VARIANT_SOLVERS = {}
+
+
+def _variant_solver(name, variant):
+    key = (name, variant)
+    if key not in _VARIANT_SOLVERS:
+        from paper_2106_10913_gb300 import AWGSolver
+        p, _, st = _pair(name)
+        _VARIANT_SOLVERS[key] = AWGSolver(p.rowptr, p.colidx, p.val, p.part, p.nparts, p.overlap, p.tau,
+                                          precisions=0b1011, variant=variant)
+    return _VARIANT_SOLVERS[key]
+
+
+@pytest.mark.parametrize("variant", ["hyb", "inex"])
+@pytest.mark.parametrize("name", ["channels64", "config1"])
+def test_block_pcg_variants(name, variant):
+    """awg_pcg_block (and the graph-driven awg_pcg_block_async) with the
+    handle's variant H_3,hyb / H_3,inex: per column the oracle's PCG
+    iterations with the same preconditioner (within 5 %, float64) and true
+    relative residuals <= 1e-8 (float64, and float16 W for H_3,hyb /
+    float32 W for H_3,inex, whose Woodbury inner matrix C^-1 - Vhat^T W is
+    ill-conditioned where A is, and so amplifies the storage error of W)."""
+    from paper_2106_10913_gb300 import FP64, MIXED_FP16, MIXED_FP32, awg_pcg_block
+    p, _, st = _pair(name)
+    sol = _variant_solver(name, {"hyb": 1, "inex": 2}[variant])
+    M = {"hyb": lambda r: O.H3_hyb_apply(st, r), "inex": lambda r: O.H3_inex_apply(st, r)}[variant]
+    B = np.random.default_rng(23).standard_normal((6, p.n))
+    b = torch.from_numpy(B).cuda()
+    for prec in (FP64, MIXED_FP16 if variant == "hyb" else MIXED_FP32):
+        x = torch.zeros_like(b)
+        status, its, rels = awg_pcg_block(sol.h, b, x, 1e-8, precision=prec, check=False)
+        assert status == 0
+        X = x.cpu().numpy()
+        for c in range(B.shape[0]):
+            assert rels[c] <= 1e-8
+            assert np.linalg.norm(st.A @ X[c] - B[c]) <= 1e-8 * np.linalg.norm(B[c]) * (1 + 1e-12)
+            if prec == FP64 and c < 3:
+                ref = O.pcg(lambda v: st.A @ v, B[c], M, rtol=1e-8)
+                assert abs(its[c] - ref.iters) <= max(1, round(0.05 * ref.iters)), (c, its[c], ref.iters)
+        xa, itsa, rela, sta = _async_solve(sol, B, prec)
+        torch.cuda.synchronize()
+        assert int(sta.item()) == 0
+        XA = xa.cpu().numpy()
+        for c in range(B.shape[0]):
+            assert abs(int(itsa[c].item()) - its[c]) <= 1
+            assert float(rela[c].item()) <= 1e-8
+            assert np.linalg.norm(st.A @ XA[c] - B[c]) <= 2e-8 * np.linalg.norm(B[c])
 
 
 @pytest.mark.parametrize("form", ["fp32", "fp16", "bf16"])
