@@ -7,8 +7,9 @@ Notation follows the paper:
   Omega^s   overlapping index sets (Def. 1), R^s restriction (Def. 2),
   D, D^s    partition of unity (Def. 3), M_mu pair multiplicity and B^s
   (Def. 5), V^s_-, L^s_-, V^s_+, L^s_+ eigen-split of B^s (Def. 6),
-  A_+, A_- (Def. 7), H^NN (Def. 8), Y_L (Def. 9), GenEO coarse space and
-  H^NN_hyb (Thm. 4), W, Pi_3, H_3,ad, H_3,hyb (Def. 10), H_3,inex (Thm. 7).
+  A_+, A_- (Def. 7), H^NN and H^AS_+ (Def. 8), Y_L (Def. 9), GenEO coarse
+  spaces with H^NN_hyb (Thm. 4) and H^AS_+,hyb / H^AS_+,ad (Thm. 3), W, Pi_3,
+  H_3,ad, H_3,hyb (Def. 10), H_3,inex (Thm. 7).
 
 Readings of points the paper leaves open (each also listed in the design
 notes of the repository):
@@ -249,6 +250,10 @@ class Setup:
     dense: bool = False
     A_plus_dense: np.ndarray = None
     info: dict = field(default_factory=dict)
+    # choice of H_2 (Thms. 3, 4): "nn_hyb" = H^NN_hyb(tau_sharp),
+    # "asp_hyb" = H^AS_+,hyb(tau_flat), "asp_ad" = H^AS_+,ad(tau_flat)
+    h2: str = "nn_hyb"
+    as_cho: list = field(default_factory=list)     # Cholesky of R^s A_+ R^sT
 
     @property
     def N(self):
@@ -323,6 +328,34 @@ def H_NN_apply(st: Setup, r: np.ndarray) -> np.ndarray:
         c = spl.V_plus.T @ t
         z[idx] += d * (spl.V_plus @ (c / lp))
     return z
+
+
+def local_A_plus(st: Setup, s: int) -> np.ndarray:
+    """R^s A_+ R^sT: a principal block of the dense A_+ (small n), else
+    through Section 4.4 item 4."""
+    if st.dense:
+        idx = st.subs[s]
+        return st.A_plus_dense[np.ix_(idx, idx)]
+    return local_A_plus_block(st, s)
+
+
+def H_plus_AS_apply(st: Setup, r: np.ndarray) -> np.ndarray:
+    """H^AS_+ r = sum_s R^sT (R^s A_+ R^sT)^-1 R^s r (Def. 8); the local
+    matrices are principal blocks of the spd A_+, so spd, and are solved by
+    Cholesky."""
+    if not st.as_cho:
+        st.as_cho = [sla.cho_factor(0.5 * (M + M.T), lower=True)
+                     for M in (local_A_plus(st, s) for s in range(st.N))]
+    z = np.zeros_like(r, dtype=float)
+    for idx, cho in zip(st.subs, st.as_cho):
+        z[idx] += sla.cho_solve(cho, r[idx])
+    return z
+
+
+def H1_apply(st: Setup, r: np.ndarray) -> np.ndarray:
+    """The one-level preconditioner inside the chosen H_2: H^NN (Thm. 4)
+    or H^AS_+ (Thm. 3)."""
+    return H_NN_apply(st, r) if st.h2 == "nn_hyb" else H_plus_AS_apply(st, r)
 
 
 # ---------------------------------------------------------------------------
@@ -415,8 +448,15 @@ def Pi_T_apply(st: Setup, x: np.ndarray) -> np.ndarray:
 
 
 def H2_apply(st: Setup, r: np.ndarray) -> np.ndarray:
-    """H^NN_hyb(tau) r = Pi H^NN Pi^T r + Z E^-1 Z^T r (Thm. 4)."""
-    u = Pi_apply(st, H_NN_apply(st, Pi_T_apply(st, r)))
+    """The two-level preconditioner H_2 for A_+ chosen by st.h2:
+      H^NN_hyb(tau_sharp) r  = Pi H^NN Pi^T r + Z E^-1 Z^T r    (Thm. 4)
+      H^AS_+,hyb(tau_flat) r = Pi H^AS_+ Pi^T r + Z E^-1 Z^T r  (Thm. 3)
+      H^AS_+,ad(tau_flat) r  = H^AS_+ r + Z E^-1 Z^T r          (Thm. 3)
+    with Pi = I - Z E^-1 Z^T A_+ and E = Z^T A_+ Z in every case."""
+    if st.h2 == "asp_ad":
+        u = H_plus_AS_apply(st, r)
+    else:
+        u = Pi_apply(st, H1_apply(st, Pi_T_apply(st, r)))
     if st.n0:
         u = u + st.Z @ coarse_E_solve(st, st.Z.T @ r)
     return u
@@ -551,8 +591,15 @@ def H3_inex_apply(st: Setup, r: np.ndarray) -> np.ndarray:
 # ---------------------------------------------------------------------------
 
 def setup(rowptr, colidx, val, n, part=None, nparts=None, overlap=1, tau=0.1, subsets=None,
-          dense=None, zero_rtol=ZERO_EIG_RTOL, with_W=True) -> Setup:
-    """Build every ingredient of H_3 from A alone (Sections 2-4)."""
+          dense=None, zero_rtol=ZERO_EIG_RTOL, with_W=True, h2="nn_hyb", tau_flat=10.0) -> Setup:
+    """Build every ingredient of H_3 from A alone (Sections 2-4).  ``tau``
+    is tau_sharp of H^NN_hyb (Thm. 4); with h2 = "asp_hyb" / "asp_ad" the
+    coarse space is V^0_AS,+(tau_flat) of Thm. 3, the eigenvectors of the
+    same pencil below 1 / tau_flat."""
+    if h2 not in ("nn_hyb", "asp_hyb", "asp_ad"):
+        raise ValueError(f"unknown H_2 {h2!r}")
+    if h2 != "nn_hyb":
+        tau = 1.0 / tau_flat
     A = csr_from(rowptr, colidx, val, n)
     if subsets is not None:
         subs = [np.asarray(s, dtype=np.int64) for s in subsets]
@@ -563,7 +610,7 @@ def setup(rowptr, colidx, val, n, part=None, nparts=None, overlap=1, tau=0.1, su
     B = splitting_matrix(A, Mmu)
     splits = [eigen_split(local_B(B, idx), zero_rtol) for idx in subs]
     dense = (n <= 6000) if dense is None else dense
-    st = Setup(A=A, n=n, subs=subs, d=d, Ds=Ds, B=B, splits=splits, tau=tau, dense=dense)
+    st = Setup(A=A, n=n, subs=subs, d=d, Ds=Ds, B=B, splits=splits, tau=tau, dense=dense, h2=h2)
     if dense:
         st.A_plus_dense = assemble_dense(st, "plus")
     geneo_nn(st, tau)

@@ -233,6 +233,52 @@ def test_thm4_geneo_bounds(tiny):
     assert ev.max() <= Ncol / st.tau * (1 + 1e-8)
 
 
+@pytest.mark.parametrize("h2", ["asp_hyb", "asp_ad"])
+def test_thm3_as_plus_bounds(tiny, h2):
+    """Thm. 3 with tau_flat = 10: 1/tau_flat <= lambda(H^AS_+,hyb A_+) <=
+    N(A_+) and 1/((1 + 2 N(A_+)) tau_flat) <= lambda(H^AS_+,ad A_+) <=
+    N(A_+) + 1; the one-level H^AS_+ is spd (Lemma after Def. 8) with
+    lambda_max(H^AS_+ A_+) <= N(A_+) (each colour class adds at most 1)."""
+    p, st0 = tiny
+    tf = 10.0
+    st = O.setup(p.rowptr, p.colidx, p.val, p.n, part=p.part, nparts=p.nparts, overlap=p.overlap,
+                 subsets=p.subsets, dense=True, h2=h2, tau_flat=tf)
+    assert st.tau == 1.0 / tf and st.h2 == h2
+    Ncol = O.colouring_constant(st.subs, O.A_plus_blocks_nonzero_fn(st))
+    Ap = O.assemble_dense(st, "plus")
+    H1 = O.dense_operator(lambda X: O.H_plus_AS_apply(st, X), st.n)
+    assert np.allclose(H1, H1.T, rtol=0, atol=1e-12 * np.abs(H1).max())
+    assert np.linalg.eigvalsh(0.5 * (H1 + H1.T)).min() > 0
+    assert O.spectrum_HA(0.5 * (H1 + H1.T), Ap).max() <= Ncol * (1 + 1e-8)
+    ev, H2, _ = _H2A_plus_spectrum(st)
+    if h2 == "asp_hyb":
+        assert ev.min() >= 1.0 / tf * (1 - 1e-8) and ev.max() <= Ncol * (1 + 1e-8)
+    else:
+        assert ev.min() >= 1.0 / ((1 + 2 * Ncol) * tf) * (1 - 1e-8) and ev.max() <= (Ncol + 1) * (1 + 1e-8)
+
+
+def test_as_plus_block_diagonal_is_exact():
+    """H^AS_+ against a closed form: with one subdomain (N = 1, A_- = 0)
+    H^AS_+ = A^-1; with A_+ block diagonal over non-overlapping subdomains
+    (two decoupled Poisson problems in one matrix, overlap 0) H^AS_+ = A^-1
+    as well, since each local block is the whole of its decoupled part."""
+    p = gi.poisson2d(9, qx=1, overlap=0)
+    st = O.setup_problem(p, dense=True, h2="asp_ad", tau_flat=10.0)
+    assert st.N == 1 and st.n_minus == 0
+    H = O.dense_operator(lambda X: O.H_plus_AS_apply(st, X), st.n)
+    Ainv = np.linalg.inv(st.A.toarray())
+    assert np.linalg.norm(H - Ainv, 2) < 1e-12 * np.linalg.norm(Ainv, 2)
+    q = gi.poisson2d(6, qx=1, overlap=0)
+    A1 = O.csr_from(q.rowptr, q.colidx, q.val, q.n)
+    A2 = sp.block_diag([A1, 2.0 * A1]).tocsr()
+    subs = [np.arange(q.n), np.arange(q.n, 2 * q.n)]
+    st2 = O.setup(A2.indptr, A2.indices, A2.data, 2 * q.n, subsets=subs, dense=True, h2="asp_hyb")
+    assert st2.n_minus == 0
+    H2 = O.dense_operator(lambda X: O.H_plus_AS_apply(st2, X), st2.n)
+    Ainv2 = np.linalg.inv(A2.toarray())
+    assert np.linalg.norm(H2 - Ainv2, 2) < 1e-12 * np.linalg.norm(Ainv2, 2)
+
+
 def test_colouring_constant_bruteforce():
     """Def. 4 on a 2x2 box partition: every pair of subdomains interacts, so
     the optimal constant is 4 and greedy must find it."""
