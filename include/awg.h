@@ -13,7 +13,9 @@
  *   - the eigen-split B^s = A^s_+ - A^s_- (Def. 6) and A_+ (Def. 7, Thm. 2),
  *   - the one-level H^NN (Def. 8) through a Cholesky factorisation of
  *     K^s = A^s_+ + sigma V^s_- V^s_-^T (Section 4.4 item 3),
- *   - the GenEO coarse space and H^NN_hyb(tau) (Def. 9, Thm. 4),
+ *   - the GenEO coarse space and H_2 = H^NN_hyb(tau) (Def. 9, Thm. 4), or
+ *     H^AS_+,hyb / H^AS_+,ad(tau_flat) with local solvers (R^s A_+ R^sT)^-1
+ *     (Def. 8, Thm. 3; awg_options.h2),
  *   - the second coarse space W = A_+^-1 [R^sT V^s_-] by multi-right-hand-
  *     side PCG with H_2 (Section 4.4 items 1-2) and F = W^T A W (Def. 10),
  * and applies H_3,ad (default), H_3,hyb (Def. 10) or H_3,inex (Thm. 7)
@@ -65,6 +67,18 @@ typedef enum {
 
 /* Variant of the AWG preconditioner (Def. 10, Thm. 7). */
 typedef enum { AWG_H3_AD = 0, AWG_H3_HYB = 1, AWG_H3_INEX = 2 } awg_variant;
+
+/* Two-level preconditioner H_2 for A_+ inside H_3 (Section 3.4):
+ * NN_HYB   H^NN_hyb(tau) of Thm. 4: local solvers D^s (A^s_+)^+ D^s, GenEO
+ *          space of the pencil (D^s^-1 A^s_+ D^s^-1, R^s A_+ R^sT) below tau;
+ * ASP_HYB  H^AS_+,hyb(tau_flat) of Thm. 3: local solvers (R^s A_+ R^sT)^-1
+ *          (each the Cholesky inverse of the dense principal block of A_+,
+ *          assembled as in Section 4.4 item 4), coarse space of the same
+ *          pencil below 1 / tau_flat, combined as Pi H^AS_+ Pi^T + Z E^-1 Z^T;
+ * ASP_AD   H^AS_+,ad(tau_flat) of Thm. 3: the same pieces combined additively,
+ *          H^AS_+ + Z E^-1 Z^T.
+ * E = Z^T A_+ Z and Pi = I - Z E^-1 Z^T A_+ in every case. */
+typedef enum { AWG_H2_NN_HYB = 0, AWG_H2_ASP_HYB = 1, AWG_H2_ASP_AD = 2 } awg_h2;
 
 /* Storage/arithmetic of the two largest operators of the apply: the local
  * pseudo-inverses D^s (A^s_+)^+ D^s and the second coarse basis W.  FP64
@@ -128,6 +142,10 @@ typedef struct {
                                AWG_MIXED_FP16 or AWG_MIXED_BF16: 1 (default)
                                the two passes over W on the tensor cores
                                (tcgen05.mma fed by TMA); 0 on the CUDA cores   */
+    int h2;                 /* awg_h2, default AWG_H2_NN_HYB                   */
+    double tau_flat;        /* tau_flat > 0 of the AS_+ choices of H_2 (their
+                               GenEO threshold is 1 / tau_flat; the tau of
+                               awg_setup is then unused); default 10           */
 } awg_options;
 
 /* Per-handle figures reported after setup (cf. Table 1 of the paper). */

@@ -628,10 +628,12 @@ def setup_problem(prob, **kw) -> Setup:
 
 def local_condition(st: Setup) -> float:
     """max_s lambda_max(A^s_+) / lambda_min+(A^s_+): the condition number of
-    the local pseudo-inverses.  Any backward-stable evaluation of
+    the local pseudo-inverses (with H^AS_+, max_s cond(R^s A_+ R^sT)).  Any backward-stable evaluation of
     (A^s_+)^+ t (this oracle's eigenvector form, or a Cholesky route) has a
     forward error of order local_condition * eps, which bounds how closely
     two correct implementations of H^NN can agree."""
+    if st.h2 != "nn_hyb":  # H^AS_+: the local solvers are (R^s A_+ R^sT)^-1
+        return float(max(np.linalg.cond(0.5 * (M + M.T)) for M in (local_A_plus(st, s) for s in range(st.N))))
     return float(max(s.L_plus.max() / s.L_plus.min() for s in st.splits if s.L_plus.size))
 
 

@@ -880,10 +880,18 @@ static awg_status coarse_e(Handle* h, const double* x, double* y0, double* c, cu
     return dense_gemv(h, h->n0, (double*)h->Einv.p, y0, c, 1.0, nullptr, 0.0, s);
 }
 
-// H_2 x = Pi H^NN Pi^T x + Z E^-1 Z^T x  (Thm. 4)
+// H_2 x = Pi H_1 Pi^T x + Z E^-1 Z^T x  (Thm. 4 with H_1 = H^NN; Thm. 3 with
+// H_1 = H^AS_+), or H_1 x + Z E^-1 Z^T x (H^AS_+,ad, Thm. 3); H_1 is the
+// local solvers the setup built
 // z = H_2 r (+ add, once the event `wait` has completed)
 static awg_status h2_1(Handle* h, int prec, const double* r, double* z, Ws& w, cudaStream_t s,
                        const double* add = nullptr, cudaEvent_t wait = nullptr) {
+    if (h->n0 > 0 && h->opt.h2 == AWG_H2_ASP_AD) {
+        AWG_TRY(coarse_e(h, r, w.y0, w.c1, s));  // c1 = E^-1 Z^T r
+        AWG_TRY(hnn1(h, prec, r, w.u, w, s));    // u = H_1 r
+        if (wait) AWG_CUDA(cudaStreamWaitEvent(s, wait, 0));
+        return zc1(h, w.c1, z, 1.0, 0.0, w.u, 1.0, s, add);  // z = u + Z c1 (+ add)
+    }
     if (h->n0 == 0) {
         AWG_TRY(hnn1(h, prec, r, z, w, s));
         if (add) {

@@ -1471,7 +1471,8 @@ struct BlockApply {
         return AWG_OK;
     }
 
-    // H_2 X = Pi H^NN Pi^T X + Z E^-1 Z^T X (Thm. 4) in two parts, so that
+    // H_2 X = Pi H_1 Pi^T X + Z E^-1 Z^T X (Thms. 3, 4; H_1 = H^NN or
+    // H^AS_+), or H_1 X + Z E^-1 Z^T X (H^AS_+,ad), in two parts, so that
     // another stream's work can be issued between them: h2a computes
     // c1 = E^-1 Z^T X, h2b the rest (+ V2 once the event `wait` completed)
     awg_status h2a(const T* X, cudaStream_t s) {
@@ -1492,6 +1493,11 @@ struct BlockApply {
             return AWG_OK;
         }
         const int n0 = h->n0;
+        if (h->opt.h2 == AWG_H2_ASP_AD) {  // H^AS_+,ad (Thm. 3): Y = H_1 X + Z c1 (+ V2)
+            AWG_TRY(hnn(prec, X, v.u, s));
+            if (wait) AWG_CUDA(cudaStreamWaitEvent(s, wait, 0));
+            return zc(v.c1, Y, (T)1, (T)0, v.u, (T)1, V2, s);
+        }
         AWG_TRY(zc(v.c1, v.x1, (T)1, (T)0, nullptr, (T)0, nullptr, s));            // x1 = Z c1
         AWG_TRY(aplus(v.x1, v.t, X, (T)-1, s));                                    // t = X - A_+ x1
         AWG_TRY(hnn(prec, v.t, v.u, s));                                           // u = H^NN t

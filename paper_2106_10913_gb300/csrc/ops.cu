@@ -236,6 +236,12 @@ awg_status blk_h2(Handle* h, const double* X, double* Y, int k, cudaStream_t s, 
     // C1 = E^-1 Z^T X
     AWG_TRY(blk_zt(h, X, C0, k, s));
     AWG_TRY(gemm_batched(h, {{Einv, C0, C1, n0, k, n0, n0, n0, n0, 0, 0, 1.0, 0.0}}, s));
+    if (h->opt.h2 == AWG_H2_ASP_AD) {  // H^AS_+,ad (Thm. 3): Y = H_1 X + Z C1
+        AWG_TRY(blk_hnn(h, X, Y, k, s, prec));
+        AWG_TRY(blk_z(h, C1, Y, k, 1.0, 1.0, s));
+        for (double* p : {C0, C1, X1, T, U}) AWG_CUDA(cudaFreeAsync(p, s));
+        return AWG_OK;
+    }
     // T = X - A_+ Z C1   (Pi^T X)
     AWG_TRY(blk_z(h, C1, X1, k, 1.0, 0.0, s));
     AWG_TRY(blk_aplus(h, X1, T, k, s));

@@ -689,6 +689,37 @@ static awg_status build_w16_correction(Handle* h, PrecOps& P, const double* W64,
     return AWG_OK;
 }
 
+// G^s = (R^s A_+ R^sT)^-1 for every subdomain (Def. 8, H^AS_+), over the
+// float64 local operators of H^NN: the dense block R^s A R^sT plus the
+// neighbour terms of A_- (Section 4.4 item 4), Cholesky, triangular inverse,
+// L^-T L^-1.  `work` holds dense_total doubles.
+static awg_status build_local_as_plus(Handle* h, double* work) {
+    cudaStream_t s = h->stream;
+    const int N = h->N;
+    AWG_TRY(assemble_local(h, (double*)h->val.p, work));
+    if (h->n_minus_all > 0) {
+        k_add_nbr_MB<<<dim3(N, 16), 256, 0, s>>>((int*)h->ns.p, (int64_t*)h->dense_off.p, (int*)h->sub_ptr.p,
+                                                 (int*)h->sub_idx.p, (int*)h->inc_ptr.p, (int*)h->inc_pos.p,
+                                                 (int*)h->inc_sub.p, (int*)h->nm_ptr.p, (int64_t*)h->vm_off.p,
+                                                 (double*)h->Vm.p, (double*)h->lam_m.p, work);
+        AWG_LAUNCH();
+    }
+    AWG_CUDA(cudaMemsetAsync(h->flag.p, 0, sizeof(int), s));
+    AWG_TRY(potrf_batched(h, work, (int*)h->ns.p, (int64_t*)h->dense_off.p, N, h->max_ns, (int*)h->flag.p, s));
+    AWG_TRY(check_flag(h, FLAG_NOT_SPD, AWG_ERR_NOT_SPD));
+    AWG_TRY(trtri_batched(h, work, (int*)h->ns.p, (int64_t*)h->dense_off.p, N, h->max_ns, s));
+    std::vector<GemmDesc> d;
+    double* G = (double*)h->prec[AWG_FP64].G.p;
+    for (int t = 0; t < N; t++) {
+        const int m = h->h_ns[t];
+        const int64_t o = h->h_dense_off[t];
+        d.push_back({work + o, work + o, G + o, m, m, m, m, m, m, 1, 0, 1.0, 0.0});
+    }
+    AWG_TRY(gemm_batched(h, d, s));  // L^-T L^-1
+    AWG_CUDA(cudaStreamSynchronize(s));
+    return AWG_OK;
+}
+
 awg_status build_setup_numeric(Handle* h) {
     cudaStream_t s = h->stream;
     const int N = h->N, n = h->n;
@@ -903,8 +934,11 @@ awg_status build_setup_numeric(Handle* h) {
         AWG_CUDA(cudaStreamSynchronize(s));
         for (DevBuf* bb : {&Q, &qvals, &dms, &dos}) dfree(h, *bb);
     }
-    dfree(h, A1);
     dfree(h, A2);
+    // H^AS_+ (Thm. 3): the local solvers become (R^s A_+ R^sT)^-1, after the
+    // GenEO solve (whose block solver applies the H^NN local operators)
+    if (h->opt.h2 != AWG_H2_NN_HYB) AWG_TRY(build_local_as_plus(h, (double*)A1.p));
+    dfree(h, A1);
     double t3 = now_ms();
     h->setup_ms[3] = t3 - t2;
 

@@ -62,9 +62,14 @@ def test_host_only_calls(lib):
     assert lib.awg_learned_grad(0, None, None, None, None, 0, None) == 1
     assert lib.awg_learned_train(1, None, None, None, 1, 1e-2, 0, None, None) == 1
     assert lib.awg_learned_data(None, None, None, None) == 1
-    assert ctypes.sizeof(pkg.awg.awg_options) == 88
+    assert ctypes.sizeof(pkg.awg.awg_options) == 96
     assert o.w16_keep == 0.1
-    assert pkg.default_options().block_tensor_cores == 1
+    d = pkg.default_options()
+    assert d.block_tensor_cores == 1 and d.h2 == pkg.H2_NN_HYB and d.tau_flat == 10.0
+    # H_2 choice and tau_flat are checked before any device work
+    for bad in ({"h2": 3}, {"h2": -1}, {"h2": pkg.H2_ASP_AD, "tau_flat": 0.0}):
+        o = pkg.default_options(**bad)
+        assert lib.awg_setup(4, 4, 1, 1, 1, 1, 1, 1, 0.1, ctypes.byref(o), None, ctypes.byref(h)) == 1
     # the block and graph-driven entry points reject bad arguments before
     # touching the device
     assert lib.awg_apply_block(None, 4, 0, None, None, 1, 1, None) == 1
