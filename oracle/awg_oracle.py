@@ -7,9 +7,9 @@ Notation follows the paper:
   Omega^s   overlapping index sets (Def. 1), R^s restriction (Def. 2),
   D, D^s    partition of unity (Def. 3), M_mu pair multiplicity and B^s
   (Def. 5), V^s_-, L^s_-, V^s_+, L^s_+ eigen-split of B^s (Def. 6),
-  A_+, A_- (Def. 7), H^NN and H^AS_+ (Def. 8), Y_L (Def. 9), GenEO coarse
-  spaces with H^NN_hyb (Thm. 4) and H^AS_+,hyb / H^AS_+,ad (Thm. 3), W, Pi_3,
-  H_3,ad, H_3,hyb (Def. 10), H_3,inex (Thm. 7).
+  A_+, A_- (Def. 7), H^NN, H^AS_+ and H^AS (Def. 8), Y_L (Def. 9), GenEO
+  coarse spaces with H^NN_hyb (Thm. 4), H^AS_+,hyb / H^AS_+,ad (Thm. 3) and
+  H^AS_hyb (Thm. 5), W, Pi_3, H_3,ad, H_3,hyb (Def. 10), H_3,inex (Thm. 7).
 
 Readings of points the paper leaves open (each also listed in the design
 notes of the repository):
@@ -250,10 +250,12 @@ class Setup:
     dense: bool = False
     A_plus_dense: np.ndarray = None
     info: dict = field(default_factory=dict)
-    # choice of H_2 (Thms. 3, 4): "nn_hyb" = H^NN_hyb(tau_sharp),
-    # "asp_hyb" = H^AS_+,hyb(tau_flat), "asp_ad" = H^AS_+,ad(tau_flat)
+    # choice of H_2 (Thms. 3-5): "nn_hyb" = H^NN_hyb(tau_sharp),
+    # "asp_hyb" = H^AS_+,hyb(tau_flat), "asp_ad" = H^AS_+,ad(tau_flat),
+    # "as_hyb" = H^AS_hyb(tau_sharp, tau_flat)
     h2: str = "nn_hyb"
-    as_cho: list = field(default_factory=list)     # Cholesky of R^s A_+ R^sT
+    as_cho: list = field(default_factory=list)     # Cholesky of the local matrices of H^AS_+ / H^AS
+    geneo_split: list = field(default_factory=list)  # H^AS: (k1, k2) columns per subdomain from each pencil
 
     @property
     def N(self):
@@ -352,10 +354,23 @@ def H_plus_AS_apply(st: Setup, r: np.ndarray) -> np.ndarray:
     return z
 
 
+def H_AS_apply(st: Setup, r: np.ndarray) -> np.ndarray:
+    """H^AS r = sum_s R^sT (R^s A R^sT)^-1 R^s r (Def. 8); the local
+    matrices are principal blocks of the spd A, solved by Cholesky."""
+    if not st.as_cho:
+        st.as_cho = [sla.cho_factor(st.A[idx][:, idx].toarray(), lower=True) for idx in st.subs]
+    z = np.zeros_like(r, dtype=float)
+    for idx, cho in zip(st.subs, st.as_cho):
+        z[idx] += sla.cho_solve(cho, r[idx])
+    return z
+
+
 def H1_apply(st: Setup, r: np.ndarray) -> np.ndarray:
-    """The one-level preconditioner inside the chosen H_2: H^NN (Thm. 4)
-    or H^AS_+ (Thm. 3)."""
-    return H_NN_apply(st, r) if st.h2 == "nn_hyb" else H_plus_AS_apply(st, r)
+    """The one-level preconditioner inside the chosen H_2: H^NN (Thm. 4),
+    H^AS_+ (Thm. 3) or H^AS (Thm. 5)."""
+    if st.h2 == "nn_hyb":
+        return H_NN_apply(st, r)
+    return H_AS_apply(st, r) if st.h2 == "as_hyb" else H_plus_AS_apply(st, r)
 
 
 # ---------------------------------------------------------------------------
@@ -398,7 +413,44 @@ def geneo_nn(st: Setup, tau: float) -> None:
             cols.append(cc.ravel())
             vals.append(Ys.ravel())
             col += k
-    n0 = col
+    _coarse_from_columns(st, col, rows, cols, vals)
+
+
+def geneo_as(st: Setup, tau_sharp: float, tau_flat: float) -> None:
+    """V^0_AS(tau_sharp, tau_flat) (Thm. 5): per subdomain the columns of
+    Y_L(1/tau_flat, D^s^-1 A^s_+ D^s^-1, R^s A R^sT) followed by those of
+    Y_L(tau_sharp, R^s A R^sT, R^s A_+ R^sT), prolonged by R^sT, and
+    E = Z^T A_+ Z.  The two sets are taken together as the basis the
+    theorem assumes; a union that is not linearly independent leaves E
+    singular, which is recorded in st.info["E_singular"]."""
+    cols, rows, vals = [], [], []
+    col = 0
+    st.Y, st.geneo_lam, st.geneo_split = [], [], []
+    for s, (idx, Ds, spl) in enumerate(zip(st.subs, st.Ds, st.splits)):
+        M_A = (spl.A_plus() / Ds[:, None]) / Ds[None, :]
+        M_A = 0.5 * (M_A + M_A.T)
+        RAR = st.A[idx][:, idx].toarray()
+        RApR = local_A_plus(st, s)
+        RApR = 0.5 * (RApR + RApR.T)
+        Y1, lam1 = Y_L(M_A, RAR, 1.0 / tau_flat)
+        Y2, lam2 = Y_L(RAR, RApR, tau_sharp)
+        Ys = np.hstack([Y1, Y2])
+        st.Y.append(Ys)
+        st.geneo_lam.append((lam1, lam2))
+        st.geneo_split.append((Y1.shape[1], Y2.shape[1]))
+        k = Ys.shape[1]
+        if k:
+            rr, cc = np.meshgrid(idx, np.arange(col, col + k), indexing="ij")
+            rows.append(rr.ravel())
+            cols.append(cc.ravel())
+            vals.append(Ys.ravel())
+            col += k
+    _coarse_from_columns(st, col, rows, cols, vals)
+
+
+def _coarse_from_columns(st: Setup, n0: int, rows, cols, vals) -> None:
+    """Z from the prolonged local columns, E = Z^T A_+ Z and its Cholesky
+    factor (Assumption 3 asks for a basis: a singular E is recorded)."""
     if n0:
         st.Z = sp.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                              shape=(st.n, n0))
@@ -408,7 +460,6 @@ def geneo_nn(st: Setup, tau: float) -> None:
         try:
             st.E_cho = sla.cho_factor(st.E, lower=True)
         except np.linalg.LinAlgError:
-            # dependent columns: Z is not a basis as Assumption 3 requires
             st.E_cho = None
             st.info["E_singular"] = True
     else:
@@ -452,6 +503,7 @@ def H2_apply(st: Setup, r: np.ndarray) -> np.ndarray:
       H^NN_hyb(tau_sharp) r  = Pi H^NN Pi^T r + Z E^-1 Z^T r    (Thm. 4)
       H^AS_+,hyb(tau_flat) r = Pi H^AS_+ Pi^T r + Z E^-1 Z^T r  (Thm. 3)
       H^AS_+,ad(tau_flat) r  = H^AS_+ r + Z E^-1 Z^T r          (Thm. 3)
+      H^AS_hyb(tau_sharp, tau_flat) r = Pi H^AS Pi^T r + Z E^-1 Z^T r (Thm. 5)
     with Pi = I - Z E^-1 Z^T A_+ and E = Z^T A_+ Z in every case."""
     if st.h2 == "asp_ad":
         u = H_plus_AS_apply(st, r)
@@ -595,10 +647,11 @@ def setup(rowptr, colidx, val, n, part=None, nparts=None, overlap=1, tau=0.1, su
     """Build every ingredient of H_3 from A alone (Sections 2-4).  ``tau``
     is tau_sharp of H^NN_hyb (Thm. 4); with h2 = "asp_hyb" / "asp_ad" the
     coarse space is V^0_AS,+(tau_flat) of Thm. 3, the eigenvectors of the
-    same pencil below 1 / tau_flat."""
-    if h2 not in ("nn_hyb", "asp_hyb", "asp_ad"):
+    same pencil below 1 / tau_flat; with h2 = "as_hyb" it is
+    V^0_AS(tau, tau_flat) of Thm. 5 (two pencils)."""
+    if h2 not in ("nn_hyb", "asp_hyb", "asp_ad", "as_hyb"):
         raise ValueError(f"unknown H_2 {h2!r}")
-    if h2 != "nn_hyb":
+    if h2 in ("asp_hyb", "asp_ad"):
         tau = 1.0 / tau_flat
     A = csr_from(rowptr, colidx, val, n)
     if subsets is not None:
@@ -613,7 +666,10 @@ def setup(rowptr, colidx, val, n, part=None, nparts=None, overlap=1, tau=0.1, su
     st = Setup(A=A, n=n, subs=subs, d=d, Ds=Ds, B=B, splits=splits, tau=tau, dense=dense, h2=h2)
     if dense:
         st.A_plus_dense = assemble_dense(st, "plus")
-    geneo_nn(st, tau)
+    if h2 == "as_hyb":
+        geneo_as(st, tau, tau_flat)
+    else:
+        geneo_nn(st, tau)
     if with_W:
         build_W(st)
     return st
@@ -632,6 +688,8 @@ def local_condition(st: Setup) -> float:
     (A^s_+)^+ t (this oracle's eigenvector form, or a Cholesky route) has a
     forward error of order local_condition * eps, which bounds how closely
     two correct implementations of H^NN can agree."""
+    if st.h2 == "as_hyb":  # H^AS: the local solvers are (R^s A R^sT)^-1
+        return float(max(np.linalg.cond(st.A[idx][:, idx].toarray()) for idx in st.subs))
     if st.h2 != "nn_hyb":  # H^AS_+: the local solvers are (R^s A_+ R^sT)^-1
         return float(max(np.linalg.cond(0.5 * (M + M.T)) for M in (local_A_plus(st, s) for s in range(st.N))))
     return float(max(s.L_plus.max() / s.L_plus.min() for s in st.splits if s.L_plus.size))

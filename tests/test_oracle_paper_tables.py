@@ -1,8 +1,8 @@
 """The oracle against the numbers the paper prints for its worked example
 (Section 5, Tables 1 and 5), stored in tests/golden with their citation:
-the eight AWG rows of Table 1 but the two with H^AS_hyb(0.1, 10) (H_2 =
-H^NN_hyb(0.1), H^AS_+,hyb(10), H^AS_+,ad(10); H_3,ad and H_3,hyb) and three
-rows of Table 5.
+the eight AWG rows of Table 1 (H_2 = H^NN_hyb(0.1), H^AS_hyb(0.1, 10),
+H^AS_+,hyb(10), H^AS_+,ad(10); H_3,ad and H_3,hyb) and three rows of
+Table 5.
 
 The coarse-space sizes #V_0 and n_- are exact integers fixed by A, the
 subdomains and tau: they pin the splitting (Def. 5), the eigen-split
@@ -32,11 +32,11 @@ def _setup(layers, E1, E2, h2="nn_hyb", tau_flat=10.0):
     """One setup per coarse space: H^AS_+,hyb and H^AS_+,ad share
     V^0_AS,+(tau_flat) (Thm. 3), so the additive one reuses the hybrid one's
     ingredients with the other H_2."""
-    fam = "nn" if h2 == "nn_hyb" else ("asp", tau_flat)
+    fam = {"nn_hyb": "nn", "as_hyb": ("as", tau_flat)}.get(h2, ("asp", tau_flat))
     key = (layers, E1, E2, fam)
     if key not in _CACHE:
         p = gi.paper_elasticity(layers=layers, E1=E1, E2=E2)
-        kw = {} if h2 == "nn_hyb" else {"h2": "asp_hyb", "tau_flat": tau_flat}
+        kw = {} if h2 == "nn_hyb" else {"h2": "as_hyb" if h2 == "as_hyb" else "asp_hyb", "tau_flat": tau_flat}
         _CACHE[key] = (p, O.setup_problem(p, **kw))
     p, st = _CACHE[key]
     if st.h2 != h2:

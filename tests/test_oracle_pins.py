@@ -279,6 +279,36 @@ def test_as_plus_block_diagonal_is_exact():
     assert np.linalg.norm(H2 - Ainv2, 2) < 1e-12 * np.linalg.norm(Ainv2, 2)
 
 
+@pytest.mark.parametrize("tau_sharp", [0.1, 0.5])
+def test_thm5_as_hyb_bounds(tiny, tau_sharp):
+    """Thm. 5 with tau_flat = 10: 1/tau_flat <= lambda(H^AS_hyb A_+) <=
+    N(A_+)/tau_sharp; H^AS is spd; the coarse columns of the two pencils are
+    independent (E non-singular) and each set is the pencil's selection."""
+    p, st0 = tiny
+    tf = 10.0
+    st = O.setup(p.rowptr, p.colidx, p.val, p.n, part=p.part, nparts=p.nparts, overlap=p.overlap,
+                 subsets=p.subsets, dense=True, h2="as_hyb", tau=tau_sharp, tau_flat=tf)
+    assert st.tau == tau_sharp and not st.info.get("E_singular")
+    for (k1, k2), (lam1, lam2), Y in zip(st.geneo_split, st.geneo_lam, st.Y):
+        assert k1 == int(np.sum(lam1 < 1.0 / tf)) and k2 == int(np.sum(lam2 < tau_sharp))
+        assert Y.shape[1] == k1 + k2
+        assert np.all(lam2 <= 1.0 + 1e-10) and np.all(lam2 > 0)  # A <= A_+ (Thm. 2)
+    Ncol = O.colouring_constant(st.subs, O.A_plus_blocks_nonzero_fn(st))
+    H1 = O.dense_operator(lambda X: O.H_AS_apply(st, X), st.n)
+    assert np.linalg.eigvalsh(0.5 * (H1 + H1.T)).min() > 0
+    ev, H2, _ = _H2A_plus_spectrum(st)
+    assert ev.min() >= 1.0 / tf * (1 - 1e-8) and ev.max() <= Ncol / tau_sharp * (1 + 1e-8)
+
+
+def test_as_one_subdomain_is_exact():
+    """N = 1: H^AS = A^-1 (its one local matrix is A)."""
+    p = gi.poisson2d(9, qx=1, overlap=0)
+    st = O.setup_problem(p, dense=True, h2="as_hyb", tau_flat=10.0)
+    H = O.dense_operator(lambda X: O.H_AS_apply(st, X), st.n)
+    Ainv = np.linalg.inv(st.A.toarray())
+    assert np.linalg.norm(H - Ainv, 2) < 1e-12 * np.linalg.norm(Ainv, 2)
+
+
 def test_colouring_constant_bruteforce():
     """Def. 4 on a 2x2 box partition: every pair of subdomains interacts, so
     the optimal constant is 4 and greedy must find it."""
