@@ -15,7 +15,8 @@
  *     K^s = A^s_+ + sigma V^s_- V^s_-^T (Section 4.4 item 3),
  *   - the GenEO coarse space and H_2 = H^NN_hyb(tau) (Def. 9, Thm. 4), or
  *     H^AS_+,hyb / H^AS_+,ad(tau_flat) with local solvers (R^s A_+ R^sT)^-1
- *     (Def. 8, Thm. 3; awg_options.h2),
+ *     (Def. 8, Thm. 3), or H^AS_hyb(tau, tau_flat) with local solvers
+ *     (R^s A R^sT)^-1 (Thm. 5) (awg_options.h2),
  *   - the second coarse space W = A_+^-1 [R^sT V^s_-] by multi-right-hand-
  *     side PCG with H_2 (Section 4.4 items 1-2) and F = W^T A W (Def. 10),
  * and applies H_3,ad (default), H_3,hyb (Def. 10) or H_3,inex (Thm. 7)
@@ -76,9 +77,15 @@ typedef enum { AWG_H3_AD = 0, AWG_H3_HYB = 1, AWG_H3_INEX = 2 } awg_variant;
  *          assembled as in Section 4.4 item 4), coarse space of the same
  *          pencil below 1 / tau_flat, combined as Pi H^AS_+ Pi^T + Z E^-1 Z^T;
  * ASP_AD   H^AS_+,ad(tau_flat) of Thm. 3: the same pieces combined additively,
- *          H^AS_+ + Z E^-1 Z^T.
+ *          H^AS_+ + Z E^-1 Z^T;
+ * AS_HYB   H^AS_hyb(tau, tau_flat) of Thm. 5: local solvers (R^s A R^sT)^-1,
+ *          coarse space of two pencils per subdomain, the eigenvectors of
+ *          (D^s^-1 A^s_+ D^s^-1, R^s A R^sT) below 1 / tau_flat followed by
+ *          those of (R^s A R^sT, R^s A_+ R^sT) below tau (both by the dense
+ *          route; awg_options.geneo_solver is not used); a union that is not
+ *          linearly independent leaves E singular (AWG_ERR_NOT_SPD).
  * E = Z^T A_+ Z and Pi = I - Z E^-1 Z^T A_+ in every case. */
-typedef enum { AWG_H2_NN_HYB = 0, AWG_H2_ASP_HYB = 1, AWG_H2_ASP_AD = 2 } awg_h2;
+typedef enum { AWG_H2_NN_HYB = 0, AWG_H2_ASP_HYB = 1, AWG_H2_ASP_AD = 2, AWG_H2_AS_HYB = 3 } awg_h2;
 
 /* Storage/arithmetic of the two largest operators of the apply: the local
  * pseudo-inverses D^s (A^s_+)^+ D^s and the second coarse basis W.  FP64
@@ -143,9 +150,9 @@ typedef struct {
                                the two passes over W on the tensor cores
                                (tcgen05.mma fed by TMA); 0 on the CUDA cores   */
     int h2;                 /* awg_h2, default AWG_H2_NN_HYB                   */
-    double tau_flat;        /* tau_flat > 0 of the AS_+ choices of H_2 (their
-                               GenEO threshold is 1 / tau_flat; the tau of
-                               awg_setup is then unused); default 10           */
+    double tau_flat;        /* tau_flat > 0 of the AS choices of H_2 (the
+                               AS_+ ones select below 1 / tau_flat and leave
+                               the tau of awg_setup unused); default 10        */
 } awg_options;
 
 /* Per-handle figures reported after setup (cf. Table 1 of the paper). */

@@ -23,7 +23,8 @@ STATUS = {0: "AWG_OK", 1: "AWG_ERR_INVALID_ARG", 2: "AWG_ERR_MIN_OVERLAP", 3: "A
           8: "AWG_ERR_CUDA", 9: "AWG_ERR_NOT_SYMMETRIC", 10: "AWG_ERR_STATE"}
 H3_AD, H3_HYB, H3_INEX = 0, 1, 2
 FP64, MIXED_FP32, MIXED_BF16, MIXED_FP16 = 0, 1, 2, 3
-H2_NN_HYB, H2_ASP_HYB, H2_ASP_AD = 0, 1, 2  # H^NN_hyb(tau) (Thm. 4), H^AS_+,hyb / ,ad(tau_flat) (Thm. 3)
+# H^NN_hyb(tau) (Thm. 4), H^AS_+,hyb / ,ad(tau_flat) (Thm. 3), H^AS_hyb(tau, tau_flat) (Thm. 5)
+H2_NN_HYB, H2_ASP_HYB, H2_ASP_AD, H2_AS_HYB = 0, 1, 2, 3
 STAGE = {"spmv": 0, "aplus": 1, "hnn": 2, "h2": 3, "h3ad": 4, "h3hyb": 5, "h3inex": 6}
 ARRAY = {"ns": (0, np.int32), "sub_idx": (1, np.int32), "n_minus": (2, np.int32),
          "n_strict": (3, np.int32), "modes": (4, np.int32), "lam_minus": (5, np.float64),

@@ -224,7 +224,7 @@ awg_status awg_setup(int n, int nnz, const int* d_rowptr, const int* d_colidx, c
         o.w_maxit < 1 || o.maxit < 1 || (o.w_precision != AWG_FP64 && o.w_precision != AWG_MIXED_FP32) ||
         o.geneo_solver < 0 || o.geneo_solver > 2 || o.geneo_block < 2 || o.geneo_block > 16 ||
         o.geneo_maxit < 1 || (o.geneo_solver == 2 && !o.learned_params) || !(o.w16_keep >= 0.0) ||
-        o.w16_keep > 1.0 || o.h2 < AWG_H2_NN_HYB || o.h2 > AWG_H2_ASP_AD || !(o.tau_flat > 0.0))
+        o.w16_keep > 1.0 || o.h2 < AWG_H2_NN_HYB || o.h2 > AWG_H2_AS_HYB || !(o.tau_flat > 0.0))
         return AWG_ERR_INVALID_ARG;
     o.precisions |= 1 << AWG_FP64;
     Handle* h = new (std::nothrow) Handle();
@@ -233,7 +233,8 @@ awg_status awg_setup(int n, int nnz, const int* d_rowptr, const int* d_colidx, c
     h->nnz = nnz;
     h->N = nparts;
     h->overlap = overlap;
-    h->tau = o.h2 == AWG_H2_NN_HYB ? tau : 1.0 / o.tau_flat;  // GenEO threshold (Thms. 3, 4)
+    // GenEO threshold: tau_sharp (Thms. 4, 5) or 1 / tau_flat (Thm. 3)
+    h->tau = (o.h2 == AWG_H2_ASP_HYB || o.h2 == AWG_H2_ASP_AD) ? 1.0 / o.tau_flat : tau;
     h->opt = o;
     if (o.geneo_solver == 2) h->h_learned.assign(o.learned_params, o.learned_params + AWG_LEARNED_NPARAM);
     h->opt.learned_params = nullptr;  // the caller's array is read during setup only

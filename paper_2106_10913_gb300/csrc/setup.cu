@@ -6,7 +6,9 @@
 //      explicit symmetric D^s (A^s_+)^+ D^s;
 //   3. GenEO pencil (M_A, M_B) = (D^s^-1 A^s_+ D^s^-1, R^s A_+ R^sT) with M_B
 //      from Section 4.4 item 4; reduced by the Cholesky factor of M_B to a
-//      standard symmetric problem; eigenvectors with lambda < tau (Def. 9);
+//      standard symmetric problem; eigenvectors with lambda < tau (Def. 9)
+//      (H^AS_hyb: two pencils, Thm. 5); with an AS choice of H_2, the local
+//      solvers (R^s A_+ R^sT)^-1 or (R^s A R^sT)^-1 (Thms. 3, 5);
 //   4. E = Z^T A_+ Z (Thm. 4), Cholesky, explicit inverse;
 //   5. W = A_+^-1 [R^sT V^s_-] (strictly negative eigenvalues, Section 4.4
 //      items 1-2) by PCG preconditioned with H_2 on all columns at once;
@@ -689,15 +691,16 @@ static awg_status build_w16_correction(Handle* h, PrecOps& P, const double* W64,
     return AWG_OK;
 }
 
-// G^s = (R^s A_+ R^sT)^-1 for every subdomain (Def. 8, H^AS_+), over the
-// float64 local operators of H^NN: the dense block R^s A R^sT plus the
-// neighbour terms of A_- (Section 4.4 item 4), Cholesky, triangular inverse,
-// L^-T L^-1.  `work` holds dense_total doubles.
-static awg_status build_local_as_plus(Handle* h, double* work) {
+// G^s = (R^s A_+ R^sT)^-1 (plus: H^AS_+) or (R^s A R^sT)^-1 (H^AS) for
+// every subdomain (Def. 8), over the float64 local operators of H^NN: the
+// dense block R^s A R^sT (plus the neighbour terms of A_-, Section 4.4 item
+// 4), Cholesky, triangular inverse, L^-T L^-1.  `work` holds dense_total
+// doubles.
+static awg_status build_local_as(Handle* h, double* work, bool plus) {
     cudaStream_t s = h->stream;
     const int N = h->N;
     AWG_TRY(assemble_local(h, (double*)h->val.p, work));
-    if (h->n_minus_all > 0) {
+    if (plus && h->n_minus_all > 0) {
         k_add_nbr_MB<<<dim3(N, 16), 256, 0, s>>>((int*)h->ns.p, (int64_t*)h->dense_off.p, (int*)h->sub_ptr.p,
                                                  (int*)h->sub_idx.p, (int*)h->inc_ptr.p, (int*)h->inc_pos.p,
                                                  (int*)h->inc_sub.p, (int*)h->nm_ptr.p, (int64_t*)h->vm_off.p,
@@ -717,6 +720,117 @@ static awg_status build_local_as_plus(Handle* h, double* work) {
     }
     AWG_TRY(gemm_batched(h, d, s));  // L^-T L^-1
     AWG_CUDA(cudaStreamSynchronize(s));
+    return AWG_OK;
+}
+
+// Y_L(thr, M_A, M_B) of every subdomain (Def. 9) by the dense route: M_B =
+// L L^T, eigenpairs of L^-1 M_A L^-T below thr, Y = L^-T Q (M_B-orthonormal
+// columns).  MA, MB and work are dense arenas (destroyed); Y gets the
+// column-major n^s x cnt[s] blocks at yoff[s].
+static awg_status dense_pencil(Handle* h, double* MA, double* MB, double* work, double thr, std::vector<int>& cnt,
+                               DevBuf& Y, std::vector<int64_t>& yoff) {
+    cudaStream_t s = h->stream;
+    const int N = h->N;
+    AWG_CUDA(cudaMemsetAsync(h->flag.p, 0, sizeof(int), s));
+    AWG_TRY(potrf_batched(h, MB, (int*)h->ns.p, (int64_t*)h->dense_off.p, N, h->max_ns, (int*)h->flag.p, s));
+    AWG_TRY(check_flag(h, FLAG_NOT_SPD, AWG_ERR_NOT_SPD));
+    AWG_TRY(trtri_batched(h, MB, (int*)h->ns.p, (int64_t*)h->dense_off.p, N, h->max_ns, s));
+    {
+        std::vector<GemmDesc> d1, d2;
+        for (int t = 0; t < N; t++) {
+            const int m = h->h_ns[t];
+            const int64_t o = h->h_dense_off[t];
+            d1.push_back({MB + o, MA + o, work + o, m, m, m, m, m, m, 0, 0, 1.0, 0.0});
+            d2.push_back({work + o, MB + o, MA + o, m, m, m, m, m, m, 0, 1, 1.0, 0.0});
+        }
+        AWG_TRY(gemm_batched(h, d1, s));  // work = L^-1 M_A
+        AWG_TRY(gemm_batched(h, d2, s));  // M_A <- work L^-T
+    }
+    k_symmetrize<<<dim3(N, 16), 256, 0, s>>>((int*)h->ns.p, (int64_t*)h->dense_off.p, MA);
+    AWG_LAUNCH();
+    std::vector<int> strict, vptr;
+    std::vector<int64_t> qoff;
+    DevBuf Q, qvals;
+    AWG_CUDA(cudaMemsetAsync(h->flag.p, 0, sizeof(int), s));
+    AWG_TRY(eig_select_batched(h, MA, (int*)h->ns.p, (int64_t*)h->dense_off.p, h->h_ns, N, h->max_ns, 1, thr, cnt,
+                               strict, Q, qoff, qvals, vptr, s));
+    AWG_TRY(check_flag(h, FLAG_EIG, AWG_ERR_EIG));
+    yoff = qoff;
+    AWG_TRY(dalloc(h, Y, std::max<size_t>(8, (size_t)qoff[N] * 8)));
+    std::vector<GemmDesc> d;
+    for (int t = 0; t < N; t++) {
+        const int m = h->h_ns[t], c = cnt[t];
+        if (c == 0) continue;
+        d.push_back({MB + h->h_dense_off[t], (double*)Q.p + qoff[t], (double*)Y.p + qoff[t], m, c, m, m, m, m, 1, 0,
+                     1.0, 0.0});  // Y = L^-T Q
+    }
+    AWG_TRY(gemm_batched(h, d, s));
+    AWG_CUDA(cudaStreamSynchronize(s));
+    dfree(h, Q);
+    dfree(h, qvals);
+    return AWG_OK;
+}
+
+// V^0_AS(tau_sharp, tau_flat) (Thm. 5): per subdomain the columns of
+// Y_L(1/tau_flat, D^s^-1 A^s_+ D^s^-1, R^s A R^sT) followed by those of
+// Y_L(tau_sharp, R^s A R^sT, R^s A_+ R^sT), both by the dense route, packed
+// into Z.  A1 holds dense_total doubles.
+static awg_status geneo_as_dense(Handle* h, double* A1) {
+    cudaStream_t s = h->stream;
+    const int N = h->N;
+    const dim3 gblk(N, 16);
+    DevBuf A2, A3, Y1, Y2;
+    AWG_TRY(dalloc(h, A2, (size_t)h->dense_total * 8));
+    AWG_TRY(dalloc(h, A3, (size_t)h->dense_total * 8));
+    std::vector<int> k1, k2;
+    std::vector<int64_t> o1, o2;
+    // pencil 1: M_A against R^s A R^sT, below 1 / tau_flat
+    AWG_TRY(assemble_local(h, (double*)h->val.p, A1));
+    AWG_TRY(assemble_local(h, (double*)h->bval.p, (double*)A2.p));
+    k_form_MA<<<gblk, 256, 0, s>>>((int*)h->ns.p, (int64_t*)h->dense_off.p, (int*)h->sub_ptr.p, (int*)h->sub_idx.p,
+                                   (double*)h->dvec.p, (int*)h->nm_ptr.p, (int64_t*)h->vm_off.p, (double*)h->Vm.p,
+                                   (double*)h->lam_m.p, (double*)A2.p);
+    AWG_LAUNCH();
+    AWG_TRY(dense_pencil(h, (double*)A2.p, A1, (double*)A3.p, 1.0 / h->opt.tau_flat, k1, Y1, o1));
+    // pencil 2: R^s A R^sT against R^s A_+ R^sT, below tau_sharp
+    AWG_TRY(assemble_local(h, (double*)h->val.p, (double*)A2.p));
+    AWG_TRY(assemble_local(h, (double*)h->val.p, A1));
+    if (h->n_minus_all > 0) {
+        k_add_nbr_MB<<<gblk, 256, 0, s>>>((int*)h->ns.p, (int64_t*)h->dense_off.p, (int*)h->sub_ptr.p,
+                                          (int*)h->sub_idx.p, (int*)h->inc_ptr.p, (int*)h->inc_pos.p,
+                                          (int*)h->inc_sub.p, (int*)h->nm_ptr.p, (int64_t*)h->vm_off.p,
+                                          (double*)h->Vm.p, (double*)h->lam_m.p, A1);
+        AWG_LAUNCH();
+    }
+    AWG_TRY(dense_pencil(h, (double*)A2.p, A1, (double*)A3.p, h->tau, k2, Y2, o2));
+    dfree(h, A2);
+    dfree(h, A3);
+    std::vector<int> mc(N);
+    for (int t = 0; t < N; t++) mc[t] = k1[t] + k2[t];
+    h->h_modes = mc;
+    h->h_mode_ptr.assign(N + 1, 0);
+    h->h_z_off.assign(N + 1, 0);
+    for (int t = 0; t < N; t++) {
+        h->h_mode_ptr[t + 1] = h->h_mode_ptr[t] + mc[t];
+        h->h_z_off[t + 1] = h->h_z_off[t] + (int64_t)h->h_ns[t] * mc[t];
+    }
+    h->n0 = h->h_mode_ptr[N];
+    AWG_TRY(upload(h, h->modes, mc.data(), N * sizeof(int)));
+    AWG_TRY(upload(h, h->mode_ptr, h->h_mode_ptr.data(), (N + 1) * sizeof(int)));
+    AWG_TRY(upload(h, h->z_off, h->h_z_off.data(), (N + 1) * sizeof(int64_t)));
+    AWG_TRY(dalloc(h, h->Z, std::max<size_t>(8, (size_t)h->h_z_off[N] * 8)));
+    for (int t = 0; t < N; t++) {  // Z^s = [Y1^s Y2^s], column-major n^s x (k1 + k2)
+        double* z = (double*)h->Z.p + h->h_z_off[t];
+        const size_t b1 = (size_t)h->h_ns[t] * k1[t] * 8, b2 = (size_t)h->h_ns[t] * k2[t] * 8;
+        if (b1) AWG_CUDA(cudaMemcpyAsync(z, (double*)Y1.p + o1[t], b1, cudaMemcpyDeviceToDevice, s));
+        if (b2) AWG_CUDA(cudaMemcpyAsync((char*)z + b1, (double*)Y2.p + o2[t], b2, cudaMemcpyDeviceToDevice, s));
+    }
+    AWG_CUDA(cudaStreamSynchronize(s));
+    dfree(h, Y1);
+    dfree(h, Y2);
+    h->geneo_dense = N;
+    h->geneo_its_max = 0;
+    h->geneo_its_sum = 0;
     return AWG_OK;
 }
 
@@ -819,125 +933,130 @@ awg_status build_setup_numeric(Handle* h) {
     h->setup_ms[2] = t2 - t1;
 
     // ---------------------------------------------- 3. GenEO
-    // A1 <- M_B = R^s A R^sT + neighbour terms; A2 <- M_A
-    DevBuf A2, A3;
-    AWG_TRY(assemble_local(h, (double*)h->val.p, (double*)A1.p));
-    if (h->n_minus_all > 0) {
-        k_add_nbr_MB<<<gblk, 256, 0, s>>>((int*)h->ns.p, (int64_t*)h->dense_off.p, (int*)h->sub_ptr.p,
-                                          (int*)h->sub_idx.p, (int*)h->inc_ptr.p, (int*)h->inc_pos.p,
-                                          (int*)h->inc_sub.p, (int*)h->nm_ptr.p, (int64_t*)h->vm_off.p,
-                                          (double*)h->Vm.p, (double*)h->lam_m.p, (double*)A1.p);
-        AWG_LAUNCH();
-    }
-    AWG_TRY(dalloc(h, A2, (size_t)h->dense_total * 8));
-    AWG_TRY(assemble_local(h, (double*)h->bval.p, (double*)A2.p));
-    k_form_MA<<<gblk, 256, 0, s>>>((int*)h->ns.p, (int64_t*)h->dense_off.p, (int*)h->sub_ptr.p,
-                                   (int*)h->sub_idx.p, (double*)h->dvec.p, (int*)h->nm_ptr.p,
-                                   (int64_t*)h->vm_off.p, (double*)h->Vm.p, (double*)h->lam_m.p,
-                                   (double*)A2.p);
-    AWG_LAUNCH();
-    // Block eigensolver first (it reads M_A and M_B and keeps them); the
-    // pencils it does not certify go to the dense eigensolver below.
-    GeneoIter gi;
-    std::vector<int> sel;
-    h->geneo_its_max = 0;
-    h->geneo_its_sum = 0;
-    if (h->opt.geneo_solver != 0) {
-        DevBuf prm;
-        if (h->opt.geneo_solver == 2)
-            AWG_TRY(upload(h, prm, h->h_learned.data(), LEARNED_NPARAM * sizeof(double)));
-        AWG_TRY(geneo_block_solve(h, (double*)A2.p, (double*)A1.p, (double*)prm.p, h->opt.geneo_block,
-                                  h->opt.geneo_maxit, 1e-13, gi));
-        dfree(h, prm);
-        for (int t = 0; t < N; t++) {
-            if (gi.ecount[t] < 0) sel.push_back(t);
-            h->geneo_its_max = std::max(h->geneo_its_max, gi.its[t]);
-            h->geneo_its_sum += gi.its[t];
-        }
+    if (h->opt.h2 == AWG_H2_AS_HYB) {  // two pencils, dense route (Thm. 5)
+        AWG_TRY(geneo_as_dense(h, (double*)A1.p));
     } else {
-        for (int t = 0; t < N; t++) sel.push_back(t);
-    }
-    h->geneo_dense = (int)sel.size();
-    // dense eigensolver on that subset: M_B = L L^T, eigenpairs of
-    // L^-1 M_A L^-T below tau, Y = L^-T Q
-    const int nsel = (int)sel.size();
-    std::vector<int> mc_sel;
-    std::vector<int64_t> qoff;
-    DevBuf Q, qvals, dms, dos;
-    if (nsel > 0) {
-        std::vector<int> hms(nsel);
-        std::vector<int64_t> hos(nsel);
-        int maxsel = 1;
-        for (int k = 0; k < nsel; k++) {
-            hms[k] = h->h_ns[sel[k]];
-            hos[k] = h->h_dense_off[sel[k]];
-            maxsel = std::max(maxsel, hms[k]);
+        // A1 <- M_B = R^s A R^sT + neighbour terms; A2 <- M_A
+        DevBuf A2, A3;
+        AWG_TRY(assemble_local(h, (double*)h->val.p, (double*)A1.p));
+        if (h->n_minus_all > 0) {
+            k_add_nbr_MB<<<gblk, 256, 0, s>>>((int*)h->ns.p, (int64_t*)h->dense_off.p, (int*)h->sub_ptr.p,
+                                              (int*)h->sub_idx.p, (int*)h->inc_ptr.p, (int*)h->inc_pos.p,
+                                              (int*)h->inc_sub.p, (int*)h->nm_ptr.p, (int64_t*)h->vm_off.p,
+                                              (double*)h->Vm.p, (double*)h->lam_m.p, (double*)A1.p);
+            AWG_LAUNCH();
         }
-        AWG_TRY(upload(h, dms, hms.data(), nsel * sizeof(int)));
-        AWG_TRY(upload(h, dos, hos.data(), nsel * sizeof(int64_t)));
-        AWG_CUDA(cudaMemsetAsync(h->flag.p, 0, sizeof(int), s));
-        AWG_TRY(potrf_batched(h, (double*)A1.p, (int*)dms.p, (int64_t*)dos.p, nsel, maxsel, (int*)h->flag.p, s));
-        AWG_TRY(check_flag(h, FLAG_NOT_SPD, AWG_ERR_NOT_SPD));
-        AWG_TRY(trtri_batched(h, (double*)A1.p, (int*)dms.p, (int64_t*)dos.p, nsel, maxsel, s));
-        AWG_TRY(dalloc(h, A3, (size_t)h->dense_total * 8));
-        {
-            std::vector<GemmDesc> d1, d2;
-            const double* Li = (const double*)A1.p;
-            for (int t : sel) {
-                const int m = h->h_ns[t];
-                const int64_t o = h->h_dense_off[t];
-                d1.push_back({Li + o, (double*)A2.p + o, (double*)A3.p + o, m, m, m, m, m, m, 0, 0, 1.0, 0.0});
-                d2.push_back({(double*)A3.p + o, Li + o, (double*)A2.p + o, m, m, m, m, m, m, 0, 1, 1.0, 0.0});
-            }
-            AWG_TRY(gemm_batched(h, d1, s));  // A3 = L^-1 M_A
-            AWG_TRY(gemm_batched(h, d2, s));  // A2 = A3 L^-T
-        }
-        dfree(h, A3);
-        k_symmetrize<<<dim3(nsel, 16), 256, 0, s>>>((int*)dms.p, (int64_t*)dos.p, (double*)A2.p);
+        AWG_TRY(dalloc(h, A2, (size_t)h->dense_total * 8));
+        AWG_TRY(assemble_local(h, (double*)h->bval.p, (double*)A2.p));
+        k_form_MA<<<gblk, 256, 0, s>>>((int*)h->ns.p, (int64_t*)h->dense_off.p, (int*)h->sub_ptr.p,
+                                       (int*)h->sub_idx.p, (double*)h->dvec.p, (int*)h->nm_ptr.p,
+                                       (int64_t*)h->vm_off.p, (double*)h->Vm.p, (double*)h->lam_m.p,
+                                       (double*)A2.p);
         AWG_LAUNCH();
-        std::vector<int> mcs, mptr;
-        AWG_CUDA(cudaMemsetAsync(h->flag.p, 0, sizeof(int), s));
-        AWG_TRY(eig_select_batched(h, (double*)A2.p, (int*)dms.p, (int64_t*)dos.p, hms, nsel, maxsel, 1,
-                                   h->tau, mc_sel, mcs, Q, qoff, qvals, mptr, s));
-        AWG_TRY(check_flag(h, FLAG_EIG, AWG_ERR_EIG));
-    }
-    {
-        std::vector<int> mc(N, 0);
-        for (int t = 0; t < N; t++)
-            if (h->opt.geneo_solver != 0 && gi.ecount[t] >= 0) mc[t] = h->h_nm[t] + gi.ecount[t];
-        for (int k = 0; k < nsel; k++) mc[sel[k]] = mc_sel[k];
-        h->h_modes = mc;
-        h->h_mode_ptr.assign(N + 1, 0);
-        h->h_z_off.assign(N + 1, 0);
-        for (int t = 0; t < N; t++) {
-            h->h_mode_ptr[t + 1] = h->h_mode_ptr[t] + mc[t];
-            h->h_z_off[t + 1] = h->h_z_off[t] + (int64_t)h->h_ns[t] * mc[t];
-        }
-        h->n0 = h->h_mode_ptr[N];
-        AWG_TRY(upload(h, h->modes, mc.data(), N * sizeof(int)));
-        AWG_TRY(upload(h, h->mode_ptr, h->h_mode_ptr.data(), (N + 1) * sizeof(int)));
-        AWG_TRY(upload(h, h->z_off, h->h_z_off.data(), (N + 1) * sizeof(int64_t)));
-        AWG_TRY(dalloc(h, h->Z, std::max<size_t>(8, (size_t)h->h_z_off[N] * 8)));
+        // Block eigensolver first (it reads M_A and M_B and keeps them); the
+        // pencils it does not certify go to the dense eigensolver below.
+        GeneoIter gi;
+        std::vector<int> sel;
+        h->geneo_its_max = 0;
+        h->geneo_its_sum = 0;
         if (h->opt.geneo_solver != 0) {
-            AWG_TRY(geneo_block_pack(h, gi, (int64_t*)h->z_off.p, (double*)h->Z.p));
-            geneo_block_free(h, gi);
+            DevBuf prm;
+            if (h->opt.geneo_solver == 2)
+                AWG_TRY(upload(h, prm, h->h_learned.data(), LEARNED_NPARAM * sizeof(double)));
+            AWG_TRY(geneo_block_solve(h, (double*)A2.p, (double*)A1.p, (double*)prm.p, h->opt.geneo_block,
+                                      h->opt.geneo_maxit, 1e-13, gi));
+            dfree(h, prm);
+            for (int t = 0; t < N; t++) {
+                if (gi.ecount[t] < 0) sel.push_back(t);
+                h->geneo_its_max = std::max(h->geneo_its_max, gi.its[t]);
+                h->geneo_its_sum += gi.its[t];
+            }
+        } else {
+            for (int t = 0; t < N; t++) sel.push_back(t);
         }
-        std::vector<GemmDesc> d;
-        const double* Li = (const double*)A1.p;
-        for (int k = 0; k < nsel; k++) {
-            const int t = sel[k], m = h->h_ns[t], c = mc_sel[k];
-            if (c == 0) continue;
-            d.push_back({Li + h->h_dense_off[t], (double*)Q.p + qoff[k], (double*)h->Z.p + h->h_z_off[t], m, c, m,
-                         m, m, m, 1, 0, 1.0, 0.0});  // Y = L^-T Q
+        h->geneo_dense = (int)sel.size();
+        // dense eigensolver on that subset: M_B = L L^T, eigenpairs of
+        // L^-1 M_A L^-T below tau, Y = L^-T Q
+        const int nsel = (int)sel.size();
+        std::vector<int> mc_sel;
+        std::vector<int64_t> qoff;
+        DevBuf Q, qvals, dms, dos;
+        if (nsel > 0) {
+            std::vector<int> hms(nsel);
+            std::vector<int64_t> hos(nsel);
+            int maxsel = 1;
+            for (int k = 0; k < nsel; k++) {
+                hms[k] = h->h_ns[sel[k]];
+                hos[k] = h->h_dense_off[sel[k]];
+                maxsel = std::max(maxsel, hms[k]);
+            }
+            AWG_TRY(upload(h, dms, hms.data(), nsel * sizeof(int)));
+            AWG_TRY(upload(h, dos, hos.data(), nsel * sizeof(int64_t)));
+            AWG_CUDA(cudaMemsetAsync(h->flag.p, 0, sizeof(int), s));
+            AWG_TRY(potrf_batched(h, (double*)A1.p, (int*)dms.p, (int64_t*)dos.p, nsel, maxsel, (int*)h->flag.p, s));
+            AWG_TRY(check_flag(h, FLAG_NOT_SPD, AWG_ERR_NOT_SPD));
+            AWG_TRY(trtri_batched(h, (double*)A1.p, (int*)dms.p, (int64_t*)dos.p, nsel, maxsel, s));
+            AWG_TRY(dalloc(h, A3, (size_t)h->dense_total * 8));
+            {
+                std::vector<GemmDesc> d1, d2;
+                const double* Li = (const double*)A1.p;
+                for (int t : sel) {
+                    const int m = h->h_ns[t];
+                    const int64_t o = h->h_dense_off[t];
+                    d1.push_back({Li + o, (double*)A2.p + o, (double*)A3.p + o, m, m, m, m, m, m, 0, 0, 1.0, 0.0});
+                    d2.push_back({(double*)A3.p + o, Li + o, (double*)A2.p + o, m, m, m, m, m, m, 0, 1, 1.0, 0.0});
+                }
+                AWG_TRY(gemm_batched(h, d1, s));  // A3 = L^-1 M_A
+                AWG_TRY(gemm_batched(h, d2, s));  // A2 = A3 L^-T
+            }
+            dfree(h, A3);
+            k_symmetrize<<<dim3(nsel, 16), 256, 0, s>>>((int*)dms.p, (int64_t*)dos.p, (double*)A2.p);
+            AWG_LAUNCH();
+            std::vector<int> mcs, mptr;
+            AWG_CUDA(cudaMemsetAsync(h->flag.p, 0, sizeof(int), s));
+            AWG_TRY(eig_select_batched(h, (double*)A2.p, (int*)dms.p, (int64_t*)dos.p, hms, nsel, maxsel, 1,
+                                       h->tau, mc_sel, mcs, Q, qoff, qvals, mptr, s));
+            AWG_TRY(check_flag(h, FLAG_EIG, AWG_ERR_EIG));
         }
-        AWG_TRY(gemm_batched(h, d, s));
-        AWG_CUDA(cudaStreamSynchronize(s));
-        for (DevBuf* bb : {&Q, &qvals, &dms, &dos}) dfree(h, *bb);
+        {
+            std::vector<int> mc(N, 0);
+            for (int t = 0; t < N; t++)
+                if (h->opt.geneo_solver != 0 && gi.ecount[t] >= 0) mc[t] = h->h_nm[t] + gi.ecount[t];
+            for (int k = 0; k < nsel; k++) mc[sel[k]] = mc_sel[k];
+            h->h_modes = mc;
+            h->h_mode_ptr.assign(N + 1, 0);
+            h->h_z_off.assign(N + 1, 0);
+            for (int t = 0; t < N; t++) {
+                h->h_mode_ptr[t + 1] = h->h_mode_ptr[t] + mc[t];
+                h->h_z_off[t + 1] = h->h_z_off[t] + (int64_t)h->h_ns[t] * mc[t];
+            }
+            h->n0 = h->h_mode_ptr[N];
+            AWG_TRY(upload(h, h->modes, mc.data(), N * sizeof(int)));
+            AWG_TRY(upload(h, h->mode_ptr, h->h_mode_ptr.data(), (N + 1) * sizeof(int)));
+            AWG_TRY(upload(h, h->z_off, h->h_z_off.data(), (N + 1) * sizeof(int64_t)));
+            AWG_TRY(dalloc(h, h->Z, std::max<size_t>(8, (size_t)h->h_z_off[N] * 8)));
+            if (h->opt.geneo_solver != 0) {
+                AWG_TRY(geneo_block_pack(h, gi, (int64_t*)h->z_off.p, (double*)h->Z.p));
+                geneo_block_free(h, gi);
+            }
+            std::vector<GemmDesc> d;
+            const double* Li = (const double*)A1.p;
+            for (int k = 0; k < nsel; k++) {
+                const int t = sel[k], m = h->h_ns[t], c = mc_sel[k];
+                if (c == 0) continue;
+                d.push_back({Li + h->h_dense_off[t], (double*)Q.p + qoff[k], (double*)h->Z.p + h->h_z_off[t], m, c, m,
+                             m, m, m, 1, 0, 1.0, 0.0});  // Y = L^-T Q
+            }
+            AWG_TRY(gemm_batched(h, d, s));
+            AWG_CUDA(cudaStreamSynchronize(s));
+            for (DevBuf* bb : {&Q, &qvals, &dms, &dos}) dfree(h, *bb);
+        }
+        dfree(h, A2);
     }
-    dfree(h, A2);
-    // H^AS_+ (Thm. 3): the local solvers become (R^s A_+ R^sT)^-1, after the
-    // GenEO solve (whose block solver applies the H^NN local operators)
-    if (h->opt.h2 != AWG_H2_NN_HYB) AWG_TRY(build_local_as_plus(h, (double*)A1.p));
+    // H^AS_+ (Thm. 3) / H^AS (Thm. 5): the local solvers become
+    // (R^s A_+ R^sT)^-1 / (R^s A R^sT)^-1, after the GenEO solve (whose block
+    // solver applies the H^NN local operators)
+    if (h->opt.h2 != AWG_H2_NN_HYB) AWG_TRY(build_local_as(h, (double*)A1.p, h->opt.h2 != AWG_H2_AS_HYB));
     dfree(h, A1);
     double t3 = now_ms();
     h->setup_ms[3] = t3 - t2;

@@ -1,13 +1,16 @@
-"""The H_2 choices of Thm. 3 on the GPU (H^AS_+,hyb(tau_flat) and
-H^AS_+,ad(tau_flat): local solvers (R^s A_+ R^sT)^-1, coarse space of the
-GenEO pencil below 1 / tau_flat) against the CPU oracle on the same seeded
-inputs, through the C ABI:
+"""The other H_2 choices on the GPU against the CPU oracle on the same
+seeded inputs, through the C ABI: H^AS_+,hyb(tau_flat) and
+H^AS_+,ad(tau_flat) of Thm. 3 (local solvers (R^s A_+ R^sT)^-1, coarse space
+of the GenEO pencil below 1 / tau_flat) and H^AS_hyb(tau_sharp, tau_flat) of
+Thm. 5 (local solvers (R^s A R^sT)^-1, coarse space of two pencils; tau_sharp
+= 0.5 so that the second pencil contributes on the channel and random
+problems):
 
 * bit-exact: eigenvalue counts and GenEO mode counts;
 * every stage of the single-RHS apply (H^AS_+, H_2, the three H_3) and of
-  the block apply within 1e-11 relative, or kappa * eps with kappa =
-  max_s cond(R^s A_+ R^sT) where the local solves are ill-conditioned; the
-  float32 forms within 1e-4;
+  the block apply within 1e-11 relative, or kappa * eps with kappa the
+  largest condition number of the local matrices (R^s A_+ R^sT or R^s A R^sT)
+  where the local solves are ill-conditioned; the float32 forms within 1e-4;
 * PCG: true relative residual <= 1e-8 and iterations within 5 % of the
   oracle's PCG with the same preconditioner.
 """
@@ -26,6 +29,8 @@ pytestmark = pytest.mark.gpu
 APPLY_RTOL = 1e-11
 MIXED_RTOL = 1e-4
 TAU_FLAT = 10.0
+TAU_SHARP_AS = 0.5
+H2S = ("asp_hyb", "asp_ad", "as_hyb")
 
 CASES = {
     "channels24": lambda: gi.channels2d(24, q=3, nchan=3, contrast=1e3, seed=5, overlap=2, tau=0.1),
@@ -38,28 +43,33 @@ _SOLVERS = {}
 
 
 def _oracle(name, h2):
-    """One oracle setup per problem: both choices share V^0_AS,+(tau_flat)
-    (Thm. 3) and W, so the additive one reuses the hybrid one's pieces."""
-    if name not in _ORACLE:
+    """One oracle setup per problem and coarse space: the two AS_+ choices
+    share V^0_AS,+(tau_flat) (Thm. 3) and W, so the additive one reuses the
+    hybrid one's pieces."""
+    fam = "as" if h2 == "as_hyb" else "asp"
+    if (name, fam) not in _ORACLE:
         p = CASES[name]()
-        _ORACLE[name] = (p, O.setup_problem(p, dense=p.n <= 6000, h2="asp_hyb", tau_flat=TAU_FLAT))
-    p, st = _ORACLE[name]
-    return p, (st if h2 == "asp_hyb" else dataclasses.replace(st, h2=h2, as_cho=st.as_cho))
+        kw = {"h2": "as_hyb", "tau": TAU_SHARP_AS} if fam == "as" else {"h2": "asp_hyb"}
+        _ORACLE[(name, fam)] = (p, O.setup_problem(p, dense=p.n <= 6000, tau_flat=TAU_FLAT, **kw))
+    p, st = _ORACLE[(name, fam)]
+    return p, (st if st.h2 == h2 else dataclasses.replace(st, h2=h2, as_cho=st.as_cho))
 
 
 def _pair(name, h2):
     key = (name, h2)
     if key not in _SOLVERS:
-        from paper_2106_10913_gb300 import AWGSolver, H2_ASP_AD, H2_ASP_HYB
+        from paper_2106_10913_gb300 import AWGSolver, H2_AS_HYB, H2_ASP_AD, H2_ASP_HYB
         p, st = _oracle(name, h2)
-        sol = AWGSolver(p.rowptr, p.colidx, p.val, p.part, p.nparts, p.overlap, p.tau, precisions=0b1011,
-                        h2={"asp_hyb": H2_ASP_HYB, "asp_ad": H2_ASP_AD}[h2], tau_flat=TAU_FLAT)
+        tau = TAU_SHARP_AS if h2 == "as_hyb" else p.tau
+        sol = AWGSolver(p.rowptr, p.colidx, p.val, p.part, p.nparts, p.overlap, tau, precisions=0b1011,
+                        h2={"asp_hyb": H2_ASP_HYB, "asp_ad": H2_ASP_AD, "as_hyb": H2_AS_HYB}[h2],
+                        tau_flat=TAU_FLAT)
         _SOLVERS[key] = (p, sol, st)
     return _SOLVERS[key]
 
 
-@pytest.fixture(scope="module", params=[(c, h) for c in CASES for h in ("asp_hyb", "asp_ad")],
-                ids=[f"{c}-{h}" for c in CASES for h in ("asp_hyb", "asp_ad")])
+@pytest.fixture(scope="module", params=[(c, h) for c in CASES for h in H2S],
+                ids=[f"{c}-{h}" for c in CASES for h in H2S])
 def pair(request):
     return _pair(*request.param)
 
@@ -70,7 +80,7 @@ def _rel(a, b):
 
 def _ref_op(st, stage):
     return {
-        "hnn": lambda v: O.H_plus_AS_apply(st, v),
+        "hnn": lambda v: O.H1_apply(st, v),
         "h2": lambda v: O.H2_apply(st, v),
         "h3ad": lambda v: O.H3_ad_apply(st, v),
         "h3hyb": lambda v: O.H3_hyb_apply(st, v),
@@ -80,6 +90,13 @@ def _ref_op(st, stage):
 
 def _tol(st):
     return max(APPLY_RTOL, O.local_condition(st) * np.finfo(float).eps)
+
+
+def test_second_pencil_contributes():
+    """The H^AS_hyb cases exercise both pencils of Thm. 5."""
+    for name in ("channels24", "random_spd60", "channels64"):
+        _, st = _oracle(name, "as_hyb")
+        assert sum(k2 for _, k2 in st.geneo_split) > 0, name
 
 
 def test_counts_exact(pair):

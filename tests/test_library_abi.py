@@ -67,7 +67,7 @@ def test_host_only_calls(lib):
     d = pkg.default_options()
     assert d.block_tensor_cores == 1 and d.h2 == pkg.H2_NN_HYB and d.tau_flat == 10.0
     # H_2 choice and tau_flat are checked before any device work
-    for bad in ({"h2": 3}, {"h2": -1}, {"h2": pkg.H2_ASP_AD, "tau_flat": 0.0}):
+    for bad in ({"h2": 4}, {"h2": -1}, {"h2": pkg.H2_ASP_AD, "tau_flat": 0.0}):
         o = pkg.default_options(**bad)
         assert lib.awg_setup(4, 4, 1, 1, 1, 1, 1, 1, 0.1, ctypes.byref(o), None, ctypes.byref(h)) == 1
     # the block and graph-driven entry points reject bad arguments before
