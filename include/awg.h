@@ -265,6 +265,9 @@ awg_status awg_pcg(awg_handle h, int precision, const double* d_b, double* d_x,
  *   9  F = W^T A W                              float64[n_minus^2]
  *  10  W (column-major n x n_minus)             float64[n*n_minus]
  *  11  Z (column-major n x n0)                  float64[n*n0]
+ *  12  the blocks of Z: per subdomain s, Y^s    float64[sum_s n^s m^s]
+ *      column-major n^s x m^s (rows in the order of Omega^s), one after
+ *      the other
  * `count` is the capacity of h_out in elements; AWG_ERR_INVALID_ARG if it
  * is too small.
  */

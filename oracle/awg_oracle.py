@@ -298,22 +298,28 @@ def assemble_dense(st: Setup, which: str) -> np.ndarray:
     return M
 
 
-def local_A_plus_block(st: Setup, s: int) -> np.ndarray:
+def local_A_plus_from(A: sp.csr_matrix, subs, split_of, s: int) -> np.ndarray:
     """R^s A_+ R^sT through Section 4.4 item 4:
-    R^s A R^sT - sum_t R^s R^tT V^t_- L^t_- V^t_-^T R^t R^sT."""
-    idx = st.subs[s]
-    M = st.A[idx][:, idx].toarray()
-    pos_s = {int(g): k for k, g in enumerate(idx)}
-    for t, (jdx, spl) in enumerate(zip(st.subs, st.splits)):
-        if spl.n_minus == 0:
-            continue
+    R^s A R^sT - sum_t R^s R^tT V^t_- L^t_- V^t_-^T R^t R^sT, with the
+    eigen-split of subdomain t given by split_of(t) (asked only for the
+    subdomains that meet Omega^s)."""
+    idx = subs[s]
+    M = A[idx][:, idx].toarray()
+    for t, jdx in enumerate(subs):
         common, ps, pt = np.intersect1d(idx, jdx, return_indices=True)
         if common.size == 0:
             continue
+        spl = split_of(t)
+        if spl.n_minus == 0:
+            continue
         Vt = spl.V_minus[pt]
         M[np.ix_(ps, ps)] += (Vt * (-spl.L_minus)) @ Vt.T
-    del pos_s
     return M
+
+
+def local_A_plus_block(st: Setup, s: int) -> np.ndarray:
+    """R^s A_+ R^sT of a set-up problem (Section 4.4 item 4)."""
+    return local_A_plus_from(st.A, st.subs, lambda t: st.splits[t], s)
 
 
 # ---------------------------------------------------------------------------
@@ -389,6 +395,34 @@ def Y_L(M_A: np.ndarray, M_B: np.ndarray, tau: float):
     return Yfull[:, :mL], lam
 
 
+def geneo_local(spl, Ds: np.ndarray, M_B: np.ndarray, tau: float):
+    """Y_L(tau, D^s^-1 A^s_+ D^s^-1, M_B) of one subdomain (Def. 9, Thm. 4)."""
+    M_A = (spl.A_plus() / Ds[:, None]) / Ds[None, :]
+    return Y_L(0.5 * (M_A + M_A.T), 0.5 * (M_B + M_B.T), tau)
+
+
+def sampled_local_geneo(A: sp.csr_matrix, subs, Ds, B: sp.csr_matrix, samples, tau: float,
+                        zero_rtol: float = ZERO_EIG_RTOL):
+    """Def. 6 and Thm. 4's pencil on chosen subdomains of a problem too large
+    for ``setup``: the eigen-splits of the sampled subdomains and of every
+    subdomain that meets them (the A_- terms of R^s A_+ R^sT), then Y_L of
+    each sampled pencil.  Returns, per sample, (eigen-split, Y_L, pencil
+    spectrum, R^s A_+ R^sT)."""
+    cache = {}
+
+    def split_of(t):
+        if t not in cache:
+            cache[t] = eigen_split(local_B(B, subs[t]), zero_rtol)
+        return cache[t]
+
+    out = []
+    for s in samples:
+        M_B = local_A_plus_from(A, subs, split_of, s)
+        Y, lam = geneo_local(split_of(s), Ds[s], M_B, tau)
+        out.append((split_of(s), Y, lam, M_B))
+    return out
+
+
 def geneo_nn(st: Setup, tau: float) -> None:
     """V^0_NN(tau) = sum_s range(R^sT Y_L(tau, D^s^-1 A^s_+ D^s^-1,
     R^s A_+ R^sT)) and E = R^0 A_+ R^0T (Thm. 4)."""
@@ -396,14 +430,7 @@ def geneo_nn(st: Setup, tau: float) -> None:
     col = 0
     st.Y, st.geneo_lam = [], []
     for s, (idx, Ds, spl) in enumerate(zip(st.subs, st.Ds, st.splits)):
-        M_A = (spl.A_plus() / Ds[:, None]) / Ds[None, :]
-        M_A = 0.5 * (M_A + M_A.T)
-        if st.dense:
-            M_B = st.A_plus_dense[np.ix_(idx, idx)]
-        else:
-            M_B = local_A_plus_block(st, s)
-        M_B = 0.5 * (M_B + M_B.T)
-        Ys, lam = Y_L(M_A, M_B, tau)
+        Ys, lam = geneo_local(spl, Ds, local_A_plus(st, s), tau)
         st.Y.append(Ys)
         st.geneo_lam.append(lam)
         k = Ys.shape[1]

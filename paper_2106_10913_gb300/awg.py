@@ -29,7 +29,7 @@ STAGE = {"spmv": 0, "aplus": 1, "hnn": 2, "h2": 3, "h3ad": 4, "h3hyb": 5, "h3ine
 ARRAY = {"ns": (0, np.int32), "sub_idx": (1, np.int32), "n_minus": (2, np.int32),
          "n_strict": (3, np.int32), "modes": (4, np.int32), "lam_minus": (5, np.float64),
          "mmu": (6, np.float64), "dvec": (7, np.float64), "E": (8, np.float64),
-         "F": (9, np.float64), "W": (10, np.float64), "Z": (11, np.float64)}
+         "F": (9, np.float64), "W": (10, np.float64), "Z": (11, np.float64), "Z_blocks": (12, np.float64)}
 
 
 class AWGError(RuntimeError):
@@ -375,8 +375,11 @@ class AWGSolver:
 
     def array(self, what: str) -> np.ndarray:
         i = self.info
-        size = {"ns": i["nparts"], "sub_idx": i["sum_ns"], "n_minus": i["nparts"],
-                "n_strict": i["nparts"], "modes": i["nparts"], "lam_minus": i["n_minus_all"],
-                "mmu": i["nnz"], "dvec": i["n"], "E": i["n0"] ** 2, "F": i["n_minus"] ** 2,
-                "W": i["n"] * i["n_minus"], "Z": i["n"] * i["n0"]}[what]
+        if what == "Z_blocks":  # sum_s n^s m^s
+            size = int(np.dot(self.array("ns").astype(np.int64), self.array("modes").astype(np.int64)))
+        else:
+            size = {"ns": i["nparts"], "sub_idx": i["sum_ns"], "n_minus": i["nparts"],
+                    "n_strict": i["nparts"], "modes": i["nparts"], "lam_minus": i["n_minus_all"],
+                    "mmu": i["nnz"], "dvec": i["n"], "E": i["n0"] ** 2, "F": i["n_minus"] ** 2,
+                    "W": i["n"] * i["n_minus"], "Z": i["n"] * i["n0"]}[what]
         return awg_get_array(self.h, what, size)

@@ -414,6 +414,7 @@ awg_status awg_get_array(awg_handle hh, int what, void* h_out, size_t count) {
         case 8: src = h->E.p; len = (size_t)h->n0 * h->n0; esz = 8; break;
         case 9: src = h->F64.p; len = (size_t)h->n_minus * h->n_minus; esz = 8; break;
         case 10: src = h->Wcm.p; len = (size_t)h->n * h->n_minus; esz = 8; break;
+        case 12: src = h->Z.p; len = (size_t)h->h_z_off[h->N]; esz = 8; break;
         case 11: {
             // dense Z, column-major n x n0, assembled on the host from the blocks
             if (count < (size_t)h->n * h->n0) return AWG_ERR_INVALID_ARG;
