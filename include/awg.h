@@ -63,7 +63,8 @@ typedef enum {
     AWG_ERR_OOM = 7,           /* device allocation failed */
     AWG_ERR_CUDA = 8,          /* any other CUDA runtime error */
     AWG_ERR_NOT_SYMMETRIC = 9, /* the CSR pattern is not structurally symmetric */
-    AWG_ERR_STATE = 10         /* call not valid for this handle (e.g. no W) */
+    AWG_ERR_STATE = 10,        /* call not valid for this handle (e.g. no W) */
+    AWG_ERR_IO = 11            /* file not written or read, or not a handle file */
 } awg_status;
 
 /* Variant of the AWG preconditioner (Def. 10, Thm. 7). */
@@ -272,6 +273,32 @@ awg_status awg_pcg(awg_handle h, int precision, const double* d_b, double* d_x,
  * is too small.
  */
 awg_status awg_get_array(awg_handle h, int what, void* h_out, size_t count);
+
+/*
+ * Checkpoint of a set-up handle: awg_save writes to the file `path` what
+ * awg_setup computed (A, the subdomains and their incidence lists, D, M_mu,
+ * B, the eigen-splits V^s_- and Lambda^s_-, the local operators of every
+ * built storage form, the GenEO basis Z with E and E^-1, W in every built
+ * form with F^-1 (and the H_3,inex matrix where built), the options and the
+ * tuned grid sizes); awg_load makes a new handle from such a file on the
+ * current device, ordered on `stream`, without repeating the setup (the
+ * setup is the expensive part: eigenproblems and the n_- solves for W).
+ * Loaded handles apply and solve exactly as the saved one (the same bytes
+ * in every operator); what is built on first use (block-path copies,
+ * tensor-core tiles, loop graphs, the block autotuner) is built again then.
+ * The file is in the byte order and type sizes of the machine that wrote it
+ * (little-endian, LP64) and carries a format tag and version.
+ *   awg_save: synchronises the handle's streams; AWG_ERR_INVALID_ARG for a
+ *     NULL argument, AWG_ERR_IO if the file cannot be written (a partial
+ *     file may be left), AWG_ERR_CUDA on a copy error.
+ *   awg_load: *out = NULL on any error; AWG_ERR_INVALID_ARG for a NULL
+ *     argument; AWG_ERR_IO if the file cannot be read, has another format
+ *     tag, version or options layout, or is truncated (checked before any
+ *     device work for the header); AWG_ERR_OOM, AWG_ERR_CUDA.  Free the
+ *     handle with awg_destroy.
+ */
+awg_status awg_save(awg_handle h, const char* path);
+awg_status awg_load(const char* path, void* stream, awg_handle* out);
 
 /* Kernel classes timed by awg_profile (index into the arrays it returns). */
 enum {

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libawg.so")
 AWG_OK = 0
 STATUS = {0: "AWG_OK", 1: "AWG_ERR_INVALID_ARG", 2: "AWG_ERR_MIN_OVERLAP", 3: "AWG_ERR_NOT_SPD",
           4: "AWG_ERR_EIG", 5: "AWG_ERR_BREAKDOWN", 6: "AWG_ERR_MAXIT", 7: "AWG_ERR_OOM",
-          8: "AWG_ERR_CUDA", 9: "AWG_ERR_NOT_SYMMETRIC", 10: "AWG_ERR_STATE"}
+          8: "AWG_ERR_CUDA", 9: "AWG_ERR_NOT_SYMMETRIC", 10: "AWG_ERR_STATE", 11: "AWG_ERR_IO"}
 H3_AD, H3_HYB, H3_INEX = 0, 1, 2
 FP64, MIXED_FP32, MIXED_BF16, MIXED_FP16 = 0, 1, 2, 3
 # H^NN_hyb(tau) (Thm. 4), H^AS_+,hyb / ,ad(tau_flat) (Thm. 3), H^AS_hyb(tau, tau_flat) (Thm. 5)
@@ -65,7 +65,7 @@ EXPORTED = ["awg_default_options", "awg_status_string", "awg_setup", "awg_destro
             "awg_get_info", "awg_apply", "awg_apply_stage", "awg_pcg", "awg_get_array",
             "awg_profile", "awg_profile_read", "awg_apply_hnn_noalloc", "awg_learned_data",
             "awg_learned_forward", "awg_learned_grad", "awg_learned_train", "awg_profile_trace",
-            "awg_apply_block", "awg_pcg_block", "awg_pcg_block_async"]
+            "awg_apply_block", "awg_pcg_block", "awg_pcg_block_async", "awg_save", "awg_load"]
 LEARNED_NPARAM, LEARNED_NFEAT = 385, 5
 GENEO_DENSE, GENEO_BLOCK, GENEO_LEARNED = 0, 1, 2
 PROF_NAMES = ["spmv", "local", "wt", "wd", "coarse", "subdomain", "prolong", "vector"]
@@ -125,6 +125,10 @@ def load_library(path: str = LIB_PATH):
     lib.awg_learned_grad.restype = I
     lib.awg_learned_train.argtypes = [I, P, P, P, I, D, I, P, P]
     lib.awg_learned_train.restype = I
+    lib.awg_save.argtypes = [P, ctypes.c_char_p]
+    lib.awg_save.restype = I
+    lib.awg_load.argtypes = [ctypes.c_char_p, P, ctypes.POINTER(P)]
+    lib.awg_load.restype = I
     _lib = lib
     return lib
 
@@ -174,6 +178,18 @@ def awg_setup(rowptr, colidx, val, partition, nparts: int, overlap: int, tau: fl
 
 def awg_destroy(h):
     load_library().awg_destroy(h)
+
+
+def awg_save(h, path) -> None:
+    """Write the set-up handle to the file `path` (awg_load reads it back)."""
+    _check(load_library().awg_save(h, os.fsencode(path)), "awg_save")
+
+
+def awg_load(path, stream=None) -> ctypes.c_void_p:
+    """A new handle from a file written by awg_save, on the current device."""
+    h = ctypes.c_void_p()
+    _check(load_library().awg_load(os.fsencode(path), _stream_ptr(stream), ctypes.byref(h)), "awg_load")
+    return h
 
 
 def awg_get_info(h) -> dict:
@@ -348,6 +364,19 @@ class AWGSolver:
         self.h = awg_setup(self.rowptr, self.colidx, self.val, part, nparts, overlap, tau,
                            default_options(**opts))
         self.info = awg_get_info(self.h)
+
+    @classmethod
+    def load(cls, path, device="cuda"):
+        """A solver on the handle stored in `path` by ``save`` (no setup)."""
+        self = cls.__new__(cls)
+        self.device = device
+        self.h = awg_load(path)
+        self.info = awg_get_info(self.h)
+        self.n = self.info["n"]
+        return self
+
+    def save(self, path):
+        awg_save(self.h, path)
 
     def close(self):
         if self.h is not None:

@@ -52,7 +52,7 @@ awg_status read_flag(Handle* h, int* out) {
 awg_status pcg1(Handle* h, int prec, int stage, const double* b, double* x, double rtol, int* iters,
                 double* relres, cudaStream_t s);
 
-static void free_all(Handle* h) {
+void free_all(Handle* h) {
     DevBuf* bufs[] = {&h->rowptr, &h->colidx, &h->val, &h->ns, &h->sub_ptr, &h->sub_idx,
                       &h->inc_ptr, &h->inc_pos, &h->inc_sub, &h->pos_sub, &h->dvec, &h->mmu,
                       &h->bval, &h->dense_off, &h->g32_off, &h->nm, &h->nstrict, &h->nm_ptr, &h->vm_off,
@@ -114,6 +114,24 @@ static void free_all(Handle* h) {
     h->h_scal = nullptr;
 }
 
+// Streams, events, pinned host words and the status flag of a handle (the
+// runtime part of a handle, shared by awg_setup and awg_load).
+awg_status runtime_init(Handle* h) {
+    AWG_CUDA(cudaMallocHost(&h->h_flag, sizeof(int)));
+    AWG_CUDA(cudaMallocHost(&h->h_scal, 16 * sizeof(double)));
+    int prio_least = 0, prio_greatest = 0;
+    AWG_CUDA(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+    AWG_CUDA(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_least));
+    AWG_CUDA(cudaStreamCreateWithPriority(&h->hp, cudaStreamNonBlocking, prio_greatest));
+    AWG_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    AWG_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    AWG_CUDA(cudaEventCreateWithFlags(&h->ev_mid, cudaEventDisableTiming));
+    AWG_CUDA(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    AWG_CUDA(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    AWG_TRY(dalloc(h, h->flag, sizeof(int)));
+    return AWG_OK;
+}
+
 static double now_ms() {
     return std::chrono::duration<double, std::milli>(
                std::chrono::steady_clock::now().time_since_epoch())
@@ -160,6 +178,7 @@ const char* awg_status_string(awg_status s) {
         case AWG_ERR_CUDA: return "AWG_ERR_CUDA";
         case AWG_ERR_NOT_SYMMETRIC: return "AWG_ERR_NOT_SYMMETRIC";
         case AWG_ERR_STATE: return "AWG_ERR_STATE";
+        case AWG_ERR_IO: return "AWG_ERR_IO";
     }
     return "AWG_ERR_UNKNOWN";
 }
@@ -168,18 +187,7 @@ static awg_status setup_impl(Handle* h, const int* d_rowptr, const int* d_colidx
                              const double* d_val, const int* d_part) {
     cudaStream_t s = h->stream;
     const double t0 = now_ms();
-    AWG_CUDA(cudaMallocHost(&h->h_flag, sizeof(int)));
-    AWG_CUDA(cudaMallocHost(&h->h_scal, 16 * sizeof(double)));
-    int prio_least = 0, prio_greatest = 0;
-    AWG_CUDA(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
-    AWG_CUDA(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_least));
-    AWG_CUDA(cudaStreamCreateWithPriority(&h->hp, cudaStreamNonBlocking, prio_greatest));
-    AWG_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-    AWG_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
-    AWG_CUDA(cudaEventCreateWithFlags(&h->ev_mid, cudaEventDisableTiming));
-    AWG_CUDA(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
-    AWG_CUDA(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
-    AWG_TRY(dalloc(h, h->flag, sizeof(int)));
+    AWG_TRY(runtime_init(h));
     AWG_TRY(dalloc(h, h->rowptr, (size_t)(h->n + 1) * sizeof(int)));
     AWG_TRY(dalloc(h, h->colidx, (size_t)h->nnz * sizeof(int)));
     AWG_TRY(dalloc(h, h->val, (size_t)h->nnz * sizeof(double)));

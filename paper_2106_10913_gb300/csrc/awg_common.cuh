@@ -228,6 +228,10 @@ inline void extra_launches(Handle* h, int k) { h->launches += (h->prof != 0) * k
 awg_status dalloc(Handle* h, DevBuf& b, size_t bytes);
 void dfree(Handle* h, DevBuf& b);
 awg_status read_flag(Handle* h, int* out);
+// api.cu: streams, events, pinned words and the flag of a new handle; release
+// of everything a handle holds
+awg_status runtime_init(Handle* h);
+void free_all(Handle* h);
 awg_status upload(Handle* h, DevBuf& b, const void* src, size_t bytes);
 
 // ------------------------------------------------------------------ device helpers

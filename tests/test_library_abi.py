@@ -73,6 +73,7 @@ def test_host_only_calls(lib):
     # the block and graph-driven entry points reject bad arguments before
     # touching the device
     assert lib.awg_apply_block(None, 4, 0, None, None, 1, 1, None) == 1
+    assert lib.awg_status_string(11) == b"AWG_ERR_IO"
     assert lib.awg_pcg_block(None, 0, None, None, 1, 1, 1e-8, None, None, None) == 1
     assert lib.awg_pcg_block_async(None, 0, None, None, 1, 1, 1e-8, None, None, None, None) == 1
 
@@ -85,3 +86,30 @@ def test_product_does_not_import_oracle():
             if f.endswith(".py"):
                 txt = open(os.path.join(dp, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_checkpoint_file_errors(lib, tmp_path):
+    """awg_save / awg_load reject bad arguments and files that are not
+    handle files (missing, another tag, another version, truncated, tables
+    that disagree with the scalars) before any device work."""
+    import struct
+    import paper_2106_10913_gb300 as pkg
+    h = ctypes.c_void_p(123)
+    assert lib.awg_save(None, b"x") == 1
+    assert lib.awg_load(None, None, ctypes.byref(h)) == 1 and not h.value
+    assert lib.awg_load(b"x", None, None) == 1
+    assert lib.awg_load(str(tmp_path / "missing").encode(), None, ctypes.byref(h)) == 11 and not h.value
+    osz = ctypes.sizeof(pkg.awg.awg_options)
+    cases = {
+        "tag": b"NOTAHNDL" + struct.pack("<II", 1, osz),
+        "version": b"AWGHNDL\n" + struct.pack("<II", 2, osz),
+        "options": b"AWGHNDL\n" + struct.pack("<II", 1, osz + 8),
+        "truncated": b"AWGHNDL\n" + struct.pack("<II", 1, osz) + b"\0" * 16,
+        "inconsistent": b"AWGHNDL\n" + struct.pack("<II", 1, osz) + b"\0" * 4096,
+    }
+    for name, data in cases.items():
+        f = tmp_path / name
+        f.write_bytes(data)
+        h = ctypes.c_void_p(123)
+        assert lib.awg_load(str(f).encode(), None, ctypes.byref(h)) == 11, name
+        assert not h.value, name
