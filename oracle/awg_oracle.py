@@ -617,6 +617,31 @@ def build_W(st: Setup) -> None:
     st.F_cho = sla.cho_factor(st.F, lower=True)
 
 
+def truncate_W(st: Setup, theta: float) -> Setup:
+    """A sparser second coarse space (the conclusion, Section 6, leaves
+    sparser approximations of it open): a copy of the setup whose W drops
+    the entries below theta * max_i |W_ij| of their column, with F = W^T A W
+    rebuilt from the truncated W so that H_3 stays spd.  theta = 0 keeps
+    W.  Thm. 8's bounds need range(W) = range(A_+^-1 V_-) and no longer
+    hold; W F^-1 W^T A is still an A-orthogonal projector.  Columns that
+    truncation makes linearly dependent leave F singular: recorded in
+    info["F_singular"] (F_cho = None)."""
+    import dataclasses
+    if st.n_minus == 0:
+        return dataclasses.replace(st, info=dict(st.info))
+    cmax = np.abs(st.W).max(axis=0)
+    Wt = np.where(np.abs(st.W) >= theta * cmax[None, :], st.W, 0.0)
+    F = Wt.T @ (st.A @ Wt)
+    F = 0.5 * (F + F.T)
+    info = dict(st.info)
+    try:
+        cho = sla.cho_factor(F, lower=True)
+    except np.linalg.LinAlgError:
+        cho = None
+        info["F_singular"] = True
+    return dataclasses.replace(st, W=Wt, F=F, F_cho=cho, info=info)
+
+
 def coarse_F_solve(st: Setup, y: np.ndarray) -> np.ndarray:
     if st.n_minus == 0:
         return np.zeros((0,) + y.shape[1:])

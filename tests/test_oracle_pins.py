@@ -328,6 +328,34 @@ def test_sampled_geneo_matches_setup(tiny):
             assert np.max(sla.subspace_angles(Y, st.Y[s])) < 1e-10
 
 
+def test_truncated_W(tiny):
+    """The sparser second coarse space: theta = 0 keeps W and F; the kept
+    entries shrink as theta grows (theta = 0.3 drops some on every tiny
+    problem); W F^-1 W^T A stays an A-orthogonal
+    projector (so its spectrum is {0, 1}) and H_3,ad stays spd with
+    lambda(H_3,ad A) in [lambda_min(H_2 A), lambda_max(H_2 A) + 1]."""
+    p, st = tiny
+    if st.n_minus == 0:
+        pytest.skip("no second coarse space")
+    s0 = O.truncate_W(st, 0.0)
+    assert np.array_equal(s0.W, st.W) and np.allclose(s0.F, st.F, rtol=0, atol=1e-14 * np.abs(st.F).max())
+    kept = [np.count_nonzero(O.truncate_W(st, th).W) for th in (0.0, 1e-4, 1e-2, 1e-1, 1.0)]
+    assert kept == sorted(kept, reverse=True) and kept[-1] >= st.n_minus  # theta = 1 keeps each column's largest
+    tr = O.truncate_W(st, 0.3)
+    assert np.count_nonzero(tr.W) < np.count_nonzero(st.W) and not tr.info.get("F_singular")
+    Ad = st.A.toarray()
+    P = tr.W @ np.linalg.solve(tr.F, tr.W.T @ Ad)
+    assert np.allclose(P @ P, P, atol=1e-9 * np.abs(P).max())
+    AP = Ad @ P
+    assert np.allclose(AP, AP.T, atol=1e-9 * np.abs(AP).max())
+    H2 = O.dense_operator(lambda X: O.H2_apply(st, X), st.n)
+    ev2 = O.spectrum_HA(0.5 * (H2 + H2.T), Ad)
+    H3 = O.dense_operator(lambda X: O.H3_ad_apply(tr, X), st.n)
+    assert np.linalg.eigvalsh(0.5 * (H3 + H3.T)).min() > 0
+    ev = O.spectrum_HA(0.5 * (H3 + H3.T), Ad)
+    assert ev.min() >= ev2.min() * (1 - 1e-8) and ev.max() <= (ev2.max() + 1) * (1 + 1e-8)
+
+
 def test_colouring_constant_bruteforce():
     """Def. 4 on a 2x2 box partition: every pair of subdomains interacts, so
     the optimal constant is 4 and greedy must find it."""
