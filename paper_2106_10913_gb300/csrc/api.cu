@@ -57,7 +57,7 @@ void free_all(Handle* h) {
                       &h->inc_ptr, &h->inc_pos, &h->inc_sub, &h->pos_sub, &h->dvec, &h->mmu,
                       &h->bval, &h->dense_off, &h->g32_off, &h->nm, &h->nstrict, &h->nm_ptr, &h->vm_off,
                       &h->Vm, &h->lam_m, &h->sigma, &h->modes, &h->mode_ptr, &h->z_off, &h->Z,
-                      &h->E, &h->Einv, &h->wcol_ptr, &h->Wcm, &h->F64, &h->ws, &h->flag, &h->red,
+                      &h->E, &h->Einv, &h->wcol_ptr, &h->Wcm, &h->F64, &h->ws, &h->flag,
                       &h->bws, &h->bval32, &h->bvm32, &h->blam32, &h->blam64, &h->bz32,
                       &h->ul_gt, &h->ul_gtoff, &h->ul_kcpre, &h->ul_tsub, &h->ul_trt, &h->g1buf, &h->g1cnt,
                       &h->bws2};

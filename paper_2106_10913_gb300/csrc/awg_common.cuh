@@ -169,7 +169,6 @@ struct Handle {
     cudaGraphExec_t g1_exec[4] = {};
     DevBuf g1buf, g1cnt;
     DevBuf flag;                         // int status word
-    DevBuf red;                          // partial-sum scratch
     int red_blocks = 0;
     int* h_flag = nullptr;               // pinned host mirror
     double* h_scal = nullptr;            // pinned host scalars
