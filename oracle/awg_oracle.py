@@ -617,6 +617,25 @@ def build_W(st: Setup) -> None:
     st.F_cho = sla.cho_factor(st.F, lower=True)
 
 
+def build_W_pcg(st: Setup, rtol: float) -> Setup:
+    """W by the paper's own route (Section 4.4 item 2): each column
+    A_+^-1 R^sT v^s_- by PCG preconditioned with H_2 from x_0 = 0, stopped
+    at the relative tolerance rtol on the preconditioned residual (PETSc's
+    default test, with which the paper's experiments ran; Table 4 varies
+    rtol), then F = W^T A W from that W.  Returns a copy of the setup."""
+    import dataclasses
+    if st.n_minus == 0:
+        return dataclasses.replace(st, info=dict(st.info))
+    V = st.Vhat.toarray()
+    W = np.zeros_like(V)
+    for j in range(V.shape[1]):
+        W[:, j] = pcg(lambda v: A_plus_apply(st, v), V[:, j], lambda r: H2_apply(st, r), rtol=rtol,
+                      norm="preconditioned").x
+    F = W.T @ (st.A @ W)
+    F = 0.5 * (F + F.T)
+    return dataclasses.replace(st, W=W, F=F, F_cho=sla.cho_factor(F, lower=True), info=dict(st.info))
+
+
 def truncate_W(st: Setup, theta: float) -> Setup:
     """A sparser second coarse space (the conclusion, Section 6, leaves
     sparser approximations of it open): a copy of the setup whose W drops

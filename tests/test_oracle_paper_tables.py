@@ -1,8 +1,9 @@
 """The oracle against the numbers the paper prints for its worked example
 (Section 5, Tables 1 and 5), stored in tests/golden with their citation:
 the eight AWG rows of Table 1 (H_2 = H^NN_hyb(0.1), H^AS_hyb(0.1, 10),
-H^AS_+,hyb(10), H^AS_+,ad(10); H_3,ad and H_3,hyb) and three rows of
-Table 5.
+H^AS_+,hyb(10), H^AS_+,ad(10); H_3,ad and H_3,hyb), three rows of Table 5
+and the twelve rows of Table 4 (W solved inexactly by PCG, two Poisson
+ratios).
 
 The coarse-space sizes #V_0 and n_- are exact integers fixed by A, the
 subdomains and tau: they pin the splitting (Def. 5), the eigen-split
@@ -69,6 +70,27 @@ def test_paper_tables(case):
     assert abs(kappa - case["kappa"]) <= 0.05 * case["kappa"]
     if "lambda_max" in case:
         assert abs(hi - case["lambda_max"]) <= 0.05 * case["lambda_max"]
+
+
+GOLD4 = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_elasticity_table4.json")))
+
+
+@pytest.mark.parametrize("case", GOLD4["cases"], ids=[c["where"] for c in GOLD4["cases"]])
+def test_paper_table4_inexact_W(case):
+    """Table 4: W from PCG solves with A_+ preconditioned by H_2, stopped at
+    rtol (Section 4.4 item 2); kappa within 5 %, It within 2."""
+    key = ("nu", case["nu"])
+    if key not in _CACHE:
+        p = gi.paper_elasticity(layers=6, E1=1e11, E2=1e7, nu=case["nu"])
+        _CACHE[key] = (p, O.setup_problem(p, with_W=False))
+    p, st = _CACHE[key]
+    O.build_Vhat(st)
+    assert st.n0 == case["n0"] and st.n_minus == case["n_minus"]
+    sw = O.build_W_pcg(st, case["w_rtol"])
+    res = O.pcg(lambda v: st.A @ v, p.b, lambda r: O.H3_ad_apply(sw, r), rtol=1e-10, norm="preconditioned")
+    assert abs(res.iters - case["It"]) <= 2
+    lo, hi = O.lanczos_extremes(res.alphas, res.betas)
+    assert abs(hi / lo - case["kappa"]) <= 0.05 * case["kappa"]
 
 
 def test_paper_central_subdomain_modes():
