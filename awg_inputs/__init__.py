@@ -16,6 +16,7 @@ from .problems import (  # noqa: F401
     grf3d,
     elasticity2d,
     paper_elasticity,
+    paper_long_domain,
     random_spd,
     batch_channels,
     box_partition,

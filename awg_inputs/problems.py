@@ -421,6 +421,29 @@ def paper_elasticity(layers: int = 6, E1: float = 1e11, E2: float = 1e7, nu: flo
                         name=f"paper_elasticity_{layers}layers")
 
 
+def paper_long_domain(N: int, E1: float = 1e11, E2: float = 1e7, nu: float = 0.3,
+                      tau: float = 0.1) -> Problem:
+    """The weak-scaling case of Section 5 (Table 6): [0,N] x [0,1], h = 1/14,
+    hard layers (E1) for y in [1/7,2/7] and [3/7,4/7], E2 elsewhere, left
+    edge clamped, gravity load, N closed unit-square subdomains in a row
+    that share only their interfaces."""
+    nex, ney = 14 * N, 14
+    bands = [(2, 4), (6, 8)]  # element rows whose centres lie in the two layers
+
+    def E_of_row(j):
+        return E1 if any(lo <= j < hi for lo, hi in bands) else E2
+
+    def subsets_of_node(i, j):
+        return [np.nonzero((i >= 14 * sx) & (i <= 14 * (sx + 1)))[0] for sx in range(N)]
+
+    def owner_of_node(i, j):
+        return np.minimum(i // 14, N - 1).astype(np.int32)
+
+    return elasticity2d(nex, ney, float(N), 1.0, E_of_row, nu=nu, owner_of_node=owner_of_node,
+                        nparts=N, overlap=0, tau=tau, rhs="gravity", subsets_of_node=subsets_of_node,
+                        name=f"paper_long_domain_{N}")
+
+
 # ---------------------------------------------------------------------------
 # Random SPD matrices for property tests
 # ---------------------------------------------------------------------------

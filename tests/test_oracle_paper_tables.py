@@ -4,8 +4,9 @@ the eight AWG rows of Table 1 (H_2 = H^NN_hyb(0.1), H^AS_hyb(0.1, 10),
 H^AS_+,hyb(10), H^AS_+,ad(10); H_3,ad and H_3,hyb), five AWG rows of Table 2
 (Poisson's ratio; the sixth disagrees with its neighbours, see the golden
 file's note), the AWG rows of Table 3 (Young's moduli), three rows of
-Table 5 and the twelve rows of Table 4 (W solved inexactly by PCG, two
-Poisson ratios).
+Table 5, the twelve rows of Table 4 (W solved inexactly by PCG, two
+Poisson ratios) and the AWG rows of Table 6 (weak scaling on a long
+domain, 2 to 29 subdomains).
 
 The coarse-space sizes #V_0 and n_- are exact integers fixed by A, the
 subdomains and tau: they pin the splitting (Def. 5), the eigen-split
@@ -93,6 +94,23 @@ def test_paper_table4_inexact_W(case):
     res = O.pcg(lambda v: st.A @ v, p.b, lambda r: O.H3_ad_apply(sw, r), rtol=1e-10, norm="preconditioned")
     assert abs(res.iters - case["It"]) <= 2
     lo, hi = O.lanczos_extremes(res.alphas, res.betas)
+    assert abs(hi / lo - case["kappa"]) <= 0.05 * case["kappa"]
+
+
+GOLD6 = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_long_domain_table6.json")))
+
+
+@pytest.mark.parametrize("case", GOLD6["cases"], ids=[c["where"] for c in GOLD6["cases"]])
+def test_paper_table6_weak_scaling(case):
+    """Table 6: the long domain with N subdomains in a row; #V_0 and n_-
+    exact, kappa within 5 %, It within 2."""
+    p = gi.paper_long_domain(case["N"])
+    st = O.setup_problem(p)
+    assert st.n0 == case["n0"] and st.n_minus == case["n_minus"]
+    res = O.pcg(lambda v: st.A @ v, p.b, lambda r: O.H3_ad_apply(st, r), rtol=1e-10, norm="preconditioned")
+    assert abs(res.iters - case["It"]) <= 2
+    lo, hi = O.lanczos_extremes(res.alphas, res.betas)
+    assert lo >= 1.0 - 1e-6
     assert abs(hi / lo - case["kappa"]) <= 0.05 * case["kappa"]
 
 
