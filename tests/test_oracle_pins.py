@@ -356,6 +356,42 @@ def test_truncated_W(tiny):
     assert ev.min() >= ev2.min() * (1 - 1e-8) and ev.max() <= (ev2.max() + 1) * (1 + 1e-8)
 
 
+def test_Pi_projector(tiny):
+    """Thm. 4's coarse projector Pi = I - Z E^-1 Z^T A_+: Pi^2 = Pi, A_+ Pi
+    symmetric (A_+-orthogonal), Pi Z = 0, and Pi_T_apply is its transpose."""
+    p, st = tiny
+    if st.n0 == 0:
+        pytest.skip("no coarse space")
+    Ap = O.assemble_dense(st, "plus")
+    P = O.dense_operator(lambda X: O.Pi_apply(st, X), st.n)
+    PT = O.dense_operator(lambda X: O.Pi_T_apply(st, X), st.n)
+    sc = np.abs(P).max()
+    assert np.allclose(P @ P, P, atol=1e-9 * sc)
+    assert np.allclose(Ap @ P, (Ap @ P).T, atol=1e-9 * np.abs(Ap @ P).max())
+    assert np.abs(P @ st.Z.toarray()).max() <= 1e-9 * sc * np.abs(st.Z.toarray()).max()
+    assert np.allclose(PT, P.T, atol=1e-12 * sc)
+
+
+def test_lanczos_extremes_and_spectrum(tiny):
+    """spectrum_HA against numpy's general eigensolver on H A, and the
+    Lanczos extremes from the PCG coefficients (run to a tight tolerance)
+    against the exact extreme eigenvalues of H_3,ad A: inside the spectrum
+    (Ritz values interlace) and close to its ends."""
+    p, st = tiny
+    Ad = st.A.toarray()
+    H = O.dense_operator(lambda X: O.H3_ad_apply(st, X), st.n)
+    H = 0.5 * (H + H.T)
+    ev = O.spectrum_HA(H, Ad)
+    ref = np.sort(np.linalg.eigvals(H @ Ad).real)
+    assert np.allclose(ev, ref, rtol=1e-8, atol=1e-10 * ref.max())
+    res = O.pcg(lambda v: Ad @ v, p.b if p.b.ndim == 1 else p.b[0], lambda r: H @ r, rtol=1e-14, maxit=4 * st.n)
+    lo, hi = O.lanczos_extremes(res.alphas, res.betas)
+    # Ritz values lie inside the spectrum; the outer ones approach its ends
+    # (the large cluster at 1 is reached more slowly than the top)
+    assert lo >= ev.min() * (1 - 1e-10) and hi <= ev.max() * (1 + 1e-10)
+    assert hi >= ev.max() * (1 - 1e-6) and lo <= ev.min() * (1 + 1e-3)
+
+
 def test_colouring_constant_bruteforce():
     """Def. 4 on a 2x2 box partition: every pair of subdomains interacts, so
     the optimal constant is 4 and greedy must find it."""
