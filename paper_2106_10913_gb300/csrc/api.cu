@@ -187,16 +187,19 @@ static awg_status setup_impl(Handle* h, const int* d_rowptr, const int* d_colidx
                              const double* d_val, const int* d_part) {
     cudaStream_t s = h->stream;
     const double t0 = now_ms();
-    AWG_TRY(runtime_init(h));
-    AWG_TRY(dalloc(h, h->rowptr, (size_t)(h->n + 1) * sizeof(int)));
-    AWG_TRY(dalloc(h, h->colidx, (size_t)h->nnz * sizeof(int)));
-    AWG_TRY(dalloc(h, h->val, (size_t)h->nnz * sizeof(double)));
-    AWG_CUDA(cudaMemcpyAsync(h->rowptr.p, d_rowptr, (size_t)(h->n + 1) * sizeof(int), cudaMemcpyDefault, s));
-    AWG_CUDA(cudaMemcpyAsync(h->colidx.p, d_colidx, (size_t)h->nnz * sizeof(int), cudaMemcpyDefault, s));
-    AWG_CUDA(cudaMemcpyAsync(h->val.p, d_val, (size_t)h->nnz * sizeof(double), cudaMemcpyDefault, s));
-    AWG_CUDA(cudaStreamSynchronize(s));
-    AWG_TRY(setup_structure(h, d_part));
-    AWG_CUDA(cudaStreamSynchronize(s));
+    {
+        NvtxRange nv_("awg_setup: structure");  // the numeric stages have ranges of their own
+        AWG_TRY(runtime_init(h));
+        AWG_TRY(dalloc(h, h->rowptr, (size_t)(h->n + 1) * sizeof(int)));
+        AWG_TRY(dalloc(h, h->colidx, (size_t)h->nnz * sizeof(int)));
+        AWG_TRY(dalloc(h, h->val, (size_t)h->nnz * sizeof(double)));
+        AWG_CUDA(cudaMemcpyAsync(h->rowptr.p, d_rowptr, (size_t)(h->n + 1) * sizeof(int), cudaMemcpyDefault, s));
+        AWG_CUDA(cudaMemcpyAsync(h->colidx.p, d_colidx, (size_t)h->nnz * sizeof(int), cudaMemcpyDefault, s));
+        AWG_CUDA(cudaMemcpyAsync(h->val.p, d_val, (size_t)h->nnz * sizeof(double), cudaMemcpyDefault, s));
+        AWG_CUDA(cudaStreamSynchronize(s));
+        AWG_TRY(setup_structure(h, d_part));
+        AWG_CUDA(cudaStreamSynchronize(s));
+    }
     h->setup_ms[0] = now_ms() - t0;
     if (h->opt.verbose)
         fprintf(stderr, "libawg: structure %.1f ms (N=%d, sum n^s=%lld, max n^s=%d)\n", h->setup_ms[0],
@@ -299,6 +302,7 @@ static int variant_stage(const Handle* h) { return 4 + h->opt.variant; }
 
 awg_status awg_apply(awg_handle hh, int precision, const double* d_r, double* d_z, int nrhs, int ld,
                      void* stream) {
+    NvtxRange nv_("awg_apply");
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h || !d_r || !d_z || nrhs < 0 || ld < h->n || precision < 0 || precision >= AWG_NPREC)
         return AWG_ERR_INVALID_ARG;
@@ -326,6 +330,7 @@ awg_status awg_apply_stage(awg_handle hh, int which, int precision, const double
 
 awg_status awg_pcg(awg_handle hh, int precision, const double* d_b, double* d_x, int nrhs, int ld,
                    double rtol, int* h_iters, double* h_relres, void* stream) {
+    NvtxRange nv_("awg_pcg");
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h || !d_b || !d_x || nrhs < 0 || ld < h->n || !(rtol > 0.0) || precision < 0 || precision >= AWG_NPREC)
         return AWG_ERR_INVALID_ARG;
@@ -369,6 +374,7 @@ awg_status awg_apply_block(awg_handle hh, int which, int precision, const double
 
 awg_status awg_pcg_block(awg_handle hh, int precision, const double* d_b, double* d_x, int nrhs, int ld,
                          double rtol, int* h_iters, double* h_relres, void* stream) {
+    NvtxRange nv_("awg_pcg_block");
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h || !d_b || !d_x || nrhs < 0 || ld < h->n || !(rtol > 0.0) || precision < 0 || precision >= AWG_NPREC)
         return AWG_ERR_INVALID_ARG;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cstdint>
@@ -200,6 +201,20 @@ struct Handle {
 };
 
 // Brackets one launch with CUDA events on its stream when profiling is on.
+// NVTX range of a host-side phase (setup stages, entry points), for
+// profilers that filter by range; next() closes the current range and opens
+// the following one, the destructor closes the last (also on early return).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    void next(const char* name) {
+        nvtxRangePop();
+        nvtxRangePushA(name);
+    }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 struct ProfScope {
     Handle* h;
     int id;

@@ -841,6 +841,7 @@ awg_status build_setup_numeric(Handle* h) {
     double t0 = now_ms();
     const dim3 gblk(N, 16);
     // ---------------------------------------------- 1. eigen-split of B^s
+    NvtxRange nv_("awg_setup: eigen-split of B^s");
     DevBuf A1;
     AWG_TRY(dalloc(h, A1, (size_t)h->dense_total * 8));
     AWG_TRY(assemble_local(h, (double*)h->bval.p, (double*)A1.p));
@@ -869,6 +870,7 @@ awg_status build_setup_numeric(Handle* h) {
     h->setup_ms[1] = t1 - t0;
 
     // ---------------------------------------------- 2. local factors
+    nv_.next("awg_setup: local factors");
     AWG_TRY(assemble_local(h, (double*)h->bval.p, (double*)A1.p));
     AWG_TRY(dalloc(h, h->sigma, N * 8));
     k_form_K<<<N, 256, 0, s>>>((int*)h->ns.p, (int64_t*)h->dense_off.p, (int*)h->nm_ptr.p,
@@ -933,6 +935,7 @@ awg_status build_setup_numeric(Handle* h) {
     h->setup_ms[2] = t2 - t1;
 
     // ---------------------------------------------- 3. GenEO
+    nv_.next("awg_setup: GenEO");
     if (h->opt.h2 == AWG_H2_AS_HYB) {  // two pencils, dense route (Thm. 5)
         AWG_TRY(geneo_as_dense(h, (double*)A1.p));
     } else {
@@ -1062,6 +1065,7 @@ awg_status build_setup_numeric(Handle* h) {
     h->setup_ms[3] = t3 - t2;
 
     // ---------------------------------------------- 4. E = Z^T A_+ Z
+    nv_.next("awg_setup: E");
     const int n0 = h->n0;
     if (n0 > 0) {
         AWG_TRY(dalloc(h, h->E, (size_t)n0 * n0 * 8));
@@ -1120,6 +1124,7 @@ awg_status build_setup_numeric(Handle* h) {
         AWG_LAUNCH();
     }
     // ---------------------------------------------- 5. W, 6. F
+    nv_.next("awg_setup: W and F");
     const int nm = h->n_minus;
     if (nm > 0) {
         AWG_TRY(build_W(h));
