@@ -24,7 +24,16 @@ notes of the repository):
   * Y_L selects lambda < tau strictly (Def. 9);
   * E = Z^T A_+ Z (Thm. 4) and F = W^T A W (Def. 10);
   * PCG stops on the unpreconditioned recurrence residual
-    ||r_k|| / ||b|| <= rtol with x_0 = 0, then checks the true residual.
+    ||r_k|| / ||b|| <= rtol with x_0 = 0, then checks the true residual
+    (PETSc's preconditioned-norm test is available for the paper's tables);
+  * W is exact by default; ``build_W_pcg`` builds it the paper's way (PCG
+    with H_2 to a tolerance), ``truncate_W`` drops its small entries;
+  * the two-pencil coarse space of H^AS_hyb (Thm. 5) takes both pencils'
+    columns side by side (a dependent union leaves E singular, recorded).
+
+``sampled_local_geneo`` evaluates the eigen-splits and GenEO pencils of
+chosen subdomains of a problem too large for ``setup`` (used for parity
+checks at full size).
 
 Parity of each function is pinned by tests in ``tests/test_oracle_*.py``
 against closed forms, exact invariants from the paper's theorems, dense
