@@ -498,6 +498,29 @@ def test_awg_spectral_bounds(tiny):
         assert nz.min() >= lo - 1e-6 and nz.max() <= hi + 1e-6
 
 
+@pytest.mark.parametrize("h2", ["asp_hyb", "asp_ad", "as_hyb"])
+def test_awg_spectral_bounds_other_H2(tiny, h2):
+    """Thm. 8 holds for any spd H_2 for A_+: with the H_2 choices of Thms. 3
+    and 5, lambda(H_3,ad A) in [min(1, l), L + 1] and lambda(H_3,hyb A),
+    lambda(H_3,inex A) in [min(1, l), max(1, L)], l and L the extreme
+    eigenvalues of H_2 A_+."""
+    p, _ = tiny
+    kw = {"tau": 0.5} if h2 == "as_hyb" else {}
+    st = O.setup(p.rowptr, p.colidx, p.val, p.n, part=p.part, nparts=p.nparts, overlap=p.overlap,
+                 subsets=p.subsets, dense=True, h2=h2, tau_flat=10.0, **kw)
+    ev2, H2, Ap = _H2A_plus_spectrum(st)
+    lo, hi = ev2.min(), ev2.max()
+    Ad = st.A.toarray()
+    tol = 1e-8 * max(1.0, hi)
+    Had = O.dense_operator(lambda X: O.H3_ad_apply(st, X), st.n)
+    ev = O.spectrum_HA(0.5 * (Had + Had.T), Ad)
+    assert ev.min() >= min(1.0, lo) - tol and ev.max() <= hi + 1 + tol
+    for apply in (O.H3_hyb_apply, O.H3_inex_apply):
+        H = O.dense_operator(lambda X: apply(st, X), st.n)
+        ev = O.spectrum_HA(0.5 * (H + H.T), Ad)
+        assert ev.min() >= min(1.0, lo) - tol and ev.max() <= max(1.0, hi) + tol
+
+
 # ----------------------------------------------------------------------------
 # Closed-form special cases
 # ----------------------------------------------------------------------------
