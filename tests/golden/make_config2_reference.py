@@ -1,0 +1,60 @@
+"""Writes ``config2_oracle.json``: the CPU oracle on the 512 x 512 channel
+problem that the benchmark times (``awg_inputs.config2``), for the
+full-size parity test.  Calls only ``oracle`` and the input generators;
+about a quarter of an hour on eight cores.
+
+    python tests/golden/make_config2_reference.py
+
+Stored: the per-subdomain counts n^s_-, strictly negative counts and GenEO
+mode counts (all 256 subdomains); n0 and n_-; the smallest relative
+distance of a GenEO pencil eigenvalue to tau (the counts are decided away
+from the threshold when it is well above the GPU block solver's 1e-6
+certificate margin); max_s cond(A^s_+); the PCG iteration count and true
+relative residual of H_3,ad on the benchmark b (rtol 1e-8); and 256 sampled
+entries of H_3,ad x for x ~ N(0,1) from default_rng(4242).
+"""
+
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import awg_inputs as gi  # noqa: E402
+import oracle as O  # noqa: E402
+
+
+def main():
+    t0 = time.time()
+    p = gi.config2()
+    st = O.setup_problem(p)
+    mm = O.minus_counts(st)
+    gap = min(float(np.min(np.abs(lam - st.tau))) / st.tau for lam in st.geneo_lam)
+    res = O.pcg(lambda v: st.A @ v, p.b, lambda r: O.H3_ad_apply(st, r), rtol=1e-8)
+    x = np.random.default_rng(4242).standard_normal(p.n)
+    y = O.H3_ad_apply(st, x)
+    idx = np.sort(np.random.default_rng(4243).choice(p.n, 256, replace=False))
+    out = {
+        "source": "oracle/awg_oracle.py on awg_inputs.config2() (512 x 512 channels at 1e6, 256 boxes, overlap 2, "
+                  "tau = 0.1), written by tests/golden/make_config2_reference.py",
+        "n": int(p.n), "n0": int(st.n0), "n_minus": int(st.n_minus),
+        "n_minus_per_subdomain": mm[:, 0].tolist(), "n_strict_per_subdomain": mm[:, 1].tolist(),
+        "modes_per_subdomain": O.mode_counts(st).tolist(),
+        "geneo_min_rel_gap_to_tau": gap,
+        "local_condition": O.local_condition(st),
+        "pcg": {"rtol": 1e-8, "iters": int(res.iters), "true_relres": float(res.true_relres)},
+        "apply_h3ad": {"x_seed": 4242, "idx_seed": 4243, "idx": idx.tolist(), "y": y[idx].tolist(),
+                       "y_max_abs": float(np.abs(y).max())},
+        "seconds": round(time.time() - t0, 1),
+    }
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "config2_oracle.json"), "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+
+
+if __name__ == "__main__":
+    main()

@@ -10,6 +10,10 @@ rest:
 
 * bit-exact over the whole problem: every Omega^s, the pair multiplicities
   M_mu and the partition of unity D;
+* against the oracle's own run on the whole problem (about a quarter of an
+  hour on the host, stored by tests/golden/make_config2_reference.py): the
+  counts of all 256 subdomains, the float64 PCG iterations and sampled
+  entries of the H_3,ad apply;
 * bit-exact on sampled subdomains (two corners, an edge, two interior ones
   crossed by channels, one with an eigenvalue 3.75 % from tau): n^s_-, the
   strict counts and the GenEO mode counts, from the oracle's eigen-splits
@@ -35,6 +39,9 @@ with an eigenvalue near tau (kappa(M_B) = 2e8, delta = 0.084), about 1e-9
 for the others.  The bound is ten times that estimate and never below 1e-8.
 """
 
+import json
+import os
+
 import numpy as np
 import pytest
 import scipy.linalg as sla
@@ -47,6 +54,7 @@ pytestmark = pytest.mark.gpu
 
 SAMPLES = [0, 8, 72, 136, 255]
 NRHS = 128
+REF = os.path.join(os.path.dirname(__file__), "golden", "config2_oracle.json")
 _STATE = {}
 
 
@@ -147,3 +155,28 @@ def test_block_graph_solve_full():
         _, its64, rel64, status = sol.pcg(b[c].contiguous(), rtol=1e-8)
         assert status == 0 and rel64[0] <= 1e-8
         assert abs(int(its_h[c]) - its64[0]) <= max(3, round(0.1 * its64[0])), (c, int(its_h[c]), its64[0])
+
+
+def test_whole_problem_against_stored_oracle():
+    """Against the oracle's own run on the whole problem, stored by
+    tests/golden/make_config2_reference.py: the counts of all 256
+    subdomains exactly, the float64 PCG iterations within 5 % (true
+    relative residual <= 1e-8) and 256 sampled entries of H_3,ad x within
+    max(1e-11, kappa_loc eps) max|H_3,ad x| (kappa_loc = max_s cond(A^s_+),
+    the accuracy of any backward-stable local pseudo-inverse)."""
+    ref = json.load(open(REF))
+    S = _full()
+    p, sol = S["p"], S["sol"]
+    assert sol.info["n0"] == ref["n0"] and sol.info["n_minus"] == ref["n_minus"]
+    assert sol.array("n_minus").tolist() == ref["n_minus_per_subdomain"]
+    assert sol.array("n_strict").tolist() == ref["n_strict_per_subdomain"]
+    assert sol.array("modes").tolist() == ref["modes_per_subdomain"]
+    ap = ref["apply_h3ad"]
+    x = torch.from_numpy(np.random.default_rng(ap["x_seed"]).standard_normal(p.n)).cuda()
+    y = sol.apply(x).cpu().numpy()
+    tol = max(1e-11, ref["local_condition"] * np.finfo(float).eps) * ap["y_max_abs"]
+    assert np.max(np.abs(y[np.array(ap["idx"])] - np.array(ap["y"]))) <= tol
+    _, its, rel, status = sol.pcg(torch.from_numpy(p.b).cuda(), rtol=1e-8)
+    assert status == 0 and rel[0] <= 1e-8
+    ri = ref["pcg"]["iters"]
+    assert abs(its[0] - ri) <= max(1, round(0.05 * ri)), (its[0], ri)
