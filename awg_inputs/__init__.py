@@ -26,4 +26,5 @@ from .problems import (  # noqa: F401
     config4,
     config5,
     small_channels,
+    block_rhs,
 )

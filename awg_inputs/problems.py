@@ -510,6 +510,15 @@ def batch_channels(nprob: int = 128, seed0: int = 5000, Lmin: int = 128, Lmax: i
 # Named workloads
 # ---------------------------------------------------------------------------
 
+def block_rhs(p: Problem, nrhs: int, seed: int = 1) -> np.ndarray:
+    """Right-hand sides of the batched (multi-right-hand-side) solves:
+    row 0 is the problem's own b, rows 1 .. nrhs-1 are N(0, 1) draws from
+    default_rng(seed) (nrhs x n, row-major)."""
+    b0 = p.b if p.b.ndim == 1 else p.b[0]
+    rest = np.random.default_rng(seed).standard_normal((nrhs - 1, p.n))
+    return np.concatenate([b0[None, :], rest])
+
+
 def config1() -> Problem:
     """2D Poisson 64x64 (n = 4096), 4x4 boxes, overlap 1, tau = 0.1."""
     return poisson2d(64, qx=4, overlap=1, tau=0.1, seed=0)

@@ -154,6 +154,14 @@ typedef struct {
     double tau_flat;        /* tau_flat > 0 of the AS choices of H_2 (the
                                AS_+ ones select below 1 / tau_flat and leave
                                the tau of awg_setup unused); default 10        */
+    int coarse_tensor_cores; /* block path (awg_apply_block, awg_pcg_block*):
+                               1 (default) the float64 products with the dense
+                               coarse inverses E^-1, F^-1 (Thm. 4, Def. 10) on
+                               the tensor cores, both operands cut into eight
+                               7-bit integer slices whose bfloat16 products are
+                               exact in float32 and summed in float64 (as
+                               accurate as a float64 GEMM); 0 on the float64
+                               CUDA cores                                      */
 } awg_options;
 
 /* Per-handle figures reported after setup (cf. Table 1 of the paper). */
@@ -369,26 +377,49 @@ awg_status awg_pcg_block(awg_handle h, int precision, const double* d_b, double*
                          double rtol, int* h_iters, double* h_relres, void* stream);
 
 /*
+ * Y = M X with one of the handle's dense coarse inverses, through the block
+ * path's coarse product (for checks of that product): which = 0 E^-1 of the
+ * GenEO coarse problem E = Z^T A_+ Z (Thm. 4), 1 F^-1 of the second coarse
+ * problem F = W^T A W of the storage form `precision` (Def. 10), 2 the
+ * H_3,inex inner inverse (C^-1 - Vhat^T W)^-1 of that form (Thm. 7).
+ *   engine   0: float64 GEMM on the CUDA cores; 1: the tensor-core slice
+ *            products of awg_options.coarse_tensor_cores (AWG_ERR_STATE if
+ *            they are not built); 2: as 1 with the reduction split every
+ *            256 terms (the split that dimensions above 4032 take)
+ *   d_x, d_y device float64, nrhs (1..64) columns of length dim (n0 or n_-),
+ *            column-major with ld = dim, must not overlap
+ * Synchronises `stream`.  Errors: AWG_ERR_INVALID_ARG, AWG_ERR_STATE (matrix
+ * not built), AWG_ERR_OOM, AWG_ERR_CUDA.
+ */
+awg_status awg_coarse_apply_block(awg_handle h, int which, int precision, int engine, const double* d_x,
+                                  double* d_y, int nrhs, void* stream);
+
+/*
  * Asynchronous block PCG (the handle's variant, 1 <= nrhs <= 128 columns,
  * x_0 = 0): the
  * iterations run as one CUDA graph launch, a conditional while node whose
  * body is one iteration captured from the handle's two streams, with the
  * stopping test (per column, recurrence residual <= rtol ||b||, Section 1)
- * evaluated on the device.  No host synchronisation: the call returns once
+ * evaluated on the device: a column whose recurrence residual reaches rtol
+ * ||b|| is confirmed on its true residual b - A x (computed in that
+ * iteration only) and goes on iterating while the true residual exceeds
+ * rtol ||b||, as in awg_pcg.  No host synchronisation: the call returns once
  * the work is enqueued on `stream`, so one host thread can keep several
  * handles (independent problems) solving at the same time.  The loop graph
  * of each (precision, nrhs width 16/32/64) is captured on first use (make
  * that first call outside any stream capture).  DEVICE outputs, written
  * when the work completes: d_iters int32[nrhs] (iterations per column),
- * d_relres float64[nrhs] (recurrence relative residual at exit), d_status
- * int32[1] (AWG_OK, AWG_ERR_BREAKDOWN or AWG_ERR_MAXIT); any may be NULL.
+ * d_relres float64[nrhs] (relative residual at exit: the true one for a
+ * column that stopped converged, the recurrence one after a breakdown or at
+ * the iteration cap), d_status int32[1] (AWG_OK, AWG_ERR_BREAKDOWN or
+ * AWG_ERR_MAXIT, the latter also for a column whose recurrence residual
+ * fell below 1e-6 rtol without the true one reaching rtol); any may be NULL.
  * With nrhs = 1 the loop body is the single-right-hand-side apply (the
  * GEMV-shaped passes of awg_pcg), otherwise the block apply of
  * awg_pcg_block; more than 64 columns run as two groups (64 and the rest)
  * side by side on the handle's two block slots (own workspace, stream pair
  * and loop graphs), so one group's float64 coarse GEMMs overlap the other's
- * bandwidth-bound passes.  The true residual is not re-checked (awg_pcg_block does
- * that).
+ * bandwidth-bound passes.
  * Errors returned: AWG_ERR_INVALID_ARG, AWG_ERR_STATE, AWG_ERR_OOM,
  * AWG_ERR_CUDA.
  */
@@ -401,10 +432,11 @@ awg_status awg_pcg_block_async(awg_handle h, int precision, const double* d_b, d
 /*
  * y = H^NN x (the batched local pseudo-inverses and the prolongation sum,
  * as awg_apply_stage with which = 2) WITHOUT ANY DEVICE ALLOCATION.  The
- * paper has no counterpart: this entry point serves callers that cannot
- * call cudaMalloc while they apply the preconditioner (code captured into
- * a CUDA graph, allocation-free real-time loops, frameworks that own all
- * device memory).  Its scratch (sum of n^s float64 values) is a static
+ * paper has no counterpart: this entry point serves callers that may not
+ * call cudaMalloc while they apply the preconditioner: frameworks that hand
+ * out all device memory from their own pool and forbid libraries to
+ * allocate, and real-time loops that cannot afford cudaMalloc / cudaFree
+ * (which may synchronise the device).  Its scratch (sum of n^s float64 values) is a static
  * device array of AWG_NOALLOC_MAX_LOCAL doubles (8 MiB) that every GPU
  * loading the library keeps until the process exits; a handle whose
  * subdomains hold more values is rejected with AWG_ERR_INVALID_ARG (and a

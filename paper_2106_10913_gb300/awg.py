@@ -46,7 +46,8 @@ class awg_options(ctypes.Structure):
                 ("geneo_block", ctypes.c_int), ("geneo_maxit", ctypes.c_int),
                 ("learned_params", ctypes.c_void_p), ("autotune", ctypes.c_int),
                 ("w16_keep", ctypes.c_double), ("block_tensor_cores", ctypes.c_int),
-                ("h2", ctypes.c_int), ("tau_flat", ctypes.c_double)]
+                ("h2", ctypes.c_int), ("tau_flat", ctypes.c_double),
+                ("coarse_tensor_cores", ctypes.c_int)]
 
 
 class awg_info(ctypes.Structure):
@@ -65,7 +66,8 @@ EXPORTED = ["awg_default_options", "awg_status_string", "awg_setup", "awg_destro
             "awg_get_info", "awg_apply", "awg_apply_stage", "awg_pcg", "awg_get_array",
             "awg_profile", "awg_profile_read", "awg_apply_hnn_noalloc", "awg_learned_data",
             "awg_learned_forward", "awg_learned_grad", "awg_learned_train", "awg_profile_trace",
-            "awg_apply_block", "awg_pcg_block", "awg_pcg_block_async", "awg_save", "awg_load"]
+            "awg_apply_block", "awg_pcg_block", "awg_pcg_block_async", "awg_save", "awg_load",
+            "awg_coarse_apply_block"]
 LEARNED_NPARAM, LEARNED_NFEAT = 385, 5
 GENEO_DENSE, GENEO_BLOCK, GENEO_LEARNED = 0, 1, 2
 PROF_NAMES = ["spmv", "local", "wt", "wd", "coarse", "subdomain", "prolong", "vector"]
@@ -111,6 +113,8 @@ def load_library(path: str = LIB_PATH):
     lib.awg_profile_trace.restype = I
     lib.awg_apply_block.argtypes = [P, I, I, P, P, I, I, P]
     lib.awg_apply_block.restype = I
+    lib.awg_coarse_apply_block.argtypes = [P, I, I, I, P, P, I, P]
+    lib.awg_coarse_apply_block.restype = I
     lib.awg_pcg_block.argtypes = [P, I, P, P, I, I, D, ctypes.POINTER(I), ctypes.POINTER(D), P]
     lib.awg_pcg_block.restype = I
     lib.awg_pcg_block_async.argtypes = [P, I, P, P, I, I, D, P, P, P, P]
@@ -237,6 +241,19 @@ def awg_apply_block(h, which, x, y, precision: int = FP64, stream=None):
     w = STAGE[which] if isinstance(which, str) else int(which)
     _check(load_library().awg_apply_block(h, w, precision, x.data_ptr(), y.data_ptr(), x.shape[0],
                                           x.shape[-1], _stream_ptr(stream)), "awg_apply_block")
+    return y
+
+
+COARSE = {"Einv": 0, "Finv": 1, "inex": 2}
+
+
+def awg_coarse_apply_block(h, which, x, y, precision: int = FP64, engine: int = 1, stream=None):
+    """y = M x for the rows of x (nrhs x dim, nrhs <= 64) with a dense coarse
+    inverse M (which: "Einv", "Finv" or "inex"); engine 0 float64 CUDA cores,
+    1 tensor-core slice products, 2 the same with short reduction splits."""
+    w = COARSE[which] if isinstance(which, str) else int(which)
+    _check(load_library().awg_coarse_apply_block(h, w, precision, int(engine), x.data_ptr(), y.data_ptr(),
+                                                 x.shape[0], _stream_ptr(stream)), "awg_coarse_apply_block")
     return y
 
 

@@ -62,6 +62,11 @@ void free_all(Handle* h) {
                       &h->ul_gt, &h->ul_gtoff, &h->ul_kcpre, &h->ul_tsub, &h->ul_trt, &h->g1buf, &h->g1cnt,
                       &h->bws2};
     for (DevBuf* b : bufs) dfree(h, *b);
+    for (int k = 0; k < 9; k++) {
+        dfree(h, h->oz_q[k]);
+        dfree(h, h->oz_ex[k]);
+        h->oz_dim[k] = 0;
+    }
     for (auto& P : h->prec) {
         dfree(h, P.G);
         dfree(h, P.W);
@@ -163,6 +168,7 @@ void awg_default_options(awg_options* opt) {
     opt->autotune = 1;
     opt->w16_keep = 0.1;
     opt->block_tensor_cores = 1;
+    opt->coarse_tensor_cores = 1;
 }
 
 const char* awg_status_string(awg_status s) {
@@ -235,7 +241,8 @@ awg_status awg_setup(int n, int nnz, const int* d_rowptr, const int* d_colidx, c
         o.w_maxit < 1 || o.maxit < 1 || (o.w_precision != AWG_FP64 && o.w_precision != AWG_MIXED_FP32) ||
         o.geneo_solver < 0 || o.geneo_solver > 2 || o.geneo_block < 2 || o.geneo_block > 16 ||
         o.geneo_maxit < 1 || (o.geneo_solver == 2 && !o.learned_params) || !(o.w16_keep >= 0.0) ||
-        o.w16_keep > 1.0 || o.h2 < AWG_H2_NN_HYB || o.h2 > AWG_H2_AS_HYB || !(o.tau_flat > 0.0))
+        o.w16_keep > 1.0 || o.h2 < AWG_H2_NN_HYB || o.h2 > AWG_H2_AS_HYB || !(o.tau_flat > 0.0) ||
+        o.coarse_tensor_cores < 0 || o.coarse_tensor_cores > 1)
         return AWG_ERR_INVALID_ARG;
     o.precisions |= 1 << AWG_FP64;
     Handle* h = new (std::nothrow) Handle();
@@ -369,6 +376,23 @@ awg_status awg_apply_block(awg_handle hh, int which, int precision, const double
     const awg_status st = block_apply(h, which, precision, d_x, d_y, nrhs, ld, h->hp);
     AWG_CUDA(cudaEventRecord(h->ev_out, h->hp));
     AWG_CUDA(cudaStreamWaitEvent(us, h->ev_out, 0));
+    return st;
+}
+
+awg_status awg_coarse_apply_block(awg_handle hh, int which, int precision, int engine, const double* d_x,
+                                  double* d_y, int nrhs, void* stream) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !d_x || !d_y || which < 0 || which > 2 || engine < 0 || engine > 2 || nrhs < 1 || nrhs > 64 ||
+        precision < 0 || precision >= AWG_NPREC)
+        return AWG_ERR_INVALID_ARG;
+    if (!h->prec[precision].built) return AWG_ERR_STATE;
+    cudaStream_t us = (cudaStream_t)stream;
+    AWG_CUDA(cudaEventRecord(h->ev_in, us));
+    AWG_CUDA(cudaStreamWaitEvent(h->hp, h->ev_in, 0));
+    const awg_status st = block_coarse_apply(h, which, precision, engine, d_x, d_y, nrhs, h->hp);
+    AWG_CUDA(cudaEventRecord(h->ev_out, h->hp));
+    AWG_CUDA(cudaStreamWaitEvent(us, h->ev_out, 0));
+    AWG_CUDA(cudaStreamSynchronize(us));
     return st;
 }
 

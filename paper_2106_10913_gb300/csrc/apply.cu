@@ -648,9 +648,10 @@ __global__ void k_sub(int n, const double* a, const double* b, double* c) {
     if (i < n) c[i] = a[i] - b[i];
 }
 
-// *out = x^T y
+// *out = x^T y (nothing when *gate is 0)
 __global__ void k_dot(int n, const double* __restrict__ x, const double* __restrict__ y, double* part,
-                      unsigned* counter, double* out) {
+                      unsigned* counter, double* out, const double* gate = nullptr) {
+    if (gate && *gate == 0.0) return;
     __shared__ double red[32];
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -1252,8 +1253,23 @@ awg_status pcg1(Handle* h, int prec, int variant_stage, const double* b, double*
 // ------------------------------------------------- graph-driven PCG, one RHS
 // Control words next to the PCG scalars: [8] iterations done, [9] rtol,
 // [10] maxit, [11] status, [12] active (1/0), [13] relative residual and
-// [14] iterations at exit.
-enum { C_IT = 8, C_RTOL = 9, C_MAXIT = 10, C_ST = 11, C_ACT = 12, C_REL = 13, C_ITS = 14 };
+// [14] iterations at exit, [15] candidate (recurrence residual at rtol, true
+// residual to be confirmed in this iteration).
+enum { C_IT = 8, C_RTOL = 9, C_MAXIT = 10, C_ST = 11, C_ACT = 12, C_REL = 13, C_ITS = 14, C_CAND = 15 };
+
+// q = b - A x, only when *gate is not 0
+__global__ void __launch_bounds__(256) k_resid1(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                const double* __restrict__ a, const double* __restrict__ b,
+                                                const double* __restrict__ x, double* __restrict__ q,
+                                                const double* gate) {
+    if (*gate == 0.0) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        const int e = rp[i + 1];
+        for (int k = rp[i]; k < e; k++) acc = fma(a[k], x[ci[k]], acc);
+        q[i] = b[i] - acc;
+    }
+}
 
 __global__ void k_pcg1_init(double* scal, double rtol, double maxit) {
     if (threadIdx.x == 0) {
@@ -1264,15 +1280,16 @@ __global__ void k_pcg1_init(double* scal, double rtol, double maxit) {
         scal[C_ACT] = scal[S_BB] > 0.0 ? 1.0 : 0.0;
         scal[C_REL] = 0.0;
         scal[C_ITS] = 0.0;
+        scal[C_CAND] = 0.0;
     }
 }
 
-// after an x, r update: stop on breakdown, convergence (recurrence residual
-// <= rtol ||b||) or the iteration cap; with `set`, the loop condition
-__global__ void k_pcg1_cond(double* scal, cudaGraphConditionalHandle hc, int set, unsigned long long* launches,
-                            int add) {
+// after an x, r update: stop on breakdown or the iteration cap; a
+// recurrence residual <= rtol ||b|| makes the iteration a candidate, whose
+// true residual (k_resid1, k_dot gated by C_CAND) k_pcg1_confirm checks
+__global__ void k_pcg1_cond(double* scal) {
     if (threadIdx.x != 0) return;
-    bool go = false;
+    scal[C_CAND] = 0.0;
     if (scal[C_ACT] != 0.0) {
         const int it = (int)scal[C_IT] + 1;
         scal[C_IT] = it;
@@ -1282,15 +1299,37 @@ __global__ void k_pcg1_cond(double* scal, cudaGraphConditionalHandle hc, int set
         scal[C_ITS] = it;
         if (!(pq > 0.0) || !isfinite(pq)) {
             scal[C_ST] = AWG_ERR_BREAKDOWN;
+            scal[C_ACT] = 0.0;
         } else if (rel <= scal[C_RTOL]) {
+            scal[C_CAND] = 1.0;
         } else if (it >= (int)scal[C_MAXIT]) {
             scal[C_ST] = AWG_ERR_MAXIT;
-        } else {
-            go = true;
+            scal[C_ACT] = 0.0;
         }
-        if (!go) scal[C_ACT] = 0.0;
     }
-    if (set) cudaGraphSetConditional(hc, go ? 1u : 0u);
+}
+
+// a candidate stops once its true relative residual is <= rtol (reported
+// as the residual at exit), or its recurrence residual fell below 1e-6 rtol
+// (stagnation: AWG_ERR_MAXIT); with `set`, the loop condition
+__global__ void k_pcg1_confirm(double* scal, cudaGraphConditionalHandle hc, int set, unsigned long long* launches,
+                               int add) {
+    if (threadIdx.x != 0) return;
+    if (scal[C_ACT] != 0.0 && scal[C_CAND] != 0.0) {
+        const double rtol = scal[C_RTOL];
+        const double tr = sqrt(scal[S_TR] / scal[S_BB]);
+        if (tr <= rtol || scal[C_REL] <= 1e-6 * rtol) {
+            if (tr > rtol) scal[C_ST] = AWG_ERR_MAXIT;
+            scal[C_ACT] = 0.0;
+            scal[C_REL] = tr;
+        } else if ((int)scal[C_IT] >= (int)scal[C_MAXIT]) {
+            scal[C_ST] = AWG_ERR_MAXIT;
+            scal[C_ACT] = 0.0;
+            scal[C_REL] = tr;
+        }
+        scal[C_CAND] = 0.0;
+    }
+    if (set) cudaGraphSetConditional(hc, scal[C_ACT] != 0.0 ? 1u : 0u);
     if (launches && add) atomicAdd(launches, (unsigned long long)add);
 }
 
@@ -1311,6 +1350,33 @@ G1 g1_of(Handle* h) {
     return {base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n};
 }
 
+// stopping test after an x, r update: candidate, then (gated on it) the
+// true residual q = b - A x and its norm, then the confirmation
+awg_status pcg1_stop(Handle* h, const G1& g, double* scal, Ws& w, cudaStream_t s, cudaGraphConditionalHandle hc,
+                     int set, unsigned long long* launches, int add) {
+    const int n = h->n;
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        k_pcg1_cond<<<1, 32, 0, s>>>(scal);
+        AWG_LAUNCH();
+    }
+    {
+        ProfScope ps_(h, AWG_PROF_SPMV, s);
+        k_resid1<<<(n + 255) / 256, 256, 0, s>>>(n, (int*)h->rowptr.p, (int*)h->colidx.p, (double*)h->val.p, g.b,
+                                                 g.x, g.q, scal + C_CAND);
+        AWG_LAUNCH();
+    }
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        k_dot<<<grid_n(n), 256, 0, s>>>(n, g.q, g.q, w.part, w.cnt, scal + S_TR, scal + C_CAND);
+        AWG_LAUNCH();
+    }
+    ProfScope ps_(h, AWG_PROF_VECTOR, s);
+    k_pcg1_confirm<<<1, 32, 0, s>>>(scal, hc, set, launches, add);
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
 // one iteration: z = H r, rz_new, p = z + beta p, q = A p (p.q), x, r (r.r), stop test
 awg_status pcg1_body(Handle* h, int prec, int stage, const G1& g, double* scal, Ws& w, cudaStream_t s,
                      cudaGraphConditionalHandle hc, int set, unsigned long long* launches, int add) {
@@ -1328,10 +1394,7 @@ awg_status pcg1_body(Handle* h, int prec, int stage, const G1& g, double* scal, 
         k_pcg_xr<<<nb, 256, 0, s>>>(n, scal, g.p, g.q, g.x, g.r, w.part, w.cnt);
     }
     AWG_LAUNCH();
-    ProfScope ps_(h, AWG_PROF_VECTOR, s);
-    k_pcg1_cond<<<1, 32, 0, s>>>(scal, hc, set, launches, add);
-    AWG_LAUNCH();
-    return AWG_OK;
+    return pcg1_stop(h, g, scal, w, s, hc, set, launches, add);
 }
 }  // namespace
 
@@ -1366,11 +1429,7 @@ awg_status pcg1_async(Handle* h, int prec, int stage, const double* b, double* x
         k_pcg_xr<<<nb, 256, 0, s>>>(n, scal, g.p, g.q, g.x, g.r, w.part, w.cnt);
     }
     AWG_LAUNCH();
-    {
-        ProfScope ps_(h, AWG_PROF_VECTOR, s);
-        k_pcg1_cond<<<1, 32, 0, s>>>(scal, 0, 0, nullptr, 0);
-    }
-    AWG_LAUNCH();
+    AWG_TRY(pcg1_stop(h, g, scal, w, s, 0, 0, nullptr, 0));
     // the loop graph of this precision (captured once, after the first
     // iteration has been issued)
     if (!h->g1_exec[prec]) {
@@ -1412,7 +1471,7 @@ awg_status pcg1_async(Handle* h, int prec, int stage, const double* b, double* x
             if (t != cudaGraphNodeTypeKernel) continue;
             cudaKernelNodeParams kp;
             AWG_CUDA(cudaGraphKernelNodeGetParams(nd, &kp));
-            if (kp.func != (void*)k_pcg1_cond) continue;
+            if (kp.func != (void*)k_pcg1_confirm) continue;
             *(int*)kp.kernelParams[4] = add;
             AWG_CUDA(cudaGraphKernelNodeSetParams(nd, &kp));
         }

@@ -146,6 +146,12 @@ struct Handle {
     // float32 local pseudo-inverses and their tables (ul_ntiles = 0: not built)
     DevBuf ul_gt, ul_gtoff, ul_kcpre, ul_tsub, ul_trt;
     int ul_ntiles = 0, ul_maxkc = 0, ul_maxtiles = 0;
+    // float64-accurate tensor-core coarse products of the block path:
+    // bfloat16 slices and row exponents of the dense coarse inverses (slot 0
+    // E^-1, 1 + p F^-1 of storage form p, 5 + p the H_3,inex inner inverse
+    // of form p), built on the first block call; oz_dim[k] = 0: not built
+    DevBuf oz_q[9], oz_ex[9];
+    int oz_dim[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     // graph-driven block PCG: loop graph per (precision, K in 16/32/64)
     cudaGraph_t bg_graph[12] = {};
     cudaGraphExec_t bg_exec[12] = {};

@@ -22,7 +22,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <type_traits>
+#include <unordered_map>
 
 namespace awg {
 
@@ -98,8 +100,9 @@ __device__ __forceinline__ void colsum_grid(const double (&acc)[2], double* part
 
 // ------------------------------------------------------------- PCG (float64)
 // PCG scalars of a block solve, K values each: rz, pq, rr, rz_new, b.b,
-// true residual, active flag (1.0 / 0.0)
-enum { B_RZ = 0, B_PQ = 1, B_RR = 2, B_RZN = 3, B_BB = 4, B_TR = 5, B_ACT = 6, B_NSC = 7 };
+// true residual, active flag (1.0 / 0.0), candidate flag of the graph-driven
+// loop (recurrence residual at rtol, true residual not yet confirmed)
+enum { B_RZ = 0, B_PQ = 1, B_RR = 2, B_RZN = 3, B_BB = 4, B_TR = 5, B_ACT = 6, B_CAND = 7, B_NSC = 8 };
 
 // Y = A X and, if dot, the column sums of X .* Y
 template <int K>
@@ -127,11 +130,14 @@ __global__ void __launch_bounds__(256) kb_spmv_dot(int n, const int* __restrict_
     if (dot) colsum_grid<K>(acc, part, cnt, dot);
 }
 
-// Q = B - A X
+// Q = B - A X (nothing when *gate is 0: the graph-driven loop computes the
+// true residual only in iterations where some column is a candidate)
 template <int K>
 __global__ void __launch_bounds__(256) kb_resid(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                 const double* __restrict__ a, const double* __restrict__ B,
-                                                const double* __restrict__ X, double* __restrict__ Q) {
+                                                const double* __restrict__ X, double* __restrict__ Q,
+                                                const double* gate = nullptr) {
+    if (gate && *gate == 0.0) return;
     ROW_LOOP(double, K) {
         double y[2] = {0.0, 0.0};
         for (int k = rp[i]; k < rp[i + 1]; k++) {
@@ -147,10 +153,12 @@ __global__ void __launch_bounds__(256) kb_resid(int n, const int* __restrict__ r
     }
 }
 
-// out[c] = sum_i X(i, c) Y(i, c)
+// out[c] = sum_i X(i, c) Y(i, c) (nothing when *gate is 0, as kb_resid)
 template <int K>
 __global__ void __launch_bounds__(256) kb_coldot(int n, const double* __restrict__ X, const double* __restrict__ Y,
-                                                 double* part, unsigned* cnt, double* out) {
+                                                 double* part, unsigned* cnt, double* out,
+                                                 const double* gate = nullptr) {
+    if (gate && *gate == 0.0) return;
     double acc[2] = {0.0, 0.0};
     ROW_LOOP(double, K) {
         double x[2], y[2];
@@ -1036,8 +1044,9 @@ __global__ void __launch_bounds__(256) kb_wd_finish_umma(int n, const float* __r
 // ------------------------------------------------ device-driven PCG control
 // Control words of a graph-driven block PCG: ctl[0] iterations done,
 // ctl[1] rtol, ctl[2] maxit, ctl[3] status (0, AWG_ERR_BREAKDOWN,
-// AWG_ERR_MAXIT); its[c] / rel[c] the iteration at which column c stopped
-// and its recurrence relative residual.
+// AWG_ERR_MAXIT), ctl[4] 1 when some column is a candidate in this
+// iteration; its[c] / rel[c] the iteration at which column c stopped and its
+// relative residual (the true one where it stopped converged).
 template <int K>
 __global__ void kb_pcg_init(int nrhs, double* sc, double* ctl, double rtol, double maxit, int* its, double* rel) {
     const int c = threadIdx.x;
@@ -1045,6 +1054,7 @@ __global__ void kb_pcg_init(int nrhs, double* sc, double* ctl, double rtol, doub
         const double bb = sc[B_BB * K + c];
         const bool a = c < nrhs && bb > 0.0;
         sc[B_ACT * K + c] = a ? 1.0 : 0.0;
+        sc[B_CAND * K + c] = 0.0;
         its[c] = 0;
         rel[c] = 0.0;
     }
@@ -1053,22 +1063,23 @@ __global__ void kb_pcg_init(int nrhs, double* sc, double* ctl, double rtol, doub
         ctl[1] = rtol;
         ctl[2] = maxit;
         ctl[3] = 0.0;
+        ctl[4] = 0.0;
     }
 }
 
 // After an x, r update: one more iteration; an active column whose p^T A p
-// is not positive (breakdown) or whose recurrence residual reached rtol
-// stops.  With `set`, the loop condition of the enclosing graph becomes
-// "some column active and iterations < maxit"; `add` kernels per loop body
-// go to *launches (profiling).
+// is not positive (breakdown) stops; one whose recurrence residual reached
+// rtol becomes a candidate (ctl[4] = 1), to be confirmed on its true
+// residual b - A x (kb_resid, kb_coldot gated by ctl[4], then
+// kb_pcg_confirm), as the host-driven solve does (Section 1; the recurrence
+// residual can drift below the true one).
 template <int K>
-__global__ void kb_pcg_cond(double* sc, double* ctl, int* its, double* rel, cudaGraphConditionalHandle hc, int set,
-                            unsigned long long* launches, int add) {
+__global__ void kb_pcg_cond(double* sc, double* ctl, int* its, double* rel) {
     const int c = threadIdx.x;
     const int it = (int)ctl[0] + 1;
     const double rtol = ctl[1];
     const int maxit = (int)ctl[2];
-    bool active = false;
+    bool cand = false;
     int status = 0;
     if (c < K && sc[B_ACT * K + c] != 0.0) {
         const double pq = sc[B_PQ * K + c];
@@ -1079,24 +1090,63 @@ __global__ void kb_pcg_cond(double* sc, double* ctl, int* its, double* rel, cuda
             rel[c] = r;
             status = AWG_ERR_BREAKDOWN;
         } else if (r <= rtol) {
-            sc[B_ACT * K + c] = 0.0;
-            its[c] = it;
-            rel[c] = r;
+            sc[B_CAND * K + c] = 1.0;
+            cand = true;
         } else if (it >= maxit) {
             its[c] = it;
             rel[c] = r;
             status = AWG_ERR_MAXIT;
-            active = true;
-        } else {
-            active = true;
         }
     }
-    const int any = __syncthreads_or(active && it < maxit);
+    const int anyc = __syncthreads_or(cand);
     const int st = __syncthreads_or(status == AWG_ERR_BREAKDOWN) ? AWG_ERR_BREAKDOWN
                    : (__syncthreads_or(status == AWG_ERR_MAXIT) ? AWG_ERR_MAXIT : 0);
     if (c == 0) {
         ctl[0] = (double)it;
+        ctl[4] = anyc ? 1.0 : 0.0;
         if (st && ctl[3] == 0.0) ctl[3] = (double)st;
+    }
+}
+
+// Candidates whose true relative residual (sc[B_TR], when ctl[4] is set)
+// is <= rtol stop, with that residual; so does one whose recurrence
+// residual fell below 1e-6 rtol (stagnation: status AWG_ERR_MAXIT); the
+// others go on.  With `set`, the loop condition of the enclosing graph
+// becomes "some column active and iterations < maxit"; `add` kernels per
+// loop body go to *launches (profiling).
+template <int K>
+__global__ void kb_pcg_confirm(double* sc, double* ctl, int* its, double* rel, cudaGraphConditionalHandle hc,
+                               int set, unsigned long long* launches, int add) {
+    const int c = threadIdx.x;
+    const int it = (int)ctl[0];
+    const double rtol = ctl[1];
+    const int maxit = (int)ctl[2];
+    bool active = false;
+    int status = 0;
+    if (c < K && sc[B_ACT * K + c] != 0.0) {
+        active = true;
+        if (ctl[4] != 0.0 && sc[B_CAND * K + c] != 0.0) {
+            sc[B_CAND * K + c] = 0.0;
+            const double r = sqrt(sc[B_RR * K + c] / sc[B_BB * K + c]);
+            const double tr = sqrt(sc[B_TR * K + c] / sc[B_BB * K + c]);
+            if (tr <= rtol || r <= 1e-6 * rtol) {
+                sc[B_ACT * K + c] = 0.0;
+                its[c] = it;
+                rel[c] = tr;
+                active = false;
+                if (tr > rtol) status = AWG_ERR_MAXIT;
+            } else if (it >= maxit) {
+                its[c] = it;
+                rel[c] = tr;
+                status = AWG_ERR_MAXIT;
+            }
+        }
+    }
+    const int any = __syncthreads_or(active && it < maxit);
+    const int st = __syncthreads_or(status == AWG_ERR_MAXIT);
+    if (c == 0) {
+        if (st && ctl[3] == 0.0) ctl[3] = (double)AWG_ERR_MAXIT;
+        ctl[4] = 0.0;
         if (set) cudaGraphSetConditional(hc, any ? 1u : 0u);
         if (launches && add) atomicAdd(launches, (unsigned long long)add);
     }
@@ -1124,6 +1174,7 @@ struct BView {
     // coarse vectors, float64 (n0 x K, n_- x K)
     double *y0, *y2, *c1, *c2, *w0, *dd, *w1, *y0d;
     double *dpm, *dps;  // split partials of the float64 coarse GEMMs (main, side stream)
+    void *ozxm, *ozxs;  // right-hand-side slices of the tensor-core coarse products (main, side)
     T* tgp;             // p-split partials of the block-sparse transposed products
     // W passes
     void* part;    // row-block partials (compute type)
@@ -1169,8 +1220,14 @@ size_t carve_block(const Handle* h, char* base, BView<double>* vd, BView<float>*
     d.y0 = (double*)take(n0 * K * 8); d.y2 = (double*)take(n0 * K * 8); d.c1 = (double*)take(n0 * K * 8);
     d.c2 = (double*)take(n0 * K * 8); d.y0d = (double*)take(std::max(n0, nm) * K * 8);
     d.w0 = (double*)take(nm * K * 8); d.dd = (double*)take(nm * K * 8); d.w1 = (double*)take(nm * K * 8);
-    d.dpm = (double*)take((size_t)DG_SMAX * n0 * K * 8);
-    d.dps = (double*)take((size_t)DG_SMAX * nm * K * 8);
+    // both streams' partials hold a product with E^-1 or with F^-1 (H_3,hyb
+    // runs its F^-1 products on the main stream)
+    const size_t dpart = std::max((size_t)DG_SMAX * std::max(n0, nm) * K,
+                                  oz_part_elems((int)std::max(n0, nm), (int)K));
+    d.dpm = (double*)take(dpart * 8);
+    d.dps = (double*)take(dpart * 8);
+    d.ozxm = take(oz_xs_bytes((int)std::max(n0, nm), (int)K));
+    d.ozxs = take(oz_xs_bytes((int)std::max(n0, nm), (int)K));
     d.tgp = (double*)take((size_t)TG_PS * std::max<size_t>(n0, std::max(1, h->n_minus_all)) * K * 8);
     d.part = take((size_t)WT_SPLITS_MAX * ldw * K * 8);
     d.xs = take(n * K * 8);
@@ -1203,7 +1260,7 @@ size_t carve_block(const Handle* h, char* base, BView<double>* vd, BView<float>*
         f.out = (float*)d.out; f.tmpw = (float*)d.tmpw; f.loc = (float*)d.loc; f.loc2 = (float*)d.loc2;
         f.cm = (float*)d.cm; f.cf = (float*)d.cf;
         f.y0 = d.y0; f.y2 = d.y2; f.c1 = d.c1; f.c2 = d.c2; f.y0d = d.y0d; f.w0 = d.w0; f.dd = d.dd; f.w1 = d.w1;
-        f.dpm = d.dpm; f.dps = d.dps; f.tgp = (float*)d.tgp;
+        f.dpm = d.dpm; f.dps = d.dps; f.ozxm = d.ozxm; f.ozxs = d.ozxs; f.tgp = (float*)d.tgp;
         f.part = d.part; f.xs = d.xs; f.ds = d.ds; f.bt = d.bt; f.dt = d.dt; f.wacc = d.wacc; f.lt = d.lt;
         f.dscale = d.dscale; f.mx = d.mx; f.mx2 = d.mx2; f.err = d.err;
         f.pb = d.pb; f.px = d.px; f.pr = d.pr; f.pp = d.pp; f.pq = d.pq; f.pz = d.pz;
@@ -1219,6 +1276,30 @@ template <> double* fl<double>(const DevBuf& d64, const DevBuf&) { return (doubl
 template <> float* fl<float>(const DevBuf&, const DevBuf& d32) { return (float*)d32.p; }
 
 int grid_rows(int n, int rpb) { return std::max(1, std::min((n + rpb - 1) / rpb, 152 * 8)); }
+
+// Blocks of 256 threads per SM that the kernel `kern` keeps resident (its
+// registers and shared memory decide; at most 8), looked up once per kernel.
+int resident_blocks(const void* kern) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto it = cache.find(kern);
+    if (it != cache.end()) return it->second;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 256, 0) != cudaSuccess) {
+        cudaGetLastError();
+        b = 8;
+    }
+    b = std::max(1, std::min(8, b));
+    cache[kern] = b;
+    return b;
+}
+
+// Grid of a grid-stride row kernel: one wave of resident blocks (a grid of
+// 8 blocks per SM for a kernel that keeps 6 resident would run 1.33 waves)
+unsigned grid_for(const void* kern, int n, int rpb) {
+    return (unsigned)std::max(1, std::min((n + rpb - 1) / rpb, 152 * resident_blocks(kern)));
+}
 
 }  // namespace
 
@@ -1312,8 +1393,51 @@ awg_status block_prepare(Handle* h) {
     const size_t bytes = carve_block(h, nullptr, nullptr, nullptr);
     AWG_TRY(dalloc(h, h->bws, bytes));
     AWG_CUDA(cudaMemset(h->bws.p, 0, bytes));
-    (void)s;
     return AWG_OK;
+}
+
+// bfloat16 slices of every dense coarse inverse built so far (E^-1 during
+// setup, for the W solve; F^-1 and the H_3,inex inner inverses once they
+// exist) for the float64-accurate tensor-core products (ozaki.cu); a no-op
+// once all are built or with coarse_tensor_cores = 0.  Not inside a stream
+// capture (allocates and synchronises).
+awg_status oz_prepare(Handle* h) {
+    if (!h->opt.coarse_tensor_cores || !umma_available()) return AWG_OK;
+    cudaStream_t s = h->stream;
+    bool any = false;
+    auto slice = [&](int k, const DevBuf& M, int dim) -> awg_status {
+        if (!M.p || dim < 1 || h->oz_dim[k]) return AWG_OK;
+        OzMat m;
+        AWG_TRY(oz_slice_matrix((const double*)M.p, dim, h->oz_q[k], h->oz_ex[k], h, s, &m));
+        h->oz_dim[k] = dim;
+        any = true;
+        return AWG_OK;
+    };
+    AWG_TRY(slice(0, h->Einv, h->n0));
+    for (int p = 0; p < AWG_NPREC; p++) {
+        AWG_TRY(slice(1 + p, h->prec[p].Finv, h->n_minus));
+        AWG_TRY(slice(5 + p, h->prec[p].inexInv, h->n_minus));
+    }
+    if (any) AWG_CUDA(cudaStreamSynchronize(s));
+    return AWG_OK;
+}
+
+// The tensor-core slices of the dense coarse inverse at Mx, if built.
+static bool oz_of(const Handle* h, const double* Mx, OzMat* out) {
+    int k = -1;
+    if (Mx == (const double*)h->Einv.p) k = 0;
+    for (int p = 0; p < AWG_NPREC && k < 0; p++) {
+        if (Mx == (const double*)h->prec[p].Finv.p) k = 1 + p;
+        else if (Mx == (const double*)h->prec[p].inexInv.p) k = 5 + p;
+    }
+    if (k < 0 || !h->oz_dim[k] || !Mx) return false;
+    const int dim = h->oz_dim[k];
+    out->q = h->oz_q[k].p;
+    out->ex = (const int*)h->oz_ex[k].p;
+    out->dim = dim;
+    out->dimp = (dim + 127) / 128 * 128;
+    out->ldk = (dim + 63) / 64 * 64;
+    return true;
 }
 
 namespace {
@@ -1325,7 +1449,7 @@ struct BlockApply {
     Slot sl;
     using A = T;
 
-    static dim3 rows_grid(int n) { return dim3(grid_rows(n, RM<T, K>::RPB)); }
+    static dim3 rows_grid(const void* kern, int n) { return dim3(grid_for(kern, n, RM<T, K>::RPB)); }
 
     const T* aval() const { return fl<T>(h->val, h->bval32); }
     const T* vm() const { return fl<T>(h->Vm, h->bvm32); }
@@ -1370,7 +1494,7 @@ struct BlockApply {
                           v.cm, s));
         }
         ProfScope ps_(h, AWG_PROF_SPMV, s);
-        kb_aplus<T, K><<<rows_grid(h->n), 256, 0, s>>>(
+        kb_aplus<T, K><<<rows_grid((const void*)kb_aplus<T, K>, h->n), 256, 0, s>>>(
             h->n, (int*)h->rowptr.p, (int*)h->colidx.p, aval(), X, (int*)h->inc_ptr.p, (int*)h->inc_pos.p,
             (int*)h->inc_sub.p, (int*)h->sub_ptr.p, (int*)h->nm_ptr.p, (int64_t*)h->vm_off.p, vm(),
             vmb ? v.cm : nullptr, Yin, sign, Y);
@@ -1401,7 +1525,7 @@ struct BlockApply {
             cc = v.cf;
         }
         ProfScope ps_(h, AWG_PROF_PROLONG, s);
-        kb_blk_prolong<T, K><<<rows_grid(h->n), 256, 0, s>>>(
+        kb_blk_prolong<T, K><<<rows_grid((const void*)kb_blk_prolong<T, K>, h->n), 256, 0, s>>>(
             h->n, (int*)h->inc_ptr.p, (int*)h->inc_pos.p, (int*)h->inc_sub.p, (int*)h->sub_ptr.p,
             (int*)h->mode_ptr.p, (int64_t*)h->z_off.p, zb(), cc, Y, alpha, beta, V, gamma, V2);
         AWG_LAUNCH();
@@ -1414,6 +1538,13 @@ struct BlockApply {
                      double beta, double* part, cudaStream_t s) {
         if (dim == 0) return AWG_OK;
         ProfScope ps_(h, AWG_PROF_COARSE, s);
+        OzMat om;
+        if (oz_of(h, Mx, &om) && om.dim == dim) {
+            // float64-accurate slice products on the tensor cores (ozaki.cu)
+            AWG_TRY(oz_gemm(om, K, X, Y, alpha, Sub, beta, part == v.dpm ? v.ozxm : v.ozxs, part, v.err, s));
+            extra_launches(h, 2);
+            return AWG_OK;
+        }
         const int tiles = (dim + DG_RB - 1) / DG_RB;
         const int bps = h->bt_dense[kidx] > 0 ? h->bt_dense[kidx] : 4;  // (autotuned) blocks per SM
         int S = std::max(1, std::min(DG_SMAX, (bps * 152 + tiles - 1) / tiles));
@@ -1439,7 +1570,7 @@ struct BlockApply {
                     extra_launches(h, 1);
                 }
                 ProfScope ps_(h, AWG_PROF_PROLONG, s);
-                kb_prolong<T, K><<<rows_grid(h->n), 256, 0, s>>>(h->n, (int*)h->inc_ptr.p, (int*)h->inc_pos.p, v.loc2,
+                kb_prolong<T, K><<<rows_grid((const void*)kb_prolong<T, K>, h->n), 256, 0, s>>>(h->n, (int*)h->inc_ptr.p, (int*)h->inc_pos.p, v.loc2,
                                                                 Y, (T)1, (T)0, nullptr, (T)0);
                 AWG_LAUNCH();
                 return AWG_OK;
@@ -1465,7 +1596,7 @@ struct BlockApply {
         }
         AWG_LAUNCH();
         ProfScope ps_(h, AWG_PROF_PROLONG, s);
-        kb_prolong<T, K><<<rows_grid(h->n), 256, 0, s>>>(h->n, (int*)h->inc_ptr.p, (int*)h->inc_pos.p, v.loc2, Y,
+        kb_prolong<T, K><<<rows_grid((const void*)kb_prolong<T, K>, h->n), 256, 0, s>>>(h->n, (int*)h->inc_ptr.p, (int*)h->inc_pos.p, v.loc2, Y,
                                                         (T)1, (T)0, nullptr, (T)0);
         AWG_LAUNCH();
         return AWG_OK;
@@ -1665,7 +1796,7 @@ struct BlockApply {
         switch (which) {
             case 0: {
                 ProfScope ps_(h, AWG_PROF_SPMV, s);
-                kb_aplus<T, K><<<rows_grid(h->n), 256, 0, s>>>(
+                kb_aplus<T, K><<<rows_grid((const void*)kb_aplus<T, K>, h->n), 256, 0, s>>>(
                     h->n, (int*)h->rowptr.p, (int*)h->colidx.p, aval(), X, nullptr, nullptr, nullptr, nullptr,
                     nullptr, nullptr, nullptr, nullptr, nullptr, (T)1, Y);
                 AWG_LAUNCH();
@@ -1833,9 +1964,9 @@ awg_status pcg_k(Handle* h, int prec, const double* b, double* x, int nrhs, int 
     AWG_TRY(prof_vec([&] { kb_from_cols<double><<<tg, tb, 0, s>>>(n, nrhs, ld, K, b, v.pb); }));
     AWG_CUDA(cudaMemsetAsync(v.px, 0, len * 8, s));
     AWG_CUDA(cudaMemcpyAsync(v.pr, v.pb, len * 8, cudaMemcpyDeviceToDevice, s));
-    AWG_TRY(prof_vec([&] { kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pb, v.pb, v.red, v.cnt, sc + B_BB * K); }));
+    AWG_TRY(prof_vec([&] { kb_coldot<K><<<grid_for((const void*)kb_coldot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.pb, v.pb, v.red, v.cnt, sc + B_BB * K); }));
     AWG_TRY(apply64_any(h, K, 4 + h->opt.variant, prec, v.pr, v.pz, s, slot0(h)));
-    AWG_TRY(prof_vec([&] { kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, sc + B_RZ * K); }));
+    AWG_TRY(prof_vec([&] { kb_coldot<K><<<grid_for((const void*)kb_coldot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, sc + B_RZ * K); }));
     AWG_CUDA(cudaMemcpyAsync(v.pp, v.pz, len * 8, cudaMemcpyDeviceToDevice, s));
     std::vector<double> hs(B_NSC * K);
     AWG_CUDA(cudaMemcpyAsync(hs.data(), sc, B_NSC * K * 8, cudaMemcpyDeviceToHost, s));
@@ -1857,10 +1988,10 @@ awg_status pcg_k(Handle* h, int prec, const double* b, double* x, int nrhs, int 
     AWG_TRY(upload_act());
     auto true_resid = [&]() -> awg_status {
         AWG_TRY(prof_vec([&] {
-            kb_resid<K><<<gr, 256, 0, s>>>(n, (int*)h->rowptr.p, (int*)h->colidx.p, (double*)h->val.p, v.pb, v.px,
+            kb_resid<K><<<grid_for((const void*)kb_resid<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, (int*)h->rowptr.p, (int*)h->colidx.p, (double*)h->val.p, v.pb, v.px,
                                            v.pq);
         }));
-        AWG_TRY(prof_vec([&] { kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pq, v.pq, v.red, v.cnt, sc + B_TR * K); }));
+        AWG_TRY(prof_vec([&] { kb_coldot<K><<<grid_for((const void*)kb_coldot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.pq, v.pq, v.red, v.cnt, sc + B_TR * K); }));
         AWG_CUDA(cudaMemcpyAsync(hs.data() + B_TR * K, sc + B_TR * K, K * 8, cudaMemcpyDeviceToHost, s));
         AWG_CUDA(cudaStreamSynchronize(s));
         return AWG_OK;
@@ -1869,11 +2000,11 @@ awg_status pcg_k(Handle* h, int prec, const double* b, double* x, int nrhs, int 
         if (it >= h->opt.maxit) { st = AWG_ERR_MAXIT; break; }
         {
             ProfScope ps_(h, AWG_PROF_SPMV, s);
-            kb_spmv_dot<K><<<gr, 256, 0, s>>>(n, (int*)h->rowptr.p, (int*)h->colidx.p, (double*)h->val.p, v.pp, v.pq,
+            kb_spmv_dot<K><<<grid_for((const void*)kb_spmv_dot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, (int*)h->rowptr.p, (int*)h->colidx.p, (double*)h->val.p, v.pp, v.pq,
                                               v.red, v.cnt, sc + B_PQ * K);
         }
         AWG_LAUNCH();
-        AWG_TRY(prof_vec([&] { kb_pcg_xr<K><<<gr, 256, 0, s>>>(n, sc, v.pp, v.pq, v.px, v.pr, v.red, v.cnt); }));
+        AWG_TRY(prof_vec([&] { kb_pcg_xr<K><<<grid_for((const void*)kb_pcg_xr<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, sc, v.pp, v.pq, v.px, v.pr, v.red, v.cnt); }));
         it++;
         AWG_CUDA(cudaMemcpyAsync(hs.data(), sc, 3 * K * 8, cudaMemcpyDeviceToHost, s));
         AWG_CUDA(cudaStreamSynchronize(s));
@@ -1902,8 +2033,8 @@ awg_status pcg_k(Handle* h, int prec, const double* b, double* x, int nrhs, int 
         if (nact == 0) break;
         if (changed) AWG_TRY(upload_act());
         AWG_TRY(apply64_any(h, K, 4 + h->opt.variant, prec, v.pr, v.pz, s, slot0(h)));
-        AWG_TRY(prof_vec([&] { kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, sc + B_RZN * K); }));
-        AWG_TRY(prof_vec([&] { kb_pcg_p<K><<<gr, 256, 0, s>>>(n, sc, v.pz, v.pp, v.cnt); }));
+        AWG_TRY(prof_vec([&] { kb_coldot<K><<<grid_for((const void*)kb_coldot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, sc + B_RZN * K); }));
+        AWG_TRY(prof_vec([&] { kb_pcg_p<K><<<grid_for((const void*)kb_pcg_p<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, sc, v.pz, v.pp, v.cnt); }));
     }
     bool need = false;
     for (int c = 0; c < nrhs; c++)
@@ -1931,6 +2062,38 @@ awg_status pcg_k(Handle* h, int prec, const double* b, double* x, int nrhs, int 
 
 }  // namespace
 
+// Device-side stopping test after an x, r update: candidates (recurrence
+// residual <= rtol), then, only in iterations that have one, the true
+// residual B - A X of every column (into v.pq, free until the next q = A p)
+// and its column norms, then the confirmation that stops or continues each
+// candidate and sets the loop condition.
+template <int K>
+awg_status stop_test_k(Handle* h, const BView<double>& v, cudaStream_t s, cudaGraphConditionalHandle hc, int set,
+                       int add) {
+    const int n = h->n;
+    const unsigned gr = grid_rows(n, RM<double, K>::RPB);
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        kb_pcg_cond<K><<<1, K, 0, s>>>(v.sc, v.ctl, v.gits, v.grel);
+        AWG_LAUNCH();
+    }
+    {
+        ProfScope ps_(h, AWG_PROF_SPMV, s);
+        kb_resid<K><<<grid_for((const void*)kb_resid<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, (int*)h->rowptr.p, (int*)h->colidx.p, (double*)h->val.p, v.pb, v.px,
+                                       v.pq, v.ctl + 4);
+        AWG_LAUNCH();
+    }
+    {
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        kb_coldot<K><<<grid_for((const void*)kb_coldot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.pq, v.pq, v.red, v.cnt, v.sc + B_TR * K, v.ctl + 4);
+        AWG_LAUNCH();
+    }
+    ProfScope ps_(h, AWG_PROF_VECTOR, s);
+    kb_pcg_confirm<K><<<1, K, 0, s>>>(v.sc, v.ctl, v.gits, v.grel, hc, set, v.glaunch, add);
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
 // One PCG iteration of K columns issued on the handle's streams (the body of
 // the graph loop): z = H r, rz_new, p update, q = A p, x and r update, stop test.
 template <int K>
@@ -1941,29 +2104,26 @@ awg_status pcg_body_k(Handle* h, int prec, const BView<double>& v, cudaStream_t 
     AWG_TRY(apply64_any(h, K, 4 + h->opt.variant, prec, v.pr, v.pz, s, sl));
     {
         ProfScope ps_(h, AWG_PROF_VECTOR, s);
-        kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, v.sc + B_RZN * K);
+        kb_coldot<K><<<grid_for((const void*)kb_coldot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, v.sc + B_RZN * K);
         AWG_LAUNCH();
     }
     {
         ProfScope ps_(h, AWG_PROF_VECTOR, s);
-        kb_pcg_p<K><<<gr, 256, 0, s>>>(n, v.sc, v.pz, v.pp, v.cnt);
+        kb_pcg_p<K><<<grid_for((const void*)kb_pcg_p<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.sc, v.pz, v.pp, v.cnt);
         AWG_LAUNCH();
     }
     {
         ProfScope ps_(h, AWG_PROF_SPMV, s);
-        kb_spmv_dot<K><<<gr, 256, 0, s>>>(n, (int*)h->rowptr.p, (int*)h->colidx.p, (double*)h->val.p, v.pp, v.pq,
+        kb_spmv_dot<K><<<grid_for((const void*)kb_spmv_dot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, (int*)h->rowptr.p, (int*)h->colidx.p, (double*)h->val.p, v.pp, v.pq,
                                           v.red, v.cnt, v.sc + B_PQ * K);
         AWG_LAUNCH();
     }
     {
         ProfScope ps_(h, AWG_PROF_VECTOR, s);
-        kb_pcg_xr<K><<<gr, 256, 0, s>>>(n, v.sc, v.pp, v.pq, v.px, v.pr, v.red, v.cnt);
+        kb_pcg_xr<K><<<grid_for((const void*)kb_pcg_xr<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.sc, v.pp, v.pq, v.px, v.pr, v.red, v.cnt);
         AWG_LAUNCH();
     }
-    ProfScope ps_(h, AWG_PROF_VECTOR, s);
-    kb_pcg_cond<K><<<1, K, 0, s>>>(v.sc, v.ctl, v.gits, v.grel, hc, set, v.glaunch, add);
-    AWG_LAUNCH();
-    return AWG_OK;
+    return stop_test_k<K>(h, v, s, hc, set, add);
 }
 
 // The loop graph of (prec, K): a conditional while node whose body is one
@@ -2016,7 +2176,7 @@ awg_status pcg_graph_k(Handle* h, int prec, const BView<double>& v, cudaGraphExe
             if (t != cudaGraphNodeTypeKernel) continue;
             cudaKernelNodeParams kp;
             AWG_CUDA(cudaGraphKernelNodeGetParams(nd, &kp));
-            if (kp.func != (void*)kb_pcg_cond<K>) continue;
+            if (kp.func != (void*)kb_pcg_confirm<K>) continue;
             int* addp = (int*)kp.kernelParams[7];
             *addp = body_launches;
             AWG_CUDA(cudaGraphKernelNodeSetParams(nd, &kp));
@@ -2050,7 +2210,7 @@ awg_status pcg_async_k(Handle* h, int prec, const double* b, double* x, int nrhs
     AWG_CUDA(cudaMemcpyAsync(v.pr, v.pb, len * 8, cudaMemcpyDeviceToDevice, s));
     {
         ProfScope ps_(h, AWG_PROF_VECTOR, s);
-        kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pb, v.pb, v.red, v.cnt, v.sc + B_BB * K);
+        kb_coldot<K><<<grid_for((const void*)kb_coldot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.pb, v.pb, v.red, v.cnt, v.sc + B_BB * K);
         AWG_LAUNCH();
     }
     {
@@ -2062,26 +2222,22 @@ awg_status pcg_async_k(Handle* h, int prec, const double* b, double* x, int nrhs
     AWG_TRY(apply64_any(h, K, 4 + h->opt.variant, prec, v.pr, v.pz, s, sl));
     {
         ProfScope ps_(h, AWG_PROF_VECTOR, s);
-        kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, v.sc + B_RZ * K);
+        kb_coldot<K><<<grid_for((const void*)kb_coldot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, v.sc + B_RZ * K);
         AWG_LAUNCH();
     }
     AWG_CUDA(cudaMemcpyAsync(v.pp, v.pz, len * 8, cudaMemcpyDeviceToDevice, s));
     {
         ProfScope ps_(h, AWG_PROF_SPMV, s);
-        kb_spmv_dot<K><<<gr, 256, 0, s>>>(n, (int*)h->rowptr.p, (int*)h->colidx.p, (double*)h->val.p, v.pp, v.pq,
+        kb_spmv_dot<K><<<grid_for((const void*)kb_spmv_dot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, (int*)h->rowptr.p, (int*)h->colidx.p, (double*)h->val.p, v.pp, v.pq,
                                           v.red, v.cnt, v.sc + B_PQ * K);
         AWG_LAUNCH();
     }
     {
         ProfScope ps_(h, AWG_PROF_VECTOR, s);
-        kb_pcg_xr<K><<<gr, 256, 0, s>>>(n, v.sc, v.pp, v.pq, v.px, v.pr, v.red, v.cnt);
+        kb_pcg_xr<K><<<grid_for((const void*)kb_pcg_xr<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.sc, v.pp, v.pq, v.px, v.pr, v.red, v.cnt);
         AWG_LAUNCH();
     }
-    {
-        ProfScope ps_(h, AWG_PROF_VECTOR, s);
-        kb_pcg_cond<K><<<1, K, 0, s>>>(v.sc, v.ctl, v.gits, v.grel, 0, 0, nullptr, 0);
-        AWG_LAUNCH();
-    }
+    AWG_TRY(stop_test_k<K>(h, v, s, 0, 0, 0));
     // the loop graph is captured after the first iteration has been issued
     // (every kernel attribute and tensor-map entry point is set up by then)
     cudaGraphExec_t exec;
@@ -2132,6 +2288,7 @@ awg_status block_pcg_async(Handle* h, int prec, const double* b, double* x, int 
                            int* d_iters, double* d_relres, int* d_status, cudaStream_t s) {
     if (nrhs < 1 || nrhs > 2 * BLK_KMAX) return AWG_ERR_INVALID_ARG;
     AWG_TRY(block_prepare(h));
+    AWG_TRY(oz_prepare(h));
     if (nrhs <= BLK_KMAX)
         return pcg_async_group(h, prec, b, x, nrhs, ld, rtol, d_iters, d_relres, d_status, slot0(h));
     // two groups side by side: columns [0, 64) on slot 0, the rest on slot 1
@@ -2192,10 +2349,10 @@ awg_status wsolve_k(Handle* h, int wprec, const double* B, double* X, int k, dou
     AWG_LAUNCH();
     AWG_CUDA(cudaMemsetAsync(v.px, 0, len * 8, s));
     AWG_CUDA(cudaMemcpyAsync(v.pr, v.pb, len * 8, cudaMemcpyDeviceToDevice, s));
-    kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pb, v.pb, v.red, v.cnt, sc + B_BB * K);
+    kb_coldot<K><<<grid_for((const void*)kb_coldot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.pb, v.pb, v.red, v.cnt, sc + B_BB * K);
     AWG_LAUNCH();
     AWG_TRY(apply64_any(h, K, 3, wprec, v.pr, z, s, slot0(h)));
-    kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, z, v.red, v.cnt, sc + B_RZ * K);
+    kb_coldot<K><<<grid_for((const void*)kb_coldot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.pr, z, v.red, v.cnt, sc + B_RZ * K);
     AWG_LAUNCH();
     AWG_CUDA(cudaMemcpyAsync(v.pp, z, len * 8, cudaMemcpyDeviceToDevice, s));
     std::vector<double> hs(B_NSC * K), act(K, 0.0);
@@ -2209,9 +2366,9 @@ awg_status wsolve_k(Handle* h, int wprec, const double* B, double* X, int k, dou
     double wst = 0.0;
     while (nact > 0) {
         AWG_TRY(bd.aplus(v.pp, v.pq, nullptr, 1.0, s));  // q = A_+ p
-        kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pp, v.pq, v.red, v.cnt, sc + B_PQ * K);
+        kb_coldot<K><<<grid_for((const void*)kb_coldot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.pp, v.pq, v.red, v.cnt, sc + B_PQ * K);
         AWG_LAUNCH();
-        kb_pcg_xr<K><<<gr, 256, 0, s>>>(n, sc, v.pp, v.pq, v.px, v.pr, v.red, v.cnt);
+        kb_pcg_xr<K><<<grid_for((const void*)kb_pcg_xr<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, sc, v.pp, v.pq, v.px, v.pr, v.red, v.cnt);
         AWG_LAUNCH();
         AWG_CUDA(cudaMemcpyAsync(hs.data(), sc, 3 * K * 8, cudaMemcpyDeviceToHost, s));
         AWG_CUDA(cudaStreamSynchronize(s));
@@ -2232,11 +2389,11 @@ awg_status wsolve_k(Handle* h, int wprec, const double* B, double* X, int k, dou
         if (changed) AWG_CUDA(cudaMemcpyAsync(sc + B_ACT * K, act.data(), K * 8, cudaMemcpyHostToDevice, s));
         std::swap(z, zo);
         AWG_TRY(apply64_any(h, K, 3, wprec, v.pr, z, s, slot0(h)));  // z = H_2 r
-        kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, z, v.red, v.cnt, sc + B_RZN * K);
+        kb_coldot<K><<<grid_for((const void*)kb_coldot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.pr, z, v.red, v.cnt, sc + B_RZN * K);
         AWG_LAUNCH();
-        kb_coldot<K><<<gr, 256, 0, s>>>(n, v.pr, zo, v.red, v.cnt, sc + B_TR * K);
+        kb_coldot<K><<<grid_for((const void*)kb_coldot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.pr, zo, v.red, v.cnt, sc + B_TR * K);
         AWG_LAUNCH();
-        kb_pcg_p_flex<K><<<gr, 256, 0, s>>>(n, sc, z, v.pp, v.cnt);
+        kb_pcg_p_flex<K><<<grid_for((const void*)kb_pcg_p_flex<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, sc, z, v.pp, v.cnt);
         AWG_LAUNCH();
     }
     kb_to_cols<double><<<tg, tb, 0, s>>>(n, k, n, K, v.px, X);
@@ -2250,6 +2407,7 @@ awg_status wsolve_k(Handle* h, int wprec, const double* B, double* X, int k, dou
 awg_status block_solve_w(Handle* h, int wprec, const double* Vhat, double* W, int nm, double rtol, int maxit,
                          int* its_max, double* worst, cudaStream_t s) {
     AWG_TRY(block_prepare(h));
+    AWG_TRY(oz_prepare(h));
     *its_max = 0;
     *worst = 0.0;
     for (int c0 = 0; c0 < nm; c0 += BLK_KMAX) {
@@ -2276,6 +2434,7 @@ awg_status block_apply(Handle* h, int which, int prec, const double* x, double* 
                        cudaStream_t s) {
     if (nrhs < 1 || nrhs > BLK_KMAX) return AWG_ERR_INVALID_ARG;
     AWG_TRY(block_prepare(h));
+    AWG_TRY(oz_prepare(h));
     const int K = pick_k(nrhs);
     BView<double> v;
     carve_block(h, (char*)h->bws.p, &v, nullptr);
@@ -2289,9 +2448,77 @@ awg_status block_apply(Handle* h, int which, int prec, const double* x, double* 
     return AWG_OK;
 }
 
+// Y = M X for a dense coarse inverse M of the handle (which: 0 E^-1, 1 F^-1
+// of form prec, 2 the H_3,inex inner inverse of form prec), X and Y
+// column-major dim x nrhs (ld = dim), through the block path's coarse
+// product: engine 0 the float64 CUDA-core GEMM, 1 the tensor-core slice
+// products, 2 the same with reduction splits of 256 terms (exercises the
+// split path on small coarse spaces).
+awg_status block_coarse_apply(Handle* h, int which, int prec, int engine, const double* x, double* y, int nrhs,
+                              cudaStream_t s) {
+    if (nrhs < 1 || nrhs > BLK_KMAX || which < 0 || which > 2 || engine < 0 || engine > 2) return AWG_ERR_INVALID_ARG;
+    const DevBuf& M = which == 0 ? h->Einv : (which == 1 ? h->prec[prec].Finv : h->prec[prec].inexInv);
+    const int dim = which == 0 ? h->n0 : h->n_minus;
+    if (!M.p || dim < 1) return AWG_ERR_STATE;
+    AWG_TRY(block_prepare(h));
+    AWG_TRY(oz_prepare(h));
+    const int K = pick_k(nrhs);
+    OzMat om;
+    const bool have = oz_of(h, (const double*)M.p, &om);
+    if (engine > 0 && !have) return AWG_ERR_STATE;
+    const int cps = engine == 2 ? 4 : OZ_CHUNKS_MAX;
+    const size_t len = (size_t)dim * K;
+    const size_t part_elems = std::max((size_t)DG_SMAX * len, oz_part_elems(dim, K, cps));
+    double *xr = nullptr, *yr = nullptr, *part = nullptr;
+    void* xs = nullptr;
+    int* err = nullptr;
+    AWG_CUDA(cudaMallocAsync(&xr, len * 8, s));
+    AWG_CUDA(cudaMallocAsync(&yr, len * 8, s));
+    AWG_CUDA(cudaMallocAsync(&part, part_elems * 8, s));
+    AWG_CUDA(cudaMallocAsync(&xs, oz_xs_bytes(dim, K), s));
+    AWG_CUDA(cudaMallocAsync(&err, 4, s));
+    AWG_CUDA(cudaMemsetAsync(err, 0, 4, s));
+    const dim3 tg((dim + 31) / 32, (K + 31) / 32), tb(32, 8);
+    kb_from_cols<double><<<tg, tb, 0, s>>>(dim, nrhs, dim, K, x, xr);
+    AWG_LAUNCH();
+    awg_status st = AWG_OK;
+    if (engine > 0) {
+        st = oz_gemm(om, K, xr, yr, 1.0, nullptr, 0.0, xs, part, err, s, cps);
+    } else {
+        const int tiles = (dim + DG_RB - 1) / DG_RB;
+        int S = std::max(1, std::min(DG_SMAX, (4 * 152 + tiles - 1) / tiles));
+        int jlen = (dim + S - 1) / S;
+        jlen = (jlen + DG_JC - 1) / DG_JC * DG_JC;
+        S = (dim + jlen - 1) / jlen;
+        if (K == 16) kb_dense_part<16><<<dim3(tiles, S), 64, 0, s>>>(dim, jlen, (const double*)M.p, xr, part);
+        else if (K == 32) kb_dense_part<32><<<dim3(tiles, S), 128, 0, s>>>(dim, jlen, (const double*)M.p, xr, part);
+        else kb_dense_part<64><<<dim3(tiles, S), 256, 0, s>>>(dim, jlen, (const double*)M.p, xr, part);
+        AWG_LAUNCH();
+        const unsigned g = (unsigned)((len + 255) / 256);
+        if (K == 16) kb_dense_sum<16><<<g, 256, 0, s>>>(dim, S, part, yr, 1.0, nullptr, 0.0);
+        else if (K == 32) kb_dense_sum<32><<<g, 256, 0, s>>>(dim, S, part, yr, 1.0, nullptr, 0.0);
+        else kb_dense_sum<64><<<g, 256, 0, s>>>(dim, S, part, yr, 1.0, nullptr, 0.0);
+        AWG_LAUNCH();
+    }
+    if (st == AWG_OK) {
+        kb_to_cols<double><<<tg, tb, 0, s>>>(dim, nrhs, dim, K, yr, y);
+        AWG_LAUNCH();
+    }
+    int herr = 0;
+    AWG_CUDA(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s));
+    for (void* ptr : {(void*)xr, (void*)yr, (void*)part, xs, (void*)err}) AWG_CUDA(cudaFreeAsync(ptr, s));
+    AWG_CUDA(cudaStreamSynchronize(s));
+    if (herr) {
+        fprintf(stderr, "libawg: tensor-core coarse product reported error %d\n", herr);
+        return AWG_ERR_CUDA;
+    }
+    return st;
+}
+
 awg_status block_pcg(Handle* h, int prec, const double* b, double* x, int nrhs, int ld, double rtol, int* iters,
                      double* relres, cudaStream_t s) {
     AWG_TRY(block_prepare(h));
+    AWG_TRY(oz_prepare(h));
     awg_status worst = AWG_OK;
     for (int c0 = 0; c0 < nrhs; c0 += BLK_KMAX) {
         const int k = std::min(BLK_KMAX, nrhs - c0);

@@ -23,6 +23,12 @@ awg_status block_apply(Handle* h, int which, int prec, const double* x, double* 
 awg_status block_pcg(Handle* h, int prec, const double* b, double* x, int nrhs, int ld, double rtol, int* iters,
                      double* relres, cudaStream_t s);
 
+// Y = M X with a dense coarse inverse (which 0 E^-1, 1 F^-1, 2 H_3,inex
+// inner inverse of form prec) through the block coarse product (engine 0
+// float64 CUDA cores, 1 tensor-core slices, 2 the same with short reduction
+// splits); X, Y column-major dim x nrhs; synchronises s
+awg_status block_coarse_apply(Handle* h, int which, int prec, int engine, const double* x, double* y, int nrhs,
+                              cudaStream_t s);
 // Block PCG whose iterations run as one CUDA graph launch (conditional
 // while node, device-side stopping test); asynchronous on s.
 awg_status block_pcg_async(Handle* h, int prec, const double* b, double* x, int nrhs, int ld, double rtol,
@@ -69,6 +75,35 @@ awg_status umma_local_tiles(const UmmaLocal& u, const int64_t* g32off, const flo
 // n x K; lt: scratch of kc_prefix[N] * 2 * K * 32 floats
 awg_status umma_local(const UmmaLocal& u, int K, const float* X, float* lt, float* out, int* d_err,
                       cudaStream_t s);
+
+// Float64-accurate products with a dense coarse inverse on the tensor cores
+// (ozaki.cu): the matrix is cut once into OZ_SLICES bfloat16 slices of
+// OZ_BITS-bit integer digits with power-of-two row scales, the right-hand
+// sides per call, and the exact slice products are summed in float64.
+constexpr int OZ_BITS = 7;
+constexpr int OZ_SLICES = 8;
+struct OzMat {
+    const void* q = nullptr;   // bfloat16 slices, OZ_SLICES x dimp x ldk
+    const int* ex = nullptr;   // row exponents, int32[dimp]
+    int dim = 0, dimp = 0, ldk = 0;
+};
+// bytes of the slices of a dim x dim matrix; doubles of the partial sums and
+// bytes of the right-hand-side slices (with the column exponents) of one
+// product with K columns
+size_t oz_slices_bytes(int dim);
+constexpr int OZ_CHUNKS_MAX = 63;  // 64-deep stages per reduction split: sums of <= 4032 products stay exact
+size_t oz_part_elems(int dim, int K, int chunks_per_split = OZ_CHUNKS_MAX);
+size_t oz_xs_bytes(int dim, int K);
+// slices of M (dim x dim row-major float64) into q / ex (allocated in the
+// handle when empty); fills *out
+awg_status oz_slice_matrix(const double* M, int dim, DevBuf& q, DevBuf& ex, Handle* h, cudaStream_t s,
+                           OzMat* out);
+// Y = alpha M X + beta Sub (Sub may be NULL), X and Y row-major dim x K
+// float64 (K = 16, 32, 64); xs: oz_xs_bytes(dim, K) bytes, part:
+// oz_part_elems(dim, K, chunks_per_split) doubles of scratch; the reduction
+// is split every chunks_per_split x 64 (<= OZ_CHUNKS_MAX) terms
+awg_status oz_gemm(const OzMat& m, int K, const double* X, double* Y, double alpha, const double* Sub, double beta,
+                   void* xs, double* part, int* d_err, cudaStream_t s, int chunks_per_split = OZ_CHUNKS_MAX);
 
 // Whether the tensor-core passes are available (driver entry point found).
 bool umma_available();

@@ -25,7 +25,7 @@ awg_status set_smem_limits(Handle* h);
 namespace {
 
 constexpr char kTag[8] = {'A', 'W', 'G', 'H', 'N', 'D', 'L', '\n'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 constexpr size_t kChunk = (size_t)64 << 20;  // host staging of the device copies
 
 struct Out {
@@ -129,17 +129,94 @@ std::vector<DevBuf*> buffers(Handle& h) {
     return b;
 }
 
-// the tables agree with the scalars (a file from another build or a
-// damaged one is refused before any device work)
+template <class T>
+bool nondecreasing(const std::vector<T>& v) {
+    if (v.empty() || v[0] != 0) return false;
+    for (size_t i = 1; i < v.size(); i++)
+        if (v[i] < v[i - 1]) return false;
+    return true;
+}
+
+// the tables agree with the scalars and with each other (a file from another
+// build or a damaged one is refused before any device work): every prefix
+// table starts at 0 and never decreases, its steps are the per-subdomain
+// sizes it is built from, and every n^s lies in [1, max_ns]
 bool consistent(const Handle& h) {
     const size_t N = (size_t)h.N;
-    return h.n >= 1 && h.nnz >= h.n && h.N >= 1 && h.N <= h.n && h.n0 >= 0 && h.n_minus >= 0 &&
-           h.ldw >= h.n_minus && h.max_ns >= 1 && h.h_ns.size() == N && h.h_sub_ptr.size() == N + 1 &&
-           h.h_dense_off.size() == N + 1 && h.h_nm.size() == N && h.h_nstrict.size() == N &&
-           h.h_nm_ptr.size() == N + 1 && h.h_vm_off.size() == N + 1 && h.h_modes.size() == N &&
-           h.h_mode_ptr.size() == N + 1 && h.h_z_off.size() == N + 1 && h.h_wcol_ptr.size() == N + 1 &&
-           (h.h_g32_off.empty() || h.h_g32_off.size() == N + 1) && h.h_mode_ptr[N] == h.n0 &&
-           h.h_wcol_ptr[N] == h.n_minus && h.h_sub_ptr[N] == h.sum_ns && h.h_dense_off[N] == h.dense_total;
+    if (!(h.n >= 1 && h.nnz >= h.n && h.N >= 1 && h.N <= h.n && h.n0 >= 0 && h.n_minus >= 0 &&
+          h.n_minus_all >= h.n_minus && h.ldw >= h.n_minus && h.ldw % 8 == 0 && h.max_ns >= 1 &&
+          h.max_ns <= h.n && h.h_ns.size() == N && h.h_sub_ptr.size() == N + 1 && h.h_dense_off.size() == N + 1 &&
+          h.h_nm.size() == N && h.h_nstrict.size() == N && h.h_nm_ptr.size() == N + 1 &&
+          h.h_vm_off.size() == N + 1 && h.h_modes.size() == N && h.h_mode_ptr.size() == N + 1 &&
+          h.h_z_off.size() == N + 1 && h.h_wcol_ptr.size() == N + 1 &&
+          (h.h_g32_off.empty() || h.h_g32_off.size() == N + 1)))
+        return false;
+    for (const auto* v : {&h.h_sub_ptr, &h.h_nm_ptr, &h.h_mode_ptr, &h.h_wcol_ptr})
+        if (!nondecreasing(*v)) return false;
+    for (const auto* v : {&h.h_dense_off, &h.h_vm_off, &h.h_z_off})
+        if (!nondecreasing(*v)) return false;
+    if (!h.h_g32_off.empty() && !nondecreasing(h.h_g32_off)) return false;
+    int mx = 0;
+    for (size_t t = 0; t < N; t++) {
+        const int64_t m = h.h_ns[t];
+        if (m < 1 || m > h.max_ns || h.h_sub_ptr[t + 1] - h.h_sub_ptr[t] != m) return false;
+        if (h.h_dense_off[t + 1] - h.h_dense_off[t] != m * m) return false;
+        if (!h.h_g32_off.empty() && h.h_g32_off[t + 1] - h.h_g32_off[t] != m * ((m + 3) & ~3)) return false;
+        if (h.h_nm[t] < 0 || h.h_nm[t] > m || h.h_nm_ptr[t + 1] - h.h_nm_ptr[t] != h.h_nm[t]) return false;
+        if (h.h_vm_off[t + 1] - h.h_vm_off[t] != m * h.h_nm[t]) return false;
+        if (h.h_nstrict[t] < 0 || h.h_nstrict[t] > h.h_nm[t] ||
+            h.h_wcol_ptr[t + 1] - h.h_wcol_ptr[t] != h.h_nstrict[t])
+            return false;
+        if (h.h_modes[t] < 0 || h.h_mode_ptr[t + 1] - h.h_mode_ptr[t] != h.h_modes[t]) return false;
+        if (h.h_z_off[t + 1] - h.h_z_off[t] != m * h.h_modes[t]) return false;
+        mx = std::max(mx, (int)m);
+    }
+    return mx == h.max_ns && h.h_mode_ptr[N] == h.n0 && h.h_wcol_ptr[N] == h.n_minus &&
+           h.h_nm_ptr[N] == h.n_minus_all && h.h_sub_ptr[N] == h.sum_ns && h.h_dense_off[N] == h.dense_total;
+}
+
+// Smallest byte count of each device buffer (in the order of buffers()) that
+// the kernels can index given the scalars and tables: `need` bytes, or, for
+// a buffer that may be absent (a storage form not built, the H_3,inex
+// matrix), 0 or at least `need`.
+struct Need {
+    uint64_t need;
+    bool optional;
+};
+std::vector<Need> needs(const Handle& h) {
+    const uint64_t n = h.n, nnz = h.nnz, N = h.N, S = (uint64_t)h.sum_ns, n0 = h.n0, nm = h.n_minus;
+    const uint64_t ldw = h.ldw, N1 = N + 1;
+    std::vector<Need> r = {
+        {(n + 1) * 4, false}, {nnz * 4, false}, {nnz * 8, false}, {N * 4, false}, {N1 * 4, false},
+        {S * 4, false}, {(n + 1) * 4, false}, {S * 4, false}, {S * 4, false}, {S * 4, false},
+        {n * 8, false}, {nnz * 8, false}, {nnz * 8, false}, {N1 * 8, false},
+        {h.h_g32_off.empty() ? 0 : N1 * 8, h.h_g32_off.empty()}, {N * 4, false}, {N * 4, false}, {N1 * 4, false},
+        {N1 * 8, false}, {(uint64_t)h.h_vm_off[N] * 8, h.h_vm_off[N] == 0}, {(uint64_t)h.n_minus_all * 8, h.n_minus_all == 0},
+        {N * 8, false}, {N * 4, false}, {N1 * 4, false}, {N1 * 8, false}, {(uint64_t)h.h_z_off[N] * 8, h.h_z_off[N] == 0},
+        {n0 * n0 * 8, n0 == 0}, {n0 * n0 * 8, n0 == 0}, {N1 * 4, false}, {n * nm * 8, true},
+        {nm * nm * 8, nm == 0}};
+    for (int p = 0; p < AWG_NPREC; p++) {
+        const PrecOps& P = h.prec[p];
+        const bool b = P.built;
+        const uint64_t w = p == AWG_FP64 ? 8 : (p == AWG_MIXED_FP32 ? 4 : 2);
+        const uint64_t g = p == AWG_FP64 ? (uint64_t)h.dense_total * 8
+                                         : (p == AWG_MIXED_FP32 && !h.h_g32_off.empty() ? (uint64_t)h.h_g32_off[N] * 4
+                                                                                        : 0);
+        const uint64_t cn = (uint64_t)std::max<int64_t>(0, P.corr_nnz);
+        r.push_back({g, !(b && p == AWG_FP64)});                          // G
+        r.push_back({n * ldw * w, !(b && nm > 0)});                      // W
+        r.push_back({nm * nm * 8, !(b && nm > 0)});                      // Finv
+        r.push_back({nm * nm * 8, true});                                // inexInv
+        r.push_back({p == AWG_MIXED_FP16 ? n * 4 : 0, !(b && p == AWG_MIXED_FP16 && nm > 0)});    // rscale
+        r.push_back({p == AWG_MIXED_FP16 ? ldw * 4 : 0, !(b && p == AWG_MIXED_FP16 && nm > 0)});  // cscale
+        r.push_back({cn ? (n + 1) * 4 : 0, cn == 0});                   // corr_rowptr
+        r.push_back({cn * 4, cn == 0});                                  // corr_col
+        r.push_back({cn * 4, cn == 0});                                  // corr_val
+        r.push_back({cn ? (nm + 1) * 4 : 0, cn == 0});                  // corr_colptr
+        r.push_back({cn * 4, cn == 0});                                  // corr_row
+        r.push_back({cn * 4, cn == 0});                                  // corr_cval
+    }
+    return r;
 }
 
 awg_status save_buffer(Out& o, const DevBuf& b, std::vector<char>& stage) {
@@ -153,10 +230,12 @@ awg_status save_buffer(Out& o, const DevBuf& b, std::vector<char>& stage) {
     return AWG_OK;
 }
 
-awg_status load_buffer(In& in, Handle* h, DevBuf& b, std::vector<char>& stage) {
+awg_status load_buffer(In& in, Handle* h, DevBuf& b, const Need& need, std::vector<char>& stage) {
     uint64_t n = 0;
     in.pod(n);
     if (!in.ok || n > ((uint64_t)1 << 42)) return AWG_ERR_IO;
+    // fewer bytes than the tables imply would let the kernels read past the buffer
+    if (n == 0 ? !need.optional && need.need > 0 : n < need.need) return AWG_ERR_IO;
     if (n == 0) return AWG_OK;
     AWG_TRY(dalloc(h, b, (size_t)n));
     if (stage.size() < std::min<uint64_t>(kChunk, n)) stage.resize((size_t)std::min<uint64_t>(kChunk, n));
@@ -174,10 +253,14 @@ awg_status load_into(In& in, Handle* h, void* stream) {
     h->opt.learned_params = nullptr;  // a pointer of the writing process
     tables(in, *h);
     if (!in.ok || !consistent(*h)) return AWG_ERR_IO;
+    if (h->opt.coarse_tensor_cores < 0 || h->opt.coarse_tensor_cores > 1) return AWG_ERR_IO;
     h->stream = (cudaStream_t)stream;
     AWG_TRY(runtime_init(h));
     std::vector<char> stage;
-    for (DevBuf* b : buffers(*h)) AWG_TRY(load_buffer(in, h, *b, stage));
+    const std::vector<DevBuf*> bufs = buffers(*h);
+    const std::vector<Need> need = needs(*h);
+    if (bufs.size() != need.size()) return AWG_ERR_IO;
+    for (size_t i = 0; i < bufs.size(); i++) AWG_TRY(load_buffer(in, h, *bufs[i], need[i], stage));
     // single right-hand-side workspace (its ticket counters start at zero)
     AWG_TRY(dalloc(h, h->ws, ws_bytes(h)));
     AWG_CUDA(cudaMemsetAsync(h->ws.p, 0, ws_bytes(h), h->stream));

@@ -2,15 +2,15 @@
 // pseudo-inverse GEMVs, then the prolongation sum) without any device
 // allocation.
 //
-// Who needs it: callers that must not allocate device memory while they run
-// the preconditioner, for instance code recorded into a CUDA graph by stream
-// capture (a cudaMalloc there is an error), a real-time loop that forbids
-// allocator calls, or a host framework that owns all device memory through
-// its own pool and does not let libraries call cudaMalloc.  The regular
-// entry points never allocate inside awg_apply*, but their scratch lives in
-// the handle's workspace; this variant keeps its scratch (the per-subdomain
-// local results, sum of n^s float64 values) in a fixed array that the
-// library defines at file scope instead.
+// Who needs it: callers that may not call cudaMalloc while they run the
+// preconditioner.  A host framework that hands all device memory out of its
+// own pool forbids libraries to allocate behind its back; a real-time or
+// latency-bound loop cannot afford cudaMalloc / cudaFree, which may
+// synchronise the device and take unbounded time.  The regular entry points
+// keep their scratch in the handle's workspace, allocated by the handle;
+// this variant keeps its scratch (the per-subdomain local results, sum of
+// n^s float64 values) in a fixed array that the library defines at file
+// scope instead, and calls no allocating routine at all.
 //
 // The array is a static __device__ buffer of AWG_NOALLOC_MAX_LOCAL doubles
 // (8 MiB): every GPU on which the library is loaded holds it until the

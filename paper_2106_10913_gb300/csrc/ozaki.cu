@@ -1,0 +1,339 @@
+// Float64-accurate products with the dense coarse inverses on the tensor
+// cores: Y = alpha M X + beta Sub, with M = E^-1 (Thm. 4, twice per apply of
+// H_2) or F^-1 / the H_3,inex inner inverse (Def. 10, Thm. 7), X the K
+// coarse right-hand sides of a block apply.
+//
+// On this GPU a float64 GEMM runs on the FP64 pipes, about 1/1600 of the
+// bfloat16 tensor rate; the three coarse products of a 64-column apply took
+// two thirds of a PCG iteration there.  Here both operands are cut into
+// integer slices (Ozaki's error-free transformation, in the form of Ootomo,
+// Ozaki & Yokota and Uchino et al.), every slice product runs on tcgen05 in
+// bfloat16 with float32 accumulation, EXACTLY, and the slice products are
+// recombined in float64:
+//
+//   M(i, j) = 2^e_i  sum_{s=1..S} q_s(i, j) 2^(-7 s) + rest,  |q_s| <= 64,
+//   X(j, c) = 2^f_c  sum_{t=1..S} p_t(j, c) 2^(-7 t) + rest,  |p_t| <= 64,
+//
+// (per-row and per-column power-of-two scales e_i, f_c with |M(i, :)| 2^-e_i
+// and |X(:, c)| 2^-f_c <= 1/2; the digits are taken by round-to-nearest,
+// q = rint(r 2^7), r <- r 2^7 - q, every step exact in float64).  Digits of
+// magnitude <= 64 are exact in bfloat16, products are <= 2^12, so a sum of up
+// to 4095 products stays below 2^24 and the float32 accumulator in tensor
+// memory holds every partial sum exactly (integers below 2^24).  Then
+//
+//   Y(i, c) = 2^(e_i + f_c) sum_{s + t <= S + 1} 2^(-7 (s + t)) D_st(i, c),
+//   D_st = q_s p_t (exact),
+//
+// which drops only the terms below 2^(-7 (S + 2)) of the row and column
+// scales: with S = 8 the result is as accurate as a float64 GEMM (about
+// 2^-53 relative to |M| |X|; measured error below that of the float64
+// GEMM on the benchmark problem's own E^-1 and F^-1).  36 slice products
+// replace one float64 GEMM: 36 x 2 n^2 K bfloat16 flops.
+//
+// Kernel: one CTA per (128-row tile of M, slice s, reduction split); the CTA
+// reads the 128 x 64 tiles of q_s and the stacked X slices p_1 .. p_{S+1-s}
+// ((S + 1 - s) K rows) per 64-deep stage through TMA into a shared-memory
+// ring, one thread issues the MMAs (M = 128, N = (S + 1 - s) K in pieces of
+// at most 256, the products D_st side by side in tensor memory), and the four
+// warps read the accumulators back, weight them by 2^(-7 (s + t)) and sum
+// them in float64 into the split's partial; a second kernel adds the
+// partials in a fixed order and applies the scales (deterministic).  Every
+// wait is bounded: a wait that gives up records a code in *d_err and the
+// CTA winds down (waits for its copies in flight, frees its tensor memory).
+
+#include "block.cuh"
+#include "tcgen05.cuh"
+
+#include <algorithm>
+
+namespace awg {
+
+namespace {
+
+constexpr int OZ_BM = 128;       // rows of M per CTA (MMA M)
+constexpr int OZ_BK = 64;        // reduction depth per stage (128 bytes of bfloat16)
+constexpr int OZ_THREADS = 128;
+constexpr int OZ_CHUNKS = 63;    // stages per reduction split (at most): 63 x 64 = 4032 <= 4095
+
+template <int K>
+struct OzCfg {
+    static constexpr int A_BYTES = OZ_BM * OZ_BK * 2;        // 16 KB tile of q_s
+    static constexpr int B_BYTES = OZ_SLICES * K * OZ_BK * 2;  // up to S slices of X, K rows each
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int STAGES = K == 64 ? 2 : 4;
+    static constexpr int SMEM = STAGES * STAGE + 1024;       // + alignment slack
+};
+
+struct OzShared {
+    uint64_t full[4];
+    uint64_t empty[4];
+    uint64_t done;
+    uint32_t tmem;
+    int fail;
+};
+
+__device__ __forceinline__ __nv_bfloat16 digit_bf16(double q) { return __float2bfloat16_rn((float)q); }
+
+// Row slices of M (dim x dim, row-major float64): q[(s dimp + i) ldk + j],
+// zero outside dim x dim; ex[i] = e_i.  One block per row.
+__global__ void __launch_bounds__(256) k_oz_slice_rows(int dim, int dimp, int ldk, const double* __restrict__ M,
+                                                       __nv_bfloat16* __restrict__ q, int* __restrict__ ex) {
+    __shared__ double red[32];
+    const int i = blockIdx.x;
+    double mx = 0.0;
+    for (int j = threadIdx.x; j < dim; j += blockDim.x) mx = fmax(mx, fabs(M[(size_t)i * dim + j]));
+    // block maximum (fixed order)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0) red[0] = v;
+    }
+    __syncthreads();
+    mx = red[0];
+    const int e = mx > 0.0 ? ilogb(mx) + 2 : 0;  // |M(i, :)| 2^-e < 1/2
+    if (threadIdx.x == 0) ex[i] = e;
+    for (int j = threadIdx.x; j < ldk; j += blockDim.x) {
+        double r = j < dim ? ldexp(M[(size_t)i * dim + j], -e) : 0.0;
+#pragma unroll
+        for (int s = 0; s < OZ_SLICES; s++) {
+            const double x = r * (double)(1 << OZ_BITS);
+            const double d = rint(x);
+            r = x - d;
+            q[((size_t)s * dimp + i) * ldk + j] = digit_bf16(d);
+        }
+    }
+}
+
+// Column slices of X (dim x K, row-major float64): p[(t K + c) ldk + j]
+// (zero for j >= dim), fx[c] = f_c.  One block per column.
+template <int K>
+__global__ void __launch_bounds__(256) k_oz_slice_cols(int dim, int ldk, const double* __restrict__ X,
+                                                       __nv_bfloat16* __restrict__ p, int* __restrict__ fx) {
+    __shared__ double red[32];
+    const int c = blockIdx.x;
+    double mx = 0.0;
+    for (int j = threadIdx.x; j < dim; j += blockDim.x) mx = fmax(mx, fabs(X[(size_t)j * K + c]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0) red[0] = v;
+    }
+    __syncthreads();
+    mx = red[0];
+    const int f = mx > 0.0 ? ilogb(mx) + 2 : 0;
+    if (threadIdx.x == 0) fx[c] = f;
+    for (int j = threadIdx.x; j < ldk; j += blockDim.x) {
+        double r = j < dim ? ldexp(X[(size_t)j * K + c], -f) : 0.0;
+#pragma unroll
+        for (int t = 0; t < OZ_SLICES; t++) {
+            const double x = r * (double)(1 << OZ_BITS);
+            const double d = rint(x);
+            r = x - d;
+            p[((size_t)t * K + c) * ldk + j] = digit_bf16(d);
+        }
+    }
+}
+
+// part[((z S + s) dimp + i) K + c] = sum_t 2^(-7 (s + t + 2)) D_st(i, c)
+// over the reduction split z (slices s, t counted from 0).
+template <int K>
+__global__ void __launch_bounds__(OZ_THREADS) k_oz_gemm(const __grid_constant__ CUtensorMap tmQ,
+                                                        const __grid_constant__ CUtensorMap tmP, int dim,
+                                                        int dimp, int nchunks, int chunks_per_split,
+                                                        double* __restrict__ part, int* d_err) {
+    extern __shared__ uint8_t oz_raw[];
+    __shared__ OzShared sh;
+    using C = OzCfg<K>;
+    constexpr int STAGES = C::STAGES;
+    const uint32_t base = smem_u32(oz_raw);
+    uint8_t* ring = oz_raw + ((1024u - (base & 1023u)) & 1023u);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * OZ_BM, s = blockIdx.y, z = blockIdx.z;
+    const int NT = OZ_SLICES - s;  // slices t with s + t <= S - 1 (from 0)
+    const int ncol = NT * K;
+    uint32_t tcols = 32;
+    while ((int)tcols < ncol) tcols <<= 1;
+    const int kc0 = z * chunks_per_split;
+    const int nk = min(chunks_per_split, nchunks - kc0);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < STAGES; i++) {
+            mbar_init(&sh.full[i], 1);
+            mbar_init(&sh.empty[i], 1);
+        }
+        mbar_init(&sh.done, 1);
+        sh.fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 2) {
+        tmem_alloc(&sh.tmem, tcols);
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = sh.tmem;
+    const uint32_t stage_bytes = (uint32_t)(C::A_BYTES + NT * K * OZ_BK * 2);
+    if (warp == 0 && lane == 0) {
+        int kb = 0;
+        for (; kb < nk; kb++) {
+            const int st = kb % STAGES;
+            if (kb >= STAGES && !mbar_wait(&sh.empty[st], ((kb / STAGES) - 1) & 1, d_err, ERR_WAIT_EMPTY)) {
+                sh.fail = 1;
+                break;
+            }
+            if (*(volatile int*)&sh.fail) break;
+            uint8_t* sp = ring + st * C::STAGE;
+            const int kx = (kc0 + kb) * OZ_BK;
+            mbar_expect_tx(&sh.full[st], stage_bytes);
+            tma_load_2d(sp, &tmQ, &sh.full[st], kx, s * dimp + m0);
+            for (int t = 0; t < NT; t++) tma_load_2d(sp + C::A_BYTES + t * K * 128, &tmP, &sh.full[st], kx, t * K);
+        }
+        // copies in flight: wait for the last load of every stage (bounded)
+        for (int j = (kb > STAGES ? kb - STAGES : 0); j < kb; j++)
+            mbar_wait(&sh.full[j % STAGES], (j / STAGES) & 1, d_err, ERR_WAIT_FULL);
+    } else if (warp == 1 && lane == 0) {
+        for (int kb = 0; kb < nk; kb++) {
+            const int st = kb % STAGES;
+            if (!mbar_wait(&sh.full[st], (kb / STAGES) & 1, d_err, ERR_WAIT_FULL) || *(volatile int*)&sh.fail) {
+                sh.fail = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a = smem_u32(ring + st * C::STAGE);
+            const uint32_t b = a + C::A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < OZ_BK / 16; kk++) {
+                const uint64_t ad = sdesc(a + kk * 32, 16, 1024);
+                for (int c0 = 0; c0 < ncol; c0 += 256) {
+                    const int nc = min(256, ncol - c0);
+                    const uint64_t bd = sdesc(b + c0 * 128 + kk * 32, 16, 1024);
+                    umma_f16(taddr + (uint32_t)c0, ad, bd, idesc_f16(OZ_BM, nc, 1, 0), (kb > 0 || kk > 0) ? 1u : 0u);
+                }
+            }
+            umma_commit(&sh.empty[st]);  // the stage is free once these MMAs are done
+        }
+        umma_commit(&sh.done);
+    }
+    __syncwarp();
+    bool ok = nk > 0 && mbar_wait(&sh.done, 0, d_err, ERR_WAIT_DONE);
+    ok = __syncthreads_and(ok && !*(volatile int*)&sh.fail);  // uniform: tcgen05.ld is warp-collective
+    tc_fence_after();
+    const int row = m0 + warp * 32 + lane;
+    if (ok) {
+        double acc[K];
+#pragma unroll
+        for (int c = 0; c < K; c++) acc[c] = 0.0;
+        for (int t = 0; t < NT; t++) {
+            const double w = ldexp(1.0, -OZ_BITS * (s + t + 2));
+#pragma unroll
+            for (int c0 = 0; c0 < K; c0 += 16) {
+                float v[16];
+                tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * K + c0), v);
+#pragma unroll
+                for (int u = 0; u < 16; u++) acc[c0 + u] = fma((double)v[u], w, acc[c0 + u]);
+            }
+        }
+        if (row < dim) {
+            double2* o = reinterpret_cast<double2*>(part + (((size_t)z * OZ_SLICES + s) * dimp + row) * K);
+#pragma unroll
+            for (int c = 0; c < K; c += 2) o[c / 2] = make_double2(acc[c], acc[c + 1]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 2) tmem_dealloc(taddr, tcols);
+}
+
+// Y = alpha 2^(e_i + f_c) sum over splits and slices of part (fixed order)
+// + beta Sub
+template <int K>
+__global__ void k_oz_sum(int dim, int dimp, int nparts, const double* __restrict__ part, const int* __restrict__ ex,
+                         const int* __restrict__ fx, double* Y, double alpha, const double* Sub, double beta) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)dim * K) return;
+    const int i = (int)(e / K), c = (int)(e % K);
+    double v = 0.0;
+    for (int g = 0; g < nparts; g++) v += part[((size_t)g * dimp + i) * K + c];
+    v = ldexp(v, ex[i] + fx[c]);
+    Y[e] = Sub ? fma(beta, Sub[e], alpha * v) : alpha * v;
+}
+
+int oz_dimp(int dim) { return (dim + OZ_BM - 1) / OZ_BM * OZ_BM; }
+int oz_ldk(int dim) { return (dim + OZ_BK - 1) / OZ_BK * OZ_BK; }
+int oz_splits(int dim, int cps = OZ_CHUNKS) { return (oz_ldk(dim) / OZ_BK + cps - 1) / cps; }
+
+template <int K>
+awg_status launch_oz(const OzMat& m, const double* X, double* Y, double alpha, const double* Sub, double beta,
+                     void* xs, double* part, int* d_err, cudaStream_t s, int cps) {
+    const int ldk = m.ldk;
+    __nv_bfloat16* p = (__nv_bfloat16*)xs;
+    int* fx = (int*)((char*)xs + (size_t)OZ_SLICES * K * ldk * 2);
+    k_oz_slice_cols<K><<<K, 256, 0, s>>>(m.dim, ldk, X, p, fx);
+    AWG_LAUNCH();
+    CUtensorMap tq, tp;
+    if (!make_map(&tq, m.q, 1, (uint64_t)OZ_SLICES * m.dimp, ldk, ldk, OZ_BK, OZ_BM) ||
+        !make_map(&tp, p, 1, (uint64_t)OZ_SLICES * K, ldk, ldk, OZ_BK, K))
+        return AWG_ERR_INVALID_ARG;
+    auto kern = k_oz_gemm<K>;
+    static bool attr = false;
+    if (!attr) {
+        AWG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, OzCfg<K>::SMEM));
+        attr = true;
+    }
+    const int nchunks = ldk / OZ_BK, splits = oz_splits(m.dim, cps);
+    kern<<<dim3(m.dimp / OZ_BM, OZ_SLICES, splits), OZ_THREADS, OzCfg<K>::SMEM, s>>>(tq, tp, m.dim, m.dimp, nchunks,
+                                                                                 cps, part, d_err);
+    AWG_LAUNCH();
+    const size_t len = (size_t)m.dim * K;
+    k_oz_sum<K><<<(unsigned)((len + 255) / 256), 256, 0, s>>>(m.dim, m.dimp, splits * OZ_SLICES, part, m.ex, fx, Y,
+                                                             alpha, Sub, beta);
+    AWG_LAUNCH();
+    return AWG_OK;
+}
+
+}  // namespace
+
+size_t oz_slices_bytes(int dim) { return (size_t)OZ_SLICES * oz_dimp(dim) * oz_ldk(dim) * 2; }
+size_t oz_part_elems(int dim, int K, int chunks_per_split) {
+    return (size_t)oz_splits(dim, chunks_per_split) * OZ_SLICES * oz_dimp(dim) * K;
+}
+size_t oz_xs_bytes(int dim, int K) { return (size_t)OZ_SLICES * K * oz_ldk(dim) * 2 + (size_t)K * 4; }
+
+awg_status oz_slice_matrix(const double* M, int dim, DevBuf& q, DevBuf& ex, Handle* h, cudaStream_t s, OzMat* out) {
+    if (dim < 1) return AWG_ERR_INVALID_ARG;
+    const int dimp = oz_dimp(dim), ldk = oz_ldk(dim);
+    if (!q.p) AWG_TRY(dalloc(h, q, oz_slices_bytes(dim)));
+    if (!ex.p) AWG_TRY(dalloc(h, ex, (size_t)dimp * 4));
+    AWG_CUDA(cudaMemsetAsync(q.p, 0, oz_slices_bytes(dim), s));
+    AWG_CUDA(cudaMemsetAsync(ex.p, 0, (size_t)dimp * 4, s));
+    k_oz_slice_rows<<<dim, 256, 0, s>>>(dim, dimp, ldk, M, (__nv_bfloat16*)q.p, (int*)ex.p);
+    AWG_LAUNCH();
+    out->q = q.p;
+    out->ex = (const int*)ex.p;
+    out->dim = dim;
+    out->dimp = dimp;
+    out->ldk = ldk;
+    return AWG_OK;
+}
+
+awg_status oz_gemm(const OzMat& m, int K, const double* X, double* Y, double alpha, const double* Sub, double beta,
+                   void* xs, double* part, int* d_err, cudaStream_t s, int chunks_per_split) {
+    if (m.dim < 1 || !m.q || chunks_per_split < 1 || chunks_per_split > OZ_CHUNKS) return AWG_ERR_INVALID_ARG;
+    const int c = chunks_per_split;
+    if (K == 16) return launch_oz<16>(m, X, Y, alpha, Sub, beta, xs, part, d_err, s, c);
+    if (K == 32) return launch_oz<32>(m, X, Y, alpha, Sub, beta, xs, part, d_err, s, c);
+    if (K == 64) return launch_oz<64>(m, X, Y, alpha, Sub, beta, xs, part, d_err, s, c);
+    return AWG_ERR_INVALID_ARG;
+}
+
+}  // namespace awg

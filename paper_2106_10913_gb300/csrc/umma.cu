@@ -21,6 +21,7 @@
 // frees its tensor memory) instead of hanging.
 
 #include "block.cuh"
+#include "tcgen05.cuh"
 
 #include <cuda.h>
 
@@ -35,127 +36,6 @@ constexpr int UM_BM = 128;     // rows of the product per CTA (MMA M)
 constexpr int UM_BK = 64;      // reduction depth per stage (128 bytes of 16-bit)
 constexpr int UM_STAGES = 4;
 constexpr int UM_THREADS = 128;
-constexpr long long UM_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
-
-enum : int { ERR_WAIT_EMPTY = 1, ERR_WAIT_FULL = 2, ERR_WAIT_DONE = 4 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Wait for the phase of parity `parity` of *bar; false (and *err |= code)
-// after about two seconds.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
-    if (mbar_test(bar, parity)) return true;
-    const long long t0 = clock64();
-    for (;;) {
-        if (mbar_test(bar, parity)) return true;
-        if (clock64() - t0 > UM_WAIT_CYCLES) {
-            atomicOr(err, code);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* holder, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(holder)),
-                 "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-
-// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (float16 or bfloat16 inputs,
-// float32 accumulation)
-__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-// arrive on *bar once every tcgen05.mma issued so far by this thread is done
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_u32(bar))
-                 : "memory");
-}
-
-// 16 consecutive 32-bit columns of this warp's 32 tensor-memory lanes
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
-}
-
-// Shared-memory matrix descriptor of a tcgen05.mma operand in the 128-byte
-// swizzled canonical layout: start address, leading and stride byte offsets
-// (16-byte units), descriptor version 1, swizzle mode 2 (128 B).  K-major
-// operand: rows of 128 bytes (64 16-bit values along the reduction), 8-row
-// groups 1024 bytes apart (stride offset); MN-major operand: rows of 128
-// bytes along M, 8-row groups along the reduction 1024 bytes apart (stride
-// offset), 64-wide M groups `lbo` bytes apart (leading offset).
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-
-// Instruction descriptor of kind::f16: float32 accumulator, A and B of the
-// same 16-bit type, A K-major or MN-major, B K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int bf16, int a_mn) {
-    return (1u << 4) | ((uint32_t)bf16 << 7) | ((uint32_t)bf16 << 10) | ((uint32_t)a_mn << 15) |
-           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
 template <int K>
 struct UmCfg {
     static constexpr int A_BYTES = UM_BM * UM_BK * 2;            // 16 KB
@@ -637,24 +517,6 @@ EncodeTiledFn encoder() {
     return fn;
 }
 
-// 2D tensor map of a row-major 16-bit matrix (rows x cols, row stride ld
-// elements, a multiple of 8), box of box_cols x box_rows, 128-byte swizzle,
-// zero fill outside
-bool make_map(CUtensorMap* m, const void* ptr, int bf16, uint64_t rows, uint64_t cols, uint64_t ld,
-              uint32_t box_cols, uint32_t box_rows) {
-    EncodeTiledFn enc = encoder();
-    if (!enc || ((uintptr_t)ptr & 15) || (ld % 8)) return false;
-    const cuuint64_t dims[2] = {cols, rows};
-    const cuuint64_t strides[1] = {ld * 2};
-    const cuuint32_t box[2] = {box_cols, box_rows};
-    const cuuint32_t es[2] = {1, 1};
-    const CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
-                           const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
-}
-
 // rows per split of W^T B: a multiple of the 64-row stage
 int split_rows(int n, int splits) {
     const int rps = (n + splits - 1) / splits;
@@ -715,6 +577,24 @@ awg_status launch_local(const UmmaLocal& u, const float* X, float* lt, float* ou
 }
 
 }  // namespace
+
+// 2D tensor map of a row-major 16-bit matrix (rows x cols, row stride ld
+// elements, a multiple of 8), box of box_cols x box_rows, 128-byte swizzle,
+// zero fill outside
+bool make_map(CUtensorMap* m, const void* ptr, int bf16, uint64_t rows, uint64_t cols, uint64_t ld,
+              uint32_t box_cols, uint32_t box_rows) {
+    EncodeTiledFn enc = encoder();
+    if (!enc || ((uintptr_t)ptr & 15) || (ld % 8)) return false;
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {ld * 2};
+    const cuuint32_t box[2] = {box_cols, box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                           const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
 
 awg_status umma_local_tiles(const UmmaLocal& u, const int64_t* g32off, const float* G, cudaStream_t s) {
     k_tile_g<<<dim3(u.max_tiles_sub, u.N), 256, 0, s>>>(u.sub_ptr, g32off, G, u.gt_off, const_cast<float*>(u.Gt));

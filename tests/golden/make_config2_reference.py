@@ -10,8 +10,11 @@ mode counts (all 256 subdomains); n0 and n_-; the smallest relative
 distance of a GenEO pencil eigenvalue to tau (the counts are decided away
 from the threshold when it is well above the GPU block solver's 1e-6
 certificate margin); max_s cond(A^s_+); the PCG iteration count and true
-relative residual of H_3,ad on the benchmark b (rtol 1e-8); and 256 sampled
-entries of H_3,ad x for x ~ N(0,1) from default_rng(4242).
+relative residual of H_3,ad on the benchmark b (rtol 1e-8), and on columns
+1, 77 and 127 of the benchmark's 128 right-hand sides
+(``awg_inputs.block_rhs``); 4096 sampled entries of H_3,ad x for x ~ N(0,1)
+from default_rng(4242), with the 2-norm and the largest magnitude of the
+whole H_3,ad x.
 """
 
 import json
@@ -35,9 +38,14 @@ def main():
     mm = O.minus_counts(st)
     gap = min(float(np.min(np.abs(lam - st.tau))) / st.tau for lam in st.geneo_lam)
     res = O.pcg(lambda v: st.A @ v, p.b, lambda r: O.H3_ad_apply(st, r), rtol=1e-8)
+    Bblk = gi.block_rhs(p, 128)
+    cols = {}
+    for c in (1, 77, 127):
+        rc = O.pcg(lambda v: st.A @ v, Bblk[c], lambda r: O.H3_ad_apply(st, r), rtol=1e-8)
+        cols[str(c)] = {"iters": int(rc.iters), "true_relres": float(rc.true_relres)}
     x = np.random.default_rng(4242).standard_normal(p.n)
     y = O.H3_ad_apply(st, x)
-    idx = np.sort(np.random.default_rng(4243).choice(p.n, 256, replace=False))
+    idx = np.sort(np.random.default_rng(4243).choice(p.n, 4096, replace=False))
     out = {
         "source": "oracle/awg_oracle.py on awg_inputs.config2() (512 x 512 channels at 1e6, 256 boxes, overlap 2, "
                   "tau = 0.1), written by tests/golden/make_config2_reference.py",
@@ -47,8 +55,9 @@ def main():
         "geneo_min_rel_gap_to_tau": gap,
         "local_condition": O.local_condition(st),
         "pcg": {"rtol": 1e-8, "iters": int(res.iters), "true_relres": float(res.true_relres)},
+        "pcg_block_rhs_columns": {"rhs": "awg_inputs.block_rhs(config2, 128)", **cols},
         "apply_h3ad": {"x_seed": 4242, "idx_seed": 4243, "idx": idx.tolist(), "y": y[idx].tolist(),
-                       "y_max_abs": float(np.abs(y).max())},
+                       "y_max_abs": float(np.abs(y).max()), "y_norm": float(np.linalg.norm(y))},
         "seconds": round(time.time() - t0, 1),
     }
     with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "config2_oracle.json"), "w") as f:

@@ -53,7 +53,12 @@ def pair(request):
 
 
 def _rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+    """Relative error of a against b, in the 2-norm and entry by entry
+    (largest |a_i - b_i| over the largest |b_i|): the larger of the two, so
+    that one wrong entry cannot hide inside the norm of a long vector."""
+    a, b = np.asarray(a), np.asarray(b)
+    return max(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300),
+               float(np.max(np.abs(a - b), initial=0.0)) / max(float(np.max(np.abs(b), initial=0.0)), 1e-300))
 
 
 def _ref_op(st, stage):
@@ -158,7 +163,7 @@ def test_block_pcg_variants(name, variant):
         for c in range(B.shape[0]):
             assert abs(int(itsa[c].item()) - its[c]) <= 1
             assert float(rela[c].item()) <= 1e-8
-            assert np.linalg.norm(st.A @ XA[c] - B[c]) <= 2e-8 * np.linalg.norm(B[c])
+            assert np.linalg.norm(st.A @ XA[c] - B[c]) <= 1e-8 * np.linalg.norm(B[c]) * (1 + 1e-12)
 
 
 @pytest.mark.parametrize("form", ["fp32", "fp16", "bf16"])
@@ -300,7 +305,7 @@ def test_block_pcg_async_matches_sync(pair, form):
         for c in range(5):
             assert abs(int(its[c].item()) - its_s[c]) <= 1
             assert float(rel[c].item()) <= 1e-8
-            assert np.linalg.norm(st.A @ X[c] - B[c]) <= 2e-8 * np.linalg.norm(B[c])
+            assert np.linalg.norm(st.A @ X[c] - B[c]) <= 1e-8 * np.linalg.norm(B[c]) * (1 + 1e-12)
 
 
 def test_block_pcg_async_concurrent_problems():
@@ -319,7 +324,7 @@ def test_block_pcg_async_concurrent_problems():
     for (p, st, B, x) in ((pa, sta, Ba, xa), (pb, stb, Bb, xb)):
         X = x.cpu().numpy()
         for c in range(B.shape[0]):
-            assert np.linalg.norm(st.A @ X[c] - B[c]) <= 2e-8 * np.linalg.norm(B[c])
+            assert np.linalg.norm(st.A @ X[c] - B[c]) <= 1e-8 * np.linalg.norm(B[c]) * (1 + 1e-12)
 
 
 @pytest.mark.parametrize("form", ["fp64", "fp16"])
@@ -338,7 +343,7 @@ def test_pcg_async_single_rhs(pair, form):
     assert abs(int(its[0].item()) - its1[0]) <= 1
     assert float(rel[0].item()) <= 1e-8
     X = x.cpu().numpy()
-    assert np.linalg.norm(st.A @ X[0] - B[0]) <= 2e-8 * np.linalg.norm(B[0])
+    assert np.linalg.norm(st.A @ X[0] - B[0]) <= 1e-8 * np.linalg.norm(B[0]) * (1 + 1e-12)
 
 
 def test_block_pcg_async_two_groups(pair):
@@ -361,4 +366,4 @@ def test_block_pcg_async_two_groups(pair):
             continue
         assert abs(int(its[c].item()) - its_s[c]) <= 1
         assert float(rel[c].item()) <= 1e-8
-        assert np.linalg.norm(st.A @ X[c] - B[c]) <= 2e-8 * np.linalg.norm(B[c])
+        assert np.linalg.norm(st.A @ X[c] - B[c]) <= 1e-8 * np.linalg.norm(B[c]) * (1 + 1e-12)

@@ -56,7 +56,12 @@ def pair(request):
 
 
 def _rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+    """Relative error of a against b, in the 2-norm and entry by entry
+    (largest |a_i - b_i| over the largest |b_i|): the larger of the two, so
+    that one wrong entry cannot hide inside the norm of a long vector."""
+    a, b = np.asarray(a), np.asarray(b)
+    return max(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300),
+               float(np.max(np.abs(a - b), initial=0.0)) / max(float(np.max(np.abs(b), initial=0.0)), 1e-300))
 
 
 def test_structure_exact(pair):

@@ -48,7 +48,12 @@ def pair(request):
 
 
 def _rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+    """Relative error of a against b, in the 2-norm and entry by entry
+    (largest |a_i - b_i| over the largest |b_i|): the larger of the two, so
+    that one wrong entry cannot hide inside the norm of a long vector."""
+    a, b = np.asarray(a), np.asarray(b)
+    return max(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300),
+               float(np.max(np.abs(a - b), initial=0.0)) / max(float(np.max(np.abs(b), initial=0.0)), 1e-300))
 
 
 def _rhs(p):
@@ -117,7 +122,7 @@ def test_batch_problems_concurrent():
             assert int(st_.item()) == 0 and float(rel.item()) <= 1e-8
             assert abs(int(its.item()) - ref.iters) <= max(1, round(0.05 * ref.iters))
             X = x.cpu().numpy()[0]
-            assert np.linalg.norm(ost.A @ X - q.b) <= 2e-8 * np.linalg.norm(q.b)
+            assert np.linalg.norm(ost.A @ X - q.b) <= 1e-8 * np.linalg.norm(q.b) * (1 + 1e-12)
     finally:
         for s_ in sols:
             s_.close()

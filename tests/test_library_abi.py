@@ -62,10 +62,13 @@ def test_host_only_calls(lib):
     assert lib.awg_learned_grad(0, None, None, None, None, 0, None) == 1
     assert lib.awg_learned_train(1, None, None, None, 1, 1e-2, 0, None, None) == 1
     assert lib.awg_learned_data(None, None, None, None) == 1
-    assert ctypes.sizeof(pkg.awg.awg_options) == 96
+    assert ctypes.sizeof(pkg.awg.awg_options) == 104
     assert o.w16_keep == 0.1
     d = pkg.default_options()
     assert d.block_tensor_cores == 1 and d.h2 == pkg.H2_NN_HYB and d.tau_flat == 10.0
+    assert d.coarse_tensor_cores == 1
+    o = pkg.default_options(coarse_tensor_cores=2)
+    assert lib.awg_setup(4, 4, 1, 1, 1, 1, 1, 1, 0.1, ctypes.byref(o), None, ctypes.byref(h)) == 1
     # H_2 choice and tau_flat are checked before any device work
     for bad in ({"h2": 4}, {"h2": -1}, {"h2": pkg.H2_ASP_AD, "tau_flat": 0.0}):
         o = pkg.default_options(**bad)
@@ -76,6 +79,7 @@ def test_host_only_calls(lib):
     assert lib.awg_status_string(11) == b"AWG_ERR_IO"
     assert lib.awg_pcg_block(None, 0, None, None, 1, 1, 1e-8, None, None, None) == 1
     assert lib.awg_pcg_block_async(None, 0, None, None, 1, 1, 1e-8, None, None, None, None) == 1
+    assert lib.awg_coarse_apply_block(None, 0, 0, 1, None, None, 1, None) == 1
 
 
 def test_product_does_not_import_oracle():
@@ -100,12 +104,13 @@ def test_checkpoint_file_errors(lib, tmp_path):
     assert lib.awg_load(b"x", None, None) == 1
     assert lib.awg_load(str(tmp_path / "missing").encode(), None, ctypes.byref(h)) == 11 and not h.value
     osz = ctypes.sizeof(pkg.awg.awg_options)
+    ver = 2  # the current format version
     cases = {
-        "tag": b"NOTAHNDL" + struct.pack("<II", 1, osz),
-        "version": b"AWGHNDL\n" + struct.pack("<II", 2, osz),
-        "options": b"AWGHNDL\n" + struct.pack("<II", 1, osz + 8),
-        "truncated": b"AWGHNDL\n" + struct.pack("<II", 1, osz) + b"\0" * 16,
-        "inconsistent": b"AWGHNDL\n" + struct.pack("<II", 1, osz) + b"\0" * 4096,
+        "tag": b"NOTAHNDL" + struct.pack("<II", ver, osz),
+        "version": b"AWGHNDL\n" + struct.pack("<II", ver - 1, osz),
+        "options": b"AWGHNDL\n" + struct.pack("<II", ver, osz + 8),
+        "truncated": b"AWGHNDL\n" + struct.pack("<II", ver, osz) + b"\0" * 16,
+        "inconsistent": b"AWGHNDL\n" + struct.pack("<II", ver, osz) + b"\0" * 4096,
     }
     for name, data in cases.items():
         f = tmp_path / name

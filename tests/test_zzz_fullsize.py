@@ -23,11 +23,13 @@ rest:
 * any size: H_3,ad (float64) symmetric to 1e-8 relative and positive on
   random vectors (an error in its composition, such as Pi for Pi^T or a
   transposed W pass, is of order 1); every one of the 128 columns ends with
-  a recurrence residual <= 1e-8 and a true relative residual <= 2e-8 (the
-  graph-driven solve stops on the recurrence residual without re-checking
-  the true one; on this problem the two drift apart by about 1e-12, the
-  float64 residual of a direct solve being 3e-13); sampled columns take
-  within 10 % (or 3) of the iterations of the float64 single-RHS solve.
+  a true relative residual <= 1e-8 (the graph-driven loop confirms each
+  column's recurrence residual on its true residual before it stops it);
+* the iterations of the benchmark's columns 0, 1, 77 and 127 within 5 % of
+  the oracle's PCG on the same columns (stored), for the float32 form (the
+  reduced-precision form the benchmark spec names: float32 local operators and
+  W, float64 coarse solves and recurrences), and the float16-W form that
+  the benchmark also times.
 
 Subspace tolerance: the block eigensolver accepts a Ritz pair at normwise
 backward error eta = 1e-13 (||M_A x - theta M_B x|| relative to
@@ -64,7 +66,7 @@ def _full():
         from paper_2106_10913_gb300 import AWGSolver
         p = gi.config2()
         params, _ = bench.train_start_network()
-        sol = AWGSolver(p.rowptr, p.colidx, p.val, p.part, p.nparts, p.overlap, p.tau, precisions=0b1001,
+        sol = AWGSolver(p.rowptr, p.colidx, p.val, p.part, p.nparts, p.overlap, p.tau, precisions=0b1011,
                         geneo_solver=2, learned_params=params)
         A = O.csr_from(p.rowptr, p.colidx, p.val, p.n)
         subs = O.grow_subdomains(A, p.part, p.nparts, p.overlap)
@@ -128,33 +130,41 @@ def test_apply_symmetric_positive_full():
     assert float(torch.dot(x, Hx)) > 0 and float(torch.dot(y, Hy)) > 0
 
 
-def test_block_graph_solve_full():
-    """The benchmark's timed launch: 128 columns (column 0 the benchmark's b)
-    in one graph-driven float16 block solve."""
+def _within_5pct(its, ref):
+    """Iteration count within 5 % of the oracle's (at least one iteration of
+    slack for counts below 20, where 5 % is less than one)."""
+    return abs(its - ref) <= max(1.0, 0.05 * ref)
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp16"])
+def test_block_graph_solve_full(form):
+    """The benchmark's timed launch: 128 columns (awg_inputs.block_rhs:
+    column 0 the benchmark's b) in one graph-driven block solve."""
     S = _full()
     p, sol, A = S["p"], S["sol"], S["A"]
-    from paper_2106_10913_gb300 import MIXED_FP16, awg_pcg_block_async
-    rng = np.random.default_rng(1)
-    Bh = rng.standard_normal((NRHS, p.n))
-    Bh[0] = p.b
+    from paper_2106_10913_gb300 import MIXED_FP16, MIXED_FP32, awg_pcg_block_async
+    prec = {"fp32": MIXED_FP32, "fp16": MIXED_FP16}[form]
+    Bh = gi.block_rhs(p, NRHS)
     b = torch.from_numpy(Bh).cuda()
     x = torch.zeros_like(b)
     its = torch.zeros(NRHS, dtype=torch.int32, device="cuda")
     rel = torch.zeros(NRHS, dtype=torch.float64, device="cuda")
     st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
-    awg_pcg_block_async(sol.h, b, x, its, rel, st, 1e-8, precision=MIXED_FP16)
+    awg_pcg_block_async(sol.h, b, x, its, rel, st, 1e-8, precision=prec)
     torch.cuda.synchronize()
     assert int(st.item()) == 0
     X = x.cpu().numpy()
     assert float(rel.max()) <= 1e-8
     R = A @ X.T - Bh.T
     true_rel = np.linalg.norm(R, axis=0) / np.linalg.norm(Bh, axis=1)
-    assert np.all(true_rel <= 2e-8), float(true_rel.max())
+    assert np.all(true_rel <= 1e-8 * (1 + 1e-12)), float(true_rel.max())
     its_h = its.cpu().numpy()
-    for c in (0, 77):
-        _, its64, rel64, status = sol.pcg(b[c].contiguous(), rtol=1e-8)
-        assert status == 0 and rel64[0] <= 1e-8
-        assert abs(int(its_h[c]) - its64[0]) <= max(3, round(0.1 * its64[0])), (c, int(its_h[c]), its64[0])
+    ref = json.load(open(REF))
+    refs = {0: ref["pcg"]["iters"]}
+    refs.update({int(c): v["iters"] for c, v in ref.get("pcg_block_rhs_columns", {}).items() if c != "rhs"})
+    print(f"[{form} graph solve: iterations {dict((c, int(its_h[c])) for c in refs)} oracle {refs}]")
+    for c, ri in refs.items():
+        assert _within_5pct(int(its_h[c]), ri), (form, c, int(its_h[c]), ri)
 
 
 def test_whole_problem_against_stored_oracle():
@@ -174,9 +184,19 @@ def test_whole_problem_against_stored_oracle():
     ap = ref["apply_h3ad"]
     x = torch.from_numpy(np.random.default_rng(ap["x_seed"]).standard_normal(p.n)).cuda()
     y = sol.apply(x).cpu().numpy()
-    tol = max(1e-11, ref["local_condition"] * np.finfo(float).eps) * ap["y_max_abs"]
-    assert np.max(np.abs(y[np.array(ap["idx"])] - np.array(ap["y"]))) <= tol
+    rtol64 = max(1e-11, ref["local_condition"] * np.finfo(float).eps)
+    idx, yref = np.array(ap["idx"]), np.array(ap["y"])
+    assert np.max(np.abs(y[idx] - yref)) <= rtol64 * ap["y_max_abs"]
+    if "y_norm" in ap:
+        assert abs(np.linalg.norm(y) - ap["y_norm"]) <= rtol64 * ap["y_norm"]
+    # the reduced-precision path (float32 local operators and W, float64
+    # coarse solves) within 1e-4 of the oracle's float64 apply
+    from paper_2106_10913_gb300 import MIXED_FP32
+    y32 = sol.apply(x, precision=MIXED_FP32).cpu().numpy()
+    assert np.max(np.abs(y32[idx] - yref)) <= 1e-4 * ap["y_max_abs"]
+    if "y_norm" in ap:
+        assert abs(np.linalg.norm(y32) - ap["y_norm"]) <= 1e-4 * ap["y_norm"]
     _, its, rel, status = sol.pcg(torch.from_numpy(p.b).cuda(), rtol=1e-8)
     assert status == 0 and rel[0] <= 1e-8
     ri = ref["pcg"]["iters"]
-    assert abs(its[0] - ri) <= max(1, round(0.05 * ri)), (its[0], ri)
+    assert _within_5pct(its[0], ri), (its[0], ri)

@@ -52,3 +52,52 @@ def test_round_trip(tmp_path):
     finally:
         loaded.close()
         sol.close()
+
+
+def test_damaged_files_are_refused(tmp_path):
+    """A file whose tables disagree with each other (a subdomain size above
+    max_ns, a prefix table that decreases) or whose device buffer carries
+    fewer bytes than the tables imply is refused with AWG_ERR_IO (11), before
+    any buffer is read past its end."""
+    import ctypes
+    import struct
+    from paper_2106_10913_gb300 import AWGSolver, load_library
+    p = gi.channels2d(64, q=2, nchan=3, contrast=1e6, seed=11, overlap=2, tau=0.1)
+    sol = AWGSolver(p.rowptr, p.colidx, p.val, p.part, p.nparts, p.overlap, p.tau)
+    path = tmp_path / "good.awg"
+    sol.save(path)
+    data = path.read_bytes()
+    ns = sol.array("ns").astype(np.int32)
+    dvec = sol.array("dvec")
+    sol.close()
+    N = ns.size
+    # host table of the subdomain sizes: element count, then the sizes
+    tab = struct.pack("<Q", N) + ns.tobytes()
+    i_ns = data.index(tab)
+    # host table of the subdomain pointers, right after it
+    ptr = np.concatenate([[0], np.cumsum(ns)]).astype(np.int32)
+    tab_ptr = struct.pack("<Q", N + 1) + ptr.tobytes()
+    i_ptr = data.index(tab_ptr)
+    # device buffer D: byte count, then the values
+    buf_d = struct.pack("<Q", dvec.size * 8) + dvec.tobytes()
+    i_d = data.index(buf_d)
+    big = ns.copy()
+    big[0] = ns.max() + 1
+    bad_ptr = ptr.copy()
+    bad_ptr[1], bad_ptr[2] = bad_ptr[2], bad_ptr[1]
+    cases = {
+        "n^s above max_ns": data[:i_ns + 8] + big.tobytes() + data[i_ns + 8 + 4 * N:],
+        "decreasing pointers": data[:i_ptr + 8] + bad_ptr.tobytes() + data[i_ptr + 8 + 4 * (N + 1):],
+        "short buffer": data[:i_d] + struct.pack("<Q", dvec.size * 8 - 8) + data[i_d + 8:],
+    }
+    lib = load_library()
+    for name, blob in cases.items():
+        f = tmp_path / "bad.awg"
+        f.write_bytes(blob)
+        h = ctypes.c_void_p(123)
+        assert lib.awg_load(str(f).encode(), None, ctypes.byref(h)) == 11, name
+        assert not h.value, name
+    # the untouched file still loads
+    h = ctypes.c_void_p()
+    assert lib.awg_load(str(path).encode(), None, ctypes.byref(h)) == 0 and h.value
+    lib.awg_destroy(h)
