@@ -220,6 +220,33 @@ def _grf(shape_full, corr_len, rng):
     return field
 
 
+def _nearest_centroid(X: np.ndarray, cent: np.ndarray, cand: int = 8) -> np.ndarray:
+    """Index of the nearest centroid of every point, the lowest index among
+    exactly equal squared distances (what a brute-force argmin returns).
+    A k-d tree over the centroids proposes `cand` candidates per point; their
+    squared distances are recomputed exactly (integer coordinates, centroids
+    on a 2^-10 grid) and compared; a point whose candidates do not settle it
+    (the last candidate as close as the first) is done by brute force."""
+    from scipy.spatial import cKDTree
+    k = cent.shape[0]
+    cand = min(cand, k)
+    _, nb = cKDTree(cent).query(X, k=cand)
+    nb = nb.reshape(X.shape[0], cand)
+    d2 = np.zeros(nb.shape)
+    for ax in range(X.shape[1]):
+        diff = X[:, ax:ax + 1] - cent[nb, ax]
+        d2 += diff * diff
+    best = d2.min(axis=1)
+    # lowest centroid index among the candidates at the minimum
+    out = np.where(d2 == best[:, None], nb, k).min(axis=1)
+    if cand < k:
+        hard = np.nonzero(d2[:, -1] <= best)[0]
+        for i in hard:
+            dd = ((X[i][None, :] - cent) ** 2).sum(axis=1)
+            out[i] = int(np.argmin(dd))
+    return out.astype(np.int64)
+
+
 def _kmeans_partition(coords: np.ndarray, k: int, rng, sweeps: int = 100) -> np.ndarray:
     """Lloyd's k-means with Forgy initialisation; ties go to the lower index.
 
@@ -231,16 +258,9 @@ def _kmeans_partition(coords: np.ndarray, k: int, rng, sweeps: int = 100) -> np.
     init = rng.choice(npts, size=k, replace=False)
     cent = coords[init].astype(np.float64)
     assign = np.full(npts, -1, dtype=np.int64)
-    chunk = 4096
+    X = coords.astype(np.float64)
     for _ in range(sweeps):
-        new = np.empty(npts, dtype=np.int64)
-        for s in range(0, npts, chunk):
-            x = coords[s:s + chunk].astype(np.float64)
-            d = np.zeros((x.shape[0], k))
-            for ax in range(coords.shape[1]):
-                diff = x[:, ax:ax + 1] - cent[None, :, ax]
-                d += diff * diff
-            new[s:s + chunk] = np.argmin(d, axis=1)
+        new = _nearest_centroid(X, cent)
         if np.array_equal(new, assign):
             break
         assign = new

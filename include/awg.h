@@ -162,6 +162,20 @@ typedef struct {
                                exact in float32 and summed in float64 (as
                                accurate as a float64 GEMM); 0 on the float64
                                CUDA cores                                      */
+    double w_drop_tol;      /* > 0: the float64 form keeps a truncated second
+                               coarse basis, the entries of W with |W_ij| >=
+                               w_drop_tol * max_i |W_ij| of their column,
+                               stored sparse by rows and by columns, and
+                               F = W^T A W rebuilt from it (so H_3 stays SPD;
+                               the conclusion, Section 6, leaves sparser
+                               second coarse spaces open).  The single-RHS
+                               applies and PCG of that form use it (H_3,ad,
+                               H_3,hyb; not H_3,inex, whose inner matrix of
+                               Thm. 7 assumes W = A_+^-1 Vhat: variant
+                               AWG_H3_INEX is refused and stage 6 returns
+                               AWG_ERR_STATE); its block forms return
+                               AWG_ERR_STATE.  The mixed forms keep the full
+                               W.  0 (default): full W                      */
 } awg_options;
 
 /* Per-handle figures reported after setup (cf. Table 1 of the paper). */
@@ -188,6 +202,8 @@ typedef struct {
                                the tensor-core W^T B pass and blocks per SM of  */
     int block_dense_bps[3]; /* the float64 coarse GEMM (autotuned on the first
                                H_3 apply of that width; 0 before)              */
+    int64_t w_kept;         /* entries kept in the float64 form's truncated W
+                               (awg_options.w_drop_tol > 0), else 0           */
 } awg_info;
 
 /* Fill *opt with the defaults above. */

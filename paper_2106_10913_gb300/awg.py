@@ -47,7 +47,7 @@ class awg_options(ctypes.Structure):
                 ("learned_params", ctypes.c_void_p), ("autotune", ctypes.c_int),
                 ("w16_keep", ctypes.c_double), ("block_tensor_cores", ctypes.c_int),
                 ("h2", ctypes.c_int), ("tau_flat", ctypes.c_double),
-                ("coarse_tensor_cores", ctypes.c_int)]
+                ("coarse_tensor_cores", ctypes.c_int), ("w_drop_tol", ctypes.c_double)]
 
 
 class awg_info(ctypes.Structure):
@@ -59,7 +59,7 @@ class awg_info(ctypes.Structure):
                 ("geneo_its_max", ctypes.c_int), ("geneo_its_sum", ctypes.c_int64),
                 ("geneo_dense", ctypes.c_int), ("wt_blocks", ctypes.c_int * 4),
                 ("wd_blocks", ctypes.c_int * 4), ("block_wt_ctas", ctypes.c_int * 3),
-                ("block_dense_bps", ctypes.c_int * 3)]
+                ("block_dense_bps", ctypes.c_int * 3), ("w_kept", ctypes.c_int64)]
 
 
 EXPORTED = ["awg_default_options", "awg_status_string", "awg_setup", "awg_destroy",

@@ -74,7 +74,8 @@ void free_all(Handle* h) {
         dfree(h, P.inexInv);
         dfree(h, P.rscale);
         dfree(h, P.cscale);
-        for (DevBuf* b : {&P.corr_rowptr, &P.corr_col, &P.corr_val, &P.corr_colptr, &P.corr_row, &P.corr_cval})
+        for (DevBuf* b : {&P.corr_rowptr, &P.corr_col, &P.corr_val, &P.corr_colptr, &P.corr_row, &P.corr_cval,
+                          &P.sp_rowptr, &P.sp_col, &P.sp_val, &P.sp_colptr, &P.sp_row, &P.sp_cval})
             dfree(h, *b);
     }
     for (int g = 0; g < 4; g++) {
@@ -169,6 +170,7 @@ void awg_default_options(awg_options* opt) {
     opt->w16_keep = 0.1;
     opt->block_tensor_cores = 1;
     opt->coarse_tensor_cores = 1;
+    opt->w_drop_tol = 0.0;
 }
 
 const char* awg_status_string(awg_status s) {
@@ -242,7 +244,8 @@ awg_status awg_setup(int n, int nnz, const int* d_rowptr, const int* d_colidx, c
         o.geneo_solver < 0 || o.geneo_solver > 2 || o.geneo_block < 2 || o.geneo_block > 16 ||
         o.geneo_maxit < 1 || (o.geneo_solver == 2 && !o.learned_params) || !(o.w16_keep >= 0.0) ||
         o.w16_keep > 1.0 || o.h2 < AWG_H2_NN_HYB || o.h2 > AWG_H2_AS_HYB || !(o.tau_flat > 0.0) ||
-        o.coarse_tensor_cores < 0 || o.coarse_tensor_cores > 1)
+        o.coarse_tensor_cores < 0 || o.coarse_tensor_cores > 1 || !(o.w_drop_tol >= 0.0) || o.w_drop_tol >= 1.0 ||
+        (o.w_drop_tol > 0.0 && o.variant == AWG_H3_INEX))
         return AWG_ERR_INVALID_ARG;
     o.precisions |= 1 << AWG_FP64;
     Handle* h = new (std::nothrow) Handle();
@@ -302,6 +305,7 @@ awg_status awg_get_info(awg_handle hh, awg_info* info) {
         info->block_wt_ctas[k] = h->bt_wt[k];
         info->block_dense_bps[k] = h->bt_dense[k];
     }
+    info->w_kept = h->prec[AWG_FP64].sp_nnz;
     return AWG_OK;
 }
 
@@ -369,6 +373,7 @@ awg_status awg_apply_block(awg_handle hh, int which, int precision, const double
         return AWG_ERR_INVALID_ARG;
     // the mixed block forms apply the float32 local pseudo-inverses
     if (!h->prec[precision].built || (precision != AWG_FP64 && !h->prec[AWG_MIXED_FP32].G.p)) return AWG_ERR_STATE;
+    if (precision == AWG_FP64 && h->n_minus > 0 && !h->prec[AWG_FP64].W.p) return AWG_ERR_STATE;  // truncated W
     if (which == 6 && h->n_minus > 0 && !h->prec[precision].inexInv.p) return AWG_ERR_STATE;
     cudaStream_t us = (cudaStream_t)stream;
     AWG_CUDA(cudaEventRecord(h->ev_in, us));
@@ -404,6 +409,7 @@ awg_status awg_pcg_block(awg_handle hh, int precision, const double* d_b, double
         return AWG_ERR_INVALID_ARG;
     // the mixed block forms apply the float32 local pseudo-inverses
     if (!h->prec[precision].built || (precision != AWG_FP64 && !h->prec[AWG_MIXED_FP32].G.p)) return AWG_ERR_STATE;
+    if (precision == AWG_FP64 && h->n_minus > 0 && !h->prec[AWG_FP64].W.p) return AWG_ERR_STATE;  // truncated W
     if (nrhs == 0) return AWG_OK;
     cudaStream_t us = (cudaStream_t)stream;
     AWG_CUDA(cudaEventRecord(h->ev_in, us));
@@ -422,6 +428,7 @@ awg_status awg_pcg_block_async(awg_handle hh, int precision, const double* d_b, 
         precision >= AWG_NPREC)
         return AWG_ERR_INVALID_ARG;
     if (!h->prec[precision].built || (precision != AWG_FP64 && !h->prec[AWG_MIXED_FP32].G.p)) return AWG_ERR_STATE;
+    if (nrhs > 1 && precision == AWG_FP64 && h->n_minus > 0 && !h->prec[AWG_FP64].W.p) return AWG_ERR_STATE;  // truncated W
     cudaStream_t us = (cudaStream_t)stream;
     AWG_CUDA(cudaEventRecord(h->ev_in, us));
     AWG_CUDA(cudaStreamWaitEvent(h->hp, h->ev_in, 0));

@@ -926,6 +926,34 @@ static int wt_row_blocks(const Handle* h, const PrecOps& P) {
     return std::min(rb, h->red_blocks);
 }
 
+// Truncated W (float64 form with w_drop_tol > 0): out[j] = sum over the
+// kept entries of column j of W(i, j) r(i) (CSC; one warp per column, lanes
+// over the entries, a fixed-order warp sum)
+__global__ void __launch_bounds__(256) k_wt_csc(int nm, const int64_t* __restrict__ colptr,
+                                                const int* __restrict__ row, const double* __restrict__ val,
+                                                const double* __restrict__ r, double* __restrict__ out) {
+    const int j = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (j >= nm) return;
+    double a = 0.0;
+    for (int64_t k = colptr[j] + lane; k < colptr[j + 1]; k += 32) a = fma(val[k], r[row[k]], a);
+    a = warp_sum(a);
+    if (lane == 0) out[j] = a;
+}
+
+// z(i) = v(i) + sum over the kept entries of row i of W(i, j) d(j) (CSR; one
+// warp per row)
+__global__ void __launch_bounds__(256) k_wd_csr(int n, const int64_t* __restrict__ rowptr,
+                                                const int* __restrict__ col, const double* __restrict__ val,
+                                                const double* __restrict__ d, const double* __restrict__ v,
+                                                double* __restrict__ z) {
+    const int i = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= n) return;
+    double a = 0.0;
+    for (int64_t k = rowptr[i] + lane; k < rowptr[i + 1]; k += 32) a = fma(val[k], d[col[k]], a);
+    a = warp_sum(a);
+    if (lane == 0) z[i] = (v ? v[i] : 0.0) + a;
+}
+
 template <typename TS>
 static awg_status wt_r_t(Handle* h, const PrecOps& P, const double* r, double* out, Ws& w,
                          cudaStream_t s) {
@@ -957,6 +985,13 @@ static awg_status wt_r_t(Handle* h, const PrecOps& P, const double* r, double* o
 
 static awg_status wt_r(Handle* h, int prec, const double* r, double* out, Ws& w, cudaStream_t s) {
     const PrecOps& P = h->prec[prec];
+    if (prec == AWG_FP64 && !P.W.p && P.sp_colptr.p) {  // truncated W
+        ProfScope ps_(h, AWG_PROF_WT, s);
+        k_wt_csc<<<(h->n_minus + 7) / 8, 256, 0, s>>>(h->n_minus, (const int64_t*)P.sp_colptr.p, (const int*)P.sp_row.p,
+                                                      (const double*)P.sp_cval.p, r, out);
+        AWG_LAUNCH();
+        return AWG_OK;
+    }
     if (prec == AWG_FP64) return wt_r_t<double>(h, P, r, out, w, s);
     if (prec == AWG_MIXED_FP32) return wt_r_t<float>(h, P, r, out, w, s);
     if (prec == AWG_MIXED_FP16) return wt_r_t<__half>(h, P, r, out, w, s);
@@ -977,6 +1012,13 @@ static awg_status w_d(Handle* h, int prec, const double* d, const double* v, dou
     // issued its bandwidth-heavy part, so it takes the whole GPU
     const int grid = std::max(1, std::min((h->n + 7) / 8, P.wd_blocks > 0 ? P.wd_blocks : 152 * 16));
     const int gd = (h->ldw + 255) / 256;
+    if (prec == AWG_FP64 && !W && P.sp_rowptr.p) {  // truncated W
+        ProfScope ps_(h, AWG_PROF_WD, s);
+        k_wd_csr<<<(h->n + 7) / 8, 256, 0, s>>>(h->n, (const int64_t*)P.sp_rowptr.p, (const int*)P.sp_col.p,
+                                                (const double*)P.sp_val.p, d, v, z);
+        AWG_LAUNCH();
+        return AWG_OK;
+    }
     if (prec == AWG_FP64) {
         double* dp = w.dpad;
         {

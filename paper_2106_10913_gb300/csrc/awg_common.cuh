@@ -66,6 +66,13 @@ struct PrecOps {
     int64_t corr_nnz = 0;
     DevBuf corr_rowptr, corr_col, corr_val;   // int32[n+1], int32[nnz], float32[nnz]
     DevBuf corr_colptr, corr_row, corr_cval;  // int32[n_-+1], int32[nnz], float32[nnz]
+    // truncated W of the float64 form (awg_options.w_drop_tol > 0): the
+    // entries with |W_ij| >= w_drop_tol * max_i |W_ij|, float64, by rows (CSR,
+    // for W d) and by columns (CSC, for W^T r), indices ascending; W stays
+    // empty then
+    int64_t sp_nnz = 0;
+    DevBuf sp_rowptr, sp_col, sp_val;     // int64[n+1], int32[nnz], float64[nnz]
+    DevBuf sp_colptr, sp_row, sp_cval;    // int64[n_-+1], int32[nnz], float64[nnz]
     // grid sizes of the W^T r and W d passes (0: defaults), set by the
     // autotuner at the end of setup
     int wt_blocks = 0, wd_blocks = 0;

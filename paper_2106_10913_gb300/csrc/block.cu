@@ -50,6 +50,13 @@ __device__ __forceinline__ void ldv(const double* p, double (&v)[2]) {
     const double2 t = *reinterpret_cast<const double2*>(p);
     v[0] = t.x; v[1] = t.y;
 }
+// two consecutive values of a float64 row kernel's columns, from float64 or
+// float32 storage
+__device__ __forceinline__ void ld2(const double* p, double (&v)[2]) { ldv(p, v); }
+__device__ __forceinline__ void ld2(const float* p, double (&v)[2]) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x; v[1] = t.y;
+}
 __device__ __forceinline__ void stv(float* p, const float (&v)[4]) {
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
@@ -82,9 +89,30 @@ __device__ __forceinline__ void colsum_grid(const double (&acc)[2], double* part
     __syncthreads();
     if (ticket != gridDim.x - 1) return;
     __threadfence();
+    // the last block adds the block partials with all its threads: thread t
+    // takes column t % K and every Q-th block from t / K (Q = 256 / K), in
+    // block order with four independent sums (the loads stay in flight);
+    // the Q sums of a column then meet in a fixed order
+    constexpr int Q = 256 / K;
+    __shared__ double qs[Q][K];
+    {
+        const int c = threadIdx.x % K, q = threadIdx.x / K;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int b = q;
+        for (; b + 3 * Q < (int)gridDim.x; b += 4 * Q) {
+            a0 += __ldcg(part + (size_t)b * K + c);
+            a1 += __ldcg(part + (size_t)(b + Q) * K + c);
+            a2 += __ldcg(part + (size_t)(b + 2 * Q) * K + c);
+            a3 += __ldcg(part + (size_t)(b + 3 * Q) * K + c);
+        }
+        for (; b < (int)gridDim.x; b += Q) a0 += __ldcg(part + (size_t)b * K + c);
+        qs[q][c] = (a0 + a1) + (a2 + a3);
+    }
+    __syncthreads();
     if (threadIdx.x < K) {
         double v = 0.0;
-        for (int b = 0; b < (int)gridDim.x; b++) v += __ldcg(part + (size_t)b * K + threadIdx.x);
+#pragma unroll
+        for (int q = 0; q < Q; q++) v += qs[q][threadIdx.x];
         out[threadIdx.x] = v;
     }
     if (threadIdx.x == 0) *cnt = 0u;
@@ -153,9 +181,10 @@ __global__ void __launch_bounds__(256) kb_resid(int n, const int* __restrict__ r
     }
 }
 
-// out[c] = sum_i X(i, c) Y(i, c) (nothing when *gate is 0, as kb_resid)
-template <int K>
-__global__ void __launch_bounds__(256) kb_coldot(int n, const double* __restrict__ X, const double* __restrict__ Y,
+// out[c] = sum_i X(i, c) Y(i, c) in float64 (Y float64, or the float32
+// output of a mixed-precision apply); nothing when *gate is 0, as kb_resid
+template <int K, typename TY = double>
+__global__ void __launch_bounds__(256) kb_coldot(int n, const double* __restrict__ X, const TY* __restrict__ Y,
                                                  double* part, unsigned* cnt, double* out,
                                                  const double* gate = nullptr) {
     if (gate && *gate == 0.0) return;
@@ -163,7 +192,7 @@ __global__ void __launch_bounds__(256) kb_coldot(int n, const double* __restrict
     ROW_LOOP(double, K) {
         double x[2], y[2];
         ldv(X + (size_t)i * K + c0, x);
-        ldv(Y + (size_t)i * K + c0, y);
+        ld2(Y + (size_t)i * K + c0, y);
         acc[0] = fma(x[0], y[0], acc[0]);
         acc[1] = fma(x[1], y[1], acc[1]);
     }
@@ -172,10 +201,11 @@ __global__ void __launch_bounds__(256) kb_coldot(int n, const double* __restrict
 
 // per column c: alpha = rz / pq (0 for inactive columns or pq <= 0);
 // X += alpha P, R -= alpha Q, rr = R . R
+// (R32, if given: R rounded to float32, the input of the next mixed-precision apply)
 template <int K>
 __global__ void __launch_bounds__(256) kb_pcg_xr(int n, double* sc, const double* __restrict__ P,
                                                  const double* __restrict__ Q, double* X, double* R,
-                                                 double* part, unsigned* cnt) {
+                                                 double* part, unsigned* cnt, float* R32 = nullptr) {
     double alpha[2], acc[2] = {0.0, 0.0};
     {
         const int cc = ((threadIdx.x & 31) % RM<double, K>::TPR) * 2;
@@ -201,14 +231,15 @@ __global__ void __launch_bounds__(256) kb_pcg_xr(int n, double* sc, const double
         }
         stv(X + e, x);
         stv(R + e, r);
+        if (R32) *reinterpret_cast<float2*>(R32 + e) = make_float2((float)r[0], (float)r[1]);
     }
     colsum_grid<K>(acc, part, cnt, sc + B_RR * K);
 }
 
 // per active column: beta = rz_new / rz, P = Z + beta P; the last block
 // then moves rz_new into rz
-template <int K>
-__global__ void __launch_bounds__(256) kb_pcg_p(int n, double* sc, const double* __restrict__ Z, double* P,
+template <int K, typename TZ = double>
+__global__ void __launch_bounds__(256) kb_pcg_p(int n, double* sc, const TZ* __restrict__ Z, double* P,
                                                 unsigned* cnt) {
     __shared__ unsigned ticket;
     double beta[2];
@@ -227,7 +258,7 @@ __global__ void __launch_bounds__(256) kb_pcg_p(int n, double* sc, const double*
     ROW_LOOP(double, K) {
         const size_t e = (size_t)i * K + c0;
         double z[2], pv[2];
-        ldv(Z + e, z);
+        ld2(Z + e, z);
         ldv(P + e, pv);
         pv[0] = a0 ? fma(beta[0], pv[0], z[0]) : pv[0];
         pv[1] = a1 ? fma(beta[1], pv[1], z[1]) : pv[1];
@@ -449,6 +480,91 @@ __global__ void __launch_bounds__(256) kb_tgemv(const int* __restrict__ sub_ptr,
 }
 
 // C(j, c) = wsign w_j sum_ps part[ps][j][c]  (fixed order)
+// Partial sums of C(c0_s + j, :) = sum_p B_s(p, j) X(idx_s(p), :) over the
+// rows [pa, pb) of split `blockIdx.y` of subdomain s = blockIdx.x, for every
+// column j of B_s (tiles of 32): each chunk of rows of X is gathered once
+// (16-byte loads of whole rows) and serves all columns of B_s.  Thread t
+// owns column c = t % K of X and JU = 32 / (256 / K) consecutive columns of
+// B_s from (t / K) JU, read from shared memory as 16-byte vectors (two
+// shared loads feed eight float32 FMAs; one shared load per FMA left the
+// kernel bound by its load/store pipe).
+template <typename T> struct V16;
+template <> struct V16<float> {
+    using type = float4;
+    static __device__ __forceinline__ float get(const float4& v, int i) {
+        return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+    }
+};
+template <> struct V16<double> {
+    using type = double2;
+    static __device__ __forceinline__ double get(const double2& v, int i) { return i == 0 ? v.x : v.y; }
+};
+constexpr int TG2_TJ = 32;
+template <typename T, int K>
+__global__ void __launch_bounds__(256) kb_tgemv2(const int* __restrict__ sub_ptr, const int* __restrict__ sub_idx,
+                                                 const int* __restrict__ colptr, const int64_t* __restrict__ boff,
+                                                 const T* __restrict__ B, const T* __restrict__ X, int ncol_total,
+                                                 T* __restrict__ part) {
+    constexpr int TG2_ROWS = sizeof(T) == 8 ? 32 : 64;  // rows per chunk (about 24 KB of shared memory)
+    constexpr int BP = TG2_TJ + 16 / (int)sizeof(T);     // padded row of bs (16-byte multiple)
+    __shared__ __align__(16) T xs[TG2_ROWS][K];
+    __shared__ __align__(16) T bs[TG2_ROWS][BP];
+    constexpr int JG = 256 / K, JU = TG2_TJ / JG;
+    constexpr int V4 = K * (int)sizeof(T) / 16;
+    constexpr int BV16 = 16 / (int)sizeof(T);            // values per 16-byte load
+    constexpr int BV = JU % BV16 == 0 ? BV16 : 1;         // (scalar loads for narrow column blocks)
+    const int s = blockIdx.x, rs = blockIdx.y;
+    const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
+    const int c0 = colptr[s], nc = colptr[s + 1] - c0;
+    if (nc == 0) return;
+    const int plen = (m + gridDim.y - 1) / gridDim.y;
+    const int pa = rs * plen, pb = min(m, pa + plen);
+    const int c = threadIdx.x % K, jb = (threadIdx.x / K) * JU;
+    const T* Bs = B + boff[s];
+    for (int j0 = 0; j0 < nc; j0 += TG2_TJ) {
+        const int jn = min(TG2_TJ, nc - j0);
+        T acc[JU];
+#pragma unroll
+        for (int u = 0; u < JU; u++) acc[u] = 0;
+        for (int q0 = pa; q0 < pb; q0 += TG2_ROWS) {
+            const int pn = min(TG2_ROWS, pb - q0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < TG2_TJ * TG2_ROWS; e += 256) {
+                const int jj = e / TG2_ROWS, pp = e % TG2_ROWS;
+                bs[pp][jj] = (jj < jn && pp < pn) ? Bs[(size_t)(j0 + jj) * m + q0 + pp] : (T)0;
+            }
+            for (int e = threadIdx.x; e < TG2_ROWS * V4; e += 256) {
+                const int pp = e / V4, cc = e % V4;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (pp < pn) v = reinterpret_cast<const float4*>(X + (size_t)sub_idx[p0 + q0 + pp] * K)[cc];
+                reinterpret_cast<float4*>(&xs[pp][0])[cc] = v;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int pp = 0; pp < TG2_ROWS; pp++) {
+                const T x = xs[pp][c];
+                if constexpr (BV == BV16) {
+                    using V = typename V16<T>::type;
+#pragma unroll
+                    for (int u0 = 0; u0 < JU; u0 += BV) {
+                        const V bv = *reinterpret_cast<const V*>(&bs[pp][jb + u0]);
+#pragma unroll
+                        for (int u = 0; u < BV; u++) acc[u0 + u] = fma(V16<T>::get(bv, u), x, acc[u0 + u]);
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < JU; u++) acc[u] = fma(bs[pp][jb + u], x, acc[u]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < JU; u++) {
+            const int jj = jb + u;
+            if (jj < jn) part[((size_t)rs * ncol_total + c0 + j0 + jj) * K + c] = acc[u];
+        }
+    }
+}
+
 template <typename T, int K>
 __global__ void kb_tg_sum(int ncol_total, const T* __restrict__ part, const T* __restrict__ w, T wsign, T* C) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1474,9 +1590,8 @@ struct BlockApply {
                      const T* w, T wsign, T* C, cudaStream_t s) {
         if (maxc == 0 || ncol_total == 0) return AWG_OK;
         ProfScope ps_(h, AWG_PROF_SUBDOMAIN, s);
-        const dim3 g(h->N, (maxc + KB_TG_C - 1) / KB_TG_C, TG_PS);
-        kb_tgemv<T, K><<<g, 256, 0, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p, colptr, boff, B, X, ncol_total,
-                                         v.tgp);
+        kb_tgemv2<T, K><<<dim3(h->N, TG_PS), 256, 0, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p, colptr, boff, B, X,
+                                                          ncol_total, v.tgp);
         AWG_LAUNCH();
         const size_t len = (size_t)ncol_total * K;
         kb_tg_sum<T, K><<<(unsigned)((len + 255) / 256), 256, 0, s>>>(ncol_total, v.tgp, w, wsign, C);
@@ -1892,6 +2007,39 @@ awg_status apply64_any(Handle* h, int K, int which, int prec, const double* X, d
     return apply64_k<64>(h, which, prec, X, Y, s, sl);
 }
 
+// A mixed-precision form on float32 block vectors, without the float64
+// conversions around it: the PCG kernels write r in float32 beside its
+// float64 copy (kb_pcg_xr) and read z in float32 (kb_coldot, kb_pcg_p), so
+// the preconditioner's input and output need no separate passes.
+// (the block autotuner is not run from here: it uses the float32 input
+// vector as scratch, so the PCG drivers call tune_first before they write r)
+template <int K>
+awg_status apply32_k(Handle* h, int which, int prec, const float* X, float* Y, cudaStream_t s, const Slot& sl) {
+    BlockApply<float, K> b{h, {}, sl};
+    carve_block(h, sl.ws, nullptr, &b.v);
+    return b.stage(which, prec, X, Y, s);
+}
+
+// The block autotuner on the first H_3 apply of width K, before a PCG
+// driver fills the apply's float32 input (X, Y float64 n x K scratch)
+template <int K>
+awg_status tune_first(Handle* h, int which, int prec, const double* X, double* Y, cudaStream_t s, const Slot& sl) {
+    constexpr int kidx = K == 16 ? 0 : (K == 32 ? 1 : 2);
+    if (which >= 4 && h->opt.autotune && h->bt_wt[kidx] == 0 && h->n_minus > 0) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        AWG_CUDA(cudaStreamIsCapturing(s, &cs));
+        if (cs == cudaStreamCaptureStatusNone) AWG_TRY(tune_k<K>(h, prec, X, Y, s, sl));
+    }
+    return AWG_OK;
+}
+
+awg_status apply32_any(Handle* h, int K, int which, int prec, const float* X, float* Y, cudaStream_t s,
+                       const Slot& sl) {
+    if (K == 16) return apply32_k<16>(h, which, prec, X, Y, s, sl);
+    if (K == 32) return apply32_k<32>(h, which, prec, X, Y, s, sl);
+    return apply32_k<64>(h, which, prec, X, Y, s, sl);
+}
+
 // Block autotuner: on the first H_3 apply of width K, time the apply (on
 // the caller's X, Y) for CTAs per SM of the W^T B pass in {1, 2, 4} and
 // blocks per SM of the float64 coarse GEMM in {2, 4, 8}, keep the fastest
@@ -1945,6 +2093,91 @@ awg_status tune_k(Handle* h, int prec, const double* X, double* Y, cudaStream_t 
 
 int pick_k(int nrhs) { return nrhs <= 16 ? 16 : (nrhs <= 32 ? 32 : 64); }
 
+// PCG steps shared by the host-driven and graph-driven block solves.  The
+// float64 form applies the preconditioner to the float64 r (v.pr) into the
+// float64 z (v.pz); the mixed forms apply it to the float32 copy of r that
+// the last x, r update wrote (v.rin) into a float32 z (v.out), which the dot
+// products and the p update read directly (z is computed in float32 there,
+// so nothing is lost), and the recurrences stay float64.
+template <int K>
+struct PcgSteps {
+    Handle* h;
+    const BView<double>& v;
+    int prec;
+    cudaStream_t s;
+    const Slot& sl;
+
+    unsigned g(const void* kern) const { return grid_for(kern, h->n, RM<double, K>::RPB); }
+    float* r32() const { return (float*)v.rin; }
+    float* z32() const { return (float*)v.out; }
+
+    // first use of the autotuner, then the float32 copy of r = b
+    awg_status start() {
+        AWG_TRY(tune_first<K>(h, 4 + h->opt.variant, prec, v.pb, v.pz, s, sl));
+        if (prec == AWG_FP64) return AWG_OK;
+        const size_t len = (size_t)h->n * K;
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        kb_cvt<double, float><<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, v.pr, r32());
+        AWG_LAUNCH();
+        return AWG_OK;
+    }
+    // z = H r, *rz = r . z (per column)
+    awg_status precond(double* rz) {
+        const int n = h->n;
+        if (prec == AWG_FP64) {
+            AWG_TRY(apply64_any(h, K, 4 + h->opt.variant, prec, v.pr, v.pz, s, sl));
+            ProfScope ps_(h, AWG_PROF_VECTOR, s);
+            kb_coldot<K><<<g((const void*)kb_coldot<K>), 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, rz);
+            AWG_LAUNCH();
+            return AWG_OK;
+        }
+        AWG_TRY(apply32_any(h, K, 4 + h->opt.variant, prec, r32(), z32(), s, sl));
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        kb_coldot<K, float><<<g((const void*)kb_coldot<K, float>), 256, 0, s>>>(n, v.pr, z32(), v.red, v.cnt, rz);
+        AWG_LAUNCH();
+        return AWG_OK;
+    }
+    // p = z (first iteration)
+    awg_status p_first() {
+        const size_t len = (size_t)h->n * K;
+        if (prec == AWG_FP64) {
+            AWG_CUDA(cudaMemcpyAsync(v.pp, v.pz, len * 8, cudaMemcpyDeviceToDevice, s));
+            return AWG_OK;
+        }
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        kb_cvt<float, double><<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, z32(), v.pp);
+        AWG_LAUNCH();
+        return AWG_OK;
+    }
+    // p = z + beta p
+    awg_status p_update() {
+        const int n = h->n;
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        if (prec == AWG_FP64)
+            kb_pcg_p<K><<<g((const void*)kb_pcg_p<K>), 256, 0, s>>>(n, v.sc, v.pz, v.pp, v.cnt);
+        else
+            kb_pcg_p<K, float><<<g((const void*)kb_pcg_p<K, float>), 256, 0, s>>>(n, v.sc, z32(), v.pp, v.cnt);
+        AWG_LAUNCH();
+        return AWG_OK;
+    }
+    // q = A p with p . q, then x, r (and the float32 r) updates with r . r
+    awg_status spmv_xr() {
+        const int n = h->n;
+        {
+            ProfScope ps_(h, AWG_PROF_SPMV, s);
+            kb_spmv_dot<K><<<g((const void*)kb_spmv_dot<K>), 256, 0, s>>>(n, (int*)h->rowptr.p, (int*)h->colidx.p,
+                                                                        (double*)h->val.p, v.pp, v.pq, v.red,
+                                                                        v.cnt, v.sc + B_PQ * K);
+            AWG_LAUNCH();
+        }
+        ProfScope ps_(h, AWG_PROF_VECTOR, s);
+        kb_pcg_xr<K><<<g((const void*)kb_pcg_xr<K>), 256, 0, s>>>(n, v.sc, v.pp, v.pq, v.px, v.pr, v.red, v.cnt,
+                                                                  prec == AWG_FP64 ? nullptr : r32());
+        AWG_LAUNCH();
+        return AWG_OK;
+    }
+};
+
 template <int K>
 awg_status pcg_k(Handle* h, int prec, const double* b, double* x, int nrhs, int ld, double rtol, int* iters,
                  double* relres, cudaStream_t s) {
@@ -1965,9 +2198,11 @@ awg_status pcg_k(Handle* h, int prec, const double* b, double* x, int nrhs, int 
     AWG_CUDA(cudaMemsetAsync(v.px, 0, len * 8, s));
     AWG_CUDA(cudaMemcpyAsync(v.pr, v.pb, len * 8, cudaMemcpyDeviceToDevice, s));
     AWG_TRY(prof_vec([&] { kb_coldot<K><<<grid_for((const void*)kb_coldot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.pb, v.pb, v.red, v.cnt, sc + B_BB * K); }));
-    AWG_TRY(apply64_any(h, K, 4 + h->opt.variant, prec, v.pr, v.pz, s, slot0(h)));
-    AWG_TRY(prof_vec([&] { kb_coldot<K><<<grid_for((const void*)kb_coldot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, sc + B_RZ * K); }));
-    AWG_CUDA(cudaMemcpyAsync(v.pp, v.pz, len * 8, cudaMemcpyDeviceToDevice, s));
+    const Slot sl0 = slot0(h);
+    PcgSteps<K> ps{h, v, prec, s, sl0};
+    AWG_TRY(ps.start());
+    AWG_TRY(ps.precond(sc + B_RZ * K));
+    AWG_TRY(ps.p_first());
     std::vector<double> hs(B_NSC * K);
     AWG_CUDA(cudaMemcpyAsync(hs.data(), sc, B_NSC * K * 8, cudaMemcpyDeviceToHost, s));
     AWG_CUDA(cudaStreamSynchronize(s));
@@ -1998,13 +2233,7 @@ awg_status pcg_k(Handle* h, int prec, const double* b, double* x, int nrhs, int 
     };
     while (nact > 0) {
         if (it >= h->opt.maxit) { st = AWG_ERR_MAXIT; break; }
-        {
-            ProfScope ps_(h, AWG_PROF_SPMV, s);
-            kb_spmv_dot<K><<<grid_for((const void*)kb_spmv_dot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, (int*)h->rowptr.p, (int*)h->colidx.p, (double*)h->val.p, v.pp, v.pq,
-                                              v.red, v.cnt, sc + B_PQ * K);
-        }
-        AWG_LAUNCH();
-        AWG_TRY(prof_vec([&] { kb_pcg_xr<K><<<grid_for((const void*)kb_pcg_xr<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, sc, v.pp, v.pq, v.px, v.pr, v.red, v.cnt); }));
+        AWG_TRY(ps.spmv_xr());
         it++;
         AWG_CUDA(cudaMemcpyAsync(hs.data(), sc, 3 * K * 8, cudaMemcpyDeviceToHost, s));
         AWG_CUDA(cudaStreamSynchronize(s));
@@ -2032,9 +2261,8 @@ awg_status pcg_k(Handle* h, int prec, const double* b, double* x, int nrhs, int 
         }
         if (nact == 0) break;
         if (changed) AWG_TRY(upload_act());
-        AWG_TRY(apply64_any(h, K, 4 + h->opt.variant, prec, v.pr, v.pz, s, slot0(h)));
-        AWG_TRY(prof_vec([&] { kb_coldot<K><<<grid_for((const void*)kb_coldot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, sc + B_RZN * K); }));
-        AWG_TRY(prof_vec([&] { kb_pcg_p<K><<<grid_for((const void*)kb_pcg_p<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, sc, v.pz, v.pp, v.cnt); }));
+        AWG_TRY(ps.precond(sc + B_RZN * K));
+        AWG_TRY(ps.p_update());
     }
     bool need = false;
     for (int c = 0; c < nrhs; c++)
@@ -2099,30 +2327,10 @@ awg_status stop_test_k(Handle* h, const BView<double>& v, cudaStream_t s, cudaGr
 template <int K>
 awg_status pcg_body_k(Handle* h, int prec, const BView<double>& v, cudaStream_t s, cudaGraphConditionalHandle hc,
                       int set, int add, const Slot& sl) {
-    const int n = h->n;
-    const unsigned gr = grid_rows(n, RM<double, K>::RPB);
-    AWG_TRY(apply64_any(h, K, 4 + h->opt.variant, prec, v.pr, v.pz, s, sl));
-    {
-        ProfScope ps_(h, AWG_PROF_VECTOR, s);
-        kb_coldot<K><<<grid_for((const void*)kb_coldot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, v.sc + B_RZN * K);
-        AWG_LAUNCH();
-    }
-    {
-        ProfScope ps_(h, AWG_PROF_VECTOR, s);
-        kb_pcg_p<K><<<grid_for((const void*)kb_pcg_p<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.sc, v.pz, v.pp, v.cnt);
-        AWG_LAUNCH();
-    }
-    {
-        ProfScope ps_(h, AWG_PROF_SPMV, s);
-        kb_spmv_dot<K><<<grid_for((const void*)kb_spmv_dot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, (int*)h->rowptr.p, (int*)h->colidx.p, (double*)h->val.p, v.pp, v.pq,
-                                          v.red, v.cnt, v.sc + B_PQ * K);
-        AWG_LAUNCH();
-    }
-    {
-        ProfScope ps_(h, AWG_PROF_VECTOR, s);
-        kb_pcg_xr<K><<<grid_for((const void*)kb_pcg_xr<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.sc, v.pp, v.pq, v.px, v.pr, v.red, v.cnt);
-        AWG_LAUNCH();
-    }
+    PcgSteps<K> ps{h, v, prec, s, sl};
+    AWG_TRY(ps.precond(v.sc + B_RZN * K));
+    AWG_TRY(ps.p_update());
+    AWG_TRY(ps.spmv_xr());
     return stop_test_k<K>(h, v, s, hc, set, add);
 }
 
@@ -2219,24 +2427,11 @@ awg_status pcg_async_k(Handle* h, int prec, const double* b, double* x, int nrhs
         AWG_LAUNCH();
     }
     // first iteration with z = H r, p = z (then the loop's iterations)
-    AWG_TRY(apply64_any(h, K, 4 + h->opt.variant, prec, v.pr, v.pz, s, sl));
-    {
-        ProfScope ps_(h, AWG_PROF_VECTOR, s);
-        kb_coldot<K><<<grid_for((const void*)kb_coldot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.pr, v.pz, v.red, v.cnt, v.sc + B_RZ * K);
-        AWG_LAUNCH();
-    }
-    AWG_CUDA(cudaMemcpyAsync(v.pp, v.pz, len * 8, cudaMemcpyDeviceToDevice, s));
-    {
-        ProfScope ps_(h, AWG_PROF_SPMV, s);
-        kb_spmv_dot<K><<<grid_for((const void*)kb_spmv_dot<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, (int*)h->rowptr.p, (int*)h->colidx.p, (double*)h->val.p, v.pp, v.pq,
-                                          v.red, v.cnt, v.sc + B_PQ * K);
-        AWG_LAUNCH();
-    }
-    {
-        ProfScope ps_(h, AWG_PROF_VECTOR, s);
-        kb_pcg_xr<K><<<grid_for((const void*)kb_pcg_xr<K>, n, RM<double, K>::RPB), 256, 0, s>>>(n, v.sc, v.pp, v.pq, v.px, v.pr, v.red, v.cnt);
-        AWG_LAUNCH();
-    }
+    PcgSteps<K> ps{h, v, prec, s, sl};
+    AWG_TRY(ps.start());
+    AWG_TRY(ps.precond(v.sc + B_RZ * K));
+    AWG_TRY(ps.p_first());
+    AWG_TRY(ps.spmv_xr());
     AWG_TRY(stop_test_k<K>(h, v, s, 0, 0, 0));
     // the loop graph is captured after the first iteration has been issued
     // (every kernel attribute and tensor-map entry point is set up by then)

@@ -95,6 +95,7 @@ void scalars(IO& io, Handle& h) {
         io.pod(P.corr_nnz);
         io.pod(P.wt_blocks);
         io.pod(P.wd_blocks);
+        io.pod(P.sp_nnz);
     }
 }
 
@@ -124,7 +125,8 @@ std::vector<DevBuf*> buffers(Handle& h) {
                               &h.wcol_ptr, &h.Wcm,     &h.F64};
     for (PrecOps& P : h.prec)
         for (DevBuf* d : {&P.G, &P.W, &P.Finv, &P.inexInv, &P.rscale, &P.cscale, &P.corr_rowptr, &P.corr_col,
-                          &P.corr_val, &P.corr_colptr, &P.corr_row, &P.corr_cval})
+                          &P.corr_val, &P.corr_colptr, &P.corr_row, &P.corr_cval, &P.sp_rowptr, &P.sp_col,
+                          &P.sp_val, &P.sp_colptr, &P.sp_row, &P.sp_cval})
             b.push_back(d);
     return b;
 }
@@ -203,8 +205,10 @@ std::vector<Need> needs(const Handle& h) {
                                          : (p == AWG_MIXED_FP32 && !h.h_g32_off.empty() ? (uint64_t)h.h_g32_off[N] * 4
                                                                                         : 0);
         const uint64_t cn = (uint64_t)std::max<int64_t>(0, P.corr_nnz);
+        const uint64_t sn = (uint64_t)std::max<int64_t>(0, P.sp_nnz);
+        const bool sparse = p == AWG_FP64 && sn > 0;
         r.push_back({g, !(b && p == AWG_FP64)});                          // G
-        r.push_back({n * ldw * w, !(b && nm > 0)});                      // W
+        r.push_back({n * ldw * w, !(b && nm > 0 && !sparse)});           // W (absent when truncated)
         r.push_back({nm * nm * 8, !(b && nm > 0)});                      // Finv
         r.push_back({nm * nm * 8, true});                                // inexInv
         r.push_back({p == AWG_MIXED_FP16 ? n * 4 : 0, !(b && p == AWG_MIXED_FP16 && nm > 0)});    // rscale
@@ -215,6 +219,12 @@ std::vector<Need> needs(const Handle& h) {
         r.push_back({cn ? (nm + 1) * 4 : 0, cn == 0});                  // corr_colptr
         r.push_back({cn * 4, cn == 0});                                  // corr_row
         r.push_back({cn * 4, cn == 0});                                  // corr_cval
+        r.push_back({sparse ? (n + 1) * 8 : 0, !sparse});                // sp_rowptr
+        r.push_back({sn * 4, !sparse});                                  // sp_col
+        r.push_back({sn * 8, !sparse});                                  // sp_val
+        r.push_back({sparse ? (nm + 1) * 8 : 0, !sparse});               // sp_colptr
+        r.push_back({sn * 4, !sparse});                                  // sp_row
+        r.push_back({sn * 8, !sparse});                                  // sp_cval
     }
     return r;
 }

@@ -568,6 +568,141 @@ static awg_status atb_sym(Handle* h, int n, int m, const double* A, const double
     return AWG_OK;
 }
 
+// ------------------------------------------------------------ truncated W
+// Wt(:, j) = W(:, j) with the entries below tol * max_i |W(i, j)| set to 0
+// (column-major n x nm); cnt[j] = entries kept.  One block per column.
+__global__ void __launch_bounds__(256) k_w_truncate(int n, const double* __restrict__ W, double tol,
+                                                    double* __restrict__ Wt, int64_t* __restrict__ cnt) {
+    __shared__ double red[32];
+    __shared__ unsigned long long kept;
+    const int j = blockIdx.x;
+    const double* w = W + (size_t)j * n;
+    double mx = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, fabs(w[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    if (threadIdx.x == 0) kept = 0ull;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0) red[0] = v;
+    }
+    __syncthreads();
+    const double thr = tol * red[0];
+    unsigned c = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double v = w[i];
+        const bool keep = fabs(v) >= thr;
+        Wt[(size_t)j * n + i] = keep ? v : 0.0;
+        c += keep;
+    }
+    atomicAdd(&kept, (unsigned long long)c);
+    __syncthreads();
+    if (threadIdx.x == 0) cnt[j] = (int64_t)kept;
+}
+
+// CSC of the truncated W: column j's nonzeros in row order at colptr[j]
+// (order-preserving compaction: warp ballots, then the warps' counts in
+// order).  One block of 256 threads per column.
+__global__ void __launch_bounds__(256) k_w_csc(int n, const double* __restrict__ Wt,
+                                               const int64_t* __restrict__ colptr, int* __restrict__ row,
+                                               double* __restrict__ val) {
+    __shared__ int wc[8];
+    const int j = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double* w = Wt + (size_t)j * n;
+    int64_t base = colptr[j];
+    for (int i0 = 0; i0 < n; i0 += 256) {
+        const int i = i0 + threadIdx.x;
+        const double v = i < n ? w[i] : 0.0;
+        const bool nz = v != 0.0;
+        const unsigned m = __ballot_sync(0xffffffffu, nz);
+        if (lane == 0) wc[warp] = __popc(m);
+        __syncthreads();
+        int off = 0;
+        for (int q = 0; q < warp; q++) off += wc[q];
+        int tot = 0;
+        for (int q = 0; q < 8; q++) tot += wc[q];
+        if (nz) {
+            const int64_t k = base + off + __popc(m & ((1u << lane) - 1u));
+            row[k] = i;
+            val[k] = v;
+        }
+        base += tot;
+        __syncthreads();
+    }
+}
+
+// CSR of the truncated W: row i's nonzeros in column order.  rcnt: a
+// thread per row counts its kept entries; rfill: the same thread writes
+// them from rowptr[i].
+__global__ void k_w_rcnt(int n, int nm, const double* __restrict__ Wt, int64_t* __restrict__ rcnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t c = 0;
+    for (int j = 0; j < nm; j++) c += Wt[(size_t)j * n + i] != 0.0;
+    rcnt[i] = c;
+}
+__global__ void k_w_rfill(int n, int nm, const double* __restrict__ Wt, const int64_t* __restrict__ rowptr,
+                          int* __restrict__ col, double* __restrict__ val) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t k = rowptr[i];
+    for (int j = 0; j < nm; j++) {
+        const double v = Wt[(size_t)j * n + i];
+        if (v != 0.0) {
+            col[k] = j;
+            val[k] = v;
+            k++;
+        }
+    }
+}
+
+// The truncated W of the float64 form (w_drop_tol > 0): the dense truncated
+// copy (column-major, caller frees it) and its CSR / CSC in P
+static awg_status build_truncated_W(Handle* h, const double* W64, double** Wt_out, PrecOps& P) {
+    cudaStream_t s = h->stream;
+    const int n = h->n, nm = h->n_minus;
+    double* Wt = nullptr;
+    int64_t* dcnt = nullptr;
+    AWG_CUDA(cudaMallocAsync(&Wt, (size_t)n * nm * 8, s));
+    AWG_CUDA(cudaMallocAsync(&dcnt, (size_t)std::max(n, nm) * 8, s));
+    k_w_truncate<<<nm, 256, 0, s>>>(n, W64, h->opt.w_drop_tol, Wt, dcnt);
+    AWG_LAUNCH();
+    std::vector<int64_t> cnt(nm), ptr(std::max(n, nm) + 1, 0);
+    AWG_CUDA(cudaMemcpyAsync(cnt.data(), dcnt, (size_t)nm * 8, cudaMemcpyDeviceToHost, s));
+    AWG_CUDA(cudaStreamSynchronize(s));
+    for (int j = 0; j < nm; j++) ptr[j + 1] = ptr[j] + cnt[j];
+    const int64_t nnz = ptr[nm];
+    P.sp_nnz = nnz;
+    AWG_TRY(upload(h, P.sp_colptr, ptr.data(), (size_t)(nm + 1) * 8));
+    AWG_TRY(dalloc(h, P.sp_row, (size_t)std::max<int64_t>(nnz, 1) * 4));
+    AWG_TRY(dalloc(h, P.sp_cval, (size_t)std::max<int64_t>(nnz, 1) * 8));
+    k_w_csc<<<nm, 256, 0, s>>>(n, Wt, (const int64_t*)P.sp_colptr.p, (int*)P.sp_row.p, (double*)P.sp_cval.p);
+    AWG_LAUNCH();
+    k_w_rcnt<<<(n + 255) / 256, 256, 0, s>>>(n, nm, Wt, dcnt);
+    AWG_LAUNCH();
+    std::vector<int64_t> rc(n);
+    AWG_CUDA(cudaMemcpyAsync(rc.data(), dcnt, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    AWG_CUDA(cudaStreamSynchronize(s));
+    ptr.assign(n + 1, 0);
+    for (int i = 0; i < n; i++) ptr[i + 1] = ptr[i] + rc[i];
+    AWG_TRY(upload(h, P.sp_rowptr, ptr.data(), (size_t)(n + 1) * 8));
+    AWG_TRY(dalloc(h, P.sp_col, (size_t)std::max<int64_t>(nnz, 1) * 4));
+    AWG_TRY(dalloc(h, P.sp_val, (size_t)std::max<int64_t>(nnz, 1) * 8));
+    k_w_rfill<<<(n + 255) / 256, 256, 0, s>>>(n, nm, Wt, (const int64_t*)P.sp_rowptr.p, (int*)P.sp_col.p,
+                                              (double*)P.sp_val.p);
+    AWG_LAUNCH();
+    AWG_CUDA(cudaFreeAsync(dcnt, s));
+    if (h->opt.verbose)
+        fprintf(stderr, "libawg: truncated W: %lld of %lld entries kept (tol %.1e)\n", (long long)nnz,
+                (long long)n * nm, h->opt.w_drop_tol);
+    *Wt_out = Wt;
+    return AWG_OK;
+}
+
 // F = Wt^T A Wt for a column-major (rounded) W, its inverse into Finv
 static awg_status build_F(Handle* h, const double* Wt, DevBuf& Finv, DevBuf* keepF) {
     cudaStream_t s = h->stream;
@@ -1132,13 +1267,24 @@ awg_status build_setup_numeric(Handle* h) {
         h->setup_ms[5] = t5 - t4;
         const double* W64 = (const double*)h->Wcm.p;
         PrecOps& P64 = h->prec[AWG_FP64];
-        AWG_TRY(build_F(h, W64, P64.Finv, &h->F64));
         const bool inex = (h->opt.variant == AWG_H3_INEX) || (n <= 200000 && nm <= 4096);
-        if (inex) AWG_TRY(build_inex(h, W64, P64.inexInv));
-        AWG_TRY(dalloc(h, P64.W, (size_t)n * h->ldw * 8));
         const unsigned gw = (unsigned)(((size_t)n * h->ldw + 255) / 256);
-        k_to_rowmajor<double><<<gw, 256, 0, s>>>(n, nm, h->ldw, W64, (double*)P64.W.p);
-        AWG_LAUNCH();
+        if (h->opt.w_drop_tol > 0.0) {
+            // the float64 form on the truncated W: F (and the H_3,inex
+            // matrix) from the truncated copy, the apply from its CSR / CSC
+            double* Wt = nullptr;
+            AWG_TRY(build_truncated_W(h, W64, &Wt, P64));
+            // (no H_3,inex matrix: Thm. 7's inner matrix C^-1 - Vhat^T W
+            // needs W = A_+^-1 Vhat, which the truncated W no longer is)
+            AWG_TRY(build_F(h, Wt, P64.Finv, &h->F64));
+            AWG_CUDA(cudaFreeAsync(Wt, s));
+        } else {
+            AWG_TRY(build_F(h, W64, P64.Finv, &h->F64));
+            if (inex) AWG_TRY(build_inex(h, W64, P64.inexInv));
+            AWG_TRY(dalloc(h, P64.W, (size_t)n * h->ldw * 8));
+            k_to_rowmajor<double><<<gw, 256, 0, s>>>(n, nm, h->ldw, W64, (double*)P64.W.p);
+            AWG_LAUNCH();
+        }
         for (int p = 1; p < AWG_NPREC; p++) {
             if (!(h->opt.precisions & (1 << p))) continue;
             PrecOps& P = h->prec[p];

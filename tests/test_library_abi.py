@@ -62,13 +62,15 @@ def test_host_only_calls(lib):
     assert lib.awg_learned_grad(0, None, None, None, None, 0, None) == 1
     assert lib.awg_learned_train(1, None, None, None, 1, 1e-2, 0, None, None) == 1
     assert lib.awg_learned_data(None, None, None, None) == 1
-    assert ctypes.sizeof(pkg.awg.awg_options) == 104
+    assert ctypes.sizeof(pkg.awg.awg_options) == 112
     assert o.w16_keep == 0.1
     d = pkg.default_options()
     assert d.block_tensor_cores == 1 and d.h2 == pkg.H2_NN_HYB and d.tau_flat == 10.0
-    assert d.coarse_tensor_cores == 1
-    o = pkg.default_options(coarse_tensor_cores=2)
-    assert lib.awg_setup(4, 4, 1, 1, 1, 1, 1, 1, 0.1, ctypes.byref(o), None, ctypes.byref(h)) == 1
+    assert d.coarse_tensor_cores == 1 and d.w_drop_tol == 0.0
+    for bad in ({"coarse_tensor_cores": 2}, {"w_drop_tol": -1.0}, {"w_drop_tol": 1.0},
+                {"w_drop_tol": 1e-4, "variant": 2}):
+        o = pkg.default_options(**bad)
+        assert lib.awg_setup(4, 4, 1, 1, 1, 1, 1, 1, 0.1, ctypes.byref(o), None, ctypes.byref(h)) == 1, bad
     # H_2 choice and tau_flat are checked before any device work
     for bad in ({"h2": 4}, {"h2": -1}, {"h2": pkg.H2_ASP_AD, "tau_flat": 0.0}):
         o = pkg.default_options(**bad)

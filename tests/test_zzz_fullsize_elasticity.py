@@ -1,0 +1,116 @@
+"""Parity at the elasticity workload's full size: Q1 plane-strain elasticity
+on a 384 x 384 element mesh of the unit square (2 dofs per node, left edge
+clamped, n = 295 680), Young's modulus in seeded layers alternating 1 and
+1e5, Poisson ratio 0.3, 16 x 16 node boxes grown by 2 layers, tau = 0.1,
+and its 32 right-hand sides solved in ONE block PCG (awg_inputs.config4).
+The CPU oracle's own run on the whole problem (tests/golden/config4_oracle.json,
+written by tests/golden/make_config4_reference.py, which calls only the
+oracle) pins:
+
+* the eigenvalue counts n^s_-, the strict counts and the GenEO mode counts
+  of all 256 subdomains, n0 and n_- (bit-exact);
+* 4096 sampled entries (and the 2-norm) of H_3,ad x: float64 form within
+  max(1e-11, kappa_loc eps) of the largest entry, float32 form within 1e-4;
+* the PCG iterations of columns 0, 1, 16 and 31 within 5 % of the oracle's,
+  for the 32 columns of one graph-driven block solve (float64 recurrences;
+  float32 local operators and W, and float16 W), every column with a true
+  relative residual <= 1e-8.
+
+Bit-exact over the whole problem as well: every Omega^s, M_mu and D.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import awg_inputs as gi
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REF = os.path.join(os.path.dirname(__file__), "golden", "config4_oracle.json")
+_STATE = {}
+
+
+def _ref():
+    if not os.path.exists(REF):
+        pytest.skip("config4_oracle.json not written yet (tests/golden/make_config4_reference.py)")
+    return json.load(open(REF))
+
+
+def _full():
+    if not _STATE:
+        from paper_2106_10913_gb300 import AWGSolver
+        p = gi.config4()
+        sol = AWGSolver(p.rowptr, p.colidx, p.val, p.part, p.nparts, p.overlap, p.tau, precisions=0b1011)
+        A = O.csr_from(p.rowptr, p.colidx, p.val, p.n)
+        _STATE.update(p=p, sol=sol, A=A)
+    return _STATE
+
+
+def _within_5pct(its, ref):
+    return abs(its - ref) <= max(1.0, 0.05 * ref)
+
+
+def test_structure_exact_elasticity():
+    S = _full()
+    p, sol, A = S["p"], S["sol"], S["A"]
+    subs = O.grow_subdomains(A, p.part, p.nparts, p.overlap)
+    assert sol.array("ns").tolist() == [len(s) for s in subs]
+    assert np.array_equal(sol.array("sub_idx"), np.concatenate(subs))
+    Mmu = O.pair_multiplicity(A, subs)
+    coo = A.tocoo()
+    assert np.array_equal(sol.array("mmu"), np.asarray(Mmu.tocsr()[coo.row, coo.col]).ravel())
+    d, _ = O.partition_of_unity(subs, p.n)
+    assert np.array_equal(sol.array("dvec"), d)
+
+
+def test_counts_and_apply_against_stored_oracle():
+    ref = _ref()
+    S = _full()
+    p, sol = S["p"], S["sol"]
+    assert sol.info["n0"] == ref["n0"] and sol.info["n_minus"] == ref["n_minus"]
+    assert sol.array("n_minus").tolist() == ref["n_minus_per_subdomain"]
+    assert sol.array("n_strict").tolist() == ref["n_strict_per_subdomain"]
+    assert sol.array("modes").tolist() == ref["modes_per_subdomain"]
+    from paper_2106_10913_gb300 import MIXED_FP32
+    ap = ref["apply_h3ad"]
+    x = torch.from_numpy(np.random.default_rng(ap["x_seed"]).standard_normal(p.n)).cuda()
+    idx, yref = np.array(ap["idx"]), np.array(ap["y"])
+    tol64 = max(1e-11, ref["local_condition"] * np.finfo(float).eps)
+    for prec, tol in ((0, tol64), (MIXED_FP32, 1e-4)):
+        y = sol.apply(x, precision=prec).cpu().numpy()
+        assert np.max(np.abs(y[idx] - yref)) <= tol * ap["y_max_abs"], prec
+        assert abs(np.linalg.norm(y) - ap["y_norm"]) <= tol * ap["y_norm"], prec
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp16"])
+def test_block_solve_32_columns(form):
+    """The workload's 32 right-hand sides in one graph-driven block solve."""
+    ref = _ref()
+    S = _full()
+    p, sol, A = S["p"], S["sol"], S["A"]
+    from paper_2106_10913_gb300 import MIXED_FP16, MIXED_FP32, awg_pcg_block_async
+    prec = {"fp32": MIXED_FP32, "fp16": MIXED_FP16}[form]
+    Bh = np.ascontiguousarray(p.b)
+    assert Bh.shape[0] == 32
+    b = torch.from_numpy(Bh).cuda()
+    x = torch.zeros_like(b)
+    its = torch.zeros(32, dtype=torch.int32, device="cuda")
+    rel = torch.zeros(32, dtype=torch.float64, device="cuda")
+    st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    awg_pcg_block_async(sol.h, b, x, its, rel, st, 1e-8, precision=prec)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    X = x.cpu().numpy()
+    R = A @ X.T - Bh.T
+    true_rel = np.linalg.norm(R, axis=0) / np.linalg.norm(Bh, axis=1)
+    assert np.all(true_rel <= 1e-8 * (1 + 1e-12)), float(true_rel.max())
+    its_h = its.cpu().numpy()
+    refs = {int(c): v["iters"] for c, v in ref["pcg_columns"].items()}
+    print(f"[elasticity {form} block solve: iterations {dict((c, int(its_h[c])) for c in refs)} oracle {refs}]")
+    for c, ri in refs.items():
+        assert _within_5pct(int(its_h[c]), ri), (form, c, int(its_h[c]), ri)
