@@ -562,10 +562,12 @@ def config3(L: int = 96, k: int = 512) -> Problem:
     return grf3d(L, k=k)
 
 
-def config4(nex: int = 384, nrhs: int = 32, seed: int = 7) -> Problem:
+def config4(nex: int = 384, nrhs: int = 32, seed: int = 7, q: int = 16) -> Problem:
     """Q1 elasticity 384x384 on the unit square, left edge clamped, layered E
     (thicknesses U{4..24} elements, alternating 1 and 1e5 starting with 1),
-    16x16 node boxes, overlap 2, 32 random right-hand sides."""
+    16x16 node boxes, overlap 2, 32 random right-hand sides.  Smaller meshes
+    with q = nex / 24 keep the subdomains' size (the coefficient draws of the
+    learned start's training and evaluation)."""
     rng = np.random.default_rng(seed)
     rowE = np.empty(nex)
     j, k = 0, 0
@@ -574,8 +576,6 @@ def config4(nex: int = 384, nrhs: int = 32, seed: int = 7) -> Problem:
         rowE[j:j + t] = 1.0 if k % 2 == 0 else 1e5
         j += t
         k += 1
-    q = 16
-
     def owner_of_node(i, jn):
         bx = np.minimum((i * q) // (nex + 1), q - 1)
         by = np.minimum((jn * q) // (nex + 1), q - 1)

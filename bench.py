@@ -42,12 +42,33 @@ WORKLOAD = ("2D heterogeneous diffusion 512x512 (n=262144), 20 channels of width
             "16x16=256 box subdomains, overlap 2, tau=0.1, single RHS ~ N(0,1), H3,ad + H_hyb^NN")
 
 
+WORKLOADS = {
+    "config3": ("3D log-normal diffusion 96^3 (n=884736), sigma 3, correlation length 8, 512 uneven k-means "
+                "subdomains, overlap 2, tau=0.1"),
+    "config4": ("Q1 plane-strain elasticity 384x384 (n=295680), layered Young's modulus 1 / 1e5, 16x16 node boxes, "
+                "overlap 2, tau=0.1, its 32 right-hand sides"),
+}
+
+
+def _workload(name, p):
+    if name == "config2":
+        return WORKLOAD
+    return WORKLOADS.get(name, f"{p.name} (n={p.n}, {p.nparts} subdomains, overlap {p.overlap}, tau={p.tau})")
+
+
 def _problem(name):
     import awg_inputs as gi
     if name == "config2":
         return gi.config2()
     if name == "config1":
         return gi.config1()
+    if name == "config3":
+        return gi.config3()
+    if name == "config4":
+        return gi.config4()
+    if name.startswith("grf"):  # grf<L>: the 3D log-normal generator at L^3 with L^3 / 1728 k-means parts
+        L = int(name[3:])
+        return gi.grf3d(L, k=max(2, round(L ** 3 / 1728)))
     if name.startswith("channels"):
         L = int(name[len("channels"):])
         return gi.channels2d(L, q=L // 32, nchan=max(1, round(20 * L / 512)), contrast=1e6, seed=2,
@@ -415,7 +436,8 @@ def run_awg(args):
     info["ns"] = ns_arr.tolist()
     info["z_entries"] = int(np.dot(ns_arr, sol.array("modes").astype(np.int64)))
     info["vm_entries"] = int(np.dot(ns_arr, sol.array("n_minus").astype(np.int64)))
-    b = torch.from_numpy(p.b).cuda()
+    b1 = p.b if p.b.ndim == 1 else p.b[0]  # single-RHS forms: the first right-hand side
+    b = torch.from_numpy(np.ascontiguousarray(b1)).cuda()
     x = torch.zeros_like(b)
     stream = torch.cuda.current_stream()
 
@@ -429,7 +451,10 @@ def run_awg(args):
     Kmax = max([args.nrhs] + [int(m.group(3)) for m in (re.match(r"(.*)_(block|graph)(\d+)$", f)
                                                          for f in args.forms.split(",")) if m])
     import awg_inputs as gi
-    Ball = gi.block_rhs(p, Kmax)
+    if p.b.ndim == 2 and p.b.shape[0] >= Kmax:  # a workload with its own right-hand sides
+        Ball = np.ascontiguousarray(p.b[:Kmax])
+    else:
+        Ball = gi.block_rhs(p, Kmax)
     bAll = torch.from_numpy(Ball).cuda()
     xAll = torch.zeros_like(bAll)
     g_its = torch.zeros(Kmax, dtype=torch.int32, device="cuda")
@@ -506,7 +531,7 @@ def run_awg(args):
         roofline["timed_in"] = [k for k, v in forms.items() if v is rform][0]
 
     # end to end: host buffers through the public API (H2D b, solve, D2H x)
-    hb = torch.from_numpy(np.ascontiguousarray(Ball[:best["nrhs"]]) if best["block"] else p.b).pin_memory()
+    hb = torch.from_numpy(np.ascontiguousarray(Ball[:best["nrhs"]]) if best["block"] else b1).pin_memory()
     hx = torch.empty_like(hb).pin_memory()
     db = torch.empty_like(hb, device="cuda")
     dx = torch.zeros_like(db)
@@ -546,7 +571,7 @@ def run_awg(args):
             "dtype": {FP64: "f64", MIXED_FP32: "f32+f64", MIXED_BF16: "bf16+f32+f64",
                       MIXED_FP16: "f16+f32+f64"}[best["prec"]],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD + (f"; batched form: {best['nrhs']} right-hand sides per block "
+            "config": {"workload": _workload(args.config, p) + (f"; batched form: {best['nrhs']} right-hand sides per block "
                                                "solve (column 0 the benchmark b, the rest seeded N(0,1)), "
                                                "each column its own PCG to 1e-8" if best["block"] else ""),
                        "form": best_name, "nrhs_per_step": best["nrhs"], "n": p.n, "nparts": p.nparts,
@@ -689,6 +714,68 @@ def train_start_network(seeds=(3, 4, 5), steps=400, lr=1e-2):
                 "seconds": round(time.perf_counter() - t0, 2)}
 
 
+def learned_start_eval(train_seeds=range(1000, 1200), test_seeds=range(2000, 2020), nex=96, steps=400, lr=1e-2):
+    """The learned start on the elasticity workload's generator: the network
+    is trained on the device on the eigenpairs that the setup itself finds
+    for 200 seeded coefficient draws (layer thicknesses from seeds
+    1000-1199; 96 x 96 elements in 4 x 4 node boxes, the subdomain size of
+    the 384 x 384 workload), then the GenEO block eigensolver runs on 20
+    held-out draws (seeds 2000-2019) from the learned start and from the
+    random start.  Reported: summed and largest solver steps, subdomains
+    sent to the dense eigensolver and GenEO stage time, per start, and
+    whether the mode counts agree (they must: both are certified)."""
+    import torch
+    import awg_inputs as gi
+    from paper_2106_10913_gb300 import (AWGSolver, LEARNED_NFEAT, MIXED_FP32, awg_learned_data,
+                                        awg_learned_train)
+    q = nex // 24
+    t0 = time.perf_counter()
+    Fs, ts = [], []
+    for sd in train_seeds:
+        pr = gi.config4(nex, nrhs=1, seed=sd, q=q)
+        sol = AWGSolver(pr.rowptr, pr.colidx, pr.val, pr.part, pr.nparts, pr.overlap, pr.tau, geneo_solver=1)
+        S = sol.info["sum_ns"]
+        F = torch.zeros((S, LEARNED_NFEAT), dtype=torch.float64, device="cuda")
+        t = torch.zeros(S, dtype=torch.float64, device="cuda")
+        awg_learned_data(sol.h, F, t)
+        torch.cuda.synchronize()
+        sol.close()
+        Fs.append(F)
+        ts.append(t)
+    data_s = time.perf_counter() - t0
+    F, t = torch.cat(Fs), torch.cat(ts)
+    rng = np.random.default_rng(0)
+    th0 = np.zeros(385)
+    o = 0
+    for fo, fi in ((16, 5), (16, 16), (1, 16)):
+        lim = np.sqrt(6.0 / (fi + fo))
+        th0[o:o + fo * fi] = rng.uniform(-lim, lim, fo * fi)
+        o += fo * fi + fo
+    t1 = time.perf_counter()
+    th, loss = awg_learned_train(F, t, th0, steps, lr, precision=MIXED_FP32)
+    train_s = time.perf_counter() - t1
+    res = {"random": {"steps_sum": 0, "steps_max": 0, "dense": 0, "geneo_ms": 0.0},
+           "learned": {"steps_sum": 0, "steps_max": 0, "dense": 0, "geneo_ms": 0.0}}
+    counts_agree = True
+    for sd in test_seeds:
+        pr = gi.config4(nex, nrhs=1, seed=sd, q=q)
+        modes = {}
+        for name, opts in (("random", {"geneo_solver": 1}), ("learned", {"geneo_solver": 2, "learned_params": th})):
+            sol = AWGSolver(pr.rowptr, pr.colidx, pr.val, pr.part, pr.nparts, pr.overlap, pr.tau, **opts)
+            r = res[name]
+            r["steps_sum"] += int(sol.info["geneo_its_sum"])
+            r["steps_max"] = max(r["steps_max"], int(sol.info["geneo_its_max"]))
+            r["dense"] += int(sol.info["geneo_dense"])
+            r["geneo_ms"] += float(sol.info["setup_ms"][3])
+            modes[name] = sol.array("modes").tolist()
+            sol.close()
+        counts_agree &= modes["random"] == modes["learned"]
+    return {"train": {"draws": len(list(train_seeds)), "samples": int(F.shape[0]), "adam_steps": steps,
+                      "loss_first": float(loss[0]), "loss_last": float(loss[-1]), "data_s": round(data_s, 1),
+                      "train_s": round(train_s, 2)},
+            "held_out_draws": len(list(test_seeds)), "mode_counts_agree": bool(counts_agree), **res}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -713,7 +800,12 @@ def main():
                     help="GenEO eigensolver of the setup: block solver from the learned start "
                          "(network trained on the device on smaller instances), from a random "
                          "start, or the dense eigensolver")
+    ap.add_argument("--learned-eval", action="store_true",
+                    help="only the learned-start evaluation on the elasticity generator (one JSON line)")
     args = ap.parse_args()
+    if args.learned_eval:
+        print(json.dumps({"learned_start_eval": learned_start_eval()}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
