@@ -620,10 +620,42 @@ def build_W(st: Setup) -> None:
         st.F = np.zeros((0, 0))
         st.F_cho = None
         return
-    st.W = solve_A_plus(st, st.Vhat.toarray())
-    F = st.W.T @ (st.A @ st.W)
+    if st.dense:
+        st.W = solve_A_plus(st, st.Vhat.toarray())
+    else:
+        st.W = _solve_A_plus_Vhat(st)
+    # F = W^T (A W), a block of columns of A W at a time (only one n x n_-
+    # array is held)
+    F = np.empty((st.n_minus, st.n_minus))
+    for j0 in range(0, st.n_minus, 512):
+        j1 = min(st.n_minus, j0 + 512)
+        F[:, j0:j1] = st.W.T @ (st.A @ st.W[:, j0:j1])
     st.F = 0.5 * (F + F.T)
     st.F_cho = sla.cho_factor(st.F, lower=True)
+
+
+def _solve_A_plus_Vhat(st: Setup) -> np.ndarray:
+    """W = A_+^-1 U for U = Vhat on a large problem, by the same Woodbury
+    form as solve_A_plus with rhs = U: X = A^-1 U, then
+    W = X - X (C^-1 + U^T X)^-1 U^T X, computed in place in X (the steps
+    and their order are those of solve_A_plus, in blocks of columns for the
+    solves and of rows for the update, so that only one n x n_- array is
+    held)."""
+    lu = st.info.get("A_lu")
+    if lu is None:
+        lu = spla.splu(st.A.tocsc())
+        st.info["A_lu"] = lu
+    U = st.Vhat.tocsc()
+    X = np.empty((st.n, st.n_minus), order="F")
+    for j0 in range(0, st.n_minus, 256):  # A^-1 U, a block of columns at a time
+        j1 = min(st.n_minus, j0 + 256)
+        X[:, j0:j1] = lu.solve(U[:, j0:j1].toarray())
+    cap = np.diag(1.0 / Lambda_strict(st)) + np.asarray(U.T @ X)
+    G = np.linalg.solve(cap, np.asarray(U.T @ X))
+    for i0 in range(0, st.n, 16384):  # X - X G, a block of rows at a time
+        i1 = min(st.n, i0 + 16384)
+        X[i0:i1] -= X[i0:i1] @ G
+    return X
 
 
 def build_W_pcg(st: Setup, rtol: float) -> Setup:
