@@ -336,13 +336,20 @@ enum {
     AWG_PROF_VECTOR = 7,     /* PCG vector updates and dot products       */
     AWG_NPROF = 8
 };
+/* Further awg_profile mask bits: AWG_PROF_SERIAL runs the apply's side-stream
+ * work (the W F^-1 W^T branch of H_3,ad / H_3,inex) in order on the main
+ * stream, so that event times are kernel times rather than times shared with
+ * concurrent kernels; AWG_PROF_COUNT (alone) counts launches, no events. */
+enum { AWG_PROF_SERIAL = 1 << 8, AWG_PROF_COUNT = 1 << 9 };
 
 /*
  * Profiling of the apply / PCG path, for benchmarks.  awg_profile(h, mask)
  * with mask != 0 resets and starts: every kernel the apply and PCG launch
  * is counted, and each launch of a kernel class k with bit (1 << k) set in
  * mask is bracketed by two CUDA events recorded on its own stream (up to a
- * pool of 65536 events).  awg_profile(h, 0) stops.
+ * pool of 65536 events); with AWG_PROF_SERIAL in mask the apply's two
+ * streams are serialised while profiling (see above).  awg_profile(h, 0)
+ * stops.
  * awg_profile_read synchronises the handle's last stream, and writes the
  * launch count to *h_launches and, per kernel class, the summed event time
  * (ms) and the number of timed launches to the HOST arrays h_ms[AWG_NPROF]

@@ -71,6 +71,9 @@ EXPORTED = ["awg_default_options", "awg_status_string", "awg_setup", "awg_destro
 LEARNED_NPARAM, LEARNED_NFEAT = 385, 5
 GENEO_DENSE, GENEO_BLOCK, GENEO_LEARNED = 0, 1, 2
 PROF_NAMES = ["spmv", "local", "wt", "wd", "coarse", "subdomain", "prolong", "vector"]
+# further awg_profile mask bits: serialise the apply's two streams while
+# profiling; count launches only
+PROF_SERIAL, PROF_COUNT = 1 << 8, 1 << 9
 
 _lib = None
 
@@ -334,7 +337,9 @@ def awg_learned_train(features, targets, params: np.ndarray, steps: int, lr: flo
 
 
 def awg_profile(h, mask: int):
-    """Start (mask = bit set of kernel classes to time, 0xFF all) or stop (0)."""
+    """Start (mask = bit set of kernel classes to time, 0xFF all; with
+    PROF_SERIAL the apply's side stream is folded into the main stream;
+    PROF_COUNT alone counts launches) or stop (0)."""
     _check(load_library().awg_profile(h, int(mask)), "awg_profile")
 
 

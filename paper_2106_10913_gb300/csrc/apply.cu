@@ -1087,13 +1087,14 @@ awg_status apply_stage(Handle* h, int which, int prec, const double* x, double* 
             if (h->n_minus == 0) return h2_1(h, prec, x, y, w, s);
             // W F^-1 W^T x on the side stream while H_2 x runs on s; the two
             // meet in the last kernel of H_2
+            const cudaStream_t side = side_stream(h, h->side, s);
             AWG_CUDA(cudaEventRecord(h->ev_fork, s));
-            AWG_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-            AWG_TRY(wt_r(h, prec, x, w.w0, w, h->side));
+            AWG_CUDA(cudaStreamWaitEvent(side, h->ev_fork, 0));
+            AWG_TRY(wt_r(h, prec, x, w.w0, w, side));
             AWG_TRY(dense_gemv(h, h->n_minus, (double*)h->prec[prec].Finv.p, w.w0, w.dd, 1.0, nullptr, 0,
-                               h->side));
-            AWG_TRY(w_d(h, prec, w.dd, nullptr, w.tmp2, w, h->side));
-            AWG_CUDA(cudaEventRecord(h->ev_join, h->side));
+                               side));
+            AWG_TRY(w_d(h, prec, w.dd, nullptr, w.tmp2, w, side));
+            AWG_CUDA(cudaEventRecord(h->ev_join, side));
             return h2_1(h, prec, x, y, w, s, w.tmp2, h->ev_join);
         }
         case 5: {  // H_3,hyb = Pi_3 H_2 Pi_3^T + W F^-1 W^T  (Def. 10)
@@ -1116,13 +1117,14 @@ awg_status apply_stage(Handle* h, int which, int prec, const double* x, double* 
         }
         case 6: {  // H_3,inex = H_2 + W (C^-1 - Vhat^T W)^-1 W^T  (Thm. 7)
             if (h->n_minus == 0) return h2_1(h, prec, x, y, w, s);
+            const cudaStream_t side = side_stream(h, h->side, s);
             AWG_CUDA(cudaEventRecord(h->ev_fork, s));
-            AWG_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-            AWG_TRY(wt_r(h, prec, x, w.w0, w, h->side));
+            AWG_CUDA(cudaStreamWaitEvent(side, h->ev_fork, 0));
+            AWG_TRY(wt_r(h, prec, x, w.w0, w, side));
             AWG_TRY(dense_gemv(h, h->n_minus, (double*)h->prec[prec].inexInv.p, w.w0, w.dd, 1.0, nullptr,
-                               0, h->side));
-            AWG_TRY(w_d(h, prec, w.dd, nullptr, w.tmp2, w, h->side));
-            AWG_CUDA(cudaEventRecord(h->ev_join, h->side));
+                               0, side));
+            AWG_TRY(w_d(h, prec, w.dd, nullptr, w.tmp2, w, side));
+            AWG_CUDA(cudaEventRecord(h->ev_join, side));
             return h2_1(h, prec, x, y, w, s, w.tmp2, h->ev_join);
         }
         default: return AWG_ERR_INVALID_ARG;

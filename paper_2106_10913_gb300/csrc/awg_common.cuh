@@ -228,6 +228,12 @@ struct NvtxRange {
     NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// The stream of an apply's side branch: `side`, or the main stream `s`
+// while a serialising profile (AWG_PROF_SERIAL) runs
+inline cudaStream_t side_stream(const Handle* h, cudaStream_t side, cudaStream_t s) {
+    return (h->prof & AWG_PROF_SERIAL) ? s : side;
+}
+
 struct ProfScope {
     Handle* h;
     int id;

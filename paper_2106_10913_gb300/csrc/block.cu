@@ -50,12 +50,45 @@ __device__ __forceinline__ void ldv(const double* p, double (&v)[2]) {
     const double2 t = *reinterpret_cast<const double2*>(p);
     v[0] = t.x; v[1] = t.y;
 }
+// float32 <-> float64 conversions on the integer pipes.  On this GPU a
+// conversion to or from float64 issues on the float64 pipes (about two
+// per clock per SM), which bound the PCG vector kernels of the mixed forms;
+// for normal numbers the conversion is a rearrangement of the IEEE 754
+// fields (sign; exponent rebiased by 1023 - 127 = 896; significand shifted
+// by 52 - 23 = 29 bits, rounded to nearest even on the way down), done here
+// with integer operations.  Zeros keep their sign; subnormals, infinities,
+// NaNs and float64 values outside the float32 normal range take the
+// hardware conversion.
+__device__ __forceinline__ double f2d(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xFFu;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)sign);
+    if (e == 0u || e == 0xFFu) return (double)f;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896u) << 52) |
+                                            ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+__device__ __forceinline__ float d2f(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    if ((b << 1) == 0ull) return __uint_as_float(sign);
+    const int e = (int)((b >> 52) & 0x7FF) - 896;
+    if (e < 1 || e > 254) return (float)d;
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull, rem = m & 0x1FFFFFFFull;
+    unsigned r = ((unsigned)e << 23) | (unsigned)(m >> 29);
+    r += (rem > 0x10000000ull || (rem == 0x10000000ull && (r & 1u))) ? 1u : 0u;  // may carry into inf
+    return __uint_as_float(r | sign);
+}
+template <typename TO, typename TI> __device__ __forceinline__ TO cvt(TI a) { return (TO)a; }
+template <> __device__ __forceinline__ double cvt<double, float>(float a) { return f2d(a); }
+template <> __device__ __forceinline__ float cvt<float, double>(double a) { return d2f(a); }
+
 // two consecutive values of a float64 row kernel's columns, from float64 or
 // float32 storage
 __device__ __forceinline__ void ld2(const double* p, double (&v)[2]) { ldv(p, v); }
 __device__ __forceinline__ void ld2(const float* p, double (&v)[2]) {
     const float2 t = *reinterpret_cast<const float2*>(p);
-    v[0] = t.x; v[1] = t.y;
+    v[0] = f2d(t.x); v[1] = f2d(t.y);
 }
 __device__ __forceinline__ void stv(float* p, const float (&v)[4]) {
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
@@ -91,22 +124,20 @@ __device__ __forceinline__ void colsum_grid(const double (&acc)[2], double* part
     __threadfence();
     // the last block adds the block partials with all its threads: thread t
     // takes column t % K and every Q-th block from t / K (Q = 256 / K), in
-    // block order with four independent sums (the loads stay in flight);
+    // block order with eight independent sums (the loads stay in flight);
     // the Q sums of a column then meet in a fixed order
     constexpr int Q = 256 / K;
     __shared__ double qs[Q][K];
     {
         const int c = threadIdx.x % K, q = threadIdx.x / K;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         int b = q;
-        for (; b + 3 * Q < (int)gridDim.x; b += 4 * Q) {
-            a0 += __ldcg(part + (size_t)b * K + c);
-            a1 += __ldcg(part + (size_t)(b + Q) * K + c);
-            a2 += __ldcg(part + (size_t)(b + 2 * Q) * K + c);
-            a3 += __ldcg(part + (size_t)(b + 3 * Q) * K + c);
+        for (; b + 7 * Q < (int)gridDim.x; b += 8 * Q) {
+#pragma unroll
+            for (int u = 0; u < 8; u++) a[u] += __ldcg(part + (size_t)(b + u * Q) * K + c);
         }
-        for (; b < (int)gridDim.x; b += Q) a0 += __ldcg(part + (size_t)b * K + c);
-        qs[q][c] = (a0 + a1) + (a2 + a3);
+        for (; b < (int)gridDim.x; b += Q) a[0] += __ldcg(part + (size_t)b * K + c);
+        qs[q][c] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
     }
     __syncthreads();
     if (threadIdx.x < K) {
@@ -231,7 +262,7 @@ __global__ void __launch_bounds__(256) kb_pcg_xr(int n, double* sc, const double
         }
         stv(X + e, x);
         stv(R + e, r);
-        if (R32) *reinterpret_cast<float2*>(R32 + e) = make_float2((float)r[0], (float)r[1]);
+        if (R32) *reinterpret_cast<float2*>(R32 + e) = make_float2(d2f(r[0]), d2f(r[1]));
     }
     colsum_grid<K>(acc, part, cnt, sc + B_RR * K);
 }
@@ -366,7 +397,7 @@ __global__ void kb_add(size_t len, const T* __restrict__ a, T* y) {
 template <typename TI, typename TO>
 __global__ void kb_cvt(size_t len, const TI* __restrict__ a, TO* __restrict__ b) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < len) b[e] = (TO)a[e];
+    if (e < len) b[e] = cvt<TO>(a[e]);
 }
 
 // ------------------------------------------------------ preconditioner ops
@@ -562,6 +593,92 @@ __global__ void __launch_bounds__(256) kb_tgemv2(const int* __restrict__ sub_ptr
             const int jj = jb + u;
             if (jj < jn) part[((size_t)rs * ncol_total + c0 + j0 + jj) * K + c] = acc[u];
         }
+    }
+}
+
+// Float32 form of the same products, as register-tiled FMA work: block
+// (s, ps) takes the local rows of split ps in chunks of 64 (X rows gathered
+// whole, B_s rows transposed, both in shared memory) and the columns q in
+// chunks of 16; thread (cq, rl) of the 4K threads owns the 16 q x 4 columns
+// 4 cq .. 4 cq + 3 of the rows p = rl (mod 16) of each chunk, 64
+// accumulators fed by one 16-byte shared load of X and four of B_s per 64
+// FMAs.  The 16 row lanes of a warp half then meet in a fixed butterfly
+// (each step halves the q range a lane keeps; lane rl ends with q = rl).
+constexpr int TG3_ROWS = 64, TG3_JP = 16;
+template <int K>
+__global__ void __launch_bounds__(4 * K) kb_tgemv3(const int* __restrict__ sub_ptr, const int* __restrict__ sub_idx,
+                                                   const int* __restrict__ colptr, const int64_t* __restrict__ boff,
+                                                   const float* __restrict__ B, const float* __restrict__ X,
+                                                   int ncol_total, float* __restrict__ part) {
+    constexpr int NT = 4 * K, CQ = K / 4;
+    __shared__ __align__(16) float xs[TG3_ROWS][K + 4];
+    __shared__ __align__(16) float bs[TG3_ROWS][TG3_JP + 4];
+    const int s = blockIdx.x, rs = blockIdx.y;
+    const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
+    const int c0 = colptr[s], nc = colptr[s + 1] - c0;
+    if (nc == 0) return;
+    const int plen = (m + gridDim.y - 1) / gridDim.y;
+    const int pa = rs * plen, pb = min(m, pa + plen);
+    const int lane = threadIdx.x & 31;
+    const int cq = 2 * (threadIdx.x >> 5) + (lane >> 4), rl = lane & 15;
+    const float* Bs = B + boff[s];
+    for (int j0 = 0; j0 < nc; j0 += TG3_JP) {
+        const int jn = min(TG3_JP, nc - j0);
+        float acc[TG3_JP][4];
+#pragma unroll
+        for (int j = 0; j < TG3_JP; j++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[j][c] = 0.f;
+        for (int q0 = pa; q0 < pb; q0 += TG3_ROWS) {
+            const int pn = min(TG3_ROWS, pb - q0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < TG3_JP * TG3_ROWS; e += NT) {
+                const int jj = e / TG3_ROWS, pp = e % TG3_ROWS;
+                bs[pp][jj] = (jj < jn && pp < pn) ? Bs[(size_t)(j0 + jj) * m + q0 + pp] : 0.f;
+            }
+            for (int e = threadIdx.x; e < TG3_ROWS * CQ; e += NT) {
+                const int pp = e / CQ, cc = e % CQ;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (pp < pn) v = reinterpret_cast<const float4*>(X + (size_t)sub_idx[p0 + q0 + pp] * K)[cc];
+                *reinterpret_cast<float4*>(&xs[pp][4 * cc]) = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < TG3_ROWS / 16; r++) {
+                const int pp = 16 * r + rl;
+                const float4 x = *reinterpret_cast<const float4*>(&xs[pp][4 * cq]);
+#pragma unroll
+                for (int j4 = 0; j4 < TG3_JP / 4; j4++) {
+                    const float4 b = *reinterpret_cast<const float4*>(&bs[pp][4 * j4]);
+                    const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        acc[4 * j4 + u][0] = fmaf(bv[u], x.x, acc[4 * j4 + u][0]);
+                        acc[4 * j4 + u][1] = fmaf(bv[u], x.y, acc[4 * j4 + u][1]);
+                        acc[4 * j4 + u][2] = fmaf(bv[u], x.z, acc[4 * j4 + u][2]);
+                        acc[4 * j4 + u][3] = fmaf(bv[u], x.w, acc[4 * j4 + u][3]);
+                    }
+                }
+            }
+        }
+        // butterfly over the 16 row lanes: at step h the lanes with bit h of
+        // rl set keep the upper half of their q range, the others the lower,
+        // and each adds what its partner sends of the half it keeps
+#pragma unroll
+        for (int h = 8; h >= 1; h >>= 1) {
+            const bool up = (rl & h) != 0;
+#pragma unroll
+            for (int j = 0; j < h; j++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const float send = up ? acc[j][c] : acc[j + h][c];
+                    const float keep = up ? acc[j + h][c] : acc[j][c];
+                    acc[j][c] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+                }
+        }
+        if (rl < jn)
+            *reinterpret_cast<float4*>(part + ((size_t)rs * ncol_total + c0 + j0 + rl) * K + 4 * cq) =
+                make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
     }
 }
 
@@ -1416,6 +1533,14 @@ int resident_blocks(const void* kern) {
 unsigned grid_for(const void* kern, int n, int rpb) {
     return (unsigned)std::max(1, std::min((n + rpb - 1) / rpb, 152 * resident_blocks(kern)));
 }
+// Grid of the PCG kernels that end in a column sum over the grid
+// (colsum_grid): two blocks per SM, so that the last block adds few
+// partials per column, and each thread keeps four rows of loads in flight,
+// enough to cover the HBM latency at 16 warps per SM
+constexpr int DOT_BPS = 2;
+unsigned grid_dot(const void* kern, int n, int rpb) {
+    return (unsigned)std::max(1, std::min((n + rpb - 1) / rpb, 152 * std::min(DOT_BPS, resident_blocks(kern))));
+}
 
 }  // namespace
 
@@ -1590,8 +1715,12 @@ struct BlockApply {
                      const T* w, T wsign, T* C, cudaStream_t s) {
         if (maxc == 0 || ncol_total == 0) return AWG_OK;
         ProfScope ps_(h, AWG_PROF_SUBDOMAIN, s);
-        kb_tgemv2<T, K><<<dim3(h->N, TG_PS), 256, 0, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p, colptr, boff, B, X,
-                                                          ncol_total, v.tgp);
+        if constexpr (std::is_same<T, float>::value)
+            kb_tgemv3<K><<<dim3(h->N, TG_PS), 4 * K, 0, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p, colptr, boff, B,
+                                                             X, ncol_total, v.tgp);
+        else
+            kb_tgemv2<T, K><<<dim3(h->N, TG_PS), 256, 0, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p, colptr, boff,
+                                                              B, X, ncol_total, v.tgp);
         AWG_LAUNCH();
         const size_t len = (size_t)ncol_total * K;
         kb_tg_sum<T, K><<<(unsigned)((len + 255) / 256), 256, 0, s>>>(ncol_total, v.tgp, w, wsign, C);
@@ -1924,18 +2053,19 @@ struct BlockApply {
             case 6: {  // H_3,inex = H_2 + W (C^-1 - Vhat^T W)^-1 W^T (Thm. 7)
                 if (h->n_minus == 0) return h2(prec, X, Y, s);
                 const double* coarse = (double*)(which == 4 ? h->prec[prec].Finv.p : h->prec[prec].inexInv.p);
+                const cudaStream_t side = side_stream(h, sl.side, s);
                 AWG_CUDA(cudaEventRecord(sl.fork, s));
-                AWG_CUDA(cudaStreamWaitEvent(sl.side, sl.fork, 0));
+                AWG_CUDA(cudaStreamWaitEvent(side, sl.fork, 0));
                 // side stream: W^T X (HBM) beside the first E^-1 (FP64 pipes),
                 // then the second coarse solve (FP64) after it, beside the
                 // local solves (FP32), and W d beside the second E^-1
-                AWG_TRY(wt(prec, X, v.w0, sl.side));
+                AWG_TRY(wt(prec, X, v.w0, side));
                 AWG_TRY(h2a(X, s));
                 AWG_CUDA(cudaEventRecord(sl.mid, s));
-                AWG_CUDA(cudaStreamWaitEvent(sl.side, sl.mid, 0));
-                AWG_TRY(dense(h->n_minus, coarse, v.w0, v.dd, 1.0, nullptr, 0.0, v.dps, sl.side));
-                AWG_TRY(wd(prec, v.dd, v.tmpw, nullptr, sl.side));
-                AWG_CUDA(cudaEventRecord(sl.join, sl.side));
+                AWG_CUDA(cudaStreamWaitEvent(side, sl.mid, 0));
+                AWG_TRY(dense(h->n_minus, coarse, v.w0, v.dd, 1.0, nullptr, 0.0, v.dps, side));
+                AWG_TRY(wd(prec, v.dd, v.tmpw, nullptr, side));
+                AWG_CUDA(cudaEventRecord(sl.join, side));
                 return h2b(prec, X, Y, s, v.tmpw, sl.join);
             }
             case 5: {  // H_3,hyb = Pi_3 H_2 Pi_3^T + W F^-1 W^T (Def. 10), in order on s
@@ -2107,7 +2237,7 @@ struct PcgSteps {
     cudaStream_t s;
     const Slot& sl;
 
-    unsigned g(const void* kern) const { return grid_for(kern, h->n, RM<double, K>::RPB); }
+    unsigned g(const void* kern) const { return grid_dot(kern, h->n, RM<double, K>::RPB); }
     float* r32() const { return (float*)v.rin; }
     float* z32() const { return (float*)v.out; }
 

@@ -159,39 +159,68 @@ __device__ __forceinline__ int oz_colexp(unsigned long long bits) {
     return bits ? (int)((bits >> 52) & 0x7FF) - 1021 : 0;
 }
 
+// round(x 2^(56 - f)) for |x| < 2^(f - 1), from the bits of x alone
+// (integer pipes; round half to even, as a float64 rounding would):
+// x = m 2^(ex - 1075) with the 53-bit significand m (ex the biased exponent,
+// 1 for subnormals), so the value is m shifted left by sh = ex - 1019 - f
+// (sh <= 2 since |x| < 2^(f - 1)), rounded where sh < 0.  Inf and NaN only
+// occur in columns flagged by f > 1025, whose results are replaced by NaN.
+__device__ __forceinline__ long long oz_fixed(double x, int f) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    if (ex == 0x7FF) return 0;
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (ex ? 0x10000000000000ull : 0ull);
+    const int sh = (ex ? ex : 1) - 1019 - f;
+    unsigned long long v;
+    if (sh >= 0) {
+        v = m << sh;
+    } else if (sh > -64) {
+        const int r = -sh;
+        const unsigned long long q = m >> r, rem = m & ((1ull << r) - 1ull), half = 1ull << (r - 1);
+        v = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+    } else {
+        v = 0;
+    }
+    return (b >> 63) ? -(long long)v : (long long)v;
+}
+
 // Column slices of X: p[(t K + c) ldk + j] = digit t of X(j, c) 2^-f_c
 // (zero for j >= dim), fx[c] = f_c.  The value is rounded once to
 // v = round(X 2^(56 - f)), |v| <= 2^55, and cut into eight balanced 7-bit
 // digits by integer shifts, most significant first: d = floor((v + 2^(w-1))
 // / 2^w), v -= d 2^w for w = 49, 42, ..., 7, then the last digit is v itself
-// (each |d| <= 64).  One block per 64 rows; a 64 x K tile of X is staged in
-// shared memory so that reads and writes are coalesced.
+// (each |d| <= 64).  One block per 16 rows (a 16 x K tile of X staged in
+// shared memory, so that reads run along the columns and writes along the
+// rows of the slices); all of it integer work.
+constexpr int OZ_XS_ROWS = 16;
 template <int K>
 __global__ void __launch_bounds__(256) k_oz_xslice(int dim, int ldk, const double* __restrict__ X,
                                                    const unsigned long long* __restrict__ mx,
                                                    __nv_bfloat16* __restrict__ p, int* __restrict__ fx) {
-    __shared__ double xs[64][K + 1];
-    const int j0 = blockIdx.x * 64;
-    for (int e = threadIdx.x; e < 64 * K; e += blockDim.x) {
+    __shared__ double xs[OZ_XS_ROWS][K + 1];
+    __shared__ int fs[K];
+    const int j0 = blockIdx.x * OZ_XS_ROWS;
+    for (int e = threadIdx.x; e < OZ_XS_ROWS * K; e += blockDim.x) {
         const int jj = e / K, c = e % K, j = j0 + jj;
         xs[jj][c] = j < dim ? X[(size_t)j * K + c] : 0.0;
     }
-    if (blockIdx.x == 0)
-        for (int c = threadIdx.x; c < K; c += blockDim.x) fx[c] = oz_colexp(mx[c]);
+    for (int c = threadIdx.x; c < K; c += blockDim.x) {
+        fs[c] = oz_colexp(mx[c]);
+        if (blockIdx.x == 0) fx[c] = fs[c];
+    }
     __syncthreads();
-    for (int e = threadIdx.x; e < 64 * K; e += blockDim.x) {
-        const int c = e / 64, jj = e % 64;
-        const int f = oz_colexp(mx[c]);
-        long long v = __double2ll_rn(ldexp(xs[jj][c], 56 - f));
+    for (int e = threadIdx.x; e < OZ_XS_ROWS * K; e += blockDim.x) {
+        const int c = e / OZ_XS_ROWS, jj = e % OZ_XS_ROWS;
+        long long v = oz_fixed(xs[jj][c], fs[c]);
         __nv_bfloat16* out = p + (size_t)c * ldk + j0 + jj;
 #pragma unroll
         for (int t = 0; t < OZ_SLICES - 1; t++) {
             const int w = OZ_BITS * (OZ_SLICES - 1 - t);
             const long long d = (v + (1ll << (w - 1))) >> w;
             v -= d << w;
-            out[(size_t)t * K * ldk] = __float2bfloat16_rn((float)d);
+            out[(size_t)t * K * ldk] = __float2bfloat16_rn((float)(int)d);  // |d| <= 64
         }
-        out[(size_t)(OZ_SLICES - 1) * K * ldk] = __float2bfloat16_rn((float)v);
+        out[(size_t)(OZ_SLICES - 1) * K * ldk] = __float2bfloat16_rn((float)(int)v);
     }
 }
 
@@ -368,7 +397,7 @@ awg_status launch_oz(const OzMat& m, const double* X, double* Y, double alpha, c
     AWG_CUDA(cudaMemsetAsync(mx, 0, K * sizeof(unsigned long long), s));
     k_oz_colmax<K><<<std::min(152, (m.dim * K + 255) / 256), 256, 0, s>>>(m.dim, X, mx);
     AWG_LAUNCH();
-    k_oz_xslice<K><<<ldk / 64, 256, 0, s>>>(m.dim, ldk, X, mx, p, fx);
+    k_oz_xslice<K><<<ldk / OZ_XS_ROWS, 256, 0, s>>>(m.dim, ldk, X, mx, p, fx);
     AWG_LAUNCH();
     CUtensorMap tq, tp;
     if (!make_map(&tq, m.q, 1, (uint64_t)OZ_SLICES * m.dimp, ldk, ldk, OZ_BK, OZ_BM) ||

@@ -367,3 +367,39 @@ def test_block_pcg_async_two_groups(pair):
         assert abs(int(its[c].item()) - its_s[c]) <= 1
         assert float(rel[c].item()) <= 1e-8
         assert np.linalg.norm(st.A @ X[c] - B[c]) <= 1e-8 * np.linalg.norm(B[c]) * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("nrhs", [1, 40])
+def test_profile_modes(nrhs):
+    """awg_profile: with PROF_COUNT alone the solve's launches are counted and
+    no kernel class is timed; with every class and PROF_SERIAL each class of
+    the H_3,ad solve is timed, and the solve (its side branch run in order on
+    the main stream) gives the same x, bit for bit, as the unprofiled one."""
+    from paper_2106_10913_gb300 import (MIXED_FP16, PROF_COUNT, PROF_SERIAL, awg_pcg, awg_pcg_block,
+                                        awg_profile, awg_profile_read)
+    p, sol, st = _pair("channels64")
+    B = gi.block_rhs(p, nrhs)
+    b = torch.from_numpy(np.ascontiguousarray(B if nrhs > 1 else B[0])).cuda()
+
+    def solve():
+        x = torch.zeros_like(b)
+        if nrhs > 1:
+            awg_pcg_block(sol.h, b, x, 1e-8, MIXED_FP16)
+        else:
+            awg_pcg(sol.h, b, x, 1e-8, MIXED_FP16)
+        torch.cuda.synchronize()
+        return x
+
+    x0 = solve()
+    awg_profile(sol.h, PROF_COUNT)
+    x1 = solve()
+    pc = awg_profile_read(sol.h)
+    awg_profile(sol.h, 0xFF | PROF_SERIAL)
+    x2 = solve()
+    ps = awg_profile_read(sol.h)
+    awg_profile(sol.h, 0)
+    assert pc["launches"] > 0 and all(v == 0 for v in pc["count"].values())
+    assert ps["launches"] == pc["launches"]
+    for k in ("spmv", "local", "wt", "wd", "coarse", "subdomain", "prolong", "vector"):
+        assert ps["count"][k] > 0 and ps["ms"][k] > 0.0, k
+    assert torch.equal(x0, x1) and torch.equal(x0, x2)
