@@ -97,10 +97,46 @@ __device__ __forceinline__ void stv(double* p, const double (&v)[2]) {
     *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
 }
 
+// Column sums of `count` partial rows src[b * K + c] (b in order, read
+// through L2) into dst[c], by all 256 threads of the block: thread t takes
+// column t % K and every Q-th row from t / K (Q = 256 / K) with eight
+// independent sums (the loads stay in flight), then the Q sums of a column
+// meet in a fixed order
+template <int K>
+__device__ __forceinline__ void sum_partials(const double* src, int count, double* dst) {
+    constexpr int Q = 256 / K;
+    __shared__ double qs[Q][K];
+    __syncthreads();
+    {
+        const int c = threadIdx.x % K, q = threadIdx.x / K;
+        double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        int b = q;
+        for (; b + 7 * Q < count; b += 8 * Q) {
+#pragma unroll
+            for (int u = 0; u < 8; u++) a[u] += __ldcg(src + (size_t)(b + u * Q) * K + c);
+        }
+        for (; b < count; b += Q) a[0] += __ldcg(src + (size_t)b * K + c);
+        qs[q][c] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < Q; q++) v += qs[q][threadIdx.x];
+        dst[threadIdx.x] = v;
+    }
+}
+
 // Per-column sums of a 256-thread block of float64 row kernels (thread
-// partials acc[j] belong to column c0 + j), then over the grid: block
-// partials go to part[b * K + c] and the last block to arrive (ticket) adds
-// them in block order.  Deterministic for a given grid.
+// partials acc[j] belong to column c0 + j), then over the grid in two
+// levels: block partials go to part[b * K + c]; the last block to arrive
+// of each group of CS_G blocks (ticket cnt[1 + g]) adds the group's
+// partials in block order into part[(CS_PMAX + g) * K + c], and the last
+// group to finish (ticket cnt[0]) adds the group sums in group order.  Two
+// short rounds of L2 loads instead of one block reading every partial;
+// deterministic for a given grid (at most CS_PMAX blocks).  The counters
+// return to zero.
+constexpr int CS_G = 128, CS_PMAX = 1216;
 template <int K>
 __device__ __forceinline__ void colsum_grid(const double (&acc)[2], double* part, unsigned* cnt, double* out) {
     using M = RM<double, K>;
@@ -118,35 +154,24 @@ __device__ __forceinline__ void colsum_grid(const double (&acc)[2], double* part
     }
     __threadfence();
     __syncthreads();
+    const int g = blockIdx.x / CS_G, g0 = g * CS_G;
+    const int gn = min(CS_G, (int)gridDim.x - g0), ng = ((int)gridDim.x + CS_G - 1) / CS_G;
+    if (threadIdx.x == 0) ticket = atomicAdd(cnt + 1 + g, 1u);
+    __syncthreads();
+    if (ticket != (unsigned)gn - 1u) return;
+    __threadfence();
+    double* gp = part + (size_t)CS_PMAX * K;
+    sum_partials<K>(part + (size_t)g0 * K, gn, ng == 1 ? out : gp + (size_t)g * K);
+    if (threadIdx.x == 0) cnt[1 + g] = 0u;
+    if (ng == 1) return;
+    __threadfence();
+    __syncthreads();
     if (threadIdx.x == 0) ticket = atomicAdd(cnt, 1u);
     __syncthreads();
-    if (ticket != gridDim.x - 1) return;
+    if (ticket != (unsigned)ng - 1u) return;
     __threadfence();
-    // the last block adds the block partials with all its threads: thread t
-    // takes column t % K and every Q-th block from t / K (Q = 256 / K), in
-    // block order with eight independent sums (the loads stay in flight);
-    // the Q sums of a column then meet in a fixed order
-    constexpr int Q = 256 / K;
-    __shared__ double qs[Q][K];
-    {
-        const int c = threadIdx.x % K, q = threadIdx.x / K;
-        double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        int b = q;
-        for (; b + 7 * Q < (int)gridDim.x; b += 8 * Q) {
-#pragma unroll
-            for (int u = 0; u < 8; u++) a[u] += __ldcg(part + (size_t)(b + u * Q) * K + c);
-        }
-        for (; b < (int)gridDim.x; b += Q) a[0] += __ldcg(part + (size_t)b * K + c);
-        qs[q][c] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-    }
-    __syncthreads();
-    if (threadIdx.x < K) {
-        double v = 0.0;
-#pragma unroll
-        for (int q = 0; q < Q; q++) v += qs[q][threadIdx.x];
-        out[threadIdx.x] = v;
-    }
-    if (threadIdx.x == 0) *cnt = 0u;
+    sum_partials<K>(gp, ng, out);
+    if (threadIdx.x == 0) cnt[0] = 0u;
 }
 
 // (unrolled by 4: the loads of four rows are in flight together)
@@ -593,92 +618,6 @@ __global__ void __launch_bounds__(256) kb_tgemv2(const int* __restrict__ sub_ptr
             const int jj = jb + u;
             if (jj < jn) part[((size_t)rs * ncol_total + c0 + j0 + jj) * K + c] = acc[u];
         }
-    }
-}
-
-// Float32 form of the same products, as register-tiled FMA work: block
-// (s, ps) takes the local rows of split ps in chunks of 64 (X rows gathered
-// whole, B_s rows transposed, both in shared memory) and the columns q in
-// chunks of 16; thread (cq, rl) of the 4K threads owns the 16 q x 4 columns
-// 4 cq .. 4 cq + 3 of the rows p = rl (mod 16) of each chunk, 64
-// accumulators fed by one 16-byte shared load of X and four of B_s per 64
-// FMAs.  The 16 row lanes of a warp half then meet in a fixed butterfly
-// (each step halves the q range a lane keeps; lane rl ends with q = rl).
-constexpr int TG3_ROWS = 64, TG3_JP = 16;
-template <int K>
-__global__ void __launch_bounds__(4 * K) kb_tgemv3(const int* __restrict__ sub_ptr, const int* __restrict__ sub_idx,
-                                                   const int* __restrict__ colptr, const int64_t* __restrict__ boff,
-                                                   const float* __restrict__ B, const float* __restrict__ X,
-                                                   int ncol_total, float* __restrict__ part) {
-    constexpr int NT = 4 * K, CQ = K / 4;
-    __shared__ __align__(16) float xs[TG3_ROWS][K + 4];
-    __shared__ __align__(16) float bs[TG3_ROWS][TG3_JP + 4];
-    const int s = blockIdx.x, rs = blockIdx.y;
-    const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
-    const int c0 = colptr[s], nc = colptr[s + 1] - c0;
-    if (nc == 0) return;
-    const int plen = (m + gridDim.y - 1) / gridDim.y;
-    const int pa = rs * plen, pb = min(m, pa + plen);
-    const int lane = threadIdx.x & 31;
-    const int cq = 2 * (threadIdx.x >> 5) + (lane >> 4), rl = lane & 15;
-    const float* Bs = B + boff[s];
-    for (int j0 = 0; j0 < nc; j0 += TG3_JP) {
-        const int jn = min(TG3_JP, nc - j0);
-        float acc[TG3_JP][4];
-#pragma unroll
-        for (int j = 0; j < TG3_JP; j++)
-#pragma unroll
-            for (int c = 0; c < 4; c++) acc[j][c] = 0.f;
-        for (int q0 = pa; q0 < pb; q0 += TG3_ROWS) {
-            const int pn = min(TG3_ROWS, pb - q0);
-            __syncthreads();
-            for (int e = threadIdx.x; e < TG3_JP * TG3_ROWS; e += NT) {
-                const int jj = e / TG3_ROWS, pp = e % TG3_ROWS;
-                bs[pp][jj] = (jj < jn && pp < pn) ? Bs[(size_t)(j0 + jj) * m + q0 + pp] : 0.f;
-            }
-            for (int e = threadIdx.x; e < TG3_ROWS * CQ; e += NT) {
-                const int pp = e / CQ, cc = e % CQ;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (pp < pn) v = reinterpret_cast<const float4*>(X + (size_t)sub_idx[p0 + q0 + pp] * K)[cc];
-                *reinterpret_cast<float4*>(&xs[pp][4 * cc]) = v;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int r = 0; r < TG3_ROWS / 16; r++) {
-                const int pp = 16 * r + rl;
-                const float4 x = *reinterpret_cast<const float4*>(&xs[pp][4 * cq]);
-#pragma unroll
-                for (int j4 = 0; j4 < TG3_JP / 4; j4++) {
-                    const float4 b = *reinterpret_cast<const float4*>(&bs[pp][4 * j4]);
-                    const float bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-                    for (int u = 0; u < 4; u++) {
-                        acc[4 * j4 + u][0] = fmaf(bv[u], x.x, acc[4 * j4 + u][0]);
-                        acc[4 * j4 + u][1] = fmaf(bv[u], x.y, acc[4 * j4 + u][1]);
-                        acc[4 * j4 + u][2] = fmaf(bv[u], x.z, acc[4 * j4 + u][2]);
-                        acc[4 * j4 + u][3] = fmaf(bv[u], x.w, acc[4 * j4 + u][3]);
-                    }
-                }
-            }
-        }
-        // butterfly over the 16 row lanes: at step h the lanes with bit h of
-        // rl set keep the upper half of their q range, the others the lower,
-        // and each adds what its partner sends of the half it keeps
-#pragma unroll
-        for (int h = 8; h >= 1; h >>= 1) {
-            const bool up = (rl & h) != 0;
-#pragma unroll
-            for (int j = 0; j < h; j++)
-#pragma unroll
-                for (int c = 0; c < 4; c++) {
-                    const float send = up ? acc[j][c] : acc[j + h][c];
-                    const float keep = up ? acc[j + h][c] : acc[j][c];
-                    acc[j][c] = keep + __shfl_xor_sync(0xffffffffu, send, h);
-                }
-        }
-        if (rl < jn)
-            *reinterpret_cast<float4*>(part + ((size_t)rs * ncol_total + c0 + j0 + rl) * K + 4 * cq) =
-                make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
     }
 }
 
@@ -1480,8 +1419,8 @@ size_t carve_block(const Handle* h, char* base, BView<double>* vd, BView<float>*
     d.pb = (double*)take(n * K * 8); d.px = (double*)take(n * K * 8); d.pr = (double*)take(n * K * 8);
     d.pp = (double*)take(n * K * 8); d.pq = (double*)take(n * K * 8); d.pz = (double*)take(n * K * 8);
     d.sc = (double*)take(B_NSC * K * 8);
-    d.red = (double*)take((size_t)1216 * K * 8);
-    d.cnt = (unsigned*)take(64);
+    d.red = (double*)take((size_t)(CS_PMAX + 64) * K * 8);  // block partials, then group sums
+    d.cnt = (unsigned*)take(256);                              // colsum_grid tickets (global, per group)
     d.ctl = (double*)take(8 * 8);
     d.gits = (int*)take(K * 4);
     d.grel = (double*)take(K * 8);
@@ -1532,14 +1471,6 @@ int resident_blocks(const void* kern) {
 // 8 blocks per SM for a kernel that keeps 6 resident would run 1.33 waves)
 unsigned grid_for(const void* kern, int n, int rpb) {
     return (unsigned)std::max(1, std::min((n + rpb - 1) / rpb, 152 * resident_blocks(kern)));
-}
-// Grid of the PCG kernels that end in a column sum over the grid
-// (colsum_grid): two blocks per SM, so that the last block adds few
-// partials per column, and each thread keeps four rows of loads in flight,
-// enough to cover the HBM latency at 16 warps per SM
-constexpr int DOT_BPS = 2;
-unsigned grid_dot(const void* kern, int n, int rpb) {
-    return (unsigned)std::max(1, std::min((n + rpb - 1) / rpb, 152 * std::min(DOT_BPS, resident_blocks(kern))));
 }
 
 }  // namespace
@@ -1715,12 +1646,8 @@ struct BlockApply {
                      const T* w, T wsign, T* C, cudaStream_t s) {
         if (maxc == 0 || ncol_total == 0) return AWG_OK;
         ProfScope ps_(h, AWG_PROF_SUBDOMAIN, s);
-        if constexpr (std::is_same<T, float>::value)
-            kb_tgemv3<K><<<dim3(h->N, TG_PS), 4 * K, 0, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p, colptr, boff, B,
-                                                             X, ncol_total, v.tgp);
-        else
-            kb_tgemv2<T, K><<<dim3(h->N, TG_PS), 256, 0, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p, colptr, boff,
-                                                              B, X, ncol_total, v.tgp);
+        kb_tgemv2<T, K><<<dim3(h->N, TG_PS), 256, 0, s>>>((int*)h->sub_ptr.p, (int*)h->sub_idx.p, colptr, boff, B, X,
+                                                          ncol_total, v.tgp);
         AWG_LAUNCH();
         const size_t len = (size_t)ncol_total * K;
         kb_tg_sum<T, K><<<(unsigned)((len + 255) / 256), 256, 0, s>>>(ncol_total, v.tgp, w, wsign, C);
@@ -2237,7 +2164,7 @@ struct PcgSteps {
     cudaStream_t s;
     const Slot& sl;
 
-    unsigned g(const void* kern) const { return grid_dot(kern, h->n, RM<double, K>::RPB); }
+    unsigned g(const void* kern) const { return grid_for(kern, h->n, RM<double, K>::RPB); }
     float* r32() const { return (float*)v.rin; }
     float* z32() const { return (float*)v.out; }
 
