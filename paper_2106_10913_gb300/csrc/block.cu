@@ -1888,9 +1888,9 @@ struct BlockApply {
     static constexpr int kidx = K == 16 ? 0 : (K == 32 ? 1 : 2);
 
     int wt_splits() const {
-        // (autotuned) CTAs per SM over the 128-column tiles of W; default 2
+        // (autotuned) CTAs per SM over the 256-column tiles of W; default 2
         const int per_sm = h->bt_wt[kidx] > 0 ? h->bt_wt[kidx] : 2;
-        const int tiles = (h->ldw + 127) / 128;
+        const int tiles = (h->ldw + 255) / 256;
         return umma_wt_splits(h->n, std::max(1, std::min(WT_SPLITS_MAX, (per_sm * 152 + tiles - 1) / tiles)));
     }
 

@@ -6,10 +6,11 @@
 // W; on the CUDA cores their K FMAs per element of W would bound them
 // instead.
 //
-// Both kernels: one CTA per 128-row tile of the product (M = 128), the K
-// right-hand sides as N, the reduction in 64-deep chunks.  W tiles and the
-// right-hand-side tiles come through TMA (cp.async.bulk.tensor, 128-byte
-// swizzle) into a 4-stage shared-memory ring guarded by mbarriers; one
+// Both kernels: one CTA per 256-row tile of the product (two M = 128
+// accumulators), the K right-hand sides as N, the reduction in 64-deep
+// chunks.  W tiles and the right-hand-side tiles come through TMA
+// (cp.async.bulk.tensor, 128-byte swizzle) into a shared-memory ring
+// guarded by mbarriers; one
 // thread issues tcgen05.mma (kind::f16, float32 accumulation in tensor
 // memory); the four warps read the accumulator back with tcgen05.ld.  The
 // right-hand sides enter as two 16-bit parts (high and low: about 22
@@ -36,15 +37,15 @@ constexpr int UM_BM = 128;     // rows of the product per CTA (MMA M)
 constexpr int UM_BK = 64;      // reduction depth per stage (128 bytes of 16-bit)
 constexpr int UM_STAGES = 4;
 constexpr int UM_THREADS = 128;
+
 template <int K>
 struct UmCfg {
-    static constexpr int A_BYTES = UM_BM * UM_BK * 2;            // 16 KB
+    static constexpr int A_BYTES = 2 * UM_BM * UM_BK * 2;        // 32 KB: 256 rows (or columns) of W
     static constexpr int B_BYTES = 2 * K * UM_BK * 2;            // hi + lo parts
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    // 4 stages up to 32 columns, 3 at 64 (2 x 97 KB: two CTAs per SM)
-    static constexpr int STAGES = K < 64 ? UM_STAGES : 3;
-    static constexpr int SMEM = STAGES * STAGE + 1024;           // + alignment slack
-    static constexpr int TMEM_COLS = K < 32 ? 32 : K;
+    static constexpr int STAGES = 2;
+    static constexpr int SMEM = STAGES * STAGE + 1024;
+    static constexpr int TMEM_COLS = 2 * K < 32 ? 32 : 2 * K;
 };
 
 struct UmShared {
@@ -56,7 +57,7 @@ struct UmShared {
 };
 
 // Shared prologue: 1024-aligned stage ring, barriers, tensor memory.
-template <int K>
+template <int K, typename C = UmCfg<K>>
 __device__ __forceinline__ uint8_t* um_setup(uint8_t* raw, UmShared& sh) {
     const uint32_t base = smem_u32(raw);
     uint8_t* ring = raw + ((1024u - (base & 1023u)) & 1023u);
@@ -72,7 +73,7 @@ __device__ __forceinline__ uint8_t* um_setup(uint8_t* raw, UmShared& sh) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 2) {
-        tmem_alloc(&sh.tmem, UmCfg<K>::TMEM_COLS);
+        tmem_alloc(&sh.tmem, C::TMEM_COLS);
         tc_fence_before();
     }
     __syncthreads();
@@ -83,11 +84,10 @@ __device__ __forceinline__ uint8_t* um_setup(uint8_t* raw, UmShared& sh) {
 // Producer / MMA issue over nk chunks; the two callbacks issue one stage's
 // TMA loads and return its shared-memory descriptors' bases.
 // LoadF(stage_ptr, bar, kb); MmaF(a_base, b_base, first)
-template <int K, typename LoadF, typename MmaF>
+template <int K, typename C = UmCfg<K>, typename LoadF, typename MmaF>
 __device__ __forceinline__ void um_mainloop(uint8_t* ring, UmShared& sh, int nk, int* d_err, LoadF load,
                                             MmaF mma) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    using C = UmCfg<K>;
     if (warp == 0 && lane == 0) {
         int kb = 0;
         for (; kb < nk; kb++) {
@@ -124,22 +124,31 @@ __device__ __forceinline__ void um_mainloop(uint8_t* ring, UmShared& sh, int nk,
     __syncwarp();
 }
 
-// W D: out(i, :) = sum_c W(i, c) (Dt_hi(:, c) + Dt_lo(:, c)) for the 128 rows
-// of this CTA.  A = W tile (K-major: rows of W, 64 columns per stage), B =
-// Dt tile (K-major: 2K rows, 64 columns of W per stage).
+// Both W passes take two 128-row tiles of the product per CTA (M = 256 in
+// two MMAs that share the right-hand-side tile of each stage), so that the
+// right-hand side, which every CTA reads whole (2K x ldw for W D, 2K x
+// rows of its split for W^T B), costs half a byte per byte of W.  Stages
+// of 32 KB of W + 2K x 64 16-bit right-hand sides, two stages (two CTAs
+// per SM at K = 64); the two accumulators side by side in tensor memory
+// (2K columns).
+
+// W D: out(i, :) = sum_c W(i, c) (Dt_hi(:, c) + Dt_lo(:, c)) for the 256
+// rows of this CTA.  A = W tile (K-major: rows of W, 64 columns per stage,
+// one 64 x 256 box: rows 0-127, then 128-255), B = Dt tile (K-major: 2K
+// rows, 64 columns of W per stage).
 template <int K, int BF16>
-__global__ void __launch_bounds__(UM_THREADS) k_umma_wd(const __grid_constant__ CUtensorMap tmW,
-                                                        const __grid_constant__ CUtensorMap tmD, int n, int ldw,
-                                                        float* __restrict__ out, int* d_err) {
+__global__ void __launch_bounds__(UM_THREADS) k_umma_wd2(const __grid_constant__ CUtensorMap tmW,
+                                                         const __grid_constant__ CUtensorMap tmD, int n, int ldw,
+                                                         float* __restrict__ out, int* d_err) {
     extern __shared__ uint8_t um_raw[];
     __shared__ UmShared sh;
     using C = UmCfg<K>;
-    uint8_t* ring = um_setup<K>(um_raw, sh);
+    uint8_t* ring = um_setup<K, C>(um_raw, sh);
     const uint32_t taddr = sh.tmem;
-    const int m0 = blockIdx.x * UM_BM;
+    const int m0 = blockIdx.x * 2 * UM_BM;
     const int nk = (ldw + UM_BK - 1) / UM_BK;
     constexpr uint32_t idesc = idesc_f16(UM_BM, K, BF16, 0);
-    um_mainloop<K>(
+    um_mainloop<K, C>(
         ring, sh, nk, d_err,
         [&](uint8_t* sp, uint64_t* bar, int kb) {
             tma_load_2d(sp, &tmW, bar, kb * UM_BK, m0);
@@ -148,28 +157,35 @@ __global__ void __launch_bounds__(UM_THREADS) k_umma_wd(const __grid_constant__ 
         [&](uint32_t a, uint32_t b, bool first) {
 #pragma unroll
             for (int kk = 0; kk < UM_BK / 16; kk++) {
-                const uint64_t ad = sdesc(a + kk * 32, 16, 1024);
                 const uint64_t bh = sdesc(b + kk * 32, 16, 1024);
                 const uint64_t bl = sdesc(b + K * 128 + kk * 32, 16, 1024);
-                umma_f16(taddr, ad, bh, idesc, (first && kk == 0) ? 0u : 1u);
-                umma_f16(taddr, ad, bl, idesc, 1u);
+#pragma unroll
+                for (int t = 0; t < 2; t++) {
+                    const uint64_t ad = sdesc(a + t * (UM_BM * 128) + kk * 32, 16, 1024);
+                    const uint32_t d = taddr + (uint32_t)(t * K);
+                    umma_f16(d, ad, bh, idesc, (first && kk == 0) ? 0u : 1u);
+                    umma_f16(d, ad, bl, idesc, 1u);
+                }
             }
         });
-    // epilogue: warp w holds rows m0 + 32 w + lane
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     bool ok = mbar_wait(&sh.done, 0, d_err, ERR_WAIT_DONE);
     ok = __syncthreads_and(ok && !*(volatile int*)&sh.fail);  // uniform: tcgen05.ld is warp-collective
     tc_fence_after();
-    const int row = m0 + warp * 32 + lane;
     if (ok) {
 #pragma unroll
-        for (int c0 = 0; c0 < K; c0 += 16) {
-            float v[16];
-            tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (row < n) {
-                float4* o = reinterpret_cast<float4*>(out + (size_t)row * K + c0);
+        for (int t = 0; t < 2; t++) {
+            const int row = m0 + t * UM_BM + warp * 32 + lane;
 #pragma unroll
-                for (int q = 0; q < 4; q++) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            for (int c0 = 0; c0 < K; c0 += 16) {
+                float v[16];
+                tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * K + c0), v);
+                if (row < n) {
+                    float4* o = reinterpret_cast<float4*>(out + (size_t)row * K + c0);
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
             }
         }
     }
@@ -179,59 +195,68 @@ __global__ void __launch_bounds__(UM_THREADS) k_umma_wd(const __grid_constant__ 
 }
 
 // W^T B: part(split, c, :) = sum over the rows i of this split of W(i, c)
-// (Bt_hi(:, i) + Bt_lo(:, i)) for the 128 columns c of this CTA.  A = W^T
-// tile (MN-major: two 64-column boxes of W side by side, 64 rows per stage),
-// B = Bt tile (K-major: 2K rows, 64 rows of W per stage).
+// (Bt_hi(:, i) + Bt_lo(:, i)) for the 256 columns c of this CTA.  A = W^T
+// tiles (MN-major: four 64-column boxes of W side by side, 64 rows per
+// stage; columns 0-127 in boxes 0 and 1, 128-255 in boxes 2 and 3), B = Bt
+// tile (K-major: 2K rows, 64 rows of W per stage).
 template <int K, int BF16>
-__global__ void __launch_bounds__(UM_THREADS) k_umma_wt(const __grid_constant__ CUtensorMap tmW,
-                                                        const __grid_constant__ CUtensorMap tmB, int n, int ldw,
-                                                        int rows_per_split, float* __restrict__ part, int* d_err) {
+__global__ void __launch_bounds__(UM_THREADS) k_umma_wt2(const __grid_constant__ CUtensorMap tmW,
+                                                         const __grid_constant__ CUtensorMap tmB, int n, int ldw,
+                                                         int rows_per_split, float* __restrict__ part, int* d_err) {
     extern __shared__ uint8_t um_raw[];
     __shared__ UmShared sh;
     using C = UmCfg<K>;
-    uint8_t* ring = um_setup<K>(um_raw, sh);
+    constexpr int BOX = UM_BK * 64 * 2;  // one 64-column x 64-row box, 8 KB
+    uint8_t* ring = um_setup<K, C>(um_raw, sh);
     const uint32_t taddr = sh.tmem;
-    const int c0 = blockIdx.x * UM_BM;
+    const int c0 = blockIdx.x * 2 * UM_BM;
     const int i0 = blockIdx.y * rows_per_split;
     const int i1 = min(n, i0 + rows_per_split);
     const int nk = i1 > i0 ? (i1 - i0 + UM_BK - 1) / UM_BK : 0;
     constexpr uint32_t idesc = idesc_f16(UM_BM, K, BF16, 1);
-    um_mainloop<K>(
+    um_mainloop<K, C>(
         ring, sh, nk, d_err,
         [&](uint8_t* sp, uint64_t* bar, int kb) {
             const int i = i0 + kb * UM_BK;
-            tma_load_2d(sp, &tmW, bar, c0, i);
-            tma_load_2d(sp + C::A_BYTES / 2, &tmW, bar, c0 + 64, i);
+#pragma unroll
+            for (int q = 0; q < 4; q++) tma_load_2d(sp + q * BOX, &tmW, bar, c0 + 64 * q, i);
             tma_load_2d(sp + C::A_BYTES, &tmB, bar, i, 0);
         },
         [&](uint32_t a, uint32_t b, bool first) {
 #pragma unroll
             for (int kk = 0; kk < UM_BK / 16; kk++) {
-                // 16 rows of W per MMA: two 8-row groups, 2048 bytes further
-                const uint64_t ad = sdesc(a + kk * 2048, C::A_BYTES / 2, 1024);
                 const uint64_t bh = sdesc(b + kk * 32, 16, 1024);
                 const uint64_t bl = sdesc(b + K * 128 + kk * 32, 16, 1024);
-                umma_f16(taddr, ad, bh, idesc, (first && kk == 0) ? 0u : 1u);
-                umma_f16(taddr, ad, bl, idesc, 1u);
+#pragma unroll
+                for (int t = 0; t < 2; t++) {
+                    // 16 rows of W per MMA: two 8-row groups, 2048 bytes further
+                    const uint64_t ad = sdesc(a + t * 2 * BOX + kk * 2048, BOX, 1024);
+                    const uint32_t d = taddr + (uint32_t)(t * K);
+                    umma_f16(d, ad, bh, idesc, (first && kk == 0) ? 0u : 1u);
+                    umma_f16(d, ad, bl, idesc, 1u);
+                }
             }
         });
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     bool ok = nk > 0 && mbar_wait(&sh.done, 0, d_err, ERR_WAIT_DONE);
     ok = __syncthreads_and(ok && !*(volatile int*)&sh.fail);  // uniform: tcgen05.ld is warp-collective
     tc_fence_after();
-    const int c = c0 + warp * 32 + lane;
-    float* o = part + ((size_t)blockIdx.y * ldw + c) * K;
 #pragma unroll
-    for (int j0 = 0; j0 < K; j0 += 16) {
-        float v[16];
-        if (ok) tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)j0, v);
-        else
+    for (int t = 0; t < 2; t++) {
+        const int c = c0 + t * UM_BM + warp * 32 + lane;
+        float* o = part + ((size_t)blockIdx.y * ldw + c) * K;
 #pragma unroll
-            for (int q = 0; q < 16; q++) v[q] = 0.f;
-        if (c < ldw) {
-            float4* o4 = reinterpret_cast<float4*>(o + j0);
+        for (int j0 = 0; j0 < K; j0 += 16) {
+            float v[16];
+            if (ok) tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * K + j0), v);
+            else
 #pragma unroll
-            for (int q = 0; q < 4; q++) o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                for (int q = 0; q < 16; q++) v[q] = 0.f;
+            if (c < ldw) {
+                float4* o4 = reinterpret_cast<float4*>(o + j0);
+#pragma unroll
+                for (int q = 0; q < 4; q++) o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
         }
     }
     tc_fence_before();
@@ -337,10 +362,14 @@ __global__ void __launch_bounds__(256) k_local_bimg(const int* __restrict__ sub_
 // (two MMAs per step: G_hi against the stacked [X_hi; X_lo], G_lo against X_hi)
 // (error about 2^-22 of each product, the float32 level).  One CTA per
 // 128-row tile (flattened list tile_sub / tile_rt); 6 warps: warp 0 issues
-// the bulk copies (one 16 KB G image and the two right-hand-side images per
-// stage), warp 1 the MMAs, warps 2-5 split the G images in shared memory
-// (hi in place, lo beside it) and read the accumulator back.
+// the bulk copies of the two right-hand-side images of each stage, warp 1
+// the MMAs, and warps 2-5 load the 16 KB G images straight into registers,
+// UL_PF images ahead (so that more of G is in flight than the two shared-
+// memory stages hold: the kernel streams G from HBM once and is bound by
+// how much of it is on the way), split them there and write hi and lo into
+// the stage; they also read the accumulator back.
 constexpr int UL_STAGES = 2;  // 2 stages: two CTAs share an SM
+constexpr int UL_PF = 3;      // G images held in registers ahead of the stage they go to
 constexpr int UL_THREADS = 192;
 template <int K>
 struct UlCfg {
@@ -399,6 +428,7 @@ __global__ void __launch_bounds__(UL_THREADS) k_umma_local(const int* __restrict
     const float* bsrc = lt + (size_t)kc_prefix[s] * 2 * K * 32;
     if (warp == 0) {
         if (lane == 0) {
+            // right-hand-side images through the bulk copy engine
             int kc = 0;
             for (; kc < KC; kc++) {
                 const int st = kc % UL_STAGES;
@@ -409,8 +439,7 @@ __global__ void __launch_bounds__(UL_THREADS) k_umma_local(const int* __restrict
                 }
                 if (*(volatile int*)&sh.fail) break;
                 uint8_t* sp = ring + st * C::STAGE;
-                mbar_expect_tx(&sh.full[st], C::A_BYTES + C::B_BYTES);
-                bulk_load(sp, gsrc + (size_t)kc * 4096, C::A_BYTES, &sh.full[st]);
+                mbar_expect_tx(&sh.full[st], C::B_BYTES);
                 bulk_load(sp + 2 * C::A_BYTES, bsrc + (size_t)kc * 2 * K * 32, C::B_BYTES, &sh.full[st]);
             }
             for (int j = (kc > UL_STAGES ? kc - UL_STAGES : 0); j < kc; j++)
@@ -424,7 +453,8 @@ __global__ void __launch_bounds__(UL_THREADS) k_umma_local(const int* __restrict
             constexpr uint32_t idesc1 = idesc_tf32(128, K);
             for (int kc = 0; kc < KC; kc++) {
                 const int st = kc % UL_STAGES;
-                if (!mbar_wait(&sh.ready[st], (kc / UL_STAGES) & 1, d_err, ERR_WAIT_FULL) ||
+                if (!mbar_wait(&sh.full[st], (kc / UL_STAGES) & 1, d_err, ERR_WAIT_FULL) ||
+                    !mbar_wait(&sh.ready[st], (kc / UL_STAGES) & 1, d_err, ERR_WAIT_FULL) ||
                     *(volatile int*)&sh.fail) {
                     sh.fail = 1;
                     break;
@@ -444,29 +474,49 @@ __global__ void __launch_bounds__(UL_THREADS) k_umma_local(const int* __restrict
             umma_commit(&sh.done);
         }
     } else {
-        // split the G image of every stage: hi = tf32(g) in place, lo = tf32(g - hi)
+        // the G images come straight into registers, UL_PF stages ahead
+        // (thread t holds 16-byte chunks t + 128 u of an image, coalesced),
+        // and are split there: hi = tf32(g) and lo = tf32(g - hi) are
+        // written into the stage once the tensor cores are done with it
         const int t = threadIdx.x - 64;
-        for (int kc = 0; kc < KC; kc++) {
-            const int st = kc % UL_STAGES;
-            if (!mbar_wait(&sh.full[st], (kc / UL_STAGES) & 1, d_err, ERR_WAIT_FULL)) {
-                sh.fail = 1;
-                break;
-            }
-            float4* a4 = reinterpret_cast<float4*>(ring + st * C::STAGE);
-            float4* l4 = reinterpret_cast<float4*>(ring + st * C::STAGE + C::A_BYTES);
+        const float4* g4 = reinterpret_cast<const float4*>(gsrc);
+        float4 g[UL_PF][8];
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const float4 g = a4[t + 128 * u];
-                float4 h, l;
-                h.x = tf32_rna(g.x); l.x = tf32_rna(g.x - h.x);
-                h.y = tf32_rna(g.y); l.y = tf32_rna(g.y - h.y);
-                h.z = tf32_rna(g.z); l.z = tf32_rna(g.z - h.z);
-                h.w = tf32_rna(g.w); l.w = tf32_rna(g.w - h.w);
-                a4[t + 128 * u] = h;
-                l4[t + 128 * u] = l;
+        for (int j = 0; j < UL_PF; j++)
+            if (j < KC)
+#pragma unroll
+                for (int u = 0; u < 8; u++) g[j][u] = __ldcs(g4 + (size_t)j * 1024 + t + 128 * u);
+        bool stop = false;
+        for (int kb = 0; kb < KC && !stop; kb += UL_PF) {
+#pragma unroll
+            for (int j = 0; j < UL_PF; j++) {
+                const int kc = kb + j;
+                if (kc >= KC || stop) break;
+                const int st = kc % UL_STAGES;
+                if (kc >= UL_STAGES && !mbar_wait(&sh.empty[st], ((kc / UL_STAGES) - 1) & 1, d_err, ERR_WAIT_EMPTY)) {
+                    sh.fail = 1;
+                    stop = true;
+                    break;
+                }
+                float4* a4 = reinterpret_cast<float4*>(ring + st * C::STAGE);
+                float4* l4 = reinterpret_cast<float4*>(ring + st * C::STAGE + C::A_BYTES);
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const float4 v = g[j][u];
+                    float4 h, l;
+                    h.x = tf32_rna(v.x); l.x = tf32_rna(v.x - h.x);
+                    h.y = tf32_rna(v.y); l.y = tf32_rna(v.y - h.y);
+                    h.z = tf32_rna(v.z); l.z = tf32_rna(v.z - h.z);
+                    h.w = tf32_rna(v.w); l.w = tf32_rna(v.w - h.w);
+                    a4[t + 128 * u] = h;
+                    l4[t + 128 * u] = l;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+                mbar_arrive(&sh.ready[st]);
+                if (kc + UL_PF < KC)
+#pragma unroll
+                    for (int u = 0; u < 8; u++) g[j][u] = __ldcs(g4 + (size_t)(kc + UL_PF) * 1024 + t + 128 * u);
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
-            mbar_arrive(&sh.ready[st]);
         }
     }
     __syncwarp();
@@ -524,37 +574,37 @@ int split_rows(int n, int splits) {
 }
 
 template <int K, int BF16>
-awg_status launch_wd(const UmmaW& u, const void* Dt, float* out, int* d_err, cudaStream_t s) {
+awg_status launch_wd2(const UmmaW& u, const void* Dt, float* out, int* d_err, cudaStream_t s) {
     CUtensorMap mW, mD;
-    if (!make_map(&mW, u.W, BF16, u.n, u.ldw, u.ldw, UM_BK, UM_BM) ||
+    if (!make_map(&mW, u.W, BF16, u.n, u.ldw, u.ldw, UM_BK, 2 * UM_BM) ||
         !make_map(&mD, Dt, BF16, 2 * K, u.ldw, u.ldw, UM_BK, 2 * K))
         return AWG_ERR_INVALID_ARG;
-    auto kern = k_umma_wd<K, BF16>;
+    auto kern = k_umma_wd2<K, BF16>;
     static bool attr = false;
     if (!attr) {
         AWG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, UmCfg<K>::SMEM));
         attr = true;
     }
-    kern<<<(u.n + UM_BM - 1) / UM_BM, UM_THREADS, UmCfg<K>::SMEM, s>>>(mW, mD, u.n, u.ldw, out, d_err);
+    kern<<<(u.n + 2 * UM_BM - 1) / (2 * UM_BM), UM_THREADS, UmCfg<K>::SMEM, s>>>(mW, mD, u.n, u.ldw, out, d_err);
     AWG_LAUNCH();
     return AWG_OK;
 }
 
 template <int K, int BF16>
-awg_status launch_wt(const UmmaW& u, const void* Bt, int ldb, float* part, int splits, int* d_err,
-                     cudaStream_t s) {
+awg_status launch_wt2(const UmmaW& u, const void* Bt, int ldb, float* part, int splits, int* d_err,
+                      cudaStream_t s) {
     CUtensorMap mW, mB;
     if (!make_map(&mW, u.W, BF16, u.n, u.ldw, u.ldw, 64, UM_BK) ||
         !make_map(&mB, Bt, BF16, 2 * K, u.n, ldb, UM_BK, 2 * K))
         return AWG_ERR_INVALID_ARG;
-    auto kern = k_umma_wt<K, BF16>;
+    auto kern = k_umma_wt2<K, BF16>;
     static bool attr = false;
     if (!attr) {
         AWG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, UmCfg<K>::SMEM));
         attr = true;
     }
     const int rps = split_rows(u.n, splits);
-    const dim3 grid((u.ldw + UM_BM - 1) / UM_BM, (u.n + rps - 1) / rps);
+    const dim3 grid((u.ldw + 2 * UM_BM - 1) / (2 * UM_BM), (u.n + rps - 1) / rps);
     kern<<<grid, UM_THREADS, UmCfg<K>::SMEM, s>>>(mW, mB, u.n, u.ldw, rps, part, d_err);
     AWG_LAUNCH();
     return AWG_OK;
@@ -619,9 +669,9 @@ int umma_wt_splits(int n, int want) {
 
 awg_status umma_wd(const UmmaW& u, int K, const void* Dt, float* out, int* d_err, cudaStream_t s) {
     if (u.n < 1 || u.ldw < 8 || (u.ldw % 8)) return AWG_ERR_INVALID_ARG;
-    if (K == 16) return u.bf16 ? launch_wd<16, 1>(u, Dt, out, d_err, s) : launch_wd<16, 0>(u, Dt, out, d_err, s);
-    if (K == 32) return u.bf16 ? launch_wd<32, 1>(u, Dt, out, d_err, s) : launch_wd<32, 0>(u, Dt, out, d_err, s);
-    if (K == 64) return u.bf16 ? launch_wd<64, 1>(u, Dt, out, d_err, s) : launch_wd<64, 0>(u, Dt, out, d_err, s);
+    if (K == 16) return u.bf16 ? launch_wd2<16, 1>(u, Dt, out, d_err, s) : launch_wd2<16, 0>(u, Dt, out, d_err, s);
+    if (K == 32) return u.bf16 ? launch_wd2<32, 1>(u, Dt, out, d_err, s) : launch_wd2<32, 0>(u, Dt, out, d_err, s);
+    if (K == 64) return u.bf16 ? launch_wd2<64, 1>(u, Dt, out, d_err, s) : launch_wd2<64, 0>(u, Dt, out, d_err, s);
     return AWG_ERR_INVALID_ARG;
 }
 
@@ -629,14 +679,14 @@ awg_status umma_wt(const UmmaW& u, int K, const void* Bt, int ldb, float* part, 
                    cudaStream_t s) {
     if (u.n < 1 || u.ldw < 8 || (u.ldw % 8) || (ldb % 8) || splits < 1) return AWG_ERR_INVALID_ARG;
     if (K == 16)
-        return u.bf16 ? launch_wt<16, 1>(u, Bt, ldb, part, splits, d_err, s)
-                      : launch_wt<16, 0>(u, Bt, ldb, part, splits, d_err, s);
+        return u.bf16 ? launch_wt2<16, 1>(u, Bt, ldb, part, splits, d_err, s)
+                      : launch_wt2<16, 0>(u, Bt, ldb, part, splits, d_err, s);
     if (K == 32)
-        return u.bf16 ? launch_wt<32, 1>(u, Bt, ldb, part, splits, d_err, s)
-                      : launch_wt<32, 0>(u, Bt, ldb, part, splits, d_err, s);
+        return u.bf16 ? launch_wt2<32, 1>(u, Bt, ldb, part, splits, d_err, s)
+                      : launch_wt2<32, 0>(u, Bt, ldb, part, splits, d_err, s);
     if (K == 64)
-        return u.bf16 ? launch_wt<64, 1>(u, Bt, ldb, part, splits, d_err, s)
-                      : launch_wt<64, 0>(u, Bt, ldb, part, splits, d_err, s);
+        return u.bf16 ? launch_wt2<64, 1>(u, Bt, ldb, part, splits, d_err, s)
+                      : launch_wt2<64, 0>(u, Bt, ldb, part, splits, d_err, s);
     return AWG_ERR_INVALID_ARG;
 }
 
