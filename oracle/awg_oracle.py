@@ -620,18 +620,26 @@ def build_W(st: Setup) -> None:
         st.F = np.zeros((0, 0))
         st.F_cho = None
         return
-    if st.dense:
+    if st.dense or st.n * st.n_minus <= _W_BLOCKED_ABOVE:
         st.W = solve_A_plus(st, st.Vhat.toarray())
+        F = st.W.T @ (st.A @ st.W)
     else:
+        # F = W^T (A W), a block of columns of A W at a time (only one
+        # n x n_- array is held)
         st.W = _solve_A_plus_Vhat(st)
-    # F = W^T (A W), a block of columns of A W at a time (only one n x n_-
-    # array is held)
-    F = np.empty((st.n_minus, st.n_minus))
-    for j0 in range(0, st.n_minus, 512):
-        j1 = min(st.n_minus, j0 + 512)
-        F[:, j0:j1] = st.W.T @ (st.A @ st.W[:, j0:j1])
+        F = np.empty((st.n_minus, st.n_minus))
+        for j0 in range(0, st.n_minus, 512):
+            j1 = min(st.n_minus, j0 + 512)
+            F[:, j0:j1] = st.W.T @ (st.A @ st.W[:, j0:j1])
     st.F = 0.5 * (F + F.T)
     st.F_cho = sla.cho_factor(st.F, lower=True)
+
+
+# Problems whose n x n_- arrays hold more values than this take the blocked
+# route below (same steps; the rounding of the blocked products differs in
+# the last bits): the elasticity workload's oracle run (n = 295 680,
+# n_- = 6659) needs it to fit in 62 GB of host memory.
+_W_BLOCKED_ABOVE = 1 << 28
 
 
 def _solve_A_plus_Vhat(st: Setup) -> np.ndarray:
