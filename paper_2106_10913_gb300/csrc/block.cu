@@ -555,41 +555,38 @@ template <> struct V16<double> {
     using type = double2;
     static __device__ __forceinline__ double get(const double2& v, int i) { return i == 0 ? v.x : v.y; }
 };
-constexpr int TG2_TJ = 32;
-template <typename T, int K>
-__global__ void __launch_bounds__(256) kb_tgemv2(const int* __restrict__ sub_ptr, const int* __restrict__ sub_idx,
-                                                 const int* __restrict__ colptr, const int64_t* __restrict__ boff,
-                                                 const T* __restrict__ B, const T* __restrict__ X, int ncol_total,
-                                                 T* __restrict__ part) {
-    constexpr int TG2_ROWS = sizeof(T) == 8 ? 32 : 64;  // rows per chunk (about 24 KB of shared memory)
-    constexpr int BP = TG2_TJ + 16 / (int)sizeof(T);     // padded row of bs (16-byte multiple)
-    __shared__ __align__(16) T xs[TG2_ROWS][K];
-    __shared__ __align__(16) T bs[TG2_ROWS][BP];
-    constexpr int JG = 256 / K, JU = TG2_TJ / JG;
+constexpr int TG2_TJ = 32;  // columns q per pass (at most)
+template <typename T> struct TG2 {
+    static constexpr int ROWS = sizeof(T) == 8 ? 32 : 64;      // rows per chunk (about 24 KB of shared memory)
+    static constexpr int BP = TG2_TJ + 16 / (int)sizeof(T);    // padded row of bs (16-byte multiple)
+};
+// One block's work with TJ columns q per pass: TJ = 16 for subdomains with
+// at most 16 columns (half the shared loads and FMAs of a 32-column pass,
+// most of which would multiply padding), 32 otherwise
+template <typename T, int K, int TJ>
+__device__ __forceinline__ void tgemv2_body(T (*xs)[K], T (*bs)[TG2<T>::BP], const int* __restrict__ sub_idx,
+                                            const T* __restrict__ Bs, const T* __restrict__ X, int p0, int m,
+                                            int c0, int nc, int pa, int pb, int rs, int ncol_total,
+                                            T* __restrict__ part) {
+    constexpr int ROWS = TG2<T>::ROWS;
+    constexpr int JG = 256 / K, JU = TJ / JG;
     constexpr int V4 = K * (int)sizeof(T) / 16;
     constexpr int BV16 = 16 / (int)sizeof(T);            // values per 16-byte load
     constexpr int BV = JU % BV16 == 0 ? BV16 : 1;         // (scalar loads for narrow column blocks)
-    const int s = blockIdx.x, rs = blockIdx.y;
-    const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
-    const int c0 = colptr[s], nc = colptr[s + 1] - c0;
-    if (nc == 0) return;
-    const int plen = (m + gridDim.y - 1) / gridDim.y;
-    const int pa = rs * plen, pb = min(m, pa + plen);
     const int c = threadIdx.x % K, jb = (threadIdx.x / K) * JU;
-    const T* Bs = B + boff[s];
-    for (int j0 = 0; j0 < nc; j0 += TG2_TJ) {
-        const int jn = min(TG2_TJ, nc - j0);
+    for (int j0 = 0; j0 < nc; j0 += TJ) {
+        const int jn = min(TJ, nc - j0);
         T acc[JU];
 #pragma unroll
         for (int u = 0; u < JU; u++) acc[u] = 0;
-        for (int q0 = pa; q0 < pb; q0 += TG2_ROWS) {
-            const int pn = min(TG2_ROWS, pb - q0);
+        for (int q0 = pa; q0 < pb; q0 += ROWS) {
+            const int pn = min(ROWS, pb - q0);
             __syncthreads();
-            for (int e = threadIdx.x; e < TG2_TJ * TG2_ROWS; e += 256) {
-                const int jj = e / TG2_ROWS, pp = e % TG2_ROWS;
+            for (int e = threadIdx.x; e < TJ * ROWS; e += 256) {
+                const int jj = e / ROWS, pp = e % ROWS;
                 bs[pp][jj] = (jj < jn && pp < pn) ? Bs[(size_t)(j0 + jj) * m + q0 + pp] : (T)0;
             }
-            for (int e = threadIdx.x; e < TG2_ROWS * V4; e += 256) {
+            for (int e = threadIdx.x; e < ROWS * V4; e += 256) {
                 const int pp = e / V4, cc = e % V4;
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (pp < pn) v = reinterpret_cast<const float4*>(X + (size_t)sub_idx[p0 + q0 + pp] * K)[cc];
@@ -597,7 +594,7 @@ __global__ void __launch_bounds__(256) kb_tgemv2(const int* __restrict__ sub_ptr
             }
             __syncthreads();
 #pragma unroll 4
-            for (int pp = 0; pp < TG2_ROWS; pp++) {
+            for (int pp = 0; pp < ROWS; pp++) {
                 const T x = xs[pp][c];
                 if constexpr (BV == BV16) {
                     using V = typename V16<T>::type;
@@ -619,6 +616,26 @@ __global__ void __launch_bounds__(256) kb_tgemv2(const int* __restrict__ sub_ptr
             if (jj < jn) part[((size_t)rs * ncol_total + c0 + j0 + jj) * K + c] = acc[u];
         }
     }
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(256) kb_tgemv2(const int* __restrict__ sub_ptr, const int* __restrict__ sub_idx,
+                                                 const int* __restrict__ colptr, const int64_t* __restrict__ boff,
+                                                 const T* __restrict__ B, const T* __restrict__ X, int ncol_total,
+                                                 T* __restrict__ part) {
+    __shared__ __align__(16) T xs[TG2<T>::ROWS][K];
+    __shared__ __align__(16) T bs[TG2<T>::ROWS][TG2<T>::BP];
+    const int s = blockIdx.x, rs = blockIdx.y;
+    const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
+    const int c0 = colptr[s], nc = colptr[s + 1] - c0;
+    if (nc == 0) return;
+    const int plen = (m + gridDim.y - 1) / gridDim.y;
+    const int pa = rs * plen, pb = min(m, pa + plen);
+    const T* Bs = B + boff[s];
+    if (nc <= 16)
+        tgemv2_body<T, K, 16>(xs, bs, sub_idx, Bs, X, p0, m, c0, nc, pa, pb, rs, ncol_total, part);
+    else
+        tgemv2_body<T, K, TG2_TJ>(xs, bs, sub_idx, Bs, X, p0, m, c0, nc, pa, pb, rs, ncol_total, part);
 }
 
 template <typename T, int K>
