@@ -302,6 +302,15 @@ def block_bytes(info, K, prec):
     return per, iter_bytes
 
 
+# DRAM bytes per launch measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) over the algorithmic bytes of the same launch, on
+# the 320x320 channel case of the 64-column float16-W block solve
+# (profiles/block64_local_w_dram_channels320.md); the traffic of a launch
+# on another size is this ratio times its algorithmic bytes (the traffic of
+# these streaming kernels grows in proportion to the operator they read)
+DRAM_RATIO_K64_FP16 = {"local": 805319680 / 798215168, "wt": 251152640 / 247659520, "wd": 237962752 / 247659520}
+
+
 def roofline_of(form, info):
     """Roofline of the dominant kernel class of a timed form (largest summed
     CUDA-event time in one extra solve with the apply's streams serialised):
@@ -355,6 +364,10 @@ def roofline_of(form, info):
            "kernel_share_of_solve": prof["ms"][dom] / prof["profiled_solve_ms"], "traffic": None,
            "timing": "CUDA events around each launch of one extra solve run with the apply's streams "
                      "serialised (AWG_PROF_SERIAL), after the timed steps"}
+    if form["block"] and K == 64 and prec == MIXED_FP16 and dom in DRAM_RATIO_K64_FP16:
+        out["traffic"] = DRAM_RATIO_K64_FP16[dom] * units
+        out["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum on the 320x320 case, scaled "
+                                 "by the algorithmic bytes of this launch")
     achieved = units / (per_launch_ms / 1000.0) / 1e9
     out.update({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "algorithmic_bytes_per_launch": units, "peak_source": f"{hbm_src} HBM copy bandwidth"})
