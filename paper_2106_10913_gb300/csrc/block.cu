@@ -478,72 +478,15 @@ __global__ void __launch_bounds__(256) kb_aplus(int n, const int* __restrict__ r
 
 // C_s(q, :) = wsign w_q sum_p B_s(p, q) X(idx_s(p), :) for every subdomain s
 // (B_s n^s x nc_s column-major; block-sparse Z^T X and V_-^T X).  Block
-// (s, qc, ps) takes the columns q of chunk qc (16 per chunk) and the local
-// positions of split ps, in chunks of 64 staged in shared memory (B_s rows
-// coalesced along p, X rows gathered whole with 16-byte loads); each thread
-// owns K / 16 outputs (q, c).  Partial sums go to part[ps][colptr[s] + q][c];
-// kb_tg_sum adds the TG_PS splits in order.
-constexpr int KB_TG_C = 16, TG_PC = 64, TG_PS = 8;
-template <typename T, int K>
-__global__ void __launch_bounds__(256) kb_tgemv(const int* __restrict__ sub_ptr, const int* __restrict__ sub_idx,
-                                                const int* __restrict__ colptr, const int64_t* __restrict__ boff,
-                                                const T* __restrict__ B, const T* __restrict__ X, int ncol_total,
-                                                T* __restrict__ part) {
-    __shared__ T bs[TG_PC][KB_TG_C + 1];
-    __shared__ __align__(16) T xs[TG_PC][K];
-    constexpr int U = K / 16;
-    const int s = blockIdx.x, cb = blockIdx.y * KB_TG_C, ps = blockIdx.z;
-    const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
-    const int c0 = colptr[s], nc = colptr[s + 1] - c0;
-    if (cb >= nc) return;
-    const int kc = min(KB_TG_C, nc - cb);
-    const int plen = (m + TG_PS - 1) / TG_PS;
-    const int pa = ps * plen, pb = min(m, pa + plen);
-    const T* Bs = B + boff[s] + (size_t)cb * m;
-    T acc[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) acc[u] = 0;
-    for (int q0 = pa; q0 < pb; q0 += TG_PC) {
-        const int pn = min(TG_PC, pb - q0);
-        __syncthreads();
-        for (int e = threadIdx.x; e < KB_TG_C * TG_PC; e += 256) {
-            const int q = e / TG_PC, pp = e % TG_PC;
-            bs[pp][q] = (q < kc && pp < pn) ? Bs[(size_t)q * m + q0 + pp] : (T)0;
-        }
-        // whole rows of X, 16 bytes per load
-        constexpr int V4 = K * (int)sizeof(T) / 16;
-        for (int e = threadIdx.x; e < TG_PC * V4; e += 256) {
-            const int pp = e / V4, cc = e % V4;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (pp < pn) v = reinterpret_cast<const float4*>(X + (size_t)sub_idx[p0 + q0 + pp] * K)[cc];
-            reinterpret_cast<float4*>(&xs[pp][0])[cc] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int o = threadIdx.x + 256 * u, q = o / K, c = o % K;
-            T a = acc[u];
-#pragma unroll 8
-            for (int pp = 0; pp < TG_PC; pp++) a = fma(bs[pp][q], xs[pp][c], a);
-            acc[u] = a;
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-        const int o = threadIdx.x + 256 * u, q = o / K, c = o % K;
-        if (q < kc) part[((size_t)ps * ncol_total + c0 + cb + q) * K + c] = acc[u];
-    }
-}
-
-// C(j, c) = wsign w_j sum_ps part[ps][j][c]  (fixed order)
-// Partial sums of C(c0_s + j, :) = sum_p B_s(p, j) X(idx_s(p), :) over the
-// rows [pa, pb) of split `blockIdx.y` of subdomain s = blockIdx.x, for every
-// column j of B_s (tiles of 32): each chunk of rows of X is gathered once
-// (16-byte loads of whole rows) and serves all columns of B_s.  Thread t
-// owns column c = t % K of X and JU = 32 / (256 / K) consecutive columns of
-// B_s from (t / K) JU, read from shared memory as 16-byte vectors (two
-// shared loads feed eight float32 FMAs; one shared load per FMA left the
-// kernel bound by its load/store pipe).
+// (s, ps) of kb_tgemv2 takes the local positions of split ps and the columns
+// of B_s in passes of 16 or 32: each chunk of rows of X is gathered once
+// into shared memory (16-byte loads of whole rows) and serves all columns of
+// the pass; thread t owns column c = t % K of X and TJ / (256 / K)
+// consecutive columns of B_s, read from shared memory as 16-byte vectors
+// (one shared load per FMA left the kernel bound by its load/store pipe).
+// Partial sums go to part[ps][colptr[s] + q][c]; kb_tg_sum adds the TG_PS
+// splits in order.
+constexpr int TG_PS = 8;
 template <typename T> struct V16;
 template <> struct V16<float> {
     using type = float4;
