@@ -427,7 +427,7 @@ __global__ void kb_cvt(size_t len, const TI* __restrict__ a, TO* __restrict__ b)
 
 // ------------------------------------------------------ preconditioner ops
 // Y = Yin + sign (A X + sum over the copies (s, q) of i of V_s(q, :) cm_s)
-// (A_+ = A + A_-, Thm. 2), cm_s = |Lambda^s_-| V^s_-^T R^s X from kb_tgemv
+// (A_+ = A + A_-, Thm. 2), cm_s = |Lambda^s_-| V^s_-^T R^s X from kb_tgemv2
 template <typename T, int K>
 __global__ void __launch_bounds__(256) kb_aplus(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                 const T* __restrict__ a, const T* __restrict__ X,
