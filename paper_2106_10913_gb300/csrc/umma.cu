@@ -368,22 +368,31 @@ __global__ void __launch_bounds__(256) k_local_bimg(const int* __restrict__ sub_
 // memory stages hold: the kernel streams G from HBM once and is bound by
 // how much of it is on the way), split them there and write hi and lo into
 // the stage; they also read the accumulator back.
-constexpr int UL_STAGES = 2;  // 2 stages: two CTAs share an SM
+constexpr int UL_STAGES = 2;  // split G stages (hi + lo): two CTAs share an SM
+constexpr int UL_BMAX = 4;    // right-hand-side stages (at most)
 constexpr int UL_PF = 3;      // G images held in registers ahead of the stage they go to
 constexpr int UL_THREADS = 192;
+// The right-hand-side images have a ring of their own, deeper than the
+// split G stages where shared memory allows (four stages up to 32 columns),
+// so that their copies from L2 are issued further ahead of the MMAs that
+// read them; at 64 columns two CTAs per SM leave room for two (two split
+// G stages of 32 KB and three right-hand-side stages of 16 KB exceed half
+// of the SM's 228 KB by the alignment slack).
 template <int K>
 struct UlCfg {
     static constexpr int A_BYTES = 128 * 32 * 4;          // 16 KB G image
     static constexpr int B_BYTES = 2 * K * 32 * 4;        // hi + lo right-hand-side images
-    static constexpr int STAGE = 2 * A_BYTES + B_BYTES;   // G hi, G lo, B
-    static constexpr int SMEM = UL_STAGES * STAGE + 1024;
+    static constexpr int A_STAGE = 2 * A_BYTES;           // G hi, G lo
+    static constexpr int B_STAGES = K == 64 ? 2 : UL_BMAX;
+    static constexpr int SMEM = UL_STAGES * A_STAGE + B_STAGES * B_BYTES + 1024;
     static constexpr int TMEM_COLS = 2 * K < 32 ? 32 : 2 * K;  // [hi*hi + lo*hi | hi*lo]
 };
 
 struct UlShared {
-    uint64_t full[UL_STAGES];
-    uint64_t ready[UL_STAGES];
-    uint64_t empty[UL_STAGES];
+    uint64_t full[UL_BMAX];      // right-hand-side stage landed
+    uint64_t bempty[UL_BMAX];    // right-hand-side stage read by the MMAs
+    uint64_t ready[UL_STAGES];   // split G stage written
+    uint64_t empty[UL_STAGES];   // split G stage read by the MMAs
     uint64_t done;
     uint32_t tmem;
     int fail;
@@ -406,11 +415,16 @@ __global__ void __launch_bounds__(UL_THREADS) k_umma_local(const int* __restrict
     const int s = tile_sub[blockIdx.x], rt = tile_rt[blockIdx.x];
     const int p0 = sub_ptr[s], m = sub_ptr[s + 1] - p0;
     const int KC = (m + 31) / 32;
+    constexpr int BS = C::B_STAGES;
+    uint8_t* bring = ring + UL_STAGES * C::A_STAGE;
     if (threadIdx.x == 0) {
         for (int i = 0; i < UL_STAGES; i++) {
-            mbar_init(&sh.full[i], 1);
             mbar_init(&sh.ready[i], 128);
             mbar_init(&sh.empty[i], 1);
+        }
+        for (int i = 0; i < BS; i++) {
+            mbar_init(&sh.full[i], 1);
+            mbar_init(&sh.bempty[i], 1);
         }
         mbar_init(&sh.done, 1);
         sh.fail = 0;
@@ -431,19 +445,17 @@ __global__ void __launch_bounds__(UL_THREADS) k_umma_local(const int* __restrict
             // right-hand-side images through the bulk copy engine
             int kc = 0;
             for (; kc < KC; kc++) {
-                const int st = kc % UL_STAGES;
-                if (kc >= UL_STAGES &&
-                    !mbar_wait(&sh.empty[st], ((kc / UL_STAGES) - 1) & 1, d_err, ERR_WAIT_EMPTY)) {
+                const int bt = kc % BS;
+                if (kc >= BS && !mbar_wait(&sh.bempty[bt], ((kc / BS) - 1) & 1, d_err, ERR_WAIT_EMPTY)) {
                     sh.fail = 1;
                     break;
                 }
                 if (*(volatile int*)&sh.fail) break;
-                uint8_t* sp = ring + st * C::STAGE;
-                mbar_expect_tx(&sh.full[st], C::B_BYTES);
-                bulk_load(sp + 2 * C::A_BYTES, bsrc + (size_t)kc * 2 * K * 32, C::B_BYTES, &sh.full[st]);
+                mbar_expect_tx(&sh.full[bt], C::B_BYTES);
+                bulk_load(bring + bt * C::B_BYTES, bsrc + (size_t)kc * 2 * K * 32, C::B_BYTES, &sh.full[bt]);
             }
-            for (int j = (kc > UL_STAGES ? kc - UL_STAGES : 0); j < kc; j++)
-                mbar_wait(&sh.full[j % UL_STAGES], (j / UL_STAGES) & 1, d_err, ERR_WAIT_FULL);
+            for (int j = (kc > BS ? kc - BS : 0); j < kc; j++)
+                mbar_wait(&sh.full[j % BS], (j / BS) & 1, d_err, ERR_WAIT_FULL);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -452,16 +464,16 @@ __global__ void __launch_bounds__(UL_THREADS) k_umma_local(const int* __restrict
             constexpr uint32_t idesc2 = idesc_tf32(128, 2 * K);
             constexpr uint32_t idesc1 = idesc_tf32(128, K);
             for (int kc = 0; kc < KC; kc++) {
-                const int st = kc % UL_STAGES;
-                if (!mbar_wait(&sh.full[st], (kc / UL_STAGES) & 1, d_err, ERR_WAIT_FULL) ||
+                const int st = kc % UL_STAGES, bt = kc % BS;
+                if (!mbar_wait(&sh.full[bt], (kc / BS) & 1, d_err, ERR_WAIT_FULL) ||
                     !mbar_wait(&sh.ready[st], (kc / UL_STAGES) & 1, d_err, ERR_WAIT_FULL) ||
                     *(volatile int*)&sh.fail) {
                     sh.fail = 1;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t a = smem_u32(ring + st * C::STAGE);
-                const uint32_t al = a + C::A_BYTES, b = a + 2 * C::A_BYTES;
+                const uint32_t a = smem_u32(ring + st * C::A_STAGE);
+                const uint32_t al = a + C::A_BYTES, b = smem_u32(bring + bt * C::B_BYTES);
 #pragma unroll
                 for (int kk = 0; kk < 4; kk++) {  // 8 TF32 values (32 bytes) per MMA
                     const uint64_t ah = sdesc(a + kk * 32, 16, 1024), alo = sdesc(al + kk * 32, 16, 1024);
@@ -469,7 +481,8 @@ __global__ void __launch_bounds__(UL_THREADS) k_umma_local(const int* __restrict
                     umma_tf32(taddr, ah, bb, idesc2, (kc == 0 && kk == 0) ? 0u : 1u);
                     umma_tf32(taddr, alo, bb, idesc1, 1u);
                 }
-                umma_commit(&sh.empty[st]);
+                umma_commit(&sh.empty[st]);   // the split G stage is free once these MMAs are done,
+                umma_commit(&sh.bempty[bt]);  // and so is the right-hand-side stage
             }
             umma_commit(&sh.done);
         }
@@ -498,8 +511,8 @@ __global__ void __launch_bounds__(UL_THREADS) k_umma_local(const int* __restrict
                     stop = true;
                     break;
                 }
-                float4* a4 = reinterpret_cast<float4*>(ring + st * C::STAGE);
-                float4* l4 = reinterpret_cast<float4*>(ring + st * C::STAGE + C::A_BYTES);
+                float4* a4 = reinterpret_cast<float4*>(ring + st * C::A_STAGE);
+                float4* l4 = reinterpret_cast<float4*>(ring + st * C::A_STAGE + C::A_BYTES);
 #pragma unroll
                 for (int u = 0; u < 8; u++) {
                     const float4 v = g[j][u];
