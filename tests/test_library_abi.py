@@ -120,3 +120,15 @@ def test_checkpoint_file_errors(lib, tmp_path):
         h = ctypes.c_void_p(123)
         assert lib.awg_load(str(f).encode(), None, ctypes.byref(h)) == 11, name
         assert not h.value, name
+
+
+def test_binding_constants_match_header():
+    """The binding's profile classes and mask bits are the header's values."""
+    import re
+    from paper_2106_10913_gb300 import awg as A
+    src = open(os.path.join(ROOT, "include", "awg.h")).read()
+    vals = {m.group(1): m.group(2) for m in re.finditer(r"(AWG_PROF_[A-Z]+)\s*=\s*([^,}]+?)\s*[,}]", src)}
+    assert int(eval(vals["AWG_PROF_SERIAL"])) == A.PROF_SERIAL
+    assert int(eval(vals["AWG_PROF_COUNT"])) == A.PROF_COUNT
+    for i, name in enumerate(A.PROF_NAMES):
+        assert int(vals["AWG_PROF_" + name.upper()]) == i, name
