@@ -226,6 +226,21 @@ def oracle_sample(steps: int = 1, warmup: int = 0):
             "s_per_iteration": t_it, "solve_s": solve_s, "step_s": t1}
 
 
+def oracle_sample_one_thread():
+    """The same oracle timing with one host thread: a child process with the
+    BLAS thread counts set to 1 before numpy loads (solves/s, or None if the
+    child fails)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json, bench; r = bench.oracle_sample(1); "
+            "print(json.dumps({'value': r['value'], 's_per_iteration': r['s_per_iteration']}))")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             cwd=os.path.dirname(os.path.abspath(__file__)), timeout=600)
+        return json.loads(out.stdout.strip().splitlines()[-1]) if out.returncode == 0 else None
+    except Exception:
+        return None
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -593,6 +608,7 @@ def run_awg(args):
 
     if rank == 0:
         cb = oracle_sample(1) if (world == 1 and not args.no_cpu_baseline) else None
+        cb1 = oracle_sample_one_thread() if cb else None
         line = {
             "metric": METRIC, "value": best["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms_per_step"],
@@ -624,8 +640,8 @@ def run_awg(args):
             "speedup_vs_plain_fp64": (best["value"] / forms["fp64"]["value"]) if "fp64" in forms else None,
             "batched_problems": batch,
             "roofline": roofline,
-            "cpu_baseline": ({k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
-                             if cb else None),
+            "cpu_baseline": ({**{k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                              "one_thread": cb1} if cb else None),
             "e2e": e2e,
             "gpu_launches": int(best["prof"]["launches"]),
             "clocks": best["clocks"],
