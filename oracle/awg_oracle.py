@@ -628,8 +628,8 @@ def build_W(st: Setup) -> None:
         # n x n_- array is held)
         st.W = _solve_A_plus_Vhat(st)
         F = np.empty((st.n_minus, st.n_minus))
-        for j0 in range(0, st.n_minus, 512):
-            j1 = min(st.n_minus, j0 + 512)
+        for j0 in range(0, st.n_minus, _W_BLOCK[2]):
+            j1 = min(st.n_minus, j0 + _W_BLOCK[2])
             F[:, j0:j1] = st.W.T @ (st.A @ st.W[:, j0:j1])
     st.F = 0.5 * (F + F.T)
     st.F_cho = sla.cho_factor(st.F, lower=True)
@@ -640,6 +640,8 @@ def build_W(st: Setup) -> None:
 # the last bits): the elasticity workload's oracle run (n = 295 680,
 # n_- = 6659) needs it to fit in 62 GB of host memory.
 _W_BLOCKED_ABOVE = 1 << 28
+# block sizes of that route: columns of A^-1 U, rows of the update, columns of A W
+_W_BLOCK = (256, 16384, 512)
 
 
 def _solve_A_plus_Vhat(st: Setup) -> np.ndarray:
@@ -655,13 +657,13 @@ def _solve_A_plus_Vhat(st: Setup) -> np.ndarray:
         st.info["A_lu"] = lu
     U = st.Vhat.tocsc()
     X = np.empty((st.n, st.n_minus), order="F")
-    for j0 in range(0, st.n_minus, 256):  # A^-1 U, a block of columns at a time
-        j1 = min(st.n_minus, j0 + 256)
+    for j0 in range(0, st.n_minus, _W_BLOCK[0]):  # A^-1 U, a block of columns at a time
+        j1 = min(st.n_minus, j0 + _W_BLOCK[0])
         X[:, j0:j1] = lu.solve(U[:, j0:j1].toarray())
     cap = np.diag(1.0 / Lambda_strict(st)) + np.asarray(U.T @ X)
     G = np.linalg.solve(cap, np.asarray(U.T @ X))
-    for i0 in range(0, st.n, 16384):  # X - X G, a block of rows at a time
-        i1 = min(st.n, i0 + 16384)
+    for i0 in range(0, st.n, _W_BLOCK[1]):  # X - X G, a block of rows at a time
+        i1 = min(st.n, i0 + _W_BLOCK[1])
         X[i0:i1] -= X[i0:i1] @ G
     return X
 

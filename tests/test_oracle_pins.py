@@ -620,3 +620,21 @@ def test_pcg_matches_scipy_cg():
     ev = np.sort(np.real(np.linalg.eigvals(Hd @ A.toarray())))
     lo, hi = O.lanczos_extremes(res.alphas, res.betas)
     assert abs(hi - ev[-1]) < 1e-3 * ev[-1]
+
+
+def test_blocked_W_route_matches_dense_solve(monkeypatch):
+    """The blocked route for W and F (large problems: A^-1 U by columns, the
+    Woodbury update by rows, F by columns) against W = A_+^-1 Vhat from the
+    densely assembled A_+ and F = W^T A W formed whole, on a problem small
+    enough for both: the same W and F to rounding."""
+    from oracle import awg_oracle as OA
+    p = gi.channels2d(40, q=4, nchan=4, contrast=1e3, seed=3, overlap=2, tau=0.1)
+    monkeypatch.setattr(OA, "_W_BLOCKED_ABOVE", 0)
+    monkeypatch.setattr(OA, "_W_BLOCK", (7, 300, 5))  # several blocks of each kind
+    st = O.setup_problem(p, dense=False)
+    assert st.n_minus > 0
+    Ap = O.assemble_dense(st, "plus")
+    W = np.linalg.solve(Ap, st.Vhat.toarray())
+    F = W.T @ (st.A @ W)
+    assert np.max(np.abs(st.W - W)) <= 1e-10 * np.max(np.abs(W))
+    assert np.max(np.abs(st.F - 0.5 * (F + F.T))) <= 1e-10 * np.max(np.abs(F))
