@@ -364,10 +364,10 @@ __global__ void __launch_bounds__(256) k_local_bimg(const int* __restrict__ sub_
 // 128-row tile (flattened list tile_sub / tile_rt); 6 warps: warp 0 issues
 // the bulk copies of the two right-hand-side images of each stage, warp 1
 // the MMAs, and warps 2-5 load the 16 KB G images straight into registers,
-// UL_PF images ahead (so that more of G is in flight than the two shared-
-// memory stages hold: the kernel streams G from HBM once and is bound by
-// how much of it is on the way), split them there and write hi and lo into
-// the stage; they also read the accumulator back.
+// UL_PF images ahead of the stage they go to (G is read from HBM once, and
+// its loads are in flight while earlier stages are split and multiplied),
+// split them there and write hi and lo into the stage; they also read the
+// accumulator back.
 constexpr int UL_STAGES = 2;  // split G stages (hi + lo): two CTAs share an SM
 constexpr int UL_BMAX = 4;    // right-hand-side stages (at most)
 constexpr int UL_PF = 3;      // G images held in registers ahead of the stage they go to
