@@ -230,7 +230,7 @@ def _nearest_centroid(X: np.ndarray, cent: np.ndarray, cand: int = 8) -> np.ndar
     from scipy.spatial import cKDTree
     k = cent.shape[0]
     cand = min(cand, k)
-    _, nb = cKDTree(cent).query(X, k=cand)
+    _, nb = cKDTree(cent).query(X, k=cand, workers=-1)  # per-point queries, on every host core
     nb = nb.reshape(X.shape[0], cand)
     d2 = np.zeros(nb.shape)
     for ax in range(X.shape[1]):
@@ -241,9 +241,10 @@ def _nearest_centroid(X: np.ndarray, cent: np.ndarray, cand: int = 8) -> np.ndar
     out = np.where(d2 == best[:, None], nb, k).min(axis=1)
     if cand < k:
         hard = np.nonzero(d2[:, -1] <= best)[0]
-        for i in hard:
-            dd = ((X[i][None, :] - cent) ** 2).sum(axis=1)
-            out[i] = int(np.argmin(dd))
+        for h0 in range(0, hard.size, 4096):  # brute force, a block of points at a time
+            hs = hard[h0:h0 + 4096]
+            dd = ((X[hs][:, None, :] - cent[None, :, :]) ** 2).sum(axis=2)
+            out[hs] = np.argmin(dd, axis=1)
     return out.astype(np.int64)
 
 
